@@ -1,0 +1,216 @@
+/*
+ * gpubp: GB300-native bound propagation, double probing and fix-and-propagate for MILP.
+ *
+ * C ABI.  Plain pointers and sizes; no C++ or framework types cross it.  Every entry point
+ * returns an int status: BP_OK (0) or a negative BP_ERR_* code; on error,
+ * bp_last_error() returns a thread-local message.  Infeasibility of a problem is a RESULT
+ * (a status field of the result struct), never an error code.
+ *
+ * Problem form (paper, Section 1): minimise c.x subject to
+ *     sum_i a_ki x_i <= g_k   for every row k,
+ *     l_i <= x_i <= u_i,      x_i integer where is_int[i] != 0.
+ * Only "<=" rows exist; an equality is passed as two rows (a.x <= b, -a.x <= -b).
+ * |value| >= 1e20 means infinite.  Feasibility tolerance: 1e-6 absolute (Section 3).
+ *
+ * Streams: every call is enqueued on the caller's cudaStream_t (passed as void*, NULL means
+ * the legacy default stream) and returns without a host synchronisation unless stated.
+ * One problem handle must not be used by two streams at the same time.
+ * Device pointers must be device-accessible addresses on the current CUDA device.
+ */
+#ifndef GPUBP_H
+#define GPUBP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+#define BP_OK 0
+#define BP_ERR_INVALID (-1)   /* malformed input: see bp_last_error() */
+#define BP_ERR_CUDA (-2)      /* a CUDA runtime call failed */
+#define BP_ERR_OOM (-3)       /* device allocation failed */
+#define BP_ERR_CAPACITY (-4)  /* an output buffer is too small; the needed size is reported */
+#define BP_ERR_TIMEOUT (-5)   /* a device-side wait gave up (co-residency lost); no hang */
+
+/* result statuses of a propagation */
+#define BP_FIXPOINT 0         /* worklist empty: no bound changes any more */
+#define BP_INFEASIBLE 1       /* a row's minimal activity exceeds g + tol, or bounds cross */
+#define BP_ROUND_LIMIT 2      /* max_rounds rounds were run */
+
+/* memory kinds for caller arrays */
+#define BP_MEM_HOST 0
+#define BP_MEM_DEVICE 1
+
+typedef struct mip_problem mip_problem;
+
+/* ----------------------------------------------------------------- parameters */
+
+/* Bound-propagation parameters (Section 2.1).  theta: minimum relative improvement for a
+ * continuous bound to move (new bound accepted iff old - new > theta * max(1, |old|), or
+ * the old bound is infinite); the paper's "threshold" whose value it does not give.
+ * Integer bounds move on any improvement after rounding floor(c + 1e-6) / ceil(c - 1e-6).
+ * max_rounds: stop after this many rounds (status BP_ROUND_LIMIT).
+ * bounds_mem: BP_MEM_DEVICE if lb/ub are device arrays, BP_MEM_HOST if host arrays (the
+ * library then copies them in and out on the stream; pinned host memory keeps it async). */
+typedef struct {
+    double theta;
+    int32_t max_rounds;
+    int32_t bounds_mem;
+} bp_params;
+
+/* Result of one propagation.  rounds: rounds that processed a non-empty worklist.
+ * nnz_updates: sum over rounds of the nonzeros of the rows processed (the work unit of
+ * the throughput metric).  first_infeasible_row / _var: the smallest infeasible row index
+ * and the smallest crossing variable index in the final round, -1 if none.
+ * n_changed: variables whose output bounds differ from the (normalised) input bounds. */
+typedef struct {
+    int32_t status;
+    int32_t rounds;
+    int32_t first_infeasible_row;
+    int32_t first_infeasible_var;
+    int64_t nnz_updates;
+    int64_t n_changed;
+    int32_t error;        /* BP_OK, or BP_ERR_TIMEOUT when a device wait gave up */
+    int32_t reserved;
+} bp_result;
+
+void bp_params_default(bp_params *p);   /* theta 1e-3, max_rounds 10000, device bounds */
+
+/* ------------------------------------------------------------- problem handle */
+
+/*
+ * mip_load_csr -- copy a MILP into library-owned device memory and build its layouts.
+ *
+ * Cites: Section 1 (problem form); Section 2.1 (rows and their transpose are both needed:
+ * activities per row, worklist of rows per changed variable).
+ *
+ * m, n:      rows and variables (0 <= m, n < 2^31).
+ * row_ptr:   int64[m+1], row_ptr[0] = 0, nondecreasing, nnz = row_ptr[m] < 2^31.
+ * col:       int32[nnz], 0 <= col < n, strictly increasing within a row.
+ * val:       double[nnz], finite, |val| >= 1e-12.
+ * g:         double[m], finite or >= 1e20 (a free row); NaN or <= -1e20 is invalid.
+ * lb, ub:    double[n] default bounds (kept on the handle; normalised: +-1e20 -> +-inf,
+ *            integer bounds rounded inward with tol 1e-6).  lb may not be +inf, ub not -inf.
+ * is_int:    uint8[n], nonzero = integer variable.
+ * c:         double[n] objective, or NULL (zeros).
+ * mem_kind:  BP_MEM_HOST or BP_MEM_DEVICE for all the arrays above.
+ * stream:    cudaStream_t used for the copies and the layout kernels.
+ * out:       receives the handle.  The caller keeps ownership of its arrays.
+ * Returns BP_OK; BP_ERR_INVALID (malformed input, message in bp_last_error()),
+ * BP_ERR_OOM or BP_ERR_CUDA.  The call synchronises the stream once (validation result).
+ */
+int mip_load_csr(int32_t m, int32_t n, const int64_t *row_ptr, const int32_t *col,
+                 const double *val, const double *g, const double *lb, const double *ub,
+                 const uint8_t *is_int, const double *c, int32_t mem_kind, void *stream,
+                 mip_problem **out);
+
+/* Releases every device resource of the handle (after synchronising its last stream). */
+int mip_free(mip_problem *p);
+
+/* Sizes of a loaded problem. */
+int mip_dims(const mip_problem *p, int32_t *m, int32_t *n, int64_t *nnz);
+
+/* Copies the handle's normalised default bounds into lb/ub (device arrays of n doubles). */
+int mip_default_bounds(const mip_problem *p, double *lb, double *ub, void *stream);
+
+/* ------------------------------------------------------------ bound propagation */
+
+/*
+ * bp_propagate -- bound propagation to a fixpoint (Section 2.1).
+ *
+ * Every round computes, for each row k of the round's worklist, the minimal activity
+ * L_min^k = sum_{a>0} a l + sum_{a<0} a u (finite part plus a count of infinite terms),
+ * declares the row infeasible if L_min^k > g_k + 1e-6, and proposes for each of its
+ * variables u_i <= (g_k - L_min^k + a_ki l_i) / a_ki (a_ki > 0) or
+ * l_i >= (g_k - L_min^k + a_ki u_i) / a_ki (a_ki < 0), rounded for integers and tested
+ * against the bounds at the START of the round (Jacobi rounds).  The next round's
+ * worklist holds the rows of every variable changed in this round ("propagation on changed
+ * constraints", Section 1); round 0 holds every row.
+ *
+ * lb, ub:  n doubles each, in: start bounds (normalised by the call), out: bounds after the
+ *          last round (on BP_INFEASIBLE: after the round that found the infeasibility).
+ *          Device or host memory per params->bounds_mem.
+ * params:  NULL for defaults.
+ * result:  host pointer.  The library enqueues a copy of the result into it; it is valid
+ *          once the stream is synchronised (at return when it is pageable memory).  May be
+ *          NULL, then the result stays on the device (see bp_result_device).
+ * Returns BP_OK (check result->status), BP_ERR_TIMEOUT (a device wait gave up; the bounds
+ * are then unspecified), BP_ERR_INVALID or BP_ERR_CUDA.
+ */
+int bp_propagate(mip_problem *p, double *lb, double *ub, const bp_params *params,
+                 bp_result *result, void *stream);
+
+/* Device address of the handle's result slot written by the last bp_propagate. */
+const bp_result *bp_result_device(const mip_problem *p);
+
+/* -------------------------------------------------------------------- probing */
+
+/*
+ * probe_split -- the two branch boxes of an integer variable (Section 2.2).
+ * Boxed [l, u]: c = ceil((l + u) / 2), down = [l, c - 1], up = [c, u] (binary: [0,0], [1,1]).
+ * Only l finite: [l, l] and [l + 1, +inf).  Only u finite: [u, u] and (-inf, u - 1].
+ * Writes box4 = {down_l, down_u, up_l, up_u}; returns 1 if the variable is probed, 0 for a
+ * continuous, fixed or free variable.  Pure host function.
+ */
+int probe_split(int32_t is_int, double l, double u, double *box4);
+
+/* Probing cache (Section 2.2).  For branch e = 2*i + b of pair i (b = 0 down, 1 up):
+ * status[e], rounds[e], nnz_updates[e]; offsets[e] .. offsets[e+1] index the implied
+ * bounds (var, l, u) of that branch: every variable whose bounds differ from the root,
+ * ascending by variable; nothing for an infeasible branch.  All arrays are caller-owned
+ * DEVICE memory: status/rounds int32[2P], nnz_updates int64[2P], offsets int64[2P+1],
+ * ent_var int32[cap], ent_l/ent_u double[cap]. */
+typedef struct {
+    int32_t *status;
+    int32_t *rounds;
+    int64_t *nnz_updates;
+    int64_t *offsets;
+    int32_t *ent_var;
+    double *ent_l;
+    double *ent_u;
+    int64_t cap;
+    int64_t needed;   /* out: entries needed (set also on BP_ERR_CAPACITY) */
+} probe_cache;
+
+/*
+ * bp_probe_batch -- double probing of P variables in one launch (Section 2.2).
+ *
+ * Branch b of pair i starts from root ∩ box (box = boxes[4i+2b], boxes[4i+2b+1] for
+ * variable var[i]) and runs bp_propagate's rounds with round 0 holding the rows of var[i].
+ * Both branches of a pair are propagated together so that they share every row load.
+ * root_lb/root_ub: device, n doubles (normally a bp_propagate fixpoint).
+ * var: device int32[P]; boxes: device double[4P] (see probe_split).
+ * Returns BP_OK, BP_ERR_CAPACITY (cache->needed holds the required entry count; the status,
+ * rounds, nnz_updates and offsets arrays are complete), BP_ERR_TIMEOUT, BP_ERR_INVALID.
+ * The call synchronises the stream once (to read the entry count).
+ */
+int bp_probe_batch(mip_problem *p, const double *root_lb, const double *root_ub, int32_t P,
+                   const int32_t *var, const double *boxes, const bp_params *params,
+                   probe_cache *cache, void *stream);
+
+/*
+ * bp_probe_priority -- probe priority keys (Section 2.2) under bounds lb/ub (device):
+ * key1 int32[n] = rows violated when the variable's contribution flips from its minimising
+ * to its maximising bound (variables with coefficients of both signs only, else 0; -1 for a
+ * variable that is not probed), key2 double[n] = largest such violation, key3 double[n] =
+ * smallest unit slack (g - L_min) / |a| over its rows.  order int32[n] receives the probed
+ * variables sorted by key1 desc, key2 desc, key3 asc, index asc; *count their number
+ * (host pointer, valid at return: the call synchronises the stream).
+ */
+int bp_probe_priority(mip_problem *p, const double *lb, const double *ub, int32_t *key1,
+                      double *key2, double *key3, int32_t *order, int32_t *count, void *stream);
+
+/* ------------------------------------------------------------------- errors */
+
+/* Thread-local message of the last error ("" if none). */
+const char *bp_last_error(void);
+
+/* Library version string. */
+const char *bp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPUBP_H */

@@ -1,0 +1,198 @@
+"""CPU oracle for bound propagation, probing, probe priority and fix-and-propagate.
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the benchmark's
+CPU-baseline leg, never by the library.  The C sources next to this file are plain
+sequential IEEE-double code (built with -ffp-contract=off); this module only marshals
+numpy arrays into them.  It shares no code with the GPU library.
+
+Problems are passed as any object with the attributes m, n, row_ptr (int64), col (int32),
+val (float64), g (float64) and is_int (uint8).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SOURCES = ["bp_oracle.c", "fp_oracle.c", "mlp_oracle.c"]
+LIB = os.path.join(HERE, "liboracle.so")
+
+FIXPOINT, INFEASIBLE, ROUND_LIMIT = 0, 1, 2
+TOL = 1e-6
+
+
+def build(force: bool = False) -> str:
+    """Compiles the oracle with gcc (-O2, no FMA contraction, no fast-math)."""
+    srcs = [os.path.join(HERE, s) for s in SOURCES if os.path.exists(os.path.join(HERE, s))]
+    newest = max(os.path.getmtime(s) for s in srcs)
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
+        return LIB
+    tmp = LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-o", tmp] + srcs + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+_lib = None
+
+
+class BpResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("rounds", C.c_int32),
+                ("first_infeasible_row", C.c_int32), ("first_infeasible_var", C.c_int32),
+                ("nnz_updates", C.c_int64), ("n_changed", C.c_int64),
+                ("candidates", C.c_int64), ("fragile", C.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def _p(a, t):
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        L = _lib
+        L.orc_load.restype = C.c_void_p
+        L.orc_load.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                               C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_uint8),
+                               C.POINTER(C.c_int32)]
+        L.orc_free.argtypes = [C.c_void_p]
+        L.orc_normalize.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.orc_bp.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                             C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int32),
+                             C.c_int32, C.c_double, C.c_int32, C.c_int32, C.POINTER(BpResult),
+                             C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        L.orc_probe_split.argtypes = [C.c_int32, C.c_double, C.c_double, C.POINTER(C.c_double)]
+        L.orc_probe_split.restype = C.c_int
+        L.orc_probe_batch.restype = C.c_int64
+        L.orc_probe_batch.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                      C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double),
+                                      C.c_double, C.c_int32, C.POINTER(C.c_int32),
+                                      C.POINTER(C.c_int32), C.POINTER(C.c_int64),
+                                      C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                      C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int64]
+        L.orc_probe_priority.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                         C.POINTER(C.c_int32), C.POINTER(C.c_double),
+                                         C.POINTER(C.c_double)]
+    return _lib
+
+
+class Problem:
+    """An oracle-side copy of a problem (CSR plus transpose)."""
+
+    def __init__(self, milp):
+        L = lib()
+        self.m, self.n = int(milp.m), int(milp.n)
+        self.row_ptr = np.ascontiguousarray(milp.row_ptr, dtype=np.int64)
+        self.col = np.ascontiguousarray(milp.col, dtype=np.int32)
+        self.val = np.ascontiguousarray(milp.val, dtype=np.float64)
+        self.g = np.ascontiguousarray(milp.g, dtype=np.float64)
+        self.is_int = np.ascontiguousarray(milp.is_int, dtype=np.uint8)
+        err = C.c_int32(0)
+        h = L.orc_load(self.m, self.n, _p(self.row_ptr, C.c_int64), _p(self.col, C.c_int32),
+                       _p(self.val, C.c_double), _p(self.g, C.c_double), _p(self.is_int, C.c_uint8),
+                       C.byref(err))
+        if not h:
+            raise ValueError(f"oracle rejected the problem (code {err.value})")
+        self.h = C.c_void_p(h)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and _lib is not None:
+            _lib.orc_free(h)
+            self.h = None
+
+    def normalize(self, lb, ub):
+        lb = np.array(lb, dtype=np.float64)
+        ub = np.array(ub, dtype=np.float64)
+        lib().orc_normalize(self.h, _p(lb, C.c_double), _p(ub, C.c_double))
+        return lb, ub
+
+    def bp(self, lb, ub, w0=None, theta=1e-3, max_rounds=10000, mode=0, dlb=None, dub=None,
+           trace=False):
+        """Bound propagation; returns (lb, ub, result dict, (dlb, dub)).  With trace=True the
+        result dict also holds the rows and nonzeros of every round."""
+        lb = np.array(lb, dtype=np.float64)
+        ub = np.array(ub, dtype=np.float64)
+        dl = np.zeros(self.n) if dlb is None else np.array(dlb, dtype=np.float64)
+        du = np.zeros(self.n) if dub is None else np.array(dub, dtype=np.float64)
+        r = BpResult()
+        if w0 is None:
+            wp, wl = None, 0
+        else:
+            w0 = np.ascontiguousarray(w0, dtype=np.int32)
+            wp, wl = _p(w0, C.c_int32), len(w0)
+        tr = tn = None
+        if trace:
+            tr = np.zeros(max(1, max_rounds), dtype=np.int64)
+            tn = np.zeros(max(1, max_rounds), dtype=np.int64)
+        lib().orc_bp(self.h, _p(lb, C.c_double), _p(ub, C.c_double), _p(dl, C.c_double),
+                     _p(du, C.c_double), wp, wl, float(theta), int(max_rounds), int(mode),
+                     C.byref(r), None if tr is None else _p(tr, C.c_int64),
+                     None if tn is None else _p(tn, C.c_int64))
+        out = r.as_dict()
+        if trace:
+            out["trace_rows"] = tr[:r.rounds].copy()
+            out["trace_nnz"] = tn[:r.rounds].copy()
+        return lb, ub, out, (dl, du)
+
+    def probe_batch(self, root_l, root_u, var, boxes, theta=1e-3, max_rounds=10000, cap=None):
+        root_l = np.ascontiguousarray(root_l, dtype=np.float64)
+        root_u = np.ascontiguousarray(root_u, dtype=np.float64)
+        var = np.ascontiguousarray(var, dtype=np.int32)
+        boxes = np.ascontiguousarray(boxes, dtype=np.float64).reshape(-1)
+        P = len(var)
+        status = np.zeros(2 * P, dtype=np.int32)
+        rounds = np.zeros(2 * P, dtype=np.int32)
+        nnzu = np.zeros(2 * P, dtype=np.int64)
+        offs = np.zeros(2 * P + 1, dtype=np.int64)
+        if cap is None:
+            cap = max(1, 64 * P)
+        while True:
+            ev = np.zeros(cap, dtype=np.int32)
+            el = np.zeros(cap)
+            eu = np.zeros(cap)
+            need = lib().orc_probe_batch(self.h, _p(root_l, C.c_double), _p(root_u, C.c_double), P,
+                                         _p(var, C.c_int32), _p(boxes, C.c_double), float(theta),
+                                         int(max_rounds), _p(status, C.c_int32), _p(rounds, C.c_int32),
+                                         _p(nnzu, C.c_int64), _p(offs, C.c_int64), _p(ev, C.c_int32),
+                                         _p(el, C.c_double), _p(eu, C.c_double), cap)
+            if need <= cap:
+                return dict(status=status, rounds=rounds, nnz_updates=nnzu, offsets=offs,
+                            var=ev[:need], l=el[:need], u=eu[:need])
+            cap = int(need)
+
+    def probe_priority(self, lb, ub):
+        lb = np.ascontiguousarray(lb, dtype=np.float64)
+        ub = np.ascontiguousarray(ub, dtype=np.float64)
+        k1 = np.zeros(self.n, dtype=np.int32)
+        k2 = np.zeros(self.n)
+        k3 = np.zeros(self.n)
+        lib().orc_probe_priority(self.h, _p(lb, C.c_double), _p(ub, C.c_double), _p(k1, C.c_int32),
+                                 _p(k2, C.c_double), _p(k3, C.c_double))
+        return k1, k2, k3
+
+
+def probe_split(is_int, l, u):
+    """Branch boxes of an integer variable (Section 2.2); None when it is not probed."""
+    out = (C.c_double * 4)()
+    ok = lib().orc_probe_split(int(is_int), float(l), float(u), out)
+    return (out[0], out[1], out[2], out[3]) if ok else None
+
+
+def priority_order(k1, k2, k3, probeable_only=True):
+    """Probe order: key1 descending, key2 descending, key3 ascending, index ascending."""
+    idx = np.arange(len(k1))
+    if probeable_only:
+        idx = idx[k1 >= 0]
+    # lexsort: last key is primary
+    order = np.lexsort((idx, k3[idx], -k2[idx], -k1[idx]))
+    return idx[order].astype(np.int32)

@@ -1,0 +1,148 @@
+"""Pins of the oracle's probing (Section 2.2): probe split, cache contents, brute-force
+soundness of cached implications, and the probe priority keys."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_20499_gb300 import synth
+from tests.helpers import dense, feasible_points, golden_problem, load_golden, milp_from_dense
+
+
+def test_probe_split_cases():
+    assert oracle.probe_split(1, 0, 1) == (0, 0, 1, 1)
+    assert oracle.probe_split(1, 0, 100) == (0, 49, 50, 100)    # x < 50 | x >= 50
+    assert oracle.probe_split(1, 0, 3) == (0, 1, 2, 3)          # x < 1.5 | x >= 1.5
+    assert oracle.probe_split(1, -3, 2) == (-3, -1, 0, 2)       # (l+u)/2 = -0.5
+    assert oracle.probe_split(1, 4, np.inf) == (4, 4, 5, np.inf)
+    assert oracle.probe_split(1, -np.inf, 7) == (7, 7, -np.inf, 6)
+    assert oracle.probe_split(0, 0, 1) is None                   # continuous
+    assert oracle.probe_split(1, 2, 2) is None                   # fixed
+    assert oracle.probe_split(1, -np.inf, np.inf) is None        # free
+
+
+def test_probe_cache_golden():
+    d = load_golden("probe_knapsack.json")
+    p = golden_problem(d)
+    P = oracle.Problem(p)
+    res = P.probe_batch(np.array(d["root_lb"], float), np.array(d["root_ub"], float), d["var"], d["boxes"])
+    for e, want in enumerate(d["expect"]):
+        assert res["status"][e] == want["status"], want["note"]
+        a, b = res["offsets"][e], res["offsets"][e + 1]
+        got = [[int(res["var"][q]), float(res["l"][q]), float(res["u"][q])] for q in range(a, b)]
+        assert got == [[int(x[0]), float(x[1]), float(x[2])] for x in want["entries"]], want["note"]
+
+
+@pytest.mark.parametrize("seed", range(15))
+def test_probe_brute_force(seed):
+    """A branch marked infeasible has no feasible point; every cached bound holds for every
+    feasible point of its branch; a branch's cache equals the plain propagation of root ∩ box
+    whose first round holds the rows of the probed variable."""
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(3, 7))
+    m = int(rng.integers(2, 6))
+    A = rng.integers(-3, 4, size=(m, n)).astype(float)
+    A[rng.uniform(size=(m, n)) < 0.35] = 0.0
+    for k in range(m):
+        if not A[k].any():
+            A[k, rng.integers(0, n)] = 1.0
+    ub = rng.integers(1, 4, size=n).astype(float)
+    lb = np.zeros(n)
+    g = rng.integers(0, 7, size=m).astype(float)
+    p = milp_from_dense(A, g, lb, ub, np.ones(n))
+    P = oracle.Problem(p)
+    rl, ru, r, _ = P.bp(lb, ub)
+    if r["status"] != oracle.FIXPOINT:
+        return
+    var, boxes = [], []
+    for j in range(n):
+        s = oracle.probe_split(1, rl[j], ru[j])
+        if s:
+            var.append(j)
+            boxes.append(s)
+    if not var:
+        return
+    res = P.probe_batch(rl, ru, var, boxes)
+    pts = feasible_points(p, rl, ru)
+    for i, v in enumerate(var):
+        for b in range(2):
+            e = 2 * i + b
+            lo, hi = boxes[i][2 * b], boxes[i][2 * b + 1]
+            inb = pts[(pts[:, v] >= lo) & (pts[:, v] <= hi)] if len(pts) else pts
+            if res["status"][e] == oracle.INFEASIBLE:
+                assert len(inb) == 0
+                continue
+            l2, u2 = rl.copy(), ru.copy()
+            for q in range(res["offsets"][e], res["offsets"][e + 1]):
+                l2[res["var"][q]] = res["l"][q]
+                u2[res["var"][q]] = res["u"][q]
+            if len(inb):
+                assert (inb >= l2).all() and (inb <= u2).all()
+            # composition: the same as one propagation from root ∩ box, round 0 = rows of v
+            sl, su = rl.copy(), ru.copy()
+            sl[v], su[v] = max(sl[v], lo), min(su[v], hi)
+            rows_v = [k for k in range(m) if A[k, v] != 0]
+            cl, cu, cr, _ = P.bp(sl, su, w0=rows_v)
+            np.testing.assert_array_equal(cl, l2)
+            np.testing.assert_array_equal(cu, u2)
+            assert cr["rounds"] == res["rounds"][e]
+
+
+def test_priority_golden():
+    d = load_golden("priority_small.json")
+    p = golden_problem(d)
+    P = oracle.Problem(p)
+    k1, k2, k3 = P.probe_priority(np.array(d["lb"], float), np.array(d["ub"], float))
+    np.testing.assert_array_equal(k1, d["key1"])
+    np.testing.assert_array_equal(k2, d["key2"])
+    np.testing.assert_array_equal(k3, d["key3"])
+    np.testing.assert_array_equal(oracle.priority_order(k1, k2, k3), d["order"])
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_priority_flip_counts_by_enumeration(seed):
+    """key1 counts the rows whose smallest activity over the box, with the variable pinned to
+    the bound that maximises its own term, exceeds g + tol; key3 is the smallest
+    (g - min activity) / |a|.  The minima come from enumerating the box's integer points."""
+    rng = np.random.default_rng(200 + seed)
+    n, m = 5, 4
+    A = rng.integers(-4, 5, size=(m, n)).astype(float)
+    A[rng.uniform(size=(m, n)) < 0.3] = 0.0
+    lb = np.zeros(n)
+    ub = rng.integers(1, 3, size=n).astype(float)
+    g = rng.integers(-2, 6, size=m).astype(float)
+    p = milp_from_dense(A, g, lb, ub, np.ones(n))
+    k1, k2, k3 = oracle.Problem(p).probe_priority(lb, ub)
+    pts = np.array(list(itertools.product(*[np.arange(0, int(u) + 1) for u in ub])), dtype=float)
+    act = pts @ A.T
+    for j in range(n):
+        rows = [k for k in range(m) if A[k, j] != 0]
+        mixed = any(A[k, j] > 0 for k in rows) and any(A[k, j] < 0 for k in rows)
+        cnt, exc, unit = 0, 0.0, np.inf
+        for k in rows:
+            lmin = act[:, k].min()
+            unit = min(unit, (g[k] - lmin) / abs(A[k, j]))
+            if mixed:
+                pin = ub[j] if A[k, j] > 0 else lb[j]
+                fl = act[pts[:, j] == pin, k].min()
+                if fl > g[k] + 1e-6:
+                    cnt += 1
+                    exc = max(exc, fl - g[k])
+        if not rows:
+            unit = np.inf
+        assert k1[j] == cnt
+        assert k2[j] == exc
+        assert k3[j] == unit
+
+
+def test_priority_order_on_probing_instance():
+    p = synth.knapsack_cover(seed=5, m=500, n=1000, nnz=10_000)
+    P = oracle.Problem(p)
+    rl, ru, r, _ = P.bp(p.lb, p.ub)
+    assert r["status"] == oracle.FIXPOINT
+    k1, k2, k3 = P.probe_priority(rl, ru)
+    order = oracle.priority_order(k1, k2, k3)
+    assert len(order) == int(((k1 >= 0)).sum())
+    keys = [(-k1[j], -k2[j], k3[j], j) for j in order]
+    assert keys == sorted(keys)
