@@ -1,0 +1,273 @@
+"""Benchmark: bound propagation throughput (nnz-updates/s) on the large mixed MILP.
+
+Workload: the 200k-row, 500k-variable, 5M-nonzero power-law instance (60% binary, 20% general
+integer, 20% continuous; Zipf(1.5) row lengths up to 100k; equality pairs), synthetic and
+seeded.  A step is one bp_propagate from the instance's default bounds to the fixpoint through
+the C ABI (all rounds, worklist of changed rows), including the copy of the start bounds into
+the propagated arrays.  The unit of work is the nnz-update: the nonzeros of every row the
+propagation processes, summed over rounds.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (plain sequential C) on the same workload.
+Multi-GPU runs (torchrun) propagate one independent replica per GPU (no data exchange); the
+value is the sum over ranks.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BP nnz-updates/s & probes/s (FP64, % HBM peak); batched vs plain on same GPU"
+UNIT = "nnz-updates/s"
+WORKLOAD = "mixed power-law MILP 200k rows x 500k vars, 5M nnz (Zipf 1.5 rows <= 100k, 60/20/20 bin/int/cont, 20% equality rows)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.stop = threading.Event()
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def finish(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        import statistics
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def algorithmic_bytes(trace_rows, trace_nnz, trace_chg, n):
+    """Bytes the propagation must move: per nonzero processed its column index (4 B) and
+    coefficient (8 B); per worklist row its extent (8 B); per changed variable its new bounds
+    written and read back (32 B); per launch the start bounds in (16 B / var), both bound
+    buffers initialised (32 B / var) and the final bounds read and written out (32 B / var)."""
+    return int(12 * sum(trace_nnz) + 8 * sum(trace_rows) + 32 * sum(trace_chg) + 80 * n)
+
+
+def run_reference(args):
+    import oracle
+    from paper_2510_20499_gb300 import synth
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    p = synth.mixed_powerlaw()
+    P = oracle.Problem(p)
+    for _ in range(args.warmup):
+        P.bp(p.lb, p.ub)
+    nnz = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, _, r, _ = P.bp(p.lb, p.ub)
+        nnz += r["nnz_updates"]
+    dt = time.perf_counter() - t0
+    v = nnz / dt
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "single CPU thread"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} full propagations of the workload"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def cpu_baseline(p, budget_s=12.0):
+    import oracle
+    P = oracle.Problem(p)
+    nnz, runs = 0, 0
+    t0 = time.perf_counter()
+    while runs == 0 or time.perf_counter() - t0 < budget_s:
+        _, _, r, _ = P.bp(p.lb, p.ub)
+        nnz += r["nnz_updates"]
+        runs += 1
+    dt = time.perf_counter() - t0
+    return {"value": nnz / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{runs} full propagations of the workload ({dt:.1f} s, single thread)"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    import paper_2510_20499_gb300 as pkg
+    from paper_2510_20499_gb300 import synth
+
+    p = synth.mixed_powerlaw()
+    prob = pkg.Problem(p)
+    dev = torch.device("cuda", local)
+    lb0 = torch.tensor(p.lb, device=dev)
+    ub0 = torch.tensor(p.ub, device=dev)
+    lb, ub = lb0.clone(), ub0.clone()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    # one traced run (untimed) gives the round structure for the byte count
+    MR = 10000
+    tr = torch.zeros(4 * MR, dtype=torch.int64, device=dev)
+    lb.copy_(lb0)
+    ub.copy_(ub0)
+    r0 = prob.propagate(lb, ub, trace=tr, max_rounds=MR)
+    t = tr[: 4 * r0["rounds"]].view(-1, 4).cpu().numpy()
+    bytes_launch = algorithmic_bytes(t[:, 0], t[:, 1], t[:, 2], p.n)
+
+    def step(timed_events=None):
+        lb.copy_(lb0)
+        ub.copy_(ub0)
+        if timed_events:
+            timed_events[0].record(stream)
+        r = prob.propagate(lb, ub, sync=False)
+        if timed_events:
+            timed_events[1].record(stream)
+        return r
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms, kern_ms, nnz = [], [], 0
+    for i in range(args.steps):
+        flush.fill_(float(i))                     # L2 flushed between timed steps (untimed)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
+        lb.copy_(lb0)
+        ub.copy_(ub0)
+        e[1].record(stream)
+        r = prob.propagate(lb, ub, sync=False)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e[0].elapsed_time(e[2]))
+        kern_ms.append(e[1].elapsed_time(e[2]))
+        nnz += r0["nnz_updates"]
+    torch.cuda.synchronize()
+    res = prob.propagate(lb.copy_(lb0), ub.copy_(ub0))
+    assert res == r0, (res, r0)
+    clocks = sampler.finish()
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = nnz * world / (total_ms / 1e3)
+
+    # end to end through the C ABI with host (pinned) bounds: copies inside the timed region
+    hl = torch.empty(p.n, dtype=torch.float64).pin_memory()
+    hu = torch.empty(p.n, dtype=torch.float64).pin_memory()
+    hl0, hu0 = torch.from_numpy(p.lb.copy()), torch.from_numpy(p.ub.copy())
+    e2e_ms = []
+    for i in range(max(3, args.steps // 2)):
+        hl.copy_(hl0)
+        hu.copy_(hu0)
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rr = prob.propagate(hl.numpy(), hu.numpy())     # library copies H2D, propagates, copies D2H
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        assert rr == r0
+    e2e_value = r0["nnz_updates"] * world / (np.median(e2e_ms) / 1e3)
+
+    hbm, peak_kind = peaks()
+    kern_avg = float(np.mean(kern_ms))
+    achieved = bytes_launch / (kern_avg / 1e3) / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "rounds": r0["rounds"], "nnz_updates_per_step": r0["nnz_updates"],
+                   "l2": "flushed between timed steps (256 MB write, untimed)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * p.n,
+                "d2h_bytes_per_step": 16 * p.n + 48},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "peak_kind": peak_kind, "bytes_per_launch": bytes_launch, "kernel": "bp_kernel",
+                     "launch_ms": kern_avg},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(p)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -58,6 +58,9 @@ typedef struct {
     double theta;
     int32_t max_rounds;
     int32_t bounds_mem;
+    int64_t *trace;      /* optional DEVICE array of 4 * max_rounds int64 (NULL: none): per round
+                            the worklist rows, their nonzeros, the variables changed and the
+                            device time in ns (globaltimer) when the round ended */
 } bp_params;
 
 /* Result of one propagation.  rounds: rounds that processed a non-empty worklist.
@@ -76,7 +79,7 @@ typedef struct {
     int32_t reserved;
 } bp_result;
 
-void bp_params_default(bp_params *p);   /* theta 1e-3, max_rounds 10000, device bounds */
+void bp_params_default(bp_params *p);   /* theta 1e-3, max_rounds 10000, device bounds, no trace */
 
 /* ------------------------------------------------------------- problem handle */
 

@@ -1,0 +1,194 @@
+"""GB300 bound propagation, probing and fix-and-propagate for MILP.
+
+Thin ctypes binding of the C ABI declared in include/gpubp.h.  It only marshals arguments:
+every step of the computation runs in the library's CUDA kernels.  PyTorch supplies device
+memory and the current stream.  Importing works without a GPU; creating a problem needs the
+compiled library and a CUDA device and raises otherwise (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgpubp.so")
+
+BP_OK, BP_ERR_INVALID, BP_ERR_CUDA, BP_ERR_OOM, BP_ERR_CAPACITY, BP_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
+FIXPOINT, INFEASIBLE, ROUND_LIMIT = 0, 1, 2
+MEM_HOST, MEM_DEVICE = 0, 1
+
+
+class BpParams(C.Structure):
+    _fields_ = [("theta", C.c_double), ("max_rounds", C.c_int32), ("bounds_mem", C.c_int32),
+                ("trace", C.c_void_p)]
+
+
+class BpResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("rounds", C.c_int32), ("first_infeasible_row", C.c_int32),
+                ("first_infeasible_var", C.c_int32), ("nnz_updates", C.c_int64), ("n_changed", C.c_int64),
+                ("error", C.c_int32), ("reserved", C.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class ProbeCache(C.Structure):
+    _fields_ = [("status", C.c_void_p), ("rounds", C.c_void_p), ("nnz_updates", C.c_void_p),
+                ("offsets", C.c_void_p), ("ent_var", C.c_void_p), ("ent_l", C.c_void_p),
+                ("ent_u", C.c_void_p), ("cap", C.c_int64), ("needed", C.c_int64)]
+
+
+class GpuBpError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"gpubp error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+# name -> (restype, argtypes); every symbol declared in include/gpubp.h
+SIGNATURES = {
+    "mip_load_csr": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
+                               C.POINTER(C.c_void_p)]),
+    "mip_free": (C.c_int, [C.c_void_p]),
+    "mip_dims": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
+    "mip_default_bounds": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "bp_params_default": (None, [C.POINTER(BpParams)]),
+    "bp_propagate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(BpParams), C.POINTER(BpResult),
+                               C.c_void_p]),
+    "bp_result_device": (C.c_void_p, [C.c_void_p]),
+    "probe_split": (C.c_int, [C.c_int32, C.c_double, C.c_double, C.POINTER(C.c_double)]),
+    "bp_probe_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                 C.POINTER(BpParams), C.POINTER(ProbeCache), C.c_void_p]),
+    "bp_probe_priority": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.POINTER(C.c_int32), C.c_void_p]),
+    "bp_last_error": (C.c_char_p, []),
+    "bp_version": (C.c_char_p, []),
+}
+
+
+def lib():
+    """The loaded library; raises if it is missing (build it with __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise GpuBpError(BP_ERR_CUDA, f"{LIB_PATH} is not built; run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name, None)
+            if f is None:
+                continue
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code):
+    if code != BP_OK:
+        raise GpuBpError(code, lib().bp_last_error().decode())
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise GpuBpError(BP_ERR_CUDA, "no CUDA device: the library has no CPU path")
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def params(theta=1e-3, max_rounds=10000, bounds_mem=MEM_DEVICE, trace=None):
+    p = BpParams()
+    lib().bp_params_default(C.byref(p))
+    p.theta, p.max_rounds, p.bounds_mem = float(theta), int(max_rounds), int(bounds_mem)
+    p.trace = trace.data_ptr() if trace is not None else None
+    return p
+
+
+class Problem:
+    """A MILP loaded into device memory (mip_load_csr).  `milp` has the attributes m, n,
+    row_ptr, col, val, g, lb, ub, is_int and optionally c (numpy arrays)."""
+
+    def __init__(self, milp, stream=None):
+        torch = _torch()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.m, self.n = int(milp.m), int(milp.n)
+        arrs = [torch.from_numpy(np.ascontiguousarray(milp.row_ptr, dtype=np.int64)),
+                torch.from_numpy(np.ascontiguousarray(milp.col, dtype=np.int32)),
+                torch.from_numpy(np.ascontiguousarray(milp.val, dtype=np.float64)),
+                torch.from_numpy(np.ascontiguousarray(milp.g, dtype=np.float64)),
+                torch.from_numpy(np.ascontiguousarray(milp.lb, dtype=np.float64)),
+                torch.from_numpy(np.ascontiguousarray(milp.ub, dtype=np.float64)),
+                torch.from_numpy(np.ascontiguousarray(milp.is_int, dtype=np.uint8))]
+        c = getattr(milp, "c", None)
+        if c is not None:
+            arrs.append(torch.from_numpy(np.ascontiguousarray(c, dtype=np.float64)))
+        d = [a.to(dev) for a in arrs]
+        h = C.c_void_p()
+        _check(lib().mip_load_csr(self.m, self.n, _ptr(d[0]), _ptr(d[1]), _ptr(d[2]), _ptr(d[3]), _ptr(d[4]),
+                                  _ptr(d[5]), _ptr(d[6]), _ptr(d[7]) if c is not None else None, MEM_DEVICE,
+                                  _stream(stream), C.byref(h)))
+        self.h = h
+        self.device = dev
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mip_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def default_bounds(self, stream=None):
+        torch = _torch()
+        lb = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        ub = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        _check(lib().mip_default_bounds(self.h, _ptr(lb), _ptr(ub), _stream(stream)))
+        return lb, ub
+
+    def propagate(self, lb, ub, theta=1e-3, max_rounds=10000, stream=None, sync=True, trace=None):
+        """bp_propagate on device tensors lb/ub (float64, modified in place) or host numpy
+        arrays (copied in and out by the library).  Returns the result dict (after a stream
+        synchronisation when sync=True).  trace: optional int64 device tensor of
+        4 * max_rounds entries (rows, nonzeros, changed variables, end time in ns per round)."""
+        host = isinstance(lb, np.ndarray)
+        if trace is not None:
+            assert trace.dtype.itemsize == 8 and trace.numel() >= 4 * max_rounds and trace.is_cuda
+        prm = params(theta, max_rounds, MEM_HOST if host else MEM_DEVICE, trace)
+        res = BpResult()
+        if host:
+            assert lb.dtype == np.float64 and ub.dtype == np.float64 and lb.flags.c_contiguous
+            lp, up = C.c_void_p(lb.ctypes.data), C.c_void_p(ub.ctypes.data)
+        else:
+            assert lb.dtype.is_floating_point and lb.element_size() == 8 and lb.is_contiguous()
+            lp, up = _ptr(lb), _ptr(ub)
+        s = _stream(stream)
+        _check(lib().bp_propagate(self.h, lp, up, C.byref(prm), C.byref(res), s))
+        if sync:
+            _torch().cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        return res.as_dict()
+
+
+def probe_split(is_int, l, u):
+    out = (C.c_double * 4)()
+    ok = lib().probe_split(int(is_int), float(l), float(u), out)
+    return (out[0], out[1], out[2], out[3]) if ok else None
+
+
+def version():
+    return lib().bp_version().decode()

@@ -1,0 +1,149 @@
+// Device-side building blocks of the GB300 bound-propagation engine.
+//
+// Bounds live as interleaved pairs {l, u} (Section 2.1 keeps l_i, u_i at 2i, 2i+1 so that
+// one gather fetches both) encoded as "ordered keys": an int64 whose signed order equals the
+// numeric order of the double.  Tightening is then a plain atomicMin / atomicMax, and every
+// comparison of bounds runs on the integer pipe: on GB300 each FP64 instruction (add, fma,
+// compare, conversion, floor) issues at about 1/70 of the FP32 rate, so the hot loops spend
+// exactly one FP64 instruction per nonzero (the fused multiply-add of the activity) and keep
+// everything else in integer or FP32 arithmetic.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gpubp {
+
+constexpr double kTol = 1e-6;        // feasibility tolerance (Section 3)
+constexpr double kInfBound = 1e20;   // |b| >= 1e20 means infinite
+constexpr int kWarp = 32;
+
+// ------------------------------------------------------------------ row classes
+// Rows are binned by length (in the spirit of logarithmic radix binning, Section 2.1):
+//   classes 0..3: at most 1, 2, 4, 8 nonzeros          -> one thread per row
+//   class 4:      9 .. kWarpMax nonzeros               -> one warp per row
+//   class 5:      kWarpMax+1 .. kChunk nonzeros        -> one thread block per row
+//   class 6:      more than kChunk nonzeros            -> kChunk-nonzero chunks, one block each
+// Every task then holds at most kPerThread nonzeros per thread, all loaded in one wave.
+constexpr int kNumClass = 7;
+constexpr int kNumThreadBins = 4;
+constexpr int kClassWarpRow = 4;
+constexpr int kClassBlockRow = 5;
+constexpr int kClassChunked = 6;
+constexpr int kPerThread = 8;
+constexpr int kThreadMax = kPerThread;            // 8
+constexpr int kWarpMax = 32 * kPerThread;         // 256
+constexpr int kChunk = 256 * kPerThread;          // 2048 (blocks of 256 threads)
+
+__host__ __device__ inline int row_class(int len) {
+    if (len <= 1) return 0;
+    if (len <= 2) return 1;
+    if (len <= 4) return 2;
+    if (len <= kThreadMax) return 3;
+    if (len <= kWarpMax) return 4;
+    if (len <= kChunk) return 5;
+    return 6;
+}
+
+// ------------------------------------------------------------------ ordered keys
+// key(d) = bits(d) for d >= +0, bits(d) ^ 0x7fff...f for negative d; -0.0 maps to +0.0 first
+// so that the two zeros compare equal, as they do in IEEE arithmetic.
+__device__ __forceinline__ long long dkey(double d) {
+    long long b = __double_as_longlong(d);
+    if (b == (long long)0x8000000000000000ULL) b = 0;
+    return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double kdec(long long k) {
+    return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffLL));
+}
+__device__ __forceinline__ bool key_is_inf(long long k) {
+    // +inf key = 0x7ff0...0; -inf key = 0xfff0...0 ^ 0x7fff...f = 0x800f...f
+    return k == 0x7ff0000000000000LL || k == (long long)0x800fffffffffffffULL;
+}
+constexpr long long kKeyPosInf = 0x7ff0000000000000LL;
+constexpr long long kKeyNegInf = (long long)0x800fffffffffffffULL;
+
+// ------------------------------------------------------------ FP32 bracketing
+// Directed conversions of a double to float by bit manipulation (integer pipe only):
+// f_dn(x) <= x <= f_up(x).  They keep the 20 mantissa bits of the double's high word, so the
+// truncation error is below one unit of the 20th bit (8 units of the float's last place);
+// rounding up adds that unit.  The bracket is what the candidate prefilter needs, not accuracy.
+__device__ __forceinline__ float mag_trunc(unsigned hi) {
+    // |x| truncated toward zero, from the high word (sign cleared)
+    unsigned mag = hi & 0x7fffffffu;
+    if (mag >= 0x47f00000u) return mag >= 0x7ff00000u ? __int_as_float(0x7f800000) : 3.4028235e38f;
+    if (mag < 0x38100000u) return 0.0f;
+    return __int_as_float((int)((mag - 0x38000000u) << 3));
+}
+__device__ __forceinline__ float mag_round_up(unsigned hi) {
+    unsigned mag = hi & 0x7fffffffu;
+    if (mag >= 0x47f00000u) return __int_as_float(0x7f800000);
+    if (mag < 0x38100000u) return mag == 0u ? 0.0f : 1.17549435e-38f;
+    return __int_as_float((int)(((mag - 0x38000000u) << 3) + 8u));
+}
+__device__ __forceinline__ float f_up(double x) {
+    unsigned hi = (unsigned)(__double_as_longlong(x) >> 32);
+    unsigned lo = (unsigned)__double_as_longlong(x);
+    if ((hi & 0x7fffffffu) == 0u && lo != 0u) return (int)hi < 0 ? 0.0f : 1.17549435e-38f;  // subnormal
+    return (int)hi < 0 ? -mag_trunc(hi) : mag_round_up(hi);
+}
+__device__ __forceinline__ float f_dn(double x) {
+    unsigned hi = (unsigned)(__double_as_longlong(x) >> 32);
+    unsigned lo = (unsigned)__double_as_longlong(x);
+    if ((hi & 0x7fffffffu) == 0u && lo != 0u) return (int)hi < 0 ? -1.17549435e-38f : 0.0f;
+    return (int)hi < 0 ? -mag_round_up(hi) : mag_trunc(hi);
+}
+__device__ __forceinline__ float fabs_up(double x) {
+    unsigned hi = (unsigned)(__double_as_longlong(x) >> 32);
+    unsigned lo = (unsigned)__double_as_longlong(x);
+    if ((hi & 0x7fffffffu) == 0u && lo != 0u) return 1.17549435e-38f;
+    return mag_round_up(hi);
+}
+
+// ------------------------------------------------------------- memory helpers
+__device__ __forceinline__ longlong2 ld_bounds(const longlong2* b, int j) {
+    // bounds change during a launch: read through L2 (never a stale L1 line)
+    return __ldcg(b + j);
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_acquire_s32(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_release_s32(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned atom_add_acqrel_u32(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+// --------------------------------------------------------------- host structs
+// Device view of a loaded problem.
+struct DevProblem {
+    int m, n, nnz;
+    const int* row_ptr;          // m+1
+    const int* col;              // nnz
+    const double* val;           // nnz
+    const double2* grow;         // m: {g, g + tol}, g = +inf for a free row
+    const int* col_ptr;          // n+1 (transpose)
+    const int* row_idx;          // nnz
+    const unsigned char* is_int; // n
+    const unsigned char* rclass; // m
+    const int* heavy_id;         // m: index among chunked rows, -1 otherwise
+    const int* part_off;         // nheavy+1: first partial slot of each chunked row
+    const int* static_list;      // m: row ids grouped by class, ascending within a class
+    const int2* static_tasks;    // all chunk tasks {row, chunk} of the chunked rows
+    int class_off[kNumClass + 1];// class segments of static_list and of worklists
+    int nheavy, nchunks;         // chunked rows, total chunks
+};
+
+}  // namespace gpubp

@@ -1,0 +1,1005 @@
+// Persistent bound-propagation engine (Section 2.1) for sm_103a.
+//
+// One cooperative launch runs a whole propagation: a prologue that normalises the caller's
+// bounds, one phase per Jacobi round, and an epilogue that writes the bounds back.  A phase
+// processes the round's worklist of rows:
+//   minimal activity  L_min = sum_{a>0} a l + sum_{a<0} a u  (finite part + count of infinite
+//                     terms), one fused multiply-add per nonzero;
+//   row verdict       infeasible if no infinite term and L_min > g + tol;
+//   candidates        u_i <= (g - L_min + a l_i) / a (a > 0), l_i >= (g - L_min + a u_i) / a
+//                     (a < 0), after an FP32 prefilter that proves most of them cannot tighten;
+//   apply             atomicMin / atomicMax of ordered keys into the next round's bounds; the
+//                     first change of a variable in the round queues its rows for the next
+//                     round ("propagation on changed constraints", Section 1).
+// Rounds are separated by one grid barrier.  All waits are bounded: a wait that runs out sets
+// BP_ERR_TIMEOUT and the launch returns.
+//
+// The rounds are latency-bound (a round is a chain of dependent L2 round trips), so every task
+// holds at most kPerThread nonzeros per thread, issues all their loads in one wave, then all
+// their bound gathers in one wave, and keeps them in registers for the candidate pass.
+//
+// Work split per phase (static round-robin, no shared dequeue counter):
+//   block tasks   [chunk partial sums][block-per-row rows]
+//   warp tasks    [fix-ups of the previous round's changes][thread-per-row bins][warp rows]
+//   block tasks   [chunk candidates] -- they wait for their row's total, which the first
+//                 block segment produces without waiting, so every wait ends.
+#include <climits>
+
+#include "bp_host.h"
+
+namespace gpubp {
+
+#ifndef GPUBP_MIN_BLOCKS
+#define GPUBP_MIN_BLOCKS 2     // resident blocks per SM the register budget is sized for
+#endif
+
+constexpr int kThreads = 256;
+constexpr int kWarpsPerBlock = kThreads / 32;
+constexpr int kSlots = kNumClass;               // staging slots: row classes 0..5, then changed vars
+constexpr int kSlotChg = kClassChunked;         // chunked rows are not staged; their slot holds variables
+constexpr int kBq = 2048;                       // per-block queue of accepted variables
+constexpr long long kSpinLimit = 4000000000LL;  // clock64 cycles (about 2 s) per wait
+static_assert(kThreads * kPerThread == kChunk, "a chunk is one wave of a block");
+
+struct BpArgs {
+    double* lb;
+    double* ub;
+    longlong2* bk[2];
+    int* vstamp;
+    int* rstamp;
+    int* list[2];
+    int* chg[2];
+    int2* task[2];
+    double* hpart;
+    int2* hpinf;
+    double* htot;
+    int2* htinf;
+    int* harr;
+    int* hready;
+    Ctl* ctl;
+    bp_result* dres;
+    const int* w0;      // rows of round 0, or null for every row
+    int w0_len;
+    double theta;
+    int max_rounds;
+    int base;           // stamp of round 0
+    long long* trace;   // optional: 4 words per round
+};
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+struct Stage {
+    int wcnt[kWarpsPerBlock][kSlots];           // per-warp private staging of appends
+    int wbuf[kWarpsPerBlock][kSlots][32];
+    int bq_n;                                   // variables with an accepted candidate in this phase
+    int bq[kBq];
+    double red_d[kWarpsPerBlock];
+    int red_n[kWarpsPerBlock], red_j[kWarpsPerBlock];
+    unsigned long long nnz;
+    int flag, last;
+    // descriptor of the current phase, read once per block by thread 0
+    int d_cnt[kNumClass];
+    int d_ntask, d_nprev;
+};
+
+// ------------------------------------------------------------------ phase state
+struct Phase {
+    int t, par, npar;
+    const longlong2* R;     // bounds at the start of the round
+    longlong2* X;           // bounds of the next round (atomics)
+    int st_v, st_r;         // variable-change stamp of this round, row stamp of next round
+};
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Global destination and counter of staging slot s.
+__device__ __forceinline__ int* slot_dst(const BpArgs& A, const DevProblem& P, const Phase& ph, int s, int pos) {
+    return s == kSlotChg ? A.chg[ph.par] + pos : A.list[ph.npar] + P.class_off[s] + pos;
+}
+__device__ __forceinline__ int* slot_ctr(const BpArgs& A, const Phase& ph, int s) {
+    return s == kSlotChg ? &A.ctl->nchg[ph.par].v : &A.ctl->cnt[ph.npar][s].v;
+}
+
+// Warp-wide: move this warp's staged entries of slot s to the global list (one atomic).
+__device__ __forceinline__ void warp_flush_slot(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph,
+                                                int s) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncwarp();
+    const int n = st.wcnt[w][s];
+    if (n == 0) return;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(slot_ctr(A, ph, s), n);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (lane < n) *slot_dst(A, P, ph, s, base + lane) = st.wbuf[w][s][lane];
+    __syncwarp();
+    if (lane == 0) st.wcnt[w][s] = 0;
+    __syncwarp();
+}
+
+__device__ void warp_flush_all(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph) {
+    for (int s = 0; s < kSlots; ++s) warp_flush_slot(st, A, P, ph, s);
+}
+
+// Warp-wide (all 32 lanes, converged): append `value` to staging slot `slot` for every lane
+// with slot >= 0.  Lanes with equal slots share one staging update; a full slot is flushed
+// with one global atomic for up to 32 entries.
+__device__ void warp_append(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, int slot, int value) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned pending = __ballot_sync(0xffffffffu, slot >= 0);
+    while (pending) {
+        const int src = __ffs(pending) - 1;
+        const int s = __shfl_sync(0xffffffffu, slot, src);
+        const unsigned grp = __ballot_sync(0xffffffffu, slot == s) & pending;
+        const int n = __popc(grp);
+        __syncwarp();
+        int cnt = st.wcnt[w][s];
+        if (cnt + n > 32) {
+            warp_flush_slot(st, A, P, ph, s);
+            cnt = 0;
+        }
+        if (grp & (1u << lane)) st.wbuf[w][s][cnt + __popc(grp & lanemask_lt())] = value;
+        __syncwarp();
+        if (lane == 0) st.wcnt[w][s] = cnt + n;
+        __syncwarp();
+        pending &= ~grp;
+    }
+}
+
+// Append of one row or variable by a single lane, straight to the global lists (only for the
+// rare paths that run outside a converged warp).
+__device__ void lane_queue_row(const BpArgs& A, const DevProblem& P, const Phase& ph, int k) {
+    if (atomicMax(&A.rstamp[k], ph.st_r) >= ph.st_r) return;
+    const int cls = P.rclass[k];
+    if (cls != kClassChunked) {
+        const int pos = atomicAdd(&A.ctl->cnt[ph.npar][cls].v, 1);
+        A.list[ph.npar][P.class_off[cls] + pos] = k;
+        return;
+    }
+    const int len = __ldg(P.row_ptr + k + 1) - __ldg(P.row_ptr + k);
+    const int nch = (len + kChunk - 1) / kChunk;
+    const int base = atomicAdd(&A.ctl->ntask[ph.npar].v, nch);
+    for (int c = 0; c < nch; ++c) A.task[ph.npar][base + c] = make_int2(k, c);
+    atomicAdd(&A.ctl->cnt[ph.npar][kClassChunked].v, 1);
+}
+
+// Warp-wide: queue the rows `k` (k < 0: none) for the next round; a row's first queuing in
+// this round wins.  Chunked rows get their chunk tasks directly (they are few).
+__device__ void warp_queue_rows(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, int k) {
+    int slot = -1;
+    if (k >= 0 && atomicMax(&A.rstamp[k], ph.st_r) < ph.st_r) {
+        const int cls = P.rclass[k];
+        if (cls != kClassChunked) {
+            slot = cls;
+        } else {
+            const int len = __ldg(P.row_ptr + k + 1) - __ldg(P.row_ptr + k);
+            const int nch = (len + kChunk - 1) / kChunk;
+            const int base = atomicAdd(&A.ctl->ntask[ph.npar].v, nch);
+            for (int c = 0; c < nch; ++c) A.task[ph.npar][base + c] = make_int2(k, c);
+            atomicAdd(&A.ctl->cnt[ph.npar][kClassChunked].v, 1);
+        }
+    }
+    warp_append(st, A, P, ph, slot, k);
+}
+
+// Variable j had a candidate accepted in this round: remember it in the block's queue (shared
+// memory only; no global round trip on the task's path).  drain_changed later keeps the first
+// report of each variable across the grid and queues its rows.  A full queue falls back to
+// doing that work from this lane.
+__device__ __forceinline__ void note_changed(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph,
+                                             int j) {
+    const int i = atomicAdd(&st.bq_n, 1);
+    if (i < kBq) {
+        st.bq[i] = j;
+        return;
+    }
+    if (atomicMax(&A.vstamp[j], ph.st_v) >= ph.st_v) return;
+    const int pos = atomicAdd(&A.ctl->nchg[ph.par].v, 1);
+    A.chg[ph.par][pos] = j;
+    const int e = __ldg(P.col_ptr + j + 1);
+    for (int s = __ldg(P.col_ptr + j); s < e; ++s) lane_queue_row(A, P, ph, __ldg(P.row_idx + s));
+}
+
+// Block-wide, once per phase: for every variable in the block's queue that changes for the
+// first time in this round (grid-wide), list it and queue its rows.  Each warp takes 32
+// variables at a time and spreads their (variable, row) pairs over its lanes, so a batch of
+// columns costs a few round trips in total.
+__device__ void drain_changed(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph) {
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int n = min(st.bq_n, kBq);
+    for (int b0 = w * 32; b0 < n; b0 += kThreads) {
+        const int idx = b0 + lane;
+        int v = idx < n ? st.bq[idx] : -1;
+        if (v >= 0 && atomicMax(&A.vstamp[v], ph.st_v) >= ph.st_v) v = -1;
+        warp_append(st, A, P, ph, v >= 0 ? kSlotChg : -1, v);
+        const int cb = v >= 0 ? __ldg(P.col_ptr + v) : 0;
+        const int deg = v >= 0 ? __ldg(P.col_ptr + v + 1) - cb : 0;
+        int incl = deg;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int excl = incl - deg;
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        for (int p0 = 0; p0 < total; p0 += 32) {
+            const int p = p0 + lane;
+            // owner lane: the last lane whose exclusive offset is <= p
+            int owner = 0;
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int e = __shfl_sync(0xffffffffu, excl, owner + step);
+                if (e <= p) owner += step;
+            }
+            const int ob = __shfl_sync(0xffffffffu, cb, owner);
+            const int oe = __shfl_sync(0xffffffffu, excl, owner);
+            const int k = p < total ? __ldg(P.row_idx + ob + (p - oe)) : -1;
+            warp_queue_rows(st, A, P, ph, k);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) st.bq_n = 0;
+    __syncthreads();
+}
+
+// Exact candidate of variable j from row activity (minfin, ninf): the oracle's operation
+// sequence (product, residual, numerator, quotient, each rounded to nearest), then the
+// integer rounding or the continuous threshold against the round-start bounds bk.
+__device__ void try_candidate(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, double a, int j,
+                              longlong2 bk, double minfin, int ninf, double g) {
+    double resid;
+    if (ninf == 1) {
+        resid = minfin;
+    } else {
+        double b = kdec(a > 0 ? bk.x : bk.y);
+        resid = __dsub_rn(minfin, __dmul_rn(a, b));
+    }
+    const double num = __dsub_rn(g, resid);
+    const double cand = __ddiv_rn(num, a);
+    if (!(fabs(cand) < kInfBound)) return;
+    const bool is_i = P.is_int[j] != 0;
+    if (a > 0) {
+        long long nk;
+        bool acc;
+        if (is_i) {
+            nk = dkey(floor(__dadd_rn(cand, kTol)));
+            acc = nk < bk.y;
+        } else if (bk.y == kKeyPosInf) {
+            nk = dkey(cand);
+            acc = true;
+        } else {
+            const double u = kdec(bk.y);
+            const double thr = __dmul_rn(A.theta, fmax(1.0, fabs(u)));
+            nk = dkey(cand);
+            acc = __dsub_rn(u, cand) > thr;
+        }
+        if (acc) {
+            atomicMin(&ph.X[j].y, nk);
+            note_changed(st, A, P, ph, j);
+        }
+    } else {
+        long long nk;
+        bool acc;
+        if (is_i) {
+            nk = dkey(ceil(__dsub_rn(cand, kTol)));
+            acc = nk > bk.x;
+        } else if (bk.x == kKeyNegInf) {
+            nk = dkey(cand);
+            acc = true;
+        } else {
+            const double l = kdec(bk.x);
+            const double thr = __dmul_rn(A.theta, fmax(1.0, fabs(l)));
+            nk = dkey(cand);
+            acc = __dsub_rn(cand, l) > thr;
+        }
+        if (acc) {
+            atomicMax(&ph.X[j].x, nk);
+            note_changed(st, A, P, ph, j);
+        }
+    }
+}
+
+// Conservative test that variable j's candidate from a row with finite activity cannot
+// tighten its bound: slack = g - L_min >= |a| (u - l) + error margin.  FP32 with directed
+// bracketing; a false "may tighten" only costs the exact evaluation.
+struct RowFilter {
+    float slack_dn;   // lower bracket of g - L_min (computed in FP64 once per row)
+    float mag_up;     // upper bracket of |g| + |L_min|
+};
+
+__device__ __forceinline__ RowFilter row_filter(double g, double minfin) {
+    RowFilter f;
+    f.slack_dn = f_dn(__dsub_rn(g, minfin));
+    f.mag_up = __fadd_ru(fabs_up(g), fabs_up(minfin));
+    return f;
+}
+
+__device__ __forceinline__ bool cannot_tighten(const RowFilter& f, double a, longlong2 bk) {
+    const double l = kdec(bk.x), u = kdec(bk.y);
+    const float a_up = fabs_up(a);
+    const float w_up = __fsub_ru(f_up(u), f_dn(l));
+    const float prod = __fmul_ru(a_up, w_up);
+    // rounding of the FP64 candidate: a few units of 2^-53 of |g| + |L_min| + |a| (|l| + |u|)
+    const float big = __fadd_ru(f.mag_up, __fmul_ru(2.0f, __fmul_ru(a_up, __fadd_ru(fabs_up(l), fabs_up(u)))));
+    const float margin = __fmul_ru(1e-15f, big);
+    return f.slack_dn >= __fadd_ru(prod, margin);
+}
+
+__device__ __forceinline__ bool row_infeasible(double minfin, int ninf, double gt) {
+    return ninf == 0 && dkey(minfin) > dkey(gt);
+}
+
+struct Acc {
+    double minfin;
+    int ninf, infj;
+};
+
+__device__ __forceinline__ Acc warp_reduce(Acc a) {
+    for (int off = 16; off > 0; off >>= 1) {
+        a.minfin = __dadd_rn(a.minfin, __shfl_xor_sync(0xffffffffu, a.minfin, off));
+        a.ninf += __shfl_xor_sync(0xffffffffu, a.ninf, off);
+        a.infj = max(a.infj, __shfl_xor_sync(0xffffffffu, a.infj, off));
+    }
+    return a;
+}
+
+// Block-wide reduction in a fixed order (deterministic); every thread gets the total.
+__device__ __forceinline__ Acc block_reduce(Stage& st, Acc a) {
+    a = warp_reduce(a);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        st.red_d[w] = a.minfin;
+        st.red_n[w] = a.ninf;
+        st.red_j[w] = a.infj;
+    }
+    __syncthreads();
+    Acc t{0.0, 0, -1};
+#pragma unroll
+    for (int i = 0; i < kWarpsPerBlock; ++i) {
+        t.minfin = __dadd_rn(t.minfin, st.red_d[i]);
+        t.ninf += st.red_n[i];
+        t.infj = max(t.infj, st.red_j[i]);
+    }
+    __syncthreads();
+    return t;
+}
+
+// A thread's share of a row range: at most kPerThread nonzeros, held in registers.
+struct Elems {
+    int j[kPerThread];
+    double a[kPerThread];
+    longlong2 bk[kPerThread];
+};
+
+// Loads the nonzeros beg + tid + i*stride (i < kPerThread, < end) in one wave, gathers their
+// bounds in a second wave, and accumulates the thread's part of the minimal activity.
+__device__ __forceinline__ Acc load_accumulate(Elems& E, const DevProblem& P, const Phase& ph, int beg, int end,
+                                               int tid, int stride) {
+#pragma unroll
+    for (int i = 0; i < kPerThread; ++i) {
+        const int q = beg + tid + i * stride;
+        E.j[i] = q < end ? __ldg(P.col + q) : -1;
+        E.a[i] = q < end ? __ldg(P.val + q) : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < kPerThread; ++i) E.bk[i] = E.j[i] >= 0 ? ld_bounds(ph.R, E.j[i]) : make_longlong2(0, 0);
+    Acc s{0.0, 0, -1};
+#pragma unroll
+    for (int i = 0; i < kPerThread; ++i) {
+        if (E.j[i] < 0) continue;
+        const long long key = E.a[i] > 0 ? E.bk[i].x : E.bk[i].y;
+        if (key_is_inf(key)) {
+            ++s.ninf;
+            s.infj = E.j[i];
+        } else {
+            s.minfin = fma(E.a[i], kdec(key), s.minfin);
+        }
+    }
+    return s;
+}
+
+// Candidates of the thread's nonzeros given the row total (registers only).
+__device__ __forceinline__ void elems_candidates(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph,
+                                                 const Elems& E, const Acc& tot, double g) {
+    if (tot.ninf >= 2) return;
+    if (tot.ninf == 1) {
+#pragma unroll
+        for (int i = 0; i < kPerThread; ++i)
+            if (E.j[i] >= 0 && E.j[i] == tot.infj)
+                try_candidate(st, A, P, ph, E.a[i], E.j[i], E.bk[i], tot.minfin, 1, g);
+        return;
+    }
+    const RowFilter f = row_filter(g, tot.minfin);
+    unsigned pass = 0;
+#pragma unroll
+    for (int i = 0; i < kPerThread; ++i)
+        if (E.j[i] >= 0 && !cannot_tighten(f, E.a[i], E.bk[i])) pass |= 1u << i;
+    if (pass) {
+#pragma unroll
+        for (int i = 0; i < kPerThread; ++i)
+            if (pass & (1u << i)) try_candidate(st, A, P, ph, E.a[i], E.j[i], E.bk[i], tot.minfin, 0, g);
+    }
+}
+
+// ------------------------------------------------------------------- row kernels
+// Thread per row (rows of at most kThreadMax nonzeros): 32 rows per warp task.
+__device__ void do_thread_rows(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph,
+                               const int* rows, int count, int tl) {
+    const int idx = tl * 32 + (threadIdx.x & 31);
+    if (idx < count) {
+        const int k = __ldcg(rows + idx);
+        const int beg = __ldg(P.row_ptr + k), end = __ldg(P.row_ptr + k + 1);
+        const double2 g2 = __ldg(P.grow + k);
+        Elems E;
+        const Acc s = load_accumulate(E, P, ph, beg, end, 0, 1);
+        atomicAdd(&st.nnz, (unsigned long long)(end - beg));
+        if (row_infeasible(s.minfin, s.ninf, g2.y)) {
+            atomicMin(&A.ctl->rowinf[ph.par].v, k);
+        } else {
+            elems_candidates(st, A, P, ph, E, s, g2.x);
+        }
+    }
+}
+
+// Warp per row (kThreadMax+1 .. kWarpMax nonzeros).
+__device__ void do_warp_row(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, int k) {
+    const int lane = threadIdx.x & 31;
+    const int beg = __ldg(P.row_ptr + k), end = __ldg(P.row_ptr + k + 1);
+    const double2 g2 = __ldg(P.grow + k);
+    Elems E;
+    const Acc tot = warp_reduce(load_accumulate(E, P, ph, beg, end, lane, 32));
+    if (lane == 0) atomicAdd(&st.nnz, (unsigned long long)(end - beg));
+    if (row_infeasible(tot.minfin, tot.ninf, g2.y)) {
+        if (lane == 0) atomicMin(&A.ctl->rowinf[ph.par].v, k);
+    } else {
+        elems_candidates(st, A, P, ph, E, tot, g2.x);
+    }
+}
+
+// Block per row (kWarpMax+1 .. kChunk nonzeros): the reduction stays in shared memory.
+__device__ void do_block_row(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, int k) {
+    const int beg = __ldg(P.row_ptr + k), end = __ldg(P.row_ptr + k + 1);
+    const double2 g2 = __ldg(P.grow + k);
+    Elems E;
+    const Acc tot = block_reduce(st, load_accumulate(E, P, ph, beg, end, threadIdx.x, kThreads));
+    if (row_infeasible(tot.minfin, tot.ninf, g2.y)) {
+        if (threadIdx.x == 0) atomicMin(&A.ctl->rowinf[ph.par].v, k);
+    } else {
+        elems_candidates(st, A, P, ph, E, tot, g2.x);
+    }
+    if (threadIdx.x == 0) atomicAdd(&st.nnz, (unsigned long long)(end - beg));
+    __syncthreads();
+}
+
+// Chunk of a long row, first half: the block's partial activity; the last chunk to arrive
+// sums the partials in chunk order (deterministic) and publishes the row total.
+__device__ void do_chunk_partial(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, int2 tk) {
+    const int k = tk.x, c = tk.y;
+    const int rb = __ldg(P.row_ptr + k), re = __ldg(P.row_ptr + k + 1);
+    const int beg = rb + c * kChunk, end = min(re, beg + kChunk);
+    Elems E;
+    const Acc part = block_reduce(st, load_accumulate(E, P, ph, beg, end, threadIdx.x, kThreads));
+    const int h = __ldg(P.heavy_id + k);
+    const int slot0 = __ldg(P.part_off + h);
+    const int nch = (re - rb + kChunk - 1) / kChunk;
+    if (threadIdx.x == 0) {
+        A.hpart[slot0 + c] = part.minfin;
+        A.hpinf[slot0 + c] = make_int2(part.ninf, part.infj);
+        __threadfence();
+        st.last = atomicAdd(&A.harr[h], 1) == nch - 1;
+    }
+    __syncthreads();
+    if (st.last && threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        __threadfence();
+        Acc s{0.0, 0, -1};
+        for (int i = lane; i < nch; i += 32) {
+            s.minfin = __dadd_rn(s.minfin, __ldcg(A.hpart + slot0 + i));
+            const int2 pi = __ldcg(A.hpinf + slot0 + i);
+            s.ninf += pi.x;
+            s.infj = max(s.infj, pi.y);
+        }
+        s = warp_reduce(s);
+        if (lane == 0) {
+            const double2 g2 = __ldg(P.grow + k);
+            if (row_infeasible(s.minfin, s.ninf, g2.y)) atomicMin(&A.ctl->rowinf[ph.par].v, k);
+            atomicAdd(&st.nnz, (unsigned long long)(re - rb));
+            A.htot[h] = s.minfin;
+            A.htinf[h] = make_int2(s.ninf, s.infj);
+            A.harr[h] = 0;
+            __threadfence();
+            st_release_s32(A.hready + h, ph.st_v);
+        }
+    }
+    __syncthreads();
+}
+
+// Chunk of a long row, second half: wait for the row total, then the chunk's candidates.
+// The chunk's nonzeros and bounds are loaded before the wait.
+__device__ bool do_chunk_candidates(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, int2 tk) {
+    const int k = tk.x, c = tk.y;
+    const int h = __ldg(P.heavy_id + k);
+    const int rb = __ldg(P.row_ptr + k), re = __ldg(P.row_ptr + k + 1);
+    const int beg = rb + c * kChunk, end = min(re, beg + kChunk);
+    Elems E;
+    (void)load_accumulate(E, P, ph, beg, end, threadIdx.x, kThreads);
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const long long t0 = clock64();
+        while (ld_acquire_s32(A.hready + h) != ph.st_v) {
+            if (clock64() - t0 > kSpinLimit) {
+                ok = 0;
+                atomicExch(&A.ctl->error, BP_ERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(32);
+        }
+        st.last = ok;
+    }
+    __syncthreads();
+    const bool ok = st.last != 0;
+    if (ok) {
+        Acc tot;
+        tot.minfin = __ldcg(A.htot + h);
+        const int2 ti = __ldcg(A.htinf + h);
+        tot.ninf = ti.x;
+        tot.infj = ti.y;
+        const double2 g2 = __ldg(P.grow + k);
+        if (!row_infeasible(tot.minfin, tot.ninf, g2.y)) elems_candidates(st, A, P, ph, E, tot, g2.x);
+    }
+    __syncthreads();
+    return ok;
+}
+
+__device__ __forceinline__ bool crossed(bool is_i, long long lk, long long uk) {
+    if (lk <= uk) return false;
+    if (is_i) return true;
+    return kdec(lk) > __dadd_rn(kdec(uk), kTol);
+}
+
+// Variables changed in the previous round: bring their new bounds into this round's
+// write buffer (atomic, so it commutes with this round's tightenings) and check crossings.
+__device__ void do_fix(const BpArgs& A, const DevProblem& P, const Phase& ph, const int* chg_prev, int nprev, int tl) {
+    const int idx = tl * 32 + (threadIdx.x & 31);
+    if (idx >= nprev) return;
+    const int v = __ldcg(chg_prev + idx);
+    const longlong2 b = ld_bounds(ph.R, v);
+    atomicMax(&ph.X[v].x, b.x);
+    atomicMin(&ph.X[v].y, b.y);
+    if (crossed(P.is_int[v] != 0, b.x, b.y)) atomicMin(&A.ctl->cross[ph.par].v, v);
+}
+
+// -------------------------------------------------------------------- barrier
+// All blocks arrive; the last one runs `book` (thread 0) and releases the others.  After the
+// release thread 0 of every block reads the stop flag and the descriptor of phase `next`
+// into shared memory (one reader per block keeps the control lines cold).
+template <class F>
+__device__ void grid_barrier(Stage& st, Ctl* ctl, const DevProblem& P, const BpArgs& A, int next, F&& book) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned gen = ld_acquire_u32(&ctl->bar_gen.v);
+        __threadfence();
+        const unsigned old = atom_add_acqrel_u32(&ctl->bar_count.v, 1u);
+        if (old == gridDim.x - 1) {
+            ctl->bar_count.v = 0;
+            book();
+            __threadfence();
+            st_release_u32(&ctl->bar_gen.v, gen + 1);
+        } else {
+            const long long t0 = clock64();
+            while (ld_acquire_u32(&ctl->bar_gen.v) == gen) {
+                if (clock64() - t0 > kSpinLimit) {
+                    atomicExch(&ctl->error, BP_ERR_TIMEOUT);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        st.flag = ld_acquire_s32(&ctl->stop) | (ld_acquire_s32(&ctl->error) != 0);
+        const int par = next & 1;
+        const bool stat = (next == 0 && !A.w0);
+#pragma unroll
+        for (int c = 0; c < kNumClass; ++c)
+            st.d_cnt[c] = stat ? P.class_off[c + 1] - P.class_off[c] : __ldcg(&ctl->cnt[par][c].v);
+        st.d_ntask = stat ? P.nchunks : __ldcg(&ctl->ntask[par].v);
+        st.d_nprev = next == 0 ? 0 : __ldcg(&ctl->nchg[par ^ 1].v);
+    }
+    __syncthreads();
+}
+
+__device__ void finish_block(Stage& st, const BpArgs& A) {
+    // the last block out writes the result slot
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned old = atom_add_acqrel_u32(&A.ctl->done.v, 1u);
+        if (old == gridDim.x - 1) {
+            Ctl* c = A.ctl;
+            bp_result r;
+            r.error = c->error;
+            r.status = c->status;
+            r.rounds = c->rounds;
+            r.first_infeasible_row = c->first_row == INT_MAX ? -1 : c->first_row;
+            r.first_infeasible_var = c->first_var.v == INT_MAX ? -1 : c->first_var.v;
+            if (r.first_infeasible_var >= 0) r.status = BP_INFEASIBLE;
+            r.nnz_updates = (int64_t)c->nnz_total;
+            r.n_changed = (int64_t)c->n_changed.v;
+            r.reserved = 0;
+            *A.dres = r;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------- kernel
+__global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProblem P, BpArgs A) {
+    __shared__ Stage st;
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int NW = gridDim.x * kWarpsPerBlock;
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthreads = gridDim.x * blockDim.x;
+    Ctl* ctl = A.ctl;
+    for (int i = threadIdx.x; i < kWarpsPerBlock * kSlots; i += kThreads) (&st.wcnt[0][0])[i] = 0;
+    if (threadIdx.x == 0) st.bq_n = 0;
+    if (threadIdx.x == 0) st.nnz = 0;
+    __syncthreads();
+
+    // ---- prologue: normalised start bounds into both buffers; rows of round 0
+    for (int v = gtid; v < P.n; v += gthreads) {
+        double l = A.lb[v], u = A.ub[v];
+        if (l <= -kInfBound) l = -INFINITY;
+        if (u >= kInfBound) u = INFINITY;
+        const bool is_i = P.is_int[v] != 0;
+        if (is_i) {
+            if (isfinite(l)) l = ceil(__dsub_rn(l, kTol));
+            if (isfinite(u)) u = floor(__dadd_rn(u, kTol));
+        }
+        const longlong2 b = make_longlong2(dkey(l), dkey(u));
+        A.bk[0][v] = b;
+        A.bk[1][v] = b;
+        if (crossed(is_i, b.x, b.y)) atomicMin(&ctl->entry_cross, v);
+    }
+    for (int h = gtid; h < P.nheavy; h += gthreads) A.harr[h] = 0;  // clean even after an aborted launch
+    Phase ph0{0, 0, 1, A.bk[0], A.bk[1], A.base, A.base};
+    if (A.w0) {
+        // queue the given rows into the round-0 lists (stamp `base` = member of round 0)
+        Phase q = ph0;
+        q.npar = 0;
+        const int gw0 = gtid >> 5, nw0 = gthreads >> 5;
+        for (int b = gw0 * 32; b < A.w0_len; b += nw0 * 32) {
+            const int i = b + lane;
+            warp_queue_rows(st, A, P, q, i < A.w0_len ? __ldg(A.w0 + i) : -1);
+        }
+        warp_flush_all(st, A, P, q);
+    }
+    grid_barrier(st, ctl, P, A, 0, [&] {
+        int rows0 = 0;
+        if (A.w0) {
+            for (int c = 0; c < kNumClass; ++c) rows0 += ctl->cnt[0][c].v;
+        } else {
+            rows0 = P.m;
+        }
+        if (ctl->entry_cross != INT_MAX) {
+            ctl->status = BP_INFEASIBLE;
+            ctl->rounds = 0;
+            ctl->result_par = 0;
+            ctl->first_var.v = ctl->entry_cross;
+            ctl->stop = 1;
+        } else if (rows0 == 0 || A.max_rounds <= 0) {
+            ctl->status = rows0 == 0 ? BP_FIXPOINT : BP_ROUND_LIMIT;
+            ctl->rounds = 0;
+            ctl->result_par = 0;
+            ctl->stop = 1;
+        }
+    });
+
+    // ---- rounds
+    for (int t = 0; !st.flag; ++t) {
+        Phase ph;
+        ph.t = t;
+        ph.par = t & 1;
+        ph.npar = ph.par ^ 1;
+        ph.R = A.bk[ph.par];
+        ph.X = A.bk[ph.npar];
+        ph.st_v = A.base + t;
+        ph.st_r = A.base + t + 1;
+        const bool stat = (t == 0 && !A.w0);
+        const int* rows = stat ? P.static_list : A.list[ph.par];
+        const int2* tasks = stat ? P.static_tasks : A.task[ph.par];
+        const int ntask = st.d_ntask;
+        const int nprev = st.d_nprev;
+        const int* chg_prev = A.chg[ph.npar];
+        int cnt[kNumClass];
+#pragma unroll
+        for (int c = 0; c < kNumClass; ++c) cnt[c] = st.d_cnt[c];
+        bool alive = true;
+        // block tasks: partial sums of chunked rows, then block-per-row rows
+        const int nblk = ntask + cnt[kClassBlockRow];
+        for (int bt = blockIdx.x; bt < nblk; bt += gridDim.x) {
+            if (bt < ntask) {
+                do_chunk_partial(st, A, P, ph, __ldcg(tasks + bt));
+            } else {
+                do_block_row(st, A, P, ph, __ldcg(rows + P.class_off[kClassBlockRow] + (bt - ntask)));
+            }
+        }
+        // warp tasks: fix-ups of the previous round's changes, thread-per-row bins, warp rows
+        const int s_fix = (nprev + 31) / 32;
+        int s_bin[kNumThreadBins];
+        int total = s_fix + cnt[kClassWarpRow];
+#pragma unroll
+        for (int c = 0; c < kNumThreadBins; ++c) {
+            s_bin[c] = (cnt[c] + 31) / 32;
+            total += s_bin[c];
+        }
+        for (int task = gw; task < total; task += NW) {
+            int tl = task;
+            if (tl < s_fix) {
+                do_fix(A, P, ph, chg_prev, nprev, tl);
+                continue;
+            }
+            tl -= s_fix;
+            bool done = false;
+#pragma unroll
+            for (int c = 0; c < kNumThreadBins; ++c) {
+                if (!done) {
+                    if (tl < s_bin[c]) {
+                        do_thread_rows(st, A, P, ph, rows + P.class_off[c], cnt[c], tl);
+                        done = true;
+                    } else {
+                        tl -= s_bin[c];
+                    }
+                }
+            }
+            if (done) continue;
+            do_warp_row(st, A, P, ph, __ldcg(rows + P.class_off[kClassWarpRow] + tl));
+        }
+        __syncthreads();
+        // block tasks that wait: candidates of chunked rows
+        for (int bt = blockIdx.x; bt < ntask && alive; bt += gridDim.x)
+            alive = do_chunk_candidates(st, A, P, ph, __ldcg(tasks + bt));
+        // changes of this block: dedupe grid-wide, list them, queue their rows
+        drain_changed(st, A, P, ph);
+        // staged appends to the global lists; nonzeros of this phase: one atomic per block
+        warp_flush_all(st, A, P, ph);
+        __syncthreads();
+        if (threadIdx.x == 0 && st.nnz) {
+            atomicAdd(&ctl->nnz[ph.par].v, st.nnz);
+            st.nnz = 0;
+        }
+        grid_barrier(st, ctl, P, A, t + 1, [&] {
+            const int par = t & 1, npar = par ^ 1;
+            int nw = 0;
+            for (int c = 0; c < kNumClass; ++c) nw += ctl->cnt[npar][c].v;
+            if (A.trace && t < A.max_rounds) {
+                int rows_t = 0;
+                if (t == 0 && !A.w0) {
+                    rows_t = P.m;
+                } else {
+                    for (int c = 0; c < kNumClass; ++c) rows_t += ctl->cnt[par][c].v;
+                }
+                A.trace[4 * t + 0] = rows_t;
+                A.trace[4 * t + 1] = (long long)ctl->nnz[par].v;
+                A.trace[4 * t + 2] = ctl->nchg[par].v;
+                A.trace[4 * t + 3] = (long long)globaltimer_ns();
+            }
+            if (ctl->cross[par].v != INT_MAX) {
+                // bounds after round t-1 cross: that round is the last one
+                ctl->status = BP_INFEASIBLE;
+                ctl->rounds = t;
+                ctl->result_par = par;
+                ctl->first_var.v = ctl->cross[par].v;
+                ctl->first_row = INT_MAX;
+                ctl->stop = 1;
+                return;
+            }
+            ctl->nnz_total += ctl->nnz[par].v;
+            ctl->rounds = t + 1;
+            ctl->result_par = npar;
+            if (ctl->rowinf[par].v != INT_MAX) {
+                ctl->status = BP_INFEASIBLE;
+                ctl->first_row = ctl->rowinf[par].v;
+                ctl->epi_par = par;
+                ctl->epi_n = ctl->nchg[par].v;
+                ctl->stop = 1;
+            } else if (nw == 0) {
+                ctl->status = BP_FIXPOINT;
+                ctl->stop = 1;
+            } else if (t + 1 >= A.max_rounds) {
+                ctl->status = BP_ROUND_LIMIT;
+                ctl->epi_par = par;
+                ctl->epi_n = ctl->nchg[par].v;
+                ctl->stop = 1;
+            } else {
+                // reset the append targets of round t+1
+                for (int c = 0; c < kNumClass; ++c) ctl->cnt[par][c].v = 0;
+                ctl->ntask[par].v = 0;
+                ctl->nchg[npar].v = 0;
+                ctl->nnz[npar].v = 0;
+                ctl->rowinf[npar].v = INT_MAX;
+                ctl->cross[npar].v = INT_MAX;
+            }
+        });
+    }
+
+    // ---- epilogue
+    if (!ld_acquire_s32(&ctl->error)) {
+        const int epi_n = __ldcg(&ctl->epi_n);
+        const longlong2* res = A.bk[__ldcg(&ctl->result_par)];
+        if (epi_n > 0) {
+            const int* lst = A.chg[__ldcg(&ctl->epi_par)];
+            for (int i = gtid; i < epi_n; i += gthreads) {
+                const int v = __ldcg(lst + i);
+                const longlong2 b = __ldcg(res + v);
+                if (crossed(P.is_int[v] != 0, b.x, b.y)) atomicMin(&ctl->first_var.v, v);
+            }
+        }
+        unsigned long long changed = 0;
+        for (int v = gtid; v < P.n; v += gthreads) {
+            double l = A.lb[v], u = A.ub[v];
+            if (l <= -kInfBound) l = -INFINITY;
+            if (u >= kInfBound) u = INFINITY;
+            if (P.is_int[v]) {
+                if (isfinite(l)) l = ceil(__dsub_rn(l, kTol));
+                if (isfinite(u)) u = floor(__dadd_rn(u, kTol));
+            }
+            const longlong2 b = __ldcg(res + v);
+            changed += (b.x != dkey(l) || b.y != dkey(u)) ? 1ull : 0ull;
+            A.lb[v] = kdec(b.x);
+            A.ub[v] = kdec(b.y);
+        }
+        for (int off = 16; off > 0; off >>= 1) changed += __shfl_xor_sync(0xffffffffu, changed, off);
+        if (lane == 0 && changed) atomicAdd(&ctl->n_changed.v, changed);
+    }
+    finish_block(st, A);
+}
+
+// ------------------------------------------------------------------------ host
+void ctl_template(Ctl* c) {
+    memset(c, 0, sizeof(Ctl));
+    c->rowinf[0].v = c->rowinf[1].v = INT_MAX;
+    c->cross[0].v = c->cross[1].v = INT_MAX;
+    c->entry_cross = INT_MAX;
+    c->first_row = INT_MAX;
+    c->first_var.v = INT_MAX;
+    c->epi_par = 0;
+    c->epi_n = 0;
+}
+
+int engine_prepare(mip_problem* p) {
+    Work& w = p->w;
+    const int m = p->m, n = p->n;
+    const DevProblem& dp = p->dp;
+    BP_TRY(dalloc(p, &w.bkey[0], (size_t)n));
+    BP_TRY(dalloc(p, &w.bkey[1], (size_t)n));
+    BP_TRY(dalloc(p, &w.vstamp, (size_t)n));
+    BP_TRY(dalloc(p, &w.rstamp, (size_t)m));
+    BP_TRY(dalloc(p, &w.list[0], (size_t)m));
+    BP_TRY(dalloc(p, &w.list[1], (size_t)m));
+    BP_TRY(dalloc(p, &w.chg[0], (size_t)n));
+    BP_TRY(dalloc(p, &w.chg[1], (size_t)n));
+    BP_TRY(dalloc(p, &w.task[0], (size_t)dp.nchunks));
+    BP_TRY(dalloc(p, &w.task[1], (size_t)dp.nchunks));
+    BP_TRY(dalloc(p, &w.hpart, (size_t)dp.nchunks));
+    BP_TRY(dalloc(p, &w.hpinf, (size_t)dp.nchunks));
+    BP_TRY(dalloc(p, &w.htot, (size_t)dp.nheavy));
+    BP_TRY(dalloc(p, &w.htinf, (size_t)dp.nheavy));
+    BP_TRY(dalloc(p, &w.harr, (size_t)dp.nheavy));
+    BP_TRY(dalloc(p, &w.hready, (size_t)dp.nheavy));
+    BP_TRY(dalloc(p, &w.ctl, 1));
+    BP_TRY(dalloc(p, &w.dres, 1));
+    BP_TRY(dalloc(p, &w.stage_lb, (size_t)n));
+    BP_TRY(dalloc(p, &w.stage_ub, (size_t)n));
+    void* h = nullptr;
+    BP_CUDA_TRY(cudaMallocHost(&h, sizeof(Ctl)));
+    p->host_allocs.push_back(h);
+    w.ctl_host = static_cast<Ctl*>(h);
+    ctl_template(w.ctl_host);
+    w.stamp_base = 1;
+    // persistent grid: every block must be resident (cooperative launch)
+    int occ = 0;
+    BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bp_kernel, kThreads, 0));
+    int sms = 0;
+    BP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+    if (occ < 1) {
+        set_error("propagation kernel cannot be resident on this device");
+        return BP_ERR_CUDA;
+    }
+    p->grid_blocks = sms * (occ > 4 ? 4 : occ);
+    return BP_OK;
+}
+
+int launch_propagate(mip_problem* p, double* lb, double* ub, const int* w0, int w0_len, double theta,
+                     int max_rounds, int64_t* trace, cudaStream_t s) {
+    Work& w = p->w;
+    const long long span = (long long)(max_rounds > 0 ? max_rounds : 0) + 3;
+    if (w.stamp_base + span >= (long long)INT_MAX - 16) {
+        // stamps would overflow: clear them and restart
+        BP_CUDA_TRY(cudaMemsetAsync(w.vstamp, 0, sizeof(int) * (p->n ? p->n : 1), s));
+        BP_CUDA_TRY(cudaMemsetAsync(w.rstamp, 0, sizeof(int) * (p->m ? p->m : 1), s));
+        BP_CUDA_TRY(cudaMemsetAsync(w.hready, 0, sizeof(int) * (p->dp.nheavy ? p->dp.nheavy : 1), s));
+        w.stamp_base = 1;
+    }
+    BpArgs a;
+    a.lb = lb;
+    a.ub = ub;
+    a.bk[0] = w.bkey[0];
+    a.bk[1] = w.bkey[1];
+    a.vstamp = w.vstamp;
+    a.rstamp = w.rstamp;
+    a.list[0] = w.list[0];
+    a.list[1] = w.list[1];
+    a.chg[0] = w.chg[0];
+    a.chg[1] = w.chg[1];
+    a.task[0] = w.task[0];
+    a.task[1] = w.task[1];
+    a.hpart = w.hpart;
+    a.hpinf = w.hpinf;
+    a.htot = w.htot;
+    a.htinf = w.htinf;
+    a.harr = w.harr;
+    a.hready = w.hready;
+    a.ctl = w.ctl;
+    a.dres = w.dres;
+    a.w0 = w0;
+    a.w0_len = w0_len;
+    a.theta = theta;
+    a.max_rounds = max_rounds;
+    a.base = (int)w.stamp_base;
+    a.trace = (long long*)trace;
+    w.stamp_base += span;
+    BP_CUDA_TRY(cudaMemcpyAsync(w.ctl, w.ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    DevProblem dp = p->dp;
+    void* args[] = {&dp, &a};
+    BP_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)bp_kernel, dim3(p->grid_blocks), dim3(kThreads), args, 0, s));
+    p->last_stream = s;
+    return BP_OK;
+}
+
+}  // namespace gpubp
+
+using namespace gpubp;
+
+extern "C" int bp_propagate(mip_problem* p, double* lb, double* ub, const bp_params* params, bp_result* result,
+                            void* stream) {
+    if (!p || (p->n && (!lb || !ub))) {
+        set_error("null argument");
+        return BP_ERR_INVALID;
+    }
+    bp_params prm;
+    if (params) {
+        prm = *params;
+    } else {
+        bp_params_default(&prm);
+    }
+    if (!(prm.theta >= 0.0) || prm.max_rounds < 0 ||
+        (prm.bounds_mem != BP_MEM_DEVICE && prm.bounds_mem != BP_MEM_HOST)) {
+        set_error("invalid parameters (theta >= 0, max_rounds >= 0, bounds_mem host/device)");
+        return BP_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    double *dl = lb, *du = ub;
+    const size_t bytes = sizeof(double) * (size_t)p->n;
+    if (prm.bounds_mem == BP_MEM_HOST) {
+        dl = p->w.stage_lb;
+        du = p->w.stage_ub;
+        if (p->n) {
+            BP_CUDA_TRY(cudaMemcpyAsync(dl, lb, bytes, cudaMemcpyHostToDevice, s));
+            BP_CUDA_TRY(cudaMemcpyAsync(du, ub, bytes, cudaMemcpyHostToDevice, s));
+        }
+    }
+    BP_TRY(launch_propagate(p, dl, du, nullptr, 0, prm.theta, prm.max_rounds, prm.trace, s));
+    if (prm.bounds_mem == BP_MEM_HOST && p->n) {
+        BP_CUDA_TRY(cudaMemcpyAsync(lb, dl, bytes, cudaMemcpyDeviceToHost, s));
+        BP_CUDA_TRY(cudaMemcpyAsync(ub, du, bytes, cudaMemcpyDeviceToHost, s));
+    }
+    if (result) BP_CUDA_TRY(cudaMemcpyAsync(result, p->w.dres, sizeof(bp_result), cudaMemcpyDeviceToHost, s));
+    return BP_OK;
+}
+
+extern "C" const bp_result* bp_result_device(const mip_problem* p) { return p ? p->w.dres : nullptr; }

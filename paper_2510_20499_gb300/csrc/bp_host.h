@@ -1,0 +1,126 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "bp_device.cuh"
+#include "gpubp.h"
+
+namespace gpubp {
+
+// Control block of one propagation launch (device memory).  Every counter that many blocks
+// update or poll sits on its own 128-byte line so that the blocks do not contend for one L2
+// line.  The layout is private to the library; it is reset from a constant template before
+// each launch.
+template <class T>
+struct alignas(128) Pad {
+    T v;
+};
+
+struct alignas(128) Ctl {
+    Pad<unsigned> bar_count;               // grid barrier: arrivals
+    Pad<unsigned> bar_gen;                 // grid barrier: generation
+    Pad<int> cnt[2][kNumClass];            // worklist rows appended, per parity and class
+    Pad<int> ntask[2];                     // chunk tasks appended, per parity
+    Pad<int> nchg[2];                      // changed variables appended, per parity
+    Pad<unsigned long long> nnz[2];        // nonzeros processed in the phase of that parity
+    Pad<int> rowinf[2];                    // smallest infeasible row of the phase
+    Pad<int> cross[2];                     // smallest crossing variable found in the phase
+    Pad<int> first_var;                    // smallest crossing variable of the final round
+    Pad<unsigned long long> n_changed;
+    Pad<unsigned> done;
+    // written once per round by the last block at the barrier, read by thread 0 of each block
+    int stop, error;
+    int entry_cross;
+    int status, rounds, result_par, first_row;
+    int epi_par, epi_n;                    // changed list to crossing-check at the end
+    unsigned long long nnz_total;
+};
+
+void ctl_template(Ctl* c);
+
+// Per-launch scratch of the propagation engine.
+struct Work {
+    longlong2* bkey[2] = {nullptr, nullptr};   // bounds as ordered keys, double-buffered
+    int* vstamp = nullptr;                     // n: last round stamp a variable changed
+    int* rstamp = nullptr;                     // m: last round stamp a row was queued
+    int* list[2] = {nullptr, nullptr};         // m each: worklist rows by class segment
+    int* chg[2] = {nullptr, nullptr};          // n each: changed variables
+    int2* task[2] = {nullptr, nullptr};        // chunk tasks {row, chunk}
+    double* hpart = nullptr;                   // partial activity per chunk slot
+    int2* hpinf = nullptr;                     // {ninf, infj} per chunk slot
+    double* htot = nullptr;                    // per chunked row: total finite activity
+    int2* htinf = nullptr;
+    int* harr = nullptr;                       // per chunked row: arrivals in this round
+    int* hready = nullptr;                     // per chunked row: stamp of a ready total
+    Ctl* ctl = nullptr;
+    Ctl* ctl_host = nullptr;                   // pinned constant template
+    bp_result* dres = nullptr;                 // device result slot
+    double* stage_lb = nullptr;                // device staging for host bounds
+    double* stage_ub = nullptr;
+    long long stamp_base = 1;
+};
+
+}  // namespace gpubp
+
+struct mip_problem {
+    int device = 0;
+    int32_t m = 0, n = 0;
+    int64_t nnz = 0;
+    gpubp::DevProblem dp{};
+    double* def_lb = nullptr;
+    double* def_ub = nullptr;
+    double* obj = nullptr;
+    gpubp::Work w;
+    int grid_blocks = 0;                       // persistent grid size
+    std::vector<void*> allocs;                 // every device allocation of the handle
+    std::vector<void*> host_allocs;            // pinned host allocations
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace gpubp {
+
+// thread-local error text
+void set_error(const char* fmt, ...);
+int fail_cuda(cudaError_t e, const char* what);
+
+// allocation helpers (record on the handle, zero-initialised)
+template <class T>
+int dalloc(mip_problem* p, T** out, size_t count) {
+    void* ptr = nullptr;
+    size_t bytes = sizeof(T) * (count ? count : 1);
+    cudaError_t e = cudaMalloc(&ptr, bytes);
+    if (e != cudaSuccess) {
+        set_error("cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        return BP_ERR_OOM;
+    }
+    p->allocs.push_back(ptr);
+    e = cudaMemset(ptr, 0, bytes);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaMemset");
+    *out = static_cast<T*>(ptr);
+    return BP_OK;
+}
+
+// exclusive scan of n ints on the device; writes the total to *total_dev if non-null.
+int scan_exclusive(const int* in, int* out, int n, int* total_dev, cudaStream_t s);
+
+int engine_prepare(mip_problem* p);     // allocates Work
+int launch_propagate(mip_problem* p, double* lb, double* ub, const int* w0, int w0_len,
+                     double theta, int max_rounds, int64_t* trace, cudaStream_t s);
+
+}  // namespace gpubp
+
+#define BP_CUDA_TRY(expr)                                           \
+    do {                                                            \
+        cudaError_t _e = (expr);                                    \
+        if (_e != cudaSuccess) return gpubp::fail_cuda(_e, #expr);  \
+    } while (0)
+#define BP_TRY(expr)                 \
+    do {                             \
+        int _r = (expr);             \
+        if (_r != BP_OK) return _r;  \
+    } while (0)

@@ -1,0 +1,46 @@
+"""Comparison of GPU propagation results with the oracle (used by the gpu tests)."""
+import numpy as np
+
+import oracle
+
+REL_CONT = 1e-9   # continuous bounds: relative agreement required with the oracle
+
+
+def run_gpu(prob, lb, ub, **kw):
+    import torch
+    gl = torch.tensor(np.asarray(lb, dtype=np.float64), device="cuda")
+    gu = torch.tensor(np.asarray(ub, dtype=np.float64), device="cuda")
+    r = prob.propagate(gl, gu, **kw)
+    return gl.cpu().numpy(), gu.cpu().numpy(), r
+
+
+def assert_bounds_match(p, gl, gu, ol, ou):
+    ints = p.is_int == 1
+    np.testing.assert_array_equal(gl[ints], ol[ints], err_msg="integer lower bounds")
+    np.testing.assert_array_equal(gu[ints], ou[ints], err_msg="integer upper bounds")
+    for g, o, what in ((gl, ol, "lower"), (gu, ou, "upper")):
+        c = ~ints
+        inf = ~np.isfinite(o[c])
+        np.testing.assert_array_equal(g[c][inf], o[c][inf], err_msg=f"infinite continuous {what} bounds")
+        fin = ~inf
+        d = np.abs(g[c][fin] - o[c][fin])
+        tol = REL_CONT * np.maximum(1.0, np.abs(o[c][fin]))
+        bad = np.flatnonzero(d > tol)
+        assert len(bad) == 0, f"continuous {what} bounds differ beyond 1e-9 rel at {len(bad)} vars, max {d.max()}"
+
+
+def compare(p, gl, gu, gr, ol, ou, orr, exact_counts=True):
+    """The GPU must match the oracle: status, rounds, work count, first infeasible indices
+    and integer bounds exactly, continuous bounds within 1e-9 relative.  Only when the
+    oracle saw a fragile decision (a decision that summation order may flip) is the run
+    compared on soundness alone."""
+    assert gr["error"] == 0, gr
+    if orr["fragile"]:
+        return False
+    for key in ("status", "rounds", "first_infeasible_row", "first_infeasible_var"):
+        assert gr[key] == orr[key], (key, gr[key], orr[key])
+    if exact_counts:
+        assert gr["nnz_updates"] == orr["nnz_updates"], (gr["nnz_updates"], orr["nnz_updates"])
+        assert gr["n_changed"] == orr["n_changed"], (gr["n_changed"], orr["n_changed"])
+    assert_bounds_match(p, gl, gu, ol, ou)
+    return True
