@@ -87,19 +87,29 @@ __device__ __forceinline__ void report(unsigned long long* err, long long idx, i
 
 __global__ void k_validate_rows(int m, int n, long long nnz, const int64_t* rp, const int32_t* col,
                                 const double* val, const double* g, unsigned long long* err) {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
-        int64_t b = rp[k], e = rp[k + 1];
+    // one warp per row
+    const int lane = threadIdx.x & 31;
+    for (long long k = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; k < m;
+         k += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const int64_t b = rp[k], e = rp[k + 1];
         // every access below stays inside [0, nnz): malformed offsets are reported, not read
-        if (e < b || b < 0 || e > nnz) { report(err, k, 1); continue; }
-        double gk = g[k];
-        if (isnan(gk) || gk <= -kInfBound) report(err, k, 4);
-        int prev = -1;
-        for (int64_t q = b; q < e; ++q) {
-            int j = col[q];
-            if (j < 0 || j >= n || j <= prev) { report(err, k, 2); break; }
-            prev = j;
-            double a = val[q];
-            if (!(fabs(a) >= 1e-12) || !(fabs(a) < kInfBound)) { report(err, k, 3); break; }
+        if (e < b || b < 0 || e > nnz) {
+            if (lane == 0) report(err, k, 1);
+            continue;
+        }
+        const double gk = g[k];
+        if (lane == 0 && (isnan(gk) || gk <= -kInfBound)) report(err, k, 4);
+        bool bad_col = false, bad_val = false;
+        for (int64_t q = b + lane; q < e; q += 32) {
+            const int j = col[q];
+            if (j < 0 || j >= n || (q > b && j <= col[q - 1])) bad_col = true;
+            const double a = val[q];
+            if (!(fabs(a) >= 1e-12) || !(fabs(a) < kInfBound)) bad_val = true;
+        }
+        if (__any_sync(0xffffffffu, bad_col)) {
+            if (lane == 0) report(err, k, 2);
+        } else if (__any_sync(0xffffffffu, bad_val)) {
+            if (lane == 0) report(err, k, 3);
         }
     }
 }
@@ -271,7 +281,7 @@ static int load_impl(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t
     unsigned long long* d_err;
     BP_TRY(dalloc(p, &d_err, 1));
     BP_CUDA_TRY(cudaMemsetAsync(d_err, 0xff, sizeof(unsigned long long), s));
-    if (m) k_validate_rows<<<grid_for(m), 256, 0, s>>>(m, n, nnz, d_rp64, d_col, d_val, d_g, d_err);
+    if (m) k_validate_rows<<<grid_for((long long)m * 32), 256, 0, s>>>(m, n, nnz, d_rp64, d_col, d_val, d_g, d_err);
     if (n) k_validate_bounds<<<grid_for(n), 256, 0, s>>>(n, d_lb, d_ub, d_err);
     BP_CUDA_TRY(cudaGetLastError());
     unsigned long long herr = 0;
