@@ -186,8 +186,9 @@ typedef struct {
  * root_lb/root_ub: device, n doubles (normally a bp_propagate fixpoint).
  * var: device int32[P]; boxes: device double[4P] (see probe_split).
  * Returns BP_OK, BP_ERR_CAPACITY (cache->needed holds the required entry count; the status,
- * rounds, nnz_updates and offsets arrays are complete), BP_ERR_TIMEOUT, BP_ERR_INVALID.
- * The call synchronises the stream once (to read the entry count).
+ * rounds, nnz_updates and offsets arrays are complete), BP_ERR_INVALID (also for a variable
+ * index outside [0, n)).  The call synchronises the stream (it checks the variable indices
+ * and reads the entry count).
  */
 int bp_probe_batch(mip_problem *p, const double *root_lb, const double *root_ub, int32_t P,
                    const int32_t *var, const double *boxes, const bp_params *params,

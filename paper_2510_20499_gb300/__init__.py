@@ -184,6 +184,42 @@ class Problem:
         return res.as_dict()
 
 
+def _probe_cache(torch, dev, P, cap):
+    return dict(status=torch.empty(2 * P, dtype=torch.int32, device=dev),
+                rounds=torch.empty(2 * P, dtype=torch.int32, device=dev),
+                nnz_updates=torch.empty(2 * P, dtype=torch.int64, device=dev),
+                offsets=torch.empty(2 * P + 1, dtype=torch.int64, device=dev),
+                var=torch.empty(max(1, cap), dtype=torch.int32, device=dev),
+                l=torch.empty(max(1, cap), dtype=torch.float64, device=dev),
+                u=torch.empty(max(1, cap), dtype=torch.float64, device=dev))
+
+
+def _probe_batch(prob, root_lb, root_ub, var, boxes, theta=1e-3, max_rounds=10000, cap=None, stream=None):
+    """bp_probe_batch on device tensors: root bounds (float64, n), var (int32, P), boxes
+    (float64, P x 4).  Returns the cache as device tensors; grows its capacity when needed."""
+    torch = _torch()
+    P = int(var.numel())
+    cap = int(cap) if cap is not None else max(1024, 16 * P)
+    prm = params(theta, max_rounds)
+    while True:
+        c = _probe_cache(torch, prob.device, P, cap)
+        pc = ProbeCache(_ptr(c["status"]).value, _ptr(c["rounds"]).value, _ptr(c["nnz_updates"]).value,
+                        _ptr(c["offsets"]).value, _ptr(c["var"]).value, _ptr(c["l"]).value, _ptr(c["u"]).value,
+                        cap, 0)
+        code = lib().bp_probe_batch(prob.h, _ptr(root_lb), _ptr(root_ub), P, _ptr(var), _ptr(boxes), C.byref(prm),
+                                    C.byref(pc), _stream(stream))
+        if code == BP_ERR_CAPACITY:
+            cap = int(pc.needed)
+            continue
+        _check(code)
+        n = int(pc.needed)
+        c["var"], c["l"], c["u"] = c["var"][:n], c["l"][:n], c["u"][:n]
+        return c
+
+
+Problem.probe_batch = _probe_batch
+
+
 def probe_split(is_int, l, u):
     out = (C.c_double * 4)()
     ok = lib().probe_split(int(is_int), float(l), float(u), out)

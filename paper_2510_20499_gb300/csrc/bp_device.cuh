@@ -126,6 +126,98 @@ __device__ __forceinline__ unsigned atom_add_acqrel_u32(unsigned* p, unsigned v)
     return old;
 }
 
+// ----------------------------------------------------------- candidate math
+// Candidate of variable j (coefficient a, round-start bounds {lk, uk}) from a row with
+// finite activity part minfin and ninf infinite terms (Section 2.1):
+//   a > 0: u <= (g - (minfin - a l)) / a,   a < 0: l >= (g - (minfin - a u)) / a
+// (with ninf == 1 the variable is the infinite term and the residual is minfin itself), each
+// operation rounded to nearest; integers round with floor(c + tol) / ceil(c - tol) and move
+// on any improvement, continuous bounds move when the improvement exceeds
+// theta * max(1, |old|) or the old bound is infinite.  Returns 1 (new upper key in *nk),
+// 2 (new lower key in *nk) or 0 (nothing).
+__device__ __forceinline__ int eval_candidate(double a, long long lk, long long uk, double minfin, int ninf,
+                                              double g, bool is_i, double theta, long long* nk) {
+    double resid;
+    if (ninf == 1) {
+        resid = minfin;
+    } else {
+        const double b = kdec(a > 0 ? lk : uk);
+        resid = __dsub_rn(minfin, __dmul_rn(a, b));
+    }
+    const double num = __dsub_rn(g, resid);
+    const double cand = __ddiv_rn(num, a);
+    if (!(fabs(cand) < kInfBound)) return 0;
+    if (a > 0) {
+        if (is_i) {
+            *nk = dkey(floor(__dadd_rn(cand, kTol)));
+            return *nk < uk ? 1 : 0;
+        }
+        *nk = dkey(cand);
+        if (uk == kKeyPosInf) return 1;
+        const double u = kdec(uk);
+        return __dsub_rn(u, cand) > __dmul_rn(theta, fmax(1.0, fabs(u))) ? 1 : 0;
+    }
+    if (is_i) {
+        *nk = dkey(ceil(__dsub_rn(cand, kTol)));
+        return *nk > lk ? 2 : 0;
+    }
+    *nk = dkey(cand);
+    if (lk == kKeyNegInf) return 2;
+    const double l = kdec(lk);
+    return __dsub_rn(cand, l) > __dmul_rn(theta, fmax(1.0, fabs(l))) ? 2 : 0;
+}
+
+// Conservative test that a candidate from a row with finite activity cannot tighten the
+// variable's bound: slack = g - L_min >= |a| (u - l) + margin, in FP32 with directed
+// brackets.  The margin covers the rounding of the FP64 candidate (a few units of 2^-53 of
+// |g| + |L_min| + |a| (|l| + |u|)), so a skipped candidate is one the exact evaluation would
+// reject; a false "may tighten" only costs that evaluation.
+struct RowFilter {
+    float slack_dn;   // lower bracket of g - L_min (computed in FP64 once per row)
+    float mag_up;     // upper bracket of |g| + |L_min|
+};
+
+__device__ __forceinline__ RowFilter row_filter(double g, double minfin) {
+    RowFilter f;
+    f.slack_dn = f_dn(__dsub_rn(g, minfin));
+    f.mag_up = __fadd_ru(fabs_up(g), fabs_up(minfin));
+    return f;
+}
+
+__device__ __forceinline__ bool cannot_tighten(const RowFilter& f, double a, long long lk, long long uk) {
+    const double l = kdec(lk), u = kdec(uk);
+    const float a_up = fabs_up(a);
+    const float w_up = __fsub_ru(f_up(u), f_dn(l));
+    const float prod = __fmul_ru(a_up, w_up);
+    const float big = __fadd_ru(f.mag_up, __fmul_ru(2.0f, __fmul_ru(a_up, __fadd_ru(fabs_up(l), fabs_up(u)))));
+    const float margin = __fmul_ru(1e-15f, big);
+    return f.slack_dn >= __fadd_ru(prod, margin);
+}
+
+// Row infeasible: no infinite term and L_min > g + tol (gt = g + tol, precomputed).
+__device__ __forceinline__ bool row_infeasible(double minfin, int ninf, double gt) {
+    return ninf == 0 && dkey(minfin) > dkey(gt);
+}
+
+// Bounds cross: integer l > u, continuous l > u + tol.
+__device__ __forceinline__ bool crossed(bool is_i, long long lk, long long uk) {
+    if (lk <= uk) return false;
+    if (is_i) return true;
+    return kdec(lk) > __dadd_rn(kdec(uk), kTol);
+}
+
+// Normalised bound keys of a caller's (l, u): |b| >= 1e20 is infinite, integer bounds rounded
+// inward with the tolerance.
+__device__ __forceinline__ longlong2 normalized_keys(double l, double u, bool is_i) {
+    if (l <= -kInfBound) l = -INFINITY;
+    if (u >= kInfBound) u = INFINITY;
+    if (is_i) {
+        if (isfinite(l)) l = ceil(__dsub_rn(l, kTol));
+        if (isfinite(u)) u = floor(__dadd_rn(u, kTol));
+    }
+    return make_longlong2(dkey(l), dkey(u));
+}
+
 // --------------------------------------------------------------- host structs
 // Device view of a loaded problem.
 struct DevProblem {

@@ -248,91 +248,19 @@ __device__ void drain_changed(Stage& st, const BpArgs& A, const DevProblem& P, c
     __syncthreads();
 }
 
-// Exact candidate of variable j from row activity (minfin, ninf): the oracle's operation
-// sequence (product, residual, numerator, quotient, each rounded to nearest), then the
-// integer rounding or the continuous threshold against the round-start bounds bk.
-__device__ void try_candidate(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, double a, int j,
-                              longlong2 bk, double minfin, int ninf, double g) {
-    double resid;
-    if (ninf == 1) {
-        resid = minfin;
-    } else {
-        double b = kdec(a > 0 ? bk.x : bk.y);
-        resid = __dsub_rn(minfin, __dmul_rn(a, b));
+// Exact candidate of variable j (see eval_candidate) and its application: atomicMin / atomicMax
+// of the new key into the next round's bounds, and a note in the block's change queue.
+__device__ __forceinline__ void try_candidate(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph,
+                                              double a, int j, longlong2 bk, double minfin, int ninf, double g) {
+    long long nk;
+    const int r = eval_candidate(a, bk.x, bk.y, minfin, ninf, g, P.is_int[j] != 0, A.theta, &nk);
+    if (r == 1) {
+        atomicMin(&ph.X[j].y, nk);
+        note_changed(st, A, P, ph, j);
+    } else if (r == 2) {
+        atomicMax(&ph.X[j].x, nk);
+        note_changed(st, A, P, ph, j);
     }
-    const double num = __dsub_rn(g, resid);
-    const double cand = __ddiv_rn(num, a);
-    if (!(fabs(cand) < kInfBound)) return;
-    const bool is_i = P.is_int[j] != 0;
-    if (a > 0) {
-        long long nk;
-        bool acc;
-        if (is_i) {
-            nk = dkey(floor(__dadd_rn(cand, kTol)));
-            acc = nk < bk.y;
-        } else if (bk.y == kKeyPosInf) {
-            nk = dkey(cand);
-            acc = true;
-        } else {
-            const double u = kdec(bk.y);
-            const double thr = __dmul_rn(A.theta, fmax(1.0, fabs(u)));
-            nk = dkey(cand);
-            acc = __dsub_rn(u, cand) > thr;
-        }
-        if (acc) {
-            atomicMin(&ph.X[j].y, nk);
-            note_changed(st, A, P, ph, j);
-        }
-    } else {
-        long long nk;
-        bool acc;
-        if (is_i) {
-            nk = dkey(ceil(__dsub_rn(cand, kTol)));
-            acc = nk > bk.x;
-        } else if (bk.x == kKeyNegInf) {
-            nk = dkey(cand);
-            acc = true;
-        } else {
-            const double l = kdec(bk.x);
-            const double thr = __dmul_rn(A.theta, fmax(1.0, fabs(l)));
-            nk = dkey(cand);
-            acc = __dsub_rn(cand, l) > thr;
-        }
-        if (acc) {
-            atomicMax(&ph.X[j].x, nk);
-            note_changed(st, A, P, ph, j);
-        }
-    }
-}
-
-// Conservative test that variable j's candidate from a row with finite activity cannot
-// tighten its bound: slack = g - L_min >= |a| (u - l) + error margin.  FP32 with directed
-// bracketing; a false "may tighten" only costs the exact evaluation.
-struct RowFilter {
-    float slack_dn;   // lower bracket of g - L_min (computed in FP64 once per row)
-    float mag_up;     // upper bracket of |g| + |L_min|
-};
-
-__device__ __forceinline__ RowFilter row_filter(double g, double minfin) {
-    RowFilter f;
-    f.slack_dn = f_dn(__dsub_rn(g, minfin));
-    f.mag_up = __fadd_ru(fabs_up(g), fabs_up(minfin));
-    return f;
-}
-
-__device__ __forceinline__ bool cannot_tighten(const RowFilter& f, double a, longlong2 bk) {
-    const double l = kdec(bk.x), u = kdec(bk.y);
-    const float a_up = fabs_up(a);
-    const float w_up = __fsub_ru(f_up(u), f_dn(l));
-    const float prod = __fmul_ru(a_up, w_up);
-    // rounding of the FP64 candidate: a few units of 2^-53 of |g| + |L_min| + |a| (|l| + |u|)
-    const float big = __fadd_ru(f.mag_up, __fmul_ru(2.0f, __fmul_ru(a_up, __fadd_ru(fabs_up(l), fabs_up(u)))));
-    const float margin = __fmul_ru(1e-15f, big);
-    return f.slack_dn >= __fadd_ru(prod, margin);
-}
-
-__device__ __forceinline__ bool row_infeasible(double minfin, int ninf, double gt) {
-    return ninf == 0 && dkey(minfin) > dkey(gt);
 }
 
 struct Acc {
@@ -419,7 +347,7 @@ __device__ __forceinline__ void elems_candidates(Stage& st, const BpArgs& A, con
     unsigned pass = 0;
 #pragma unroll
     for (int i = 0; i < kPerThread; ++i)
-        if (E.j[i] >= 0 && !cannot_tighten(f, E.a[i], E.bk[i])) pass |= 1u << i;
+        if (E.j[i] >= 0 && !cannot_tighten(f, E.a[i], E.bk[i].x, E.bk[i].y)) pass |= 1u << i;
     if (pass) {
 #pragma unroll
         for (int i = 0; i < kPerThread; ++i)
@@ -557,12 +485,6 @@ __device__ bool do_chunk_candidates(Stage& st, const BpArgs& A, const DevProblem
     return ok;
 }
 
-__device__ __forceinline__ bool crossed(bool is_i, long long lk, long long uk) {
-    if (lk <= uk) return false;
-    if (is_i) return true;
-    return kdec(lk) > __dadd_rn(kdec(uk), kTol);
-}
-
 // Variables changed in the previous round: bring their new bounds into this round's
 // write buffer (atomic, so it commutes with this round's tightenings) and check crossings.
 __device__ void do_fix(const BpArgs& A, const DevProblem& P, const Phase& ph, const int* chg_prev, int nprev, int tl) {
@@ -652,15 +574,8 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
 
     // ---- prologue: normalised start bounds into both buffers; rows of round 0
     for (int v = gtid; v < P.n; v += gthreads) {
-        double l = A.lb[v], u = A.ub[v];
-        if (l <= -kInfBound) l = -INFINITY;
-        if (u >= kInfBound) u = INFINITY;
         const bool is_i = P.is_int[v] != 0;
-        if (is_i) {
-            if (isfinite(l)) l = ceil(__dsub_rn(l, kTol));
-            if (isfinite(u)) u = floor(__dadd_rn(u, kTol));
-        }
-        const longlong2 b = make_longlong2(dkey(l), dkey(u));
+        const longlong2 b = normalized_keys(A.lb[v], A.ub[v], is_i);
         A.bk[0][v] = b;
         A.bk[1][v] = b;
         if (crossed(is_i, b.x, b.y)) atomicMin(&ctl->entry_cross, v);
@@ -841,15 +756,9 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
         }
         unsigned long long changed = 0;
         for (int v = gtid; v < P.n; v += gthreads) {
-            double l = A.lb[v], u = A.ub[v];
-            if (l <= -kInfBound) l = -INFINITY;
-            if (u >= kInfBound) u = INFINITY;
-            if (P.is_int[v]) {
-                if (isfinite(l)) l = ceil(__dsub_rn(l, kTol));
-                if (isfinite(u)) u = floor(__dadd_rn(u, kTol));
-            }
+            const longlong2 in = normalized_keys(A.lb[v], A.ub[v], P.is_int[v] != 0);
             const longlong2 b = __ldcg(res + v);
-            changed += (b.x != dkey(l) || b.y != dkey(u)) ? 1ull : 0ull;
+            changed += (b.x != in.x || b.y != in.y) ? 1ull : 0ull;
             A.lb[v] = kdec(b.x);
             A.ub[v] = kdec(b.y);
         }

@@ -80,6 +80,9 @@ struct mip_problem {
     std::vector<void*> allocs;                 // every device allocation of the handle
     std::vector<void*> host_allocs;            // pinned host allocations
     cudaStream_t last_stream = nullptr;
+    void* probe_work = nullptr;                // probing scratch (created on first use)
+    void* prio_work = nullptr;                 // priority / sort scratch (created on first use)
+    void (*free_hooks[4])(mip_problem*) = {nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace gpubp {

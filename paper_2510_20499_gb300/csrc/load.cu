@@ -418,6 +418,8 @@ extern "C" int mip_load_csr(int32_t m, int32_t n, const int64_t* row_ptr, const 
 extern "C" int mip_free(mip_problem* p) {
     if (!p) return BP_OK;
     cudaDeviceSynchronize();
+    for (auto hook : p->free_hooks)
+        if (hook) hook(p);
     for (void* a : p->allocs) cudaFree(a);
     for (void* a : p->host_allocs) cudaFreeHost(a);
     delete p;

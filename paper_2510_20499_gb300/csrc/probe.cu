@@ -1,0 +1,667 @@
+// Batched double probing (Section 2.2): bp_probe_batch.
+//
+// A probe propagation starts from the rows of one variable and usually stays small, so a grid
+// barrier per round would cost more than the work.  Each thread block therefore runs whole
+// probe pairs on its own: it takes a pair (both branches of one variable) from a counter and
+// runs their Jacobi rounds with block barriers only.  The two branches are propagated
+// together ("double propagation", Section 2.2): a worklist row carries a mask of the branches
+// whose worklist holds it, and one load of its coefficients and columns serves both.
+//
+// Bounds of a branch are root ∩ scratch, where the block's dense scratch holds neutral keys
+// (-inf, +inf) except for the variables the branch tightened; only those are reset after a
+// pair, so neither the root nor the scratch is ever copied in full.  Stamps are 64-bit epochs
+// that only grow, so no stamp array is ever cleared.
+#include <climits>
+
+#include "bp_host.h"
+
+namespace gpubp {
+
+constexpr int kPThreads = 256;
+constexpr int kPWarps = kPThreads / 32;
+constexpr int kPLane = 4;                  // nonzeros per lane held in registers per segment
+constexpr int kPSeg = 32 * kPLane;         // row segment processed in one wave by a warp
+constexpr int kPSort = 4096;               // touched lists up to this size are sorted in shared memory
+
+struct ProbeArgs {
+    const longlong2* root;       // n root keys
+    const int* var;
+    const double* boxes;         // 4 per pair
+    int npairs;
+    // per-block scratch, strided by block
+    longlong2* S;                // [2 branch][2 parity][n]
+    unsigned long long* vst;     // [2 branch][n]  last epoch a variable changed
+    unsigned long long* rw;      // [m]  (epoch << 2) | branch mask of the row's worklist entry
+    int* wl;                     // [2 parity][m]
+    int* chg;                    // [2 branch][2 parity][n]
+    int* touched;                // [2 branch][n]
+    unsigned long long* ep;      // [1] epoch counter of the block
+    int* pair_ctr;
+    double theta;
+    int max_rounds;
+    // outputs
+    int* status;
+    int* rounds;
+    int64_t* nnzu;
+    long long* ecount;           // per branch: entries
+    long long* estart;           // per branch: start in the temp arrays
+    int* evar;
+    double* el;
+    double* eu;
+    unsigned long long* ectr;
+    long long ecap;
+    int* error;
+};
+
+__device__ __forceinline__ longlong2 neutral_keys() { return make_longlong2(kKeyNegInf, kKeyPosInf); }
+
+__device__ __forceinline__ longlong2 meet(longlong2 r, longlong2 s) {
+    return make_longlong2(r.x > s.x ? r.x : s.x, r.y < s.y ? r.y : s.y);
+}
+
+__device__ __forceinline__ long long box_key(double x) {
+    if (x <= -kInfBound) return kKeyNegInf;
+    if (x >= kInfBound) return kKeyPosInf;
+    return dkey(x);
+}
+
+struct ProbeShared {
+    int pair, v;
+    int alive[2];
+    int status[2], rounds[2];
+    unsigned long long nnz[2];
+    int rowinf[2], cross[2];
+    int nw[2];                   // worklist entries per parity
+    int wcount[2][2];            // [parity][branch] entries holding the branch
+    int nchg[2][2];              // [branch][parity]
+    int ntouch[2];
+    unsigned long long ep_pair, ep_t;
+    int sortbuf[kPSort];
+    int scan[kPThreads];
+    int out_base;
+};
+
+__global__ void __launch_bounds__(kPThreads) probe_kernel(DevProblem P, ProbeArgs A) {
+    __shared__ ProbeShared sh;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int n = P.n, m = P.m;
+    longlong2* S = A.S + (size_t)blockIdx.x * 4 * n;
+    unsigned long long* vst = A.vst + (size_t)blockIdx.x * 2 * n;
+    unsigned long long* rw = A.rw + (size_t)blockIdx.x * m;
+    int* wl = A.wl + (size_t)blockIdx.x * 2 * m;
+    int* chg = A.chg + (size_t)blockIdx.x * 4 * n;
+    int* touched = A.touched + (size_t)blockIdx.x * 2 * n;
+    unsigned long long* epp = A.ep + blockIdx.x;
+    auto Sb = [&](int b, int p) { return S + (size_t)(2 * b + p) * n; };
+    auto chgb = [&](int b, int p) { return chg + (size_t)(2 * b + p) * n; };
+
+    for (;;) {
+        if (tid == 0) {
+            sh.pair = atomicAdd(A.pair_ctr, 1);
+            const unsigned long long e = *epp + 1;
+            *epp = e;
+            sh.ep_pair = e;
+        }
+        __syncthreads();
+        const int pair = sh.pair;
+        if (pair >= A.npairs) break;
+        const unsigned long long ep_pair = sh.ep_pair;
+        // ---- branch set-up: start box = root ∩ branch box of the probed variable
+        if (tid < 2) {
+            const int b = tid;
+            const int v = A.var[pair];
+            const longlong2 r = A.root[v];
+            const longlong2 bx = make_longlong2(box_key(A.boxes[4 * pair + 2 * b]), box_key(A.boxes[4 * pair + 2 * b + 1]));
+            const longlong2 s0 = meet(r, bx);
+            Sb(b, 0)[v] = s0;
+            Sb(b, 1)[v] = s0;
+            vst[(size_t)b * n + v] = ep_pair;
+            touched[(size_t)b * n] = v;
+            sh.ntouch[b] = 1;
+            sh.nnz[b] = 0;
+            sh.rounds[b] = 0;
+            sh.v = v;
+            if (crossed(P.is_int[v] != 0, s0.x, s0.y)) {
+                sh.status[b] = BP_INFEASIBLE;
+                sh.alive[b] = 0;
+            } else {
+                sh.status[b] = BP_FIXPOINT;
+                sh.alive[b] = 1;
+            }
+            sh.nchg[b][0] = sh.nchg[b][1] = 0;
+            sh.wcount[0][b] = 0;
+        }
+        if (tid == 0) sh.nw[0] = 0;
+        __syncthreads();
+        // ---- round 0 worklist: the rows of the probed variable, for the live branches
+        const int v = sh.v;
+        const unsigned mask0 = (unsigned)(sh.alive[0] | (sh.alive[1] << 1));
+        if (mask0) {
+            const int cb = P.col_ptr[v], ce = P.col_ptr[v + 1];
+            for (int s = cb + tid; s < ce; s += kPThreads) {
+                const int k = P.row_idx[s];
+                rw[k] = (ep_pair << 2) | mask0;
+                wl[s - cb] = k;
+            }
+            if (tid == 0) {
+                sh.nw[0] = ce - cb;
+                sh.wcount[0][0] = (mask0 & 1) ? ce - cb : 0;
+                sh.wcount[0][1] = (mask0 & 2) ? ce - cb : 0;
+            }
+        }
+        __syncthreads();
+
+        for (int t = 0;; ++t) {
+            const int par = t & 1, np = par ^ 1;
+            // branches whose worklist is empty or that hit the round limit stop here
+            if (tid < 2) {
+                const int b = tid;
+                if (sh.alive[b]) {
+                    if (sh.wcount[par][b] == 0) {
+                        sh.alive[b] = 0;
+                        sh.status[b] = BP_FIXPOINT;
+                        sh.rounds[b] = t;
+                    } else if (t >= A.max_rounds) {
+                        sh.alive[b] = 0;
+                        sh.status[b] = BP_ROUND_LIMIT;
+                        sh.rounds[b] = t;
+                    }
+                }
+                sh.rowinf[b] = 0;
+                sh.cross[b] = 0;
+                sh.nchg[b][par] = 0;
+                sh.wcount[np][b] = 0;
+            }
+            if (tid == 0) {
+                sh.nw[np] = 0;
+                sh.ep_t = ++*epp;
+            }
+            __syncthreads();
+            const unsigned live = (unsigned)(sh.alive[0] | (sh.alive[1] << 1));
+            if (!live) break;
+            const unsigned long long ep_t = sh.ep_t;
+            // fix-ups of the previous round's changes into this round's write buffers
+            if (t > 0) {
+                for (int b = 0; b < 2; ++b) {
+                    if (!(live >> b & 1)) continue;
+                    const int nprev = sh.nchg[b][np];
+                    const int* cl = chgb(b, np);
+                    longlong2* R = Sb(b, par);
+                    longlong2* X = Sb(b, np);
+                    for (int i = tid; i < nprev; i += kPThreads) {
+                        const int u = cl[i];
+                        const longlong2 rv = R[u];
+                        atomicMax(&X[u].x, rv.x);
+                        atomicMin(&X[u].y, rv.y);
+                    }
+                }
+            }
+            // ---- rows of this round: one warp per row, both branches per load
+            const int nw = sh.nw[par];
+            const int* W = wl + (size_t)par * m;
+            for (int e = w; e < nw; e += kPWarps) {
+                const int k = W[e];
+                const unsigned mask = (unsigned)(rw[k] & 3ull) & live;
+                if (!mask) continue;
+                const int beg = P.row_ptr[k], end = P.row_ptr[k + 1];
+                const double2 g2 = P.grow[k];
+                double mf[2] = {0.0, 0.0};
+                int ni[2] = {0, 0}, ij[2] = {-1, -1};
+                int jj[kPLane];
+                double aa[kPLane];
+                longlong2 bb[2][kPLane];
+                const bool one_seg = end - beg <= kPSeg;
+                for (int s0 = beg; s0 < end; s0 += kPSeg) {
+#pragma unroll
+                    for (int i = 0; i < kPLane; ++i) {
+                        const int q = s0 + lane + 32 * i;
+                        jj[i] = q < end ? P.col[q] : -1;
+                        aa[i] = q < end ? P.val[q] : 0.0;
+                    }
+#pragma unroll
+                    for (int i = 0; i < kPLane; ++i) {
+                        if (jj[i] < 0) continue;
+                        const longlong2 r = __ldcg(A.root + jj[i]);
+#pragma unroll
+                        for (int b = 0; b < 2; ++b)
+                            bb[b][i] = (mask >> b & 1) ? meet(r, __ldcg(Sb(b, par) + jj[i])) : r;
+                    }
+#pragma unroll
+                    for (int i = 0; i < kPLane; ++i) {
+                        if (jj[i] < 0) continue;
+#pragma unroll
+                        for (int b = 0; b < 2; ++b) {
+                            if (!(mask >> b & 1)) continue;
+                            const long long key = aa[i] > 0 ? bb[b][i].x : bb[b][i].y;
+                            if (key_is_inf(key)) {
+                                ++ni[b];
+                                ij[b] = jj[i];
+                            } else {
+                                mf[b] = fma(aa[i], kdec(key), mf[b]);
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    for (int off = 16; off > 0; off >>= 1) {
+                        mf[b] = __dadd_rn(mf[b], __shfl_xor_sync(0xffffffffu, mf[b], off));
+                        ni[b] += __shfl_xor_sync(0xffffffffu, ni[b], off);
+                        ij[b] = max(ij[b], __shfl_xor_sync(0xffffffffu, ij[b], off));
+                    }
+                }
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    if (!(mask >> b & 1)) continue;
+                    if (lane == 0) atomicAdd(&sh.nnz[b], (unsigned long long)(end - beg));
+                    if (row_infeasible(mf[b], ni[b], g2.y)) {
+                        if (lane == 0) sh.rowinf[b] = 1;
+                        continue;
+                    }
+                    if (ni[b] >= 2) continue;
+                    const RowFilter f = row_filter(g2.x, mf[b]);
+                    longlong2* X = Sb(b, np);
+                    for (int s0 = beg; s0 < end; s0 += kPSeg) {
+#pragma unroll
+                        for (int i = 0; i < kPLane; ++i) {
+                            int j;
+                            double a;
+                            longlong2 bk;
+                            if (one_seg) {
+                                j = jj[i];
+                                a = aa[i];
+                                bk = bb[b][i];
+                            } else {
+                                const int q = s0 + lane + 32 * i;
+                                j = q < end ? P.col[q] : -1;
+                                a = q < end ? P.val[q] : 0.0;
+                                bk = j >= 0 ? meet(__ldcg(A.root + j), __ldcg(Sb(b, par) + j)) : make_longlong2(0, 0);
+                            }
+                            if (j < 0) continue;
+                            if (ni[b] == 1 ? j != ij[b] : cannot_tighten(f, a, bk.x, bk.y)) continue;
+                            long long nk;
+                            const int r = eval_candidate(a, bk.x, bk.y, mf[b], ni[b], g2.x, P.is_int[j] != 0, A.theta, &nk);
+                            if (!r) continue;
+                            if (r == 1) atomicMin(&X[j].y, nk);
+                            else atomicMax(&X[j].x, nk);
+                            const unsigned long long old = atomicMax(&vst[(size_t)b * n + j], ep_t);
+                            if (old < ep_t) chgb(b, par)[atomicAdd(&sh.nchg[b][par], 1)] = j;
+                            if (old < ep_pair) touched[(size_t)b * n + atomicAdd(&sh.ntouch[b], 1)] = j;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            // ---- verdicts of the round: infeasible rows, crossing bounds
+            for (int b = 0; b < 2; ++b) {
+                if (!(live >> b & 1) || sh.rowinf[b]) continue;
+                const int nc = sh.nchg[b][par];
+                const int* cl = chgb(b, par);
+                const longlong2* X = Sb(b, np);
+                for (int i = tid; i < nc; i += kPThreads) {
+                    const int u = cl[i];
+                    const longlong2 x = meet(__ldcg(A.root + u), X[u]);
+                    if (crossed(P.is_int[u] != 0, x.x, x.y)) sh.cross[b] = 1;
+                }
+            }
+            __syncthreads();
+            if (tid < 2) {
+                const int b = tid;
+                if (live >> b & 1) {
+                    sh.rounds[b] = t + 1;
+                    if (sh.rowinf[b] || sh.cross[b]) {
+                        sh.alive[b] = 0;
+                        sh.status[b] = BP_INFEASIBLE;
+                    }
+                }
+            }
+            __syncthreads();
+            // ---- next worklist: rows of the variables changed in this round
+            for (int b = 0; b < 2; ++b) {
+                if (!sh.alive[b]) continue;
+                const int nc = sh.nchg[b][par];
+                const int* cl = chgb(b, par);
+                const unsigned bit = 1u << b;
+                // warp per changed variable, lanes over its rows
+                for (int i = w; i < nc; i += kPWarps) {
+                    const int u = cl[i];
+                    const int cb = P.col_ptr[u], ce = P.col_ptr[u + 1];
+                    for (int s = cb + lane; s < ce; s += 32) {
+                        const int k = P.row_idx[s];
+                        unsigned long long old = rw[k], nv;
+                        bool first;
+                        do {
+                            first = (old >> 2) != ep_t;
+                            if (!first && (old & bit)) break;
+                            nv = first ? ((ep_t << 2) | bit) : (old | bit);
+                            const unsigned long long seen = atomicCAS(&rw[k], old, nv);
+                            if (seen == old) {
+                                atomicAdd(&sh.wcount[np][b], 1);
+                                if (first) wl[(size_t)np * m + atomicAdd(&sh.nw[np], 1)] = k;
+                                break;
+                            }
+                            old = seen;
+                        } while (true);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+
+        // ---- outputs of the pair
+        for (int b = 0; b < 2; ++b) {
+            const int e = 2 * pair + b;
+            const bool feas = sh.status[b] != BP_INFEASIBLE;
+            const int nt = sh.ntouch[b];
+            const int* tl = touched + (size_t)b * n;
+            const longlong2* F = Sb(b, sh.rounds[b] & 1);
+            // sorted touched variables: in shared memory when few, else in index order from the stamps
+            const bool small = nt <= kPSort;
+            if (feas && small) {
+                for (int i = tid; i < kPSort; i += kPThreads) sh.sortbuf[i] = i < nt ? tl[i] : INT_MAX;
+                __syncthreads();
+                for (int size = 2; size <= kPSort; size <<= 1) {
+                    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                        for (int i = tid; i < kPSort; i += kPThreads) {
+                            const int jx = i ^ stride;
+                            if (jx > i) {
+                                const bool up = (i & size) == 0;
+                                const int x = sh.sortbuf[i], y = sh.sortbuf[jx];
+                                if ((x > y) == up) {
+                                    sh.sortbuf[i] = y;
+                                    sh.sortbuf[jx] = x;
+                                }
+                            }
+                        }
+                        __syncthreads();
+                    }
+                }
+            }
+            // count the entries that differ from the root, in variable order
+            const int span = feas ? (small ? nt : n) : 0;
+            long long cnt = 0;
+            for (int base = 0; base < span; base += kPThreads) {
+                const int i = base + tid;
+                int u = -1;
+                if (i < span) u = small ? sh.sortbuf[i] : (vst[(size_t)b * n + i] >= ep_pair ? i : -1);
+                int d = 0;
+                if (u >= 0) {
+                    const longlong2 r = A.root[u];
+                    const longlong2 x = meet(r, F[u]);
+                    d = (x.x != r.x || x.y != r.y) ? 1 : 0;
+                }
+                sh.scan[tid] = d;
+                __syncthreads();
+                for (int o = 1; o < kPThreads; o <<= 1) {
+                    const int y = tid >= o ? sh.scan[tid - o] : 0;
+                    __syncthreads();
+                    sh.scan[tid] += y;
+                    __syncthreads();
+                }
+                cnt += sh.scan[kPThreads - 1];
+                __syncthreads();
+            }
+            if (tid == 0) {
+                sh.out_base = (int)0;
+                A.status[e] = sh.status[b];
+                A.rounds[e] = sh.rounds[b];
+                A.nnzu[e] = (int64_t)sh.nnz[b];
+                A.ecount[e] = cnt;
+                const unsigned long long base = cnt ? atomicAdd(A.ectr, (unsigned long long)cnt) : 0ull;
+                A.estart[e] = (long long)base;
+                sh.ep_t = base;   // reuse as the write base
+            }
+            __syncthreads();
+            const unsigned long long wbase = sh.ep_t;
+            long long written = 0;
+            for (int base = 0; base < span && cnt; base += kPThreads) {
+                const int i = base + tid;
+                int u = -1;
+                if (i < span) u = small ? sh.sortbuf[i] : (vst[(size_t)b * n + i] >= ep_pair ? i : -1);
+                int d = 0;
+                longlong2 x = make_longlong2(0, 0);
+                if (u >= 0) {
+                    const longlong2 r = A.root[u];
+                    x = meet(r, F[u]);
+                    d = (x.x != r.x || x.y != r.y) ? 1 : 0;
+                }
+                sh.scan[tid] = d;
+                __syncthreads();
+                for (int o = 1; o < kPThreads; o <<= 1) {
+                    const int y = tid >= o ? sh.scan[tid - o] : 0;
+                    __syncthreads();
+                    sh.scan[tid] += y;
+                    __syncthreads();
+                }
+                if (d) {
+                    const long long pos = (long long)wbase + written + sh.scan[tid] - 1;
+                    if (pos < A.ecap) {
+                        A.evar[pos] = u;
+                        A.el[pos] = kdec(x.x);
+                        A.eu[pos] = kdec(x.y);
+                    }
+                }
+                written += sh.scan[kPThreads - 1];
+                __syncthreads();
+            }
+            // reset the touched variables of the branch to neutral
+            for (int i = tid; i < nt; i += kPThreads) {
+                const int u = tl[i];
+                Sb(b, 0)[u] = neutral_keys();
+                Sb(b, 1)[u] = neutral_keys();
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void k_root_keys(int n, const double* lb, const double* ub, const unsigned char* is_int, longlong2* out) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        out[v] = normalized_keys(lb[v], ub[v], is_int[v] != 0);
+}
+
+__global__ void k_fill_neutral(size_t count, longlong2* S) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        S[i] = neutral_keys();
+}
+
+// offsets (exclusive scan of the entry counts) and the copy of every branch's entries to its
+// place, in branch order; one block, the counts are few
+__global__ void k_probe_offsets(int nb, const long long* ecount, int64_t* offsets, unsigned long long* total) {
+    __shared__ long long carry;
+    __shared__ long long sc[1024];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += 1024) {
+        const int i = base + threadIdx.x;
+        const long long v = i < nb ? ecount[i] : 0;
+        sc[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {
+            const long long y = threadIdx.x >= o ? sc[threadIdx.x - o] : 0;
+            __syncthreads();
+            sc[threadIdx.x] += y;
+            __syncthreads();
+        }
+        if (i < nb) offsets[i] = (int64_t)(carry + sc[threadIdx.x] - v);
+        __syncthreads();
+        if (threadIdx.x == 0) carry += sc[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        offsets[nb] = (int64_t)carry;
+        *total = (unsigned long long)carry;
+    }
+}
+
+__global__ void k_probe_copy(int nb, const long long* ecount, const long long* estart, const int64_t* offsets,
+                             const int* tv, const double* tl, const double* tu, int* ov, double* ol, double* ou) {
+    const int lane = threadIdx.x & 31;
+    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += (gridDim.x * blockDim.x) >> 5) {
+        const long long c = ecount[b], s = estart[b], o = offsets[b];
+        for (long long i = lane; i < c; i += 32) {
+            ov[o + i] = tv[s + i];
+            ol[o + i] = tl[s + i];
+            ou[o + i] = tu[s + i];
+        }
+    }
+}
+
+struct ProbeWork {
+    int blocks = 0;
+    longlong2* S = nullptr;
+    unsigned long long* vst = nullptr;
+    unsigned long long* rw = nullptr;
+    int* wl = nullptr;
+    int* chg = nullptr;
+    int* touched = nullptr;
+    unsigned long long* ep = nullptr;
+    int* ctr = nullptr;
+    unsigned long long* ectr = nullptr;
+    long long* ecount = nullptr;
+    long long* estart = nullptr;
+    int cap_branches = 0;
+    int* tv = nullptr;
+    double* tl = nullptr;
+    double* tu = nullptr;
+    long long tcap = 0;
+};
+
+static ProbeWork* probe_work(mip_problem* p) { return static_cast<ProbeWork*>(p->probe_work); }
+
+static void probe_work_free(mip_problem* p) {
+    delete probe_work(p);   // device buffers are in p->allocs
+    p->probe_work = nullptr;
+}
+
+static int probe_prepare(mip_problem* p, int nbranches, long long cap, cudaStream_t s) {
+    if (!p->probe_work) {
+        ProbeWork* pw = new ProbeWork();
+        p->probe_work = pw;
+        p->free_hooks[0] = probe_work_free;
+        int sms = 0;
+        BP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+        pw->blocks = 2 * sms;
+        const size_t B = (size_t)pw->blocks, n = (size_t)p->n, m = (size_t)p->m;
+        BP_TRY(dalloc(p, &pw->S, B * 4 * n));
+        BP_TRY(dalloc(p, &pw->vst, B * 2 * n));
+        BP_TRY(dalloc(p, &pw->rw, B * m));
+        BP_TRY(dalloc(p, &pw->wl, B * 2 * m));
+        BP_TRY(dalloc(p, &pw->chg, B * 4 * n));
+        BP_TRY(dalloc(p, &pw->touched, B * 2 * n));
+        BP_TRY(dalloc(p, &pw->ep, B));
+        BP_TRY(dalloc(p, &pw->ctr, 1));
+        BP_TRY(dalloc(p, &pw->ectr, 1));
+        if (B * 4 * n) k_fill_neutral<<<1024, 256, 0, s>>>(B * 4 * n, pw->S);
+        BP_CUDA_TRY(cudaGetLastError());
+    }
+    ProbeWork* pw = probe_work(p);
+    if (nbranches > pw->cap_branches) {
+        BP_TRY(dalloc(p, &pw->ecount, (size_t)nbranches));
+        BP_TRY(dalloc(p, &pw->estart, (size_t)nbranches));
+        pw->cap_branches = nbranches;
+    }
+    if (cap > pw->tcap) {
+        BP_TRY(dalloc(p, &pw->tv, (size_t)cap));
+        BP_TRY(dalloc(p, &pw->tl, (size_t)cap));
+        BP_TRY(dalloc(p, &pw->tu, (size_t)cap));
+        pw->tcap = cap;
+    }
+    return BP_OK;
+}
+
+}  // namespace gpubp
+
+using namespace gpubp;
+
+extern "C" int bp_probe_batch(mip_problem* p, const double* root_lb, const double* root_ub, int32_t npairs,
+                              const int32_t* var, const double* boxes, const bp_params* params, probe_cache* cache,
+                              void* stream) {
+    if (!p || !cache || npairs < 0 || (npairs && (!var || !boxes)) || (p->n && (!root_lb || !root_ub))) {
+        set_error("bp_probe_batch: null or negative argument");
+        return BP_ERR_INVALID;
+    }
+    if (npairs && (!cache->status || !cache->rounds || !cache->nnz_updates || !cache->offsets) ||
+        cache->cap < 0 || (cache->cap > 0 && (!cache->ent_var || !cache->ent_l || !cache->ent_u))) {
+        set_error("bp_probe_batch: cache arrays missing");
+        return BP_ERR_INVALID;
+    }
+    bp_params prm;
+    if (params) prm = *params;
+    else bp_params_default(&prm);
+    if (!(prm.theta >= 0.0) || prm.max_rounds < 0) {
+        set_error("bp_probe_batch: invalid parameters");
+        return BP_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cache->needed = 0;
+    if (npairs == 0) {
+        int64_t zero = 0;
+        if (cache->offsets) BP_CUDA_TRY(cudaMemcpyAsync(cache->offsets, &zero, sizeof(zero), cudaMemcpyHostToDevice, s));
+        BP_CUDA_TRY(cudaStreamSynchronize(s));
+        return BP_OK;
+    }
+    // variables must be in range: checked on the device copy by a small kernel would cost a
+    // sync; the host reads them once (the call synchronises anyway)
+    {
+        std::vector<int32_t> hv((size_t)npairs);
+        BP_CUDA_TRY(cudaMemcpyAsync(hv.data(), var, sizeof(int32_t) * npairs, cudaMemcpyDeviceToHost, s));
+        BP_CUDA_TRY(cudaStreamSynchronize(s));
+        for (int32_t x : hv)
+            if (x < 0 || x >= p->n) {
+                set_error("bp_probe_batch: variable index %d out of range", x);
+                return BP_ERR_INVALID;
+            }
+    }
+    BP_TRY(probe_prepare(p, 2 * npairs, cache->cap > 0 ? cache->cap : 1, s));
+    ProbeWork* pw = probe_work(p);
+    longlong2* root = p->w.bkey[0];
+    if (p->n) k_root_keys<<<(p->n + 255) / 256 < 1216 ? (p->n + 255) / 256 : 1216, 256, 0, s>>>(p->n, root_lb, root_ub, p->dp.is_int, root);
+    BP_CUDA_TRY(cudaMemsetAsync(pw->ctr, 0, sizeof(int), s));
+    BP_CUDA_TRY(cudaMemsetAsync(pw->ectr, 0, sizeof(unsigned long long), s));
+    ProbeArgs a;
+    a.root = root;
+    a.var = var;
+    a.boxes = boxes;
+    a.npairs = npairs;
+    a.S = pw->S;
+    a.vst = pw->vst;
+    a.rw = pw->rw;
+    a.wl = pw->wl;
+    a.chg = pw->chg;
+    a.touched = pw->touched;
+    a.ep = pw->ep;
+    a.pair_ctr = pw->ctr;
+    a.theta = prm.theta;
+    a.max_rounds = prm.max_rounds;
+    a.status = cache->status;
+    a.rounds = cache->rounds;
+    a.nnzu = cache->nnz_updates;
+    a.ecount = pw->ecount;
+    a.estart = pw->estart;
+    a.evar = pw->tv;
+    a.el = pw->tl;
+    a.eu = pw->tu;
+    a.ectr = pw->ectr;
+    a.ecap = pw->tcap;
+    a.error = nullptr;
+    probe_kernel<<<pw->blocks, kPThreads, 0, s>>>(p->dp, a);
+    BP_CUDA_TRY(cudaGetLastError());
+    const int nb = 2 * npairs;
+    k_probe_offsets<<<1, 1024, 0, s>>>(nb, pw->ecount, cache->offsets, pw->ectr);
+    unsigned long long total = 0;
+    BP_CUDA_TRY(cudaMemcpyAsync(&total, pw->ectr, sizeof(total), cudaMemcpyDeviceToHost, s));
+    BP_CUDA_TRY(cudaStreamSynchronize(s));
+    cache->needed = (int64_t)total;
+    if ((long long)total > cache->cap) {
+        set_error("probing cache needs %llu entries, capacity %lld", total, (long long)cache->cap);
+        return BP_ERR_CAPACITY;
+    }
+    if (total) {
+        k_probe_copy<<<(nb * 32 + 255) / 256 < 1216 ? (nb * 32 + 255) / 256 : 1216, 256, 0, s>>>(
+            nb, pw->ecount, pw->estart, cache->offsets, pw->tv, pw->tl, pw->tu, cache->ent_var, cache->ent_l, cache->ent_u);
+        BP_CUDA_TRY(cudaGetLastError());
+    }
+    p->last_stream = s;
+    return BP_OK;
+}

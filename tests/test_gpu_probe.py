@@ -1,0 +1,112 @@
+"""GPU batched double probing (bp_probe_batch through the C ABI) against the CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_20499_gb300 import synth
+from tests.helpers import golden_problem, load_golden
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("gpu tests need a CUDA device")
+    import paper_2510_20499_gb300 as pkg
+    return pkg
+
+
+def _pairs(p, rl, ru, count, seed):
+    rng = np.random.default_rng(seed)
+    cand = [j for j in range(p.n) if oracle.probe_split(p.is_int[j], rl[j], ru[j])]
+    pick = rng.choice(cand, size=min(count, len(cand)), replace=False) if cand else []
+    var = np.array(pick, dtype=np.int32)
+    boxes = np.array([oracle.probe_split(p.is_int[j], rl[j], ru[j]) for j in var], dtype=np.float64).reshape(-1, 4)
+    return var, boxes
+
+
+def _gpu_probe(pkg, p, rl, ru, var, boxes, **kw):
+    import torch
+    prob = pkg.Problem(p)
+    c = prob.probe_batch(torch.tensor(rl, device="cuda"), torch.tensor(ru, device="cuda"),
+                         torch.tensor(var, device="cuda"), torch.tensor(boxes, device="cuda"), **kw)
+    return {k: v.cpu().numpy() for k, v in c.items()}
+
+
+def _compare(p, g, o):
+    np.testing.assert_array_equal(g["status"], o["status"])
+    np.testing.assert_array_equal(g["rounds"], o["rounds"])
+    np.testing.assert_array_equal(g["nnz_updates"], o["nnz_updates"])
+    np.testing.assert_array_equal(g["offsets"], o["offsets"])
+    np.testing.assert_array_equal(g["var"], o["var"])
+    ints = p.is_int[o["var"]] == 1
+    np.testing.assert_array_equal(g["l"][ints], o["l"][ints])
+    np.testing.assert_array_equal(g["u"][ints], o["u"][ints])
+    for a, b in ((g["l"], o["l"]), (g["u"], o["u"])):
+        fin = np.isfinite(b) & ~ints
+        assert (np.abs(a[fin] - b[fin]) <= 1e-9 * np.maximum(1, np.abs(b[fin]))).all()
+        np.testing.assert_array_equal(a[~np.isfinite(b)], b[~np.isfinite(b)])
+
+
+def test_golden_probe(pkg):
+    d = load_golden("probe_knapsack.json")
+    p = golden_problem(d)
+    rl, ru = np.array(d["root_lb"], float), np.array(d["root_ub"], float)
+    g = _gpu_probe(pkg, p, rl, ru, np.array(d["var"], np.int32), np.array(d["boxes"], float))
+    for e, want in enumerate(d["expect"]):
+        assert g["status"][e] == want["status"]
+        a, b = g["offsets"][e], g["offsets"][e + 1]
+        got = [[int(g["var"][q]), float(g["l"][q]), float(g["u"][q])] for q in range(a, b)]
+        assert got == [[int(x[0]), float(x[1]), float(x[2])] for x in want["entries"]], want["note"]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_knapsack_cover_probes(pkg, seed):
+    p = synth.knapsack_cover(seed=40 + seed, m=2000, n=4000, nnz=40_000)
+    P = oracle.Problem(p)
+    rl, ru, r, _ = P.bp(p.lb, p.ub)
+    assert r["status"] == oracle.FIXPOINT
+    var, boxes = _pairs(p, rl, ru, 300, seed)
+    o = P.probe_batch(rl, ru, var, boxes)
+    g = _gpu_probe(pkg, p, rl, ru, var, boxes)
+    _compare(p, g, o)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_mixed_probes(pkg, seed):
+    """General integers, continuous variables, infinite bounds, long rows, equality pairs."""
+    p = synth.random_milp(500 + seed, m=600, n=800, len_lo=1, len_hi=300, inf_fraction=0.1,
+                          eq_fraction=0.2, int_fraction=0.7)
+    P = oracle.Problem(p)
+    rl, ru, r, _ = P.bp(p.lb, p.ub)
+    if r["status"] == oracle.INFEASIBLE:
+        pytest.skip("root infeasible")
+    var, boxes = _pairs(p, rl, ru, 200, seed)
+    o = P.probe_batch(rl, ru, var, boxes)
+    g = _gpu_probe(pkg, p, rl, ru, var, boxes)
+    _compare(p, g, o)
+
+
+def test_probe_round_limit_and_capacity(pkg):
+    p = synth.knapsack_cover(seed=9, m=1000, n=2000, nnz=20_000)
+    P = oracle.Problem(p)
+    rl, ru, _, _ = P.bp(p.lb, p.ub)
+    var, boxes = _pairs(p, rl, ru, 100, 1)
+    o = P.probe_batch(rl, ru, var, boxes, max_rounds=1)
+    g = _gpu_probe(pkg, p, rl, ru, var, boxes, max_rounds=1, cap=1)   # forces the capacity path
+    _compare(p, g, o)
+
+
+def test_probes_full_size(pkg):
+    """The 50k x 100k, 1M-nonzero probing instance: 2,048 pairs chosen by the priority order."""
+    p = synth.knapsack_cover()
+    P = oracle.Problem(p)
+    rl, ru, r, _ = P.bp(p.lb, p.ub)
+    k1, k2, k3 = P.probe_priority(rl, ru)
+    var = oracle.priority_order(k1, k2, k3)[:2048].astype(np.int32)
+    boxes = np.array([oracle.probe_split(1, rl[j], ru[j]) for j in var], dtype=np.float64).reshape(-1, 4)
+    o = P.probe_batch(rl, ru, var, boxes)
+    g = _gpu_probe(pkg, p, rl, ru, var, boxes)
+    _compare(p, g, o)
