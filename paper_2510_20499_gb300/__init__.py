@@ -220,6 +220,24 @@ def _probe_batch(prob, root_lb, root_ub, var, boxes, theta=1e-3, max_rounds=1000
 Problem.probe_batch = _probe_batch
 
 
+def _probe_priority(prob, lb, ub, stream=None):
+    """bp_probe_priority on device bounds; returns (key1, key2, key3, order) device tensors,
+    order holding only the probed variables."""
+    torch = _torch()
+    n = prob.n
+    k1 = torch.empty(n, dtype=torch.int32, device=prob.device)
+    k2 = torch.empty(n, dtype=torch.float64, device=prob.device)
+    k3 = torch.empty(n, dtype=torch.float64, device=prob.device)
+    order = torch.empty(max(1, n), dtype=torch.int32, device=prob.device)
+    cnt = C.c_int32(0)
+    _check(lib().bp_probe_priority(prob.h, _ptr(lb), _ptr(ub), _ptr(k1), _ptr(k2), _ptr(k3), _ptr(order),
+                                   C.byref(cnt), _stream(stream)))
+    return k1, k2, k3, order[:cnt.value]
+
+
+Problem.probe_priority = _probe_priority
+
+
 def probe_split(is_int, l, u):
     out = (C.c_double * 4)()
     ok = lib().probe_split(int(is_int), float(l), float(u), out)

@@ -228,6 +228,7 @@ struct DevProblem {
     const double2* grow;         // m: {g, g + tol}, g = +inf for a free row
     const int* col_ptr;          // n+1 (transpose)
     const int* row_idx;          // nnz
+    const double* col_val;       // nnz: coefficients in transpose order
     const unsigned char* is_int; // n
     const unsigned char* rclass; // m
     const int* heavy_id;         // m: index among chunked rows, -1 otherwise

@@ -112,6 +112,13 @@ int dalloc(mip_problem* p, T** out, size_t count) {
 int scan_exclusive(const int* in, int* out, int n, int* total_dev, cudaStream_t s);
 
 int engine_prepare(mip_problem* p);     // allocates Work
+
+// normalised bound keys of caller bounds (device arrays of n doubles)
+int root_keys(mip_problem* p, const double* lb, const double* ub, longlong2* out, cudaStream_t s);
+
+// stable LSD radix sort of (key, value) pairs on bits [begin_bit, end_bit)
+int radix_sort_pairs(unsigned long long* keys, int* vals, unsigned long long* tmp_keys, int* tmp_vals, int n,
+                     int begin_bit, int end_bit, cudaStream_t s);
 int launch_propagate(mip_problem* p, double* lb, double* ub, const int* w0, int w0_len,
                      double theta, int max_rounds, int64_t* trace, cudaStream_t s);
 

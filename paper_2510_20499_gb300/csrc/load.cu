@@ -171,8 +171,8 @@ __global__ void k_col_count(long long nnz, const int32_t* col, int* cnt) {
         atomicAdd(&cnt[col[q]], 1);
 }
 
-__global__ void k_col_scatter(int m, const int* rp, const int32_t* col, const int* col_ptr, int* fill,
-                              int* row_idx) {
+__global__ void k_col_scatter(int m, const int* rp, const int32_t* col, const double* val, const int* col_ptr,
+                              int* fill, int* row_idx, double* col_val) {
     // one warp per row
     int lane = threadIdx.x & 31;
     for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < m; k += (gridDim.x * blockDim.x) >> 5) {
@@ -180,6 +180,7 @@ __global__ void k_col_scatter(int m, const int* rp, const int32_t* col, const in
             int j = col[q];
             int pos = atomicAdd(&fill[j], 1);
             row_idx[col_ptr[j] + pos] = k;
+            col_val[col_ptr[j] + pos] = val[q];
         }
     }
 }
@@ -356,13 +357,15 @@ static int load_impl(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t
     }
     // transpose
     int *d_colcnt, *d_colptr, *d_fill, *d_rowidx;
+    double* d_colval;
+    BP_TRY(dalloc(p, &d_colval, (size_t)nnz));
     BP_TRY(dalloc(p, &d_colcnt, (size_t)n + 1));
     BP_TRY(dalloc(p, &d_colptr, (size_t)n + 1));
     BP_TRY(dalloc(p, &d_fill, (size_t)n + 1));
     BP_TRY(dalloc(p, &d_rowidx, (size_t)nnz));
     if (nnz) k_col_count<<<grid_for(nnz), 256, 0, s>>>(nnz, d_col, d_colcnt);
     BP_TRY(scan_exclusive(d_colcnt, d_colptr, n + 1, nullptr, s));
-    if (nnz) k_col_scatter<<<grid_for((long long)m * 32), 256, 0, s>>>(m, d_rp, d_col, d_colptr, d_fill, d_rowidx);
+    if (nnz) k_col_scatter<<<grid_for((long long)m * 32), 256, 0, s>>>(m, d_rp, d_col, d_val, d_colptr, d_fill, d_rowidx, d_colval);
     // bounds and types
     unsigned char* d_isint;
     BP_TRY(dalloc(p, &d_isint, (size_t)n));
@@ -379,6 +382,7 @@ static int load_impl(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t
     dp.grow = d_grow;
     dp.col_ptr = d_colptr;
     dp.row_idx = d_rowidx;
+    dp.col_val = d_colval;
     dp.is_int = d_isint;
     dp.rclass = d_rclass;
     dp.heavy_id = d_heavy;

@@ -507,6 +507,16 @@ __global__ void k_probe_copy(int nb, const long long* ecount, const long long* e
     }
 }
 
+// normalised keys of caller bounds (device arrays) into out
+int root_keys(mip_problem* p, const double* lb, const double* ub, longlong2* out, cudaStream_t s) {
+    if (p->n) {
+        const int g = (p->n + 255) / 256 < 1216 ? (p->n + 255) / 256 : 1216;
+        k_root_keys<<<g, 256, 0, s>>>(p->n, lb, ub, p->dp.is_int, out);
+        BP_CUDA_TRY(cudaGetLastError());
+    }
+    return BP_OK;
+}
+
 struct ProbeWork {
     int blocks = 0;
     longlong2* S = nullptr;
@@ -616,7 +626,7 @@ extern "C" int bp_probe_batch(mip_problem* p, const double* root_lb, const doubl
     BP_TRY(probe_prepare(p, 2 * npairs, cache->cap > 0 ? cache->cap : 1, s));
     ProbeWork* pw = probe_work(p);
     longlong2* root = p->w.bkey[0];
-    if (p->n) k_root_keys<<<(p->n + 255) / 256 < 1216 ? (p->n + 255) / 256 : 1216, 256, 0, s>>>(p->n, root_lb, root_ub, p->dp.is_int, root);
+    BP_TRY(root_keys(p, root_lb, root_ub, root, s));
     BP_CUDA_TRY(cudaMemsetAsync(pw->ctr, 0, sizeof(int), s));
     BP_CUDA_TRY(cudaMemsetAsync(pw->ectr, 0, sizeof(unsigned long long), s));
     ProbeArgs a;

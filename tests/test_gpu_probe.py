@@ -110,3 +110,52 @@ def test_probes_full_size(pkg):
     o = P.probe_batch(rl, ru, var, boxes)
     g = _gpu_probe(pkg, p, rl, ru, var, boxes)
     _compare(p, g, o)
+
+
+def _gpu_priority(pkg, p, lb, ub):
+    import torch
+    prob = pkg.Problem(p)
+    k1, k2, k3, order = prob.probe_priority(torch.tensor(lb, device="cuda"), torch.tensor(ub, device="cuda"))
+    return k1.cpu().numpy(), k2.cpu().numpy(), k3.cpu().numpy(), order.cpu().numpy()
+
+
+def test_priority_golden(pkg):
+    d = load_golden("priority_small.json")
+    p = golden_problem(d)
+    k1, k2, k3, order = _gpu_priority(pkg, p, np.array(d["lb"], float), np.array(d["ub"], float))
+    np.testing.assert_array_equal(k1, d["key1"])
+    np.testing.assert_array_equal(k2, d["key2"])
+    np.testing.assert_array_equal(k3, d["key3"])
+    np.testing.assert_array_equal(order, d["order"])
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_priority_exact_data(pkg, seed):
+    """Integer coefficients and bounds: keys and order identical to the oracle's."""
+    p = synth.knapsack_cover(seed=60 + seed, m=5000, n=10_000, nnz=100_000)
+    P = oracle.Problem(p)
+    rl, ru, _, _ = P.bp(p.lb, p.ub)
+    o1, o2, o3 = P.probe_priority(rl, ru)
+    g1, g2, g3, gord = _gpu_priority(pkg, p, rl, ru)
+    np.testing.assert_array_equal(g1, o1)
+    np.testing.assert_array_equal(g2, o2)
+    np.testing.assert_array_equal(g3, o3)
+    np.testing.assert_array_equal(gord, oracle.priority_order(o1, o2, o3))
+
+
+def test_priority_general_data(pkg):
+    """Non-integer data (activities summed in another order): key1 identical, key2 and key3
+    within 1e-9 relative, and the GPU order sorted by the GPU keys."""
+    p = synth.random_milp(77, m=3000, n=4000, len_lo=1, len_hi=60, inf_fraction=0.05, int_fraction=0.8)
+    P = oracle.Problem(p)
+    rl, ru, r, _ = P.bp(p.lb, p.ub)
+    o1, o2, o3 = P.probe_priority(rl, ru)
+    g1, g2, g3, gord = _gpu_priority(pkg, p, rl, ru)
+    np.testing.assert_array_equal(g1, o1)
+    for g, o in ((g2, o2), (g3, o3)):
+        fin = np.isfinite(o)
+        np.testing.assert_array_equal(np.isfinite(g), fin)
+        assert (np.abs(g[fin] - o[fin]) <= 1e-9 * np.maximum(1, np.abs(o[fin]))).all()
+    assert sorted(gord.tolist()) == np.flatnonzero(o1 >= 0).tolist()
+    keys = [(-g1[j], -g2[j], g3[j], j) for j in gord]
+    assert keys == sorted(keys)
