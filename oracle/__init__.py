@@ -82,7 +82,47 @@ def lib():
         L.orc_probe_priority.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                          C.POINTER(C.c_int32), C.POINTER(C.c_double),
                                          C.POINTER(C.c_double)]
+        _bind_fp(L)
     return _lib
+
+
+class FpParams(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("bulk_rule", C.c_int32), ("fraction", C.c_double),
+                ("last_single", C.c_int32), ("theta", C.c_double), ("max_rounds", C.c_int32)]
+
+
+class FpResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("bulks", C.c_int32), ("bp_runs", C.c_int32), ("recoveries", C.c_int32),
+                ("fixed_by_choice", C.c_int32), ("pad", C.c_int32), ("nnz_updates", C.c_int64),
+                ("fragile", C.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}
+
+
+class Cache(C.Structure):
+    _fields_ = [("npairs", C.c_int32), ("var", C.POINTER(C.c_int32)), ("boxes", C.POINTER(C.c_double)),
+                ("status", C.POINTER(C.c_int32)), ("offsets", C.POINTER(C.c_int64)),
+                ("ent_var", C.POINTER(C.c_int32)), ("ent_l", C.POINTER(C.c_double)),
+                ("ent_u", C.POINTER(C.c_double))]
+
+
+def _bind_fp(L):
+    L.orc_fix_and_propagate.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                        C.POINTER(C.c_double), C.POINTER(Cache), C.POINTER(FpParams),
+                                        C.POINTER(C.c_double), C.POINTER(FpResult)]
+    L.orc_uniform.restype = C.c_double
+    L.orc_uniform.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64]
+    L.orc_splitmix64.restype = C.c_uint64
+    L.orc_splitmix64.argtypes = [C.c_uint64]
+
+
+def uniform(seed, bulk, var, draw):
+    return lib().orc_uniform(seed, bulk, var, draw)
+
+
+def splitmix64(z):
+    return lib().orc_splitmix64(z)
 
 
 class Problem:
@@ -179,6 +219,39 @@ class Problem:
         lib().orc_probe_priority(self.h, _p(lb, C.c_double), _p(ub, C.c_double), _p(k1, C.c_int32),
                                  _p(k2, C.c_double), _p(k3, C.c_double))
         return k1, k2, k3
+
+
+def _fix_and_propagate(self, x, lb, ub, seed=1, bulk_rule=0, fraction=0.01, last_single=36, theta=1e-3,
+                       max_rounds=10000, cache=None):
+    """Fix-and-propagate (Algorithm 1); cache: dict from probe_batch plus 'pairs' and 'boxes'.
+    Returns (x_out, result dict)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    lb = np.ascontiguousarray(lb, dtype=np.float64)
+    ub = np.ascontiguousarray(ub, dtype=np.float64)
+    out = np.zeros(self.n)
+    prm = FpParams(seed, bulk_rule, fraction, last_single, theta, max_rounds)
+    res = FpResult()
+    cp = None
+    keep = []
+    if cache is not None:
+        arrs = [np.ascontiguousarray(cache["pairs"], dtype=np.int32),
+                np.ascontiguousarray(cache["boxes"], dtype=np.float64).reshape(-1),
+                np.ascontiguousarray(cache["status"], dtype=np.int32),
+                np.ascontiguousarray(cache["offsets"], dtype=np.int64),
+                np.ascontiguousarray(cache["var"], dtype=np.int32),
+                np.ascontiguousarray(cache["l"], dtype=np.float64),
+                np.ascontiguousarray(cache["u"], dtype=np.float64)]
+        keep = arrs
+        cp = Cache(len(arrs[0]), _p(arrs[0], C.c_int32), _p(arrs[1], C.c_double), _p(arrs[2], C.c_int32),
+                   _p(arrs[3], C.c_int64), _p(arrs[4], C.c_int32), _p(arrs[5], C.c_double), _p(arrs[6], C.c_double))
+    lib().orc_fix_and_propagate(self.h, _p(x, C.c_double), _p(lb, C.c_double), _p(ub, C.c_double),
+                                C.byref(cp) if cp is not None else None, C.byref(prm), _p(out, C.c_double),
+                                C.byref(res))
+    del keep
+    return out, res.as_dict()
+
+
+Problem.fix_and_propagate = _fix_and_propagate
 
 
 def probe_split(is_int, l, u):

@@ -38,35 +38,11 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include "oracle.h"
+
 #define ORC_TOL 1e-6
 #define ORC_INF 1e20
 #define ORC_U 1.1102230246251565e-16 /* 2^-53, unit roundoff of binary64 */
-
-enum { ORC_FIXPOINT = 0, ORC_INFEASIBLE = 1, ORC_ROUND_LIMIT = 2 };
-
-typedef struct {
-    int32_t m, n;
-    int64_t nnz;
-    int64_t *row_ptr;
-    int32_t *col;
-    double *val;
-    double *g;
-    uint8_t *is_int;
-    int64_t *col_ptr; /* transpose: rows of each variable */
-    int32_t *row_idx;
-    double *col_val;
-} orc_problem;
-
-typedef struct {
-    int32_t status;
-    int32_t rounds;
-    int32_t first_infeasible_row;
-    int32_t first_infeasible_var;
-    int64_t nnz_updates;
-    int64_t n_changed;
-    int64_t candidates;
-    int64_t fragile;
-} orc_bp_result;
 
 static double gam(double k) { return k * ORC_U / (1.0 - k * ORC_U); }
 

@@ -1,0 +1,386 @@
+/*
+ * Oracle of bulk fix-and-propagate rounding (Section 2.3, Algorithm 1 "Bound Propagation
+ * Rounding", repair and LP polish off as in the paper's experiments).
+ *
+ * TEST INFRASTRUCTURE ONLY: called by the tests and the benchmark's CPU leg, never by the
+ * library.  Plain sequential C over IEEE double (-ffp-contract=off).
+ *
+ * Steps, in the paper's order, with the readings of the design notes where the paper is open:
+ *  1. propagate the start bounds (every row);
+ *  2. initial sort of the integer variables (Section 2.3): binary (u - l <= 1) before ternary
+ *     (u - l = 2) before the rest, then ascending fractionality |x - round(x)|, then index;
+ *  3. per bulk:
+ *     - bulk size: ceil(sqrt(remaining)) or ceil(fraction * integer variables); one variable
+ *       at a time for the last `last_single` (36 in the paper) and in recovery;
+ *     - for bulks larger than one, a stable implied-slack sort of the unfixed variables:
+ *       S_i = sum over rows with a finite minimal activity of (a / slack)^2,
+ *       slack = max(g - L_min, tol), descending (Section 2.3 equation);
+ *     - two candidate values per variable drawn from the rounding distribution (random near
+ *       .5, nearest away from .5: P(up) = 0 for f <= .25, 1 for f >= .75, linear between);
+ *       single-variable bulks try the drawn value and the other integer neighbour;
+ *     - with a probing cache, a fixing is kept only if its value and the cached implications
+ *       of the branch containing it agree with the fixings kept before it (Section 2.2), and
+ *       the cached bounds tighten the start of the propagation (warm start);
+ *     - both candidate vectors are propagated from the rows of the variables whose bounds
+ *       they change; the first feasible result is kept (probe 0 first);
+ *     - both infeasible: a bulk's variables are retried one by one (recovery); a single
+ *       variable that fails both ways ends the search (repair disabled, Section 3): the
+ *       remaining integer variables are rounded to the nearest value inside their bounds
+ *       without propagation and the result is INFEASIBLE.
+ *  4. FEASIBLE when every integer variable is fixed and the last propagation was feasible.
+ *
+ * The random draws use splitmix64 (Steele, Lea, Flood, "Fast splittable pseudorandom number
+ * generators", OOPSLA 2014) chained over (seed, bulk, variable, draw); the 53 high bits give a
+ * uniform double in [0, 1).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "oracle.h"
+
+#define FP_TOL 1e-6
+
+typedef struct {
+    uint64_t seed;
+    int32_t bulk_rule;      /* 0: ceil(sqrt(remaining)), 1: ceil(fraction * integer variables) */
+    double fraction;
+    int32_t last_single;
+    double theta;
+    int32_t max_rounds;
+} orc_fp_params;
+
+typedef struct {
+    int32_t status;         /* 0 feasible (all integers fixed, propagation feasible), 1 infeasible */
+    int32_t bulks;
+    int32_t bp_runs;
+    int32_t recoveries;
+    int32_t fixed_by_choice; /* kept fixings of the chosen candidate vectors, summed over bulks */
+    int32_t pad;
+    int64_t nnz_updates;
+    int64_t fragile;
+} orc_fp_result;
+
+/* probing cache in the layout of bp_probe_batch */
+typedef struct {
+    int32_t npairs;
+    const int32_t *var;
+    const double *boxes;
+    const int32_t *status;
+    const int64_t *offsets;
+    const int32_t *ent_var;
+    const double *ent_l;
+    const double *ent_u;
+} orc_cache;
+
+static uint64_t splitmix64(uint64_t z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+uint64_t orc_splitmix64(uint64_t z) { return splitmix64(z); }
+
+double orc_uniform(uint64_t seed, uint64_t bulk, uint64_t var, uint64_t draw)
+{
+    uint64_t h = splitmix64(seed);
+    h = splitmix64(h ^ bulk);
+    h = splitmix64(h ^ var);
+    h = splitmix64(h ^ draw);
+    return (double)(h >> 11) * (1.0 / 9007199254740992.0);
+}
+
+static double clampd(double x, double l, double u) { return x < l ? l : (x > u ? u : x); }
+
+/* one draw from the rounding distribution of x (already inside the bounds) */
+static double draw_value(double x, uint64_t seed, uint64_t bulk, int32_t j, int d)
+{
+    const double fl = floor(x);
+    const double f = x - fl;
+    if (f == 0.0) return x;
+    double pup;
+    if (f <= 0.25) pup = 0.0;
+    else if (f >= 0.75) pup = 1.0;
+    else pup = (f - 0.25) / 0.5;
+    const double u = orc_uniform(seed, bulk, (uint64_t)j, (uint64_t)d);
+    return u < pup ? fl + 1.0 : fl;
+}
+
+static uint64_t isqrt_ceil(uint64_t r)
+{
+    uint64_t s = (uint64_t)sqrt((double)r);
+    while (s * s > r) --s;
+    while ((s + 1) * (s + 1) <= r) ++s;
+    return s * s == r ? s : s + 1;
+}
+
+/* sort helpers (stable merge sort over an index array with a key comparator) */
+typedef struct {
+    const int32_t *cls;
+    const double *frac;
+    const double *S;
+} sort_ctx;
+
+static int cmp_initial(const sort_ctx *c, int32_t a, int32_t b)
+{
+    if (c->cls[a] != c->cls[b]) return c->cls[a] < c->cls[b] ? -1 : 1;
+    if (c->frac[a] != c->frac[b]) return c->frac[a] < c->frac[b] ? -1 : 1;
+    return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+static int cmp_slack(const sort_ctx *c, int32_t a, int32_t b)
+{
+    if (c->S[a] != c->S[b]) return c->S[a] > c->S[b] ? -1 : 1;   /* descending; ties keep order */
+    return 0;
+}
+
+static void merge_sort(int32_t *v, int32_t *tmp, int64_t n, const sort_ctx *c, int (*cmp)(const sort_ctx *, int32_t, int32_t))
+{
+    for (int64_t width = 1; width < n; width *= 2) {
+        for (int64_t lo = 0; lo < n; lo += 2 * width) {
+            int64_t mid = lo + width < n ? lo + width : n;
+            int64_t hi = lo + 2 * width < n ? lo + 2 * width : n;
+            int64_t i = lo, j = mid, k = lo;
+            while (i < mid && j < hi) tmp[k++] = cmp(c, v[j], v[i]) < 0 ? v[j++] : v[i++];
+            while (i < mid) tmp[k++] = v[i++];
+            while (j < hi) tmp[k++] = v[j++];
+        }
+        memcpy(v, tmp, sizeof(int32_t) * (size_t)n);
+    }
+}
+
+/* implied slack S_i of every variable under bounds (l, u) */
+static void implied_slack(const orc_problem *p, const double *l, const double *u, double *S)
+{
+    for (int32_t j = 0; j < p->n; ++j) S[j] = 0.0;
+    for (int32_t k = 0; k < p->m; ++k) {
+        if (isinf(p->g[k])) continue;
+        double minfin = 0.0;
+        int ninf = 0;
+        for (int64_t q = p->row_ptr[k]; q < p->row_ptr[k + 1]; ++q) {
+            const double a = p->val[q];
+            const double b = a > 0 ? l[p->col[q]] : u[p->col[q]];
+            if (isinf(b)) { ninf++; continue; }
+            const double t = a * b;
+            minfin = minfin + t;
+        }
+        if (ninf) continue;
+        double slack = p->g[k] - minfin;
+        if (slack < FP_TOL) slack = FP_TOL;
+        for (int64_t q = p->row_ptr[k]; q < p->row_ptr[k + 1]; ++q) {
+            const double s = p->val[q] / slack;
+            const double s2 = s * s;
+            S[p->col[q]] = S[p->col[q]] + s2;
+        }
+    }
+}
+
+/* cache branch of (j, value): entry index 2*pair + b, or -1 */
+static int64_t cache_branch(const orc_cache *c, const int32_t *pair_of, int32_t j, double val)
+{
+    if (!c) return -1;
+    const int32_t i = pair_of[j];
+    if (i < 0) return -1;
+    for (int b = 0; b < 2; ++b) {
+        const double lo = c->boxes[4 * i + 2 * b], hi = c->boxes[4 * i + 2 * b + 1];
+        if (val >= lo && val <= hi) return 2 * (int64_t)i + b;
+    }
+    return -1;
+}
+
+static int var_cross(int is_i, double l, double u) { return is_i ? l > u : l > u + FP_TOL; }
+
+int orc_fix_and_propagate(const orc_problem *p, const double *x, const double *lb0, const double *ub0,
+                          const orc_cache *cache, const orc_fp_params *prm, double *x_out, orc_fp_result *res)
+{
+    const int32_t n = p->n;
+    memset(res, 0, sizeof(*res));
+    double *l = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+    double *u = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+    double *cl[2], *cu[2];
+    for (int i = 0; i < 2; ++i) {
+        cl[i] = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+        cu[i] = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+    }
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    int32_t *work = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    int32_t *tmp = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    int32_t *cls = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    double *frac = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+    double *S = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+    double *val[2];
+    val[0] = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+    val[1] = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+    int32_t *recq = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    int32_t *w0 = (int32_t *)malloc(sizeof(int32_t) * (size_t)(p->m ? p->m : 1));
+    uint8_t *rowmark = (uint8_t *)calloc((size_t)(p->m ? p->m : 1), 1);
+    int32_t *pair_of = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    for (int32_t j = 0; j < n; ++j) pair_of[j] = -1;
+    if (cache)
+        for (int32_t i = cache->npairs - 1; i >= 0; --i) pair_of[cache->var[i]] = i;   /* first pair wins */
+
+    memcpy(l, lb0, sizeof(double) * (size_t)n);
+    memcpy(u, ub0, sizeof(double) * (size_t)n);
+    orc_bp_result r;
+    orc_bp(p, l, u, NULL, NULL, NULL, 0, prm->theta, prm->max_rounds, 0, &r, NULL, NULL);
+    res->bp_runs++;
+    res->nnz_updates += r.nnz_updates;
+    res->fragile += r.fragile;
+    int infeasible = r.status == ORC_INFEASIBLE;
+
+    /* initial order (under the propagated start bounds) */
+    int64_t nint = 0;
+    for (int32_t j = 0; j < n; ++j) {
+        if (!p->is_int[j]) continue;
+        const double w = u[j] - l[j];
+        cls[j] = w <= 1.0 ? 0 : (w == 2.0 ? 1 : 2);
+        const double xh = clampd(x[j], l[j], u[j]);
+        const double f = xh - floor(xh);
+        frac[j] = f < 1.0 - f ? f : 1.0 - f;
+        order[nint++] = j;
+    }
+    sort_ctx ctx = {cls, frac, S};
+    merge_sort(order, tmp, nint, &ctx, cmp_initial);
+
+    int rounding_infeasible = infeasible;
+    int64_t nrec = 0, rec_pos = 0;
+    uint64_t bulk_index = 0;
+    while (!rounding_infeasible) {
+        /* unfixed integer variables in the initial order */
+        int64_t nun = 0;
+        for (int64_t i = 0; i < nint; ++i)
+            if (l[order[i]] < u[order[i]]) work[nun++] = order[i];
+        if (nun == 0) break;
+        int64_t bsize;
+        int single = 0;
+        int32_t *bulk = work;
+        int32_t one;
+        while (rec_pos < nrec && !(l[recq[rec_pos]] < u[recq[rec_pos]])) rec_pos++;
+        if (rec_pos < nrec) {
+            one = recq[rec_pos++];
+            bulk = &one;
+            bsize = 1;
+            single = 1;
+        } else {
+            nrec = rec_pos = 0;
+            if (nun <= prm->last_single) {
+                bsize = 1;
+            } else if (prm->bulk_rule == 0) {
+                bsize = (int64_t)isqrt_ceil((uint64_t)nun);
+            } else {
+                bsize = (int64_t)ceil(prm->fraction * (double)nint);
+                if (bsize < 1) bsize = 1;
+            }
+            if (bsize > nun) bsize = nun;
+            if (bsize > 1) {
+                implied_slack(p, l, u, S);
+                merge_sort(work, tmp, nun, &ctx, cmp_slack);
+            }
+            single = bsize == 1;
+        }
+        /* candidate values */
+        for (int64_t i = 0; i < bsize; ++i) {
+            const int32_t j = bulk[i];
+            const double xh = clampd(x[j], l[j], u[j]);
+            const double v0 = clampd(draw_value(xh, prm->seed, bulk_index, j, 0), l[j], u[j]);
+            double v1;
+            if (single) {
+                const double fl = floor(xh);
+                v1 = clampd(v0 == fl ? fl + 1.0 : fl, l[j], u[j]);
+            } else {
+                v1 = clampd(draw_value(xh, prm->seed, bulk_index, j, 1), l[j], u[j]);
+            }
+            val[0][j] = v0;
+            val[1][j] = v1;
+        }
+        /* start boxes: kept fixings and their cached implications */
+        int kept[2] = {0, 0};
+        for (int c = 0; c < 2; ++c) {
+            memcpy(cl[c], l, sizeof(double) * (size_t)n);
+            memcpy(cu[c], u, sizeof(double) * (size_t)n);
+            for (int64_t i = 0; i < bsize; ++i) {
+                const int32_t j = bulk[i];
+                const double v = val[c][j];
+                if (!(v >= cl[c][j] && v <= cu[c][j])) continue;
+                const int64_t e = cache_branch(cache, pair_of, j, v);
+                int ok = 1;
+                if (e >= 0) {
+                    if (cache->status[e] == ORC_INFEASIBLE) ok = 0;
+                    for (int64_t q = cache->offsets[e]; ok && q < cache->offsets[e + 1]; ++q) {
+                        const int32_t w = cache->ent_var[q];
+                        const double lo = cache->ent_l[q] > cl[c][w] ? cache->ent_l[q] : cl[c][w];
+                        const double hi = cache->ent_u[q] < cu[c][w] ? cache->ent_u[q] : cu[c][w];
+                        if (w == j ? !(v >= lo && v <= hi) : var_cross(p->is_int[w], lo, hi)) ok = 0;
+                    }
+                }
+                if (!ok) continue;
+                kept[c]++;
+                cl[c][j] = v;
+                cu[c][j] = v;
+                if (e >= 0)
+                    for (int64_t q = cache->offsets[e]; q < cache->offsets[e + 1]; ++q) {
+                        const int32_t w = cache->ent_var[q];
+                        if (w == j) continue;
+                        if (cache->ent_l[q] > cl[c][w]) cl[c][w] = cache->ent_l[q];
+                        if (cache->ent_u[q] < cu[c][w]) cu[c][w] = cache->ent_u[q];
+                    }
+            }
+        }
+        /* double propagation */
+        int feasible[2] = {0, 0};
+        for (int c = 0; c < 2; ++c) {
+            if (!kept[c]) continue;
+            int32_t nw = 0;
+            memset(rowmark, 0, (size_t)p->m);
+            for (int32_t j = 0; j < n; ++j) {
+                if (cl[c][j] == l[j] && cu[c][j] == u[j]) continue;
+                for (int64_t s = p->col_ptr[j]; s < p->col_ptr[j + 1]; ++s) rowmark[p->row_idx[s]] = 1;
+            }
+            for (int32_t k = 0; k < p->m; ++k)
+                if (rowmark[k]) w0[nw++] = k;
+            orc_bp(p, cl[c], cu[c], NULL, NULL, w0, nw, prm->theta, prm->max_rounds, 0, &r, NULL, NULL);
+            res->bp_runs++;
+            res->nnz_updates += r.nnz_updates;
+            res->fragile += r.fragile;
+            feasible[c] = r.status != ORC_INFEASIBLE;
+        }
+        res->bulks++;
+        bulk_index++;
+        const int pick = feasible[0] ? 0 : (feasible[1] ? 1 : -1);
+        if (pick >= 0) {
+            res->fixed_by_choice += kept[pick];
+            memcpy(l, cl[pick], sizeof(double) * (size_t)n);
+            memcpy(u, cu[pick], sizeof(double) * (size_t)n);
+        } else if (!single) {
+            memcpy(recq, bulk, sizeof(int32_t) * (size_t)bsize);
+            nrec = bsize;
+            rec_pos = 0;
+            res->recoveries++;
+        } else {
+            rounding_infeasible = 1;
+        }
+    }
+    /* remaining integer variables: nearest value inside the bounds, no propagation */
+    for (int64_t i = 0; i < nint; ++i) {
+        const int32_t j = order[i];
+        if (l[j] < u[j]) {
+            const double v = clampd(floor(clampd(x[j], l[j], u[j]) + 0.5), l[j], u[j]);
+            l[j] = u[j] = v;
+        }
+    }
+    for (int32_t j = 0; j < n; ++j) {
+        if (p->is_int[j]) {
+            x_out[j] = l[j];
+        } else {
+            x_out[j] = clampd(x[j], l[j], u[j]);
+        }
+    }
+    res->status = rounding_infeasible ? 1 : 0;
+    for (int i = 0; i < 2; ++i) { free(cl[i]); free(cu[i]); free(val[i]); }
+    free(l); free(u); free(order); free(work); free(tmp); free(cls); free(frac); free(S);
+    free(recq); free(w0); free(rowmark); free(pair_of);
+    return 0;
+}

@@ -1,0 +1,131 @@
+"""Pins of the oracle's fix-and-propagate rounding (Algorithm 1, Section 2.3)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_20499_gb300 import synth
+from tests.helpers import dense, feasible_points, load_golden, milp_from_dense
+
+
+def test_splitmix64_reference_values():
+    """The generator's published reference outputs for the state 1234567 (SplitMix64, Steele,
+    Lea and Flood 2014; the same values as the reference C implementation's test)."""
+    gamma = 0x9E3779B97F4A7C15
+    want = [6457827717110365317, 3203168211198807973, 9817491932198370423, 4593380528125082431,
+            16408922859458223821]
+    s = 1234567
+    for w in want:
+        assert oracle.splitmix64(s) == w
+        s = (s + gamma) % (1 << 64)
+
+
+def test_uniform_range_and_independence():
+    u = np.array([oracle.uniform(7, b, j, d) for b in range(20) for j in range(50) for d in range(2)])
+    assert ((u >= 0) & (u < 1)).all()
+    assert abs(u.mean() - 0.5) < 0.03
+    assert len(set(u.tolist())) == len(u)
+
+
+@pytest.mark.parametrize("case", range(5))
+def test_golden(case):
+    c = load_golden("fp_small.json")["cases"][case]
+    p = synth.Milp(c["m"], c["n"], np.array(c["row_ptr"], dtype=np.int64), np.array(c["col"], dtype=np.int32),
+                   np.array(c["val"], float), np.array(c["g"], float), np.array(c["lb"], float),
+                   np.array(c["ub"], float), np.array(c["is_int"], dtype=np.uint8), np.zeros(c["n"]))
+    for seed in (1, 2, 3):
+        x, r = oracle.Problem(p).fix_and_propagate(c["x"], p.lb, p.ub, seed=seed)
+        assert r["status"] == c["status"], c["note"]
+        np.testing.assert_array_equal(x, c["x_out"])
+        assert r["bulks"] == c["bulks"] and r["bp_runs"] == c["bp_runs"] and r["recoveries"] == c["recoveries"]
+
+
+@pytest.mark.parametrize("f,p_up", [(0.1, 0.0), (0.25, 0.0), (0.28, 0.06), (0.3, 0.1), (0.5, 0.5), (0.7, 0.9), (0.72, 0.94), (0.75, 1.0), (0.9, 1.0)])
+def test_rounding_distribution(f, p_up):
+    """P(round up) = 0 up to f = .25, 1 from f = .75, linear between (random near .5, nearest
+    away from .5).  Measured on a problem without rows: every fixing succeeds, so x_out is the
+    first draw of each variable."""
+    n = 2000
+    p = milp_from_dense(np.zeros((0, n)), [], np.zeros(n), np.full(n, 5.0), np.ones(n))
+    x = np.full(n, 2.0 + f)
+    out, r = oracle.Problem(p).fix_and_propagate(x, p.lb, p.ub, seed=11, last_single=0)
+    assert r["status"] == 0
+    up = (out == 3.0).mean()
+    assert set(np.unique(out)) <= {2.0, 3.0}
+    sd = math.sqrt(max(p_up * (1 - p_up), 1e-12) / n)
+    assert abs(up - p_up) <= 5 * sd + 1e-12
+
+
+def test_bulk_sizes_without_rows():
+    """Without rows every candidate is feasible: bulk sizes follow ceil(sqrt(remaining)) down
+    to 36 remaining, then one variable per bulk."""
+    n = 1000
+    p = milp_from_dense(np.zeros((0, n)), [], np.zeros(n), np.ones(n), np.ones(n))
+    _, r = oracle.Problem(p).fix_and_propagate(np.full(n, 0.5), p.lb, p.ub)
+    rem, bulks = n, 0
+    while rem > 36:
+        rem -= math.isqrt(rem - 1) + 1     # ceil(sqrt(rem))
+        bulks += 1
+    bulks += rem
+    assert r["bulks"] == bulks and r["status"] == 0 and r["bp_runs"] == 1 + 2 * bulks
+    _, r = oracle.Problem(p).fix_and_propagate(np.full(n, 0.5), p.lb, p.ub, bulk_rule=1, fraction=0.05)
+    rem, bulks = n, 0
+    while rem > 36:
+        rem -= 50
+        bulks += 1
+    assert r["bulks"] == bulks + rem
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_brute_force_soundness(seed):
+    """A FEASIBLE result is an integer point satisfying every row; a problem without integer
+    points never ends FEASIBLE."""
+    rng = np.random.default_rng(seed)
+    n, m = int(rng.integers(3, 8)), int(rng.integers(1, 6))
+    A = rng.integers(-4, 5, size=(m, n)).astype(float)
+    A[rng.uniform(size=(m, n)) < 0.3] = 0.0
+    for k in range(m):
+        if not A[k].any():
+            A[k, rng.integers(0, n)] = 1.0
+    ub = rng.integers(1, 4, size=n).astype(float)
+    g = rng.integers(-2, 8, size=m).astype(float)
+    p = milp_from_dense(A, g, np.zeros(n), ub, np.ones(n))
+    pts = feasible_points(p, p.lb, p.ub)
+    for s in range(3):
+        x, r = oracle.Problem(p).fix_and_propagate(rng.uniform(0, ub), p.lb, p.ub, seed=s)
+        if r["status"] == 0:
+            assert (A @ x <= g + 1e-6).all() and (x >= 0).all() and (x <= ub).all()
+            assert (x == np.round(x)).all()
+        if len(pts) == 0:
+            assert r["status"] == 1
+
+
+def test_cache_keeps_only_consistent_fixings():
+    """With the probing cache of every binary, a result marked FEASIBLE is feasible and no
+    fixing whose cached branch is infeasible is used (checked by brute force)."""
+    for seed in range(10):
+        p = synth.knapsack_cover(seed=seed, m=8, n=12, nnz=40)
+        P = oracle.Problem(p)
+        rl, ru, r, _ = P.bp(p.lb, p.ub)
+        if r["status"] != 0:
+            continue
+        var = np.array([j for j in range(p.n) if rl[j] < ru[j]], dtype=np.int32)
+        boxes = np.array([oracle.probe_split(1, rl[j], ru[j]) for j in var], dtype=float).reshape(-1, 4)
+        cache = P.probe_batch(rl, ru, var, boxes)
+        cache["pairs"], cache["boxes"] = var, boxes
+        A = dense(p)
+        for s in range(3):
+            x0 = np.random.default_rng(s).uniform(0, 1, p.n)
+            x, r = P.fix_and_propagate(x0, p.lb, p.ub, seed=s, cache=cache)
+            if r["status"] == 0:
+                assert (A @ x <= p.g + 1e-6).all()
+
+
+def test_deterministic_per_seed():
+    p = synth.random_milp(3, 300, 400, len_lo=2, len_hi=10, integer_coefs=True, int_fraction=1.0, slack_scale=0.3)
+    x0 = np.random.default_rng(0).uniform(0, 20, p.n)
+    a = oracle.Problem(p).fix_and_propagate(x0, p.lb, p.ub, seed=5)
+    b = oracle.Problem(p).fix_and_propagate(x0, p.lb, p.ub, seed=5)
+    np.testing.assert_array_equal(a[0], b[0])
+    assert a[1] == b[1]
