@@ -206,6 +206,89 @@ int bp_probe_batch(mip_problem *p, const double *root_lb, const double *root_ub,
 int bp_probe_priority(mip_problem *p, const double *lb, const double *ub, int32_t *key1,
                       double *key2, double *key3, int32_t *order, int32_t *count, void *stream);
 
+/* ------------------------------------------------------------ fix-and-propagate */
+
+#define FP_BULK_SQRT 0        /* bulk size ceil(sqrt(remaining unfixed integer variables)) */
+#define FP_BULK_FRACTION 1    /* bulk size ceil(fraction * integer variables) */
+#define FP_FEASIBLE 0
+#define FP_INFEASIBLE 1
+
+/* Parameters of fix_and_propagate.  seed: key of the counter-based random draws.
+ * last_single: the last variables are fixed one at a time (36 in the paper, Section 2.3).
+ * theta, max_rounds: as in bp_params, for every propagation.
+ * order_score (DEVICE double[n] or NULL): when given, the initial order ranks variables by
+ *   class (binary, ternary, rest), then descending score, then fractionality, then index.
+ * up_prob (DEVICE double[n] or NULL): when given, replaces the rounding distribution's
+ *   probability of rounding up for fractions strictly between 0.25 and 0.75 (the random band);
+ *   outside the band the nearest value is always drawn.  Propagation still judges every fix. */
+typedef struct {
+    uint64_t seed;
+    int32_t bulk_rule;
+    int32_t last_single;
+    double fraction;
+    double theta;
+    int32_t max_rounds;
+    int32_t reserved;
+    const double *order_score;
+    const double *up_prob;
+} fp_params;
+
+/* A probing cache (bp_probe_batch's layout, all DEVICE arrays): the pairs' variables and
+ * branch boxes, and per branch its status, entry offsets and implied bounds. */
+typedef struct {
+    int32_t npairs;
+    int32_t reserved;
+    const int32_t *var;
+    const double *boxes;
+    const int32_t *status;
+    const int64_t *offsets;
+    const int32_t *ent_var;
+    const double *ent_l;
+    const double *ent_u;
+} fp_cache;
+
+/* Result of fix_and_propagate.  bulks: iterations (bulk and single); bp_runs: propagations
+ * (the start one and every candidate vector with at least one kept fixing); recoveries: bulks
+ * that failed both ways and were retried one variable at a time; fixed_by_choice: kept
+ * fixings of the chosen vectors; nnz_updates: summed over all propagations. */
+typedef struct {
+    int32_t status;
+    int32_t bulks;
+    int32_t bp_runs;
+    int32_t recoveries;
+    int32_t fixed_by_choice;
+    int32_t reserved;
+    int64_t nnz_updates;
+} fp_result;
+
+void fp_params_default(fp_params *p);   /* seed 1, sqrt rule, last_single 36, fraction 0.01 */
+
+/*
+ * fix_and_propagate -- bulk rounding with bound propagation (Section 2.3, Algorithm 1;
+ * repair and LP polish off, as in the paper's experiments).
+ *
+ * Propagates the start bounds, sorts the integer variables (binary, ternary, rest; then
+ * fractionality of x), and fixes them in bulks: per bulk a stable implied-slack sort
+ * (S_i = sum over rows of (a / slack)^2, descending), two candidate values per variable drawn
+ * from the rounding distribution, the probing cache's conflict filter and warm start (when a
+ * cache is given), a propagation of each candidate vector from the rows of the variables it
+ * changes, and the first feasible result kept.  A bulk failing both ways is retried one
+ * variable at a time; a single variable failing both ways ends the search and the remaining
+ * integer variables are rounded to the nearest value inside their bounds (FP_INFEASIBLE).
+ *
+ * x:        DEVICE double[n], the point to round (e.g. an LP relaxation solution).
+ * lb, ub:   DEVICE double[n] start bounds (not modified).
+ * cache:    NULL or a probing cache (see fp_cache).
+ * x_out:    DEVICE double[n]: integer variables at their fixed values, continuous variables
+ *           x clamped to their final bounds.
+ * result:   HOST pointer, valid at return (the call synchronises the stream: every bulk's
+ *           control decision reads a few words back).
+ * Returns BP_OK, BP_ERR_INVALID, BP_ERR_OOM, BP_ERR_CUDA or BP_ERR_TIMEOUT.
+ */
+int fix_and_propagate(mip_problem *p, const double *x, const double *lb, const double *ub,
+                      const fp_cache *cache, const fp_params *params, double *x_out,
+                      fp_result *result, void *stream);
+
 /* ------------------------------------------------------------------- errors */
 
 /* Thread-local message of the last error ("" if none). */

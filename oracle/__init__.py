@@ -88,7 +88,8 @@ def lib():
 
 class FpParams(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("bulk_rule", C.c_int32), ("fraction", C.c_double),
-                ("last_single", C.c_int32), ("theta", C.c_double), ("max_rounds", C.c_int32)]
+                ("last_single", C.c_int32), ("theta", C.c_double), ("max_rounds", C.c_int32),
+                ("order_score", C.POINTER(C.c_double)), ("up_prob", C.POINTER(C.c_double))]
 
 
 class FpResult(C.Structure):
@@ -222,14 +223,17 @@ class Problem:
 
 
 def _fix_and_propagate(self, x, lb, ub, seed=1, bulk_rule=0, fraction=0.01, last_single=36, theta=1e-3,
-                       max_rounds=10000, cache=None):
+                       max_rounds=10000, cache=None, order_score=None, up_prob=None):
     """Fix-and-propagate (Algorithm 1); cache: dict from probe_batch plus 'pairs' and 'boxes'.
     Returns (x_out, result dict)."""
     x = np.ascontiguousarray(x, dtype=np.float64)
     lb = np.ascontiguousarray(lb, dtype=np.float64)
     ub = np.ascontiguousarray(ub, dtype=np.float64)
     out = np.zeros(self.n)
-    prm = FpParams(seed, bulk_rule, fraction, last_single, theta, max_rounds)
+    osc = None if order_score is None else np.ascontiguousarray(order_score, dtype=np.float64)
+    upp = None if up_prob is None else np.ascontiguousarray(up_prob, dtype=np.float64)
+    prm = FpParams(seed, bulk_rule, fraction, last_single, theta, max_rounds,
+                   None if osc is None else _p(osc, C.c_double), None if upp is None else _p(upp, C.c_double))
     res = FpResult()
     cp = None
     keep = []

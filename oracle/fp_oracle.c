@@ -49,6 +49,8 @@ typedef struct {
     int32_t last_single;
     double theta;
     int32_t max_rounds;
+    const double *order_score;  /* optional: initial order by class, descending score, fractionality, index */
+    const double *up_prob;      /* optional: P(up) for fractions strictly inside (0.25, 0.75) */
 } orc_fp_params;
 
 typedef struct {
@@ -96,7 +98,7 @@ double orc_uniform(uint64_t seed, uint64_t bulk, uint64_t var, uint64_t draw)
 static double clampd(double x, double l, double u) { return x < l ? l : (x > u ? u : x); }
 
 /* one draw from the rounding distribution of x (already inside the bounds) */
-static double draw_value(double x, uint64_t seed, uint64_t bulk, int32_t j, int d)
+static double draw_value(double x, uint64_t seed, uint64_t bulk, int32_t j, int d, const double *up_prob)
 {
     const double fl = floor(x);
     const double f = x - fl;
@@ -104,7 +106,7 @@ static double draw_value(double x, uint64_t seed, uint64_t bulk, int32_t j, int 
     double pup;
     if (f <= 0.25) pup = 0.0;
     else if (f >= 0.75) pup = 1.0;
-    else pup = (f - 0.25) / 0.5;
+    else pup = up_prob ? up_prob[j] : (f - 0.25) / 0.5;
     const double u = orc_uniform(seed, bulk, (uint64_t)j, (uint64_t)d);
     return u < pup ? fl + 1.0 : fl;
 }
@@ -122,11 +124,13 @@ typedef struct {
     const int32_t *cls;
     const double *frac;
     const double *S;
+    const double *score;
 } sort_ctx;
 
 static int cmp_initial(const sort_ctx *c, int32_t a, int32_t b)
 {
     if (c->cls[a] != c->cls[b]) return c->cls[a] < c->cls[b] ? -1 : 1;
+    if (c->score && c->score[a] != c->score[b]) return c->score[a] > c->score[b] ? -1 : 1;
     if (c->frac[a] != c->frac[b]) return c->frac[a] < c->frac[b] ? -1 : 1;
     return a < b ? -1 : (a > b ? 1 : 0);
 }
@@ -242,7 +246,7 @@ int orc_fix_and_propagate(const orc_problem *p, const double *x, const double *l
         frac[j] = f < 1.0 - f ? f : 1.0 - f;
         order[nint++] = j;
     }
-    sort_ctx ctx = {cls, frac, S};
+    sort_ctx ctx = {cls, frac, S, prm->order_score};
     merge_sort(order, tmp, nint, &ctx, cmp_initial);
 
     int rounding_infeasible = infeasible;
@@ -285,13 +289,13 @@ int orc_fix_and_propagate(const orc_problem *p, const double *x, const double *l
         for (int64_t i = 0; i < bsize; ++i) {
             const int32_t j = bulk[i];
             const double xh = clampd(x[j], l[j], u[j]);
-            const double v0 = clampd(draw_value(xh, prm->seed, bulk_index, j, 0), l[j], u[j]);
+            const double v0 = clampd(draw_value(xh, prm->seed, bulk_index, j, 0, prm->up_prob), l[j], u[j]);
             double v1;
             if (single) {
                 const double fl = floor(xh);
                 v1 = clampd(v0 == fl ? fl + 1.0 : fl, l[j], u[j]);
             } else {
-                v1 = clampd(draw_value(xh, prm->seed, bulk_index, j, 1), l[j], u[j]);
+                v1 = clampd(draw_value(xh, prm->seed, bulk_index, j, 1, prm->up_prob), l[j], u[j]);
             }
             val[0][j] = v0;
             val[1][j] = v1;

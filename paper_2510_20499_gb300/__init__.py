@@ -40,6 +40,26 @@ class ProbeCache(C.Structure):
                 ("ent_u", C.c_void_p), ("cap", C.c_int64), ("needed", C.c_int64)]
 
 
+class FpParams(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("bulk_rule", C.c_int32), ("last_single", C.c_int32),
+                ("fraction", C.c_double), ("theta", C.c_double), ("max_rounds", C.c_int32),
+                ("reserved", C.c_int32), ("order_score", C.c_void_p), ("up_prob", C.c_void_p)]
+
+
+class FpCache(C.Structure):
+    _fields_ = [("npairs", C.c_int32), ("reserved", C.c_int32), ("var", C.c_void_p), ("boxes", C.c_void_p),
+                ("status", C.c_void_p), ("offsets", C.c_void_p), ("ent_var", C.c_void_p),
+                ("ent_l", C.c_void_p), ("ent_u", C.c_void_p)]
+
+
+class FpResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("bulks", C.c_int32), ("bp_runs", C.c_int32), ("recoveries", C.c_int32),
+                ("fixed_by_choice", C.c_int32), ("reserved", C.c_int32), ("nnz_updates", C.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
 class GpuBpError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"gpubp error {code}: {msg}")
@@ -65,6 +85,9 @@ SIGNATURES = {
                                  C.POINTER(BpParams), C.POINTER(ProbeCache), C.c_void_p]),
     "bp_probe_priority": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.POINTER(C.c_int32), C.c_void_p]),
+    "fp_params_default": (None, [C.POINTER(FpParams)]),
+    "fix_and_propagate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(FpCache),
+                                    C.POINTER(FpParams), C.c_void_p, C.POINTER(FpResult), C.c_void_p]),
     "bp_last_error": (C.c_char_p, []),
     "bp_version": (C.c_char_p, []),
 }
@@ -236,6 +259,33 @@ def _probe_priority(prob, lb, ub, stream=None):
 
 
 Problem.probe_priority = _probe_priority
+
+
+def _fix_and_propagate(prob, x, lb, ub, seed=1, bulk_rule=0, fraction=0.01, last_single=36, theta=1e-3,
+                       max_rounds=10000, cache=None, order_score=None, up_prob=None, stream=None):
+    """fix_and_propagate on device tensors (x, lb, ub float64).  cache: the dict returned by
+    probe_batch plus 'pairs' (int32 device) and 'boxes' (float64 device, P x 4).
+    Returns (x_out device tensor, result dict)."""
+    torch = _torch()
+    prm = FpParams()
+    lib().fp_params_default(C.byref(prm))
+    prm.seed, prm.bulk_rule, prm.fraction, prm.last_single = int(seed), int(bulk_rule), float(fraction), int(last_single)
+    prm.theta, prm.max_rounds = float(theta), int(max_rounds)
+    prm.order_score = order_score.data_ptr() if order_score is not None else None
+    prm.up_prob = up_prob.data_ptr() if up_prob is not None else None
+    fc = None
+    if cache is not None:
+        fc = FpCache(int(cache["pairs"].numel()), 0, cache["pairs"].data_ptr(), cache["boxes"].data_ptr(),
+                     cache["status"].data_ptr(), cache["offsets"].data_ptr(), cache["var"].data_ptr(),
+                     cache["l"].data_ptr(), cache["u"].data_ptr())
+    out = torch.empty_like(x)
+    res = FpResult()
+    _check(lib().fix_and_propagate(prob.h, _ptr(x), _ptr(lb), _ptr(ub), C.byref(fc) if fc is not None else None,
+                                   C.byref(prm), _ptr(out), C.byref(res), _stream(stream)))
+    return out, res.as_dict()
+
+
+Problem.fix_and_propagate = _fix_and_propagate
 
 
 def probe_split(is_int, l, u):

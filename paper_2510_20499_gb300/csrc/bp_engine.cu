@@ -60,6 +60,8 @@ struct BpArgs {
     bp_result* dres;
     const int* w0;      // rows of round 0, or null for every row
     int w0_len;
+    const int* w0v;     // or: variables whose rows form round 0 (count in *w0v_len)
+    const int* w0v_len;
     double theta;
     int max_rounds;
     int base;           // stamp of round 0
@@ -526,7 +528,7 @@ __device__ void grid_barrier(Stage& st, Ctl* ctl, const DevProblem& P, const BpA
         __threadfence();
         st.flag = ld_acquire_s32(&ctl->stop) | (ld_acquire_s32(&ctl->error) != 0);
         const int par = next & 1;
-        const bool stat = (next == 0 && !A.w0);
+        const bool stat = (next == 0 && !A.w0 && !A.w0v);
 #pragma unroll
         for (int c = 0; c < kNumClass; ++c)
             st.d_cnt[c] = stat ? P.class_off[c + 1] - P.class_off[c] : __ldcg(&ctl->cnt[par][c].v);
@@ -592,10 +594,25 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
             warp_queue_rows(st, A, P, q, i < A.w0_len ? __ldg(A.w0 + i) : -1);
         }
         warp_flush_all(st, A, P, q);
+    } else if (A.w0v) {
+        // queue the rows of the given variables (one warp per variable)
+        Phase q = ph0;
+        q.npar = 0;
+        const int gw0 = gtid >> 5, nw0 = gthreads >> 5;
+        const int nv = *A.w0v_len;
+        for (int b = gw0; b < nv; b += nw0) {
+            const int u = __ldg(A.w0v + b);
+            const int cb = __ldg(P.col_ptr + u), ce = __ldg(P.col_ptr + u + 1);
+            for (int s0 = cb; s0 < ce; s0 += 32) {
+                const int sidx = s0 + lane;
+                warp_queue_rows(st, A, P, q, sidx < ce ? __ldg(P.row_idx + sidx) : -1);
+            }
+        }
+        warp_flush_all(st, A, P, q);
     }
     grid_barrier(st, ctl, P, A, 0, [&] {
         int rows0 = 0;
-        if (A.w0) {
+        if (A.w0 || A.w0v) {
             for (int c = 0; c < kNumClass; ++c) rows0 += ctl->cnt[0][c].v;
         } else {
             rows0 = P.m;
@@ -624,7 +641,7 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
         ph.X = A.bk[ph.npar];
         ph.st_v = A.base + t;
         ph.st_r = A.base + t + 1;
-        const bool stat = (t == 0 && !A.w0);
+        const bool stat = (t == 0 && !A.w0 && !A.w0v);
         const int* rows = stat ? P.static_list : A.list[ph.par];
         const int2* tasks = stat ? P.static_tasks : A.task[ph.par];
         const int ntask = st.d_ntask;
@@ -693,7 +710,7 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
             for (int c = 0; c < kNumClass; ++c) nw += ctl->cnt[npar][c].v;
             if (A.trace && t < A.max_rounds) {
                 int rows_t = 0;
-                if (t == 0 && !A.w0) {
+                if (t == 0 && !A.w0 && !A.w0v) {
                     rows_t = P.m;
                 } else {
                     for (int c = 0; c < kNumClass; ++c) rows_t += ctl->cnt[par][c].v;
@@ -824,7 +841,7 @@ int engine_prepare(mip_problem* p) {
 }
 
 int launch_propagate(mip_problem* p, double* lb, double* ub, const int* w0, int w0_len, double theta,
-                     int max_rounds, int64_t* trace, cudaStream_t s) {
+                     int max_rounds, int64_t* trace, cudaStream_t s, const int* w0v, const int* w0v_len) {
     Work& w = p->w;
     const long long span = (long long)(max_rounds > 0 ? max_rounds : 0) + 3;
     if (w.stamp_base + span >= (long long)INT_MAX - 16) {
@@ -857,6 +874,8 @@ int launch_propagate(mip_problem* p, double* lb, double* ub, const int* w0, int 
     a.dres = w.dres;
     a.w0 = w0;
     a.w0_len = w0_len;
+    a.w0v = w0v;
+    a.w0v_len = w0v_len;
     a.theta = theta;
     a.max_rounds = max_rounds;
     a.base = (int)w.stamp_base;

@@ -119,8 +119,11 @@ int root_keys(mip_problem* p, const double* lb, const double* ub, longlong2* out
 // stable LSD radix sort of (key, value) pairs on bits [begin_bit, end_bit)
 int radix_sort_pairs(unsigned long long* keys, int* vals, unsigned long long* tmp_keys, int* tmp_vals, int n,
                      int begin_bit, int end_bit, cudaStream_t s);
+// one propagation on device bounds lb/ub (modified in place); round 0 holds every row, or the
+// rows w0[0..w0_len), or the rows of the variables w0v[0..*w0v_len) (count read on the device)
 int launch_propagate(mip_problem* p, double* lb, double* ub, const int* w0, int w0_len,
-                     double theta, int max_rounds, int64_t* trace, cudaStream_t s);
+                     double theta, int max_rounds, int64_t* trace, cudaStream_t s,
+                     const int* w0v = nullptr, const int* w0v_len = nullptr);
 
 }  // namespace gpubp
 

@@ -1,0 +1,528 @@
+// Bulk fix-and-propagate rounding (Section 2.3, Algorithm 1): fix_and_propagate.
+//
+// The loop itself is sequential (every bulk depends on the previous result), so the host
+// drives it and reads a few words per bulk for its control decisions; every step on the data
+// runs in kernels: the list of unfixed variables, the implied-slack sums and the stable radix
+// sorts, the counter-based draws, the probing-cache conflict filter, the start boxes of the
+// two candidate vectors, their propagations (the persistent engine, round 0 = rows of the
+// variables the vector changes) and the final rounding.
+//
+// Random draws: splitmix64 (Steele, Lea, Flood, OOPSLA 2014) chained over (seed, bulk,
+// variable, draw); the 53 high bits give a uniform double in [0, 1).
+#include <climits>
+#include <cmath>
+#include <type_traits>
+#include <vector>
+
+#include "bp_host.h"
+
+namespace gpubp {
+
+__device__ __forceinline__ unsigned long long sm64(unsigned long long z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double uniform01(unsigned long long seed, unsigned long long bulk, unsigned long long var,
+                                            unsigned long long draw) {
+    unsigned long long h = sm64(seed);
+    h = sm64(h ^ bulk);
+    h = sm64(h ^ var);
+    h = sm64(h ^ draw);
+    return __dmul_rn(__ull2double_rn(h >> 11), 1.0 / 9007199254740992.0);
+}
+
+__device__ __forceinline__ double clampd(double x, double l, double u) { return x < l ? l : (x > u ? u : x); }
+
+__device__ __forceinline__ double draw_value(double x, unsigned long long seed, unsigned long long bulk, int j, int d,
+                                             const double* up_prob) {
+    const double fl = floor(x);
+    const double f = __dsub_rn(x, fl);
+    if (f == 0.0) return x;
+    double pup;
+    if (f <= 0.25) pup = 0.0;
+    else if (f >= 0.75) pup = 1.0;
+    else pup = up_prob ? up_prob[j] : __ddiv_rn(__dsub_rn(f, 0.25), 0.5);
+    return uniform01(seed, bulk, (unsigned long long)j, (unsigned long long)d) < pup ? __dadd_rn(fl, 1.0) : fl;
+}
+
+// radix key of a double, ascending (descending when desc)
+__device__ __forceinline__ unsigned long long fp_sort_key(double d, bool desc) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(d == 0.0 ? 0.0 : d);
+    b = (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+    return desc ? ~b : b;
+}
+
+__global__ void k_intvars_flag(int n, const unsigned char* is_int, int* flag) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) flag[j] = is_int[j] ? 1 : 0;
+}
+
+__global__ void k_compact_idx(int n, const int* flag, const int* pos, int* out) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        if (flag[j]) out[pos[j]] = j;
+}
+
+// initial order keys: pass 0 fractionality (ascending), pass 1 score (descending), pass 2 class
+__global__ void k_initial_keys(int nint, const int* vars, const double* x, const double* l, const double* u,
+                               const double* score, int which, unsigned long long* keys) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nint; i += gridDim.x * blockDim.x) {
+        const int j = vars[i];
+        if (which == 0) {
+            const double xh = clampd(x[j], l[j], u[j]);
+            const double f = __dsub_rn(xh, floor(xh));
+            const double g = __dsub_rn(1.0, f);
+            keys[i] = fp_sort_key(f < g ? f : g, false);
+        } else if (which == 1) {
+            keys[i] = fp_sort_key(score[j], true);
+        } else {
+            const double w = __dsub_rn(u[j], l[j]);
+            keys[i] = w <= 1.0 ? 0ull : (w == 2.0 ? 1ull : 2ull);
+        }
+    }
+}
+
+__global__ void k_unset_flag(int nint, const int* order, const double* l, const double* u, int* flag) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nint; i += gridDim.x * blockDim.x) {
+        const int j = order[i];
+        flag[i] = l[j] < u[j] ? 1 : 0;
+    }
+}
+
+__global__ void k_compact_list(int nint, const int* order, const int* flag, const int* pos, int* out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nint; i += gridDim.x * blockDim.x)
+        if (flag[i]) out[pos[i]] = order[i];
+}
+
+// row minimal activities (finite part, count of infinite terms) under bounds (l, u)
+__global__ void k_row_act(DevProblem P, const double* l, const double* u, double* minfin, int* ninf) {
+    const int lane = threadIdx.x & 31;
+    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < P.m; k += (gridDim.x * blockDim.x) >> 5) {
+        double s = 0.0;
+        int c = 0;
+        for (int q = P.row_ptr[k] + lane; q < P.row_ptr[k + 1]; q += 32) {
+            const double a = P.val[q];
+            const double b = a > 0 ? l[P.col[q]] : u[P.col[q]];
+            if (isinf(b)) ++c;
+            else s = fma(a, b, s);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            s = __dadd_rn(s, __shfl_xor_sync(0xffffffffu, s, o));
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+        }
+        if (lane == 0) {
+            minfin[k] = s;
+            ninf[k] = c;
+        }
+    }
+}
+
+// implied slack S_i = sum over the variable's rows (ascending, as the transpose stores them)
+// with a finite minimal activity of (a / max(g - L_min, tol))^2; keys descending
+__global__ void k_implied_slack(DevProblem P, int cnt, const int* vars, const double* minfin, const int* ninf,
+                                unsigned long long* keys) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+        const int j = vars[i];
+        double S = 0.0;
+        for (int s = P.col_ptr[j]; s < P.col_ptr[j + 1]; ++s) {
+            const int k = P.row_idx[s];
+            const double g = P.grow[k].x;
+            if (isinf(g) || ninf[k]) continue;
+            double slack = __dsub_rn(g, minfin[k]);
+            if (slack < kTol) slack = kTol;
+            const double sv = __ddiv_rn(P.col_val[s], slack);
+            S = __dadd_rn(S, __dmul_rn(sv, sv));
+        }
+        keys[i] = fp_sort_key(S, true);
+    }
+}
+
+__global__ void k_draws(int bsize, const int* bulk, const double* x, const double* l, const double* u,
+                        unsigned long long seed, unsigned long long bulk_index, int single, const double* up_prob,
+                        double* v0, double* v1) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < bsize; i += gridDim.x * blockDim.x) {
+        const int j = bulk[i];
+        const double xh = clampd(x[j], l[j], u[j]);
+        const double a = clampd(draw_value(xh, seed, bulk_index, j, 0, up_prob), l[j], u[j]);
+        double b;
+        if (single) {
+            const double fl = floor(xh);
+            b = clampd(a == fl ? __dadd_rn(fl, 1.0) : fl, l[j], u[j]);
+        } else {
+            b = clampd(draw_value(xh, seed, bulk_index, j, 1, up_prob), l[j], u[j]);
+        }
+        v0[i] = a;
+        v1[i] = b;
+    }
+}
+
+__global__ void k_apply_plain(int bsize, const int* bulk, const double* v, double* cl, double* cu, int* kept) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < bsize; i += gridDim.x * blockDim.x) {
+        const int j = bulk[i];
+        cl[j] = v[i];
+        cu[j] = v[i];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *kept = bsize;
+}
+
+__device__ __forceinline__ bool var_crossed(bool is_i, double l, double u) {
+    return is_i ? l > u : l > __dadd_rn(u, kTol);
+}
+
+// probing-cache conflict filter and warm start: one warp, the bulk in order; a fixing is kept
+// if its value lies in the current box and its branch (when cached) is feasible and agrees
+// with every bound implied so far; then the branch's implied bounds tighten the box
+__global__ void k_apply_cache(int bsize, const int* bulk, const double* v, double* cl, double* cu,
+                              const unsigned char* is_int, const int* pair_of, fp_cache c, int* kept) {
+    const int lane = threadIdx.x;
+    int nk = 0;
+    for (int i = 0; i < bsize; ++i) {
+        const int j = bulk[i];
+        const double val = v[i];
+        __syncwarp();
+        if (!(val >= cl[j] && val <= cu[j])) continue;
+        const int pi = pair_of[j];
+        long long e = -1;
+        if (pi >= 0) {
+            for (int b = 0; b < 2; ++b) {
+                const double lo = c.boxes[4 * pi + 2 * b], hi = c.boxes[4 * pi + 2 * b + 1];
+                if (val >= lo && val <= hi) {
+                    e = 2ll * pi + b;
+                    break;
+                }
+            }
+        }
+        bool ok = true;
+        if (e >= 0) {
+            if (c.status[e] == BP_INFEASIBLE) ok = false;
+            bool bad = false;
+            if (ok) {
+                for (long long q = c.offsets[e] + lane; q < c.offsets[e + 1]; q += 32) {
+                    const int w = c.ent_var[q];
+                    const double lo = c.ent_l[q] > cl[w] ? c.ent_l[q] : cl[w];
+                    const double hi = c.ent_u[q] < cu[w] ? c.ent_u[q] : cu[w];
+                    if (w == j ? !(val >= lo && val <= hi) : var_crossed(is_int[w] != 0, lo, hi)) bad = true;
+                }
+            }
+            if (__any_sync(0xffffffffu, bad)) ok = false;
+        }
+        if (!ok) continue;
+        ++nk;
+        __syncwarp();
+        if (lane == 0) {
+            cl[j] = val;
+            cu[j] = val;
+        }
+        __syncwarp();
+        if (e >= 0) {
+            for (long long q = c.offsets[e] + lane; q < c.offsets[e + 1]; q += 32) {
+                const int w = c.ent_var[q];
+                if (w == j) continue;
+                if (c.ent_l[q] > cl[w]) cl[w] = c.ent_l[q];
+                if (c.ent_u[q] < cu[w]) cu[w] = c.ent_u[q];
+            }
+        }
+    }
+    if (lane == 0) *kept = nk;
+}
+
+// variables whose start box differs from the current bounds (round 0 of the propagation)
+__global__ void k_diff(int n, const double* cl, const double* cu, const double* l, const double* u, int* list,
+                       int* count) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        if (cl[j] != l[j] || cu[j] != u[j]) list[atomicAdd(count, 1)] = j;
+}
+
+__global__ void k_pair_of(int npairs, const int* var, int* pair_of) {
+    // first pair of each variable wins
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npairs; i += gridDim.x * blockDim.x)
+        atomicMin(&pair_of[var[i]], i);
+}
+
+__global__ void k_pair_of_clear(int n, int* pair_of) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        pair_of[j] = pair_of[j] == INT_MAX ? -1 : pair_of[j];
+}
+
+__global__ void k_fill_int(int n, int* a, int v) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) a[j] = v;
+}
+
+__global__ void k_finalize(int n, const unsigned char* is_int, const double* x, const double* l, const double* u,
+                           int rounding_infeasible, double* x_out) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        if (is_int[j]) {
+            double v = l[j];
+            if (l[j] < u[j]) v = clampd(floor(__dadd_rn(clampd(x[j], l[j], u[j]), 0.5)), l[j], u[j]);
+            x_out[j] = v;
+        } else {
+            x_out[j] = clampd(x[j], l[j], u[j]);
+        }
+    }
+}
+
+static int gridn(long long work) {
+    long long b = (work + 255) / 256;
+    return (int)(b < 1 ? 1 : (b > 1216 ? 1216 : b));
+}
+
+// per-bulk control words read back by the host
+struct FpCtl {
+    int nun;
+    int kept[2];
+    int pad;
+    bp_result res[2];
+};
+
+}  // namespace gpubp
+
+using namespace gpubp;
+
+extern "C" void fp_params_default(fp_params* p) {
+    if (!p) return;
+    p->seed = 1;
+    p->bulk_rule = FP_BULK_SQRT;
+    p->last_single = 36;
+    p->fraction = 0.01;
+    p->theta = 1e-3;
+    p->max_rounds = 10000;
+    p->reserved = 0;
+    p->order_score = nullptr;
+    p->up_prob = nullptr;
+}
+
+extern "C" int fix_and_propagate(mip_problem* p, const double* x, const double* lb, const double* ub,
+                                 const fp_cache* cache, const fp_params* params, double* x_out, fp_result* result,
+                                 void* stream) {
+    if (!p || !result || (p->n && (!x || !lb || !ub || !x_out))) {
+        set_error("fix_and_propagate: null argument");
+        return BP_ERR_INVALID;
+    }
+    fp_params prm;
+    if (params) prm = *params;
+    else fp_params_default(&prm);
+    if (!(prm.theta >= 0.0) || prm.max_rounds < 0 || prm.last_single < 0 ||
+        (prm.bulk_rule != FP_BULK_SQRT && prm.bulk_rule != FP_BULK_FRACTION) ||
+        (prm.bulk_rule == FP_BULK_FRACTION && !(prm.fraction > 0.0))) {
+        set_error("fix_and_propagate: invalid parameters");
+        return BP_ERR_INVALID;
+    }
+    if (cache && cache->npairs > 0 &&
+        (!cache->var || !cache->boxes || !cache->status || !cache->offsets)) {
+        set_error("fix_and_propagate: incomplete cache");
+        return BP_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = p->n;
+    memset(result, 0, sizeof(*result));
+    // scratch (stream-ordered allocations, freed at the end)
+    std::vector<void*> tmp;
+    auto alloc = [&](auto** ptr, size_t count) -> int {
+        void* q = nullptr;
+        cudaError_t e = cudaMallocAsync(&q, (count ? count : 1) * sizeof(**ptr), s);
+        if (e != cudaSuccess) return fail_cuda(e, "cudaMallocAsync");
+        tmp.push_back(q);
+        *ptr = static_cast<std::remove_reference_t<decltype(*ptr)>>(q);
+        return BP_OK;
+    };
+    auto release = [&]() {
+        for (void* q : tmp) cudaFreeAsync(q, s);
+        tmp.clear();
+    };
+    int rc = BP_OK;
+    double *Bl, *Bu, *cl[2], *cu[2], *v[2], *rmin;
+    int *flag, *pos, *ivars, *order, *work, *twork, *rninf, *dlist[2], *dcnt, *pair_of = nullptr, *total;
+    unsigned long long *keys, *tkeys;
+    FpCtl* dctl;
+    FpCtl* hctl = nullptr;
+#define FP_ALLOC(ptr, cnt)                      \
+    do {                                        \
+        rc = alloc(&ptr, (size_t)(cnt));        \
+        if (rc != BP_OK) { release(); return rc; } \
+    } while (0)
+    FP_ALLOC(Bl, n);
+    FP_ALLOC(Bu, n);
+    for (int c = 0; c < 2; ++c) {
+        FP_ALLOC(cl[c], n);
+        FP_ALLOC(cu[c], n);
+        FP_ALLOC(v[c], n);
+        FP_ALLOC(dlist[c], n);
+    }
+    FP_ALLOC(rmin, p->m);
+    FP_ALLOC(rninf, p->m);
+    FP_ALLOC(flag, n);
+    FP_ALLOC(pos, n);
+    FP_ALLOC(ivars, n);
+    FP_ALLOC(order, n);
+    FP_ALLOC(work, n);
+    FP_ALLOC(twork, n);
+    FP_ALLOC(keys, n);
+    FP_ALLOC(tkeys, n);
+    FP_ALLOC(dcnt, 2);
+    FP_ALLOC(total, 1);
+    FP_ALLOC(dctl, 1);
+    if (cudaMallocHost(&hctl, sizeof(FpCtl)) != cudaSuccess) {
+        release();
+        set_error("pinned host allocation failed");
+        return BP_ERR_OOM;
+    }
+    auto fail = [&](int code) {
+        release();
+        cudaFreeHost(hctl);
+        return code;
+    };
+#define FP_TRY(expr)                      \
+    do {                                  \
+        int _r = (expr);                  \
+        if (_r != BP_OK) return fail(_r); \
+    } while (0)
+#define FP_CUDA(expr)                                        \
+    do {                                                     \
+        cudaError_t _e = (expr);                             \
+        if (_e != cudaSuccess) return fail(fail_cuda(_e, #expr)); \
+    } while (0)
+    const bool use_cache = cache && cache->npairs > 0;
+    if (use_cache) {
+        FP_ALLOC(pair_of, n);
+        k_fill_int<<<gridn(n), 256, 0, s>>>(n, pair_of, INT_MAX);
+        k_pair_of<<<gridn(cache->npairs), 256, 0, s>>>(cache->npairs, cache->var, pair_of);
+        k_pair_of_clear<<<gridn(n), 256, 0, s>>>(n, pair_of);
+    }
+    // ---- propagate the start bounds
+    FP_CUDA(cudaMemcpyAsync(Bl, lb, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    FP_CUDA(cudaMemcpyAsync(Bu, ub, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    FP_TRY(launch_propagate(p, Bl, Bu, nullptr, 0, prm.theta, prm.max_rounds, nullptr, s));
+    FP_CUDA(cudaMemcpyAsync(hctl->res, p->w.dres, sizeof(bp_result), cudaMemcpyDeviceToHost, s));
+    // integer variables and their initial order
+    k_intvars_flag<<<gridn(n), 256, 0, s>>>(n, p->dp.is_int, flag);
+    FP_TRY(scan_exclusive(flag, pos, n, total, s));
+    k_compact_idx<<<gridn(n), 256, 0, s>>>(n, flag, pos, ivars);
+    int nint = 0;
+    FP_CUDA(cudaMemcpyAsync(&nint, total, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FP_CUDA(cudaStreamSynchronize(s));
+    if (hctl->res[0].error) return fail(BP_ERR_TIMEOUT);
+    result->bp_runs = 1;
+    result->nnz_updates = hctl->res[0].nnz_updates;
+    bool rounding_infeasible = hctl->res[0].status == BP_INFEASIBLE;
+    FP_CUDA(cudaMemcpyAsync(order, ivars, sizeof(int) * nint, cudaMemcpyDeviceToDevice, s));
+    {
+        const int passes[3] = {0, 1, 2};
+        for (int which : passes) {
+            if (which == 1 && !prm.order_score) continue;
+            if (nint == 0) break;
+            k_initial_keys<<<gridn(nint), 256, 0, s>>>(nint, order, x, Bl, Bu, prm.order_score, which, keys);
+            FP_TRY(radix_sort_pairs(keys, order, tkeys, twork, nint, 0, which == 2 ? 8 : 64, s));
+        }
+    }
+    std::vector<int> recq;
+    size_t rec_pos = 0;
+    unsigned long long bulk_index = 0;
+    while (!rounding_infeasible) {
+        // unfixed integer variables in the initial order
+        int nun = 0;
+        if (nint) {
+            k_unset_flag<<<gridn(nint), 256, 0, s>>>(nint, order, Bl, Bu, flag);
+            FP_TRY(scan_exclusive(flag, pos, nint, total, s));
+            k_compact_list<<<gridn(nint), 256, 0, s>>>(nint, order, flag, pos, work);
+            FP_CUDA(cudaMemcpyAsync(&nun, total, sizeof(int), cudaMemcpyDeviceToHost, s));
+            FP_CUDA(cudaStreamSynchronize(s));
+        }
+        if (nun == 0) break;
+        long long bsize = 1;
+        bool single = false;
+        const int* bulk = work;
+        // recovery: the failed bulk's variables one at a time, skipping those fixed meanwhile
+        while (rec_pos < recq.size()) {
+            double lu[2];
+            FP_CUDA(cudaMemcpyAsync(&lu[0], Bl + recq[rec_pos], sizeof(double), cudaMemcpyDeviceToHost, s));
+            FP_CUDA(cudaMemcpyAsync(&lu[1], Bu + recq[rec_pos], sizeof(double), cudaMemcpyDeviceToHost, s));
+            FP_CUDA(cudaStreamSynchronize(s));
+            if (lu[0] < lu[1]) break;
+            ++rec_pos;
+        }
+        if (rec_pos < recq.size()) {
+            const int j = recq[rec_pos++];
+            FP_CUDA(cudaMemcpyAsync(twork, &j, sizeof(int), cudaMemcpyHostToDevice, s));
+            bulk = twork;
+            bsize = 1;
+            single = true;
+        } else {
+            recq.clear();
+            rec_pos = 0;
+            if (nun <= prm.last_single) {
+                bsize = 1;
+            } else if (prm.bulk_rule == FP_BULK_SQRT) {
+                long long r = (long long)std::sqrt((double)nun);
+                while (r * r > nun) --r;
+                while ((r + 1) * (r + 1) <= nun) ++r;
+                bsize = r * r == nun ? r : r + 1;
+            } else {
+                bsize = (long long)std::ceil(prm.fraction * (double)nint);
+                if (bsize < 1) bsize = 1;
+            }
+            if (bsize > nun) bsize = nun;
+            if (bsize > 1) {
+                if (p->m) k_row_act<<<gridn((long long)p->m * 32), 256, 0, s>>>(p->dp, Bl, Bu, rmin, rninf);
+                k_implied_slack<<<gridn(nun), 256, 0, s>>>(p->dp, nun, work, rmin, rninf, keys);
+                FP_TRY(radix_sort_pairs(keys, work, tkeys, twork, nun, 0, 64, s));
+            }
+            single = bsize == 1;
+        }
+        // candidate values and start boxes of the two vectors
+        k_draws<<<gridn(bsize), 256, 0, s>>>((int)bsize, bulk, x, Bl, Bu, prm.seed, bulk_index, single ? 1 : 0,
+                                               prm.up_prob, v[0], v[1]);
+        FP_CUDA(cudaMemsetAsync(dcnt, 0, 2 * sizeof(int), s));
+        for (int c = 0; c < 2; ++c) {
+            FP_CUDA(cudaMemcpyAsync(cl[c], Bl, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+            FP_CUDA(cudaMemcpyAsync(cu[c], Bu, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+            if (use_cache) {
+                k_apply_cache<<<1, 32, 0, s>>>((int)bsize, bulk, v[c], cl[c], cu[c], p->dp.is_int, pair_of, *cache,
+                                               &dctl->kept[c]);
+            } else {
+                k_apply_plain<<<gridn(bsize), 256, 0, s>>>((int)bsize, bulk, v[c], cl[c], cu[c], &dctl->kept[c]);
+            }
+            k_diff<<<gridn(n), 256, 0, s>>>(n, cl[c], cu[c], Bl, Bu, dlist[c], dcnt + c);
+            FP_CUDA(cudaGetLastError());
+            // double propagation: each vector from the rows of the variables it changes
+            FP_TRY(launch_propagate(p, cl[c], cu[c], nullptr, 0, prm.theta, prm.max_rounds, nullptr, s, dlist[c],
+                                    dcnt + c));
+            FP_CUDA(cudaMemcpyAsync(&dctl->res[c], p->w.dres, sizeof(bp_result), cudaMemcpyDeviceToDevice, s));
+        }
+        FP_CUDA(cudaMemcpyAsync(hctl, dctl, sizeof(FpCtl), cudaMemcpyDeviceToHost, s));
+        FP_CUDA(cudaStreamSynchronize(s));
+        bool feas[2];
+        for (int c = 0; c < 2; ++c) {
+            if (hctl->res[c].error) return fail(BP_ERR_TIMEOUT);
+            if (hctl->kept[c] > 0) {
+                result->bp_runs++;
+                result->nnz_updates += hctl->res[c].nnz_updates;
+            }
+            feas[c] = hctl->kept[c] > 0 && hctl->res[c].status != BP_INFEASIBLE;
+        }
+        result->bulks++;
+        bulk_index++;
+        const int pick = feas[0] ? 0 : (feas[1] ? 1 : -1);
+        if (pick >= 0) {
+            result->fixed_by_choice += hctl->kept[pick];
+            std::swap(Bl, cl[pick]);
+            std::swap(Bu, cu[pick]);
+        } else if (!single) {
+            recq.resize((size_t)bsize);
+            FP_CUDA(cudaMemcpyAsync(recq.data(), bulk, sizeof(int) * bsize, cudaMemcpyDeviceToHost, s));
+            FP_CUDA(cudaStreamSynchronize(s));
+            rec_pos = 0;
+            result->recoveries++;
+        } else {
+            rounding_infeasible = true;
+        }
+    }
+    k_finalize<<<gridn(n), 256, 0, s>>>(n, p->dp.is_int, x, Bl, Bu, rounding_infeasible ? 1 : 0, x_out);
+    FP_CUDA(cudaGetLastError());
+    result->status = rounding_infeasible ? FP_INFEASIBLE : FP_FEASIBLE;
+    release();
+    FP_CUDA(cudaStreamSynchronize(s));
+    cudaFreeHost(hctl);
+    p->last_stream = s;
+    return BP_OK;
+}

@@ -171,17 +171,26 @@ __global__ void k_col_count(long long nnz, const int32_t* col, int* cnt) {
         atomicAdd(&cnt[col[q]], 1);
 }
 
-__global__ void k_col_scatter(int m, const int* rp, const int32_t* col, const double* val, const int* col_ptr,
-                              int* fill, int* row_idx, double* col_val) {
-    // one warp per row
-    int lane = threadIdx.x & 31;
-    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < m; k += (gridDim.x * blockDim.x) >> 5) {
-        for (int q = rp[k] + lane; q < rp[k + 1]; q += 32) {
-            int j = col[q];
-            int pos = atomicAdd(&fill[j], 1);
-            row_idx[col_ptr[j] + pos] = k;
-            col_val[col_ptr[j] + pos] = val[q];
-        }
+// transpose in a deterministic order: every column lists its rows ascending
+__global__ void k_row_of(int m, const int* rp, int* row_of) {
+    const int lane = threadIdx.x & 31;
+    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < m; k += (gridDim.x * blockDim.x) >> 5)
+        for (int q = rp[k] + lane; q < rp[k + 1]; q += 32) row_of[q] = k;
+}
+
+__global__ void k_col_keys(long long nnz, const int32_t* col, unsigned long long* keys, int* pos) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nnz; q += (long long)gridDim.x * blockDim.x) {
+        keys[q] = (unsigned long long)col[q];
+        pos[q] = (int)q;
+    }
+}
+
+__global__ void k_col_fill(long long nnz, const int* pos, const int* row_of, const double* val, int* row_idx,
+                           double* col_val) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nnz; i += (long long)gridDim.x * blockDim.x) {
+        const int q = pos[i];
+        row_idx[i] = row_of[q];
+        col_val[i] = val[q];
     }
 }
 
@@ -365,7 +374,23 @@ static int load_impl(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t
     BP_TRY(dalloc(p, &d_rowidx, (size_t)nnz));
     if (nnz) k_col_count<<<grid_for(nnz), 256, 0, s>>>(nnz, d_col, d_colcnt);
     BP_TRY(scan_exclusive(d_colcnt, d_colptr, n + 1, nullptr, s));
-    if (nnz) k_col_scatter<<<grid_for((long long)m * 32), 256, 0, s>>>(m, d_rp, d_col, d_val, d_colptr, d_fill, d_rowidx, d_colval);
+    if (nnz) {
+        int *row_of = nullptr, *pos = nullptr, *tpos = nullptr;
+        unsigned long long *keys = nullptr, *tkeys = nullptr;
+        BP_CUDA_TRY(cudaMallocAsync(&row_of, sizeof(int) * nnz, s));
+        BP_CUDA_TRY(cudaMallocAsync(&pos, sizeof(int) * nnz, s));
+        BP_CUDA_TRY(cudaMallocAsync(&tpos, sizeof(int) * nnz, s));
+        BP_CUDA_TRY(cudaMallocAsync(&keys, sizeof(unsigned long long) * nnz, s));
+        BP_CUDA_TRY(cudaMallocAsync(&tkeys, sizeof(unsigned long long) * nnz, s));
+        k_row_of<<<grid_for((long long)m * 32), 256, 0, s>>>(m, d_rp, row_of);
+        k_col_keys<<<grid_for(nnz), 256, 0, s>>>(nnz, d_col, keys, pos);
+        int bits = 8;
+        while (bits < 32 && (1ll << bits) < (long long)n) bits += 8;
+        BP_TRY(radix_sort_pairs(keys, pos, tkeys, tpos, (int)nnz, 0, bits, s));
+        k_col_fill<<<grid_for(nnz), 256, 0, s>>>(nnz, pos, row_of, d_val, d_rowidx, d_colval);
+        BP_CUDA_TRY(cudaGetLastError());
+        for (void* q : {(void*)row_of, (void*)pos, (void*)tpos, (void*)keys, (void*)tkeys}) BP_CUDA_TRY(cudaFreeAsync(q, s));
+    }
     // bounds and types
     unsigned char* d_isint;
     BP_TRY(dalloc(p, &d_isint, (size_t)n));

@@ -129,3 +129,24 @@ def test_deterministic_per_seed():
     b = oracle.Problem(p).fix_and_propagate(x0, p.lb, p.ub, seed=5)
     np.testing.assert_array_equal(a[0], b[0])
     assert a[1] == b[1]
+
+
+def test_up_prob_hook_only_inside_band():
+    n = 400
+    p = milp_from_dense(np.zeros((0, n)), [], np.zeros(n), np.full(n, 5.0), np.ones(n))
+    x = np.where(np.arange(n) % 2 == 0, 2.5, 2.1)          # in band / below band
+    for pu, want in ((1.0, 3.0), (0.0, 2.0)):
+        out, r = oracle.Problem(p).fix_and_propagate(x, p.lb, p.ub, seed=3, last_single=0, up_prob=np.full(n, pu))
+        assert (out[0::2] == want).all()                   # f = 0.5: the hook decides
+        assert (out[1::2] == 2.0).all()                    # f = 0.1: nearest, hook ignored
+
+
+def test_order_score_hook():
+    """Two binaries with equal fractionality and y + z <= 1: the first fixed wins.  Without a
+    score the lower index goes first; a higher score for z puts z first."""
+    p = milp_from_dense(np.array([[1.0, 1.0]]), [1.0], np.zeros(2), np.ones(2), np.ones(2))
+    x = np.array([0.8, 0.8])
+    out, _ = oracle.Problem(p).fix_and_propagate(x, p.lb, p.ub)
+    np.testing.assert_array_equal(out, [1.0, 0.0])
+    out, _ = oracle.Problem(p).fix_and_propagate(x, p.lb, p.ub, order_score=np.array([0.0, 1.0]))
+    np.testing.assert_array_equal(out, [0.0, 1.0])
