@@ -148,6 +148,34 @@ int bp_propagate(mip_problem *p, double *lb, double *ub, const bp_params *params
 /* Device address of the handle's result slot written by the last bp_propagate. */
 const bp_result *bp_result_device(const mip_problem *p);
 
+/* ------------------------------------------------------- batches of instances */
+
+/*
+ * mip_set_instances -- declare the loaded problem a batch of independent instances laid out
+ * block-diagonally: instance i owns rows [row_off[i], row_off[i+1]) and variables
+ * [col_off[i], col_off[i+1]), and no row has a nonzero outside its instance's variables.
+ * row_off, col_off: int32[ninst+1] in host or device memory (mem_kind), row_off[0] = 0,
+ * row_off[ninst] = m, col_off[0] = 0, col_off[ninst] = n, nondecreasing; 1 <= ninst <= 1024.
+ * The layout is validated on the device and kept on the handle.  Synchronises the stream.
+ * Returns BP_OK or BP_ERR_INVALID.
+ */
+int mip_set_instances(mip_problem *p, int32_t ninst, const int32_t *row_off, const int32_t *col_off,
+                      int32_t mem_kind, void *stream);
+
+/*
+ * bp_propagate_batch -- bound propagation of every instance of the batch in one persistent
+ * launch (the batched form; Section 2.1 per instance).  Each instance is propagated exactly
+ * as bp_propagate would propagate it alone (its own status, round count, work count and
+ * first infeasible indices); an infeasible instance stops without stopping the others.
+ * lb, ub:   DEVICE double[n], in/out, as for bp_propagate.
+ * results:  DEVICE bp_result[ninst]; first infeasible row / variable are indices of the whole
+ *           (concatenated) problem.  No host synchronisation: the call can be captured in a
+ *           CUDA graph.
+ * Returns BP_OK, BP_ERR_INVALID (no batch declared) or BP_ERR_CUDA.
+ */
+int bp_propagate_batch(mip_problem *p, double *lb, double *ub, const bp_params *params,
+                       bp_result *results, void *stream);
+
 /* -------------------------------------------------------------------- probing */
 
 /*

@@ -88,6 +88,9 @@ SIGNATURES = {
     "fp_params_default": (None, [C.POINTER(FpParams)]),
     "fix_and_propagate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(FpCache),
                                     C.POINTER(FpParams), C.c_void_p, C.POINTER(FpResult), C.c_void_p]),
+    "mip_set_instances": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "bp_propagate_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(BpParams), C.c_void_p,
+                                     C.c_void_p]),
     "bp_last_error": (C.c_char_p, []),
     "bp_version": (C.c_char_p, []),
 }
@@ -286,6 +289,44 @@ def _fix_and_propagate(prob, x, lb, ub, seed=1, bulk_rule=0, fraction=0.01, last
 
 
 Problem.fix_and_propagate = _fix_and_propagate
+
+RESULT_FIELDS = [f for f, _ in BpResult._fields_ if f != "reserved"]
+
+
+def _set_instances(prob, row_off, col_off, stream=None):
+    """mip_set_instances with host offsets (numpy int32, length ninst+1)."""
+    ro = np.ascontiguousarray(row_off, dtype=np.int32)
+    co = np.ascontiguousarray(col_off, dtype=np.int32)
+    _check(lib().mip_set_instances(prob.h, len(ro) - 1, C.c_void_p(ro.ctypes.data), C.c_void_p(co.ctypes.data),
+                                   MEM_HOST, _stream(stream)))
+    prob.ninst = len(ro) - 1
+
+
+def _propagate_batch(prob, lb, ub, results=None, theta=1e-3, max_rounds=10000, stream=None):
+    """bp_propagate_batch on device bounds; results: an int64 device tensor of
+    ninst * 6 words (bp_result layout) or None (allocated).  Asynchronous: returns the
+    device results tensor; decode it with batch_results()."""
+    torch = _torch()
+    if results is None:
+        results = torch.empty(prob.ninst * C.sizeof(BpResult) // 4, dtype=torch.int32, device=prob.device)
+    prm = params(theta, max_rounds)
+    _check(lib().bp_propagate_batch(prob.h, _ptr(lb), _ptr(ub), C.byref(prm), _ptr(results), _stream(stream)))
+    return results
+
+
+def batch_results(results):
+    """Decodes a device results tensor of bp_propagate_batch into a list of dicts."""
+    raw = results.cpu().numpy().tobytes()
+    size = C.sizeof(BpResult)
+    out = []
+    for i in range(len(raw) // size):
+        r = BpResult.from_buffer_copy(raw[i * size:(i + 1) * size])
+        out.append(r.as_dict())
+    return out
+
+
+Problem.set_instances = _set_instances
+Problem.propagate_batch = _propagate_batch
 
 
 def probe_split(is_int, l, u):

@@ -38,6 +38,7 @@ constexpr int kWarpsPerBlock = kThreads / 32;
 constexpr int kSlots = kNumClass;               // staging slots: row classes 0..5, then changed vars
 constexpr int kSlotChg = kClassChunked;         // chunked rows are not staged; their slot holds variables
 constexpr int kBq = 2048;                       // per-block queue of accepted variables
+constexpr int kMaxInst = kMaxInstances;         // instances per batched launch
 constexpr long long kSpinLimit = 4000000000LL;  // clock64 cycles (about 2 s) per wait
 static_assert(kThreads * kPerThread == kChunk, "a chunk is one wave of a block");
 
@@ -64,8 +65,19 @@ struct BpArgs {
     const int* w0v_len;
     double theta;
     int max_rounds;
-    int base;           // stamp of round 0
+    int* stamp;         // device word: stamp of round 0, advanced at exit (graph replays stay valid)
     long long* trace;   // optional: 4 words per round
+    // instances: a batch of independent problems laid out block-diagonally (rows
+    // [row_off[i], row_off[i+1]) and variables [col_off[i], col_off[i+1]) form instance i).
+    // One instance (ninst = 1, null offsets) is a plain propagation.
+    int ninst;
+    const int* row_off;
+    const int* col_off;
+    InstState* inst;
+    unsigned long long* i_nnz;   // [2][ninst] nonzeros processed in the phase of that parity
+    int* i_rowinf;               // [2][ninst] smallest infeasible row of the phase
+    int* i_cross;                // [2][ninst] smallest crossing variable found in the phase
+    int* i_chg;                  // [2][ninst] a variable of the instance changed in the phase
 };
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
@@ -86,6 +98,12 @@ struct Stage {
     // descriptor of the current phase, read once per block by thread 0
     int d_cnt[kNumClass];
     int d_ntask, d_nprev;
+    // instances (offsets, and the live / pending-check flags of the current phase)
+    int roff[kMaxInst + 1], coff[kMaxInst + 1];
+    unsigned char alive[kMaxInst], pending[kMaxInst];
+    unsigned long long i_nnz[kMaxInst];
+    int any_alive;
+    int last_block;
 };
 
 // ------------------------------------------------------------------ phase state
@@ -95,6 +113,23 @@ struct Phase {
     longlong2* X;           // bounds of the next round (atomics)
     int st_v, st_r;         // variable-change stamp of this round, row stamp of next round
 };
+
+// instance of row k / variable v (binary search in the shared-memory offsets)
+__device__ __forceinline__ int find_inst(const int* off, int ninst, int x) {
+    int lo = 0, hi = ninst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+__device__ __forceinline__ int row_inst(const Stage& st, const BpArgs& A, int k) {
+    return A.ninst == 1 ? 0 : find_inst(st.roff, A.ninst, k);
+}
+__device__ __forceinline__ int var_inst(const Stage& st, const BpArgs& A, int v) {
+    return A.ninst == 1 ? 0 : find_inst(st.coff, A.ninst, v);
+}
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
@@ -203,6 +238,7 @@ __device__ __forceinline__ void note_changed(Stage& st, const BpArgs& A, const D
         return;
     }
     if (atomicMax(&A.vstamp[j], ph.st_v) >= ph.st_v) return;
+    A.i_chg[ph.par * A.ninst + var_inst(st, A, j)] = 1;
     const int pos = atomicAdd(&A.ctl->nchg[ph.par].v, 1);
     A.chg[ph.par][pos] = j;
     const int e = __ldg(P.col_ptr + j + 1);
@@ -221,6 +257,7 @@ __device__ void drain_changed(Stage& st, const BpArgs& A, const DevProblem& P, c
         const int idx = b0 + lane;
         int v = idx < n ? st.bq[idx] : -1;
         if (v >= 0 && atomicMax(&A.vstamp[v], ph.st_v) >= ph.st_v) v = -1;
+        if (v >= 0) A.i_chg[ph.par * A.ninst + var_inst(st, A, v)] = 1;
         warp_append(st, A, P, ph, v >= 0 ? kSlotChg : -1, v);
         const int cb = v >= 0 ? __ldg(P.col_ptr + v) : 0;
         const int deg = v >= 0 ? __ldg(P.col_ptr + v + 1) - cb : 0;
@@ -362,15 +399,17 @@ __device__ __forceinline__ void elems_candidates(Stage& st, const BpArgs& A, con
 __device__ void do_thread_rows(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph,
                                const int* rows, int count, int tl) {
     const int idx = tl * 32 + (threadIdx.x & 31);
-    if (idx < count) {
-        const int k = __ldcg(rows + idx);
+    const int k = idx < count ? __ldcg(rows + idx) : -1;
+    const int ki = k >= 0 ? row_inst(st, A, k) : 0;
+    if (k >= 0 && st.alive[ki]) {
         const int beg = __ldg(P.row_ptr + k), end = __ldg(P.row_ptr + k + 1);
         const double2 g2 = __ldg(P.grow + k);
         Elems E;
         const Acc s = load_accumulate(E, P, ph, beg, end, 0, 1);
         atomicAdd(&st.nnz, (unsigned long long)(end - beg));
+        atomicAdd(&st.i_nnz[ki], (unsigned long long)(end - beg));
         if (row_infeasible(s.minfin, s.ninf, g2.y)) {
-            atomicMin(&A.ctl->rowinf[ph.par].v, k);
+            atomicMin(&A.i_rowinf[ph.par * A.ninst + ki], k);
         } else {
             elems_candidates(st, A, P, ph, E, s, g2.x);
         }
@@ -380,13 +419,18 @@ __device__ void do_thread_rows(Stage& st, const BpArgs& A, const DevProblem& P, 
 // Warp per row (kThreadMax+1 .. kWarpMax nonzeros).
 __device__ void do_warp_row(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, int k) {
     const int lane = threadIdx.x & 31;
+    const int ki = row_inst(st, A, k);
+    if (!st.alive[ki]) return;
     const int beg = __ldg(P.row_ptr + k), end = __ldg(P.row_ptr + k + 1);
     const double2 g2 = __ldg(P.grow + k);
     Elems E;
     const Acc tot = warp_reduce(load_accumulate(E, P, ph, beg, end, lane, 32));
-    if (lane == 0) atomicAdd(&st.nnz, (unsigned long long)(end - beg));
+    if (lane == 0) {
+        atomicAdd(&st.nnz, (unsigned long long)(end - beg));
+        atomicAdd(&st.i_nnz[ki], (unsigned long long)(end - beg));
+    }
     if (row_infeasible(tot.minfin, tot.ninf, g2.y)) {
-        if (lane == 0) atomicMin(&A.ctl->rowinf[ph.par].v, k);
+        if (lane == 0) atomicMin(&A.i_rowinf[ph.par * A.ninst + ki], k);
     } else {
         elems_candidates(st, A, P, ph, E, tot, g2.x);
     }
@@ -394,16 +438,21 @@ __device__ void do_warp_row(Stage& st, const BpArgs& A, const DevProblem& P, con
 
 // Block per row (kWarpMax+1 .. kChunk nonzeros): the reduction stays in shared memory.
 __device__ void do_block_row(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, int k) {
+    const int ki = row_inst(st, A, k);
+    if (!st.alive[ki]) return;
     const int beg = __ldg(P.row_ptr + k), end = __ldg(P.row_ptr + k + 1);
     const double2 g2 = __ldg(P.grow + k);
     Elems E;
     const Acc tot = block_reduce(st, load_accumulate(E, P, ph, beg, end, threadIdx.x, kThreads));
     if (row_infeasible(tot.minfin, tot.ninf, g2.y)) {
-        if (threadIdx.x == 0) atomicMin(&A.ctl->rowinf[ph.par].v, k);
+        if (threadIdx.x == 0) atomicMin(&A.i_rowinf[ph.par * A.ninst + ki], k);
     } else {
         elems_candidates(st, A, P, ph, E, tot, g2.x);
     }
-    if (threadIdx.x == 0) atomicAdd(&st.nnz, (unsigned long long)(end - beg));
+    if (threadIdx.x == 0) {
+        atomicAdd(&st.nnz, (unsigned long long)(end - beg));
+        atomicAdd(&st.i_nnz[ki], (unsigned long long)(end - beg));
+    }
     __syncthreads();
 }
 
@@ -411,6 +460,8 @@ __device__ void do_block_row(Stage& st, const BpArgs& A, const DevProblem& P, co
 // sums the partials in chunk order (deterministic) and publishes the row total.
 __device__ void do_chunk_partial(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, int2 tk) {
     const int k = tk.x, c = tk.y;
+    const int ki = row_inst(st, A, k);
+    if (!st.alive[ki]) return;
     const int rb = __ldg(P.row_ptr + k), re = __ldg(P.row_ptr + k + 1);
     const int beg = rb + c * kChunk, end = min(re, beg + kChunk);
     Elems E;
@@ -438,8 +489,9 @@ __device__ void do_chunk_partial(Stage& st, const BpArgs& A, const DevProblem& P
         s = warp_reduce(s);
         if (lane == 0) {
             const double2 g2 = __ldg(P.grow + k);
-            if (row_infeasible(s.minfin, s.ninf, g2.y)) atomicMin(&A.ctl->rowinf[ph.par].v, k);
+            if (row_infeasible(s.minfin, s.ninf, g2.y)) atomicMin(&A.i_rowinf[ph.par * A.ninst + ki], k);
             atomicAdd(&st.nnz, (unsigned long long)(re - rb));
+            atomicAdd(&st.i_nnz[ki], (unsigned long long)(re - rb));
             A.htot[h] = s.minfin;
             A.htinf[h] = make_int2(s.ninf, s.infj);
             A.harr[h] = 0;
@@ -454,6 +506,7 @@ __device__ void do_chunk_partial(Stage& st, const BpArgs& A, const DevProblem& P
 // The chunk's nonzeros and bounds are loaded before the wait.
 __device__ bool do_chunk_candidates(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, int2 tk) {
     const int k = tk.x, c = tk.y;
+    if (!st.alive[row_inst(st, A, k)]) return true;
     const int h = __ldg(P.heavy_id + k);
     const int rb = __ldg(P.row_ptr + k), re = __ldg(P.row_ptr + k + 1);
     const int beg = rb + c * kChunk, end = min(re, beg + kChunk);
@@ -489,42 +542,56 @@ __device__ bool do_chunk_candidates(Stage& st, const BpArgs& A, const DevProblem
 
 // Variables changed in the previous round: bring their new bounds into this round's
 // write buffer (atomic, so it commutes with this round's tightenings) and check crossings.
-__device__ void do_fix(const BpArgs& A, const DevProblem& P, const Phase& ph, const int* chg_prev, int nprev, int tl) {
+__device__ void do_fix(const Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, const int* chg_prev,
+                       int nprev, int tl) {
     const int idx = tl * 32 + (threadIdx.x & 31);
     if (idx >= nprev) return;
     const int v = __ldcg(chg_prev + idx);
+    const int vi = var_inst(st, A, v);
+    if (!st.alive[vi] && !st.pending[vi]) return;
     const longlong2 b = ld_bounds(ph.R, v);
-    atomicMax(&ph.X[v].x, b.x);
-    atomicMin(&ph.X[v].y, b.y);
-    if (crossed(P.is_int[v] != 0, b.x, b.y)) atomicMin(&A.ctl->cross[ph.par].v, v);
+    if (st.alive[vi]) {
+        atomicMax(&ph.X[v].x, b.x);
+        atomicMin(&ph.X[v].y, b.y);
+    }
+    if (crossed(P.is_int[v] != 0, b.x, b.y)) atomicMin(&A.i_cross[ph.par * A.ninst + vi], v);
 }
 
 // -------------------------------------------------------------------- barrier
-// All blocks arrive; the last one runs `book` (thread 0) and releases the others.  After the
-// release thread 0 of every block reads the stop flag and the descriptor of phase `next`
-// into shared memory (one reader per block keeps the control lines cold).
+// All blocks arrive; all threads of the last one run `book` (it may use __syncthreads) and
+// thread 0 releases the others.  After the release every block reads the stop flag, the
+// descriptor of phase `next` and the instances' live / pending flags into shared memory.
 template <class F>
 __device__ void grid_barrier(Stage& st, Ctl* ctl, const DevProblem& P, const BpArgs& A, int next, F&& book) {
     __syncthreads();
+    unsigned gen = 0;
     if (threadIdx.x == 0) {
-        const unsigned gen = ld_acquire_u32(&ctl->bar_gen.v);
+        gen = ld_acquire_u32(&ctl->bar_gen.v);
         __threadfence();
         const unsigned old = atom_add_acqrel_u32(&ctl->bar_count.v, 1u);
-        if (old == gridDim.x - 1) {
+        st.last_block = old == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (st.last_block) {
+        __threadfence();
+        book();
+        __syncthreads();
+        if (threadIdx.x == 0) {
             ctl->bar_count.v = 0;
-            book();
             __threadfence();
             st_release_u32(&ctl->bar_gen.v, gen + 1);
-        } else {
-            const long long t0 = clock64();
-            while (ld_acquire_u32(&ctl->bar_gen.v) == gen) {
-                if (clock64() - t0 > kSpinLimit) {
-                    atomicExch(&ctl->error, BP_ERR_TIMEOUT);
-                    break;
-                }
-                __nanosleep(64);
-            }
         }
+    } else if (threadIdx.x == 0) {
+        const long long t0 = clock64();
+        while (ld_acquire_u32(&ctl->bar_gen.v) == gen) {
+            if (clock64() - t0 > kSpinLimit) {
+                atomicExch(&ctl->error, BP_ERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(64);
+        }
+    }
+    if (threadIdx.x == 0) {
         __threadfence();
         st.flag = ld_acquire_s32(&ctl->stop) | (ld_acquire_s32(&ctl->error) != 0);
         const int par = next & 1;
@@ -536,28 +603,52 @@ __device__ void grid_barrier(Stage& st, Ctl* ctl, const DevProblem& P, const BpA
         st.d_nprev = next == 0 ? 0 : __ldcg(&ctl->nchg[par ^ 1].v);
     }
     __syncthreads();
+    for (int i = threadIdx.x; i < A.ninst; i += kThreads) {
+        st.alive[i] = (unsigned char)__ldcg(&A.inst[i].alive);
+        st.pending[i] = (unsigned char)__ldcg(&A.inst[i].pending);
+        st.i_nnz[i] = 0;
+    }
+    __syncthreads();
+}
+
+// Flushes the block's per-instance nonzero counts of the phase.
+__device__ void flush_inst_nnz(Stage& st, const BpArgs& A, int par) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < A.ninst; i += kThreads)
+        if (st.i_nnz[i]) atomicAdd(&A.i_nnz[par * A.ninst + i], st.i_nnz[i]);
+    __syncthreads();
 }
 
 __device__ void finish_block(Stage& st, const BpArgs& A) {
-    // the last block out writes the result slot
+    // the last block out writes the result slots
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        const unsigned old = atom_add_acqrel_u32(&A.ctl->done.v, 1u);
-        if (old == gridDim.x - 1) {
-            Ctl* c = A.ctl;
-            bp_result r;
-            r.error = c->error;
-            r.status = c->status;
-            r.rounds = c->rounds;
-            r.first_infeasible_row = c->first_row == INT_MAX ? -1 : c->first_row;
-            r.first_infeasible_var = c->first_var.v == INT_MAX ? -1 : c->first_var.v;
-            if (r.first_infeasible_var >= 0) r.status = BP_INFEASIBLE;
-            r.nnz_updates = (int64_t)c->nnz_total;
-            r.n_changed = (int64_t)c->n_changed.v;
-            r.reserved = 0;
-            *A.dres = r;
-        }
+        st.last_block = atom_add_acqrel_u32(&A.ctl->done.v, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!st.last_block) return;
+    __threadfence();
+    const int err = __ldcg(&A.ctl->error);
+    if (threadIdx.x == 0) {
+        const int b0 = __ldcg(A.stamp);
+        const int b = b0 > (1 << 30) ? 1 : b0;
+        *A.stamp = b + __ldcg(&A.ctl->phases) + 3;
+    }
+    for (int i = threadIdx.x; i < A.ninst; i += kThreads) {
+        const InstState* I = A.inst + i;
+        bp_result r;
+        r.error = err;
+        r.status = __ldcg(&I->status);
+        r.rounds = __ldcg(&I->rounds);
+        const int fr = __ldcg(&I->first_row), fv = __ldcg(&I->first_var);
+        r.first_infeasible_row = fr == INT_MAX ? -1 : fr;
+        r.first_infeasible_var = fv == INT_MAX ? -1 : fv;
+        if (r.first_infeasible_var >= 0) r.status = BP_INFEASIBLE;
+        r.nnz_updates = (int64_t)__ldcg(&I->nnz_total);
+        r.n_changed = (int64_t)__ldcg(&I->n_changed);
+        r.reserved = 0;
+        A.dres[i] = r;
     }
 }
 
@@ -572,7 +663,43 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
     for (int i = threadIdx.x; i < kWarpsPerBlock * kSlots; i += kThreads) (&st.wcnt[0][0])[i] = 0;
     if (threadIdx.x == 0) st.bq_n = 0;
     if (threadIdx.x == 0) st.nnz = 0;
+    for (int i = threadIdx.x; i <= A.ninst; i += kThreads) {
+        st.roff[i] = A.ninst == 1 ? (i ? P.m : 0) : A.row_off[i];
+        st.coff[i] = A.ninst == 1 ? (i ? P.n : 0) : A.col_off[i];
+    }
+    // stamps: this launch's round t uses base + t; the base lives on the device so that a
+    // replayed CUDA graph keeps advancing it; when it grows large the stamp arrays restart
+    int base = __ldcg(A.stamp);
+    if (base > (1 << 30)) {
+        for (int v = gtid; v < P.n; v += gthreads) A.vstamp[v] = 0;
+        for (int k = gtid; k < P.m; k += gthreads) A.rstamp[k] = 0;
+        for (int h = gtid; h < P.nheavy; h += gthreads) A.hready[h] = 0;
+        base = 1;
+    }
+    // per-instance state and per-phase arrays
+    for (int i = gtid; i < A.ninst; i += gthreads) {
+        InstState I;
+        I.status = BP_FIXPOINT;
+        I.rounds = 0;
+        I.result_par = 0;
+        I.first_row = INT_MAX;
+        I.first_var = INT_MAX;
+        I.alive = 1;
+        I.pending = 0;
+        I.entry_cross = INT_MAX;
+        I.nnz_total = 0;
+        I.n_changed = 0;
+        A.inst[i] = I;
+        for (int q = 0; q < 2; ++q) {
+            A.i_nnz[q * A.ninst + i] = 0;
+            A.i_rowinf[q * A.ninst + i] = INT_MAX;
+            A.i_cross[q * A.ninst + i] = INT_MAX;
+            A.i_chg[q * A.ninst + i] = 0;
+        }
+    }
     __syncthreads();
+    // all instance state must be initialised before any block updates it
+    grid_barrier(st, ctl, P, A, -1, [&] {});
 
     // ---- prologue: normalised start bounds into both buffers; rows of round 0
     for (int v = gtid; v < P.n; v += gthreads) {
@@ -580,10 +707,10 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
         const longlong2 b = normalized_keys(A.lb[v], A.ub[v], is_i);
         A.bk[0][v] = b;
         A.bk[1][v] = b;
-        if (crossed(is_i, b.x, b.y)) atomicMin(&ctl->entry_cross, v);
+        if (crossed(is_i, b.x, b.y)) atomicMin(&A.inst[var_inst(st, A, v)].entry_cross, v);
     }
     for (int h = gtid; h < P.nheavy; h += gthreads) A.harr[h] = 0;  // clean even after an aborted launch
-    Phase ph0{0, 0, 1, A.bk[0], A.bk[1], A.base, A.base};
+    Phase ph0{0, 0, 1, A.bk[0], A.bk[1], base, base};
     if (A.w0) {
         // queue the given rows into the round-0 lists (stamp `base` = member of round 0)
         Phase q = ph0;
@@ -612,23 +739,27 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
     }
     grid_barrier(st, ctl, P, A, 0, [&] {
         int rows0 = 0;
-        if (A.w0 || A.w0v) {
+        if (A.w0 || A.w0v)
             for (int c = 0; c < kNumClass; ++c) rows0 += ctl->cnt[0][c].v;
-        } else {
-            rows0 = P.m;
+        if (threadIdx.x == 0) st.any_alive = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < A.ninst; i += kThreads) {
+            InstState* I = A.inst + i;
+            const int ri = (A.w0 || A.w0v) ? rows0 : st.roff[i + 1] - st.roff[i];
+            const int ec = __ldcg(&I->entry_cross);
+            if (ec != INT_MAX) {
+                I->status = BP_INFEASIBLE;
+                I->first_var = ec;
+                I->alive = 0;
+            } else if (ri == 0 || A.max_rounds <= 0) {
+                I->status = ri == 0 ? BP_FIXPOINT : BP_ROUND_LIMIT;
+                I->alive = 0;
+            } else {
+                atomicOr(&st.any_alive, 1);
+            }
         }
-        if (ctl->entry_cross != INT_MAX) {
-            ctl->status = BP_INFEASIBLE;
-            ctl->rounds = 0;
-            ctl->result_par = 0;
-            ctl->first_var.v = ctl->entry_cross;
-            ctl->stop = 1;
-        } else if (rows0 == 0 || A.max_rounds <= 0) {
-            ctl->status = rows0 == 0 ? BP_FIXPOINT : BP_ROUND_LIMIT;
-            ctl->rounds = 0;
-            ctl->result_par = 0;
-            ctl->stop = 1;
-        }
+        __syncthreads();
+        if (threadIdx.x == 0 && !st.any_alive) ctl->stop = 1;
     });
 
     // ---- rounds
@@ -639,8 +770,8 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
         ph.npar = ph.par ^ 1;
         ph.R = A.bk[ph.par];
         ph.X = A.bk[ph.npar];
-        ph.st_v = A.base + t;
-        ph.st_r = A.base + t + 1;
+        ph.st_v = base + t;
+        ph.st_r = base + t + 1;
         const bool stat = (t == 0 && !A.w0 && !A.w0v);
         const int* rows = stat ? P.static_list : A.list[ph.par];
         const int2* tasks = stat ? P.static_tasks : A.task[ph.par];
@@ -672,7 +803,7 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
         for (int task = gw; task < total; task += NW) {
             int tl = task;
             if (tl < s_fix) {
-                do_fix(A, P, ph, chg_prev, nprev, tl);
+                do_fix(st, A, P, ph, chg_prev, nprev, tl);
                 continue;
             }
             tl -= s_fix;
@@ -704,57 +835,81 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
             atomicAdd(&ctl->nnz[ph.par].v, st.nnz);
             st.nnz = 0;
         }
+        flush_inst_nnz(st, A, ph.par);
         grid_barrier(st, ctl, P, A, t + 1, [&] {
             const int par = t & 1, npar = par ^ 1;
-            int nw = 0;
-            for (int c = 0; c < kNumClass; ++c) nw += ctl->cnt[npar][c].v;
-            if (A.trace && t < A.max_rounds) {
-                int rows_t = 0;
-                if (t == 0 && !A.w0 && !A.w0v) {
-                    rows_t = P.m;
-                } else {
-                    for (int c = 0; c < kNumClass; ++c) rows_t += ctl->cnt[par][c].v;
+            if (threadIdx.x == 0) st.any_alive = 0;
+            __syncthreads();
+            for (int i = threadIdx.x; i < A.ninst; i += kThreads) {
+                InstState* I = A.inst + i;
+                const int cross = __ldcg(A.i_cross + par * A.ninst + i);
+                int alive = __ldcg(&I->alive);
+                if (alive) {
+                    if (cross != INT_MAX) {
+                        // bounds after round t-1 cross: that round is the instance's last
+                        I->status = BP_INFEASIBLE;
+                        I->rounds = t;
+                        I->result_par = par;
+                        I->first_var = cross;
+                        I->first_row = INT_MAX;
+                        alive = 0;
+                    } else {
+                        I->nnz_total = __ldcg(&I->nnz_total) + __ldcg(A.i_nnz + par * A.ninst + i);
+                        I->rounds = t + 1;
+                        I->result_par = npar;
+                        const int rinf = __ldcg(A.i_rowinf + par * A.ninst + i);
+                        if (rinf != INT_MAX) {
+                            I->status = BP_INFEASIBLE;
+                            I->first_row = rinf;
+                            alive = 0;
+                            I->pending = 1;     // crossing check of this round's changes
+                        } else if (!__ldcg(A.i_chg + par * A.ninst + i)) {
+                            I->status = BP_FIXPOINT;
+                            alive = 0;
+                        } else if (t + 1 >= A.max_rounds) {
+                            I->status = BP_ROUND_LIMIT;
+                            alive = 0;
+                            I->pending = 1;
+                        }
+                    }
+                    I->alive = alive;
+                } else if (__ldcg(&I->pending)) {
+                    // the crossing check of the instance's last round ran in this phase
+                    if (cross != INT_MAX && cross < __ldcg(&I->first_var)) I->first_var = cross;
+                    I->pending = 0;
                 }
-                A.trace[4 * t + 0] = rows_t;
-                A.trace[4 * t + 1] = (long long)ctl->nnz[par].v;
-                A.trace[4 * t + 2] = ctl->nchg[par].v;
-                A.trace[4 * t + 3] = (long long)globaltimer_ns();
+                if (alive) atomicOr(&st.any_alive, 1);
+                A.i_nnz[npar * A.ninst + i] = 0;
+                A.i_rowinf[npar * A.ninst + i] = INT_MAX;
+                A.i_cross[npar * A.ninst + i] = INT_MAX;
+                A.i_chg[npar * A.ninst + i] = 0;
             }
-            if (ctl->cross[par].v != INT_MAX) {
-                // bounds after round t-1 cross: that round is the last one
-                ctl->status = BP_INFEASIBLE;
-                ctl->rounds = t;
-                ctl->result_par = par;
-                ctl->first_var.v = ctl->cross[par].v;
-                ctl->first_row = INT_MAX;
-                ctl->stop = 1;
-                return;
-            }
-            ctl->nnz_total += ctl->nnz[par].v;
-            ctl->rounds = t + 1;
-            ctl->result_par = npar;
-            if (ctl->rowinf[par].v != INT_MAX) {
-                ctl->status = BP_INFEASIBLE;
-                ctl->first_row = ctl->rowinf[par].v;
-                ctl->epi_par = par;
-                ctl->epi_n = ctl->nchg[par].v;
-                ctl->stop = 1;
-            } else if (nw == 0) {
-                ctl->status = BP_FIXPOINT;
-                ctl->stop = 1;
-            } else if (t + 1 >= A.max_rounds) {
-                ctl->status = BP_ROUND_LIMIT;
-                ctl->epi_par = par;
-                ctl->epi_n = ctl->nchg[par].v;
-                ctl->stop = 1;
-            } else {
-                // reset the append targets of round t+1
-                for (int c = 0; c < kNumClass; ++c) ctl->cnt[par][c].v = 0;
-                ctl->ntask[par].v = 0;
-                ctl->nchg[npar].v = 0;
-                ctl->nnz[npar].v = 0;
-                ctl->rowinf[npar].v = INT_MAX;
-                ctl->cross[npar].v = INT_MAX;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                if (A.trace && t < A.max_rounds) {
+                    int rows_t = 0;
+                    if (t == 0 && !A.w0 && !A.w0v) {
+                        rows_t = P.m;
+                    } else {
+                        for (int c = 0; c < kNumClass; ++c) rows_t += ctl->cnt[par][c].v;
+                    }
+                    A.trace[4 * t + 0] = rows_t;
+                    A.trace[4 * t + 1] = (long long)ctl->nnz[par].v;
+                    A.trace[4 * t + 2] = ctl->nchg[par].v;
+                    A.trace[4 * t + 3] = (long long)globaltimer_ns();
+                }
+                ctl->phases = t + 1;
+                if (!st.any_alive) {
+                    ctl->stop = 1;
+                    ctl->epi_par = par;
+                    ctl->epi_n = ctl->nchg[par].v;
+                } else {
+                    // reset the append targets of round t+1
+                    for (int c = 0; c < kNumClass; ++c) ctl->cnt[par][c].v = 0;
+                    ctl->ntask[par].v = 0;
+                    ctl->nchg[npar].v = 0;
+                    ctl->nnz[npar].v = 0;
+                }
             }
         });
     }
@@ -762,25 +917,33 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
     // ---- epilogue
     if (!ld_acquire_s32(&ctl->error)) {
         const int epi_n = __ldcg(&ctl->epi_n);
-        const longlong2* res = A.bk[__ldcg(&ctl->result_par)];
         if (epi_n > 0) {
+            // crossing check of the last round of the instances whose check is pending
             const int* lst = A.chg[__ldcg(&ctl->epi_par)];
             for (int i = gtid; i < epi_n; i += gthreads) {
                 const int v = __ldcg(lst + i);
-                const longlong2 b = __ldcg(res + v);
-                if (crossed(P.is_int[v] != 0, b.x, b.y)) atomicMin(&ctl->first_var.v, v);
+                const int vi = var_inst(st, A, v);
+                if (!__ldcg(&A.inst[vi].pending)) continue;
+                const longlong2 b = __ldcg(A.bk[__ldcg(&A.inst[vi].result_par)] + v);
+                if (crossed(P.is_int[v] != 0, b.x, b.y)) atomicMin(&A.inst[vi].first_var, v);
             }
         }
-        unsigned long long changed = 0;
-        for (int v = gtid; v < P.n; v += gthreads) {
-            const longlong2 in = normalized_keys(A.lb[v], A.ub[v], P.is_int[v] != 0);
-            const longlong2 b = __ldcg(res + v);
-            changed += (b.x != in.x || b.y != in.y) ? 1ull : 0ull;
-            A.lb[v] = kdec(b.x);
-            A.ub[v] = kdec(b.y);
+        for (int vb = blockIdx.x * kThreads; vb < P.n; vb += gthreads) {
+            const int v = vb + threadIdx.x;
+            int changed = 0, vi = -1;
+            if (v < P.n) {
+                vi = var_inst(st, A, v);
+                const longlong2 in = normalized_keys(A.lb[v], A.ub[v], P.is_int[v] != 0);
+                const longlong2 b = __ldcg(A.bk[__ldcg(&A.inst[vi].result_par)] + v);
+                changed = (b.x != in.x || b.y != in.y) ? 1 : 0;
+                A.lb[v] = kdec(b.x);
+                A.ub[v] = kdec(b.y);
+            }
+            // one atomic per instance present in the warp
+            const unsigned peers = __match_any_sync(0xffffffffu, vi);
+            const int total = __popc(__ballot_sync(0xffffffffu, changed) & peers);
+            if (vi >= 0 && lane == __ffs(peers) - 1 && total) atomicAdd(&A.inst[vi].n_changed, (unsigned long long)total);
         }
-        for (int off = 16; off > 0; off >>= 1) changed += __shfl_xor_sync(0xffffffffu, changed, off);
-        if (lane == 0 && changed) atomicAdd(&ctl->n_changed.v, changed);
     }
     finish_block(st, A);
 }
@@ -788,13 +951,21 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
 // ------------------------------------------------------------------------ host
 void ctl_template(Ctl* c) {
     memset(c, 0, sizeof(Ctl));
-    c->rowinf[0].v = c->rowinf[1].v = INT_MAX;
-    c->cross[0].v = c->cross[1].v = INT_MAX;
-    c->entry_cross = INT_MAX;
-    c->first_row = INT_MAX;
-    c->first_var.v = INT_MAX;
     c->epi_par = 0;
     c->epi_n = 0;
+}
+
+static int ensure_instances(mip_problem* p, int ninst) {
+    Work& w = p->w;
+    if (ninst <= w.inst_cap) return BP_OK;
+    BP_TRY(dalloc(p, &w.dres, (size_t)ninst));
+    BP_TRY(dalloc(p, &w.inst, (size_t)ninst));
+    BP_TRY(dalloc(p, &w.i_nnz, 2 * (size_t)ninst));
+    BP_TRY(dalloc(p, &w.i_rowinf, 2 * (size_t)ninst));
+    BP_TRY(dalloc(p, &w.i_cross, 2 * (size_t)ninst));
+    BP_TRY(dalloc(p, &w.i_chg, 2 * (size_t)ninst));
+    w.inst_cap = ninst;
+    return BP_OK;
 }
 
 int engine_prepare(mip_problem* p) {
@@ -818,7 +989,7 @@ int engine_prepare(mip_problem* p) {
     BP_TRY(dalloc(p, &w.harr, (size_t)dp.nheavy));
     BP_TRY(dalloc(p, &w.hready, (size_t)dp.nheavy));
     BP_TRY(dalloc(p, &w.ctl, 1));
-    BP_TRY(dalloc(p, &w.dres, 1));
+    BP_TRY(ensure_instances(p, 1));
     BP_TRY(dalloc(p, &w.stage_lb, (size_t)n));
     BP_TRY(dalloc(p, &w.stage_ub, (size_t)n));
     void* h = nullptr;
@@ -826,7 +997,11 @@ int engine_prepare(mip_problem* p) {
     p->host_allocs.push_back(h);
     w.ctl_host = static_cast<Ctl*>(h);
     ctl_template(w.ctl_host);
-    w.stamp_base = 1;
+    {
+        const int one = 1;
+        BP_TRY(dalloc(p, &w.stamp, 1));
+        BP_CUDA_TRY(cudaMemcpy(w.stamp, &one, sizeof(int), cudaMemcpyHostToDevice));
+    }
     // persistent grid: every block must be resident (cooperative launch)
     int occ = 0;
     BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bp_kernel, kThreads, 0));
@@ -841,16 +1016,14 @@ int engine_prepare(mip_problem* p) {
 }
 
 int launch_propagate(mip_problem* p, double* lb, double* ub, const int* w0, int w0_len, double theta,
-                     int max_rounds, int64_t* trace, cudaStream_t s, const int* w0v, const int* w0v_len) {
+                     int max_rounds, int64_t* trace, cudaStream_t s, const int* w0v, const int* w0v_len, int ninst,
+                     const int* row_off, const int* col_off) {
     Work& w = p->w;
-    const long long span = (long long)(max_rounds > 0 ? max_rounds : 0) + 3;
-    if (w.stamp_base + span >= (long long)INT_MAX - 16) {
-        // stamps would overflow: clear them and restart
-        BP_CUDA_TRY(cudaMemsetAsync(w.vstamp, 0, sizeof(int) * (p->n ? p->n : 1), s));
-        BP_CUDA_TRY(cudaMemsetAsync(w.rstamp, 0, sizeof(int) * (p->m ? p->m : 1), s));
-        BP_CUDA_TRY(cudaMemsetAsync(w.hready, 0, sizeof(int) * (p->dp.nheavy ? p->dp.nheavy : 1), s));
-        w.stamp_base = 1;
+    if (ninst < 1 || ninst > kMaxInstances || (ninst > 1 && (!row_off || !col_off || w0 || w0v))) {
+        set_error("invalid instance batch (1 <= instances <= %d, offsets required)", kMaxInstances);
+        return BP_ERR_INVALID;
     }
+    BP_TRY(ensure_instances(p, ninst));
     BpArgs a;
     a.lb = lb;
     a.ub = ub;
@@ -878,9 +1051,16 @@ int launch_propagate(mip_problem* p, double* lb, double* ub, const int* w0, int 
     a.w0v_len = w0v_len;
     a.theta = theta;
     a.max_rounds = max_rounds;
-    a.base = (int)w.stamp_base;
+    a.stamp = w.stamp;
     a.trace = (long long*)trace;
-    w.stamp_base += span;
+    a.ninst = ninst;
+    a.row_off = row_off;
+    a.col_off = col_off;
+    a.inst = w.inst;
+    a.i_nnz = w.i_nnz;
+    a.i_rowinf = w.i_rowinf;
+    a.i_cross = w.i_cross;
+    a.i_chg = w.i_chg;
     BP_CUDA_TRY(cudaMemcpyAsync(w.ctl, w.ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     DevProblem dp = p->dp;
     void* args[] = {&dp, &a};

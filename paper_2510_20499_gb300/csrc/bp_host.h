@@ -28,17 +28,18 @@ struct alignas(128) Ctl {
     Pad<int> ntask[2];                     // chunk tasks appended, per parity
     Pad<int> nchg[2];                      // changed variables appended, per parity
     Pad<unsigned long long> nnz[2];        // nonzeros processed in the phase of that parity
-    Pad<int> rowinf[2];                    // smallest infeasible row of the phase
-    Pad<int> cross[2];                     // smallest crossing variable found in the phase
-    Pad<int> first_var;                    // smallest crossing variable of the final round
-    Pad<unsigned long long> n_changed;
     Pad<unsigned> done;
     // written once per round by the last block at the barrier, read by thread 0 of each block
     int stop, error;
-    int entry_cross;
-    int status, rounds, result_par, first_row;
     int epi_par, epi_n;                    // changed list to crossing-check at the end
-    unsigned long long nnz_total;
+    int phases;                            // phases run (advances the stamp base at exit)
+};
+
+// State of one instance of a (possibly batched) propagation.
+struct InstState {
+    int status, rounds, result_par, first_row, first_var;
+    int alive, pending, entry_cross;
+    unsigned long long nnz_total, n_changed;
 };
 
 void ctl_template(Ctl* c);
@@ -59,10 +60,16 @@ struct Work {
     int* hready = nullptr;                     // per chunked row: stamp of a ready total
     Ctl* ctl = nullptr;
     Ctl* ctl_host = nullptr;                   // pinned constant template
-    bp_result* dres = nullptr;                 // device result slot
+    bp_result* dres = nullptr;                 // device result slots (one per instance)
+    InstState* inst = nullptr;                 // per-instance state
+    unsigned long long* i_nnz = nullptr;       // [2][ninst]
+    int* i_rowinf = nullptr;                   // [2][ninst]
+    int* i_cross = nullptr;                    // [2][ninst]
+    int* i_chg = nullptr;                      // [2][ninst]
+    int inst_cap = 0;
     double* stage_lb = nullptr;                // device staging for host bounds
     double* stage_ub = nullptr;
-    long long stamp_base = 1;
+    int* stamp = nullptr;                      // device: stamp of the next launch's round 0
 };
 
 }  // namespace gpubp
@@ -81,6 +88,9 @@ struct mip_problem {
     std::vector<void*> host_allocs;            // pinned host allocations
     cudaStream_t last_stream = nullptr;
     void* probe_work = nullptr;                // probing scratch (created on first use)
+    int ninst = 0;                             // instance batch (mip_set_instances)
+    int* inst_row_off = nullptr;
+    int* inst_col_off = nullptr;
     void* prio_work = nullptr;                 // priority / sort scratch (created on first use)
     void (*free_hooks[4])(mip_problem*) = {nullptr, nullptr, nullptr, nullptr};
 };
@@ -123,7 +133,9 @@ int radix_sort_pairs(unsigned long long* keys, int* vals, unsigned long long* tm
 // rows w0[0..w0_len), or the rows of the variables w0v[0..*w0v_len) (count read on the device)
 int launch_propagate(mip_problem* p, double* lb, double* ub, const int* w0, int w0_len,
                      double theta, int max_rounds, int64_t* trace, cudaStream_t s,
-                     const int* w0v = nullptr, const int* w0v_len = nullptr);
+                     const int* w0v = nullptr, const int* w0v_len = nullptr, int ninst = 1,
+                     const int* row_off = nullptr, const int* col_off = nullptr);
+constexpr int kMaxInstances = 1024;
 
 }  // namespace gpubp
 
