@@ -36,6 +36,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the probing and batch measurements")
     return ap.parse_args()
 
 
@@ -143,6 +144,104 @@ def cpu_baseline(p, budget_s=12.0):
     dt = time.perf_counter() - t0
     return {"value": nnz / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{runs} full propagations of the workload ({dt:.1f} s, single thread)"}
+
+
+def probing_extra(pkg, torch, dev):
+    """Probes/s on the 50k x 100k, 1M-nonzero knapsack/cover instance: 2,048 variables (the
+    top of the priority order) at 0 and 1, i.e. 4,096 propagations, in one batched launch,
+    against one bp_propagate_from launch per branch on the same GPU."""
+    import numpy as np
+    from paper_2510_20499_gb300 import synth
+    p = synth.knapsack_cover()
+    prob = pkg.Problem(p)
+    rl = torch.tensor(p.lb, device=dev)
+    ru = torch.tensor(p.ub, device=dev)
+    prob.propagate(rl, ru)
+    _, _, _, order = prob.probe_priority(rl, ru)
+    var = order[:2048].contiguous()
+    P = int(var.numel())
+    lo = rl[var.long()]
+    hi = ru[var.long()]
+    boxes = torch.stack([lo, lo, hi, hi], dim=1).contiguous()      # binaries: [l, l] and [u, u]
+    c = prob.probe_batch(rl, ru, var, boxes)                       # warm-up, sizes the cache
+    cap = int(c["var"].numel()) + 1024
+    times = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        c = prob.probe_batch(rl, ru, var, boxes, cap=cap)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    t_batch = float(np.median(times))
+    nnz = int(c["nnz_updates"].sum().item())
+    # one launch per branch
+    hv = var.cpu().numpy()
+    hb = boxes.cpu().numpy()
+    wl, wu = rl.clone(), ru.clone()
+    vt = torch.empty(1, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(P):
+        vt.fill_(int(hv[i]))
+        for b in range(2):
+            wl.copy_(rl)
+            wu.copy_(ru)
+            wl[int(hv[i])] = float(hb[i, 2 * b])
+            wu[int(hv[i])] = float(hb[i, 2 * b + 1])
+            prob.propagate_from(wl, wu, vt, sync=False)
+    e1.record()
+    torch.cuda.synchronize()
+    t_plain = e0.elapsed_time(e1)
+    return {"workload": "knapsack/cover 50k x 100k, 1M nnz; 2,048 priority pairs = 4,096 propagations",
+            "probes_per_s": 2 * P / (t_batch / 1e3), "ms_batched": t_batch,
+            "probes_per_s_plain": 2 * P / (t_plain / 1e3), "ms_plain": t_plain,
+            "speedup_batched_vs_plain": t_plain / t_batch, "nnz_updates": nnz,
+            "cache_entries": int(c["var"].numel())}
+
+
+def batch_extra(pkg, torch, dev):
+    """Aggregate nnz-updates/s of 64 uneven instances (nnz log-uniform in [1e3, 5e5]) in one
+    persistent launch captured in a CUDA graph."""
+    import numpy as np
+    from paper_2510_20499_gb300 import synth
+    parts = synth.uneven_batch()
+    big, ro, co = synth.block_diagonal(parts)
+    prob = pkg.Problem(big)
+    prob.set_instances(ro, co)
+    lb0 = torch.tensor(big.lb, device=dev)
+    ub0 = torch.tensor(big.ub, device=dev)
+    lb, ub = lb0.clone(), ub0.clone()
+    res = torch.empty(len(parts) * 12, dtype=torch.int32, device=dev)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        prob.propagate_batch(lb, ub, results=res)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        lb.copy_(lb0)
+        ub.copy_(ub0)
+        prob.propagate_batch(lb, ub, results=res)
+    times = []
+    for _ in range(5):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    rs = pkg.batch_results(res)
+    nnz = sum(r["nnz_updates"] for r in rs)
+    t = float(np.median(times))
+    return {"workload": f"{len(parts)} uneven instances, {big.nnz} nnz total (one graph-captured launch)",
+            "nnz_updates_per_s": nnz / (t / 1e3), "ms": t, "nnz_updates": nnz,
+            "rounds_max": max(r["rounds"] for r in rs),
+            "infeasible": sum(1 for r in rs if r["status"] == 1)}
 
 
 def main():
@@ -260,6 +359,8 @@ def main():
                      "peak_kind": peak_kind, "bytes_per_launch": bytes_launch, "kernel": "bp_kernel",
                      "launch_ms": kern_avg},
     }
+    if rank == 0 and not args.no_extras:
+        out["extras"] = {"probing": probing_extra(pkg, torch, dev), "batch": batch_extra(pkg, torch, dev)}
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(p)
     if rank == 0:

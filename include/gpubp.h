@@ -139,11 +139,23 @@ int mip_default_bounds(const mip_problem *p, double *lb, double *ub, void *strea
  * result:  host pointer.  The library enqueues a copy of the result into it; it is valid
  *          once the stream is synchronised (at return when it is pageable memory).  May be
  *          NULL, then the result stays on the device (see bp_result_device).
- * Returns BP_OK (check result->status), BP_ERR_TIMEOUT (a device wait gave up; the bounds
- * are then unspecified), BP_ERR_INVALID or BP_ERR_CUDA.
+ * Returns BP_OK (then check result->error and result->status), BP_ERR_INVALID or
+ * BP_ERR_CUDA.  Device-side errors arrive in result->error: BP_ERR_TIMEOUT when a device wait
+ * gave up (the bounds are then unspecified).
  */
 int bp_propagate(mip_problem *p, double *lb, double *ub, const bp_params *params,
                  bp_result *result, void *stream);
+
+/*
+ * bp_propagate_from -- bp_propagate whose round 0 holds only the rows of the given variables
+ * (for bounds that are a fixpoint except for those variables, e.g. after fixing them; a probe
+ * run one launch at a time).  vars: DEVICE int32[nvars], 0 <= vars[i] < n, duplicates
+ * allowed.  The range is checked on the device: an out-of-range index is never dereferenced,
+ * the launch stops after its set-up and result->error is BP_ERR_INVALID (bounds unspecified).
+ * Other arguments as for bp_propagate (device bounds only).
+ */
+int bp_propagate_from(mip_problem *p, double *lb, double *ub, const int32_t *vars, int32_t nvars,
+                      const bp_params *params, bp_result *result, void *stream);
 
 /* Device address of the handle's result slot written by the last bp_propagate. */
 const bp_result *bp_result_device(const mip_problem *p);

@@ -80,6 +80,8 @@ SIGNATURES = {
     "bp_propagate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(BpParams), C.POINTER(BpResult),
                                C.c_void_p]),
     "bp_result_device": (C.c_void_p, [C.c_void_p]),
+    "bp_propagate_from": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(BpParams),
+                                    C.POINTER(BpResult), C.c_void_p]),
     "probe_split": (C.c_int, [C.c_int32, C.c_double, C.c_double, C.POINTER(C.c_double)]),
     "bp_probe_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
                                  C.POINTER(BpParams), C.POINTER(ProbeCache), C.c_void_p]),
@@ -325,6 +327,18 @@ def batch_results(results):
     return out
 
 
+def _propagate_from(prob, lb, ub, vars_dev, theta=1e-3, max_rounds=10000, stream=None, sync=True):
+    """bp_propagate_from: round 0 holds the rows of the variables in vars_dev (int32 device)."""
+    prm = params(theta, max_rounds)
+    res = BpResult()
+    _check(lib().bp_propagate_from(prob.h, _ptr(lb), _ptr(ub), _ptr(vars_dev), int(vars_dev.numel()), C.byref(prm),
+                                   C.byref(res), _stream(stream)))
+    if sync:
+        _torch().cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+    return res.as_dict()
+
+
+Problem.propagate_from = _propagate_from
 Problem.set_instances = _set_instances
 Problem.propagate_batch = _propagate_batch
 

@@ -729,6 +729,10 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
         const int nv = *A.w0v_len;
         for (int b = gw0; b < nv; b += nw0) {
             const int u = __ldg(A.w0v + b);
+            if (u < 0 || u >= P.n) {   // caller's index out of range: skipped, reported
+                if (lane == 0) atomicExch(&ctl->error, BP_ERR_INVALID);
+                continue;
+            }
             const int cb = __ldg(P.col_ptr + u), ce = __ldg(P.col_ptr + u + 1);
             for (int s0 = cb; s0 < ce; s0 += 32) {
                 const int sidx = s0 + lane;
@@ -1111,3 +1115,26 @@ extern "C" int bp_propagate(mip_problem* p, double* lb, double* ub, const bp_par
 }
 
 extern "C" const bp_result* bp_result_device(const mip_problem* p) { return p ? p->w.dres : nullptr; }
+
+extern "C" int bp_propagate_from(mip_problem* p, double* lb, double* ub, const int32_t* vars, int32_t nvars,
+                                 const bp_params* params, bp_result* result, void* stream) {
+    if (!p || nvars < 0 || (nvars && !vars) || (p->n && (!lb || !ub))) {
+        set_error("bp_propagate_from: null or negative argument");
+        return BP_ERR_INVALID;
+    }
+    bp_params prm;
+    if (params) prm = *params;
+    else bp_params_default(&prm);
+    if (!(prm.theta >= 0.0) || prm.max_rounds < 0 || prm.bounds_mem != BP_MEM_DEVICE) {
+        set_error("bp_propagate_from: invalid parameters (device bounds only)");
+        return BP_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    Work& w = p->w;
+    if (!w.nvars_dev) BP_TRY(dalloc(p, &w.nvars_dev, 1));
+    BP_CUDA_TRY(cudaMemcpyAsync(w.nvars_dev, &nvars, sizeof(int), cudaMemcpyHostToDevice, s));
+    BP_TRY(launch_propagate(p, lb, ub, nullptr, 0, prm.theta, prm.max_rounds, prm.trace, s, vars ? vars : w.nvars_dev,
+                            w.nvars_dev));
+    if (result) BP_CUDA_TRY(cudaMemcpyAsync(result, p->w.dres, sizeof(bp_result), cudaMemcpyDeviceToHost, s));
+    return BP_OK;
+}

@@ -70,6 +70,7 @@ struct Work {
     double* stage_lb = nullptr;                // device staging for host bounds
     double* stage_ub = nullptr;
     int* stamp = nullptr;                      // device: stamp of the next launch's round 0
+    int* nvars_dev = nullptr;                  // device word: variable count of bp_propagate_from
 };
 
 }  // namespace gpubp
