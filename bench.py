@@ -214,7 +214,7 @@ def batch_extra(pkg, torch, dev):
     lb0 = torch.tensor(big.lb, device=dev)
     ub0 = torch.tensor(big.ub, device=dev)
     lb, ub = lb0.clone(), ub0.clone()
-    res = torch.empty(len(parts) * 12, dtype=torch.int32, device=dev)
+    res = torch.empty(len(parts) * pkg.C.sizeof(pkg.BpResult) // 4, dtype=torch.int32, device=dev)
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
