@@ -157,6 +157,32 @@ int bp_propagate(mip_problem *p, double *lb, double *ub, const bp_params *params
 int bp_propagate_from(mip_problem *p, double *lb, double *ub, const int32_t *vars, int32_t nvars,
                       const bp_params *params, bp_result *result, void *stream);
 
+/*
+ * bp_propagate_noalloc -- bp_propagate on device bounds that allocates nothing.  The paper has
+ * no counterpart: this call serves callers that may not allocate device memory while they run
+ * (a solver that reserves its whole device budget at start-up, or a host framework whose caching
+ * allocator holds the free memory, where a cudaMalloc/cudaFree from the library could fail or
+ * stall every stream of the device mid-search).
+ *
+ * The per-call scratch is a fixed array of BP_NOALLOC_SCRATCH_BYTES (32 MiB) in the library's
+ * static device memory, one per device, instead of the handle's own buffers.  A problem needs
+ * about 44 n + 12 m + 32 (chunks of rows longer than 2048) + 24 (such rows) bytes plus 4 KB;
+ * a larger problem is rejected with BP_ERR_CAPACITY before anything is enqueued (bp_last_error
+ * gives the bytes needed).  Each call clears the part of the scratch that must start at zero.
+ *
+ * Set-up: the first call on a device, with the handle's device current, looks up the array's
+ * device address (cudaGetSymbolAddress, which may load the module holding it); make that first
+ * call before any stream capture.  Calls that overlap in time on one device, from any handle,
+ * stream or thread, share the one array and race: order them.  The handle must not be used by
+ * another call meanwhile either.
+ *
+ * Arguments and results as for bp_propagate, with params->bounds_mem == BP_MEM_DEVICE.  The
+ * handle's device must be current (BP_ERR_INVALID otherwise).  result may be NULL.
+ */
+#define BP_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int bp_propagate_noalloc(mip_problem *p, double *lb, double *ub, const bp_params *params,
+                         bp_result *result, void *stream);
+
 /* Device address of the handle's result slot written by the last bp_propagate. */
 const bp_result *bp_result_device(const mip_problem *p);
 

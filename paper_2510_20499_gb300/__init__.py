@@ -80,6 +80,8 @@ SIGNATURES = {
     "bp_propagate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(BpParams), C.POINTER(BpResult),
                                C.c_void_p]),
     "bp_result_device": (C.c_void_p, [C.c_void_p]),
+    "bp_propagate_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(BpParams),
+                                       C.POINTER(BpResult), C.c_void_p]),
     "bp_propagate_from": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(BpParams),
                                     C.POINTER(BpResult), C.c_void_p]),
     "probe_split": (C.c_int, [C.c_int32, C.c_double, C.c_double, C.POINTER(C.c_double)]),
@@ -96,6 +98,9 @@ SIGNATURES = {
     "bp_last_error": (C.c_char_p, []),
     "bp_version": (C.c_char_p, []),
 }
+
+
+NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024   # BP_NOALLOC_SCRATCH_BYTES
 
 
 def lib():
@@ -338,7 +343,19 @@ def _propagate_from(prob, lb, ub, vars_dev, theta=1e-3, max_rounds=10000, stream
     return res.as_dict()
 
 
+def _propagate_noalloc(prob, lb, ub, theta=1e-3, max_rounds=10000, stream=None, sync=True):
+    """bp_propagate_noalloc on device bounds: the propagation of propagate(), with its scratch in
+    the library's fixed static device array (no allocation; calls on one device must not overlap)."""
+    prm = params(theta, max_rounds)
+    res = BpResult()
+    _check(lib().bp_propagate_noalloc(prob.h, _ptr(lb), _ptr(ub), C.byref(prm), C.byref(res), _stream(stream)))
+    if sync:
+        _torch().cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+    return res.as_dict()
+
+
 Problem.propagate_from = _propagate_from
+Problem.propagate_noalloc = _propagate_noalloc
 Problem.set_instances = _set_instances
 Problem.propagate_batch = _propagate_batch
 
