@@ -60,6 +60,23 @@ class FpResult(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
+class BpTuning(C.Structure):
+    _fields_ = [("warp_min", C.c_int32), ("block_min", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("reserved", C.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class BpTuneReport(C.Structure):
+    _fields_ = [("best", BpTuning), ("best_ms", C.c_float), ("default_ms", C.c_float), ("tried", C.c_int32),
+                ("rejected", C.c_int32)]
+
+    def as_dict(self):
+        return dict(best=self.best.as_dict(), best_ms=self.best_ms, default_ms=self.default_ms, tried=self.tried,
+                    rejected=self.rejected)
+
+
 class GpuBpError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"gpubp error {code}: {msg}")
@@ -80,6 +97,10 @@ SIGNATURES = {
     "bp_propagate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(BpParams), C.POINTER(BpResult),
                                C.c_void_p]),
     "bp_result_device": (C.c_void_p, [C.c_void_p]),
+    "bp_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(BpTuning)]),
+    "bp_set_tuning": (C.c_int, [C.c_void_p, C.POINTER(BpTuning), C.c_void_p]),
+    "bp_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(BpParams), C.c_int32,
+                              C.POINTER(BpTuneReport), C.c_void_p]),
     "bp_propagate_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(BpParams),
                                        C.POINTER(BpResult), C.c_void_p]),
     "bp_propagate_from": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(BpParams),
@@ -354,6 +375,29 @@ def _propagate_noalloc(prob, lb, ub, theta=1e-3, max_rounds=10000, stream=None, 
     return res.as_dict()
 
 
+def _get_tuning(prob):
+    t = BpTuning()
+    _check(lib().bp_get_tuning(prob.h, C.byref(t)))
+    return t.as_dict()
+
+
+def _set_tuning(prob, warp_min, block_min, blocks_per_sm, stream=None):
+    t = BpTuning(int(warp_min), int(block_min), int(blocks_per_sm), 0)
+    _check(lib().bp_set_tuning(prob.h, C.byref(t), _stream(stream)))
+
+
+def _autotune(prob, lb, ub, reps=3, theta=1e-3, max_rounds=10000, stream=None):
+    """bp_autotune on device start bounds; returns the report dict (the best configuration is
+    left set on the handle)."""
+    rep = BpTuneReport()
+    prm = params(theta, max_rounds)
+    _check(lib().bp_autotune(prob.h, _ptr(lb), _ptr(ub), C.byref(prm), int(reps), C.byref(rep), _stream(stream)))
+    return rep.as_dict()
+
+
+Problem.get_tuning = _get_tuning
+Problem.set_tuning = _set_tuning
+Problem.autotune = _autotune
 Problem.propagate_from = _propagate_from
 Problem.propagate_noalloc = _propagate_noalloc
 Problem.set_instances = _set_instances

@@ -44,6 +44,18 @@ __host__ __device__ inline int row_class(int len) {
     return 6;
 }
 
+// Class of a row under tunable split points (the autotuner's search space): rows of warp_min
+// or more nonzeros go to one warp, rows of block_min or more to one block, shorter rows to the
+// thread bins above.  2 <= warp_min <= kThreadMax + 1 and warp_min <= block_min <= kWarpMax + 1;
+// rows longer than kChunk are always chunked.  warp_min = kThreadMax + 1, block_min = kWarpMax + 1
+// reproduce row_class.
+__host__ __device__ inline int row_class_tuned(int len, int warp_min, int block_min) {
+    if (len > kChunk) return kClassChunked;
+    if (len >= block_min) return kClassBlockRow;
+    if (len >= warp_min) return kClassWarpRow;
+    return row_class(len);
+}
+
 // ------------------------------------------------------------------ ordered keys
 // key(d) = bits(d) for d >= +0, bits(d) ^ 0x7fff...f for negative d; -0.0 maps to +0.0 first
 // so that the two zeros compare equal, as they do in IEEE arithmetic.

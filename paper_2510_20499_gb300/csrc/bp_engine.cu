@@ -1015,7 +1015,9 @@ int engine_prepare(mip_problem* p) {
         set_error("propagation kernel cannot be resident on this device");
         return BP_ERR_CUDA;
     }
-    p->grid_blocks = sms * (occ > 4 ? 4 : occ);
+    p->sms = sms;
+    p->occ_max = occ > 4 ? 4 : occ;
+    p->grid_blocks = sms * p->occ_max;
     return BP_OK;
 }
 

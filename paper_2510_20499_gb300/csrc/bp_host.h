@@ -93,6 +93,10 @@ struct mip_problem {
     int* inst_row_off = nullptr;
     int* inst_col_off = nullptr;
     void* prio_work = nullptr;                 // priority / sort scratch (created on first use)
+    // row-class split points and grid shape (bp_set_tuning / bp_autotune)
+    int tune_warp_min = 2;                     // rows of 2+ nonzeros: a warp each (measured faster)
+    int tune_block_min = gpubp::kWarpMax + 1;
+    int sms = 0, occ_max = 0;                  // SMs and resident blocks per SM of bp_kernel
     void (*free_hooks[4])(mip_problem*) = {nullptr, nullptr, nullptr, nullptr};
 };
 
@@ -123,6 +127,10 @@ int dalloc(mip_problem* p, T** out, size_t count) {
 int scan_exclusive(const int* in, int* out, int n, int* total_dev, cudaStream_t s);
 
 int engine_prepare(mip_problem* p);     // allocates Work
+
+// row classes and class lists (rclass, static_list, class_off, heavy_id) from the row lengths
+// and the handle's split points
+int classify_rows(mip_problem* p, cudaStream_t s);
 
 // normalised bound keys of caller bounds (device arrays of n doubles)
 int root_keys(mip_problem* p, const double* lb, const double* ub, longlong2* out, cudaStream_t s);

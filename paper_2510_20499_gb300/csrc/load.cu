@@ -136,6 +136,11 @@ __global__ void k_rows(int m, const int64_t* rp64, const double* g, int* rp, dou
     }
 }
 
+__global__ void k_reclass(int m, const int* rp, int warp_min, int block_min, unsigned char* rclass) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x)
+        rclass[k] = (unsigned char)row_class_tuned(rp[k + 1] - rp[k], warp_min, block_min);
+}
+
 __global__ void k_class_flag(int m, const unsigned char* rclass, int c, int* flag) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x)
         flag[k] = rclass[k] == c ? 1 : 0;
@@ -229,6 +234,45 @@ static int upload(mip_problem* p, const T* src, size_t count, int mem_kind, T** 
     return BP_OK;
 }
 
+// Row classes under the handle's split points, and the class-grouped static row list (each
+// class ascending by row).  The chunked rows' ids (heavy_id) are rebuilt with them; they do not
+// depend on the split points.
+int classify_rows(mip_problem* p, cudaStream_t s) {
+    DevProblem& dp = p->dp;
+    const int m = p->m;
+    int counts[kNumClass] = {};
+    if (m) {
+        unsigned char* rclass = const_cast<unsigned char*>(dp.rclass);
+        int* list = const_cast<int*>(dp.static_list);
+        int* heavy = const_cast<int*>(dp.heavy_id);
+        k_reclass<<<grid_for(m), 256, 0, s>>>(m, dp.row_ptr, p->tune_warp_min, p->tune_block_min, rclass);
+        BP_CUDA_TRY(cudaGetLastError());
+        int *flag = nullptr, *pos = nullptr, *total = nullptr;
+        BP_CUDA_TRY(cudaMallocAsync(&flag, sizeof(int) * ((size_t)m + 1), s));
+        BP_CUDA_TRY(cudaMallocAsync(&pos, sizeof(int) * ((size_t)m + 1), s));
+        BP_CUDA_TRY(cudaMallocAsync(&total, sizeof(int), s));
+        int base = 0;
+        for (int cl = 0; cl < kNumClass; ++cl) {
+            k_class_flag<<<grid_for(m), 256, 0, s>>>(m, rclass, cl, flag);
+            BP_TRY(scan_exclusive(flag, pos, m, total, s));
+            k_class_scatter<<<grid_for(m), 256, 0, s>>>(m, rclass, cl, pos, base, list,
+                                                        cl == kClassChunked ? heavy : nullptr);
+            BP_CUDA_TRY(cudaMemcpyAsync(&counts[cl], total, sizeof(int), cudaMemcpyDeviceToHost, s));
+            BP_CUDA_TRY(cudaStreamSynchronize(s));
+            base += counts[cl];
+        }
+        for (void* q : {(void*)flag, (void*)pos, (void*)total}) BP_CUDA_TRY(cudaFreeAsync(q, s));
+    }
+    int base = 0;
+    for (int cl = 0; cl < kNumClass; ++cl) {
+        dp.class_off[cl] = base;
+        base += counts[cl];
+    }
+    dp.class_off[kNumClass] = base;
+    dp.nheavy = counts[kClassChunked];
+    return BP_OK;
+}
+
 static int load_impl(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
                      const double* g, const double* lb, const double* ub, const uint8_t* is_int,
                      const double* c, int32_t mem_kind, cudaStream_t s, mip_problem* p) {
@@ -312,40 +356,24 @@ static int load_impl(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t
     dp.m = m;
     dp.n = n;
     dp.nnz = (int)nnz;
-    int *d_rp, *d_chunks, *d_tmp, *d_list, *d_heavy, *d_total;
+    int *d_rp, *d_chunks, *d_list, *d_heavy, *d_total;
     double2* d_grow;
     unsigned char* d_rclass;
     BP_TRY(dalloc(p, &d_rp, (size_t)m + 1));
     BP_TRY(dalloc(p, &d_grow, (size_t)m));
     BP_TRY(dalloc(p, &d_rclass, (size_t)m));
     BP_TRY(dalloc(p, &d_chunks, (size_t)m));
-    BP_TRY(dalloc(p, &d_tmp, (size_t)m + 1));
     BP_TRY(dalloc(p, &d_list, (size_t)m));
     BP_TRY(dalloc(p, &d_heavy, (size_t)m));
     BP_TRY(dalloc(p, &d_total, 1));
     BP_CUDA_TRY(cudaMemsetAsync(d_heavy, 0xff, sizeof(int) * (m ? m : 1), s));
     k_rows<<<grid_for(m + 1), 256, 0, s>>>(m, d_rp64, d_g, d_rp, d_grow, d_rclass, d_chunks);
     BP_CUDA_TRY(cudaGetLastError());
-    int counts[kNumClass];
-    int* d_pos;
-    BP_TRY(dalloc(p, &d_pos, (size_t)m + 1));
-    int base = 0;
-    for (int cl = 0; cl < kNumClass; ++cl) {
-        dp.class_off[cl] = base;
-        if (m) {
-            k_class_flag<<<grid_for(m), 256, 0, s>>>(m, d_rclass, cl, d_tmp);
-            BP_TRY(scan_exclusive(d_tmp, d_pos, m, d_total, s));
-            k_class_scatter<<<grid_for(m), 256, 0, s>>>(m, d_rclass, cl, d_pos, base, d_list,
-                                                        cl == kClassChunked ? d_heavy : nullptr);
-            BP_CUDA_TRY(cudaMemcpyAsync(&counts[cl], d_total, sizeof(int), cudaMemcpyDeviceToHost, s));
-            BP_CUDA_TRY(cudaStreamSynchronize(s));
-        } else {
-            counts[cl] = 0;
-        }
-        base += counts[cl];
-    }
-    dp.class_off[kNumClass] = base;
-    dp.nheavy = counts[kClassChunked];
+    dp.row_ptr = d_rp;
+    dp.rclass = d_rclass;
+    dp.heavy_id = d_heavy;
+    dp.static_list = d_list;
+    BP_TRY(classify_rows(p, s));
     // chunk plan
     int* d_chunk_pos;
     BP_TRY(dalloc(p, &d_chunk_pos, (size_t)m + 1));
@@ -401,7 +429,6 @@ static int load_impl(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t
         k_norm_bounds<<<grid_for(n), 256, 0, s>>>(n, d_lb, d_ub, d_isint, p->def_lb, p->def_ub);
     }
     BP_CUDA_TRY(cudaGetLastError());
-    dp.row_ptr = d_rp;
     dp.col = d_col;
     dp.val = d_val;
     dp.grow = d_grow;
@@ -409,10 +436,7 @@ static int load_impl(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t
     dp.row_idx = d_rowidx;
     dp.col_val = d_colval;
     dp.is_int = d_isint;
-    dp.rclass = d_rclass;
-    dp.heavy_id = d_heavy;
     dp.part_off = d_part_off;
-    dp.static_list = d_list;
     dp.static_tasks = d_tasks;
     BP_TRY(engine_prepare(p));
     BP_CUDA_TRY(cudaStreamSynchronize(s));
