@@ -277,15 +277,16 @@ int bp_probe_priority(mip_problem *p, const double *lb, const double *ub, int32_
 /* Split points of the row classes and grid shape of the propagation engine.  Rows are binned
  * by length (Section 2.1): rows with fewer than warp_min nonzeros are handled one per thread,
  * rows of warp_min .. block_min-1 one per warp, rows of block_min .. 2048 one per block, longer
- * rows in 2048-nonzero chunks.  blocks_per_sm: thread blocks per SM of the persistent grid.
- * Valid: 2 <= warp_min <= 9, warp_min <= block_min <= 257, 1 <= blocks_per_sm <= the number
- * that can be resident (2 on GB300).  Defaults: 2, 257, all resident (on GB300 a warp per row
- * beat a thread per row for rows of 2..8 nonzeros on every workload measured). */
+ * rows in chunks of chunk_len nonzeros, one block each.  blocks_per_sm: thread blocks per SM of
+ * the persistent grid.  Valid: 2 <= warp_min <= 9, warp_min <= block_min <= 257,
+ * 1 <= blocks_per_sm <= the number that can be resident (2 on GB300), chunk_len in
+ * {256, 512, 1024, 2048}.  Defaults: 2, 257, all resident, 2048 (on GB300 a warp per row beat a
+ * thread per row for rows of 2..8 nonzeros on every workload measured). */
 typedef struct {
     int32_t warp_min;
     int32_t block_min;
     int32_t blocks_per_sm;
-    int32_t reserved;
+    int32_t chunk_len;
 } bp_tuning;
 
 /* What bp_autotune measured.  best_ms / default_ms: median launch time of the chosen and the
@@ -308,10 +309,10 @@ int bp_get_tuning(const mip_problem *p, bp_tuning *out);
 int bp_set_tuning(mip_problem *p, const bp_tuning *t, void *stream);
 
 /*
- * bp_autotune -- times every configuration of a small grid (warp_min in {2, 5, 9}, block_min in
- * {65, 129, 257}, every valid blocks_per_sm) with one warm-up and `reps` (<= 0: 3) propagations
- * from lb/ub (DEVICE, n doubles each, not modified; the handle's staging buffers hold the
- * working bounds), and keeps the fastest configuration whose results equal the defaults'.  A
+ * bp_autotune -- times every configuration of a small grid (warp_min in {2, 9}, block_min in
+ * {65, 257}, every valid blocks_per_sm, every valid chunk_len) with one warm-up and `reps`
+ * (<= 0: 3) propagations from lb/ub (DEVICE, n doubles each, not modified; the handle's
+ * staging buffers hold the working bounds), and keeps the fastest configuration whose results equal the defaults'.  A
  * handle with an instance batch (mip_set_instances) is tuned on bp_propagate_batch, otherwise
  * on bp_propagate.  report (host, may be NULL) receives the measurements.  The call synchronises
  * the stream; on an error the defaults are restored.

@@ -62,7 +62,7 @@ class FpResult(C.Structure):
 
 class BpTuning(C.Structure):
     _fields_ = [("warp_min", C.c_int32), ("block_min", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("chunk_len", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
@@ -381,8 +381,8 @@ def _get_tuning(prob):
     return t.as_dict()
 
 
-def _set_tuning(prob, warp_min, block_min, blocks_per_sm, stream=None):
-    t = BpTuning(int(warp_min), int(block_min), int(blocks_per_sm), 0)
+def _set_tuning(prob, warp_min, block_min, blocks_per_sm, chunk_len=2048, stream=None):
+    t = BpTuning(int(warp_min), int(block_min), int(blocks_per_sm), int(chunk_len))
     _check(lib().bp_set_tuning(prob.h, C.byref(t), _stream(stream)))
 
 

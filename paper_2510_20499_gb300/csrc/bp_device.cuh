@@ -22,7 +22,8 @@ constexpr int kWarp = 32;
 //   classes 0..3: at most 1, 2, 4, 8 nonzeros          -> one thread per row
 //   class 4:      9 .. kWarpMax nonzeros               -> one warp per row
 //   class 5:      kWarpMax+1 .. kChunk nonzeros        -> one thread block per row
-//   class 6:      more than kChunk nonzeros            -> kChunk-nonzero chunks, one block each
+//   class 6:      more than kChunk nonzeros            -> chunks of chunk_len <= kChunk nonzeros,
+//                                                         one block each
 // Every task then holds at most kPerThread nonzeros per thread, all loaded in one wave.
 constexpr int kNumClass = 7;
 constexpr int kNumThreadBins = 4;
@@ -33,6 +34,11 @@ constexpr int kPerThread = 8;
 constexpr int kThreadMax = kPerThread;            // 8
 constexpr int kWarpMax = 32 * kPerThread;         // 256
 constexpr int kChunk = 256 * kPerThread;          // 2048 (blocks of 256 threads)
+constexpr int kChunkMin = 256;                    // smallest chunk length of a chunked row
+// default split points (bp_autotune may pick others): a warp per row from 2 nonzeros, a block
+// per row from kWarpMax + 1, chunks of kDefaultChunkLen
+constexpr int kDefaultWarpMin = 2;
+constexpr int kDefaultChunkLen = kChunk;
 
 __host__ __device__ inline int row_class(int len) {
     if (len <= 1) return 0;
@@ -243,11 +249,13 @@ struct DevProblem {
     const double* col_val;       // nnz: coefficients in transpose order
     const unsigned char* is_int; // n
     const unsigned char* rclass; // m
+    const int* rinfo;            // m: class | chunks << 3 (chunks of a chunked row, else 0)
     const int* heavy_id;         // m: index among chunked rows, -1 otherwise
     const int* part_off;         // nheavy+1: first partial slot of each chunked row
     const int* static_list;      // m: row ids grouped by class, ascending within a class
     const int2* static_tasks;    // all chunk tasks {row, chunk} of the chunked rows
     int class_off[kNumClass + 1];// class segments of static_list and of worklists
+    int chunk_len;               // nonzeros per chunk of a chunked row (kChunkMin .. kChunk)
     int nheavy, nchunks;         // chunked rows, total chunks
 };
 

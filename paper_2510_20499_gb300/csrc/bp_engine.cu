@@ -40,7 +40,7 @@ constexpr int kSlotChg = kClassChunked;         // chunked rows are not staged; 
 constexpr int kBq = 2048;                       // per-block queue of accepted variables
 constexpr int kMaxInst = kMaxInstances;         // instances per batched launch
 constexpr long long kSpinLimit = 4000000000LL;  // clock64 cycles (about 2 s) per wait
-static_assert(kThreads * kPerThread == kChunk, "a chunk is one wave of a block");
+static_assert(kThreads * kPerThread == kChunk, "the longest chunk is one wave of a block");
 
 struct BpArgs {
     double* lb;
@@ -94,7 +94,9 @@ struct Stage {
     double red_d[kWarpsPerBlock];
     int red_n[kWarpsPerBlock], red_j[kWarpsPerBlock];
     unsigned long long nnz;
-    int flag, last;
+    int flag, last, ok;
+    double tot_d;                               // row total of a fused chunk task
+    int tot_n, tot_j;
     // descriptor of the current phase, read once per block by thread 0
     int d_cnt[kNumClass];
     int d_ntask, d_nprev;
@@ -193,15 +195,15 @@ __device__ void warp_append(Stage& st, const BpArgs& A, const DevProblem& P, con
 // Append of one row or variable by a single lane, straight to the global lists (only for the
 // rare paths that run outside a converged warp).
 __device__ void lane_queue_row(const BpArgs& A, const DevProblem& P, const Phase& ph, int k) {
+    const int info = __ldg(P.rinfo + k);   // issued before the stamp atomic: no dependency
     if (atomicMax(&A.rstamp[k], ph.st_r) >= ph.st_r) return;
-    const int cls = P.rclass[k];
+    const int cls = info & 7;
     if (cls != kClassChunked) {
         const int pos = atomicAdd(&A.ctl->cnt[ph.npar][cls].v, 1);
         A.list[ph.npar][P.class_off[cls] + pos] = k;
         return;
     }
-    const int len = __ldg(P.row_ptr + k + 1) - __ldg(P.row_ptr + k);
-    const int nch = (len + kChunk - 1) / kChunk;
+    const int nch = info >> 3;
     const int base = atomicAdd(&A.ctl->ntask[ph.npar].v, nch);
     for (int c = 0; c < nch; ++c) A.task[ph.npar][base + c] = make_int2(k, c);
     atomicAdd(&A.ctl->cnt[ph.npar][kClassChunked].v, 1);
@@ -211,13 +213,13 @@ __device__ void lane_queue_row(const BpArgs& A, const DevProblem& P, const Phase
 // this round wins.  Chunked rows get their chunk tasks directly (they are few).
 __device__ void warp_queue_rows(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, int k) {
     int slot = -1;
+    const int info = k >= 0 ? __ldg(P.rinfo + k) : 0;   // issued before the stamp atomic
     if (k >= 0 && atomicMax(&A.rstamp[k], ph.st_r) < ph.st_r) {
-        const int cls = P.rclass[k];
+        const int cls = info & 7;
         if (cls != kClassChunked) {
             slot = cls;
         } else {
-            const int len = __ldg(P.row_ptr + k + 1) - __ldg(P.row_ptr + k);
-            const int nch = (len + kChunk - 1) / kChunk;
+            const int nch = info >> 3;
             const int base = atomicAdd(&A.ctl->ntask[ph.npar].v, nch);
             for (int c = 0; c < nch; ++c) A.task[ph.npar][base + c] = make_int2(k, c);
             atomicAdd(&A.ctl->cnt[ph.npar][kClassChunked].v, 1);
@@ -256,11 +258,13 @@ __device__ void drain_changed(Stage& st, const BpArgs& A, const DevProblem& P, c
     for (int b0 = w * 32; b0 < n; b0 += kThreads) {
         const int idx = b0 + lane;
         int v = idx < n ? st.bq[idx] : -1;
+        // the column extent is loaded alongside the stamp atomic (independent round trips)
+        const int cb = v >= 0 ? __ldg(P.col_ptr + v) : 0;
+        const int ce = v >= 0 ? __ldg(P.col_ptr + v + 1) : 0;
         if (v >= 0 && atomicMax(&A.vstamp[v], ph.st_v) >= ph.st_v) v = -1;
         if (v >= 0) A.i_chg[ph.par * A.ninst + var_inst(st, A, v)] = 1;
         warp_append(st, A, P, ph, v >= 0 ? kSlotChg : -1, v);
-        const int cb = v >= 0 ? __ldg(P.col_ptr + v) : 0;
-        const int deg = v >= 0 ? __ldg(P.col_ptr + v + 1) - cb : 0;
+        const int deg = v >= 0 ? ce - cb : 0;
         int incl = deg;
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, incl, o);
@@ -326,13 +330,20 @@ __device__ __forceinline__ Acc block_reduce(Stage& st, Acc a) {
         st.red_j[w] = a.infj;
     }
     __syncthreads();
-    Acc t{0.0, 0, -1};
+    if (threadIdx.x == 0) {   // one thread sums the warps' partials (the FP64 pipe is narrow)
+        Acc t{0.0, 0, -1};
 #pragma unroll
-    for (int i = 0; i < kWarpsPerBlock; ++i) {
-        t.minfin = __dadd_rn(t.minfin, st.red_d[i]);
-        t.ninf += st.red_n[i];
-        t.infj = max(t.infj, st.red_j[i]);
+        for (int i = 0; i < kWarpsPerBlock; ++i) {
+            t.minfin = __dadd_rn(t.minfin, st.red_d[i]);
+            t.ninf += st.red_n[i];
+            t.infj = max(t.infj, st.red_j[i]);
+        }
+        st.red_d[0] = t.minfin;
+        st.red_n[0] = t.ninf;
+        st.red_j[0] = t.infj;
     }
+    __syncthreads();
+    const Acc t{st.red_d[0], st.red_n[0], st.red_j[0]};
     __syncthreads();
     return t;
 }
@@ -456,50 +467,118 @@ __device__ void do_block_row(Stage& st, const BpArgs& A, const DevProblem& P, co
     __syncthreads();
 }
 
+// Sum of the partials of chunked row k in chunk order (deterministic), by warp 0 of the last
+// chunk to arrive; lane 0 checks the row, counts its nonzeros, publishes the total and releases
+// the waiting chunks.  Returns the total in lane 0.
+__device__ Acc chunk_total(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, int k, int ki, int h,
+                           int slot0, int nch, int len, double g_tol) {
+    const int lane = threadIdx.x;
+    __threadfence();
+    Acc s{0.0, 0, -1};
+    for (int i = lane; i < nch; i += 32) {
+        s.minfin = __dadd_rn(s.minfin, __ldcg(A.hpart + slot0 + i));
+        const int2 pi = __ldcg(A.hpinf + slot0 + i);
+        s.ninf += pi.x;
+        s.infj = max(s.infj, pi.y);
+    }
+    s = warp_reduce(s);
+    if (lane == 0) {
+        if (row_infeasible(s.minfin, s.ninf, g_tol)) atomicMin(&A.i_rowinf[ph.par * A.ninst + ki], k);
+        atomicAdd(&st.nnz, (unsigned long long)len);
+        atomicAdd(&st.i_nnz[ki], (unsigned long long)len);
+        A.htot[h] = s.minfin;
+        A.htinf[h] = make_int2(s.ninf, s.infj);
+        A.harr[h] = 0;
+        __threadfence();
+        st_release_s32(A.hready + h, ph.st_v);
+    }
+    return s;
+}
+
+// Thread 0: writes the block's partial of chunk c and arrives; true for the last arrival.
+__device__ __forceinline__ bool chunk_arrive(const BpArgs& A, const Acc& part, int h, int slot0, int c, int nch) {
+    A.hpart[slot0 + c] = part.minfin;
+    A.hpinf[slot0 + c] = make_int2(part.ninf, part.infj);
+    __threadfence();
+    return atomicAdd(&A.harr[h], 1) == nch - 1;
+}
+
 // Chunk of a long row, first half: the block's partial activity; the last chunk to arrive
-// sums the partials in chunk order (deterministic) and publishes the row total.
+// sums the partials and publishes the row total.  The row's metadata loads are issued before
+// the nonzeros' so that their round trips overlap.
 __device__ void do_chunk_partial(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, int2 tk) {
     const int k = tk.x, c = tk.y;
     const int ki = row_inst(st, A, k);
     if (!st.alive[ki]) return;
     const int rb = __ldg(P.row_ptr + k), re = __ldg(P.row_ptr + k + 1);
-    const int beg = rb + c * kChunk, end = min(re, beg + kChunk);
-    Elems E;
-    const Acc part = block_reduce(st, load_accumulate(E, P, ph, beg, end, threadIdx.x, kThreads));
     const int h = __ldg(P.heavy_id + k);
     const int slot0 = __ldg(P.part_off + h);
-    const int nch = (re - rb + kChunk - 1) / kChunk;
-    if (threadIdx.x == 0) {
-        A.hpart[slot0 + c] = part.minfin;
-        A.hpinf[slot0 + c] = make_int2(part.ninf, part.infj);
-        __threadfence();
-        st.last = atomicAdd(&A.harr[h], 1) == nch - 1;
+    const double g_tol = __ldg(&P.grow[k].y);
+    const int beg = rb + c * P.chunk_len, end = min(re, beg + P.chunk_len);
+    const int nch = (re - rb + P.chunk_len - 1) / P.chunk_len;
+    Elems E;
+    const Acc part = block_reduce(st, load_accumulate(E, P, ph, beg, end, threadIdx.x, kThreads));
+    if (threadIdx.x == 0) st.last = chunk_arrive(A, part, h, slot0, c, nch);
+    __syncthreads();
+    if (st.last && threadIdx.x < 32) (void)chunk_total(st, A, P, ph, k, ki, h, slot0, nch, re - rb, g_tol);
+    __syncthreads();
+}
+
+// Chunk of a long row, both halves at once.  Used when every chunk task of the round is the
+// first task of its block: then no block can wait on a chunk whose block is itself waiting,
+// and the chunk's nonzeros and bounds stay in registers from the partial sum to the
+// candidates instead of being loaded twice.  Returns false when the wait gave up.
+__device__ bool do_chunk_fused(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, int2 tk) {
+    const int k = tk.x, c = tk.y;
+    const int ki = row_inst(st, A, k);
+    if (!st.alive[ki]) return true;
+    const int rb = __ldg(P.row_ptr + k), re = __ldg(P.row_ptr + k + 1);
+    const int h = __ldg(P.heavy_id + k);
+    const int slot0 = __ldg(P.part_off + h);
+    const double2 g2 = __ldg(P.grow + k);
+    const int beg = rb + c * P.chunk_len, end = min(re, beg + P.chunk_len);
+    const int nch = (re - rb + P.chunk_len - 1) / P.chunk_len;
+    Elems E;
+    const Acc part = block_reduce(st, load_accumulate(E, P, ph, beg, end, threadIdx.x, kThreads));
+    if (threadIdx.x == 0) st.last = chunk_arrive(A, part, h, slot0, c, nch);
+    __syncthreads();
+    if (st.last) {
+        if (threadIdx.x < 32) {
+            const Acc t = chunk_total(st, A, P, ph, k, ki, h, slot0, nch, re - rb, g2.y);
+            if (threadIdx.x == 0) {
+                st.tot_d = t.minfin;
+                st.tot_n = t.ninf;
+                st.tot_j = t.infj;
+                st.ok = 1;
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        int ok = 1;
+        const long long t0 = clock64();
+        while (ld_acquire_s32(A.hready + h) != ph.st_v) {
+            if (clock64() - t0 > kSpinLimit) {
+                ok = 0;
+                atomicExch(&A.ctl->error, BP_ERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(32);
+        }
+        if (ok) {
+            st.tot_d = __ldcg(A.htot + h);
+            const int2 ti = __ldcg(A.htinf + h);
+            st.tot_n = ti.x;
+            st.tot_j = ti.y;
+        }
+        st.ok = ok;
     }
     __syncthreads();
-    if (st.last && threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        __threadfence();
-        Acc s{0.0, 0, -1};
-        for (int i = lane; i < nch; i += 32) {
-            s.minfin = __dadd_rn(s.minfin, __ldcg(A.hpart + slot0 + i));
-            const int2 pi = __ldcg(A.hpinf + slot0 + i);
-            s.ninf += pi.x;
-            s.infj = max(s.infj, pi.y);
-        }
-        s = warp_reduce(s);
-        if (lane == 0) {
-            const double2 g2 = __ldg(P.grow + k);
-            if (row_infeasible(s.minfin, s.ninf, g2.y)) atomicMin(&A.i_rowinf[ph.par * A.ninst + ki], k);
-            atomicAdd(&st.nnz, (unsigned long long)(re - rb));
-            atomicAdd(&st.i_nnz[ki], (unsigned long long)(re - rb));
-            A.htot[h] = s.minfin;
-            A.htinf[h] = make_int2(s.ninf, s.infj);
-            A.harr[h] = 0;
-            __threadfence();
-            st_release_s32(A.hready + h, ph.st_v);
-        }
+    const bool ok = st.ok != 0;
+    if (ok) {
+        const Acc tot{st.tot_d, st.tot_n, st.tot_j};
+        if (!row_infeasible(tot.minfin, tot.ninf, g2.y)) elems_candidates(st, A, P, ph, E, tot, g2.x);
     }
     __syncthreads();
+    return ok;
 }
 
 // Chunk of a long row, second half: wait for the row total, then the chunk's candidates.
@@ -509,7 +588,7 @@ __device__ bool do_chunk_candidates(Stage& st, const BpArgs& A, const DevProblem
     if (!st.alive[row_inst(st, A, k)]) return true;
     const int h = __ldg(P.heavy_id + k);
     const int rb = __ldg(P.row_ptr + k), re = __ldg(P.row_ptr + k + 1);
-    const int beg = rb + c * kChunk, end = min(re, beg + kChunk);
+    const int beg = rb + c * P.chunk_len, end = min(re, beg + P.chunk_len);
     Elems E;
     (void)load_accumulate(E, P, ph, beg, end, threadIdx.x, kThreads);
     if (threadIdx.x == 0) {
@@ -567,7 +646,7 @@ __device__ void grid_barrier(Stage& st, Ctl* ctl, const DevProblem& P, const BpA
     unsigned gen = 0;
     if (threadIdx.x == 0) {
         gen = ld_acquire_u32(&ctl->bar_gen.v);
-        __threadfence();
+        __threadfence();   // the block's writes (all threads, ordered by the barrier above)
         const unsigned old = atom_add_acqrel_u32(&ctl->bar_count.v, 1u);
         st.last_block = old == gridDim.x - 1;
     }
@@ -603,10 +682,20 @@ __device__ void grid_barrier(Stage& st, Ctl* ctl, const DevProblem& P, const BpA
         st.d_nprev = next == 0 ? 0 : __ldcg(&ctl->nchg[par ^ 1].v);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < A.ninst; i += kThreads) {
-        st.alive[i] = (unsigned char)__ldcg(&A.inst[i].alive);
-        st.pending[i] = (unsigned char)__ldcg(&A.inst[i].pending);
-        st.i_nnz[i] = 0;
+    if (A.ninst == 1 && next > 0) {
+        // one instance: it is alive while the rounds go on (its end stops them), and its pending
+        // crossing check is read only after the rounds
+        if (threadIdx.x == 0) {
+            st.alive[0] = 1;
+            st.pending[0] = 0;
+            st.i_nnz[0] = 0;
+        }
+    } else {
+        for (int i = threadIdx.x; i < A.ninst; i += kThreads) {
+            st.alive[i] = (unsigned char)__ldcg(&A.inst[i].alive);
+            st.pending[i] = (unsigned char)__ldcg(&A.inst[i].pending);
+            st.i_nnz[i] = 0;
+        }
     }
     __syncthreads();
 }
@@ -786,11 +875,17 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
 #pragma unroll
         for (int c = 0; c < kNumClass; ++c) cnt[c] = st.d_cnt[c];
         bool alive = true;
-        // block tasks: partial sums of chunked rows, then block-per-row rows
+        // block tasks: partial sums of chunked rows (with their candidates when every chunk task
+        // is the first task of its block), then block-per-row rows
+        const bool fused = ntask <= (int)gridDim.x;
         const int nblk = ntask + cnt[kClassBlockRow];
         for (int bt = blockIdx.x; bt < nblk; bt += gridDim.x) {
             if (bt < ntask) {
-                do_chunk_partial(st, A, P, ph, __ldcg(tasks + bt));
+                if (fused) {
+                    alive = do_chunk_fused(st, A, P, ph, __ldcg(tasks + bt)) && alive;
+                } else {
+                    do_chunk_partial(st, A, P, ph, __ldcg(tasks + bt));
+                }
             } else {
                 do_block_row(st, A, P, ph, __ldcg(rows + P.class_off[kClassBlockRow] + (bt - ntask)));
             }
@@ -804,7 +899,11 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
             s_bin[c] = (cnt[c] + 31) / 32;
             total += s_bin[c];
         }
-        for (int task = gw; task < total; task += NW) {
+        // warp tasks are numbered from the first block without a block task, so that a short
+        // round's few warp tasks do not queue behind a block task
+        const int w0 = (min(nblk, (int)gridDim.x) * kWarpsPerBlock) % NW;
+        const int gw_r = gw >= w0 ? gw - w0 : gw - w0 + NW;
+        for (int task = gw_r; task < total; task += NW) {
             int tl = task;
             if (tl < s_fix) {
                 do_fix(st, A, P, ph, chg_prev, nprev, tl);
@@ -828,7 +927,7 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
         }
         __syncthreads();
         // block tasks that wait: candidates of chunked rows
-        for (int bt = blockIdx.x; bt < ntask && alive; bt += gridDim.x)
+        for (int bt = blockIdx.x; !fused && bt < ntask && alive; bt += gridDim.x)
             alive = do_chunk_candidates(st, A, P, ph, __ldcg(tasks + bt));
         // changes of this block: dedupe grid-wide, list them, queue their rows
         drain_changed(st, A, P, ph);
@@ -846,8 +945,15 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
             __syncthreads();
             for (int i = threadIdx.x; i < A.ninst; i += kThreads) {
                 InstState* I = A.inst + i;
+                // every word the decision may need, loaded at once (one round trip)
                 const int cross = __ldcg(A.i_cross + par * A.ninst + i);
                 int alive = __ldcg(&I->alive);
+                const int pending = __ldcg(&I->pending);
+                const int first_var = __ldcg(&I->first_var);
+                const unsigned long long nnz_total = __ldcg(&I->nnz_total);
+                const unsigned long long nnz_phase = __ldcg(A.i_nnz + par * A.ninst + i);
+                const int rinf = __ldcg(A.i_rowinf + par * A.ninst + i);
+                const int chg = __ldcg(A.i_chg + par * A.ninst + i);
                 if (alive) {
                     if (cross != INT_MAX) {
                         // bounds after round t-1 cross: that round is the instance's last
@@ -858,16 +964,15 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
                         I->first_row = INT_MAX;
                         alive = 0;
                     } else {
-                        I->nnz_total = __ldcg(&I->nnz_total) + __ldcg(A.i_nnz + par * A.ninst + i);
+                        I->nnz_total = nnz_total + nnz_phase;
                         I->rounds = t + 1;
                         I->result_par = npar;
-                        const int rinf = __ldcg(A.i_rowinf + par * A.ninst + i);
                         if (rinf != INT_MAX) {
                             I->status = BP_INFEASIBLE;
                             I->first_row = rinf;
                             alive = 0;
                             I->pending = 1;     // crossing check of this round's changes
-                        } else if (!__ldcg(A.i_chg + par * A.ninst + i)) {
+                        } else if (!chg) {
                             I->status = BP_FIXPOINT;
                             alive = 0;
                         } else if (t + 1 >= A.max_rounds) {
@@ -877,9 +982,9 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
                         }
                     }
                     I->alive = alive;
-                } else if (__ldcg(&I->pending)) {
+                } else if (pending) {
                     // the crossing check of the instance's last round ran in this phase
-                    if (cross != INT_MAX && cross < __ldcg(&I->first_var)) I->first_var = cross;
+                    if (cross != INT_MAX && cross < first_var) I->first_var = cross;
                     I->pending = 0;
                 }
                 if (alive) atomicOr(&st.any_alive, 1);
@@ -984,10 +1089,10 @@ int engine_prepare(mip_problem* p) {
     BP_TRY(dalloc(p, &w.list[1], (size_t)m));
     BP_TRY(dalloc(p, &w.chg[0], (size_t)n));
     BP_TRY(dalloc(p, &w.chg[1], (size_t)n));
-    BP_TRY(dalloc(p, &w.task[0], (size_t)dp.nchunks));
-    BP_TRY(dalloc(p, &w.task[1], (size_t)dp.nchunks));
-    BP_TRY(dalloc(p, &w.hpart, (size_t)dp.nchunks));
-    BP_TRY(dalloc(p, &w.hpinf, (size_t)dp.nchunks));
+    BP_TRY(dalloc(p, &w.task[0], (size_t)p->chunk_cap));
+    BP_TRY(dalloc(p, &w.task[1], (size_t)p->chunk_cap));
+    BP_TRY(dalloc(p, &w.hpart, (size_t)p->chunk_cap));
+    BP_TRY(dalloc(p, &w.hpinf, (size_t)p->chunk_cap));
     BP_TRY(dalloc(p, &w.htot, (size_t)dp.nheavy));
     BP_TRY(dalloc(p, &w.htinf, (size_t)dp.nheavy));
     BP_TRY(dalloc(p, &w.harr, (size_t)dp.nheavy));

@@ -94,9 +94,10 @@ struct mip_problem {
     int* inst_col_off = nullptr;
     void* prio_work = nullptr;                 // priority / sort scratch (created on first use)
     // row-class split points and grid shape (bp_set_tuning / bp_autotune)
-    int tune_warp_min = 2;                     // rows of 2+ nonzeros: a warp each (measured faster)
+    int tune_warp_min = gpubp::kDefaultWarpMin;
     int tune_block_min = gpubp::kWarpMax + 1;
     int sms = 0, occ_max = 0;                  // SMs and resident blocks per SM of bp_kernel
+    int chunk_cap = 0;                         // capacity of chunk-indexed arrays (smallest chunk length)
     void (*free_hooks[4])(mip_problem*) = {nullptr, nullptr, nullptr, nullptr};
 };
 
@@ -131,6 +132,8 @@ int engine_prepare(mip_problem* p);     // allocates Work
 // row classes and class lists (rclass, static_list, class_off, heavy_id) from the row lengths
 // and the handle's split points
 int classify_rows(mip_problem* p, cudaStream_t s);
+// chunk plan of the chunked rows at dp.chunk_len (static_tasks, part_off, nchunks)
+int plan_chunks(mip_problem* p, cudaStream_t s);
 
 // normalised bound keys of caller bounds (device arrays of n doubles)
 int root_keys(mip_problem* p, const double* lb, const double* ub, longlong2* out, cudaStream_t s);

@@ -122,23 +122,29 @@ __global__ void k_validate_bounds(int n, const double* lb, const double* ub, uns
 }
 
 // ---------------------------------------------------------------- layouts
-__global__ void k_rows(int m, const int64_t* rp64, const double* g, int* rp, double2* grow,
-                       unsigned char* rclass, int* chunks) {
+__global__ void k_rows(int m, const int64_t* rp64, const double* g, int* rp, double2* grow) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= m; k += gridDim.x * blockDim.x) {
         rp[k] = (int)rp64[k];
         if (k == m) continue;
-        int len = (int)(rp64[k + 1] - rp64[k]);
         double gk = g[k] >= kInfBound ? (double)INFINITY : g[k];
         grow[k] = make_double2(gk, __dadd_rn(gk, kTol));
-        int c = row_class(len);
-        rclass[k] = (unsigned char)c;
-        chunks[k] = c == kClassChunked ? (len + kChunk - 1) / kChunk : 0;
     }
 }
 
-__global__ void k_reclass(int m, const int* rp, int warp_min, int block_min, unsigned char* rclass) {
+// chunks of each chunked row at chunk length `len_c` (0 for other rows)
+__global__ void k_row_chunks(int m, const int* rp, const unsigned char* rclass, int len_c, int* chunks) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x)
-        rclass[k] = (unsigned char)row_class_tuned(rp[k + 1] - rp[k], warp_min, block_min);
+        chunks[k] = rclass[k] == kClassChunked ? (rp[k + 1] - rp[k] + len_c - 1) / len_c : 0;
+}
+
+__global__ void k_reclass(int m, const int* rp, int warp_min, int block_min, int len_c, unsigned char* rclass,
+                          int* rinfo) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+        const int len = rp[k + 1] - rp[k];
+        const int c = row_class_tuned(len, warp_min, block_min);
+        rclass[k] = (unsigned char)c;
+        rinfo[k] = c | ((c == kClassChunked ? (len + len_c - 1) / len_c : 0) << 3);
+    }
 }
 
 __global__ void k_class_flag(int m, const unsigned char* rclass, int c, int* flag) {
@@ -245,7 +251,8 @@ int classify_rows(mip_problem* p, cudaStream_t s) {
         unsigned char* rclass = const_cast<unsigned char*>(dp.rclass);
         int* list = const_cast<int*>(dp.static_list);
         int* heavy = const_cast<int*>(dp.heavy_id);
-        k_reclass<<<grid_for(m), 256, 0, s>>>(m, dp.row_ptr, p->tune_warp_min, p->tune_block_min, rclass);
+        k_reclass<<<grid_for(m), 256, 0, s>>>(m, dp.row_ptr, p->tune_warp_min, p->tune_block_min, dp.chunk_len,
+                                              rclass, const_cast<int*>(dp.rinfo));
         BP_CUDA_TRY(cudaGetLastError());
         int *flag = nullptr, *pos = nullptr, *total = nullptr;
         BP_CUDA_TRY(cudaMallocAsync(&flag, sizeof(int) * ((size_t)m + 1), s));
@@ -271,6 +278,58 @@ int classify_rows(mip_problem* p, cudaStream_t s) {
     dp.class_off[kNumClass] = base;
     dp.nheavy = counts[kClassChunked];
     return BP_OK;
+}
+
+// Chunk plan of the chunked rows at the handle's chunk length: every chunk task {row, chunk}
+// (static_tasks, the round-0 task list) and each row's first partial-sum slot (part_off).  The
+// first call sizes the task and slot arrays for the smallest chunk length, so that later plans
+// (bp_set_tuning) fit: ceil(len / kChunkMin) <= (kChunk / kChunkMin) ceil(len / kChunk).
+int plan_chunks(mip_problem* p, cudaStream_t s) {
+    DevProblem& dp = p->dp;
+    const int m = p->m;
+    int *chunks = nullptr, *pos = nullptr, *total = nullptr;
+    const size_t words = (size_t)m + 1;
+    BP_CUDA_TRY(cudaMallocAsync(&chunks, sizeof(int) * words, s));
+    BP_CUDA_TRY(cudaMallocAsync(&pos, sizeof(int) * words, s));
+    BP_CUDA_TRY(cudaMallocAsync(&total, sizeof(int), s));
+    auto count = [&](int len_c, int* out) -> int {
+        *out = 0;
+        if (!m) return BP_OK;
+        k_row_chunks<<<grid_for(m), 256, 0, s>>>(m, dp.row_ptr, dp.rclass, len_c, chunks);
+        BP_CUDA_TRY(cudaGetLastError());
+        BP_TRY(scan_exclusive(chunks, pos, m, total, s));
+        BP_CUDA_TRY(cudaMemcpyAsync(out, total, sizeof(int), cudaMemcpyDeviceToHost, s));
+        BP_CUDA_TRY(cudaStreamSynchronize(s));
+        return BP_OK;
+    };
+    int rc = BP_OK;
+    if (p->chunk_cap == 0) {
+        int n_max = 0;
+        rc = count(kChunk, &n_max);
+        if (rc == BP_OK) {
+            p->chunk_cap = (kChunk / kChunkMin) * n_max;
+            int2* tasks = nullptr;
+            int* part_off = nullptr;
+            rc = dalloc(p, &tasks, (size_t)p->chunk_cap);
+            if (rc == BP_OK) rc = dalloc(p, &part_off, (size_t)dp.nheavy + 1);
+            dp.static_tasks = tasks;
+            dp.part_off = part_off;
+        }
+    }
+    int nchunks = 0;
+    if (rc == BP_OK) rc = count(dp.chunk_len, &nchunks);
+    if (rc == BP_OK) {
+        dp.nchunks = nchunks;
+        if (m) {
+            k_heavy_tasks<<<grid_for(m), 256, 0, s>>>(m, dp.rclass, chunks, pos, const_cast<int2*>(dp.static_tasks));
+            k_heavy_part_off<<<grid_for(m), 256, 0, s>>>(m, dp.rclass, dp.heavy_id, pos, const_cast<int*>(dp.part_off),
+                                                         nchunks, dp.nheavy);
+            if (cudaGetLastError() != cudaSuccess) rc = BP_ERR_CUDA;
+        }
+    }
+    for (void* q : {(void*)chunks, (void*)pos, (void*)total}) cudaFreeAsync(q, s);
+    BP_CUDA_TRY(cudaStreamSynchronize(s));
+    return rc;
 }
 
 static int load_impl(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
@@ -356,42 +415,28 @@ static int load_impl(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t
     dp.m = m;
     dp.n = n;
     dp.nnz = (int)nnz;
-    int *d_rp, *d_chunks, *d_list, *d_heavy, *d_total;
+    int *d_rp, *d_list, *d_heavy;
     double2* d_grow;
     unsigned char* d_rclass;
     BP_TRY(dalloc(p, &d_rp, (size_t)m + 1));
     BP_TRY(dalloc(p, &d_grow, (size_t)m));
     BP_TRY(dalloc(p, &d_rclass, (size_t)m));
-    BP_TRY(dalloc(p, &d_chunks, (size_t)m));
     BP_TRY(dalloc(p, &d_list, (size_t)m));
     BP_TRY(dalloc(p, &d_heavy, (size_t)m));
-    BP_TRY(dalloc(p, &d_total, 1));
     BP_CUDA_TRY(cudaMemsetAsync(d_heavy, 0xff, sizeof(int) * (m ? m : 1), s));
-    k_rows<<<grid_for(m + 1), 256, 0, s>>>(m, d_rp64, d_g, d_rp, d_grow, d_rclass, d_chunks);
+    k_rows<<<grid_for(m + 1), 256, 0, s>>>(m, d_rp64, d_g, d_rp, d_grow);
     BP_CUDA_TRY(cudaGetLastError());
+    int* d_rinfo;
+    BP_TRY(dalloc(p, &d_rinfo, (size_t)m));
     dp.row_ptr = d_rp;
     dp.rclass = d_rclass;
+    dp.rinfo = d_rinfo;
     dp.heavy_id = d_heavy;
     dp.static_list = d_list;
+    dp.chunk_len = kDefaultChunkLen;
     BP_TRY(classify_rows(p, s));
     // chunk plan
-    int* d_chunk_pos;
-    BP_TRY(dalloc(p, &d_chunk_pos, (size_t)m + 1));
-    int nchunks = 0;
-    if (m) {
-        BP_TRY(scan_exclusive(d_chunks, d_chunk_pos, m, d_total, s));
-        BP_CUDA_TRY(cudaMemcpyAsync(&nchunks, d_total, sizeof(int), cudaMemcpyDeviceToHost, s));
-        BP_CUDA_TRY(cudaStreamSynchronize(s));
-    }
-    dp.nchunks = nchunks;
-    int2* d_tasks;
-    int* d_part_off;
-    BP_TRY(dalloc(p, &d_tasks, (size_t)nchunks));
-    BP_TRY(dalloc(p, &d_part_off, (size_t)dp.nheavy + 1));
-    if (m) {
-        k_heavy_tasks<<<grid_for(m), 256, 0, s>>>(m, d_rclass, d_chunks, d_chunk_pos, d_tasks);
-        k_heavy_part_off<<<grid_for(m), 256, 0, s>>>(m, d_rclass, d_heavy, d_chunk_pos, d_part_off, nchunks, dp.nheavy);
-    }
+    BP_TRY(plan_chunks(p, s));
     // transpose
     int *d_colcnt, *d_colptr, *d_fill, *d_rowidx;
     double* d_colval;
@@ -436,8 +481,6 @@ static int load_impl(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t
     dp.row_idx = d_rowidx;
     dp.col_val = d_colval;
     dp.is_int = d_isint;
-    dp.part_off = d_part_off;
-    dp.static_tasks = d_tasks;
     BP_TRY(engine_prepare(p));
     BP_CUDA_TRY(cudaStreamSynchronize(s));
     return BP_OK;

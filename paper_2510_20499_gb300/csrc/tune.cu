@@ -17,17 +17,23 @@ using namespace gpubp;
 
 namespace {
 
+bool chunk_len_valid(int c) { return c == 256 || c == 512 || c == 1024 || c == kChunk; }
+
 bool tuning_valid(const mip_problem* p, const bp_tuning* t) {
     return t->warp_min >= 2 && t->warp_min <= kThreadMax + 1 && t->block_min >= t->warp_min &&
-           t->block_min <= kWarpMax + 1 && t->blocks_per_sm >= 1 && t->blocks_per_sm <= p->occ_max;
+           t->block_min <= kWarpMax + 1 && t->blocks_per_sm >= 1 && t->blocks_per_sm <= p->occ_max &&
+           chunk_len_valid(t->chunk_len);
 }
 
 int apply(mip_problem* p, const bp_tuning* t, cudaStream_t s) {
-    const bool reclass = t->warp_min != p->tune_warp_min || t->block_min != p->tune_block_min;
+    const bool rechunk = t->chunk_len != p->dp.chunk_len;
+    const bool reclass = rechunk || t->warp_min != p->tune_warp_min || t->block_min != p->tune_block_min;
     p->tune_warp_min = t->warp_min;
     p->tune_block_min = t->block_min;
+    p->dp.chunk_len = t->chunk_len;
     p->grid_blocks = p->sms * t->blocks_per_sm;
-    if (reclass) BP_TRY(classify_rows(p, s));
+    if (reclass) BP_TRY(classify_rows(p, s));   // row classes and chunk counts per row
+    if (rechunk) BP_TRY(plan_chunks(p, s));     // chunk tasks and partial-sum slots
     return BP_OK;
 }
 
@@ -52,7 +58,7 @@ extern "C" int bp_get_tuning(const mip_problem* p, bp_tuning* out) {
     out->warp_min = p->tune_warp_min;
     out->block_min = p->tune_block_min;
     out->blocks_per_sm = p->sms ? p->grid_blocks / p->sms : 0;
-    out->reserved = 0;
+    out->chunk_len = p->dp.chunk_len;
     return BP_OK;
 }
 
@@ -62,9 +68,10 @@ extern "C" int bp_set_tuning(mip_problem* p, const bp_tuning* t, void* stream) {
         return BP_ERR_INVALID;
     }
     if (!tuning_valid(p, t)) {
-        set_error("bp_set_tuning: need 2 <= warp_min <= %d, warp_min <= block_min <= %d, 1 <= blocks_per_sm <= %d "
-                  "(got %d, %d, %d)",
-                  kThreadMax + 1, kWarpMax + 1, p->occ_max, t->warp_min, t->block_min, t->blocks_per_sm);
+        set_error("bp_set_tuning: need 2 <= warp_min <= %d, warp_min <= block_min <= %d, 1 <= blocks_per_sm <= %d, "
+                  "chunk_len in {256, 512, 1024, %d} (got %d, %d, %d, %d)",
+                  kThreadMax + 1, kWarpMax + 1, p->occ_max, kChunk, t->warp_min, t->block_min, t->blocks_per_sm,
+                  t->chunk_len);
         return BP_ERR_INVALID;
     }
     cudaStream_t s = (cudaStream_t)stream;
@@ -129,33 +136,37 @@ extern "C" int bp_autotune(mip_problem* p, const double* lb, const double* ub, c
 
     bp_tune_report rep;
     memset(&rep, 0, sizeof(rep));
-    const bp_tuning defaults{2, kWarpMax + 1, p->occ_max, 0};
+    const bp_tuning defaults{kDefaultWarpMin, kWarpMax + 1, p->occ_max, kDefaultChunkLen};
     std::vector<bp_result> ref, cur;
     int rc = measure(defaults, &rep.default_ms, &ref);
     rep.best = defaults;
     rep.best_ms = rep.default_ms;
     rep.tried = 1;
-    static const int kWarpMins[] = {2, 5, kThreadMax + 1};
-    static const int kBlockMins[] = {65, 129, kWarpMax + 1};
+    static const int kWarpMins[] = {2, kThreadMax + 1};
+    static const int kBlockMins[] = {65, kWarpMax + 1};
+    static const int kChunkLens[] = {256, 512, 1024, kChunk};
     for (int bps = 1; rc == BP_OK && bps <= p->occ_max; ++bps)
         for (int wm : kWarpMins)
-            for (int bm : kBlockMins) {
-                if (rc != BP_OK) break;
-                const bp_tuning t{wm, bm, bps, 0};
-                if (wm == defaults.warp_min && bm == defaults.block_min && bps == defaults.blocks_per_sm) continue;
-                float ms = 0.f;
-                rc = measure(t, &ms, &cur);
-                if (rc != BP_OK) break;
-                ++rep.tried;
-                if (!same_results(ref, cur)) {
-                    ++rep.rejected;
-                    continue;
+            for (int bm : kBlockMins)
+                for (int cl : kChunkLens) {
+                    if (rc != BP_OK) break;
+                    const bp_tuning t{wm, bm, bps, cl};
+                    if (wm == defaults.warp_min && bm == defaults.block_min && bps == defaults.blocks_per_sm &&
+                        cl == defaults.chunk_len)
+                        continue;
+                    float ms = 0.f;
+                    rc = measure(t, &ms, &cur);
+                    if (rc != BP_OK) break;
+                    ++rep.tried;
+                    if (!same_results(ref, cur)) {
+                        ++rep.rejected;
+                        continue;
+                    }
+                    if (ms < rep.best_ms) {
+                        rep.best_ms = ms;
+                        rep.best = t;
+                    }
                 }
-                if (ms < rep.best_ms) {
-                    rep.best_ms = ms;
-                    rep.best = t;
-                }
-            }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != BP_OK) {

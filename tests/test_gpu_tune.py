@@ -19,7 +19,8 @@ def pkg():
     return pkg
 
 
-CONFIGS = [(9, 257, 2), (2, 2, 2), (2, 65, 1), (5, 129, 2), (9, 9, 1), (5, 257, 1), (2, 257, 2), (9, 65, 2)]
+CONFIGS = [(9, 257, 2, 2048), (2, 2, 2, 2048), (2, 65, 1, 512), (5, 129, 2, 1024), (9, 9, 1, 256),
+           (5, 257, 1, 2048), (2, 257, 2, 256), (9, 65, 2, 512), (2, 257, 1, 1024)]
 
 
 def exact_problems():
@@ -34,10 +35,10 @@ def exact_problems():
 def test_defaults(pkg):
     prob = pkg.Problem(synth.binary_knapsack())
     t = prob.get_tuning()
-    assert t["warp_min"] == 2 and t["block_min"] == 257 and t["blocks_per_sm"] >= 1
+    assert t["warp_min"] == 2 and t["block_min"] == 257 and t["blocks_per_sm"] >= 1 and t["chunk_len"] == 2048
 
 
-@pytest.mark.parametrize("cfg", CONFIGS, ids=[f"w{c[0]}-b{c[1]}-g{c[2]}" for c in CONFIGS])
+@pytest.mark.parametrize("cfg", CONFIGS, ids=[f"w{c[0]}-b{c[1]}-g{c[2]}-c{c[3]}" for c in CONFIGS])
 def test_every_configuration_matches_oracle(pkg, cfg):
     for p in exact_problems():
         lb, ub = synth.tighten_random(7, p, 12, planted=True)
@@ -46,7 +47,7 @@ def test_every_configuration_matches_oracle(pkg, cfg):
         if cfg[2] > prob.get_tuning()["blocks_per_sm"]:
             pytest.skip("fewer resident blocks per SM on this device")
         prob.set_tuning(*cfg)
-        assert prob.get_tuning() == dict(warp_min=cfg[0], block_min=cfg[1], blocks_per_sm=cfg[2])
+        assert prob.get_tuning() == dict(warp_min=cfg[0], block_min=cfg[1], blocks_per_sm=cfg[2], chunk_len=cfg[3])
         gl, gu, gr = run_gpu(prob, lb, ub)
         assert compare(p, gl, gu, gr, ol, ou, orr), "oracle saw a fragile decision on exact data"
 
@@ -54,7 +55,8 @@ def test_every_configuration_matches_oracle(pkg, cfg):
 def test_invalid_tuning_rejected(pkg):
     prob = pkg.Problem(synth.binary_knapsack())
     bps = prob.get_tuning()["blocks_per_sm"]
-    for bad in [(1, 257, 1), (10, 257, 1), (9, 8, 1), (9, 258, 1), (9, 257, 0), (9, 257, bps + 1)]:
+    for bad in [(1, 257, 1, 2048), (10, 257, 1, 2048), (9, 8, 1, 2048), (9, 258, 1, 2048), (9, 257, 0, 2048),
+                (9, 257, bps + 1, 2048), (9, 257, 1, 300), (9, 257, 1, 4096), (9, 257, 1, 128)]:
         with pytest.raises(pkg.GpuBpError) as e:
             prob.set_tuning(*bad)
         assert e.value.code == pkg.BP_ERR_INVALID
@@ -68,7 +70,7 @@ def test_autotune_single_keeps_results(pkg):
     ol, ou, orr, _ = oracle.Problem(p).bp(p.lb, p.ub)
     before = run_gpu(prob, p.lb, p.ub)
     rep = prob.autotune(torch.tensor(p.lb, device="cuda"), torch.tensor(p.ub, device="cuda"), reps=2)
-    assert rep["tried"] >= 9 and rep["best_ms"] <= rep["default_ms"]
+    assert rep["tried"] >= 16 and rep["best_ms"] <= rep["default_ms"]
     assert prob.get_tuning() == rep["best"]
     after = run_gpu(prob, p.lb, p.ub)
     assert after[2] == before[2]
@@ -88,7 +90,7 @@ def test_autotune_batch_keeps_results(pkg):
     r0 = pkg.batch_results(prob.propagate_batch(lb, ub))
     b0 = (lb.cpu().numpy(), ub.cpu().numpy())
     rep = prob.autotune(lb0, ub0, reps=2)
-    assert rep["tried"] >= 9
+    assert rep["tried"] >= 16
     lb, ub = lb0.clone(), ub0.clone()
     r1 = pkg.batch_results(prob.propagate_batch(lb, ub))
     assert r1 == r0
