@@ -17,7 +17,7 @@ import subprocess
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["bp_oracle.c", "fp_oracle.c", "mlp_oracle.c"]
+SOURCES = ["bp_oracle.c", "fp_oracle.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 
 FIXPOINT, INFEASIBLE, ROUND_LIMIT = 0, 1, 2
