@@ -403,6 +403,83 @@ int fix_and_propagate(mip_problem *p, const double *x, const double *lb, const d
                       const fp_cache *cache, const fp_params *params, double *x_out,
                       fp_result *result, void *stream);
 
+/* ------------------------------------------------------------ learned scorer */
+/*
+ * A 16-64-64-2 multilayer perceptron (ReLU) that re-ranks the integer variables of
+ * fix_and_propagate and proposes the rounding direction of ambiguous fractions.  The paper
+ * has no counterpart; it only changes the order and the draw probabilities that
+ * fix_and_propagate already takes (fp_params.order_score, fp_params.up_prob), and propagation
+ * still judges every fixing.
+ *
+ * Arithmetic: BF16 operands on the tensor cores (tcgen05) with FP32 accumulation.  Features,
+ * hidden activations and back-propagated pre-activation gradients are rounded to BF16 (nearest,
+ * ties to even); weights are FP32 masters rounded to BF16 for the products; biases, logits,
+ * the output-layer gradient and all sums stay FP32.
+ *
+ * Parameters (SCORER_NPARAM floats): W1 [64 x 16], b1 [64], W2 [64 x 64], b2 [64], W3 [2 x 64],
+ * b3 [2]; each weight matrix [out x in], row-major.  Output 0 is the order score (a logit:
+ * larger = fixed earlier within its class), output 1 the logit of rounding up.
+ * A scorer lives on the device that was current at scorer_create; one scorer must not be used
+ * by two calls at once.
+ */
+#define SCORER_IN 16
+#define SCORER_HIDDEN 64
+#define SCORER_OUT 2
+#define SCORER_NPARAM 5378
+typedef struct scorer scorer;
+
+/* Creates a scorer with He-uniform weights (parameter i of matrix L: (2u - 1) sqrt(6 / fan_in),
+ * u the splitmix64 uniform of (seed, 1000 + L, i, 0)) and zero biases.  Only in=16, hidden=64,
+ * out=2 is built (BP_ERR_INVALID otherwise). */
+int scorer_create(int32_t in, int32_t hidden, int32_t out, uint64_t seed, scorer **out_scorer);
+void scorer_free(scorer *s);
+
+/* Host copies of the parameter vector; set_params also resets the Adam state. */
+int scorer_get_params(const scorer *s, float *host_params);
+int scorer_set_params(scorer *s, const float *host_params);
+
+/*
+ * scorer_features -- the 16 features of variables vars[0..nvars) (DEVICE int32), standardised
+ * over those variables (mean 0, population standard deviation 1; a constant feature becomes 0)
+ * and rounded to BF16, into feat (DEVICE, nvars x 16 BF16 bit patterns, row-major).  In order:
+ * degree, log(1 + degree), objective coefficient, up locks (positive coefficients), down locks,
+ * log(1 + min(u - l, 1e9)), binary (integer with u - l <= 1), integer, frac(x), |frac(x) - 0.5|,
+ * probing-cache implications of the down and up branch, down and up branch infeasible, the
+ * implied slack sum S_i of the Section 2.3 rounding order (rows with no infinite term,
+ * slack = max(g - L_min, 1e-6)) and the sum of |a| over the column.  x, lb, ub: DEVICE double[n];
+ * cache: NULL or a probing cache (its first pair of a variable counts).  Asynchronous.
+ */
+int scorer_features(mip_problem *p, const double *x, const double *lb, const double *ub,
+                    const fp_cache *cache, const int32_t *vars, int32_t nvars, uint16_t *feat,
+                    void *stream);
+
+/* Logits of rows x 16 BF16 features (DEVICE) into out (DEVICE float, rows x 2).  Asynchronous. */
+int scorer_forward(scorer *s, const uint16_t *feat, int32_t rows, float *out, void *stream);
+
+/* scorer_forward into logits (DEVICE float, rows x 2), then order_score[vars[r]] = logit 0
+ * and up_prob[vars[r]] = sigmoid(logit 1) (DEVICE double[n] each, either may be NULL): the
+ * fp_params inputs of fix_and_propagate.  Asynchronous. */
+int scorer_scores(scorer *s, const uint16_t *feat, const int32_t *vars, int32_t rows, float *logits,
+                  double *order_score, double *up_prob, void *stream);
+
+/*
+ * Loss of a batch and its gradient: binary cross-entropy with logits per output, averaged over
+ * that output's labels; labels: DEVICE float, rows x 2, NaN = no label.  scorer_gradient copies
+ * the gradient (SCORER_NPARAM floats) and the loss to host memory (either may be NULL) and
+ * synchronises; scorer_train_step then takes one Adam step (beta 0.9 / 0.999, eps 1e-8,
+ * bias-corrected, learning rate lr > 0) and, when loss is not NULL, synchronises to return it.
+ * Returns BP_ERR_TIMEOUT if a tensor-core wait gave up.
+ */
+int scorer_gradient(scorer *s, const uint16_t *feat, const float *labels, int32_t rows,
+                    float *grad, float *loss, void *stream);
+int scorer_train_step(scorer *s, const uint16_t *feat, const float *labels, int32_t rows, float lr,
+                      float *loss, void *stream);
+
+/* Parameters to / from a file (magic "GPUBPML1", the three sizes and the count, then the
+ * floats, little-endian). */
+int scorer_save(const scorer *s, const char *path);
+int scorer_load(scorer *s, const char *path);
+
 /* ------------------------------------------------------------------- errors */
 
 /* Thread-local message of the last error ("" if none). */

@@ -97,6 +97,21 @@ SIGNATURES = {
     "bp_propagate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(BpParams), C.POINTER(BpResult),
                                C.c_void_p]),
     "bp_result_device": (C.c_void_p, [C.c_void_p]),
+    "scorer_create": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(C.c_void_p)]),
+    "scorer_free": (None, [C.c_void_p]),
+    "scorer_get_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "scorer_set_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "scorer_features": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_int32, C.c_void_p, C.c_void_p]),
+    "scorer_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "scorer_scores": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                C.c_void_p, C.c_void_p]),
+    "scorer_gradient": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                  C.c_void_p]),
+    "scorer_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_void_p,
+                                    C.c_void_p]),
+    "scorer_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "scorer_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "bp_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(BpTuning)]),
     "bp_set_tuning": (C.c_int, [C.c_void_p, C.POINTER(BpTuning), C.c_void_p]),
     "bp_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(BpParams), C.c_int32,
@@ -304,11 +319,7 @@ def _fix_and_propagate(prob, x, lb, ub, seed=1, bulk_rule=0, fraction=0.01, last
     prm.theta, prm.max_rounds = float(theta), int(max_rounds)
     prm.order_score = order_score.data_ptr() if order_score is not None else None
     prm.up_prob = up_prob.data_ptr() if up_prob is not None else None
-    fc = None
-    if cache is not None:
-        fc = FpCache(int(cache["pairs"].numel()), 0, cache["pairs"].data_ptr(), cache["boxes"].data_ptr(),
-                     cache["status"].data_ptr(), cache["offsets"].data_ptr(), cache["var"].data_ptr(),
-                     cache["l"].data_ptr(), cache["u"].data_ptr())
+    fc = _fp_cache_struct(cache) if cache is not None else None
     out = torch.empty_like(x)
     res = FpResult()
     _check(lib().fix_and_propagate(prob.h, _ptr(x), _ptr(lb), _ptr(ub), C.byref(fc) if fc is not None else None,
@@ -395,6 +406,90 @@ def _autotune(prob, lb, ub, reps=3, theta=1e-3, max_rounds=10000, stream=None):
     return rep.as_dict()
 
 
+def _fp_cache_struct(cache):
+    return FpCache(int(cache["pairs"].numel()), 0, cache["pairs"].data_ptr(), cache["boxes"].data_ptr(),
+                   cache["status"].data_ptr(), cache["offsets"].data_ptr(), cache["var"].data_ptr(),
+                   cache["l"].data_ptr(), cache["u"].data_ptr())
+
+
+def _scorer_features(prob, x, lb, ub, vars_, cache=None, stream=None):
+    """scorer_features: BF16 features (torch.bfloat16, nvars x 16) of the variables vars_
+    (int32 device tensor) under device bounds lb/ub and point x.  cache: as for
+    fix_and_propagate (probe_batch's dict plus 'pairs' and 'boxes') or None."""
+    torch = _torch()
+    nv = int(vars_.numel())
+    feat = torch.empty((nv, 16), dtype=torch.bfloat16, device=prob.device)
+    fc = _fp_cache_struct(cache) if cache is not None else None
+    _check(lib().scorer_features(prob.h, _ptr(x), _ptr(lb), _ptr(ub), C.byref(fc) if fc is not None else None,
+                                 _ptr(vars_), nv, _ptr(feat), _stream(stream)))
+    return feat
+
+
+class Scorer:
+    """The learned rounding scorer (16-64-64-2 MLP on the tensor cores)."""
+
+    NPARAM = 5378
+
+    def __init__(self, seed=1):
+        h = C.c_void_p()
+        _check(lib().scorer_create(16, 64, 2, int(seed), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().scorer_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        out = np.zeros(self.NPARAM, dtype=np.float32)
+        _check(lib().scorer_get_params(self.h, C.c_void_p(out.ctypes.data)))
+        return out
+
+    def set_params(self, theta):
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        assert t.size == self.NPARAM
+        _check(lib().scorer_set_params(self.h, C.c_void_p(t.ctypes.data)))
+
+    def forward(self, feat, stream=None):
+        torch = _torch()
+        out = torch.empty((feat.shape[0], 2), dtype=torch.float32, device=feat.device)
+        _check(lib().scorer_forward(self.h, _ptr(feat), int(feat.shape[0]), _ptr(out), _stream(stream)))
+        return out
+
+    def scores(self, feat, vars_, order_score=None, up_prob=None, stream=None):
+        torch = _torch()
+        logits = torch.empty((feat.shape[0], 2), dtype=torch.float32, device=feat.device)
+        _check(lib().scorer_scores(self.h, _ptr(feat), _ptr(vars_), int(feat.shape[0]), _ptr(logits),
+                                   _ptr(order_score), _ptr(up_prob), _stream(stream)))
+        return logits
+
+    def gradient(self, feat, labels, stream=None):
+        g = np.zeros(self.NPARAM, dtype=np.float32)
+        loss = C.c_float(0.0)
+        _check(lib().scorer_gradient(self.h, _ptr(feat), _ptr(labels), int(feat.shape[0]),
+                                     C.c_void_p(g.ctypes.data), C.byref(loss), _stream(stream)))
+        return g, float(loss.value)
+
+    def train_step(self, feat, labels, lr, stream=None):
+        loss = C.c_float(0.0)
+        _check(lib().scorer_train_step(self.h, _ptr(feat), _ptr(labels), int(feat.shape[0]), float(lr),
+                                       C.byref(loss), _stream(stream)))
+        return float(loss.value)
+
+    def save(self, path):
+        _check(lib().scorer_save(self.h, str(path).encode()))
+
+    def load(self, path):
+        _check(lib().scorer_load(self.h, str(path).encode()))
+
+
+Problem.scorer_features = _scorer_features
 Problem.get_tuning = _get_tuning
 Problem.set_tuning = _set_tuning
 Problem.autotune = _autotune
