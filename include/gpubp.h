@@ -330,8 +330,10 @@ int bp_autotune(mip_problem *p, const double *lb, const double *ub, const bp_par
 /* Parameters of fix_and_propagate.  seed: key of the counter-based random draws.
  * last_single: the last variables are fixed one at a time (36 in the paper, Section 2.3).
  * theta, max_rounds: as in bp_params, for every propagation.
- * order_score (DEVICE double[n] or NULL): when given, the initial order ranks variables by
- *   class (binary, ternary, rest), then descending score, then fractionality, then index.
+ * order_score (DEVICE double[n] or NULL): when given, the integer variables are ranked by
+ *   class (binary, ternary, rest), then descending score, then fractionality, then index, and
+ *   every bulk takes the unfixed variables in that order: the score replaces the per-bulk
+ *   implied-slack sort (NULL keeps the paper's order).
  * up_prob (DEVICE double[n] or NULL): when given, replaces the rounding distribution's
  *   probability of rounding up for fractions strictly between 0.25 and 0.75 (the random band);
  *   outside the band the nearest value is always drawn.  Propagation still judges every fix. */
@@ -474,6 +476,19 @@ int scorer_gradient(scorer *s, const uint16_t *feat, const float *labels, int32_
                     float *grad, float *loss, void *stream);
 int scorer_train_step(scorer *s, const uint16_t *feat, const float *labels, int32_t rows, float lr,
                       float *loss, void *stream);
+
+/*
+ * scorer_labels -- training labels from fix_and_propagate trajectories (no counterpart in the
+ * paper).  Adds the outcome of one run that ended FP_FEASIBLE, with weight `weight` (1 / the
+ * number of such runs gives shares), to labels (DEVICE float, nvars x 2) of the variables
+ * vars[0..nvars) (DEVICE int32): column 0 += weight when the run fixed the variable to the
+ * nearest integer of x, floor(x + 1/2) (the order label), column 1 += weight when it fixed it
+ * above x (the rounding-direction label).  first != 0 starts the sums: column 0 at 0, column 1
+ * at 0, or at NaN (no label) where x is integral.  x, x_out: DEVICE double[n] (x_out as written
+ * by fix_and_propagate).  Asynchronous; BP_ERR_INVALID for null or negative arguments.
+ */
+int scorer_labels(const double *x, const double *x_out, const int32_t *vars, int32_t nvars, float weight,
+                  int32_t first, float *labels, void *stream);
 
 /* Parameters to / from a file (magic "GPUBPML1", the three sizes and the count, then the
  * floats, little-endian). */

@@ -14,7 +14,9 @@
  *       at a time for the last `last_single` (36 in the paper) and in recovery;
  *     - for bulks larger than one, a stable implied-slack sort of the unfixed variables:
  *       S_i = sum over rows with a finite minimal activity of (a / slack)^2,
- *       slack = max(g - L_min, tol), descending (Section 2.3 equation);
+ *       slack = max(g - L_min, tol), descending (Section 2.3 equation); with a learned order
+ *       score (no counterpart in the paper) the score ranks the variables within their class
+ *       instead and the implied-slack sort is skipped;
  *     - two candidate values per variable drawn from the rounding distribution (random near
  *       .5, nearest away from .5: P(up) = 0 for f <= .25, 1 for f >= .75, linear between);
  *       single-variable bulks try the drawn value and the other integer neighbour;
@@ -49,7 +51,8 @@ typedef struct {
     int32_t last_single;
     double theta;
     int32_t max_rounds;
-    const double *order_score;  /* optional: initial order by class, descending score, fractionality, index */
+    const double *order_score;  /* optional: order by class, descending score, fractionality, index; no
+                                 * per-bulk implied-slack sort */
     const double *up_prob;      /* optional: P(up) for fractions strictly inside (0.25, 0.75) */
 } orc_fp_params;
 
@@ -279,7 +282,9 @@ int orc_fix_and_propagate(const orc_problem *p, const double *x, const double *l
                 if (bsize < 1) bsize = 1;
             }
             if (bsize > nun) bsize = nun;
-            if (bsize > 1) {
+            /* a learned order score replaces the per-bulk implied-slack order: the bulks then
+             * follow the initial order (class, score, fractionality, index) */
+            if (bsize > 1 && !prm->order_score) {
                 implied_slack(p, l, u, S);
                 merge_sort(work, tmp, nun, &ctx, cmp_slack);
             }

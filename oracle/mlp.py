@@ -224,3 +224,27 @@ def standardize(F):
 
 def features(p, x, lb, ub, vars_, cache=None):
     return standardize(raw_features(p, x, lb, ub, vars_, cache))
+
+
+# ------------------------------------------------------------------------------- labels
+def trajectory_labels(x, x_outs, vars_):
+    """Training labels of the variables `vars_` from the results x_out of fix-and-propagate runs
+    that ended feasible (all integer variables fixed, propagation feasible).  Column 0: the share
+    of runs that fixed the variable to the nearest integer of x, floor(x + 1/2) (the order label:
+    a variable whose nearest value holds is fixed early).  Column 1: the share of runs that fixed
+    it above x (the rounding-direction label); NaN (no label) where x is integral.  With no run
+    both columns are NaN."""
+    v = np.asarray(vars_, dtype=np.int64)
+    xv = np.asarray(x, dtype=np.float64)[v]
+    Y = np.zeros((len(v), 2))
+    if len(x_outs) == 0:
+        Y[:] = np.nan
+        return Y
+    w = 1.0 / len(x_outs)
+    near = np.floor(xv + 0.5)
+    for xo in x_outs:
+        fixed = np.asarray(xo, dtype=np.float64)[v]
+        Y[:, 0] += w * (fixed == near)
+        Y[:, 1] += w * (fixed > xv)
+    Y[xv == np.floor(xv), 1] = np.nan
+    return Y

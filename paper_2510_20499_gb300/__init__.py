@@ -110,6 +110,8 @@ SIGNATURES = {
                                   C.c_void_p]),
     "scorer_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_void_p,
                                     C.c_void_p]),
+    "scorer_labels": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_int32, C.c_void_p,
+                                C.c_void_p]),
     "scorer_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "scorer_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "bp_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(BpTuning)]),
@@ -211,6 +213,7 @@ class Problem:
                                   _stream(stream), C.byref(h)))
         self.h = h
         self.device = dev
+        self.int_vars = np.flatnonzero(np.asarray(milp.is_int) != 0).astype(np.int32)   # host copy
 
     def close(self):
         if getattr(self, "h", None):
@@ -476,17 +479,27 @@ class Scorer:
                                      C.c_void_p(g.ctypes.data), C.byref(loss), _stream(stream)))
         return g, float(loss.value)
 
-    def train_step(self, feat, labels, lr, stream=None):
+    def train_step(self, feat, labels, lr, stream=None, want_loss=True):
+        """One Adam step; returns the batch loss (the call then synchronises), or None with
+        want_loss=False (asynchronous)."""
         loss = C.c_float(0.0)
         _check(lib().scorer_train_step(self.h, _ptr(feat), _ptr(labels), int(feat.shape[0]), float(lr),
-                                       C.byref(loss), _stream(stream)))
-        return float(loss.value)
+                                       C.byref(loss) if want_loss else None, _stream(stream)))
+        return float(loss.value) if want_loss else None
 
     def save(self, path):
         _check(lib().scorer_save(self.h, str(path).encode()))
 
     def load(self, path):
         _check(lib().scorer_load(self.h, str(path).encode()))
+
+
+def scorer_labels(x, x_out, vars_, labels, weight=1.0, first=False, stream=None):
+    """scorer_labels: adds one feasible fix_and_propagate result x_out to the labels
+    (float32 device tensor, nvars x 2) of the variables vars_ (int32 device tensor)."""
+    _check(lib().scorer_labels(_ptr(x), _ptr(x_out), _ptr(vars_), int(vars_.numel()), float(weight),
+                               1 if first else 0, _ptr(labels), _stream(stream)))
+    return labels
 
 
 Problem.scorer_features = _scorer_features

@@ -462,7 +462,8 @@ extern "C" int fix_and_propagate(mip_problem* p, const double* x, const double* 
                 if (bsize < 1) bsize = 1;
             }
             if (bsize > nun) bsize = nun;
-            if (bsize > 1) {
+            // a learned order score replaces the per-bulk implied-slack order
+            if (bsize > 1 && !prm.order_score) {
                 if (p->m) k_row_act<<<gridn((long long)p->m * 32), 256, 0, s>>>(p->dp, Bl, Bu, rmin, rninf);
                 k_implied_slack<<<gridn(nun), 256, 0, s>>>(p->dp, nun, work, rmin, rninf, keys);
                 FP_TRY(radix_sort_pairs(keys, work, tkeys, twork, nun, 0, 64, s));

@@ -567,6 +567,22 @@ __global__ void k_scores(const float* z, const int* vars, int rows, double* orde
     }
 }
 
+// labels of one feasible trajectory (see scorer_labels)
+__global__ void k_labels(const double* x, const double* x_out, const int* vars, int nvars, float w, int first,
+                         float* labels) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nvars; r += gridDim.x * blockDim.x) {
+        const int j = vars[r];
+        const double xj = x[j], fixed = x_out[j];
+        const double fl = floor(xj);
+        float y0 = first ? 0.0f : labels[2 * (size_t)r];
+        float y1 = first ? (xj == fl ? __int_as_float(0x7fc00000) : 0.0f) : labels[2 * (size_t)r + 1];
+        if (fixed == floor(__dadd_rn(xj, 0.5))) y0 += w;
+        if (fixed > xj) y1 += w;      // NaN stays NaN
+        labels[2 * (size_t)r] = y0;
+        labels[2 * (size_t)r + 1] = y1;
+    }
+}
+
 int grid_for(long long work) {
     long long b = (work + 255) / 256;
     return (int)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
@@ -816,6 +832,18 @@ extern "C" int scorer_features(mip_problem* p, const double* x, const double* lb
     BP_CUDA_TRY(cudaGetLastError());
     for (void* q : {(void*)minfin, (void*)ninf, (void*)raw, (void*)stats, (void*)pair_of})
         if (q) BP_CUDA_TRY(cudaFreeAsync(q, st));
+    return BP_OK;
+}
+
+extern "C" int scorer_labels(const double* x, const double* x_out, const int32_t* vars, int32_t nvars, float weight,
+                             int32_t first, float* labels, void* stream) {
+    if (nvars < 0 || (nvars && (!x || !x_out || !vars || !labels))) {
+        set_error("scorer_labels: null or negative argument");
+        return BP_ERR_INVALID;
+    }
+    if (nvars == 0) return BP_OK;
+    k_labels<<<grid_for(nvars), 256, 0, (cudaStream_t)stream>>>(x, x_out, vars, nvars, weight, first ? 1 : 0, labels);
+    BP_CUDA_TRY(cudaGetLastError());
     return BP_OK;
 }
 

@@ -117,3 +117,26 @@ def test_general_data_soundness(pkg):
             # continuous variables are only clamped (no LP polish); check the integer part's rows
             # against the continuous variables' final ranges by the propagated bounds being feasible
             assert np.isfinite(gx).all()
+
+
+def test_order_score_replaces_implied_slack_order(pkg):
+    """The hand-worked case of the oracle's pin: with the score, one bulk and no recovery."""
+    from tests.helpers import milp_from_dense
+    A = np.array([[10.0, 10.0, 0.0, 0.0], [0.0, 0.0, 1.0, 1.0]])
+    p = milp_from_dense(A, [10.0, 1.5], np.zeros(4), np.ones(4), np.ones(4))
+    x = np.full(4, 0.8)
+    r = _check(p, x, last_single=0)
+    assert (r["bulks"], r["recoveries"]) == (4, 2)
+    r = _check(p, x, last_single=0, order_score=np.array([3.0, 0.0, 2.0, 1.0]))
+    assert (r["bulks"], r["recoveries"]) == (1, 0)
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_hooks_fraction_rule(pkg, seed):
+    """Score order (no implied-slack sort) and up probabilities under the 1% bulk rule."""
+    p = synth.random_milp(61 + seed, 3000, 5000, len_lo=2, len_hi=30, integer_coefs=True, int_fraction=1.0,
+                          slack_scale=0.3)
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0, 20, p.n)
+    _check(p, x, seed=seed, bulk_rule=1, fraction=0.01, order_score=rng.standard_normal(p.n),
+           up_prob=rng.uniform(0, 1, p.n))

@@ -223,3 +223,25 @@ def test_scores_scatter(pkg):
     np.testing.assert_allclose(u[v], 1 / (1 + np.exp(-z[:, 1])), rtol=1e-12)
     rest = np.setdiff1d(np.arange(1000), v)
     assert np.all(o[rest] == -7.0) and np.all(u[rest] == -7.0)
+
+
+@pytest.mark.parametrize("runs", [1, 2, 4])
+def test_labels_match_oracle(pkg, runs):
+    """scorer_labels over `runs` feasible results against the oracle's trajectory labels
+    (weights 1, 1/2, 1/4: the float32 sums are exact)."""
+    import torch
+    rng = np.random.default_rng(runs)
+    n = 3000
+    x = np.where(rng.random(n) < 0.2, rng.integers(0, 5, n).astype(float), rng.uniform(0, 5, n))
+    x[:8] = [0.5, 1.5, 2.0, 0.49999999999999994, 3.5, 4.0, 0.25, 0.75]    # ties and integral values
+    outs = [np.floor(x) + (rng.random(n) < 0.5) for _ in range(runs)]
+    vars_ = rng.permutation(n)[:2500].astype(np.int32)
+    want = mlp.trajectory_labels(x, outs, vars_)
+    xd = torch.tensor(x, device="cuda")
+    vd = torch.tensor(vars_, device="cuda")
+    lab = torch.full((len(vars_), 2), 7.0, dtype=torch.float32, device="cuda")
+    for i, o in enumerate(outs):
+        pkg.scorer_labels(xd, torch.tensor(o, device="cuda"), vd, lab, weight=1.0 / runs, first=(i == 0))
+    got = lab.cpu().numpy().astype(np.float64)
+    np.testing.assert_array_equal(np.isnan(got), np.isnan(want))
+    np.testing.assert_array_equal(got[~np.isnan(got)], want[~np.isnan(want)])

@@ -150,3 +150,24 @@ def test_order_score_hook():
     np.testing.assert_array_equal(out, [1.0, 0.0])
     out, _ = oracle.Problem(p).fix_and_propagate(x, p.lb, p.ub, order_score=np.array([0.0, 1.0]))
     np.testing.assert_array_equal(out, [0.0, 1.0])
+
+
+def test_order_score_replaces_implied_slack_order():
+    """Binaries y1..y4, all at x = 0.8 (always rounded up), rows 10 y1 + 10 y2 <= 10 and
+    y3 + y4 <= 1.5, no single-variable tail.  Implied slack: S = (10/10)^2 = 1 for y1, y2 and
+    (1/1.5)^2 = 0.44 for y3, y4, so the plain order puts {y1, y2} in the first bulk of
+    ceil(sqrt(4)) = 2: both vectors set y1 = y2 = 1 and fail, the recovery fixes y1 = 1
+    (propagation then fixes y2 = 0), and the next bulk {y3, y4} fails the same way before y3 = 1
+    fixes y4 = 0: 4 bulks, 2 recoveries.  A score ranking y1, y3, y4, y2 replaces the
+    implied-slack order: the first bulk {y1, y3} succeeds and propagation fixes the others
+    (1 bulk, no recovery)."""
+    A = np.array([[10.0, 10.0, 0.0, 0.0], [0.0, 0.0, 1.0, 1.0]])
+    p = milp_from_dense(A, [10.0, 1.5], np.zeros(4), np.ones(4), np.ones(4))
+    x = np.full(4, 0.8)
+    out, r = oracle.Problem(p).fix_and_propagate(x, p.lb, p.ub, last_single=0)
+    np.testing.assert_array_equal(out, [1.0, 0.0, 1.0, 0.0])
+    assert (r["bulks"], r["recoveries"], r["status"]) == (4, 2, 0)
+    out, r = oracle.Problem(p).fix_and_propagate(x, p.lb, p.ub, last_single=0,
+                                                 order_score=np.array([3.0, 0.0, 2.0, 1.0]))
+    np.testing.assert_array_equal(out, [1.0, 0.0, 1.0, 0.0])
+    assert (r["bulks"], r["recoveries"], r["status"]) == (1, 0, 0)

@@ -141,3 +141,18 @@ def test_training_reduces_loss():
         loss, g = mlp.loss_grad(theta, X, Y)
         theta = opt.step(theta, g, 1e-2)
     assert loss < 0.3 * l0, (l0, loss)
+
+
+def test_trajectory_labels_hand_worked():
+    """x = (0.3, 0.5, 2.0, 6.7), two feasible runs fixing (0, 1, 2, 7) and (1, 1, 2, 6).
+    Nearest integers floor(x + 1/2) = (0, 1, 2, 7): order labels (1/2, 1, 1, 1/2).  Fixed above
+    x: (0, 1, -, 1) and (1, 1, -, 0): direction labels (1/2, 1, NaN, 1/2); x = 2 is integral.
+    Only the listed variables (3, 0) are labelled, in that order."""
+    x = np.array([0.3, 0.5, 2.0, 6.7])
+    runs = [np.array([0.0, 1.0, 2.0, 7.0]), np.array([1.0, 1.0, 2.0, 6.0])]
+    Y = mlp.trajectory_labels(x, runs, np.arange(4))
+    np.testing.assert_array_equal(Y[:, 0], [0.5, 1.0, 1.0, 0.5])
+    np.testing.assert_array_equal(Y[[0, 1, 3], 1], [0.5, 1.0, 0.5])
+    assert np.isnan(Y[2, 1])
+    np.testing.assert_array_equal(mlp.trajectory_labels(x, runs, [3, 0]), Y[[3, 0]])
+    assert np.isnan(mlp.trajectory_labels(x, [], [0, 1])).all()
