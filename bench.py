@@ -36,7 +36,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the probing and batch measurements")
+    ap.add_argument("--no-extras", action="store_true", help="skip the probing, batch, learned and scorer measurements")
+    ap.add_argument("--extras", default="probing,batch,learned,scorer",
+                    help="comma-separated subset of the extra measurements to run")
     return ap.parse_args()
 
 
@@ -47,6 +49,15 @@ def peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def tensor_peak():
+    """Dense BF16 TFLOP/s for a kernel timed alone (the measured burst figure, else the fallback)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"])
+    return 1900.0
 
 
 class ClockSampler:
@@ -268,6 +279,118 @@ def batch_extra(pkg, torch, dev):
             "infeasible": sum(1 for r in rs if r["status"] == 1)}
 
 
+def _verified(pkg, torch, prob, p, xo):
+    """A FEASIBLE fix-and-propagate result checked again: integer values integral, a fresh
+    propagation from the original bounds with the integer variables fixed not infeasible, and
+    (with SciPy) a continuous completion within 1e-6 of every row (HiGHS)."""
+    import numpy as np
+    ints = p.is_int == 1
+    if not (xo[ints] == np.round(xo[ints])).all():
+        return False
+    lo, hi = p.lb.copy(), p.ub.copy()
+    lo[ints] = hi[ints] = xo[ints]
+    lt, ut = torch.tensor(lo, device=prob.device), torch.tensor(hi, device=prob.device)
+    if prob.propagate(lt, ut)["status"] == 1:
+        return False
+    try:
+        import scipy.sparse as sp
+        from scipy.optimize import linprog
+    except ImportError:
+        return True
+    A = sp.csr_matrix((p.val, p.col, p.row_ptr), shape=(p.m, p.n))
+    cont = np.flatnonzero(~ints)
+    rhs = p.g - A[:, np.flatnonzero(ints)] @ xo[ints] + 1e-6
+    r = linprog(np.zeros(len(cont)), A_ub=A[:, cont], b_ub=rhs, bounds=list(zip(p.lb[cont], p.ub[cont])),
+                method="highs")
+    return r.status == 0
+
+
+def learned_extra(pkg, torch, dev):
+    """The learned rounding order against the paper's order in fix-and-propagate (1% of the
+    integer variables per bulk).  The scorer is trained on the feasible plain trajectories of
+    16 instances with 100k nonzeros (8 seeds each), then both orders run on held-out instances:
+    12 with 100k nonzeros (4 seeds) and 8 with 1M nonzeros (2 seeds), the same seeds for both.
+    Feasible means verified again (fresh propagation with the integers fixed, and a continuous
+    completion by HiGHS)."""
+    import numpy as np
+    from paper_2510_20499_gb300 import learned, synth
+    fp = dict(bulk_rule=1, fraction=0.01)
+    t0 = time.perf_counter()
+    data = []
+    for i in range(16):
+        p, x = synth.rounding_instance(i, 100_000)
+        prob = pkg.Problem(p)
+        xd, lb, ub = (torch.tensor(a, device=dev) for a in (x, p.lb, p.ub))
+        data.append(learned.collect(prob, xd, lb, ub, seeds=range(100, 108), **fp))
+    scorer = pkg.Scorer(seed=3)
+    losses = learned.train(scorer, data, epochs=6, batch=4096, lr=3e-3, seed=0)
+    t_train = time.perf_counter() - t0
+    out = {"workload": "rounding instances (mixed power-law, planted point + N(0, 0.3) as the fractional point)",
+           "train": {"instances": 16, "nnz": 100_000, "runs": 16 * 8,
+                     "feasible_runs": int(sum(d["feasible"] for d in data)),
+                     "labelled_rows": int(sum(d["feat"].shape[0] for d in data if d["labels"] is not None)),
+                     "loss_first_last": [losses[0], losses[-1]] if losses else None, "seconds": t_train}}
+    for nnz, idx, seeds in ((100_000, range(1000, 1012), range(1, 5)), (1_000_000, range(2000, 2008), range(1, 3))):
+        arms = {"plain": [], "learned": []}
+        t_run = {"plain": 0.0, "learned": 0.0}
+        for i in idx:
+            p, x = synth.rounding_instance(i, nnz)
+            prob = pkg.Problem(p)
+            xd, lb, ub = (torch.tensor(a, device=dev) for a in (x, p.lb, p.ub))
+            order, up = learned.scores(prob, scorer, xd, lb, ub)
+            for s in seeds:
+                for arm, kw in (("plain", {}), ("learned", dict(order_score=order, up_prob=up))):
+                    torch.cuda.synchronize()
+                    ta = time.perf_counter()
+                    xo, r = prob.fix_and_propagate(xd, lb, ub, seed=s, **kw, **fp)
+                    t_run[arm] += time.perf_counter() - ta
+                    r["verified"] = r["status"] == 0 and _verified(pkg, torch, prob, p, xo.cpu().numpy())
+                    arms[arm].append(r)
+        rep = {}
+        for arm, rs in arms.items():
+            ok = [r for r in rs if r["verified"]]
+            rep[arm] = {"runs": len(rs), "feasible_reported": sum(r["status"] == 0 for r in rs),
+                        "feasible_verified": len(ok),
+                        "bulks_to_feasibility": float(np.mean([r["bulks"] for r in ok])) if ok else None,
+                        "bulks_mean_all_runs": float(np.mean([r["bulks"] for r in rs])),
+                        "seconds_per_run": t_run[arm] / len(rs)}
+        out[f"test_{nnz // 1000}k_nnz"] = rep
+    return out
+
+
+def scorer_extra(pkg, torch, dev, tflops_peak):
+    """The scorer's forward and training-step throughput on 1M rows of BF16 features (the
+    tcgen05 MLP kernel k_mlp), against the measured BF16 tensor peak."""
+    scorer = pkg.Scorer(seed=3)
+    rows = 1_000_000
+    g = torch.Generator(device="cpu")
+    g.manual_seed(0)
+    X = torch.randn(rows, 16, generator=g).to(dev).to(torch.bfloat16)
+    Y = (torch.rand(rows, 2, generator=g) > 0.5).float().to(dev)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(20):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 20
+    t_f = timed(lambda: scorer.forward(X))
+    t_t = timed(lambda: scorer.train_step(X, Y, 1e-6, want_loss=False))
+    fl_f = 2 * (16 * 64 + 64 * 64 + 64 * 2)          # forward flops per row
+    fl_t = 3 * fl_f                                   # forward + input and weight gradients
+    achieved = fl_f * rows / (t_f / 1e3) / 1e12
+    return {"rows": rows, "forward_ms": t_f, "forward_rows_per_s": rows / (t_f / 1e3),
+            "train_step_ms": t_t, "train_rows_per_s": rows / (t_t / 1e3),
+            "roofline": {"bound": "tensor", "kernel": "k_mlp (forward)", "achieved": achieved,
+                         "peak": tflops_peak, "unit": "TFLOP/s", "frac": achieved / tflops_peak,
+                         "train_achieved": fl_t * rows / (t_t / 1e3) / 1e12}}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -384,7 +507,13 @@ def main():
                      "launch_ms": kern_avg},
     }
     if rank == 0 and not args.no_extras:
-        out["extras"] = {"probing": probing_extra(pkg, torch, dev), "batch": batch_extra(pkg, torch, dev)}
+        todo = [e for e in args.extras.split(",") if e]
+        bad = [e for e in todo if e not in ("probing", "batch", "learned", "scorer")]
+        if bad:
+            raise SystemExit(f"unknown extras: {bad}")
+        fns = {"probing": lambda: probing_extra(pkg, torch, dev), "batch": lambda: batch_extra(pkg, torch, dev),
+               "learned": lambda: learned_extra(pkg, torch, dev), "scorer": lambda: scorer_extra(pkg, torch, dev, tensor_peak())}
+        out["extras"] = {e: fns[e]() for e in todo}
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(p)
     if rank == 0:
