@@ -110,7 +110,7 @@ class ClockSampler:
 # DRAM bytes (read + write) of one bp_kernel launch on this workload, from the ncu capture
 # summarised in profiles/bp_kernel_mixed_powerlaw_5M.md; reported only while the kernel's
 # sources are the ones that capture was taken on.
-NCU_TRAFFIC = {"sources_sha256_16": "904a3c6cdd2fcf75", "bytes": 192_924_160}
+NCU_TRAFFIC = {"sources_sha256_16": "a6edf4a42e5ce993", "bytes": 196_685_056}
 KERNEL_SOURCES = ["bp_engine.cu", "bp_device.cuh", "bp_host.h"]
 
 
