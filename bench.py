@@ -131,6 +131,21 @@ def algorithmic_bytes(trace_rows, trace_nnz, trace_chg, n):
     return int(12 * sum(trace_nnz) + 8 * sum(trace_rows) + 32 * sum(trace_chg) + 80 * n)
 
 
+def whole_job(units, ms, device):
+    """Whole-job totals over the ranks of the process group (one replica per rank, no exchange
+    on the data path): the units all ranks processed and the slowest rank's time.  Without a
+    process group: the local values."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return units, ms
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([int(units)], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return int(u.item()), float(t.item())
+
+
 def run_reference(args):
     import oracle
     from paper_2510_20499_gb300 import synth
@@ -464,12 +479,8 @@ def main():
     res = prob.propagate(lb.copy_(lb0), ub.copy_(ub0))
     assert res == r0, (res, r0)
     clocks = sampler.finish()
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = nnz * world / (total_ms / 1e3)
+    nnz_all, total_ms = whole_job(nnz, float(sum(step_ms)), dev)
+    value = nnz_all / (total_ms / 1e3)
 
     # end to end through the C ABI with host (pinned) bounds: copies inside the timed region
     hl = torch.empty(p.n, dtype=torch.float64).pin_memory()
