@@ -74,10 +74,10 @@ struct BpArgs {
     const int* row_off;
     const int* col_off;
     InstState* inst;
-    unsigned long long* i_nnz;   // [2][ninst] nonzeros processed in the phase of that parity
-    int* i_rowinf;               // [2][ninst] smallest infeasible row of the phase
-    int* i_cross;                // [2][ninst] smallest crossing variable found in the phase
-    int* i_chg;                  // [2][ninst] a variable of the instance changed in the phase
+    unsigned long long* i_nnz;   // [kPhaseSlots][ninst] nonzeros processed in the round of that slot
+    int* i_rowinf;               // [kPhaseSlots][ninst] smallest infeasible row of the round
+    int* i_cross;                // [kPhaseSlots][ninst] smallest crossing variable found in the round
+    int* i_chg;                  // [kPhaseSlots][ninst] a variable of the instance changed in the round
 };
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
@@ -100,17 +100,23 @@ struct Stage {
     // descriptor of the current phase, read once per block by thread 0
     int d_cnt[kNumClass];
     int d_ntask, d_nprev;
-    // instances (offsets, and the live / pending-check flags of the current phase)
+    // instances (offsets; live and pending-check flags and result buffer, kept by every block
+    // from the same verdicts)
     int roff[kMaxInst + 1], coff[kMaxInst + 1];
-    unsigned char alive[kMaxInst], pending[kMaxInst];
+    unsigned char alive[kMaxInst], pending[kMaxInst], rpar[kMaxInst];
     unsigned long long i_nnz[kMaxInst];
     int any_alive;
     int last_block;
+    unsigned bar_k;                              // grid barriers passed in this launch
+    int epi_n, epi_par;                          // variables changed in the last round, their list
 };
 
 // ------------------------------------------------------------------ phase state
 struct Phase {
     int t, par, npar;
+    // counter slots of this round and of the next
+    __device__ __forceinline__ int s3() const { return t % kPhaseSlots; }
+    __device__ __forceinline__ int ns3() const { return (t + 1) % kPhaseSlots; }
     const longlong2* R;     // bounds at the start of the round
     longlong2* X;           // bounds of the next round (atomics)
     int st_v, st_r;         // variable-change stamp of this round, row stamp of next round
@@ -144,7 +150,7 @@ __device__ __forceinline__ int* slot_dst(const BpArgs& A, const DevProblem& P, c
     return s == kSlotChg ? A.chg[ph.par] + pos : A.list[ph.npar] + P.class_off[s] + pos;
 }
 __device__ __forceinline__ int* slot_ctr(const BpArgs& A, const Phase& ph, int s) {
-    return s == kSlotChg ? &A.ctl->nchg[ph.par].v : &A.ctl->cnt[ph.npar][s].v;
+    return s == kSlotChg ? &A.ctl->nchg[ph.s3()].v : &A.ctl->cnt[ph.ns3()][s].v;
 }
 
 // Warp-wide: move this warp's staged entries of slot s to the global list (one atomic).
@@ -199,14 +205,14 @@ __device__ void lane_queue_row(const BpArgs& A, const DevProblem& P, const Phase
     if (atomicMax(&A.rstamp[k], ph.st_r) >= ph.st_r) return;
     const int cls = info & 7;
     if (cls != kClassChunked) {
-        const int pos = atomicAdd(&A.ctl->cnt[ph.npar][cls].v, 1);
+        const int pos = atomicAdd(&A.ctl->cnt[ph.ns3()][cls].v, 1);
         A.list[ph.npar][P.class_off[cls] + pos] = k;
         return;
     }
     const int nch = info >> 3;
-    const int base = atomicAdd(&A.ctl->ntask[ph.npar].v, nch);
+    const int base = atomicAdd(&A.ctl->ntask[ph.ns3()].v, nch);
     for (int c = 0; c < nch; ++c) A.task[ph.npar][base + c] = make_int2(k, c);
-    atomicAdd(&A.ctl->cnt[ph.npar][kClassChunked].v, 1);
+    atomicAdd(&A.ctl->cnt[ph.ns3()][kClassChunked].v, 1);
 }
 
 // Warp-wide: queue the rows `k` (k < 0: none) for the next round; a row's first queuing in
@@ -220,9 +226,9 @@ __device__ void warp_queue_rows(Stage& st, const BpArgs& A, const DevProblem& P,
             slot = cls;
         } else {
             const int nch = info >> 3;
-            const int base = atomicAdd(&A.ctl->ntask[ph.npar].v, nch);
+            const int base = atomicAdd(&A.ctl->ntask[ph.ns3()].v, nch);
             for (int c = 0; c < nch; ++c) A.task[ph.npar][base + c] = make_int2(k, c);
-            atomicAdd(&A.ctl->cnt[ph.npar][kClassChunked].v, 1);
+            atomicAdd(&A.ctl->cnt[ph.ns3()][kClassChunked].v, 1);
         }
     }
     warp_append(st, A, P, ph, slot, k);
@@ -240,8 +246,8 @@ __device__ __forceinline__ void note_changed(Stage& st, const BpArgs& A, const D
         return;
     }
     if (atomicMax(&A.vstamp[j], ph.st_v) >= ph.st_v) return;
-    A.i_chg[ph.par * A.ninst + var_inst(st, A, j)] = 1;
-    const int pos = atomicAdd(&A.ctl->nchg[ph.par].v, 1);
+    A.i_chg[ph.s3() * A.ninst + var_inst(st, A, j)] = 1;
+    const int pos = atomicAdd(&A.ctl->nchg[ph.s3()].v, 1);
     A.chg[ph.par][pos] = j;
     const int e = __ldg(P.col_ptr + j + 1);
     for (int s = __ldg(P.col_ptr + j); s < e; ++s) lane_queue_row(A, P, ph, __ldg(P.row_idx + s));
@@ -262,7 +268,7 @@ __device__ void drain_changed(Stage& st, const BpArgs& A, const DevProblem& P, c
         const int cb = v >= 0 ? __ldg(P.col_ptr + v) : 0;
         const int ce = v >= 0 ? __ldg(P.col_ptr + v + 1) : 0;
         if (v >= 0 && atomicMax(&A.vstamp[v], ph.st_v) >= ph.st_v) v = -1;
-        if (v >= 0) A.i_chg[ph.par * A.ninst + var_inst(st, A, v)] = 1;
+        if (v >= 0) A.i_chg[ph.s3() * A.ninst + var_inst(st, A, v)] = 1;
         warp_append(st, A, P, ph, v >= 0 ? kSlotChg : -1, v);
         const int deg = v >= 0 ? ce - cb : 0;
         int incl = deg;
@@ -420,7 +426,7 @@ __device__ void do_thread_rows(Stage& st, const BpArgs& A, const DevProblem& P, 
         atomicAdd(&st.nnz, (unsigned long long)(end - beg));
         atomicAdd(&st.i_nnz[ki], (unsigned long long)(end - beg));
         if (row_infeasible(s.minfin, s.ninf, g2.y)) {
-            atomicMin(&A.i_rowinf[ph.par * A.ninst + ki], k);
+            atomicMin(&A.i_rowinf[ph.s3() * A.ninst + ki], k);
         } else {
             elems_candidates(st, A, P, ph, E, s, g2.x);
         }
@@ -441,7 +447,7 @@ __device__ void do_warp_row(Stage& st, const BpArgs& A, const DevProblem& P, con
         atomicAdd(&st.i_nnz[ki], (unsigned long long)(end - beg));
     }
     if (row_infeasible(tot.minfin, tot.ninf, g2.y)) {
-        if (lane == 0) atomicMin(&A.i_rowinf[ph.par * A.ninst + ki], k);
+        if (lane == 0) atomicMin(&A.i_rowinf[ph.s3() * A.ninst + ki], k);
     } else {
         elems_candidates(st, A, P, ph, E, tot, g2.x);
     }
@@ -456,7 +462,7 @@ __device__ void do_block_row(Stage& st, const BpArgs& A, const DevProblem& P, co
     Elems E;
     const Acc tot = block_reduce(st, load_accumulate(E, P, ph, beg, end, threadIdx.x, kThreads));
     if (row_infeasible(tot.minfin, tot.ninf, g2.y)) {
-        if (threadIdx.x == 0) atomicMin(&A.i_rowinf[ph.par * A.ninst + ki], k);
+        if (threadIdx.x == 0) atomicMin(&A.i_rowinf[ph.s3() * A.ninst + ki], k);
     } else {
         elems_candidates(st, A, P, ph, E, tot, g2.x);
     }
@@ -483,7 +489,7 @@ __device__ Acc chunk_total(Stage& st, const BpArgs& A, const DevProblem& P, cons
     }
     s = warp_reduce(s);
     if (lane == 0) {
-        if (row_infeasible(s.minfin, s.ninf, g_tol)) atomicMin(&A.i_rowinf[ph.par * A.ninst + ki], k);
+        if (row_infeasible(s.minfin, s.ninf, g_tol)) atomicMin(&A.i_rowinf[ph.s3() * A.ninst + ki], k);
         atomicAdd(&st.nnz, (unsigned long long)len);
         atomicAdd(&st.i_nnz[ki], (unsigned long long)len);
         A.htot[h] = s.minfin;
@@ -633,78 +639,168 @@ __device__ void do_fix(const Stage& st, const BpArgs& A, const DevProblem& P, co
         atomicMax(&ph.X[v].x, b.x);
         atomicMin(&ph.X[v].y, b.y);
     }
-    if (crossed(P.is_int[v] != 0, b.x, b.y)) atomicMin(&A.i_cross[ph.par * A.ninst + vi], v);
+    if (crossed(P.is_int[v] != 0, b.x, b.y)) atomicMin(&A.i_cross[ph.s3() * A.ninst + vi], v);
 }
 
 // -------------------------------------------------------------------- barrier
-// All blocks arrive; all threads of the last one run `book` (it may use __syncthreads) and
-// thread 0 releases the others.  After the release every block reads the stop flag, the
-// descriptor of phase `next` and the instances' live / pending flags into shared memory.
-template <class F>
-__device__ void grid_barrier(Stage& st, Ctl* ctl, const DevProblem& P, const BpArgs& A, int next, F&& book) {
+// Grid barrier: every block arrives once on a count that only grows within the launch and
+// waits until all blocks have arrived at this barrier (the launch's bar_k-th).  No block
+// resets anything or releases the others, so no bookkeeping sits on the others' path: after
+// the barrier each block reads the round's counters itself and takes the same decisions.
+__device__ void grid_sync(Stage& st, Ctl* ctl) {
     __syncthreads();
-    unsigned gen = 0;
     if (threadIdx.x == 0) {
-        gen = ld_acquire_u32(&ctl->bar_gen.v);
         __threadfence();   // the block's writes (all threads, ordered by the barrier above)
-        const unsigned old = atom_add_acqrel_u32(&ctl->bar_count.v, 1u);
-        st.last_block = old == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (st.last_block) {
-        __threadfence();
-        book();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            ctl->bar_count.v = 0;
-            __threadfence();
-            st_release_u32(&ctl->bar_gen.v, gen + 1);
-        }
-    } else if (threadIdx.x == 0) {
+        atom_add_acqrel_u32(&ctl->bar_count.v, 1u);
+        const unsigned target = gridDim.x * (st.bar_k + 1u);
         const long long t0 = clock64();
-        while (ld_acquire_u32(&ctl->bar_gen.v) == gen) {
+        while (ld_acquire_u32(&ctl->bar_count.v) < target) {
             if (clock64() - t0 > kSpinLimit) {
                 atomicExch(&ctl->error, BP_ERR_TIMEOUT);
                 break;
             }
-            __nanosleep(64);
+            __nanosleep(32);
         }
-    }
-    if (threadIdx.x == 0) {
         __threadfence();
-        st.flag = ld_acquire_s32(&ctl->stop) | (ld_acquire_s32(&ctl->error) != 0);
-        const int par = next & 1;
-        const bool stat = (next == 0 && !A.w0 && !A.w0v);
-#pragma unroll
-        for (int c = 0; c < kNumClass; ++c)
-            st.d_cnt[c] = stat ? P.class_off[c + 1] - P.class_off[c] : __ldcg(&ctl->cnt[par][c].v);
-        st.d_ntask = stat ? P.nchunks : __ldcg(&ctl->ntask[par].v);
-        st.d_nprev = next == 0 ? 0 : __ldcg(&ctl->nchg[par ^ 1].v);
+        st.bar_k += 1u;
     }
     __syncthreads();
-    if (A.ninst == 1 && next > 0) {
-        // one instance: it is alive while the rounds go on (its end stops them), and its pending
-        // crossing check is read only after the rounds
-        if (threadIdx.x == 0) {
-            st.alive[0] = 1;
-            st.pending[0] = 0;
-            st.i_nnz[0] = 0;
+}
+
+// Descriptor of round `next` into shared memory (thread 0): its worklist counts per class,
+// its chunk tasks and the previous round's changed variables.
+__device__ __forceinline__ void load_descriptor(Stage& st, Ctl* ctl, const DevProblem& P, const BpArgs& A,
+                                                int next) {
+    const int sl = next % kPhaseSlots;
+    const bool stat = (next == 0 && !A.w0 && !A.w0v);
+#pragma unroll
+    for (int c = 0; c < kNumClass; ++c)
+        st.d_cnt[c] = stat ? P.class_off[c + 1] - P.class_off[c] : __ldcg(&ctl->cnt[sl][c].v);
+    st.d_ntask = stat ? P.nchunks : __ldcg(&ctl->ntask[sl].v);
+    st.d_nprev = next == 0 ? 0 : __ldcg(&ctl->nchg[(next - 1) % kPhaseSlots].v);
+}
+
+// After the barrier that ends round t.  Every block takes the instances' verdicts of round t
+// from the same counters, so all reach the same live / pending flags and result buffers (kept
+// in shared memory), reads the descriptor of round t+1 and decides whether to stop.  Block 0
+// also records the verdicts in the instance states, writes the trace, and clears the counter
+// slots that round t+2 appends to: slot t % 3 of the worklist counts and slot (t+2) % 3 of the
+// rest, whose last readers finished before this barrier.
+__device__ __noinline__ void end_round(Stage& st, Ctl* ctl, const DevProblem& P, const BpArgs& A, int t) {
+    const int sl = t % kPhaseSlots, sl1 = (t + 1) % kPhaseSlots, sl2 = (t + 2) % kPhaseSlots;
+    const int par = t & 1, npar = par ^ 1;
+    const bool writer = blockIdx.x == 0;
+    // thread 0: the descriptor of round t+1, the error flag and the round's nonzeros, loaded
+    // together with the verdict words below (one round trip)
+    int d_cnt[kNumClass], d_ntask = 0, d_nprev = 0, err = 0, rows_t = 0;
+    unsigned long long nnz_t = 0;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int c = 0; c < kNumClass; ++c) {
+            rows_t += st.d_cnt[c];
+            d_cnt[c] = __ldcg(&ctl->cnt[sl1][c].v);
         }
-    } else {
-        for (int i = threadIdx.x; i < A.ninst; i += kThreads) {
-            st.alive[i] = (unsigned char)__ldcg(&A.inst[i].alive);
-            st.pending[i] = (unsigned char)__ldcg(&A.inst[i].pending);
-            st.i_nnz[i] = 0;
+        d_ntask = __ldcg(&ctl->ntask[sl1].v);
+        d_nprev = __ldcg(&ctl->nchg[sl].v);
+        err = __ldcg(&ctl->error);
+        if (writer && A.trace) nnz_t = __ldcg(&ctl->nnz[sl].v);
+    }
+    int any_alive = 0;
+    for (int i = threadIdx.x; i < A.ninst; i += kThreads) {
+        const int cross = __ldcg(A.i_cross + sl * A.ninst + i);
+        const int rinf = __ldcg(A.i_rowinf + sl * A.ninst + i);
+        const int chg = __ldcg(A.i_chg + sl * A.ninst + i);
+        int alive = st.alive[i], pending = st.pending[i];
+        if (alive) {
+            InstState* I = A.inst + i;
+            if (cross != INT_MAX) {
+                // bounds after round t-1 cross: that round is the instance's last
+                alive = 0;
+                st.rpar[i] = (unsigned char)par;
+                if (writer) {
+                    I->status = BP_INFEASIBLE;
+                    I->rounds = t;
+                    I->result_par = par;
+                    I->first_var = cross;
+                    I->first_row = INT_MAX;
+                }
+            } else {
+                st.rpar[i] = (unsigned char)npar;
+                int status = -1;
+                if (rinf != INT_MAX) {
+                    status = BP_INFEASIBLE;
+                    alive = 0;
+                    pending = 1;     // crossing check of this round's changes
+                } else if (!chg) {
+                    status = BP_FIXPOINT;
+                    alive = 0;
+                } else if (t + 1 >= A.max_rounds) {
+                    status = BP_ROUND_LIMIT;
+                    alive = 0;
+                    pending = 1;
+                }
+                if (writer) {
+                    I->nnz_total = __ldcg(&I->nnz_total) + __ldcg(A.i_nnz + sl * A.ninst + i);
+                    I->rounds = t + 1;
+                    I->result_par = npar;
+                    if (status >= 0) I->status = status;
+                    if (rinf != INT_MAX) I->first_row = rinf;
+                    I->pending = pending;
+                }
+            }
+            if (writer) I->alive = alive;
+        } else if (pending) {
+            // the crossing check of the instance's last round ran in this round
+            pending = 0;
+            if (writer) {
+                InstState* I = A.inst + i;
+                if (cross != INT_MAX && cross < __ldcg(&I->first_var)) I->first_var = cross;
+                I->pending = 0;
+            }
+        }
+        st.alive[i] = (unsigned char)alive;
+        st.pending[i] = (unsigned char)pending;
+        st.i_nnz[i] = 0;
+        any_alive |= alive;
+        if (writer) {
+            A.i_nnz[sl2 * A.ninst + i] = 0;
+            A.i_rowinf[sl2 * A.ninst + i] = INT_MAX;
+            A.i_cross[sl2 * A.ninst + i] = INT_MAX;
+            A.i_chg[sl2 * A.ninst + i] = 0;
+        }
+    }
+    any_alive = __syncthreads_or(any_alive);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int c = 0; c < kNumClass; ++c) st.d_cnt[c] = d_cnt[c];
+        st.d_ntask = d_ntask;
+        st.d_nprev = d_nprev;
+        st.flag = (!any_alive || err) ? 1 : 0;
+        st.epi_n = d_nprev;   // variables changed in round t (checked at the end when it is the last)
+        st.epi_par = par;
+        if (writer) {
+            if (A.trace && t < A.max_rounds) {
+                A.trace[4 * t + 0] = rows_t;
+                A.trace[4 * t + 1] = (long long)nnz_t;
+                A.trace[4 * t + 2] = d_nprev;
+                A.trace[4 * t + 3] = (long long)globaltimer_ns();
+            }
+            ctl->phases = t + 1;
+#pragma unroll
+            for (int c = 0; c < kNumClass; ++c) ctl->cnt[sl][c].v = 0;
+            ctl->ntask[sl].v = 0;
+            ctl->nchg[sl2].v = 0;
+            ctl->nnz[sl2].v = 0;
         }
     }
     __syncthreads();
 }
 
-// Flushes the block's per-instance nonzero counts of the phase.
-__device__ void flush_inst_nnz(Stage& st, const BpArgs& A, int par) {
+// Flushes the block's per-instance nonzero counts of round slot `sl`.
+__device__ void flush_inst_nnz(Stage& st, const BpArgs& A, int sl) {
     __syncthreads();
     for (int i = threadIdx.x; i < A.ninst; i += kThreads)
-        if (st.i_nnz[i]) atomicAdd(&A.i_nnz[par * A.ninst + i], st.i_nnz[i]);
+        if (st.i_nnz[i]) atomicAdd(&A.i_nnz[sl * A.ninst + i], st.i_nnz[i]);
     __syncthreads();
 }
 
@@ -750,8 +846,19 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthreads = gridDim.x * blockDim.x;
     Ctl* ctl = A.ctl;
     for (int i = threadIdx.x; i < kWarpsPerBlock * kSlots; i += kThreads) (&st.wcnt[0][0])[i] = 0;
-    if (threadIdx.x == 0) st.bq_n = 0;
-    if (threadIdx.x == 0) st.nnz = 0;
+    if (threadIdx.x == 0) {
+        st.bq_n = 0;
+        st.nnz = 0;
+        st.bar_k = 0;
+        st.epi_n = 0;
+        st.epi_par = 0;
+    }
+    for (int i = threadIdx.x; i < A.ninst; i += kThreads) {
+        st.alive[i] = 1;
+        st.pending[i] = 0;
+        st.rpar[i] = 0;
+        st.i_nnz[i] = 0;
+    }
     for (int i = threadIdx.x; i <= A.ninst; i += kThreads) {
         st.roff[i] = A.ninst == 1 ? (i ? P.m : 0) : A.row_off[i];
         st.coff[i] = A.ninst == 1 ? (i ? P.n : 0) : A.col_off[i];
@@ -779,7 +886,7 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
         I.nnz_total = 0;
         I.n_changed = 0;
         A.inst[i] = I;
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < kPhaseSlots; ++q) {
             A.i_nnz[q * A.ninst + i] = 0;
             A.i_rowinf[q * A.ninst + i] = INT_MAX;
             A.i_cross[q * A.ninst + i] = INT_MAX;
@@ -788,7 +895,7 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
     }
     __syncthreads();
     // all instance state must be initialised before any block updates it
-    grid_barrier(st, ctl, P, A, -1, [&] {});
+    grid_sync(st, ctl);
 
     // ---- prologue: normalised start bounds into both buffers; rows of round 0
     for (int v = gtid; v < P.n; v += gthreads) {
@@ -803,7 +910,8 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
     if (A.w0) {
         // queue the given rows into the round-0 lists (stamp `base` = member of round 0)
         Phase q = ph0;
-        q.npar = 0;
+        q.npar = 0;     // round 0's list and counter slot (t = -1: next slot 0)
+        q.t = -1;
         const int gw0 = gtid >> 5, nw0 = gthreads >> 5;
         for (int b = gw0 * 32; b < A.w0_len; b += nw0 * 32) {
             const int i = b + lane;
@@ -813,7 +921,8 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
     } else if (A.w0v) {
         // queue the rows of the given variables (one warp per variable)
         Phase q = ph0;
-        q.npar = 0;
+        q.npar = 0;     // round 0's list and counter slot (t = -1: next slot 0)
+        q.t = -1;
         const int gw0 = gtid >> 5, nw0 = gthreads >> 5;
         const int nv = *A.w0v_len;
         for (int b = gw0; b < nv; b += nw0) {
@@ -830,30 +939,40 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
         }
         warp_flush_all(st, A, P, q);
     }
-    grid_barrier(st, ctl, P, A, 0, [&] {
+    grid_sync(st, ctl);
+    // every block: which instances run round 0 (block 0 records the others' verdicts)
+    {
         int rows0 = 0;
         if (A.w0 || A.w0v)
-            for (int c = 0; c < kNumClass; ++c) rows0 += ctl->cnt[0][c].v;
+            for (int c = 0; c < kNumClass; ++c) rows0 += __ldcg(&ctl->cnt[0][c].v);
         if (threadIdx.x == 0) st.any_alive = 0;
         __syncthreads();
         for (int i = threadIdx.x; i < A.ninst; i += kThreads) {
             InstState* I = A.inst + i;
             const int ri = (A.w0 || A.w0v) ? rows0 : st.roff[i + 1] - st.roff[i];
             const int ec = __ldcg(&I->entry_cross);
+            int alive = 1;
             if (ec != INT_MAX) {
-                I->status = BP_INFEASIBLE;
-                I->first_var = ec;
-                I->alive = 0;
+                alive = 0;
+                if (blockIdx.x == 0) {
+                    I->status = BP_INFEASIBLE;
+                    I->first_var = ec;
+                }
             } else if (ri == 0 || A.max_rounds <= 0) {
-                I->status = ri == 0 ? BP_FIXPOINT : BP_ROUND_LIMIT;
-                I->alive = 0;
-            } else {
-                atomicOr(&st.any_alive, 1);
+                alive = 0;
+                if (blockIdx.x == 0) I->status = ri == 0 ? BP_FIXPOINT : BP_ROUND_LIMIT;
             }
+            if (blockIdx.x == 0) I->alive = alive;
+            st.alive[i] = (unsigned char)alive;
+            if (alive) atomicOr(&st.any_alive, 1);
         }
         __syncthreads();
-        if (threadIdx.x == 0 && !st.any_alive) ctl->stop = 1;
-    });
+        if (threadIdx.x == 0) {
+            load_descriptor(st, ctl, P, A, 0);
+            st.flag = (!st.any_alive || __ldcg(&ctl->error)) ? 1 : 0;
+        }
+        __syncthreads();
+    }
 
     // ---- rounds
     for (int t = 0; !st.flag; ++t) {
@@ -935,105 +1054,25 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
         warp_flush_all(st, A, P, ph);
         __syncthreads();
         if (threadIdx.x == 0 && st.nnz) {
-            atomicAdd(&ctl->nnz[ph.par].v, st.nnz);
+            atomicAdd(&ctl->nnz[ph.s3()].v, st.nnz);
             st.nnz = 0;
         }
-        flush_inst_nnz(st, A, ph.par);
-        grid_barrier(st, ctl, P, A, t + 1, [&] {
-            const int par = t & 1, npar = par ^ 1;
-            if (threadIdx.x == 0) st.any_alive = 0;
-            __syncthreads();
-            for (int i = threadIdx.x; i < A.ninst; i += kThreads) {
-                InstState* I = A.inst + i;
-                // every word the decision may need, loaded at once (one round trip)
-                const int cross = __ldcg(A.i_cross + par * A.ninst + i);
-                int alive = __ldcg(&I->alive);
-                const int pending = __ldcg(&I->pending);
-                const int first_var = __ldcg(&I->first_var);
-                const unsigned long long nnz_total = __ldcg(&I->nnz_total);
-                const unsigned long long nnz_phase = __ldcg(A.i_nnz + par * A.ninst + i);
-                const int rinf = __ldcg(A.i_rowinf + par * A.ninst + i);
-                const int chg = __ldcg(A.i_chg + par * A.ninst + i);
-                if (alive) {
-                    if (cross != INT_MAX) {
-                        // bounds after round t-1 cross: that round is the instance's last
-                        I->status = BP_INFEASIBLE;
-                        I->rounds = t;
-                        I->result_par = par;
-                        I->first_var = cross;
-                        I->first_row = INT_MAX;
-                        alive = 0;
-                    } else {
-                        I->nnz_total = nnz_total + nnz_phase;
-                        I->rounds = t + 1;
-                        I->result_par = npar;
-                        if (rinf != INT_MAX) {
-                            I->status = BP_INFEASIBLE;
-                            I->first_row = rinf;
-                            alive = 0;
-                            I->pending = 1;     // crossing check of this round's changes
-                        } else if (!chg) {
-                            I->status = BP_FIXPOINT;
-                            alive = 0;
-                        } else if (t + 1 >= A.max_rounds) {
-                            I->status = BP_ROUND_LIMIT;
-                            alive = 0;
-                            I->pending = 1;
-                        }
-                    }
-                    I->alive = alive;
-                } else if (pending) {
-                    // the crossing check of the instance's last round ran in this phase
-                    if (cross != INT_MAX && cross < first_var) I->first_var = cross;
-                    I->pending = 0;
-                }
-                if (alive) atomicOr(&st.any_alive, 1);
-                A.i_nnz[npar * A.ninst + i] = 0;
-                A.i_rowinf[npar * A.ninst + i] = INT_MAX;
-                A.i_cross[npar * A.ninst + i] = INT_MAX;
-                A.i_chg[npar * A.ninst + i] = 0;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                if (A.trace && t < A.max_rounds) {
-                    int rows_t = 0;
-                    if (t == 0 && !A.w0 && !A.w0v) {
-                        rows_t = P.m;
-                    } else {
-                        for (int c = 0; c < kNumClass; ++c) rows_t += ctl->cnt[par][c].v;
-                    }
-                    A.trace[4 * t + 0] = rows_t;
-                    A.trace[4 * t + 1] = (long long)ctl->nnz[par].v;
-                    A.trace[4 * t + 2] = ctl->nchg[par].v;
-                    A.trace[4 * t + 3] = (long long)globaltimer_ns();
-                }
-                ctl->phases = t + 1;
-                if (!st.any_alive) {
-                    ctl->stop = 1;
-                    ctl->epi_par = par;
-                    ctl->epi_n = ctl->nchg[par].v;
-                } else {
-                    // reset the append targets of round t+1
-                    for (int c = 0; c < kNumClass; ++c) ctl->cnt[par][c].v = 0;
-                    ctl->ntask[par].v = 0;
-                    ctl->nchg[npar].v = 0;
-                    ctl->nnz[npar].v = 0;
-                }
-            }
-        });
+        flush_inst_nnz(st, A, ph.s3());
+        grid_sync(st, ctl);
+        end_round(st, ctl, P, A, t);
     }
 
     // ---- epilogue
     if (!ld_acquire_s32(&ctl->error)) {
-        const int epi_n = __ldcg(&ctl->epi_n);
+        const int epi_n = st.epi_n;
         if (epi_n > 0) {
             // crossing check of the last round of the instances whose check is pending
-            const int* lst = A.chg[__ldcg(&ctl->epi_par)];
+            const int* lst = A.chg[st.epi_par];
             for (int i = gtid; i < epi_n; i += gthreads) {
                 const int v = __ldcg(lst + i);
                 const int vi = var_inst(st, A, v);
-                if (!__ldcg(&A.inst[vi].pending)) continue;
-                const longlong2 b = __ldcg(A.bk[__ldcg(&A.inst[vi].result_par)] + v);
+                if (!st.pending[vi]) continue;
+                const longlong2 b = __ldcg(A.bk[st.rpar[vi]] + v);
                 if (crossed(P.is_int[v] != 0, b.x, b.y)) atomicMin(&A.inst[vi].first_var, v);
             }
         }
@@ -1043,7 +1082,7 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
             if (v < P.n) {
                 vi = var_inst(st, A, v);
                 const longlong2 in = normalized_keys(A.lb[v], A.ub[v], P.is_int[v] != 0);
-                const longlong2 b = __ldcg(A.bk[__ldcg(&A.inst[vi].result_par)] + v);
+                const longlong2 b = __ldcg(A.bk[st.rpar[vi]] + v);
                 changed = (b.x != in.x || b.y != in.y) ? 1 : 0;
                 A.lb[v] = kdec(b.x);
                 A.ub[v] = kdec(b.y);
@@ -1058,21 +1097,17 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
 }
 
 // ------------------------------------------------------------------------ host
-void ctl_template(Ctl* c) {
-    memset(c, 0, sizeof(Ctl));
-    c->epi_par = 0;
-    c->epi_n = 0;
-}
+void ctl_template(Ctl* c) { memset(c, 0, sizeof(Ctl)); }
 
 static int ensure_instances(mip_problem* p, int ninst) {
     Work& w = p->w;
     if (ninst <= w.inst_cap) return BP_OK;
     BP_TRY(dalloc(p, &w.dres, (size_t)ninst));
     BP_TRY(dalloc(p, &w.inst, (size_t)ninst));
-    BP_TRY(dalloc(p, &w.i_nnz, 2 * (size_t)ninst));
-    BP_TRY(dalloc(p, &w.i_rowinf, 2 * (size_t)ninst));
-    BP_TRY(dalloc(p, &w.i_cross, 2 * (size_t)ninst));
-    BP_TRY(dalloc(p, &w.i_chg, 2 * (size_t)ninst));
+    BP_TRY(dalloc(p, &w.i_nnz, kPhaseSlots * (size_t)ninst));
+    BP_TRY(dalloc(p, &w.i_rowinf, kPhaseSlots * (size_t)ninst));
+    BP_TRY(dalloc(p, &w.i_cross, kPhaseSlots * (size_t)ninst));
+    BP_TRY(dalloc(p, &w.i_chg, kPhaseSlots * (size_t)ninst));
     w.inst_cap = ninst;
     return BP_OK;
 }

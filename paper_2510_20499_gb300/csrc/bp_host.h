@@ -21,18 +21,21 @@ struct alignas(128) Pad {
     T v;
 };
 
+// Per-round counters rotate over kPhaseSlots slots: round t reads the counts of its worklist
+// from slot t % 3 and appends the next round's into slot (t + 1) % 3; its changed variables,
+// nonzeros and per-instance verdicts go to slot t % 3.  A slot is cleared two rounds after its
+// last reader, so no clearing races a reader or an append.
+constexpr int kPhaseSlots = 3;
+
 struct alignas(128) Ctl {
-    Pad<unsigned> bar_count;               // grid barrier: arrivals
-    Pad<unsigned> bar_gen;                 // grid barrier: generation
-    Pad<int> cnt[2][kNumClass];            // worklist rows appended, per parity and class
-    Pad<int> ntask[2];                     // chunk tasks appended, per parity
-    Pad<int> nchg[2];                      // changed variables appended, per parity
-    Pad<unsigned long long> nnz[2];        // nonzeros processed in the phase of that parity
+    Pad<unsigned> bar_count;                  // grid barrier arrivals, monotonic within a launch
+    Pad<int> cnt[kPhaseSlots][kNumClass];     // worklist rows of a round, per class
+    Pad<int> ntask[kPhaseSlots];              // chunk tasks of a round
+    Pad<int> nchg[kPhaseSlots];               // variables changed in a round
+    Pad<unsigned long long> nnz[kPhaseSlots]; // nonzeros processed in a round
     Pad<unsigned> done;
-    // written once per round by the last block at the barrier, read by thread 0 of each block
-    int stop, error;
-    int epi_par, epi_n;                    // changed list to crossing-check at the end
-    int phases;                            // phases run (advances the stamp base at exit)
+    int error;
+    int phases;                               // phases run (advances the stamp base at exit)
 };
 
 // State of one instance of a (possibly batched) propagation.
@@ -62,10 +65,10 @@ struct Work {
     Ctl* ctl_host = nullptr;                   // pinned constant template
     bp_result* dres = nullptr;                 // device result slots (one per instance)
     InstState* inst = nullptr;                 // per-instance state
-    unsigned long long* i_nnz = nullptr;       // [2][ninst]
-    int* i_rowinf = nullptr;                   // [2][ninst]
-    int* i_cross = nullptr;                    // [2][ninst]
-    int* i_chg = nullptr;                      // [2][ninst]
+    unsigned long long* i_nnz = nullptr;       // [kPhaseSlots][ninst]
+    int* i_rowinf = nullptr;                   // [kPhaseSlots][ninst]
+    int* i_cross = nullptr;                    // [kPhaseSlots][ninst]
+    int* i_chg = nullptr;                      // [kPhaseSlots][ninst]
     int inst_cap = 0;
     double* stage_lb = nullptr;                // device staging for host bounds
     double* stage_ub = nullptr;

@@ -79,10 +79,10 @@ size_t layout(const mip_problem* p, Carve& c, Work& w) {
     w.harr = c.take<int>(nheavy);
     w.dres = c.take<bp_result>(1);
     w.inst = c.take<InstState>(1);
-    w.i_nnz = c.take<unsigned long long>(2);
-    w.i_rowinf = c.take<int>(2);
-    w.i_cross = c.take<int>(2);
-    w.i_chg = c.take<int>(2);
+    w.i_nnz = c.take<unsigned long long>(kPhaseSlots);
+    w.i_rowinf = c.take<int>(kPhaseSlots);
+    w.i_cross = c.take<int>(kPhaseSlots);
+    w.i_chg = c.take<int>(kPhaseSlots);
     w.inst_cap = 1;
     return zero_bytes;
 }
