@@ -253,8 +253,9 @@ typedef struct {
  * var: device int32[P]; boxes: device double[4P] (see probe_split).
  * Returns BP_OK, BP_ERR_CAPACITY (cache->needed holds the required entry count; the status,
  * rounds, nnz_updates and offsets arrays are complete), BP_ERR_INVALID (also for a variable
- * index outside [0, n)).  The call synchronises the stream (it checks the variable indices
- * and reads the entry count).
+ * index outside [0, n): the kernel skips such a pair and flags it; the other arrays are then
+ * incomplete).  The call synchronises the stream once (it reads the entry count and the
+ * index flag together).
  */
 int bp_probe_batch(mip_problem *p, const double *root_lb, const double *root_ub, int32_t P,
                    const int32_t *var, const double *boxes, const bp_params *params,

@@ -17,7 +17,15 @@
 
 namespace gpubp {
 
-constexpr int kPThreads = 256;
+#ifndef GPUBP_PROBE_THREADS
+#define GPUBP_PROBE_THREADS 128
+#endif
+#ifndef GPUBP_PROBE_BLOCKS_PER_SM
+#define GPUBP_PROBE_BLOCKS_PER_SM 4
+#endif
+constexpr int kPThreads = GPUBP_PROBE_THREADS;     // a pair's few rows per round need few warps
+constexpr int kPBlocksPerSM = GPUBP_PROBE_BLOCKS_PER_SM;
+constexpr size_t kPScratchBudget = (size_t)16 << 30;   // bytes of per-block scratch at most
 constexpr int kPWarps = kPThreads / 32;
 constexpr int kPLane = 4;                  // nonzeros per lane held in registers per segment
 constexpr int kPSeg = 32 * kPLane;         // row segment processed in one wave by a warp
@@ -81,7 +89,7 @@ struct ProbeShared {
     int out_base;
 };
 
-__global__ void __launch_bounds__(kPThreads) probe_kernel(DevProblem P, ProbeArgs A) {
+__global__ void __launch_bounds__(kPThreads, kPBlocksPerSM) probe_kernel(DevProblem P, ProbeArgs A) {
     __shared__ ProbeShared sh;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int n = P.n, m = P.m;
@@ -110,6 +118,10 @@ __global__ void __launch_bounds__(kPThreads) probe_kernel(DevProblem P, ProbeArg
         if (tid < 2) {
             const int b = tid;
             const int v = A.var[pair];
+            if (v < 0 || v >= n) {   // caller's index out of range: the call reports BP_ERR_INVALID
+                if (b == 0) atomicExch(A.error, 1);
+                sh.v = -1;
+            } else {
             const longlong2 r = A.root[v];
             const longlong2 bx = make_longlong2(box_key(A.boxes[4 * pair + 2 * b]), box_key(A.boxes[4 * pair + 2 * b + 1]));
             const longlong2 s0 = meet(r, bx);
@@ -130,9 +142,11 @@ __global__ void __launch_bounds__(kPThreads) probe_kernel(DevProblem P, ProbeArg
             }
             sh.nchg[b][0] = sh.nchg[b][1] = 0;
             sh.wcount[0][b] = 0;
+            }
         }
         if (tid == 0) sh.nw[0] = 0;
         __syncthreads();
+        if (sh.v < 0) continue;
         // ---- round 0 worklist: the rows of the probed variable, for the live branches
         const int v = sh.v;
         const unsigned mask0 = (unsigned)(sh.alive[0] | (sh.alive[1] << 1));
@@ -355,14 +369,60 @@ __global__ void __launch_bounds__(kPThreads) probe_kernel(DevProblem P, ProbeArg
             const int nt = sh.ntouch[b];
             const int* tl = touched + (size_t)b * n;
             const longlong2* F = Sb(b, sh.rounds[b] & 1);
-            // sorted touched variables: in shared memory when few, else in index order from the stamps
-            const bool small = nt <= kPSort;
-            if (feas && small) {
-                for (int i = tid; i < kPSort; i += kPThreads) sh.sortbuf[i] = i < nt ? tl[i] : INT_MAX;
+            if (!feas || nt <= 32) {
+                // few touched variables (the usual case): one warp sorts them with shuffles and
+                // writes the entries that differ from the root, in variable order
+                if (w == 0) {
+                    int x = (feas && lane < nt) ? tl[lane] : INT_MAX;
+                    for (int k = 2; k <= 32; k <<= 1) {
+                        for (int j = k >> 1; j > 0; j >>= 1) {
+                            const int y = __shfl_xor_sync(0xffffffffu, x, j);
+                            x = (((lane & j) == 0) == ((lane & k) == 0)) ? min(x, y) : max(x, y);
+                        }
+                    }
+                    int d = 0;
+                    longlong2 xv = make_longlong2(0, 0);
+                    if (x != INT_MAX) {
+                        const longlong2 r = A.root[x];
+                        xv = meet(r, F[x]);
+                        d = (xv.x != r.x || xv.y != r.y) ? 1 : 0;
+                    }
+                    const unsigned msk = __ballot_sync(0xffffffffu, d);
+                    const int cnt = __popc(msk);
+                    unsigned long long base = 0;
+                    if (lane == 0) {
+                        A.status[e] = sh.status[b];
+                        A.rounds[e] = sh.rounds[b];
+                        A.nnzu[e] = (int64_t)sh.nnz[b];
+                        A.ecount[e] = cnt;
+                        base = cnt ? atomicAdd(A.ectr, (unsigned long long)cnt) : 0ull;
+                        A.estart[e] = (long long)base;
+                    }
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (d) {
+                        unsigned lt;
+                        asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+                        const long long pos = (long long)base + __popc(msk & lt);
+                        if (pos < A.ecap) {
+                            A.evar[pos] = x;
+                            A.el[pos] = kdec(xv.x);
+                            A.eu[pos] = kdec(xv.y);
+                        }
+                    }
+                }
                 __syncthreads();
-                for (int size = 2; size <= kPSort; size <<= 1) {
+            } else {
+            // sorted touched variables: in shared memory (the next power of two at or above the
+            // count) when few, else in index order from the stamps
+            const bool small = nt <= kPSort;
+            if (small) {
+                int p2 = 64;
+                while (p2 < nt) p2 <<= 1;
+                for (int i = tid; i < p2; i += kPThreads) sh.sortbuf[i] = i < nt ? tl[i] : INT_MAX;
+                __syncthreads();
+                for (int size = 2; size <= p2; size <<= 1) {
                     for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                        for (int i = tid; i < kPSort; i += kPThreads) {
+                        for (int i = tid; i < p2; i += kPThreads) {
                             const int jx = i ^ stride;
                             if (jx > i) {
                                 const bool up = (i & size) == 0;
@@ -378,7 +438,7 @@ __global__ void __launch_bounds__(kPThreads) probe_kernel(DevProblem P, ProbeArg
                 }
             }
             // count the entries that differ from the root, in variable order
-            const int span = feas ? (small ? nt : n) : 0;
+            const int span = small ? nt : n;
             long long cnt = 0;
             for (int base = 0; base < span; base += kPThreads) {
                 const int i = base + tid;
@@ -443,6 +503,7 @@ __global__ void __launch_bounds__(kPThreads) probe_kernel(DevProblem P, ProbeArg
                 }
                 written += sh.scan[kPThreads - 1];
                 __syncthreads();
+            }
             }
             // reset the touched variables of the branch to neutral
             for (int i = tid; i < nt; i += kPThreads) {
@@ -551,7 +612,13 @@ static int probe_prepare(mip_problem* p, int nbranches, long long cap, cudaStrea
         p->free_hooks[0] = probe_work_free;
         int sms = 0;
         BP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
-        pw->blocks = 2 * sms;
+        // blocks: kPBlocksPerSM per SM, fewer when their dense scratch (104 n + 16 m bytes each)
+        // would pass the budget, at least one per SM
+        const size_t per_block = 104 * (size_t)p->n + 16 * (size_t)p->m + 64;
+        size_t nb = (size_t)kPBlocksPerSM * sms;
+        if (nb * per_block > kPScratchBudget) nb = kPScratchBudget / per_block;
+        if (nb < (size_t)sms) nb = (size_t)sms;
+        pw->blocks = (int)nb;
         const size_t B = (size_t)pw->blocks, n = (size_t)p->n, m = (size_t)p->m;
         BP_TRY(dalloc(p, &pw->S, B * 4 * n));
         BP_TRY(dalloc(p, &pw->vst, B * 2 * n));
@@ -561,7 +628,7 @@ static int probe_prepare(mip_problem* p, int nbranches, long long cap, cudaStrea
         BP_TRY(dalloc(p, &pw->touched, B * 2 * n));
         BP_TRY(dalloc(p, &pw->ep, B));
         BP_TRY(dalloc(p, &pw->ctr, 1));
-        BP_TRY(dalloc(p, &pw->ectr, 1));
+        BP_TRY(dalloc(p, &pw->ectr, 2));
         if (B * 4 * n) k_fill_neutral<<<1024, 256, 0, s>>>(B * 4 * n, pw->S);
         BP_CUDA_TRY(cudaGetLastError());
     }
@@ -611,24 +678,12 @@ extern "C" int bp_probe_batch(mip_problem* p, const double* root_lb, const doubl
         BP_CUDA_TRY(cudaStreamSynchronize(s));
         return BP_OK;
     }
-    // variables must be in range: checked on the device copy by a small kernel would cost a
-    // sync; the host reads them once (the call synchronises anyway)
-    {
-        std::vector<int32_t> hv((size_t)npairs);
-        BP_CUDA_TRY(cudaMemcpyAsync(hv.data(), var, sizeof(int32_t) * npairs, cudaMemcpyDeviceToHost, s));
-        BP_CUDA_TRY(cudaStreamSynchronize(s));
-        for (int32_t x : hv)
-            if (x < 0 || x >= p->n) {
-                set_error("bp_probe_batch: variable index %d out of range", x);
-                return BP_ERR_INVALID;
-            }
-    }
     BP_TRY(probe_prepare(p, 2 * npairs, cache->cap > 0 ? cache->cap : 1, s));
     ProbeWork* pw = probe_work(p);
     longlong2* root = p->w.bkey[0];
     BP_TRY(root_keys(p, root_lb, root_ub, root, s));
     BP_CUDA_TRY(cudaMemsetAsync(pw->ctr, 0, sizeof(int), s));
-    BP_CUDA_TRY(cudaMemsetAsync(pw->ectr, 0, sizeof(unsigned long long), s));
+    BP_CUDA_TRY(cudaMemsetAsync(pw->ectr, 0, 2 * sizeof(unsigned long long), s));   // entry total, index error
     ProbeArgs a;
     a.root = root;
     a.var = var;
@@ -654,14 +709,19 @@ extern "C" int bp_probe_batch(mip_problem* p, const double* root_lb, const doubl
     a.eu = pw->tu;
     a.ectr = pw->ectr;
     a.ecap = pw->tcap;
-    a.error = nullptr;
+    a.error = reinterpret_cast<int*>(pw->ectr + 1);
     probe_kernel<<<pw->blocks, kPThreads, 0, s>>>(p->dp, a);
     BP_CUDA_TRY(cudaGetLastError());
     const int nb = 2 * npairs;
     k_probe_offsets<<<1, 1024, 0, s>>>(nb, pw->ecount, cache->offsets, pw->ectr);
-    unsigned long long total = 0;
-    BP_CUDA_TRY(cudaMemcpyAsync(&total, pw->ectr, sizeof(total), cudaMemcpyDeviceToHost, s));
+    unsigned long long words[2] = {0, 0};   // entry total and the index check, read together
+    BP_CUDA_TRY(cudaMemcpyAsync(words, pw->ectr, sizeof(words), cudaMemcpyDeviceToHost, s));
     BP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (words[1]) {
+        set_error("bp_probe_batch: a variable index is outside [0, n)");
+        return BP_ERR_INVALID;
+    }
+    const unsigned long long total = words[0];
     cache->needed = (int64_t)total;
     if ((long long)total > cache->cap) {
         set_error("probing cache needs %llu entries, capacity %lld", total, (long long)cache->cap);

@@ -159,3 +159,23 @@ def test_priority_general_data(pkg):
     assert sorted(gord.tolist()) == np.flatnonzero(o1 >= 0).tolist()
     keys = [(-g1[j], -g2[j], g3[j], j) for j in gord]
     assert keys == sorted(keys)
+
+
+def test_probe_index_out_of_range(pkg):
+    """A variable index outside [0, n) is reported (BP_ERR_INVALID), never dereferenced, and the
+    handle stays usable: the same call with valid indices then matches the oracle."""
+    import torch
+    p = synth.knapsack_cover(seed=11, m=300, n=600, nnz=4000)
+    P = oracle.Problem(p)
+    rl, ru, _, _ = P.bp(p.lb, p.ub)
+    var, boxes = _pairs(p, rl, ru, 40, 3)
+    prob = pkg.Problem(p)
+    dl, du = torch.tensor(rl, device="cuda"), torch.tensor(ru, device="cuda")
+    for bad in (p.n, -1):
+        v = var.copy()
+        v[7] = bad
+        with pytest.raises(pkg.GpuBpError) as e:
+            prob.probe_batch(dl, du, torch.tensor(v, device="cuda"), torch.tensor(boxes, device="cuda"))
+        assert e.value.code == pkg.BP_ERR_INVALID
+    c = prob.probe_batch(dl, du, torch.tensor(var, device="cuda"), torch.tensor(boxes, device="cuda"))
+    _compare(p, {k: x.cpu().numpy() for k, x in c.items()}, P.probe_batch(rl, ru, var, boxes))
