@@ -30,6 +30,8 @@ constexpr int kPWarps = kPThreads / 32;
 constexpr int kPLane = 4;                  // nonzeros per lane held in registers per segment
 constexpr int kPSeg = 32 * kPLane;         // row segment processed in one wave by a warp
 constexpr int kPSort = 4096;               // touched lists up to this size are sorted in shared memory
+constexpr int kTSet = 1024;                // set of the variables a pair touched (shared memory)
+constexpr int kTProbe = 32;                // linear probes before the set counts as full
 
 struct ProbeArgs {
     const longlong2* root;       // n root keys
@@ -84,10 +86,44 @@ struct ProbeShared {
     int nchg[2][2];              // [branch][parity]
     int ntouch[2];
     unsigned long long ep_pair, ep_t;
+    int tset[kTSet];             // open addressing, variable + 1 (0 = empty); cleared per pair
+    int tset_full;
     int sortbuf[kPSort];
     int scan[kPThreads];
     int out_base;
 };
+
+// The pair's touched-variable set: a variable outside it has its root bounds in both branches,
+// so its gathers read the (L2-resident) root keys and skip the block's dense scratch, which is
+// spread over gigabytes and misses L2.  A full set answers "touched" for every variable, which
+// only costs the scratch read.
+__device__ __forceinline__ unsigned tset_hash(int j) { return ((unsigned)j * 2654435761u) >> 22; }   // 10 bits
+
+__device__ __forceinline__ void tset_insert(ProbeShared& sh, int j) {
+    const int key = j + 1;
+    unsigned h = tset_hash(j);
+    for (int q = 0; q < kTProbe; ++q, h = (h + 1) & (kTSet - 1)) {
+        const int cur = sh.tset[h];
+        if (cur == key) return;
+        if (cur == 0) {
+            const int seen = atomicCAS(&sh.tset[h], 0, key);
+            if (seen == 0 || seen == key) return;
+        }
+    }
+    sh.tset_full = 1;
+}
+
+__device__ __forceinline__ bool tset_has(const ProbeShared& sh, int j) {
+    if (sh.tset_full) return true;
+    const int key = j + 1;
+    unsigned h = tset_hash(j);
+    for (int q = 0; q < kTProbe; ++q, h = (h + 1) & (kTSet - 1)) {
+        const int cur = sh.tset[h];
+        if (cur == key) return true;
+        if (cur == 0) return false;
+    }
+    return true;
+}
 
 __global__ void __launch_bounds__(kPThreads, kPBlocksPerSM) probe_kernel(DevProblem P, ProbeArgs A) {
     __shared__ ProbeShared sh;
@@ -114,6 +150,8 @@ __global__ void __launch_bounds__(kPThreads, kPBlocksPerSM) probe_kernel(DevProb
         const int pair = sh.pair;
         if (pair >= A.npairs) break;
         const unsigned long long ep_pair = sh.ep_pair;
+        for (int i = tid; i < kTSet; i += kPThreads) sh.tset[i] = 0;
+        if (tid == 0) sh.tset_full = 0;
         // ---- branch set-up: start box = root ∩ branch box of the probed variable
         if (tid < 2) {
             const int b = tid;
@@ -149,6 +187,7 @@ __global__ void __launch_bounds__(kPThreads, kPBlocksPerSM) probe_kernel(DevProb
         if (sh.v < 0) continue;
         // ---- round 0 worklist: the rows of the probed variable, for the live branches
         const int v = sh.v;
+        if (tid == 0) tset_insert(sh, v);
         const unsigned mask0 = (unsigned)(sh.alive[0] | (sh.alive[1] << 1));
         if (mask0) {
             const int cb = P.col_ptr[v], ce = P.col_ptr[v + 1];
@@ -238,7 +277,7 @@ __global__ void __launch_bounds__(kPThreads, kPBlocksPerSM) probe_kernel(DevProb
                         const longlong2 r = __ldcg(A.root + jj[i]);
 #pragma unroll
                         for (int b = 0; b < 2; ++b)
-                            bb[b][i] = (mask >> b & 1) ? meet(r, __ldcg(Sb(b, par) + jj[i])) : r;
+                            bb[b][i] = (mask >> b & 1) && tset_has(sh, jj[i]) ? meet(r, __ldcg(Sb(b, par) + jj[i])) : r;
                     }
 #pragma unroll
                     for (int i = 0; i < kPLane; ++i) {
@@ -289,7 +328,9 @@ __global__ void __launch_bounds__(kPThreads, kPBlocksPerSM) probe_kernel(DevProb
                                 const int q = s0 + lane + 32 * i;
                                 j = q < end ? P.col[q] : -1;
                                 a = q < end ? P.val[q] : 0.0;
-                                bk = j >= 0 ? meet(__ldcg(A.root + j), __ldcg(Sb(b, par) + j)) : make_longlong2(0, 0);
+                                bk = j < 0 ? make_longlong2(0, 0)
+                                           : tset_has(sh, j) ? meet(__ldcg(A.root + j), __ldcg(Sb(b, par) + j))
+                                                             : __ldcg(A.root + j);
                             }
                             if (j < 0) continue;
                             if (ni[b] == 1 ? j != ij[b] : cannot_tighten(f, a, bk.x, bk.y)) continue;
@@ -300,7 +341,10 @@ __global__ void __launch_bounds__(kPThreads, kPBlocksPerSM) probe_kernel(DevProb
                             else atomicMax(&X[j].x, nk);
                             const unsigned long long old = atomicMax(&vst[(size_t)b * n + j], ep_t);
                             if (old < ep_t) chgb(b, par)[atomicAdd(&sh.nchg[b][par], 1)] = j;
-                            if (old < ep_pair) touched[(size_t)b * n + atomicAdd(&sh.ntouch[b], 1)] = j;
+                            if (old < ep_pair) {
+                                touched[(size_t)b * n + atomicAdd(&sh.ntouch[b], 1)] = j;
+                                tset_insert(sh, j);
+                            }
                         }
                     }
                 }
