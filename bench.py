@@ -368,6 +368,7 @@ def learned_extra(pkg, torch, dev):
                         "feasible_verified": len(ok),
                         "bulks_to_feasibility": float(np.mean([r["bulks"] for r in ok])) if ok else None,
                         "bulks_mean_all_runs": float(np.mean([r["bulks"] for r in rs])),
+                        "fixed_by_choice_mean": float(np.mean([r["fixed_by_choice"] for r in rs])),
                         "seconds_per_run": t_run[arm] / len(rs)}
         out[f"test_{nnz // 1000}k_nnz"] = rep
     return out
