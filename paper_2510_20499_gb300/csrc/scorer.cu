@@ -42,23 +42,27 @@ constexpr int kImgW3 = 10240;             // [16 out (2 used) x 64 in]
 constexpr int kImgW2T = 12288;            // [64 in x 64 out]
 constexpr int kImgBytes = 20480;
 
-// shared memory of the MLP kernel, byte offsets (1 KB aligned tiles)
+// shared memory of the forward kernel, byte offsets (1 KB aligned tiles)
 constexpr int kSX = 0;                    // X tile       128 x 16
 constexpr int kSH1 = kSX + 4096;          // H1 tile      128 x 64
 constexpr int kSH2 = kSH1 + 16384;        // H2 tile      128 x 64
 constexpr int kSW = kSH2 + 16384;         // weight images
-constexpr int kSDZ2 = kSW + kImgBytes;    // dZ2 tile     128 x 64           (training)
-constexpr int kSAW = kSDZ2 + 16384;       // [dZ2 | dZ1]^T 128 x 128 (K = rows) (training)
-constexpr int kSBW = kSAW + 32768;        // [H1 | X | 1]^T 96 x 128            (training)
-constexpr int kSF = kSBW + 24576;         // floats: b1[64] b2[64] b3[4] w3q[128] dz[256] red[4]
-constexpr int kSFloats = 64 + 64 + 4 + 128 + 256 + 4;
-constexpr int kSMisc = kSF + kSFloats * 4;   // mbarrier (8) and TMEM address (4)
-constexpr int kSmemTrain = kSMisc + 16;
-// forward only: the training tiles are left out, so that several CTAs share an SM (their
-// tiles' latency chains overlap)
+constexpr int kSFloats = 64 + 64 + 4 + 128 + 256 + 4;   // b1[64] b2[64] b3[4] w3q[128] dz[256] red[4]
 constexpr int kSFFwd = kSW + kImgBytes;
-constexpr int kSMiscFwd = kSFFwd + kSFloats * 4;
-constexpr int kSmemFwd = kSMiscFwd + 16;
+constexpr int kSMiscFwd = kSFFwd + kSFloats * 4;        // mbarrier (8) and TMEM address (4)
+constexpr int kSmemFwd = kSMiscFwd + 16;  // 58 KB: several CTAs share an SM, their tiles' chains overlap
+// shared memory of the training kernel: tiles that are dead by the time another is written
+// share space, so that two CTAs fit on an SM (110.7 KB each)
+constexpr int kTH1 = 0;                   // H1 tile      128 x 64   (read by layer 2 only)
+constexpr int kTDZ2 = kTH1;               // dZ2 tile     128 x 64   (written after layer 3)
+constexpr int kTH2 = kTH1 + 16384;        // H2 tile      128 x 64
+constexpr int kTW = kTH2 + 16384;         // weight images
+constexpr int kTAW = kTW + kImgBytes;     // [dZ2 | dZ1]^T 128 x 128 (K = rows)
+constexpr int kTX = kTAW;                 // X tile       128 x 16   (read by layer 1 only)
+constexpr int kTBW = kTAW + 32768;        // [H1 | X | 1]^T 96 x 128
+constexpr int kTF = kTBW + 24576;         // floats
+constexpr int kTMisc = kTF + kSFloats * 4;
+constexpr int kSmemTrain = kTMisc + 16;
 constexpr int kTmemColsTrain = 256;       // 0..63: layer 1 / layer 3 / dH1, 64..127: layer 2, 128..223: weight grads
 constexpr int kTmemColsFwd = 128;         // 0..63: layer 1 / layer 3, 64..127: layer 2
 constexpr int kTmemColsSM = 512;          // tensor memory columns of an SM
@@ -122,14 +126,14 @@ template <bool kTrain>
 __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp(MlpArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     const int t = threadIdx.x, warp = t >> 5;
-    unsigned char* Xs = sm + kSX;
-    unsigned char* H1s = sm + kSH1;
-    unsigned char* H2s = sm + kSH2;
-    unsigned char* Ws = sm + kSW;
-    unsigned char* DZ2s = sm + kSDZ2;
-    unsigned char* Aw = sm + kSAW;
-    unsigned char* Bw = sm + kSBW;
-    constexpr int kF = kTrain ? kSF : kSFFwd, kMisc = kTrain ? kSMisc : kSMiscFwd;
+    unsigned char* Xs = sm + (kTrain ? kTX : kSX);
+    unsigned char* H1s = sm + (kTrain ? kTH1 : kSH1);
+    unsigned char* H2s = sm + (kTrain ? kTH2 : kSH2);
+    unsigned char* Ws = sm + (kTrain ? kTW : kSW);
+    unsigned char* DZ2s = sm + kTDZ2;     // training only
+    unsigned char* Aw = sm + kTAW;
+    unsigned char* Bw = sm + kTBW;
+    constexpr int kF = kTrain ? kTF : kSFFwd, kMisc = kTrain ? kTMisc : kSMiscFwd;
     constexpr uint32_t kTmemCols = kTrain ? kTmemColsTrain : kTmemColsFwd;
     float* b1 = reinterpret_cast<float*>(sm + kF);
     float* b2 = b1 + 64;
@@ -615,12 +619,13 @@ struct scorer {
     int device = 0;
     int sms = 0;
     int fwd_per_sm = 1;        // resident forward CTAs per SM (shared memory and tensor memory bound)
+    int train_per_sm = 1;      // resident training CTAs per SM
     float* params = nullptr;   // FP32 masters
     float* m = nullptr;
     float* v = nullptr;
     long long steps = 0;       // Adam steps taken
     unsigned char* wimg = nullptr;
-    float* partial = nullptr;  // sms x (kNParam + 1)
+    float* partial = nullptr;  // sms x train_per_sm x (kNParam + 1)
     float* grad = nullptr;     // kNParam + 1 (last: loss)
     int* counts = nullptr;
     int* error = nullptr;
@@ -658,7 +663,8 @@ int gradient(scorer* s, const uint16_t* feat, const float* labels, int rows, cud
     k_label_counts<<<lb < 4 * s->sms ? (lb > 0 ? lb : 1) : 4 * s->sms, 256, 0, st>>>(labels, rows, s->counts);
     MlpArgs a{feat, rows, s->wimg, s->params, nullptr, labels, s->counts, s->partial, s->error};
     const int ntiles = (rows + kTile - 1) / kTile;
-    const int grid = ntiles < s->sms ? (ntiles > 0 ? ntiles : 1) : s->sms;
+    const int cap = s->sms * s->train_per_sm;
+    const int grid = ntiles < cap ? (ntiles > 0 ? ntiles : 1) : cap;
     k_mlp<true><<<grid, kMlpThreads, kSmemTrain, st>>>(a);
     BP_CUDA_TRY(cudaGetLastError());
     k_grad_sum<<<grid_for(kNParam + 1), 256, 0, st>>>(s->partial, grid, s->grad);
@@ -677,11 +683,20 @@ extern "C" int scorer_create(int32_t in, int32_t hidden, int32_t out, uint64_t s
     scorer* s = new scorer();
     BP_CUDA_TRY(cudaGetDevice(&s->device));
     BP_CUDA_TRY(cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device));
+    int smem_sm = 0;
+    BP_CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, s->device));
+    // CTAs per SM: as many as shared memory (1 KB reserved per CTA) and tensor memory hold.  The
+    // occupancy calculator reports 1 for these kernels, yet measured on GB300 several CTAs per SM
+    // run faster.  Extra CTAs are safe whatever the residency: a CTA never waits on another, and
+    // tcgen05.alloc only waits for columns that a running CTA frees at its end.
+    s->fwd_per_sm = std::max(1, std::min(smem_sm / (kSmemFwd + 1024), kTmemColsSM / kTmemColsFwd));
+    s->train_per_sm = std::max(1, std::min(smem_sm / (kSmemTrain + 1024), kTmemColsSM / kTmemColsTrain));
     bool okalloc = cudaMalloc(&s->params, sizeof(float) * kNParam) == cudaSuccess &&
                    cudaMalloc(&s->m, sizeof(float) * kNParam) == cudaSuccess &&
                    cudaMalloc(&s->v, sizeof(float) * kNParam) == cudaSuccess &&
                    cudaMalloc(&s->wimg, kImgBytes) == cudaSuccess &&
-                   cudaMalloc(&s->partial, sizeof(float) * (size_t)s->sms * (kNParam + 1)) == cudaSuccess &&
+                   cudaMalloc(&s->partial, sizeof(float) * (size_t)s->sms * s->train_per_sm * (kNParam + 1)) ==
+                       cudaSuccess &&
                    cudaMalloc(&s->grad, sizeof(float) * (kNParam + 1)) == cudaSuccess &&
                    cudaMalloc(&s->counts, 2 * sizeof(int)) == cudaSuccess &&
                    cudaMalloc(&s->error, sizeof(int)) == cudaSuccess;
@@ -694,23 +709,18 @@ extern "C" int scorer_create(int32_t in, int32_t hidden, int32_t out, uint64_t s
     cudaError_t e = cudaFuncSetAttribute(k_mlp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTrain);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_mlp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemFwd);
-    // the forward kernel's CTAs share an SM only with a shared-memory carveout that holds them
+    // several CTAs share an SM only with a shared-memory carveout that holds them
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_mlp<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
-    int smem_sm = 0;
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, s->device);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_mlp<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) {
         scorer_release(s);
         delete s;
         return fail_cuda(e, "cudaFuncSetAttribute");
     }
-    // Forward CTAs per SM: as many as shared memory (1 KB reserved per CTA) and tensor memory
-    // (kTmemColsFwd columns each) hold.  The occupancy calculator reports 1 for this kernel, yet
-    // measured on GB300 three CTAs per SM run 1.3-1.4x faster than one.  Extra CTAs are safe
-    // whatever the residency: a CTA never waits on another, and tcgen05.alloc only waits for
-    // columns that a running CTA frees at its end.
-    s->fwd_per_sm = std::max(1, std::min(smem_sm / (kSmemFwd + 1024), kTmemColsSM / kTmemColsFwd));
     // He-uniform weights, zero biases (splitmix64 chain, as the rounding draws)
     std::vector<float> h(kNParam, 0.0f);
     auto sm64 = [](uint64_t z) {
