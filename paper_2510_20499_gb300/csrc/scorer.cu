@@ -42,15 +42,17 @@ constexpr int kImgW3 = 10240;             // [16 out (2 used) x 64 in]
 constexpr int kImgW2T = 12288;            // [64 in x 64 out]
 constexpr int kImgBytes = 20480;
 
-// shared memory of the forward kernel, byte offsets (1 KB aligned tiles)
+// shared memory of the forward kernel, byte offsets (1 KB aligned tiles).  H2 overwrites H1
+// (layer 2 has read H1 by then) and the transposed W2 image of the backward pass is left out:
+// 34 KB, so that six CTAs share an SM and their tiles' latency chains overlap.
 constexpr int kSX = 0;                    // X tile       128 x 16
-constexpr int kSH1 = kSX + 4096;          // H1 tile      128 x 64
-constexpr int kSH2 = kSH1 + 16384;        // H2 tile      128 x 64
-constexpr int kSW = kSH2 + 16384;         // weight images
+constexpr int kSH1 = kSX + 4096;          // H1, then H2  128 x 64
+constexpr int kSW = kSH1 + 16384;         // weight images W1, W2, W3
+constexpr int kImgFwdBytes = kImgW2T;     // the images the forward pass reads
 constexpr int kSFloats = 64 + 64 + 4 + 128 + 256 + 4;   // b1[64] b2[64] b3[4] w3q[128] dz[256] red[4]
-constexpr int kSFFwd = kSW + kImgBytes;
+constexpr int kSFFwd = kSW + kImgFwdBytes;
 constexpr int kSMiscFwd = kSFFwd + kSFloats * 4;        // mbarrier (8) and TMEM address (4)
-constexpr int kSmemFwd = kSMiscFwd + 16;  // 58 KB: several CTAs share an SM, their tiles' chains overlap
+constexpr int kSmemFwd = kSMiscFwd + 16;
 // shared memory of the training kernel: tiles that are dead by the time another is written
 // share space, so that two CTAs fit on an SM (110.7 KB each)
 constexpr int kTH1 = 0;                   // H1 tile      128 x 64   (read by layer 2 only)
@@ -64,7 +66,7 @@ constexpr int kTF = kTBW + 24576;         // floats
 constexpr int kTMisc = kTF + kSFloats * 4;
 constexpr int kSmemTrain = kTMisc + 16;
 constexpr int kTmemColsTrain = 256;       // 0..63: layer 1 / layer 3 / dH1, 64..127: layer 2, 128..223: weight grads
-constexpr int kTmemColsFwd = 128;         // 0..63: layer 1 / layer 3, 64..127: layer 2
+constexpr int kTmemColsFwd = 64;          // 0..63: layer 1, then layer 2, then layer 3 (each read out first)
 constexpr int kTmemColsSM = 512;          // tensor memory columns of an SM
 
 struct MlpArgs {
@@ -128,13 +130,14 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp(MlpArgs a) {
     const int t = threadIdx.x, warp = t >> 5;
     unsigned char* Xs = sm + (kTrain ? kTX : kSX);
     unsigned char* H1s = sm + (kTrain ? kTH1 : kSH1);
-    unsigned char* H2s = sm + (kTrain ? kTH2 : kSH2);
+    unsigned char* H2s = sm + (kTrain ? kTH2 : kSH1);
     unsigned char* Ws = sm + (kTrain ? kTW : kSW);
     unsigned char* DZ2s = sm + kTDZ2;     // training only
     unsigned char* Aw = sm + kTAW;
     unsigned char* Bw = sm + kTBW;
     constexpr int kF = kTrain ? kTF : kSFFwd, kMisc = kTrain ? kTMisc : kSMiscFwd;
     constexpr uint32_t kTmemCols = kTrain ? kTmemColsTrain : kTmemColsFwd;
+    constexpr uint32_t kL2 = kTrain ? 64 : 0;   // accumulator columns of layer 2
     float* b1 = reinterpret_cast<float*>(sm + kF);
     float* b2 = b1 + 64;
     float* b3 = b2 + 64;
@@ -145,7 +148,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp(MlpArgs a) {
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kMisc + 8);
     const uint32_t mbar = tc::smem_u32(mbar_p);
 
-    for (int i = t; i < kImgBytes / 16; i += kMlpThreads)
+    for (int i = t; i < (kTrain ? kImgBytes : kImgFwdBytes) / 16; i += kMlpThreads)
         reinterpret_cast<uint4*>(Ws)[i] = reinterpret_cast<const uint4*>(a.wimg)[i];
     if (t < kHid) {
         b1[t] = a.params[ob1 + t];
@@ -213,13 +216,13 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp(MlpArgs a) {
         // ---- layer 2: D[64..127] = H1 W2^T
         if (t == 0) {
             for (int kk = 0; kk < 4; ++kk)
-                tc::mma(tm + 64, tc::sdesc(tc::smem_u32(H1s) + 256 * kk, 128, 1024), tc::sdesc(sW2 + 256 * kk, 128, 1024),
+                tc::mma(tm + kL2, tc::sdesc(tc::smem_u32(H1s) + 256 * kk, 128, 1024), tc::sdesc(sW2 + 256 * kk, 128, 1024),
                         tc::idesc_bf16(128, 64), kk > 0);
             tc::commit(mbar);
         }
         if (!(ok = wait_mma(mbar, phase))) break;
         uint16_t h2[kHid];
-        hidden_from_tmem(tm + lane + 64, b2, H2s, t, h2);
+        hidden_from_tmem(tm + lane + kL2, b2, H2s, t, h2);
         sync_for_mma();
         // ---- layer 3: D[0..15] = H2 W3^T (2 of 16 output columns used)
         if (t == 0) {
