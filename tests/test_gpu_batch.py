@@ -117,3 +117,30 @@ def test_set_instances_rejects_crossing_rows(pkg):
     prob = pkg.Problem(big)
     with pytest.raises(pkg.GpuBpError):
         prob.set_instances(ro, [0, co[2], co[1] + 1, co[3]] if co[2] > co[1] + 1 else [0, 1, 2, co[3]])
+
+
+def test_uneven_batch_full_size_autotuned(pkg):
+    """The benchmark's batch (64 instances, nnz log-uniform in [1e3, 5e5], 5.4M nonzeros) in
+    the configurations the benchmark times: the default split points and the ones bp_autotune
+    picks.  Every instance against its own oracle run."""
+    import torch
+    parts = synth.uneven_batch()
+    big, ro, co = synth.block_diagonal(parts)
+    prob = pkg.Problem(big)
+    prob.set_instances(ro, co)
+    lb0 = torch.tensor(big.lb, device="cuda")
+    ub0 = torch.tensor(big.ub, device="cuda")
+
+    def run():
+        gl, gu = lb0.clone(), ub0.clone()
+        res = prob.propagate_batch(gl, gu)
+        torch.cuda.synchronize()
+        return gl.cpu().numpy(), gu.cpu().numpy(), pkg.batch_results(res)
+
+    gl, gu, gres = run()
+    _compare_instances(parts, ro, co, gl, gu, gres)
+    prob.autotune(lb0, ub0, reps=1)
+    gl2, gu2, gres2 = run()
+    assert gres2 == gres
+    np.testing.assert_array_equal(gl2, gl)
+    np.testing.assert_array_equal(gu2, gu)

@@ -123,3 +123,22 @@ def test_learned_order_beats_plain(pkg, trained):
     assert parity >= 1
     if ok0:
         assert mean_bulks(ok1) < mean_bulks(ok0)
+
+
+def test_plain_fix_and_propagate_1m_matches_oracle(pkg):
+    """Fix-and-propagate at the size the benchmark times it (1M nonzeros, 1% bulks) against the
+    oracle's run: same verdict, bulks, recoveries and fixings; integer values bit-exact and
+    continuous values within 1e-9 when the oracle reports no fragile decision."""
+    p, x = synth.rounding_instance(2000, 1_000_000)
+    prob = pkg.Problem(p)
+    xd, lb, ub = _dev(p, x)
+    xo, r = prob.fix_and_propagate(xd, lb, ub, seed=1, **FP)
+    xo = xo.cpu().numpy()
+    ox, orr = oracle.Problem(p).fix_and_propagate(x, p.lb, p.ub, seed=1, **FP)
+    if orr["fragile"]:
+        pytest.skip(f"the oracle reports {orr['fragile']} fragile decisions")
+    for key in ("status", "bulks", "bp_runs", "recoveries", "fixed_by_choice", "nnz_updates"):
+        assert r[key] == orr[key], (key, r[key], orr[key])
+    ints = p.is_int == 1
+    np.testing.assert_array_equal(xo[ints], ox[ints])
+    np.testing.assert_allclose(xo[~ints], ox[~ints], rtol=1e-9, atol=1e-9)
