@@ -184,8 +184,30 @@ def cpu_baseline(p, budget_s=12.0):
         nnz += r["nnz_updates"]
         runs += 1
     dt = time.perf_counter() - t0
-    return {"value": nnz / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{runs} full propagations of the workload ({dt:.1f} s, single thread)"}
+    out = {"value": nnz / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{runs} full propagations of the workload ({dt:.1f} s, single thread)"}
+    out["probing"] = cpu_probing_baseline()
+    return out
+
+
+def cpu_probing_baseline(pairs=512):
+    """The oracle's double probing on the probing workload (knapsack/cover 50k x 100k, 1M nnz),
+    on the first `pairs` variables of the priority order (a bounded sample of the 2,048 the GPU
+    probes), single thread."""
+    import numpy as np
+    import oracle
+    from paper_2510_20499_gb300 import synth
+    p = synth.knapsack_cover()
+    P = oracle.Problem(p)
+    rl, ru, _, _ = P.bp(p.lb, p.ub)
+    k1, k2, k3 = P.probe_priority(rl, ru)
+    var = oracle.priority_order(k1, k2, k3)[:pairs].astype(np.int32)
+    boxes = np.array([oracle.probe_split(1, rl[j], ru[j]) for j in var], dtype=np.float64).reshape(-1, 4)
+    t0 = time.perf_counter()
+    P.probe_batch(rl, ru, var, boxes)
+    dt = time.perf_counter() - t0
+    return {"probes_per_s": 2 * len(var) / dt, "cores": 1, "kind": "oracle",
+            "sample": f"{len(var)} priority pairs = {2 * len(var)} propagations ({dt:.1f} s, single thread)"}
 
 
 def probing_extra(pkg, torch, dev):
