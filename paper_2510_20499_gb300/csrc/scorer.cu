@@ -111,7 +111,13 @@ __device__ __forceinline__ void hidden_from_tmem(uint32_t taddr, const float* bi
         float v[16];
         tc::tmem_ld16(taddr + 16 * c4, v);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) hb[16 * c4 + j] = tc::bf16_bits(fmaxf(v[j] + bias[16 * c4 + j], 0.0f));
+        for (int j = 0; j < 16; j += 2) {
+            // ReLU output is finite (fmaxf drops a NaN sum): the packed hardware conversion applies
+            const uint32_t pk = tc::bf16x2_bits(fmaxf(v[j] + bias[16 * c4 + j], 0.0f),
+                                                fmaxf(v[j + 1] + bias[16 * c4 + j + 1], 0.0f));
+            hb[16 * c4 + j] = (uint16_t)pk;
+            hb[16 * c4 + j + 1] = (uint16_t)(pk >> 16);
+        }
     }
 #pragma unroll
     for (int kc = 0; kc < 8; ++kc) {
@@ -125,7 +131,7 @@ __device__ __forceinline__ void hidden_from_tmem(uint32_t taddr, const float* bi
 }
 
 template <bool kTrain>
-__global__ void __launch_bounds__(kMlpThreads, 1) k_mlp(MlpArgs a) {
+__global__ void __launch_bounds__(kMlpThreads, kTrain ? 2 : 6) k_mlp(MlpArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     const int t = threadIdx.x, warp = t >> 5;
     unsigned char* Xs = sm + (kTrain ? kTX : kSX);
@@ -258,8 +264,12 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp(MlpArgs a) {
             // [dZ2 | dZ1]^T (column t)
             uint16_t g2[kHid];
 #pragma unroll
-            for (int i = 0; i < kHid; ++i)
-                g2[i] = h2[i] != 0 ? tc::bf16_bits(d0 * w3q[i] + d1 * w3q[kHid + i]) : (uint16_t)0;
+            for (int i = 0; i < kHid; i += 2) {   // finite products: the packed conversion applies
+                const uint32_t pk = tc::bf16x2_bits(d0 * w3q[i] + d1 * w3q[kHid + i],
+                                                    d0 * w3q[i + 1] + d1 * w3q[kHid + i + 1]);
+                g2[i] = h2[i] != 0 ? (uint16_t)pk : (uint16_t)0;
+                g2[i + 1] = h2[i + 1] != 0 ? (uint16_t)(pk >> 16) : (uint16_t)0;
+            }
 #pragma unroll
             for (int kc = 0; kc < 8; ++kc) {
                 uint4 q;
@@ -293,9 +303,11 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp(MlpArgs a) {
                 float v[16];
                 tc::tmem_ld16(tm + lane + 16 * c4, v);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
+                for (int j = 0; j < 16; j += 2) {
                     const int i = 16 * c4 + j;
-                    *at16(Aw, tc::tile_off(64 + i, t, kTile)) = h1[i] != 0 ? tc::bf16_bits(v[j]) : (uint16_t)0;
+                    const uint32_t pk = tc::bf16x2_bits(v[j], v[j + 1]);
+                    *at16(Aw, tc::tile_off(64 + i, t, kTile)) = h1[i] != 0 ? (uint16_t)pk : (uint16_t)0;
+                    *at16(Aw, tc::tile_off(64 + i + 1, t, kTile)) = h1[i + 1] != 0 ? (uint16_t)(pk >> 16) : (uint16_t)0;
                 }
             }
             sync_for_mma();

@@ -10,6 +10,7 @@
 // offset) and K * 16 bytes apart along R (its stride byte offset).  One MMA consumes a K = 16
 // slice, i.e. two core matrices along K; slice s starts 256 * s bytes after the tile.
 #pragma once
+#include <cuda_bf16.h>
 #include <cstdint>
 
 namespace gpubp {
@@ -114,6 +115,12 @@ __device__ __forceinline__ uint16_t bf16_bits(float f) {
     return (uint16_t)(r >> 16);
 }
 __device__ __forceinline__ float bf16_float(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
+// Two finite floats to BF16 (nearest, ties to even) in one hardware conversion: lo in bits 0..15,
+// hi in bits 16..31.  Equal to bf16_bits on every finite value.
+__device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
 
 }  // namespace tc
 }  // namespace gpubp
