@@ -85,7 +85,7 @@ struct ProbeShared {
     int wcount[2][2];            // [parity][branch] entries holding the branch
     int nchg[2][2];              // [branch][parity]
     int ntouch[2];
-    unsigned long long ep_pair, ep_t;
+    unsigned long long ep_pair, ep_t, ep;
     int tset[kTSet];             // open addressing, variable + 1 (0 = empty); cleared per pair
     int tset_full;
     int sortbuf[kPSort];
@@ -138,17 +138,21 @@ __global__ void __launch_bounds__(kPThreads, kPBlocksPerSM) probe_kernel(DevProb
     unsigned long long* epp = A.ep + blockIdx.x;
     auto Sb = [&](int b, int p) { return S + (size_t)(2 * b + p) * n; };
     auto chgb = [&](int b, int p) { return chg + (size_t)(2 * b + p) * n; };
+    // the block's epoch counter: in shared memory during the launch (thread 0 only), stored
+    // back at the end so that the next launch continues from it
+    if (tid == 0) sh.ep = *epp;
 
     for (;;) {
         if (tid == 0) {
             sh.pair = atomicAdd(A.pair_ctr, 1);
-            const unsigned long long e = *epp + 1;
-            *epp = e;
-            sh.ep_pair = e;
+            sh.ep_pair = ++sh.ep;
         }
         __syncthreads();
         const int pair = sh.pair;
-        if (pair >= A.npairs) break;
+        if (pair >= A.npairs) {
+            if (tid == 0) *epp = sh.ep;
+            break;
+        }
         const unsigned long long ep_pair = sh.ep_pair;
         for (int i = tid; i < kTSet; i += kPThreads) sh.tset[i] = 0;
         if (tid == 0) sh.tset_full = 0;
@@ -227,7 +231,7 @@ __global__ void __launch_bounds__(kPThreads, kPBlocksPerSM) probe_kernel(DevProb
             }
             if (tid == 0) {
                 sh.nw[np] = 0;
-                sh.ep_t = ++*epp;
+                sh.ep_t = ++sh.ep;
             }
             __syncthreads();
             const unsigned live = (unsigned)(sh.alive[0] | (sh.alive[1] << 1));
