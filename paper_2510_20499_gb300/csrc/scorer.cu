@@ -187,15 +187,31 @@ __global__ void __launch_bounds__(kMlpThreads, kTrain ? 2 : 6) k_mlp(MlpArgs a) 
         inv_c1 = a.counts[1] > 0 ? 1.0f / (float)a.counts[1] : 0.0f;
     }
     const int ntiles = (a.rows + kTile - 1) / kTile;
+    // this thread's feature row of a tile (zero past the last row)
+    auto load_row = [&](int tl, uint4& v0, uint4& v1) {
+        const int r = tl * kTile + t;
+        v0 = make_uint4(0, 0, 0, 0);
+        v1 = make_uint4(0, 0, 0, 0);
+        if (tl < ntiles && r < a.rows) {
+            const uint4* src = reinterpret_cast<const uint4*>(a.feat + (size_t)r * kIn);
+            v0 = src[0];
+            v1 = src[1];
+        }
+    };
+    // forward: the next tile's features are loaded while this tile's MMA chain runs
+    uint4 nx0, nx1;
+    if (!kTrain) load_row(blockIdx.x, nx0, nx1);
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int row = tile * kTile + t;
         const bool in = row < a.rows;
         // ---- features: X tile (A of layer 1) and, in training, rows 64..79 of [H1 | X | 1]^T
-        uint4 x0 = make_uint4(0, 0, 0, 0), x1 = make_uint4(0, 0, 0, 0);
-        if (in) {
-            const uint4* src = reinterpret_cast<const uint4*>(a.feat + (size_t)row * kIn);
-            x0 = src[0];
-            x1 = src[1];
+        uint4 x0, x1;
+        if (kTrain) {
+            load_row(tile, x0, x1);
+        } else {
+            x0 = nx0;
+            x1 = nx1;
+            load_row(tile + gridDim.x, nx0, nx1);
         }
         *reinterpret_cast<uint4*>(Xs + tc::tile_off(t, 0, kIn)) = x0;
         *reinterpret_cast<uint4*>(Xs + tc::tile_off(t, 8, kIn)) = x1;
