@@ -491,8 +491,11 @@ int scorer_train_step(scorer *s, const uint16_t *feat, const float *labels, int3
 int scorer_labels(const double *x, const double *x_out, const int32_t *vars, int32_t nvars, float weight,
                   int32_t first, float *labels, void *stream);
 
-/* Parameters to / from a file (magic "GPUBPML1", the three sizes and the count, then the
- * floats, little-endian). */
+/* Parameters and Adam state to / from a file, so that training resumes where it stopped
+ * (magic "GPUBPML2", the three sizes and the parameter count as int32, the Adam step count as
+ * int64, then the parameters and Adam's first and second moments as floats, little-endian).
+ * scorer_load also reads the parameters-only layout "GPUBPML1" and then starts a fresh Adam
+ * state.  The calls synchronise the device. */
 int scorer_save(const scorer *s, const char *path);
 int scorer_load(scorer *s, const char *path);
 

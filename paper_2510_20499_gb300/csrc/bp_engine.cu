@@ -24,6 +24,7 @@
 //   block tasks   [chunk candidates] -- they wait for their row's total, which the first
 //                 block segment produces without waiting, so every wait ends.
 #include <climits>
+#include <cstdlib>
 
 #include "bp_host.h"
 
@@ -70,6 +71,7 @@ struct BpArgs {
     // instances: a batch of independent problems laid out block-diagonally (rows
     // [row_off[i], row_off[i+1]) and variables [col_off[i], col_off[i+1]) form instance i).
     // One instance (ninst = 1, null offsets) is a plain propagation.
+    int skip_block;     // test only (GPUBP_TEST_SKIP_BLOCK): this block leaves without arriving, -1 none
     int ninst;
     const int* row_off;
     const int* col_off;
@@ -1058,12 +1060,18 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
             st.nnz = 0;
         }
         flush_inst_nnz(st, A, ph.s3());
+        if (A.skip_block == (int)blockIdx.x) {
+            // test-only failure: this block stops arriving at the grid barrier, so the others'
+            // bounded waits run out and the launch reports BP_ERR_TIMEOUT
+            st.flag = 2;
+            break;
+        }
         grid_sync(st, ctl);
         end_round(st, ctl, P, A, t);
     }
 
     // ---- epilogue
-    if (!ld_acquire_s32(&ctl->error)) {
+    if (st.flag != 2 && !ld_acquire_s32(&ctl->error)) {
         const int epi_n = st.epi_n;
         if (epi_n > 0) {
             // crossing check of the last round of the instances whose check is pending
@@ -1199,6 +1207,12 @@ int launch_propagate(mip_problem* p, double* lb, double* ub, const int* w0, int 
     a.max_rounds = max_rounds;
     a.stamp = w.stamp;
     a.trace = (long long*)trace;
+    // test-only failure injection: GPUBP_TEST_SKIP_BLOCK=b makes block b leave the rounds
+    // without arriving at the grid barrier (the failure-detection tests; never set otherwise)
+    {
+        const char* e = getenv("GPUBP_TEST_SKIP_BLOCK");
+        a.skip_block = (e && *e) ? atoi(e) : -1;
+    }
     a.ninst = ninst;
     a.row_off = row_off;
     a.col_off = col_off;

@@ -921,22 +921,29 @@ extern "C" int scorer_labels(const double* x, const double* x_out, const int32_t
     return BP_OK;
 }
 
+// File layout: magic "GPUBPML2", int32 {in, hidden, out, nparam}, int64 Adam steps, then the
+// parameters, Adam's first and second moments (nparam floats each), little-endian.  Files of
+// the first layout ("GPUBPML1": sizes and parameters only) still load, with a fresh Adam state.
 extern "C" int scorer_save(const scorer* s, const char* path) {
     if (!s || !path) {
         set_error("scorer_save: null argument");
         return BP_ERR_INVALID;
     }
-    std::vector<float> h(kNParam);
-    BP_TRY(scorer_get_params(s, h.data()));
+    std::vector<float> h(3 * (size_t)kNParam);
+    BP_CUDA_TRY(cudaDeviceSynchronize());
+    BP_CUDA_TRY(cudaMemcpy(h.data(), s->params, sizeof(float) * kNParam, cudaMemcpyDeviceToHost));
+    BP_CUDA_TRY(cudaMemcpy(h.data() + kNParam, s->m, sizeof(float) * kNParam, cudaMemcpyDeviceToHost));
+    BP_CUDA_TRY(cudaMemcpy(h.data() + 2 * kNParam, s->v, sizeof(float) * kNParam, cudaMemcpyDeviceToHost));
     FILE* f = fopen(path, "wb");
     if (!f) {
         set_error("scorer_save: cannot open %s", path);
         return BP_ERR_INVALID;
     }
-    const char magic[8] = {'G', 'P', 'U', 'B', 'P', 'M', 'L', '1'};
+    const char magic[8] = {'G', 'P', 'U', 'B', 'P', 'M', 'L', '2'};
     const int32_t dims[4] = {kIn, kHid, kOut, kNParam};
-    bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(dims, 4, 4, f) == 4 &&
-              fwrite(h.data(), sizeof(float), kNParam, f) == (size_t)kNParam;
+    const int64_t steps = s->steps;
+    bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(dims, 4, 4, f) == 4 && fwrite(&steps, 8, 1, f) == 1 &&
+              fwrite(h.data(), sizeof(float), h.size(), f) == h.size();
     ok = (fclose(f) == 0) && ok;
     if (!ok) {
         set_error("scorer_save: write to %s failed", path);
@@ -957,15 +964,24 @@ extern "C" int scorer_load(scorer* s, const char* path) {
     }
     char magic[8];
     int32_t dims[4];
-    std::vector<float> h(kNParam);
-    bool ok = fread(magic, 1, 8, f) == 8 && fread(dims, 4, 4, f) == 4 &&
-              fread(h.data(), sizeof(float), kNParam, f) == (size_t)kNParam;
+    bool ok = fread(magic, 1, 8, f) == 8 && fread(dims, 4, 4, f) == 4;
+    const bool v1 = ok && memcmp(magic, "GPUBPML1", 8) == 0;
+    const bool v2 = ok && memcmp(magic, "GPUBPML2", 8) == 0;
+    ok = ok && (v1 || v2) && dims[0] == kIn && dims[1] == kHid && dims[2] == kOut && dims[3] == kNParam;
+    int64_t steps = 0;
+    std::vector<float> h((v2 ? 3 : 1) * (size_t)kNParam);
+    if (ok && v2) ok = fread(&steps, 8, 1, f) == 1 && steps >= 0;
+    if (ok) ok = fread(h.data(), sizeof(float), h.size(), f) == h.size();
     fclose(f);
-    const char want[8] = {'G', 'P', 'U', 'B', 'P', 'M', 'L', '1'};
-    if (!ok || memcmp(magic, want, 8) != 0 || dims[0] != kIn || dims[1] != kHid || dims[2] != kOut ||
-        dims[3] != kNParam) {
+    if (!ok) {
         set_error("scorer_load: %s is not a 16-64-2 scorer file", path);
         return BP_ERR_INVALID;
     }
-    return scorer_set_params(s, h.data());
+    BP_TRY(scorer_set_params(s, h.data()));   // parameters, fresh Adam state
+    if (v2) {
+        BP_CUDA_TRY(cudaMemcpy(s->m, h.data() + kNParam, sizeof(float) * kNParam, cudaMemcpyHostToDevice));
+        BP_CUDA_TRY(cudaMemcpy(s->v, h.data() + 2 * kNParam, sizeof(float) * kNParam, cudaMemcpyHostToDevice));
+        s->steps = steps;
+    }
+    return BP_OK;
 }

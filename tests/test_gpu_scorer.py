@@ -245,3 +245,26 @@ def test_labels_match_oracle(pkg, runs):
     got = lab.cpu().numpy().astype(np.float64)
     np.testing.assert_array_equal(np.isnan(got), np.isnan(want))
     np.testing.assert_array_equal(got[~np.isnan(got)], want[~np.isnan(want)])
+
+
+def test_checkpoint_resumes_training(pkg):
+    """Three Adam steps, save, load into a fresh scorer, three more steps: the same parameters as
+    six steps without the interruption (the training step is deterministic)."""
+    import torch
+    rng = np.random.default_rng(71)
+    X = bf16_tensor(rng.standard_normal((1000, 16)))
+    Y = torch.tensor(labels_for(mlp.bf16(rng.standard_normal((1000, 16))), rng), device="cuda")
+    a = pkg.Scorer(seed=4)
+    for _ in range(6):
+        a.train_step(X, Y, 1e-2)
+    b = pkg.Scorer(seed=4)
+    for _ in range(3):
+        b.train_step(X, Y, 1e-2)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "ckpt.bin")
+        b.save(path)
+        c = pkg.Scorer(seed=99)
+        c.load(path)
+    for _ in range(3):
+        c.train_step(X, Y, 1e-2)
+    np.testing.assert_array_equal(c.get_params(), a.get_params())
