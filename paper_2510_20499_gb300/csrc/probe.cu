@@ -21,20 +21,23 @@ namespace gpubp {
 #define GPUBP_PROBE_THREADS 128
 #endif
 #ifndef GPUBP_PROBE_BLOCKS_PER_SM
-#define GPUBP_PROBE_BLOCKS_PER_SM 4
+#define GPUBP_PROBE_BLOCKS_PER_SM 5
+#endif
+#ifndef GPUBP_PROBE_GLANES
+#define GPUBP_PROBE_GLANES 0                   // lanes per worklist row; 0 = chosen from the row lengths
 #endif
 constexpr int kPThreads = GPUBP_PROBE_THREADS;     // a pair's few rows per round need few warps
 constexpr int kPBlocksPerSM = GPUBP_PROBE_BLOCKS_PER_SM;
 constexpr size_t kPScratchBudget = (size_t)16 << 30;   // bytes of per-block scratch at most
 constexpr int kPWarps = kPThreads / 32;
 constexpr int kPLane = 4;                  // nonzeros per lane held in registers per segment
-constexpr int kPSeg = 32 * kPLane;         // row segment processed in one wave by a warp
 constexpr int kPSort = 4096;               // touched lists up to this size are sorted in shared memory
 constexpr int kTSet = 1024;                // set of the variables a pair touched (shared memory)
 constexpr int kTProbe = 32;                // linear probes before the set counts as full
 
 struct ProbeArgs {
     const longlong2* root;       // n root keys
+    const float* rowcap;         // m: per-row cap of the candidate filter at the root (k_probe_rowcap)
     const int* var;
     const double* boxes;         // 4 per pair
     int npairs;
@@ -47,6 +50,7 @@ struct ProbeArgs {
     int* touched;                // [2 branch][n]
     unsigned long long* ep;      // [1] epoch counter of the block
     int* pair_ctr;
+    int glanes;                  // lanes per worklist row: 8, 16 or 32 (a warp takes 32 / glanes rows)
     double theta;
     int max_rounds;
     // outputs
@@ -88,7 +92,14 @@ struct ProbeShared {
     unsigned long long ep_pair, ep_t, ep;
     int tset[kTSet];             // open addressing, variable + 1 (0 = empty); cleared per pair
     int tset_full;
-    int sortbuf[kPSort];
+    union {
+        int sortbuf[kPSort];     // output phase: the touched variables being sorted
+        struct {                 // rows phase: each warp's queue of candidates that passed the filter
+            double a[kPWarps][32], mf[kPWarps][32], g[kPWarps][32];
+            long long lk[kPWarps][32], uk[kPWarps][32];
+            int j[kPWarps][32], bn[kPWarps][32];   // variable; branch | (infinite terms << 1)
+        } q;
+    };
     int scan[kPThreads];
     int out_base;
 };
@@ -123,6 +134,37 @@ __device__ __forceinline__ bool tset_has(const ProbeShared& sh, int j) {
         if (cur == 0) return false;
     }
     return true;
+}
+
+__device__ __forceinline__ bool positive(double a) { return __double_as_longlong(a) >= 0; }   // a != 0
+
+// Per-row cap of the candidate filter for a probe batch.  A branch's bounds lie inside the root
+// bounds, so for every nonzero the filter's product |a| (u - l) is at most its value at the root
+// and its margin term 2e-15 |a| (|l'| + |u'|) at most 4e-15 |a| (|l| + |u|) (|l'| + |u'| <=
+// 2 max(|l|, |u|) for l <= l' <= u' <= u).  The cap is the maximum over the row of the product
+// plus twice that bound (FP32, rounded up; +inf when a bound is infinite); the factor two, and
+// 2e-15 in place of 1e-15 on |g| + |L_min| below, absorb the different order of the upward
+// roundings.  A row whose slack bracket reaches cap + 2e-15 (|g| + |L_min|) lets no candidate
+// through the per-nonzero filter in any branch, so the filter loop is skipped.
+__global__ void k_probe_rowcap(DevProblem P, const longlong2* root, float* cap) {
+    const int lane = threadIdx.x & 31;
+    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < P.m; k += (gridDim.x * blockDim.x) >> 5) {
+        float c = 0.0f;
+        for (int q = P.row_ptr[k] + lane; q < P.row_ptr[k + 1]; q += 32) {
+            const longlong2 b = root[P.col[q]];
+            if (key_is_inf(b.x) || key_is_inf(b.y)) {
+                c = __int_as_float(0x7f800000);
+                continue;
+            }
+            const double l = kdec(b.x), u = kdec(b.y);
+            const float a_up = fabs_up(P.val[q]);
+            const float prod = __fmul_ru(a_up, __fsub_ru(f_up(u), f_dn(l)));
+            const float mt = __fmul_ru(1e-15f, __fmul_ru(8.0f, __fmul_ru(a_up, __fadd_ru(fabs_up(l), fabs_up(u)))));
+            c = fmaxf(c, __fadd_ru(prod, mt));
+        }
+        for (int off = 16; off > 0; off >>= 1) c = fmaxf(c, __shfl_xor_sync(0xffffffffu, c, off));
+        if (lane == 0) cap[k] = c;
+    }
 }
 
 __global__ void __launch_bounds__(kPThreads, kPBlocksPerSM) probe_kernel(DevProblem P, ProbeArgs A) {
@@ -253,35 +295,55 @@ __global__ void __launch_bounds__(kPThreads, kPBlocksPerSM) probe_kernel(DevProb
                     }
                 }
             }
-            // ---- rows of this round: one warp per row, both branches per load
+            // ---- rows of this round: a group of G lanes per row (32 / G rows per warp at a
+            // time, so that the short rows of a probe overlap their load latencies), both branches
+            // per load
             const int nw = sh.nw[par];
             const int* W = wl + (size_t)par * m;
-            for (int e = w; e < nw; e += kPWarps) {
-                const int k = W[e];
-                const unsigned mask = (unsigned)(rw[k] & 3ull) & live;
-                if (!mask) continue;
-                const int beg = P.row_ptr[k], end = P.row_ptr[k + 1];
-                const double2 g2 = P.grow[k];
+            const int G = A.glanes, gpw = 32 / G, gl = lane & (G - 1);
+            const int seg = G * kPLane;
+            for (int e0 = w * gpw; e0 < nw; e0 += kPWarps * gpw) {
+                const int e = e0 + lane / G;
+                const int k = e < nw ? W[e] : -1;
+                const unsigned mask = k >= 0 ? (unsigned)(rw[k] & 3ull) & live : 0u;
+                if (!__any_sync(0xffffffffu, mask != 0)) continue;
+                int beg = 0, end = 0;
+                double2 g2 = make_double2(0.0, 0.0);
+                float rcap = 0.0f;
+                if (mask) {
+                    beg = P.row_ptr[k];
+                    end = P.row_ptr[k + 1];
+                    g2 = P.grow[k];
+                    rcap = A.rowcap[k];
+                }
                 double mf[2] = {0.0, 0.0};
                 int ni[2] = {0, 0}, ij[2] = {-1, -1};
                 int jj[kPLane];
                 double aa[kPLane];
-                longlong2 bb[2][kPLane];
-                const bool one_seg = end - beg <= kPSeg;
-                for (int s0 = beg; s0 < end; s0 += kPSeg) {
+                long long kk[2][kPLane];   // per branch: the bound key of the minimum contribution
+                for (int s0 = beg; s0 < end; s0 += seg) {
 #pragma unroll
                     for (int i = 0; i < kPLane; ++i) {
-                        const int q = s0 + lane + 32 * i;
+                        const int q = s0 + gl + G * i;
                         jj[i] = q < end ? P.col[q] : -1;
                         aa[i] = q < end ? P.val[q] : 0.0;
                     }
 #pragma unroll
                     for (int i = 0; i < kPLane; ++i) {
                         if (jj[i] < 0) continue;
-                        const longlong2 r = __ldcg(A.root + jj[i]);
+                        // only the bound of the minimum contribution: l for a > 0, u for a < 0
+                        const bool tj = tset_has(sh, jj[i]), pos = positive(aa[i]);
+                        const int h = 2 * jj[i] + (pos ? 0 : 1);
+                        const long long r = __ldcg(reinterpret_cast<const long long*>(A.root) + h);
 #pragma unroll
-                        for (int b = 0; b < 2; ++b)
-                            bb[b][i] = (mask >> b & 1) && tset_has(sh, jj[i]) ? meet(r, __ldcg(Sb(b, par) + jj[i])) : r;
+                        for (int b = 0; b < 2; ++b) {
+                            long long x = r;
+                            if ((mask >> b & 1) && tj) {
+                                const long long y = __ldcg(reinterpret_cast<const long long*>(Sb(b, par)) + h);
+                                x = pos ? (y > r ? y : r) : (y < r ? y : r);
+                            }
+                            kk[b][i] = x;
+                        }
                     }
 #pragma unroll
                     for (int i = 0; i < kPLane; ++i) {
@@ -289,7 +351,7 @@ __global__ void __launch_bounds__(kPThreads, kPBlocksPerSM) probe_kernel(DevProb
 #pragma unroll
                         for (int b = 0; b < 2; ++b) {
                             if (!(mask >> b & 1)) continue;
-                            const long long key = aa[i] > 0 ? bb[b][i].x : bb[b][i].y;
+                            const long long key = kk[b][i];
                             if (key_is_inf(key)) {
                                 ++ni[b];
                                 ij[b] = jj[i];
@@ -299,48 +361,30 @@ __global__ void __launch_bounds__(kPThreads, kPBlocksPerSM) probe_kernel(DevProb
                         }
                     }
                 }
+                // group reductions (xor offsets below G stay inside the group)
 #pragma unroll
                 for (int b = 0; b < 2; ++b) {
-                    for (int off = 16; off > 0; off >>= 1) {
+                    for (int off = G >> 1; off > 0; off >>= 1) {
                         mf[b] = __dadd_rn(mf[b], __shfl_xor_sync(0xffffffffu, mf[b], off));
                         ni[b] += __shfl_xor_sync(0xffffffffu, ni[b], off);
                         ij[b] = max(ij[b], __shfl_xor_sync(0xffffffffu, ij[b], off));
                     }
                 }
-#pragma unroll
-                for (int b = 0; b < 2; ++b) {
-                    if (!(mask >> b & 1)) continue;
-                    if (lane == 0) atomicAdd(&sh.nnz[b], (unsigned long long)(end - beg));
-                    if (row_infeasible(mf[b], ni[b], g2.y)) {
-                        if (lane == 0) sh.rowinf[b] = 1;
-                        continue;
-                    }
-                    if (ni[b] >= 2) continue;
-                    const RowFilter f = row_filter(g2.x, mf[b]);
-                    longlong2* X = Sb(b, np);
-                    for (int s0 = beg; s0 < end; s0 += kPSeg) {
-#pragma unroll
-                        for (int i = 0; i < kPLane; ++i) {
-                            int j;
-                            double a;
-                            longlong2 bk;
-                            if (one_seg) {
-                                j = jj[i];
-                                a = aa[i];
-                                bk = bb[b][i];
-                            } else {
-                                const int q = s0 + lane + 32 * i;
-                                j = q < end ? P.col[q] : -1;
-                                a = q < end ? P.val[q] : 0.0;
-                                bk = j < 0 ? make_longlong2(0, 0)
-                                           : tset_has(sh, j) ? meet(__ldcg(A.root + j), __ldcg(Sb(b, par) + j))
-                                                             : __ldcg(A.root + j);
-                            }
-                            if (j < 0) continue;
-                            if (ni[b] == 1 ? j != ij[b] : cannot_tighten(f, a, bk.x, bk.y)) continue;
-                            long long nk;
-                            const int r = eval_candidate(a, bk.x, bk.y, mf[b], ni[b], g2.x, P.is_int[j] != 0, A.theta, &nk);
-                            if (!r) continue;
+                // Candidates: the FP32 filter runs per nonzero; the few that pass go to the warp's
+                // queue, and the exact FP64 evaluation (a division, slow on this part) runs once per
+                // 32 queued candidates with every lane busy, instead of once per register slot that
+                // has a candidate in some lane.
+                int qn = 0;   // warp-uniform queue length
+                auto flush = [&]() {
+                    __syncwarp();
+                    if (lane < qn) {
+                        const int j = sh.q.j[w][lane], bn = sh.q.bn[w][lane], b = bn & 1;
+                        const long long lk = sh.q.lk[w][lane], uk = sh.q.uk[w][lane];
+                        long long nk;
+                        const int r = eval_candidate(sh.q.a[w][lane], lk, uk, sh.q.mf[w][lane], bn >> 1, sh.q.g[w][lane],
+                                                     P.is_int[j] != 0, A.theta, &nk);
+                        if (r) {
+                            longlong2* X = Sb(b, np);
                             if (r == 1) atomicMin(&X[j].y, nk);
                             else atomicMax(&X[j].x, nk);
                             const unsigned long long old = atomicMax(&vst[(size_t)b * n + j], ep_t);
@@ -351,7 +395,65 @@ __global__ void __launch_bounds__(kPThreads, kPBlocksPerSM) probe_kernel(DevProb
                             }
                         }
                     }
+                    __syncwarp();
+                    qn = 0;
+                };
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    bool rowok = false;
+                    RowFilter f{};
+                    if (mask >> b & 1) {
+                        if (gl == 0) atomicAdd(&sh.nnz[b], (unsigned long long)(end - beg));
+                        if (row_infeasible(mf[b], ni[b], g2.y)) {
+                            if (gl == 0) sh.rowinf[b] = 1;
+                        } else if (ni[b] < 2) {
+                            f = row_filter(g2.x, mf[b]);
+                            // the row-level cap (NaN-safe: an infinite cap keeps the filter loop)
+                            rowok = !(ni[b] == 0 && f.slack_dn >= __fadd_ru(rcap, __fmul_ru(2e-15f, f.mag_up)));
+                        }
+                    }
+                    if (!__any_sync(0xffffffffu, rowok)) continue;
+                    const int nseg = rowok ? (end - beg + seg - 1) / seg : 0;
+                    const int nseg_w = __reduce_max_sync(0xffffffffu, nseg);
+                    for (int si = 0; si < nseg_w; ++si) {
+                        const int s0 = beg + si * seg;
+#pragma unroll
+                        for (int i = 0; i < kPLane; ++i) {
+                            bool want = false;
+                            int j = -1;
+                            double a = 0.0;
+                            longlong2 bk = make_longlong2(0, 0);
+                            // the row's nonzeros are read again (L2) rather than held in registers
+                            // since the activity pass: few rows get here, and the freed registers
+                            // let more blocks share an SM
+                            const int q = s0 + gl + G * i;
+                            if (si < nseg && q < end) {
+                                j = P.col[q];
+                                a = P.val[q];
+                                bk = tset_has(sh, j) ? meet(__ldcg(A.root + j), __ldcg(Sb(b, par) + j)) : __ldcg(A.root + j);
+                                want = ni[b] == 1 ? j == ij[b] : !cannot_tighten(f, a, bk.x, bk.y);
+                            }
+                            const unsigned bal = __ballot_sync(0xffffffffu, want);
+                            if (bal) {
+                                if (qn + __popc(bal) > 32) flush();
+                                if (want) {
+                                    unsigned lt;
+                                    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+                                    const int pos = qn + __popc(bal & lt);
+                                    sh.q.a[w][pos] = a;
+                                    sh.q.mf[w][pos] = mf[b];
+                                    sh.q.g[w][pos] = g2.x;
+                                    sh.q.lk[w][pos] = bk.x;
+                                    sh.q.uk[w][pos] = bk.y;
+                                    sh.q.j[w][pos] = j;
+                                    sh.q.bn[w][pos] = b | (ni[b] << 1);
+                                }
+                                qn += __popc(bal);
+                            }
+                        }
+                    }
                 }
+                if (qn) flush();
             }
             __syncthreads();
             // ---- verdicts of the round: infeasible rows, crossing bounds
@@ -628,6 +730,7 @@ int root_keys(mip_problem* p, const double* lb, const double* ub, longlong2* out
 
 struct ProbeWork {
     int blocks = 0;
+    int glanes = 32;
     longlong2* S = nullptr;
     unsigned long long* vst = nullptr;
     unsigned long long* rw = nullptr;
@@ -644,7 +747,18 @@ struct ProbeWork {
     double* tl = nullptr;
     double* tu = nullptr;
     long long tcap = 0;
+    float* rowcap = nullptr;     // m
 };
+
+// Lanes per worklist row in the probe kernel: with kPLane nonzeros per lane, a group of G lanes
+// covers 4 G nonzeros per segment; rows of a probe are few per round, so the narrowest group whose
+// segment holds the average row (with room for its spread) keeps the most rows in flight.
+static int probe_group_lanes(int m, long long nnz) {
+    const double avg = m ? (double)nnz / m : 0.0;
+    if (avg <= 0.5 * 8 * kPLane) return 8;
+    if (avg <= 0.75 * 16 * kPLane) return 16;
+    return 32;
+}
 
 static ProbeWork* probe_work(mip_problem* p) { return static_cast<ProbeWork*>(p->probe_work); }
 
@@ -677,8 +791,10 @@ static int probe_prepare(mip_problem* p, int nbranches, long long cap, cudaStrea
         BP_TRY(dalloc(p, &pw->ep, B));
         BP_TRY(dalloc(p, &pw->ctr, 1));
         BP_TRY(dalloc(p, &pw->ectr, 2));
+        BP_TRY(dalloc(p, &pw->rowcap, m));
         if (B * 4 * n) k_fill_neutral<<<1024, 256, 0, s>>>(B * 4 * n, pw->S);
         BP_CUDA_TRY(cudaGetLastError());
+        pw->glanes = GPUBP_PROBE_GLANES ? GPUBP_PROBE_GLANES : probe_group_lanes(p->m, p->nnz);
     }
     ProbeWork* pw = probe_work(p);
     if (nbranches > pw->cap_branches) {
@@ -730,10 +846,16 @@ extern "C" int bp_probe_batch(mip_problem* p, const double* root_lb, const doubl
     ProbeWork* pw = probe_work(p);
     longlong2* root = p->w.bkey[0];
     BP_TRY(root_keys(p, root_lb, root_ub, root, s));
+    if (p->m) {
+        const int g = (p->m + 7) / 8 < 1216 ? (p->m + 7) / 8 : 1216;
+        k_probe_rowcap<<<g, 256, 0, s>>>(p->dp, root, pw->rowcap);
+        BP_CUDA_TRY(cudaGetLastError());
+    }
     BP_CUDA_TRY(cudaMemsetAsync(pw->ctr, 0, sizeof(int), s));
     BP_CUDA_TRY(cudaMemsetAsync(pw->ectr, 0, 2 * sizeof(unsigned long long), s));   // entry total, index error
     ProbeArgs a;
     a.root = root;
+    a.rowcap = pw->rowcap;
     a.var = var;
     a.boxes = boxes;
     a.npairs = npairs;
@@ -745,6 +867,7 @@ extern "C" int bp_probe_batch(mip_problem* p, const double* root_lb, const doubl
     a.touched = pw->touched;
     a.ep = pw->ep;
     a.pair_ctr = pw->ctr;
+    a.glanes = pw->glanes;
     a.theta = prm.theta;
     a.max_rounds = prm.max_rounds;
     a.status = cache->status;

@@ -89,6 +89,36 @@ def test_mixed_probes(pkg, seed):
     _compare(p, g, o)
 
 
+@pytest.mark.parametrize("seed", range(3))
+def test_powerlaw_probes(pkg, seed):
+    """Short rows on average (12.5 nonzeros: 8 lanes per row in the probe kernel) with a power-law
+    tail up to 500 nonzeros, so that long rows take many segments of a narrow lane group."""
+    p = synth.mixed_powerlaw(seed=700 + seed, m=2000, n=5000, nnz=25_000, max_row=500, inf_fraction=0.1)
+    P = oracle.Problem(p)
+    rl, ru, r, _ = P.bp(p.lb, p.ub)
+    if r["status"] == oracle.INFEASIBLE:
+        pytest.skip("root infeasible")
+    var, boxes = _pairs(p, rl, ru, 300, seed)
+    o = P.probe_batch(rl, ru, var, boxes)
+    g = _gpu_probe(pkg, p, rl, ru, var, boxes)
+    _compare(p, g, o)
+
+
+@pytest.mark.parametrize("lens", [(3, 9), (20, 60)])
+def test_probe_lane_groups(pkg, lens):
+    """Average row lengths that select 8 and 16 lanes per row (6 and 40 nonzeros)."""
+    lo, hi = lens
+    m, n = 2000, 4000
+    p = synth.knapsack_cover(seed=60 + lo, m=m, n=n, nnz=m * (lo + hi) // 2, len_lo=lo, len_hi=hi)
+    P = oracle.Problem(p)
+    rl, ru, r, _ = P.bp(p.lb, p.ub)
+    assert r["status"] == oracle.FIXPOINT
+    var, boxes = _pairs(p, rl, ru, 300, lo)
+    o = P.probe_batch(rl, ru, var, boxes)
+    g = _gpu_probe(pkg, p, rl, ru, var, boxes)
+    _compare(p, g, o)
+
+
 def test_probe_round_limit_and_capacity(pkg):
     p = synth.knapsack_cover(seed=9, m=1000, n=2000, nnz=20_000)
     P = oracle.Problem(p)
