@@ -254,8 +254,9 @@ typedef struct {
  * Returns BP_OK, BP_ERR_CAPACITY (cache->needed holds the required entry count; the status,
  * rounds, nnz_updates and offsets arrays are complete), BP_ERR_INVALID (also for a variable
  * index outside [0, n): the kernel skips such a pair and flags it; the other arrays are then
- * incomplete).  The call synchronises the stream once (it reads the entry count and the
- * index flag together).
+ * incomplete).  The call synchronises the stream once, at its end: the copy into the cache is
+ * launched before the host knows the entry count and checks the capacity on the device, and
+ * the count and the index flag are read back together.
  */
 int bp_probe_batch(mip_problem *p, const double *root_lb, const double *root_ub, int32_t P,
                    const int32_t *var, const double *boxes, const bp_params *params,

@@ -146,8 +146,14 @@ __device__ __forceinline__ bool positive(double a) { return __double_as_longlong
 // 2e-15 in place of 1e-15 on |g| + |L_min| below, absorb the different order of the upward
 // roundings.  A row whose slack bracket reaches cap + 2e-15 (|g| + |L_min|) lets no candidate
 // through the per-nonzero filter in any branch, so the filter loop is skipped.
-__global__ void k_probe_rowcap(DevProblem P, const longlong2* root, float* cap) {
+__global__ void k_probe_rowcap(DevProblem P, const longlong2* root, float* cap, int* pair_ctr,
+                               unsigned long long* ectr) {
     const int lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {   // the launch's counters: next pair, entry total, index flag
+        *pair_ctr = 0;
+        ectr[0] = 0;
+        ectr[1] = 0;
+    }
     for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < P.m; k += (gridDim.x * blockDim.x) >> 5) {
         float c = 0.0f;
         for (int q = P.row_ptr[k] + lane; q < P.row_ptr[k + 1]; q += 32) {
@@ -679,34 +685,56 @@ __global__ void k_fill_neutral(size_t count, longlong2* S) {
 // offsets (exclusive scan of the entry counts) and the copy of every branch's entries to its
 // place, in branch order; one block, the counts are few
 __global__ void k_probe_offsets(int nb, const long long* ecount, int64_t* offsets, unsigned long long* total) {
-    __shared__ long long carry;
-    __shared__ long long sc[1024];
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int base = 0; base < nb; base += 1024) {
-        const int i = base + threadIdx.x;
-        const long long v = i < nb ? ecount[i] : 0;
-        sc[threadIdx.x] = v;
-        __syncthreads();
-        for (int o = 1; o < 1024; o <<= 1) {
-            const long long y = threadIdx.x >= o ? sc[threadIdx.x - o] : 0;
-            __syncthreads();
-            sc[threadIdx.x] += y;
-            __syncthreads();
+    // one block of 1024 threads, 4 consecutive counts per thread per tile of 4,096: a serial sum
+    // per thread, shuffle scans within and across the warps
+    __shared__ long long wsum[32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    long long carry = 0;
+    for (int base = 0; base < nb; base += 4096) {
+        const int i0 = base + 4 * t;
+        long long v[4], own = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = i0 + k < nb ? ecount[i0 + k] : 0;
+            own += v[k];
         }
-        if (i < nb) offsets[i] = (int64_t)(carry + sc[threadIdx.x] - v);
+        long long x = own;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
         __syncthreads();
-        if (threadIdx.x == 0) carry += sc[1023];
+        if (w == 0) {
+            long long z = wsum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long y = __shfl_up_sync(0xffffffffu, z, o);
+                if (lane >= o) z += y;
+            }
+            wsum[lane] = z;
+        }
+        __syncthreads();
+        long long ex = carry + (w ? wsum[w - 1] : 0) + x - own;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (i0 + k < nb) offsets[i0 + k] = (int64_t)ex;
+            ex += v[k];
+        }
+        carry += wsum[31];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
+    if (t == 0) {
         offsets[nb] = (int64_t)carry;
         *total = (unsigned long long)carry;
     }
 }
 
+// copy of every branch's entries to the cache, launched before the host knows the total: it
+// does nothing when the total passes the cache's capacity (the call then reports BP_ERR_CAPACITY)
 __global__ void k_probe_copy(int nb, const long long* ecount, const long long* estart, const int64_t* offsets,
+                             const unsigned long long* total, long long cap,
                              const int* tv, const double* tl, const double* tu, int* ov, double* ol, double* ou) {
+    if ((long long)*total > cap) return;
     const int lane = threadIdx.x & 31;
     for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += (gridDim.x * blockDim.x) >> 5) {
         const long long c = ecount[b], s = estart[b], o = offsets[b];
@@ -846,13 +874,11 @@ extern "C" int bp_probe_batch(mip_problem* p, const double* root_lb, const doubl
     ProbeWork* pw = probe_work(p);
     longlong2* root = p->w.bkey[0];
     BP_TRY(root_keys(p, root_lb, root_ub, root, s));
-    if (p->m) {
-        const int g = (p->m + 7) / 8 < 1216 ? (p->m + 7) / 8 : 1216;
-        k_probe_rowcap<<<g, 256, 0, s>>>(p->dp, root, pw->rowcap);
+    {
+        const int g = p->m / 8 + 1 < 1216 ? p->m / 8 + 1 : 1216;
+        k_probe_rowcap<<<g, 256, 0, s>>>(p->dp, root, pw->rowcap, pw->ctr, pw->ectr);
         BP_CUDA_TRY(cudaGetLastError());
     }
-    BP_CUDA_TRY(cudaMemsetAsync(pw->ctr, 0, sizeof(int), s));
-    BP_CUDA_TRY(cudaMemsetAsync(pw->ectr, 0, 2 * sizeof(unsigned long long), s));   // entry total, index error
     ProbeArgs a;
     a.root = root;
     a.rowcap = pw->rowcap;
@@ -885,9 +911,15 @@ extern "C" int bp_probe_batch(mip_problem* p, const double* root_lb, const doubl
     BP_CUDA_TRY(cudaGetLastError());
     const int nb = 2 * npairs;
     k_probe_offsets<<<1, 1024, 0, s>>>(nb, pw->ecount, cache->offsets, pw->ectr);
+    BP_CUDA_TRY(cudaGetLastError());
+    k_probe_copy<<<(nb * 32 + 255) / 256 < 1216 ? (nb * 32 + 255) / 256 : 1216, 256, 0, s>>>(
+        nb, pw->ecount, pw->estart, cache->offsets, pw->ectr, cache->cap, pw->tv, pw->tl, pw->tu, cache->ent_var,
+        cache->ent_l, cache->ent_u);
+    BP_CUDA_TRY(cudaGetLastError());
     unsigned long long words[2] = {0, 0};   // entry total and the index check, read together
     BP_CUDA_TRY(cudaMemcpyAsync(words, pw->ectr, sizeof(words), cudaMemcpyDeviceToHost, s));
     BP_CUDA_TRY(cudaStreamSynchronize(s));
+    p->last_stream = s;
     if (words[1]) {
         set_error("bp_probe_batch: a variable index is outside [0, n)");
         return BP_ERR_INVALID;
@@ -898,11 +930,5 @@ extern "C" int bp_probe_batch(mip_problem* p, const double* root_lb, const doubl
         set_error("probing cache needs %llu entries, capacity %lld", total, (long long)cache->cap);
         return BP_ERR_CAPACITY;
     }
-    if (total) {
-        k_probe_copy<<<(nb * 32 + 255) / 256 < 1216 ? (nb * 32 + 255) / 256 : 1216, 256, 0, s>>>(
-            nb, pw->ecount, pw->estart, cache->offsets, pw->tv, pw->tl, pw->tu, cache->ent_var, cache->ent_l, cache->ent_u);
-        BP_CUDA_TRY(cudaGetLastError());
-    }
-    p->last_stream = s;
     return BP_OK;
 }
