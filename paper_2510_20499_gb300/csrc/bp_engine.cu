@@ -885,6 +885,7 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
         I.alive = 1;
         I.pending = 0;
         I.entry_cross = INT_MAX;
+        I.start_rows = 0;
         I.nnz_total = 0;
         I.n_changed = 0;
         A.inst[i] = I;
@@ -934,6 +935,7 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
                 continue;
             }
             const int cb = __ldg(P.col_ptr + u), ce = __ldg(P.col_ptr + u + 1);
+            if (A.ninst > 1 && lane == 0 && ce > cb) atomicAdd(&A.inst[var_inst(st, A, u)].start_rows, 1);
             for (int s0 = cb; s0 < ce; s0 += 32) {
                 const int sidx = s0 + lane;
                 warp_queue_rows(st, A, P, q, sidx < ce ? __ldg(P.row_idx + sidx) : -1);
@@ -951,7 +953,11 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
         __syncthreads();
         for (int i = threadIdx.x; i < A.ninst; i += kThreads) {
             InstState* I = A.inst + i;
-            const int ri = (A.w0 || A.w0v) ? rows0 : st.roff[i + 1] - st.roff[i];
+            // rows in round 0: with a variable start list and several instances, each
+            // instance's own (a nonzero count is all that matters here)
+            const int ri = (A.w0v && A.ninst > 1) ? __ldcg(&I->start_rows)
+                           : (A.w0 || A.w0v)      ? rows0
+                                                  : st.roff[i + 1] - st.roff[i];
             const int ec = __ldcg(&I->entry_cross);
             int alive = 1;
             if (ec != INT_MAX) {
@@ -1173,8 +1179,9 @@ int launch_propagate(mip_problem* p, double* lb, double* ub, const int* w0, int 
                      int max_rounds, int64_t* trace, cudaStream_t s, const int* w0v, const int* w0v_len, int ninst,
                      const int* row_off, const int* col_off) {
     Work& w = p->w;
-    if (ninst < 1 || ninst > kMaxInstances || (ninst > 1 && (!row_off || !col_off || w0 || w0v))) {
-        set_error("invalid instance batch (1 <= instances <= %d, offsets required)", kMaxInstances);
+    if (ninst < 1 || ninst > kMaxInstances || (ninst > 1 && (!row_off || !col_off || w0))) {
+        set_error("invalid instance batch (1 <= instances <= %d, offsets required, no row start list)",
+                  kMaxInstances);
         return BP_ERR_INVALID;
     }
     BP_TRY(ensure_instances(p, ninst));

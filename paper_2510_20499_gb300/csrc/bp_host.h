@@ -42,6 +42,7 @@ struct alignas(128) Ctl {
 struct InstState {
     int status, rounds, result_par, first_row, first_var;
     int alive, pending, entry_cross;
+    int start_rows;              // variables of the start list (w0v) with rows, in this instance
     unsigned long long nnz_total, n_changed;
 };
 
@@ -96,6 +97,8 @@ struct mip_problem {
     int* inst_row_off = nullptr;
     int* inst_col_off = nullptr;
     void* prio_work = nullptr;                 // priority / sort scratch (created on first use)
+    mip_problem* twin = nullptr;               // two copies of this problem as an instance pair
+                                               // (fix_and_propagate's candidates; first use)
     // row-class split points and grid shape (bp_set_tuning / bp_autotune)
     int tune_warp_min = gpubp::kDefaultWarpMin;
     int tune_block_min = gpubp::kWarpMax + 1;

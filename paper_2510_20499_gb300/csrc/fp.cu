@@ -227,11 +227,86 @@ __global__ void k_apply_cache(int bsize, const int* bulk, const double* v, doubl
     if (lane == 0) *kept = nk;
 }
 
-// variables whose start box differs from the current bounds (round 0 of the propagation)
-__global__ void k_diff(int n, const double* cl, const double* cu, const double* l, const double* u, int* list,
-                       int* count) {
+// variables whose start box differs from the current bounds (round 0 of the propagation),
+// appended as off + j (the candidate's copy in the instance pair)
+__global__ void k_diff(int n, const double* cl, const double* cu, const double* l, const double* u, int off,
+                       int* list, int* count) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
-        if (cl[j] != l[j] || cu[j] != u[j]) list[atomicAdd(count, 1)] = j;
+        if (cl[j] != l[j] || cu[j] != u[j]) list[atomicAdd(count, 1)] = off + j;
+}
+
+// The two copies of a problem, block-diagonal: rows k and m + k, variables j and n + j.
+__global__ void k_twin_arrays(DevProblem P, const double* lb, const double* ub, int64_t* rp, int* col, double* val,
+                              double* g, double* l2, double* u2, unsigned char* is_int) {
+    const long long m = P.m, n = P.n, nnz = P.nnz;
+    const long long top = 2 * nnz > 2 * m + 1 ? (2 * nnz > 2 * n ? 2 * nnz : 2 * n) : (2 * m + 1 > 2 * n ? 2 * m + 1 : 2 * n);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < top; i += (long long)gridDim.x * blockDim.x) {
+        if (i <= 2 * m) rp[i] = i < m ? P.row_ptr[i] : P.row_ptr[i - m] + nnz;
+        if (i < 2 * m) g[i] = P.grow[i < m ? i : i - m].x;
+        if (i < 2 * nnz) {
+            const long long q = i < nnz ? i : i - nnz;
+            col[i] = P.col[q] + (i < nnz ? 0 : (int)n);
+            val[i] = P.val[q];
+        }
+        if (i < 2 * n) {
+            const long long j = i < n ? i : i - n;
+            l2[i] = lb[j];
+            u2[i] = ub[j];
+            is_int[i] = P.is_int[j];
+        }
+    }
+}
+
+static void twin_free(mip_problem* p) {
+    if (p->twin) mip_free(p->twin);
+    p->twin = nullptr;
+}
+
+// The instance pair on which both candidate vectors of a bulk propagate in one launch (built
+// on first use, kept with the handle): the bulk's two propagations then share the launch, its
+// grid barriers and its rounds, and each copy's status, rounds and nonzeros stay its own.
+static int twin_problem(mip_problem* p, cudaStream_t s, mip_problem** out) {
+    if (!p->twin) {
+        const size_t m = (size_t)p->m, n = (size_t)p->n, nnz = (size_t)p->nnz;
+        void* buf[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+        const size_t bytes[7] = {8 * (2 * m + 1), 4 * 2 * nnz + 4, 8 * 2 * nnz + 8, 8 * 2 * m + 8, 8 * 2 * n + 8,
+                                 8 * 2 * n + 8, 2 * n + 1};
+        int rc = BP_OK;
+        for (int i = 0; i < 7 && rc == BP_OK; ++i)
+            if (cudaMalloc(&buf[i], bytes[i]) != cudaSuccess) {
+                set_error("fix_and_propagate: allocation of the instance pair failed");
+                rc = BP_ERR_OOM;
+            }
+        mip_problem* t = nullptr;
+        if (rc == BP_OK) {
+            const long long top = 2 * (long long)(nnz > m + 1 ? (nnz > n ? nnz : n) : (m + 1 > n ? m + 1 : n));
+            const int grid = (int)((top + 255) / 256 < 1216 ? (top + 255) / 256 : 1216);
+            k_twin_arrays<<<grid > 0 ? grid : 1, 256, 0, s>>>(p->dp, p->def_lb, p->def_ub, (int64_t*)buf[0], (int*)buf[1],
+                                                            (double*)buf[2], (double*)buf[3], (double*)buf[4],
+                                                            (double*)buf[5], (unsigned char*)buf[6]);
+            if (cudaGetLastError() != cudaSuccess) {
+                set_error("fix_and_propagate: instance pair kernel failed to launch");
+                rc = BP_ERR_CUDA;
+            }
+        }
+        if (rc == BP_OK)
+            rc = mip_load_csr(2 * p->m, 2 * p->n, (int64_t*)buf[0], (int*)buf[1], (double*)buf[2], (double*)buf[3],
+                              (double*)buf[4], (double*)buf[5], (uint8_t*)buf[6], nullptr, BP_MEM_DEVICE, s, &t);
+        cudaStreamSynchronize(s);
+        for (void* b : buf)
+            if (b) cudaFree(b);
+        if (rc != BP_OK) return rc;
+        const int32_t ro[3] = {0, p->m, 2 * p->m}, co[3] = {0, p->n, 2 * p->n};
+        rc = mip_set_instances(t, 2, ro, co, BP_MEM_HOST, s);
+        if (rc != BP_OK) {
+            mip_free(t);
+            return rc;
+        }
+        p->twin = t;
+        p->free_hooks[1] = twin_free;
+    }
+    *out = p->twin;
+    return BP_OK;
 }
 
 __global__ void k_pair_of(int npairs, const int* var, int* pair_of) {
@@ -332,7 +407,7 @@ extern "C" int fix_and_propagate(mip_problem* p, const double* x, const double* 
     };
     int rc = BP_OK;
     double *Bl, *Bu, *cl[2], *cu[2], *v[2], *rmin;
-    int *flag, *pos, *ivars, *order, *work, *twork, *rninf, *dlist[2], *dcnt, *pair_of = nullptr, *total;
+    int *flag, *pos, *ivars, *order, *work, *twork, *rninf, *dlist, *dcnt, *pair_of = nullptr, *total;
     unsigned long long *keys, *tkeys;
     FpCtl* dctl;
     FpCtl* hctl = nullptr;
@@ -343,12 +418,13 @@ extern "C" int fix_and_propagate(mip_problem* p, const double* x, const double* 
     } while (0)
     FP_ALLOC(Bl, n);
     FP_ALLOC(Bu, n);
-    for (int c = 0; c < 2; ++c) {
-        FP_ALLOC(cl[c], n);
-        FP_ALLOC(cu[c], n);
-        FP_ALLOC(v[c], n);
-        FP_ALLOC(dlist[c], n);
-    }
+    // the candidates' bounds: the two halves of one array each, as the instance pair reads them
+    FP_ALLOC(cl[0], 2 * (size_t)n);
+    FP_ALLOC(cu[0], 2 * (size_t)n);
+    cl[1] = cl[0] + n;
+    cu[1] = cu[0] + n;
+    for (int c = 0; c < 2; ++c) FP_ALLOC(v[c], n);
+    FP_ALLOC(dlist, 2 * (size_t)n);
     FP_ALLOC(rmin, p->m);
     FP_ALLOC(rninf, p->m);
     FP_ALLOC(flag, n);
@@ -389,6 +465,8 @@ extern "C" int fix_and_propagate(mip_problem* p, const double* x, const double* 
         k_pair_of<<<gridn(cache->npairs), 256, 0, s>>>(cache->npairs, cache->var, pair_of);
         k_pair_of_clear<<<gridn(n), 256, 0, s>>>(n, pair_of);
     }
+    mip_problem* tw = nullptr;
+    FP_TRY(twin_problem(p, s, &tw));
     // ---- propagate the start bounds
     FP_CUDA(cudaMemcpyAsync(Bl, lb, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     FP_CUDA(cudaMemcpyAsync(Bu, ub, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
@@ -473,7 +551,7 @@ extern "C" int fix_and_propagate(mip_problem* p, const double* x, const double* 
         // candidate values and start boxes of the two vectors
         k_draws<<<gridn(bsize), 256, 0, s>>>((int)bsize, bulk, x, Bl, Bu, prm.seed, bulk_index, single ? 1 : 0,
                                                prm.up_prob, v[0], v[1]);
-        FP_CUDA(cudaMemsetAsync(dcnt, 0, 2 * sizeof(int), s));
+        FP_CUDA(cudaMemsetAsync(dcnt, 0, sizeof(int), s));
         for (int c = 0; c < 2; ++c) {
             FP_CUDA(cudaMemcpyAsync(cl[c], Bl, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
             FP_CUDA(cudaMemcpyAsync(cu[c], Bu, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
@@ -483,13 +561,14 @@ extern "C" int fix_and_propagate(mip_problem* p, const double* x, const double* 
             } else {
                 k_apply_plain<<<gridn(bsize), 256, 0, s>>>((int)bsize, bulk, v[c], cl[c], cu[c], &dctl->kept[c]);
             }
-            k_diff<<<gridn(n), 256, 0, s>>>(n, cl[c], cu[c], Bl, Bu, dlist[c], dcnt + c);
+            k_diff<<<gridn(n), 256, 0, s>>>(n, cl[c], cu[c], Bl, Bu, c * n, dlist, dcnt);
             FP_CUDA(cudaGetLastError());
-            // double propagation: each vector from the rows of the variables it changes
-            FP_TRY(launch_propagate(p, cl[c], cu[c], nullptr, 0, prm.theta, prm.max_rounds, nullptr, s, dlist[c],
-                                    dcnt + c));
-            FP_CUDA(cudaMemcpyAsync(&dctl->res[c], p->w.dres, sizeof(bp_result), cudaMemcpyDeviceToDevice, s));
         }
+        // double propagation in one launch: each vector from the rows of the variables it
+        // changes, as the two instances of the pair
+        FP_TRY(launch_propagate(tw, cl[0], cu[0], nullptr, 0, prm.theta, prm.max_rounds, nullptr, s, dlist, dcnt, 2,
+                                tw->inst_row_off, tw->inst_col_off));
+        FP_CUDA(cudaMemcpyAsync(dctl->res, tw->w.dres, 2 * sizeof(bp_result), cudaMemcpyDeviceToDevice, s));
         FP_CUDA(cudaMemcpyAsync(hctl, dctl, sizeof(FpCtl), cudaMemcpyDeviceToHost, s));
         FP_CUDA(cudaStreamSynchronize(s));
         bool feas[2];
@@ -506,8 +585,8 @@ extern "C" int fix_and_propagate(mip_problem* p, const double* x, const double* 
         const int pick = feas[0] ? 0 : (feas[1] ? 1 : -1);
         if (pick >= 0) {
             result->fixed_by_choice += hctl->kept[pick];
-            std::swap(Bl, cl[pick]);
-            std::swap(Bu, cu[pick]);
+            FP_CUDA(cudaMemcpyAsync(Bl, cl[pick], sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+            FP_CUDA(cudaMemcpyAsync(Bu, cu[pick], sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
         } else if (!single) {
             recq.resize((size_t)bsize);
             FP_CUDA(cudaMemcpyAsync(recq.data(), bulk, sizeof(int) * bsize, cudaMemcpyDeviceToHost, s));
