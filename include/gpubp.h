@@ -401,6 +401,9 @@ void fp_params_default(fp_params *p);   /* seed 1, sqrt rule, last_single 36, fr
  *           x clamped to their final bounds.
  * result:   HOST pointer, valid at return (the call synchronises the stream: every bulk's
  *           control decision reads a few words back).
+ * Memory: the first call on a handle also loads a second copy of the problem, as two
+ * instances of a block-diagonal pair, so that each bulk's two candidate vectors propagate in
+ * one launch; the handle keeps it until mip_free (about twice the handle's own device memory).
  * Returns BP_OK, BP_ERR_INVALID, BP_ERR_OOM, BP_ERR_CUDA or BP_ERR_TIMEOUT.
  */
 int fix_and_propagate(mip_problem *p, const double *x, const double *lb, const double *ub,
