@@ -110,7 +110,7 @@ class ClockSampler:
 # DRAM bytes (read + write) of one bp_kernel launch on this workload, from the ncu capture
 # summarised in profiles/bp_kernel_mixed_powerlaw_5M.md; reported only while the kernel's
 # sources are the ones that capture was taken on.
-NCU_TRAFFIC = {"sources_sha256_16": "d9d29cc7c1e822eb", "bytes": 197_384_192}
+NCU_TRAFFIC = {"sources_sha256_16": "86daee5486a4bae9", "bytes": 196_688_384}
 KERNEL_SOURCES = ["bp_engine.cu", "bp_device.cuh", "bp_host.h"]
 
 
