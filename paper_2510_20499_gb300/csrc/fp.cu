@@ -344,11 +344,44 @@ static int gridn(long long work) {
 
 // per-bulk control words read back by the host
 struct FpCtl {
-    int nun;
     int kept[2];
-    int pad;
+    int ucnt[2];      // unfixed integer variables under each candidate's propagated bounds
     bp_result res[2];
 };
+
+// Blocks of row c (blockIdx.y) count the integer variables left unfixed by candidate c (bounds
+// l + c n, u + c n) into out[c], zeroed by k_fill_pair: the next bulk's unfixed count, read with
+// the candidates' results in one transfer.
+__global__ void k_count_unset2(int nint, const int* order, const double* l, const double* u, int n, int* out) {
+    __shared__ int part[8];
+    const double* lc = l + (size_t)blockIdx.y * n;
+    const double* uc = u + (size_t)blockIdx.y * n;
+    int c = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nint; i += gridDim.x * blockDim.x) {
+        const int j = order[i];
+        c += lc[j] < uc[j] ? 1 : 0;
+    }
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        if (t) atomicAdd(out + blockIdx.y, t);
+    }
+}
+
+// both candidates start from the current bounds: (l, u) into both halves of (cl, cu)
+__global__ void k_fill_pair(int n, const double* l, const double* u, double* cl, double* cu, int* ucnt) {
+    if (blockIdx.x == 0 && threadIdx.x < 2) ucnt[threadIdx.x] = 0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const double a = l[j], b = u[j];
+        cl[j] = a;
+        cl[n + j] = a;
+        cu[j] = b;
+        cu[n + j] = b;
+    }
+}
 
 }  // namespace gpubp
 
@@ -406,7 +439,7 @@ extern "C" int fix_and_propagate(mip_problem* p, const double* x, const double* 
         tmp.clear();
     };
     int rc = BP_OK;
-    double *Bl, *Bu, *cl[2], *cu[2], *v[2], *rmin;
+    double *Bl, *Bu, *cl[2], *cu[2], *v[2], *rmin, *L4, *U4;
     int *flag, *pos, *ivars, *order, *work, *twork, *rninf, *dlist, *dcnt, *pair_of = nullptr, *total;
     unsigned long long *keys, *tkeys;
     FpCtl* dctl;
@@ -416,13 +449,14 @@ extern "C" int fix_and_propagate(mip_problem* p, const double* x, const double* 
         rc = alloc(&ptr, (size_t)(cnt));        \
         if (rc != BP_OK) { release(); return rc; } \
     } while (0)
-    FP_ALLOC(Bl, n);
-    FP_ALLOC(Bu, n);
-    // the candidates' bounds: the two halves of one array each, as the instance pair reads them
-    FP_ALLOC(cl[0], 2 * (size_t)n);
-    FP_ALLOC(cu[0], 2 * (size_t)n);
-    cl[1] = cl[0] + n;
-    cu[1] = cu[0] + n;
+    // Four bound slots: the current bounds in one, the two candidates in the two halves of the
+    // other pair (slots 0-1 or 2-3), so the instance pair reads them as one array and a picked
+    // candidate becomes the current bounds without a copy.
+    FP_ALLOC(L4, 4 * (size_t)n);
+    FP_ALLOC(U4, 4 * (size_t)n);
+    int cur = 0;
+    Bl = L4;
+    Bu = U4;
     for (int c = 0; c < 2; ++c) FP_ALLOC(v[c], n);
     FP_ALLOC(dlist, 2 * (size_t)n);
     FP_ALLOC(rmin, p->m);
@@ -496,6 +530,8 @@ extern "C" int fix_and_propagate(mip_problem* p, const double* x, const double* 
     std::vector<int> recq;
     size_t rec_pos = 0;
     unsigned long long bulk_index = 0;
+    bool have_nun = false;   // the unfixed count came with the previous bulk's results
+    int next_nun = 0;
     while (!rounding_infeasible) {
         // unfixed integer variables in the initial order
         int nun = 0;
@@ -503,9 +539,14 @@ extern "C" int fix_and_propagate(mip_problem* p, const double* x, const double* 
             k_unset_flag<<<gridn(nint), 256, 0, s>>>(nint, order, Bl, Bu, flag);
             FP_TRY(scan_exclusive(flag, pos, nint, total, s));
             k_compact_list<<<gridn(nint), 256, 0, s>>>(nint, order, flag, pos, work);
-            FP_CUDA(cudaMemcpyAsync(&nun, total, sizeof(int), cudaMemcpyDeviceToHost, s));
-            FP_CUDA(cudaStreamSynchronize(s));
+            if (have_nun) {
+                nun = next_nun;
+            } else {
+                FP_CUDA(cudaMemcpyAsync(&nun, total, sizeof(int), cudaMemcpyDeviceToHost, s));
+                FP_CUDA(cudaStreamSynchronize(s));
+            }
         }
+        have_nun = false;
         if (nun == 0) break;
         long long bsize = 1;
         bool single = false;
@@ -552,9 +593,13 @@ extern "C" int fix_and_propagate(mip_problem* p, const double* x, const double* 
         k_draws<<<gridn(bsize), 256, 0, s>>>((int)bsize, bulk, x, Bl, Bu, prm.seed, bulk_index, single ? 1 : 0,
                                                prm.up_prob, v[0], v[1]);
         FP_CUDA(cudaMemsetAsync(dcnt, 0, sizeof(int), s));
+        const int cp = ((cur >> 1) ^ 1) * 2;   // first slot of the candidates' pair
+        cl[0] = L4 + (size_t)cp * n;
+        cu[0] = U4 + (size_t)cp * n;
+        cl[1] = cl[0] + n;
+        cu[1] = cu[0] + n;
+        k_fill_pair<<<gridn(n), 256, 0, s>>>(n, Bl, Bu, cl[0], cu[0], dctl->ucnt);
         for (int c = 0; c < 2; ++c) {
-            FP_CUDA(cudaMemcpyAsync(cl[c], Bl, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-            FP_CUDA(cudaMemcpyAsync(cu[c], Bu, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
             if (use_cache) {
                 k_apply_cache<<<1, 32, 0, s>>>((int)bsize, bulk, v[c], cl[c], cu[c], p->dp.is_int, pair_of, *cache,
                                                &dctl->kept[c]);
@@ -569,6 +614,10 @@ extern "C" int fix_and_propagate(mip_problem* p, const double* x, const double* 
         FP_TRY(launch_propagate(tw, cl[0], cu[0], nullptr, 0, prm.theta, prm.max_rounds, nullptr, s, dlist, dcnt, 2,
                                 tw->inst_row_off, tw->inst_col_off));
         FP_CUDA(cudaMemcpyAsync(dctl->res, tw->w.dres, 2 * sizeof(bp_result), cudaMemcpyDeviceToDevice, s));
+        {
+            const int gx = (nint + 1023) / 1024 < 64 ? (nint + 1023) / 1024 : 64;
+            k_count_unset2<<<dim3(gx > 0 ? gx : 1, 2), 256, 0, s>>>(nint, order, cl[0], cu[0], n, dctl->ucnt);
+        }
         FP_CUDA(cudaMemcpyAsync(hctl, dctl, sizeof(FpCtl), cudaMemcpyDeviceToHost, s));
         FP_CUDA(cudaStreamSynchronize(s));
         bool feas[2];
@@ -585,14 +634,19 @@ extern "C" int fix_and_propagate(mip_problem* p, const double* x, const double* 
         const int pick = feas[0] ? 0 : (feas[1] ? 1 : -1);
         if (pick >= 0) {
             result->fixed_by_choice += hctl->kept[pick];
-            FP_CUDA(cudaMemcpyAsync(Bl, cl[pick], sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-            FP_CUDA(cudaMemcpyAsync(Bu, cu[pick], sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+            cur = cp + pick;
+            Bl = L4 + (size_t)cur * n;
+            Bu = U4 + (size_t)cur * n;
+            next_nun = hctl->ucnt[pick];
+            have_nun = nint > 0;
         } else if (!single) {
             recq.resize((size_t)bsize);
             FP_CUDA(cudaMemcpyAsync(recq.data(), bulk, sizeof(int) * bsize, cudaMemcpyDeviceToHost, s));
             FP_CUDA(cudaStreamSynchronize(s));
             rec_pos = 0;
             result->recoveries++;
+            next_nun = nun;   // the bounds did not move
+            have_nun = true;
         } else {
             rounding_infeasible = true;
         }
