@@ -42,7 +42,7 @@ __global__ void k_sort_scatter(const unsigned long long* keys, const int* vals, 
                                int ntiles, const int* uniform, unsigned long long* okeys, int* ovals) {
     __shared__ int run[kRadix];                       // elements of each digit already placed by this tile
     __shared__ int wcnt[kSortThreads / 32][kRadix];   // per-warp digit counts of the current chunk
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int w = threadIdx.x >> 5;
     const int t0 = blockIdx.x * kSortTile, t1 = min(n, t0 + kSortTile);
     if (*uniform) {   // nothing moves: copy
         for (int i = t0 + threadIdx.x; i < t1; i += blockDim.x) {
