@@ -404,7 +404,9 @@ void fp_params_default(fp_params *p);   /* seed 1, sqrt rule, last_single 36, fr
  * Memory: the first call on a handle also loads a second copy of the problem, as two
  * instances of a block-diagonal pair, so that each bulk's two candidate vectors propagate in
  * one launch; the handle keeps it until mip_free (about twice the handle's own device memory).
- * Returns BP_OK, BP_ERR_INVALID, BP_ERR_OOM, BP_ERR_CUDA or BP_ERR_TIMEOUT.
+ * The pair's indices are 32-bit, so m, n and nnz must each be below 2^30 (BP_ERR_CAPACITY
+ * otherwise).
+ * Returns BP_OK, BP_ERR_INVALID, BP_ERR_CAPACITY, BP_ERR_OOM, BP_ERR_CUDA or BP_ERR_TIMEOUT.
  */
 int fix_and_propagate(mip_problem *p, const double *x, const double *lb, const double *ub,
                       const fp_cache *cache, const fp_params *params, double *x_out,

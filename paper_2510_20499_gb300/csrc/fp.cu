@@ -267,6 +267,11 @@ static void twin_free(mip_problem* p) {
 // grid barriers and its rounds, and each copy's status, rounds and nonzeros stay its own.
 static int twin_problem(mip_problem* p, cudaStream_t s, mip_problem** out) {
     if (!p->twin) {
+        if ((long long)p->nnz >= (1ll << 30) || p->m >= (1 << 30) || p->n >= (1 << 30)) {
+            set_error("fix_and_propagate: the candidate pair holds two copies of the problem, so m, n and "
+                      "nnz must each be below 2^30 (nnz = %lld)", (long long)p->nnz);
+            return BP_ERR_CAPACITY;
+        }
         const size_t m = (size_t)p->m, n = (size_t)p->n, nnz = (size_t)p->nnz;
         void* buf[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
         const size_t bytes[7] = {8 * (2 * m + 1), 4 * 2 * nnz + 4, 8 * 2 * nnz + 8, 8 * 2 * m + 8, 8 * 2 * n + 8,
