@@ -285,3 +285,49 @@ def test_mixed_instance_small_runs_clean():
     assert r["fragile"] == 0
     # the planted point stays inside the bounds (soundness on a known feasible point)
     assert (p.x0 >= ol - 1e-6).all() and (p.x0 <= ou + 1e-6).all()
+
+
+def _rows_of(p, vars_):
+    """Rows holding any of the given variables (ascending)."""
+    col = np.asarray(p.col)
+    row_of = np.repeat(np.arange(p.m), np.diff(p.row_ptr))
+    return np.unique(row_of[np.isin(col, vars_)]).astype(np.int32)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_block_diagonal_pair_propagates_each_copy_alone(seed):
+    """Two copies of one problem side by side (rows k and m + k, variables j and n + j), each
+    started from its own fixings: propagated together from the union of their start rows, every
+    copy ends with the bounds of its own propagation, the nonzeros add up and the rounds are the
+    larger of the two. Jacobi rounds never couple disjoint blocks; this is what lets the two
+    candidate vectors of a fix-and-propagate bulk share one propagation."""
+    p = synth.random_milp(900 + seed, m=250, n=320, len_lo=1, len_hi=12, int_fraction=0.8, integer_coefs=True)
+    P = oracle.Problem(p)
+    rl, ru, r, _ = P.bp(p.lb, p.ub)
+    if r["status"] != oracle.FIXPOINT:
+        pytest.skip("root not at a fixpoint")
+    rng = np.random.default_rng(seed)
+    free = np.flatnonzero((rl < ru) & (p.is_int == 1))
+    starts = []
+    for c in range(2):
+        fix = rng.choice(free, size=min(6, len(free)), replace=False)
+        l, u = rl.copy(), ru.copy()
+        for j in fix:   # round the variable to one of its bounds, as a rounding bulk does
+            v = l[j] if rng.uniform() < 0.5 else u[j]
+            if not np.isfinite(v):
+                v = l[j] if np.isfinite(l[j]) else u[j]
+            l[j] = u[j] = v
+        starts.append((l, u, _rows_of(p, fix)))
+    alone = [P.bp(l, u, w0=w) for l, u, w in starts]
+    if any(a[2]["status"] == oracle.INFEASIBLE for a in alone):
+        pytest.skip("a copy is infeasible: the pair would stop with it")
+    pair, ro, co = synth.block_diagonal([p, p])
+    PP = oracle.Problem(pair)
+    w0 = np.concatenate([starts[0][2], starts[1][2] + p.m]).astype(np.int32)
+    L, U, R, _ = PP.bp(np.concatenate([starts[0][0], starts[1][0]]), np.concatenate([starts[0][1], starts[1][1]]), w0=w0)
+    for c in range(2):
+        np.testing.assert_array_equal(L[c * p.n:(c + 1) * p.n], alone[c][0])
+        np.testing.assert_array_equal(U[c * p.n:(c + 1) * p.n], alone[c][1])
+    assert R["status"] == oracle.FIXPOINT
+    assert R["nnz_updates"] == alone[0][2]["nnz_updates"] + alone[1][2]["nnz_updates"]
+    assert R["rounds"] == max(alone[0][2]["rounds"], alone[1][2]["rounds"])
