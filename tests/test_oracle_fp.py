@@ -171,3 +171,22 @@ def test_order_score_replaces_implied_slack_order():
                                                  order_score=np.array([3.0, 0.0, 2.0, 1.0]))
     np.testing.assert_array_equal(out, [1.0, 0.0, 1.0, 0.0])
     assert (r["bulks"], r["recoveries"], r["status"]) == (1, 0, 0)
+
+
+def test_recovery_one_variable_at_a_time():
+    """Hand-worked recovery (Section 2.3: a bulk that fails both ways is retried one variable at
+    a time). Binaries x1, x2 at x = (0.9, 0.9), row x1 + x2 <= 1, one bulk of both (bulk rule
+    fraction 1.0, no single-variable tail). f = 0.9 >= 0.75 draws 1 in both vectors, so both
+    candidates are (1, 1) and the row is violated: the bulk fails both ways. Recovery takes x1
+    alone: it draws 1, which propagates x2 <= 0, and every variable is fixed.
+    Counts: bulks 2 (the failed pair, then x1), propagations 5 (start, two per bulk), one
+    recovery, one fixing by choice. Nonzeros: start 2 (one round over the row); each failed
+    candidate 2; x1 = 1 takes two rounds (the row, then the row again for x2) = 4; x1 = 0 takes
+    one round = 2; total 12."""
+    p = milp_from_dense(np.array([[1.0, 1.0]]), [1.0], np.zeros(2), np.ones(2), np.ones(2))
+    for seed in (1, 2, 3):
+        xo, r = oracle.Problem(p).fix_and_propagate(np.array([0.9, 0.9]), p.lb, p.ub, seed=seed, bulk_rule=1,
+                                                    fraction=1.0, last_single=0)
+        assert r["status"] == 0
+        assert list(xo) == [1.0, 0.0]
+        assert (r["bulks"], r["bp_runs"], r["recoveries"], r["fixed_by_choice"], r["nnz_updates"]) == (2, 5, 1, 1, 12)
