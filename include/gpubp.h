@@ -166,13 +166,16 @@ int bp_propagate_from(mip_problem *p, double *lb, double *ub, const int32_t *var
  *
  * The per-call scratch is a fixed array of BP_NOALLOC_SCRATCH_BYTES (32 MiB) in the library's
  * static device memory, one per device, instead of the handle's own buffers.  A problem needs
- * about 44 n + 12 m + 32 (chunks of rows longer than 2048) + 24 (such rows) bytes plus 4 KB;
+ * 44 n + 12 m + 32 P bytes, P the pieces of its long rows (about nnz / 256 + rows longer than
+ * 256 nonzeros at the default piece length), plus at most 10 KB of control block and alignment;
  * a larger problem is rejected with BP_ERR_CAPACITY before anything is enqueued (bp_last_error
- * gives the bytes needed).  Each call clears the part of the scratch that must start at zero.
+ * gives the exact bytes needed).  Each call clears the part of the scratch that must start at
+ * zero.
  *
- * Set-up: the first call on a device, with the handle's device current, looks up the array's
- * device address (cudaGetSymbolAddress, which may load the module holding it); make that first
- * call before any stream capture.  Calls that overlap in time on one device, from any handle,
+ * Set-up: mip_load_csr looks up the array's device address on the handle's device
+ * (cudaGetSymbolAddress), which loads the module holding it and so reserves its 32 MiB there,
+ * together with the handle's own memory.  This entry point then allocates nothing, on its first
+ * call as on every later one.  Calls that overlap in time on one device, from any handle,
  * stream or thread, share the one array and race: order them.  The handle must not be used by
  * another call meanwhile either.
  *
@@ -278,11 +281,12 @@ int bp_probe_priority(mip_problem *p, const double *lb, const double *ub, int32_
 
 /* Split points of the row classes and grid shape of the propagation engine.  Rows are binned
  * by length (Section 2.1): rows with fewer than warp_min nonzeros are handled one per thread,
- * rows of warp_min .. block_min-1 one per warp, rows of block_min .. 2048 one per block, longer
- * rows in chunks of chunk_len nonzeros, one block each.  blocks_per_sm: thread blocks per SM of
- * the persistent grid.  Valid: 2 <= warp_min <= 9, warp_min <= block_min <= 257,
+ * rows of warp_min .. block_min-1 one per warp, and rows of block_min or more nonzeros (every
+ * row longer than 256) in pieces of chunk_len nonzeros, one warp each, whose partial
+ * activities are summed after a grid-wide phase barrier.  blocks_per_sm: thread blocks per SM
+ * of the persistent grid.  Valid: 2 <= warp_min <= 9, warp_min <= block_min <= 257,
  * 1 <= blocks_per_sm <= the number that can be resident (2 on GB300), chunk_len in
- * {256, 512, 1024, 2048}.  Defaults: 2, 257, all resident, 2048 (on GB300 a warp per row beat a
+ * {32, 64, 128, 256}.  Defaults: 2, 257, all resident, 256 (on GB300 a warp per row beat a
  * thread per row for rows of 2..8 nonzeros on every workload measured). */
 typedef struct {
     int32_t warp_min;

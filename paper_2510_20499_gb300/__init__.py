@@ -395,7 +395,7 @@ def _get_tuning(prob):
     return t.as_dict()
 
 
-def _set_tuning(prob, warp_min, block_min, blocks_per_sm, chunk_len=2048, stream=None):
+def _set_tuning(prob, warp_min, block_min, blocks_per_sm, chunk_len=256, stream=None):
     t = BpTuning(int(warp_min), int(block_min), int(blocks_per_sm), int(chunk_len))
     _check(lib().bp_set_tuning(prob.h, C.byref(t), _stream(stream)))
 

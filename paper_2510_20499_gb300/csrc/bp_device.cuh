@@ -21,43 +21,43 @@ constexpr int kWarp = 32;
 // Rows are binned by length (in the spirit of logarithmic radix binning, Section 2.1):
 //   classes 0..3: at most 1, 2, 4, 8 nonzeros          -> one thread per row
 //   class 4:      9 .. kWarpMax nonzeros               -> one warp per row
-//   class 5:      kWarpMax+1 .. kChunk nonzeros        -> one thread block per row
-//   class 6:      more than kChunk nonzeros            -> chunks of chunk_len <= kChunk nonzeros,
-//                                                         one block each
-// Every task then holds at most kPerThread nonzeros per thread, all loaded in one wave.
+//   class 5:      (unused)
+//   class 6:      more than kWarpMax nonzeros          -> "piece rows": pieces of chunk_len
+//                                                         (kPieceMin .. kPieceMax) nonzeros, one
+//                                                         warp each; a round sums the pieces'
+//                                                         partial activities after a phase barrier
+// Every task then holds at most kPerThread nonzeros per lane, all loaded in one wave, and all
+// work of a round is warp-sized, so that it spreads over every SM of the grid.
 constexpr int kNumClass = 7;
 constexpr int kNumThreadBins = 4;
 constexpr int kClassWarpRow = 4;
-constexpr int kClassBlockRow = 5;
-constexpr int kClassChunked = 6;
+constexpr int kClassPieces = 6;
 constexpr int kPerThread = 8;
 constexpr int kThreadMax = kPerThread;            // 8
 constexpr int kWarpMax = 32 * kPerThread;         // 256
-constexpr int kChunk = 256 * kPerThread;          // 2048 (blocks of 256 threads)
-constexpr int kChunkMin = 256;                    // smallest chunk length of a chunked row
-// default split points (bp_autotune may pick others): a warp per row from 2 nonzeros, a block
-// per row from kWarpMax + 1, chunks of kDefaultChunkLen
+constexpr int kPieceMax = kWarpMax;               // nonzeros of one piece: one wave of a warp
+constexpr int kPieceMin = 32;                     // shortest piece length (sizes the piece lists)
+// default split points (bp_autotune may pick others): a warp per row from 2 nonzeros, pieces
+// for rows longer than kWarpMax, pieces of kDefaultChunkLen nonzeros
 constexpr int kDefaultWarpMin = 2;
-constexpr int kDefaultChunkLen = kChunk;
+constexpr int kDefaultChunkLen = kPieceMax;
 
 __host__ __device__ inline int row_class(int len) {
     if (len <= 1) return 0;
     if (len <= 2) return 1;
     if (len <= 4) return 2;
     if (len <= kThreadMax) return 3;
-    if (len <= kWarpMax) return 4;
-    if (len <= kChunk) return 5;
-    return 6;
+    if (len <= kWarpMax) return kClassWarpRow;
+    return kClassPieces;
 }
 
-// Class of a row under tunable split points (the autotuner's search space): rows of warp_min
-// or more nonzeros go to one warp, rows of block_min or more to one block, shorter rows to the
+// Class of a row under tunable split points (the autotuner's search space): rows of block_min
+// or more nonzeros are piece rows, rows of warp_min or more go to one warp, shorter rows to the
 // thread bins above.  2 <= warp_min <= kThreadMax + 1 and warp_min <= block_min <= kWarpMax + 1;
-// rows longer than kChunk are always chunked.  warp_min = kThreadMax + 1, block_min = kWarpMax + 1
-// reproduce row_class.
+// rows longer than kWarpMax are always piece rows.  warp_min = kThreadMax + 1,
+// block_min = kWarpMax + 1 reproduce row_class.
 __host__ __device__ inline int row_class_tuned(int len, int warp_min, int block_min) {
-    if (len > kChunk) return kClassChunked;
-    if (len >= block_min) return kClassBlockRow;
+    if (len > kWarpMax || len >= block_min) return kClassPieces;
     if (len >= warp_min) return kClassWarpRow;
     return row_class(len);
 }
@@ -249,14 +249,12 @@ struct DevProblem {
     const double* col_val;       // nnz: coefficients in transpose order
     const unsigned char* is_int; // n
     const unsigned char* rclass; // m
-    const int* rinfo;            // m: class | chunks << 3 (chunks of a chunked row, else 0)
-    const int* heavy_id;         // m: index among chunked rows, -1 otherwise
-    const int* part_off;         // nheavy+1: first partial slot of each chunked row
+    const int* rinfo;            // m: class | pieces << 3 (pieces of a piece row, else 0)
     const int* static_list;      // m: row ids grouped by class, ascending within a class
-    const int2* static_tasks;    // all chunk tasks {row, chunk} of the chunked rows
+    const int2* static_tasks;    // every piece {row, piece} of the piece rows (round 0)
     int class_off[kNumClass + 1];// class segments of static_list and of worklists
-    int chunk_len;               // nonzeros per chunk of a chunked row (kChunkMin .. kChunk)
-    int nheavy, nchunks;         // chunked rows, total chunks
+    int chunk_len;               // nonzeros per piece of a piece row (kPieceMin .. kPieceMax)
+    int nlong, npieces;          // piece rows, their pieces at chunk_len
 };
 
 }  // namespace gpubp

@@ -14,15 +14,20 @@
 // Rounds are separated by one grid barrier.  All waits are bounded: a wait that runs out sets
 // BP_ERR_TIMEOUT and the launch returns.
 //
-// The rounds are latency-bound (a round is a chain of dependent L2 round trips), so every task
-// holds at most kPerThread nonzeros per thread, issues all their loads in one wave, then all
-// their bound gathers in one wave, and keeps them in registers for the candidate pass.
-//
-// Work split per phase (static round-robin, no shared dequeue counter):
-//   block tasks   [chunk partial sums][block-per-row rows]
-//   warp tasks    [fix-ups of the previous round's changes][thread-per-row bins][warp rows]
-//   block tasks   [chunk candidates] -- they wait for their row's total, which the first
-//                 block segment produces without waiting, so every wait ends.
+// The rounds are latency-bound (a round is a chain of dependent L2 round trips and of
+// synchronising operations, each a few hundred cycles on GB300), so all work of a round is
+// warp-sized and spread over every SM, and a round holds as few synchronising steps as
+// possible:
+//   phase A   warp tasks [pieces][fix-ups of the previous round's changes][thread-per-row
+//             bins][warp rows]: short rows are finished here (activity, verdict, candidates);
+//             a piece (a slice of at most kPieceMax nonzeros of a long row) stores its partial
+//             activity in its slot;
+//   barrier   only when the round has pieces;
+//   phase B   every piece sums its row's partials in slot order (the same order for every piece
+//             of the row, so all see the same total), the first piece records the row's verdict
+//             and work, and each piece evaluates its own nonzeros' candidates;
+//   then the changed variables are listed and their rows queued for the next round, and the
+//   round ends at the grid barrier.  No task ever waits for another task.
 #include <climits>
 #include <cstdlib>
 
@@ -37,11 +42,11 @@ namespace gpubp {
 constexpr int kThreads = 256;
 constexpr int kWarpsPerBlock = kThreads / 32;
 constexpr int kSlots = kNumClass;               // staging slots: row classes 0..5, then changed vars
-constexpr int kSlotChg = kClassChunked;         // chunked rows are not staged; their slot holds variables
+constexpr int kSlotChg = kClassPieces;          // piece rows are not staged; their slot holds variables
 constexpr int kBq = 2048;                       // per-block queue of accepted variables
 constexpr int kMaxInst = kMaxInstances;         // instances per batched launch
 constexpr long long kSpinLimit = 4000000000LL;  // clock64 cycles (about 2 s) per wait
-static_assert(kThreads * kPerThread == kChunk, "the longest chunk is one wave of a block");
+static_assert(32 * kPerThread == kPieceMax, "the longest piece is one wave of a warp");
 
 struct BpArgs {
     double* lb;
@@ -54,10 +59,6 @@ struct BpArgs {
     int2* task[2];
     double* hpart;
     int2* hpinf;
-    double* htot;
-    int2* htinf;
-    int* harr;
-    int* hready;
     Ctl* ctl;
     bp_result* dres;
     const int* w0;      // rows of round 0, or null for every row
@@ -93,12 +94,8 @@ struct Stage {
     int wbuf[kWarpsPerBlock][kSlots][32];
     int bq_n;                                   // variables with an accepted candidate in this phase
     int bq[kBq];
-    double red_d[kWarpsPerBlock];
-    int red_n[kWarpsPerBlock], red_j[kWarpsPerBlock];
     unsigned long long nnz;
-    int flag, last, ok;
-    double tot_d;                               // row total of a fused chunk task
-    int tot_n, tot_j;
+    int flag;
     // descriptor of the current phase, read once per block by thread 0
     int d_cnt[kNumClass];
     int d_ntask, d_nprev;
@@ -206,7 +203,7 @@ __device__ void lane_queue_row(const BpArgs& A, const DevProblem& P, const Phase
     const int info = __ldg(P.rinfo + k);   // issued before the stamp atomic: no dependency
     if (atomicMax(&A.rstamp[k], ph.st_r) >= ph.st_r) return;
     const int cls = info & 7;
-    if (cls != kClassChunked) {
+    if (cls != kClassPieces) {
         const int pos = atomicAdd(&A.ctl->cnt[ph.ns3()][cls].v, 1);
         A.list[ph.npar][P.class_off[cls] + pos] = k;
         return;
@@ -214,24 +211,34 @@ __device__ void lane_queue_row(const BpArgs& A, const DevProblem& P, const Phase
     const int nch = info >> 3;
     const int base = atomicAdd(&A.ctl->ntask[ph.ns3()].v, nch);
     for (int c = 0; c < nch; ++c) A.task[ph.npar][base + c] = make_int2(k, c);
-    atomicAdd(&A.ctl->cnt[ph.ns3()][kClassChunked].v, 1);
+    atomicAdd(&A.ctl->cnt[ph.ns3()][kClassPieces].v, 1);
 }
 
 // Warp-wide: queue the rows `k` (k < 0: none) for the next round; a row's first queuing in
-// this round wins.  Chunked rows get their chunk tasks directly (they are few).
+// this round wins.  A piece row gets its pieces, contiguous and in row order, in the piece list
+// (the lanes with piece rows write them together).
 __device__ void warp_queue_rows(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, int k) {
-    int slot = -1;
+    const int lane = threadIdx.x & 31;
+    int slot = -1, nch = 0, base = 0;
     const int info = k >= 0 ? __ldg(P.rinfo + k) : 0;   // issued before the stamp atomic
     if (k >= 0 && atomicMax(&A.rstamp[k], ph.st_r) < ph.st_r) {
         const int cls = info & 7;
-        if (cls != kClassChunked) {
+        if (cls != kClassPieces) {
             slot = cls;
         } else {
-            const int nch = info >> 3;
-            const int base = atomicAdd(&A.ctl->ntask[ph.ns3()].v, nch);
-            for (int c = 0; c < nch; ++c) A.task[ph.npar][base + c] = make_int2(k, c);
-            atomicAdd(&A.ctl->cnt[ph.ns3()][kClassChunked].v, 1);
+            nch = info >> 3;
+            base = atomicAdd(&A.ctl->ntask[ph.ns3()].v, nch);
+            atomicAdd(&A.ctl->cnt[ph.ns3()][kClassPieces].v, 1);
         }
+    }
+    unsigned longs = __ballot_sync(0xffffffffu, nch > 0);
+    while (longs) {
+        const int src = __ffs(longs) - 1;
+        const int kk = __shfl_sync(0xffffffffu, k, src);
+        const int nn = __shfl_sync(0xffffffffu, nch, src);
+        const int bb = __shfl_sync(0xffffffffu, base, src);
+        for (int c = lane; c < nn; c += 32) A.task[ph.npar][bb + c] = make_int2(kk, c);
+        longs &= longs - 1;
     }
     warp_append(st, A, P, ph, slot, k);
 }
@@ -328,34 +335,6 @@ __device__ __forceinline__ Acc warp_reduce(Acc a) {
     return a;
 }
 
-// Block-wide reduction in a fixed order (deterministic); every thread gets the total.
-__device__ __forceinline__ Acc block_reduce(Stage& st, Acc a) {
-    a = warp_reduce(a);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) {
-        st.red_d[w] = a.minfin;
-        st.red_n[w] = a.ninf;
-        st.red_j[w] = a.infj;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {   // one thread sums the warps' partials (the FP64 pipe is narrow)
-        Acc t{0.0, 0, -1};
-#pragma unroll
-        for (int i = 0; i < kWarpsPerBlock; ++i) {
-            t.minfin = __dadd_rn(t.minfin, st.red_d[i]);
-            t.ninf += st.red_n[i];
-            t.infj = max(t.infj, st.red_j[i]);
-        }
-        st.red_d[0] = t.minfin;
-        st.red_n[0] = t.ninf;
-        st.red_j[0] = t.infj;
-    }
-    __syncthreads();
-    const Acc t{st.red_d[0], st.red_n[0], st.red_j[0]};
-    __syncthreads();
-    return t;
-}
-
 // A thread's share of a row range: at most kPerThread nonzeros, held in registers.
 struct Elems {
     int j[kPerThread];
@@ -388,6 +367,19 @@ __device__ __forceinline__ Acc load_accumulate(Elems& E, const DevProblem& P, co
         }
     }
     return s;
+}
+
+// The loads of load_accumulate without the sum (the candidate pass of a piece).
+__device__ __forceinline__ void load_elems(Elems& E, const DevProblem& P, const Phase& ph, int beg, int end, int tid,
+                                           int stride) {
+#pragma unroll
+    for (int i = 0; i < kPerThread; ++i) {
+        const int q = beg + tid + i * stride;
+        E.j[i] = q < end ? __ldg(P.col + q) : -1;
+        E.a[i] = q < end ? __ldg(P.val + q) : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < kPerThread; ++i) E.bk[i] = E.j[i] >= 0 ? ld_bounds(ph.R, E.j[i]) : make_longlong2(0, 0);
 }
 
 // Candidates of the thread's nonzeros given the row total (registers only).
@@ -455,176 +447,57 @@ __device__ void do_warp_row(Stage& st, const BpArgs& A, const DevProblem& P, con
     }
 }
 
-// Block per row (kWarpMax+1 .. kChunk nonzeros): the reduction stays in shared memory.
-__device__ void do_block_row(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, int k) {
-    const int ki = row_inst(st, A, k);
-    if (!st.alive[ki]) return;
-    const int beg = __ldg(P.row_ptr + k), end = __ldg(P.row_ptr + k + 1);
-    const double2 g2 = __ldg(P.grow + k);
+// Piece u = {row k, piece c} of a piece row, phase A: the partial activity of its nonzeros
+// [row start + c chunk_len, + chunk_len) into slot u.
+__device__ void do_piece_partial(const Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, int u,
+                                 int2 tk) {
+    const int lane = threadIdx.x & 31;
+    const int k = tk.x, c = tk.y;
+    if (!st.alive[row_inst(st, A, k)]) return;
+    const int rb = __ldg(P.row_ptr + k), re = __ldg(P.row_ptr + k + 1);
+    const int beg = rb + c * P.chunk_len, end = min(re, beg + P.chunk_len);
     Elems E;
-    const Acc tot = block_reduce(st, load_accumulate(E, P, ph, beg, end, threadIdx.x, kThreads));
-    if (row_infeasible(tot.minfin, tot.ninf, g2.y)) {
-        if (threadIdx.x == 0) atomicMin(&A.i_rowinf[ph.s3() * A.ninst + ki], k);
-    } else {
-        elems_candidates(st, A, P, ph, E, tot, g2.x);
-    }
-    if (threadIdx.x == 0) {
-        atomicAdd(&st.nnz, (unsigned long long)(end - beg));
-        atomicAdd(&st.i_nnz[ki], (unsigned long long)(end - beg));
-    }
-    __syncthreads();
-}
-
-// Sum of the partials of chunked row k in chunk order (deterministic), by warp 0 of the last
-// chunk to arrive; lane 0 checks the row, counts its nonzeros, publishes the total and releases
-// the waiting chunks.  Returns the total in lane 0.
-__device__ Acc chunk_total(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, int k, int ki, int h,
-                           int slot0, int nch, int len, double g_tol) {
-    const int lane = threadIdx.x;
-    __threadfence();
-    Acc s{0.0, 0, -1};
-    for (int i = lane; i < nch; i += 32) {
-        s.minfin = __dadd_rn(s.minfin, __ldcg(A.hpart + slot0 + i));
-        const int2 pi = __ldcg(A.hpinf + slot0 + i);
-        s.ninf += pi.x;
-        s.infj = max(s.infj, pi.y);
-    }
-    s = warp_reduce(s);
+    const Acc s = warp_reduce(load_accumulate(E, P, ph, beg, end, lane, 32));
     if (lane == 0) {
-        if (row_infeasible(s.minfin, s.ninf, g_tol)) atomicMin(&A.i_rowinf[ph.s3() * A.ninst + ki], k);
-        atomicAdd(&st.nnz, (unsigned long long)len);
-        atomicAdd(&st.i_nnz[ki], (unsigned long long)len);
-        A.htot[h] = s.minfin;
-        A.htinf[h] = make_int2(s.ninf, s.infj);
-        A.harr[h] = 0;
-        __threadfence();
-        st_release_s32(A.hready + h, ph.st_v);
+        A.hpart[u] = s.minfin;
+        A.hpinf[u] = make_int2(s.ninf, s.infj);
     }
-    return s;
 }
 
-// Thread 0: writes the block's partial of chunk c and arrives; true for the last arrival.
-__device__ __forceinline__ bool chunk_arrive(const BpArgs& A, const Acc& part, int h, int slot0, int c, int nch) {
-    A.hpart[slot0 + c] = part.minfin;
-    A.hpinf[slot0 + c] = make_int2(part.ninf, part.infj);
-    __threadfence();
-    return atomicAdd(&A.harr[h], 1) == nch - 1;
-}
-
-// Chunk of a long row, first half: the block's partial activity; the last chunk to arrive
-// sums the partials and publishes the row total.  The row's metadata loads are issued before
-// the nonzeros' so that their round trips overlap.
-__device__ void do_chunk_partial(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, int2 tk) {
+// Piece u, phase B: the row total is the sum of the row's piece partials in slot order (the
+// pieces of a row sit in consecutive slots, piece c in slot u - c + c); every piece of the row
+// computes it in the same order and gets the same value.  The first piece records the row's
+// verdict and its nonzeros; each piece then reloads its own nonzeros and bounds (L2) and
+// evaluates their candidates.
+__device__ void do_piece_candidates(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, int u,
+                                    int2 tk) {
+    const int lane = threadIdx.x & 31;
     const int k = tk.x, c = tk.y;
     const int ki = row_inst(st, A, k);
     if (!st.alive[ki]) return;
     const int rb = __ldg(P.row_ptr + k), re = __ldg(P.row_ptr + k + 1);
-    const int h = __ldg(P.heavy_id + k);
-    const int slot0 = __ldg(P.part_off + h);
-    const double g_tol = __ldg(&P.grow[k].y);
-    const int beg = rb + c * P.chunk_len, end = min(re, beg + P.chunk_len);
-    const int nch = (re - rb + P.chunk_len - 1) / P.chunk_len;
-    Elems E;
-    const Acc part = block_reduce(st, load_accumulate(E, P, ph, beg, end, threadIdx.x, kThreads));
-    if (threadIdx.x == 0) st.last = chunk_arrive(A, part, h, slot0, c, nch);
-    __syncthreads();
-    if (st.last && threadIdx.x < 32) (void)chunk_total(st, A, P, ph, k, ki, h, slot0, nch, re - rb, g_tol);
-    __syncthreads();
-}
-
-// Chunk of a long row, both halves at once.  Used when every chunk task of the round is the
-// first task of its block: then no block can wait on a chunk whose block is itself waiting,
-// and the chunk's nonzeros and bounds stay in registers from the partial sum to the
-// candidates instead of being loaded twice.  Returns false when the wait gave up.
-__device__ bool do_chunk_fused(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, int2 tk) {
-    const int k = tk.x, c = tk.y;
-    const int ki = row_inst(st, A, k);
-    if (!st.alive[ki]) return true;
-    const int rb = __ldg(P.row_ptr + k), re = __ldg(P.row_ptr + k + 1);
-    const int h = __ldg(P.heavy_id + k);
-    const int slot0 = __ldg(P.part_off + h);
+    const int npc = __ldg(P.rinfo + k) >> 3;
     const double2 g2 = __ldg(P.grow + k);
-    const int beg = rb + c * P.chunk_len, end = min(re, beg + P.chunk_len);
-    const int nch = (re - rb + P.chunk_len - 1) / P.chunk_len;
-    Elems E;
-    const Acc part = block_reduce(st, load_accumulate(E, P, ph, beg, end, threadIdx.x, kThreads));
-    if (threadIdx.x == 0) st.last = chunk_arrive(A, part, h, slot0, c, nch);
-    __syncthreads();
-    if (st.last) {
-        if (threadIdx.x < 32) {
-            const Acc t = chunk_total(st, A, P, ph, k, ki, h, slot0, nch, re - rb, g2.y);
-            if (threadIdx.x == 0) {
-                st.tot_d = t.minfin;
-                st.tot_n = t.ninf;
-                st.tot_j = t.infj;
-                st.ok = 1;
-            }
-        }
-    } else if (threadIdx.x == 0) {
-        int ok = 1;
-        const long long t0 = clock64();
-        while (ld_acquire_s32(A.hready + h) != ph.st_v) {
-            if (clock64() - t0 > kSpinLimit) {
-                ok = 0;
-                atomicExch(&A.ctl->error, BP_ERR_TIMEOUT);
-                break;
-            }
-            __nanosleep(32);
-        }
-        if (ok) {
-            st.tot_d = __ldcg(A.htot + h);
-            const int2 ti = __ldcg(A.htinf + h);
-            st.tot_n = ti.x;
-            st.tot_j = ti.y;
-        }
-        st.ok = ok;
+    const int first = u - c;
+    Acc t{0.0, 0, -1};
+    for (int i = lane; i < npc; i += 32) {
+        t.minfin = __dadd_rn(t.minfin, __ldcg(A.hpart + first + i));
+        const int2 pi = __ldcg(A.hpinf + first + i);
+        t.ninf += pi.x;
+        t.infj = max(t.infj, pi.y);
     }
-    __syncthreads();
-    const bool ok = st.ok != 0;
-    if (ok) {
-        const Acc tot{st.tot_d, st.tot_n, st.tot_j};
-        if (!row_infeasible(tot.minfin, tot.ninf, g2.y)) elems_candidates(st, A, P, ph, E, tot, g2.x);
+    t = warp_reduce(t);
+    const bool infeasible = row_infeasible(t.minfin, t.ninf, g2.y);
+    if (c == 0 && lane == 0) {
+        atomicAdd(&st.nnz, (unsigned long long)(re - rb));
+        atomicAdd(&st.i_nnz[ki], (unsigned long long)(re - rb));
+        if (infeasible) atomicMin(&A.i_rowinf[ph.s3() * A.ninst + ki], k);
     }
-    __syncthreads();
-    return ok;
-}
-
-// Chunk of a long row, second half: wait for the row total, then the chunk's candidates.
-// The chunk's nonzeros and bounds are loaded before the wait.
-__device__ bool do_chunk_candidates(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, int2 tk) {
-    const int k = tk.x, c = tk.y;
-    if (!st.alive[row_inst(st, A, k)]) return true;
-    const int h = __ldg(P.heavy_id + k);
-    const int rb = __ldg(P.row_ptr + k), re = __ldg(P.row_ptr + k + 1);
+    if (infeasible || t.ninf >= 2) return;
     const int beg = rb + c * P.chunk_len, end = min(re, beg + P.chunk_len);
     Elems E;
-    (void)load_accumulate(E, P, ph, beg, end, threadIdx.x, kThreads);
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        const long long t0 = clock64();
-        while (ld_acquire_s32(A.hready + h) != ph.st_v) {
-            if (clock64() - t0 > kSpinLimit) {
-                ok = 0;
-                atomicExch(&A.ctl->error, BP_ERR_TIMEOUT);
-                break;
-            }
-            __nanosleep(32);
-        }
-        st.last = ok;
-    }
-    __syncthreads();
-    const bool ok = st.last != 0;
-    if (ok) {
-        Acc tot;
-        tot.minfin = __ldcg(A.htot + h);
-        const int2 ti = __ldcg(A.htinf + h);
-        tot.ninf = ti.x;
-        tot.infj = ti.y;
-        const double2 g2 = __ldg(P.grow + k);
-        if (!row_infeasible(tot.minfin, tot.ninf, g2.y)) elems_candidates(st, A, P, ph, E, tot, g2.x);
-    }
-    __syncthreads();
-    return ok;
+    load_elems(E, P, ph, beg, end, lane, 32);
+    elems_candidates(st, A, P, ph, E, t, g2.x);
 }
 
 // Variables changed in the previous round: bring their new bounds into this round's
@@ -649,10 +522,13 @@ __device__ void do_fix(const Stage& st, const BpArgs& A, const DevProblem& P, co
 // waits until all blocks have arrived at this barrier (the launch's bar_k-th).  No block
 // resets anything or releases the others, so no bookkeeping sits on the others' path: after
 // the barrier each block reads the round's counters itself and takes the same decisions.
+// The arrival is one acquire-release atomic of thread 0 after the block barrier (release is
+// cumulative over the writes the block barrier ordered before it) and the wait a tight spin of
+// acquire loads: on GB300 a separate fence costs 450-950 cycles and a sleep in the spin at least
+// 500 cycles of reaction time, and both sit on every round's critical path.
 __device__ void grid_sync(Stage& st, Ctl* ctl) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();   // the block's writes (all threads, ordered by the barrier above)
         atom_add_acqrel_u32(&ctl->bar_count.v, 1u);
         const unsigned target = gridDim.x * (st.bar_k + 1u);
         const long long t0 = clock64();
@@ -661,16 +537,14 @@ __device__ void grid_sync(Stage& st, Ctl* ctl) {
                 atomicExch(&ctl->error, BP_ERR_TIMEOUT);
                 break;
             }
-            __nanosleep(32);
         }
-        __threadfence();
         st.bar_k += 1u;
     }
     __syncthreads();
 }
 
 // Descriptor of round `next` into shared memory (thread 0): its worklist counts per class,
-// its chunk tasks and the previous round's changed variables.
+// its pieces and the previous round's changed variables.
 __device__ __forceinline__ void load_descriptor(Stage& st, Ctl* ctl, const DevProblem& P, const BpArgs& A,
                                                 int next) {
     const int sl = next % kPhaseSlots;
@@ -678,7 +552,7 @@ __device__ __forceinline__ void load_descriptor(Stage& st, Ctl* ctl, const DevPr
 #pragma unroll
     for (int c = 0; c < kNumClass; ++c)
         st.d_cnt[c] = stat ? P.class_off[c + 1] - P.class_off[c] : __ldcg(&ctl->cnt[sl][c].v);
-    st.d_ntask = stat ? P.nchunks : __ldcg(&ctl->ntask[sl].v);
+    st.d_ntask = stat ? P.npieces : __ldcg(&ctl->ntask[sl].v);
     st.d_nprev = next == 0 ? 0 : __ldcg(&ctl->nchg[(next - 1) % kPhaseSlots].v);
 }
 
@@ -843,7 +717,9 @@ __device__ void finish_block(Stage& st, const BpArgs& A) {
 __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProblem P, BpArgs A) {
     __shared__ Stage st;
     const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    // warp tasks are numbered across blocks first, so that a short round's few tasks land on
+    // different SMs
+    const int gw_r = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
     const int NW = gridDim.x * kWarpsPerBlock;
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthreads = gridDim.x * blockDim.x;
     Ctl* ctl = A.ctl;
@@ -871,7 +747,6 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
     if (base > (1 << 30)) {
         for (int v = gtid; v < P.n; v += gthreads) A.vstamp[v] = 0;
         for (int k = gtid; k < P.m; k += gthreads) A.rstamp[k] = 0;
-        for (int h = gtid; h < P.nheavy; h += gthreads) A.hready[h] = 0;
         base = 1;
     }
     // per-instance state and per-phase arrays
@@ -908,7 +783,6 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
         A.bk[1][v] = b;
         if (crossed(is_i, b.x, b.y)) atomicMin(&A.inst[var_inst(st, A, v)].entry_cross, v);
     }
-    for (int h = gtid; h < P.nheavy; h += gthreads) A.harr[h] = 0;  // clean even after an aborted launch
     Phase ph0{0, 0, 1, A.bk[0], A.bk[1], base, base};
     if (A.w0) {
         // queue the given rows into the round-0 lists (stamp `base` = member of round 0)
@@ -1001,37 +875,23 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
         int cnt[kNumClass];
 #pragma unroll
         for (int c = 0; c < kNumClass; ++c) cnt[c] = st.d_cnt[c];
-        bool alive = true;
-        // block tasks: partial sums of chunked rows (with their candidates when every chunk task
-        // is the first task of its block), then block-per-row rows
-        const bool fused = ntask <= (int)gridDim.x;
-        const int nblk = ntask + cnt[kClassBlockRow];
-        for (int bt = blockIdx.x; bt < nblk; bt += gridDim.x) {
-            if (bt < ntask) {
-                if (fused) {
-                    alive = do_chunk_fused(st, A, P, ph, __ldcg(tasks + bt)) && alive;
-                } else {
-                    do_chunk_partial(st, A, P, ph, __ldcg(tasks + bt));
-                }
-            } else {
-                do_block_row(st, A, P, ph, __ldcg(rows + P.class_off[kClassBlockRow] + (bt - ntask)));
-            }
-        }
-        // warp tasks: fix-ups of the previous round's changes, thread-per-row bins, warp rows
+        // phase A, warp tasks: pieces of piece rows (partials), fix-ups of the previous round's
+        // changes, thread-per-row bins, warp rows
         const int s_fix = (nprev + 31) / 32;
         int s_bin[kNumThreadBins];
-        int total = s_fix + cnt[kClassWarpRow];
+        int total = ntask + s_fix + cnt[kClassWarpRow];
 #pragma unroll
         for (int c = 0; c < kNumThreadBins; ++c) {
             s_bin[c] = (cnt[c] + 31) / 32;
             total += s_bin[c];
         }
-        // warp tasks are numbered from the first block without a block task, so that a short
-        // round's few warp tasks do not queue behind a block task
-        const int w0 = (min(nblk, (int)gridDim.x) * kWarpsPerBlock) % NW;
-        const int gw_r = gw >= w0 ? gw - w0 : gw - w0 + NW;
         for (int task = gw_r; task < total; task += NW) {
             int tl = task;
+            if (tl < ntask) {
+                do_piece_partial(st, A, P, ph, tl, __ldcg(tasks + tl));
+                continue;
+            }
+            tl -= ntask;
             if (tl < s_fix) {
                 do_fix(st, A, P, ph, chg_prev, nprev, tl);
                 continue;
@@ -1052,10 +912,11 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
             if (done) continue;
             do_warp_row(st, A, P, ph, __ldcg(rows + P.class_off[kClassWarpRow] + tl));
         }
-        __syncthreads();
-        // block tasks that wait: candidates of chunked rows
-        for (int bt = blockIdx.x; !fused && bt < ntask && alive; bt += gridDim.x)
-            alive = do_chunk_candidates(st, A, P, ph, __ldcg(tasks + bt));
+        // phase B: every piece's row total and candidates, once all partials are written
+        if (ntask > 0) {
+            grid_sync(st, ctl);
+            for (int task = gw_r; task < ntask; task += NW) do_piece_candidates(st, A, P, ph, task, __ldcg(tasks + task));
+        }
         // changes of this block: dedupe grid-wide, list them, queue their rows
         drain_changed(st, A, P, ph);
         // staged appends to the global lists; nonzeros of this phase: one atomic per block
@@ -1142,10 +1003,6 @@ int engine_prepare(mip_problem* p) {
     BP_TRY(dalloc(p, &w.task[1], (size_t)p->chunk_cap));
     BP_TRY(dalloc(p, &w.hpart, (size_t)p->chunk_cap));
     BP_TRY(dalloc(p, &w.hpinf, (size_t)p->chunk_cap));
-    BP_TRY(dalloc(p, &w.htot, (size_t)dp.nheavy));
-    BP_TRY(dalloc(p, &w.htinf, (size_t)dp.nheavy));
-    BP_TRY(dalloc(p, &w.harr, (size_t)dp.nheavy));
-    BP_TRY(dalloc(p, &w.hready, (size_t)dp.nheavy));
     BP_TRY(dalloc(p, &w.ctl, 1));
     BP_TRY(ensure_instances(p, 1));
     BP_TRY(dalloc(p, &w.stage_lb, (size_t)n));
@@ -1172,6 +1029,9 @@ int engine_prepare(mip_problem* p) {
     p->sms = sms;
     p->occ_max = occ > 4 ? 4 : occ;
     p->grid_blocks = sms * p->occ_max;
+    // the no-allocation entry point's static scratch is reserved here, with the handle's other
+    // memory, never by that entry point's first call
+    BP_TRY(noalloc_prepare(p->device));
     return BP_OK;
 }
 
@@ -1200,10 +1060,6 @@ int launch_propagate(mip_problem* p, double* lb, double* ub, const int* w0, int 
     a.task[1] = w.task[1];
     a.hpart = w.hpart;
     a.hpinf = w.hpinf;
-    a.htot = w.htot;
-    a.htinf = w.htinf;
-    a.harr = w.harr;
-    a.hready = w.hready;
     a.ctl = w.ctl;
     a.dres = w.dres;
     a.w0 = w0;

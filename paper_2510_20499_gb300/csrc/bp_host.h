@@ -30,7 +30,7 @@ constexpr int kPhaseSlots = 3;
 struct alignas(128) Ctl {
     Pad<unsigned> bar_count;                  // grid barrier arrivals, monotonic within a launch
     Pad<int> cnt[kPhaseSlots][kNumClass];     // worklist rows of a round, per class
-    Pad<int> ntask[kPhaseSlots];              // chunk tasks of a round
+    Pad<int> ntask[kPhaseSlots];              // pieces of a round
     Pad<int> nchg[kPhaseSlots];               // variables changed in a round
     Pad<unsigned long long> nnz[kPhaseSlots]; // nonzeros processed in a round
     Pad<unsigned> done;
@@ -55,13 +55,9 @@ struct Work {
     int* rstamp = nullptr;                     // m: last round stamp a row was queued
     int* list[2] = {nullptr, nullptr};         // m each: worklist rows by class segment
     int* chg[2] = {nullptr, nullptr};          // n each: changed variables
-    int2* task[2] = {nullptr, nullptr};        // chunk tasks {row, chunk}
-    double* hpart = nullptr;                   // partial activity per chunk slot
-    int2* hpinf = nullptr;                     // {ninf, infj} per chunk slot
-    double* htot = nullptr;                    // per chunked row: total finite activity
-    int2* htinf = nullptr;
-    int* harr = nullptr;                       // per chunked row: arrivals in this round
-    int* hready = nullptr;                     // per chunked row: stamp of a ready total
+    int2* task[2] = {nullptr, nullptr};        // pieces {row, piece} of the piece rows of a round
+    double* hpart = nullptr;                   // partial activity per piece slot
+    int2* hpinf = nullptr;                     // {ninf, infj} per piece slot
     Ctl* ctl = nullptr;
     Ctl* ctl_host = nullptr;                   // pinned constant template
     bp_result* dres = nullptr;                 // device result slots (one per instance)
@@ -103,7 +99,7 @@ struct mip_problem {
     int tune_warp_min = gpubp::kDefaultWarpMin;
     int tune_block_min = gpubp::kWarpMax + 1;
     int sms = 0, occ_max = 0;                  // SMs and resident blocks per SM of bp_kernel
-    int chunk_cap = 0;                         // capacity of chunk-indexed arrays (smallest chunk length)
+    int chunk_cap = 0;                         // capacity of piece-indexed arrays (any piece length)
     void (*free_hooks[4])(mip_problem*) = {nullptr, nullptr, nullptr, nullptr};
 };
 
@@ -134,11 +130,14 @@ int dalloc(mip_problem* p, T** out, size_t count) {
 int scan_exclusive(const int* in, int* out, int n, int* total_dev, cudaStream_t s);
 
 int engine_prepare(mip_problem* p);     // allocates Work
+// resolves the static scratch of bp_propagate_noalloc on device `dev` (current), loading the
+// module that holds it; called when a handle is prepared
+int noalloc_prepare(int dev);
 
-// row classes and class lists (rclass, static_list, class_off, heavy_id) from the row lengths
+// row classes and class lists (rclass, rinfo, static_list, class_off, nlong) from the row lengths
 // and the handle's split points
 int classify_rows(mip_problem* p, cudaStream_t s);
-// chunk plan of the chunked rows at dp.chunk_len (static_tasks, part_off, nchunks)
+// piece plan of the piece rows at dp.chunk_len (static_tasks, npieces)
 int plan_chunks(mip_problem* p, cudaStream_t s);
 
 // normalised bound keys of caller bounds (device arrays of n doubles)

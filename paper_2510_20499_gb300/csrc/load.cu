@@ -1,8 +1,9 @@
 // mip_load_csr: validation and device layouts of a MILP (Sections 1 and 2.1).
 //
 // Everything runs on the GPU: the row checks, the transpose (rows of each variable, needed
-// to queue the rows of a changed variable), the length classes of the rows and the chunk
-// plan of long rows.
+// to queue the rows of a changed variable), the length classes of the rows and the piece
+// plan of long rows (pieces of one warp each).
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -131,10 +132,10 @@ __global__ void k_rows(int m, const int64_t* rp64, const double* g, int* rp, dou
     }
 }
 
-// chunks of each chunked row at chunk length `len_c` (0 for other rows)
-__global__ void k_row_chunks(int m, const int* rp, const unsigned char* rclass, int len_c, int* chunks) {
+// pieces of each piece row at piece length `len_c` (0 for other rows)
+__global__ void k_row_pieces(int m, const int* rp, const unsigned char* rclass, int len_c, int* pieces) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x)
-        chunks[k] = rclass[k] == kClassChunked ? (rp[k + 1] - rp[k] + len_c - 1) / len_c : 0;
+        pieces[k] = rclass[k] == kClassPieces ? (rp[k + 1] - rp[k] + len_c - 1) / len_c : 0;
 }
 
 __global__ void k_reclass(int m, const int* rp, int warp_min, int block_min, int len_c, unsigned char* rclass,
@@ -143,7 +144,7 @@ __global__ void k_reclass(int m, const int* rp, int warp_min, int block_min, int
         const int len = rp[k + 1] - rp[k];
         const int c = row_class_tuned(len, warp_min, block_min);
         rclass[k] = (unsigned char)c;
-        rinfo[k] = c | ((c == kClassChunked ? (len + len_c - 1) / len_c : 0) << 3);
+        rinfo[k] = c | ((c == kClassPieces ? (len + len_c - 1) / len_c : 0) << 3);
     }
 }
 
@@ -152,29 +153,19 @@ __global__ void k_class_flag(int m, const unsigned char* rclass, int c, int* fla
         flag[k] = rclass[k] == c ? 1 : 0;
 }
 
-__global__ void k_class_scatter(int m, const unsigned char* rclass, int c, const int* pos, int base,
-                                int* list, int* heavy_id) {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
-        if (rclass[k] != c) continue;
-        list[base + pos[k]] = k;
-        if (heavy_id && c == kClassChunked) heavy_id[k] = pos[k];
-    }
+__global__ void k_class_scatter(int m, const unsigned char* rclass, int c, const int* pos, int base, int* list) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x)
+        if (rclass[k] == c) list[base + pos[k]] = k;
 }
 
-__global__ void k_heavy_tasks(int m, const unsigned char* rclass, const int* chunks, const int* chunk_pos,
+// every piece {row, piece} of the piece rows, rows ascending, pieces in row order
+__global__ void k_piece_tasks(int m, const unsigned char* rclass, const int* pieces, const int* piece_pos,
                               int2* tasks) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
-        if (rclass[k] != kClassChunked) continue;
-        int base = chunk_pos[k];
-        for (int c = 0; c < chunks[k]; ++c) tasks[base + c] = make_int2(k, c);
+        if (rclass[k] != kClassPieces) continue;
+        const int base = piece_pos[k];
+        for (int c = 0; c < pieces[k]; ++c) tasks[base + c] = make_int2(k, c);
     }
-}
-
-__global__ void k_heavy_part_off(int m, const unsigned char* rclass, const int* heavy_id,
-                                 const int* chunk_pos, int* part_off, int nchunks, int nheavy) {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x)
-        if (rclass[k] == kClassChunked) part_off[heavy_id[k]] = chunk_pos[k];
-    if (blockIdx.x == 0 && threadIdx.x == 0) part_off[nheavy] = nchunks;
 }
 
 __global__ void k_col_count(long long nnz, const int32_t* col, int* cnt) {
@@ -241,8 +232,7 @@ static int upload(mip_problem* p, const T* src, size_t count, int mem_kind, T** 
 }
 
 // Row classes under the handle's split points, and the class-grouped static row list (each
-// class ascending by row).  The chunked rows' ids (heavy_id) are rebuilt with them; they do not
-// depend on the split points.
+// class ascending by row).
 int classify_rows(mip_problem* p, cudaStream_t s) {
     DevProblem& dp = p->dp;
     const int m = p->m;
@@ -250,7 +240,6 @@ int classify_rows(mip_problem* p, cudaStream_t s) {
     if (m) {
         unsigned char* rclass = const_cast<unsigned char*>(dp.rclass);
         int* list = const_cast<int*>(dp.static_list);
-        int* heavy = const_cast<int*>(dp.heavy_id);
         k_reclass<<<grid_for(m), 256, 0, s>>>(m, dp.row_ptr, p->tune_warp_min, p->tune_block_min, dp.chunk_len,
                                               rclass, const_cast<int*>(dp.rinfo));
         BP_CUDA_TRY(cudaGetLastError());
@@ -262,8 +251,7 @@ int classify_rows(mip_problem* p, cudaStream_t s) {
         for (int cl = 0; cl < kNumClass; ++cl) {
             k_class_flag<<<grid_for(m), 256, 0, s>>>(m, rclass, cl, flag);
             BP_TRY(scan_exclusive(flag, pos, m, total, s));
-            k_class_scatter<<<grid_for(m), 256, 0, s>>>(m, rclass, cl, pos, base, list,
-                                                        cl == kClassChunked ? heavy : nullptr);
+            k_class_scatter<<<grid_for(m), 256, 0, s>>>(m, rclass, cl, pos, base, list);
             BP_CUDA_TRY(cudaMemcpyAsync(&counts[cl], total, sizeof(int), cudaMemcpyDeviceToHost, s));
             BP_CUDA_TRY(cudaStreamSynchronize(s));
             base += counts[cl];
@@ -276,59 +264,50 @@ int classify_rows(mip_problem* p, cudaStream_t s) {
         base += counts[cl];
     }
     dp.class_off[kNumClass] = base;
-    dp.nheavy = counts[kClassChunked];
+    dp.nlong = counts[kClassPieces];
     return BP_OK;
 }
 
-// Chunk plan of the chunked rows at the handle's chunk length: every chunk task {row, chunk}
-// (static_tasks, the round-0 task list) and each row's first partial-sum slot (part_off).  The
-// first call sizes the task and slot arrays for the smallest chunk length, so that later plans
-// (bp_set_tuning) fit: ceil(len / kChunkMin) <= (kChunk / kChunkMin) ceil(len / kChunk).
+// Piece plan of the piece rows at the handle's piece length: every piece {row, piece}
+// (static_tasks, the round-0 piece list).  The first call sizes the piece lists for the
+// shortest piece length and any split point, so that later plans (bp_set_tuning) fit: a row of
+// len nonzeros has at most len / kPieceMin + 1 pieces, so nnz / kPieceMin + m bound them all.
 int plan_chunks(mip_problem* p, cudaStream_t s) {
     DevProblem& dp = p->dp;
     const int m = p->m;
-    int *chunks = nullptr, *pos = nullptr, *total = nullptr;
-    const size_t words = (size_t)m + 1;
-    BP_CUDA_TRY(cudaMallocAsync(&chunks, sizeof(int) * words, s));
-    BP_CUDA_TRY(cudaMallocAsync(&pos, sizeof(int) * words, s));
-    BP_CUDA_TRY(cudaMallocAsync(&total, sizeof(int), s));
-    auto count = [&](int len_c, int* out) -> int {
-        *out = 0;
-        if (!m) return BP_OK;
-        k_row_chunks<<<grid_for(m), 256, 0, s>>>(m, dp.row_ptr, dp.rclass, len_c, chunks);
-        BP_CUDA_TRY(cudaGetLastError());
-        BP_TRY(scan_exclusive(chunks, pos, m, total, s));
-        BP_CUDA_TRY(cudaMemcpyAsync(out, total, sizeof(int), cudaMemcpyDeviceToHost, s));
-        BP_CUDA_TRY(cudaStreamSynchronize(s));
-        return BP_OK;
-    };
     int rc = BP_OK;
     if (p->chunk_cap == 0) {
-        int n_max = 0;
-        rc = count(kChunk, &n_max);
-        if (rc == BP_OK) {
-            p->chunk_cap = (kChunk / kChunkMin) * n_max;
-            int2* tasks = nullptr;
-            int* part_off = nullptr;
-            rc = dalloc(p, &tasks, (size_t)p->chunk_cap);
-            if (rc == BP_OK) rc = dalloc(p, &part_off, (size_t)dp.nheavy + 1);
-            dp.static_tasks = tasks;
-            dp.part_off = part_off;
+        const long long cap = (long long)dp.nnz / kPieceMin + (long long)m + 1;
+        if (cap > INT_MAX) {
+            set_error("piece lists of %lld entries exceed 32-bit indices", cap);
+            return BP_ERR_CAPACITY;
         }
+        p->chunk_cap = (int)cap;
+        int2* tasks = nullptr;
+        BP_TRY(dalloc(p, &tasks, (size_t)p->chunk_cap));
+        dp.static_tasks = tasks;
     }
-    int nchunks = 0;
-    if (rc == BP_OK) rc = count(dp.chunk_len, &nchunks);
+    dp.npieces = 0;
+    if (!m) return BP_OK;
+    int *pieces = nullptr, *pos = nullptr, *total = nullptr;
+    const size_t words = (size_t)m + 1;
+    BP_CUDA_TRY(cudaMallocAsync(&pieces, sizeof(int) * words, s));
+    BP_CUDA_TRY(cudaMallocAsync(&pos, sizeof(int) * words, s));
+    BP_CUDA_TRY(cudaMallocAsync(&total, sizeof(int), s));
+    k_row_pieces<<<grid_for(m), 256, 0, s>>>(m, dp.row_ptr, dp.rclass, dp.chunk_len, pieces);
+    if (cudaGetLastError() != cudaSuccess) rc = BP_ERR_CUDA;
+    if (rc == BP_OK) rc = scan_exclusive(pieces, pos, m, total, s);
+    int np = 0;
+    if (rc == BP_OK && cudaMemcpyAsync(&np, total, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = BP_ERR_CUDA;
+    if (rc == BP_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = BP_ERR_CUDA;
     if (rc == BP_OK) {
-        dp.nchunks = nchunks;
-        if (m) {
-            k_heavy_tasks<<<grid_for(m), 256, 0, s>>>(m, dp.rclass, chunks, pos, const_cast<int2*>(dp.static_tasks));
-            k_heavy_part_off<<<grid_for(m), 256, 0, s>>>(m, dp.rclass, dp.heavy_id, pos, const_cast<int*>(dp.part_off),
-                                                         nchunks, dp.nheavy);
-            if (cudaGetLastError() != cudaSuccess) rc = BP_ERR_CUDA;
-        }
+        dp.npieces = np;
+        k_piece_tasks<<<grid_for(m), 256, 0, s>>>(m, dp.rclass, pieces, pos, const_cast<int2*>(dp.static_tasks));
+        if (cudaGetLastError() != cudaSuccess) rc = BP_ERR_CUDA;
     }
-    for (void* q : {(void*)chunks, (void*)pos, (void*)total}) cudaFreeAsync(q, s);
+    for (void* q : {(void*)pieces, (void*)pos, (void*)total}) cudaFreeAsync(q, s);
     BP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (rc == BP_ERR_CUDA) set_error("piece plan: CUDA error");
     return rc;
 }
 
@@ -415,15 +394,13 @@ static int load_impl(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t
     dp.m = m;
     dp.n = n;
     dp.nnz = (int)nnz;
-    int *d_rp, *d_list, *d_heavy;
+    int *d_rp, *d_list;
     double2* d_grow;
     unsigned char* d_rclass;
     BP_TRY(dalloc(p, &d_rp, (size_t)m + 1));
     BP_TRY(dalloc(p, &d_grow, (size_t)m));
     BP_TRY(dalloc(p, &d_rclass, (size_t)m));
     BP_TRY(dalloc(p, &d_list, (size_t)m));
-    BP_TRY(dalloc(p, &d_heavy, (size_t)m));
-    BP_CUDA_TRY(cudaMemsetAsync(d_heavy, 0xff, sizeof(int) * (m ? m : 1), s));
     k_rows<<<grid_for(m + 1), 256, 0, s>>>(m, d_rp64, d_g, d_rp, d_grow);
     BP_CUDA_TRY(cudaGetLastError());
     int* d_rinfo;
@@ -431,11 +408,10 @@ static int load_impl(int32_t m, int32_t n, const int64_t* row_ptr, const int32_t
     dp.row_ptr = d_rp;
     dp.rclass = d_rclass;
     dp.rinfo = d_rinfo;
-    dp.heavy_id = d_heavy;
     dp.static_list = d_list;
     dp.chunk_len = kDefaultChunkLen;
     BP_TRY(classify_rows(p, s));
-    // chunk plan
+    // piece plan
     BP_TRY(plan_chunks(p, s));
     // transpose
     int *d_colcnt, *d_colptr, *d_fill, *d_rowidx;

@@ -23,8 +23,10 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 unsigned char* g_scratch_ptr[kMaxDevices] = {};   // device address of the array, per device
 
-// Once per device, with that device current: the device address of the scratch array.  On
-// the first call this may load the module that holds the array.
+// Once per device, with that device current: the device address of the scratch array.  The
+// first lookup loads the module that holds the array (CUDA loads modules lazily), which reserves
+// the array's memory on the device; handle creation makes that first lookup (noalloc_prepare), so
+// that bp_propagate_noalloc itself never causes it.
 int scratch_base(int dev, unsigned char** out) {
     std::lock_guard<std::mutex> lock(g_setup_mu);
     if (!g_scratch_ptr[dev]) {
@@ -52,17 +54,15 @@ struct Carve {
 };
 
 // Lays out the scratch of one single-instance propagation.  The buffers that must start at
-// zero come first, so that one memset clears them: the stamp word, the control block, the
-// row and variable stamps and the ready stamps of chunked rows.  Returns the bytes of that
-// prefix; c.off is the total.
+// zero come first, so that one memset clears them: the stamp word, the control block and the
+// row and variable stamps.  Returns the bytes of that prefix; c.off is the total.
 size_t layout(const mip_problem* p, Carve& c, Work& w) {
     const size_t n = (size_t)p->n, m = (size_t)p->m;
-    const size_t nchunks = (size_t)p->dp.nchunks, nheavy = (size_t)p->dp.nheavy;
+    const size_t npieces = (size_t)p->dp.npieces;   // a round holds at most every piece once
     w.stamp = c.take<int>(1);
     w.ctl = c.take<Ctl>(1);
     w.vstamp = c.take<int>(n);
     w.rstamp = c.take<int>(m);
-    w.hready = c.take<int>(nheavy);
     const size_t zero_bytes = c.off;
     w.bkey[0] = c.take<longlong2>(n);
     w.bkey[1] = c.take<longlong2>(n);
@@ -70,13 +70,10 @@ size_t layout(const mip_problem* p, Carve& c, Work& w) {
     w.list[1] = c.take<int>(m);
     w.chg[0] = c.take<int>(n);
     w.chg[1] = c.take<int>(n);
-    w.task[0] = c.take<int2>(nchunks);
-    w.task[1] = c.take<int2>(nchunks);
-    w.hpart = c.take<double>(nchunks);
-    w.hpinf = c.take<int2>(nchunks);
-    w.htot = c.take<double>(nheavy);
-    w.htinf = c.take<int2>(nheavy);
-    w.harr = c.take<int>(nheavy);
+    w.task[0] = c.take<int2>(npieces);
+    w.task[1] = c.take<int2>(npieces);
+    w.hpart = c.take<double>(npieces);
+    w.hpinf = c.take<int2>(npieces);
     w.dres = c.take<bp_result>(1);
     w.inst = c.take<InstState>(1);
     w.i_nnz = c.take<unsigned long long>(kPhaseSlots);
@@ -88,6 +85,13 @@ size_t layout(const mip_problem* p, Carve& c, Work& w) {
 }
 
 }  // namespace
+
+int noalloc_prepare(int dev) {
+    if (dev < 0 || dev >= kMaxDevices) return BP_OK;   // the entry point rejects such devices itself
+    unsigned char* base = nullptr;
+    return scratch_base(dev, &base);
+}
+
 }  // namespace gpubp
 
 using namespace gpubp;

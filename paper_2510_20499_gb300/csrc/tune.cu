@@ -17,7 +17,7 @@ using namespace gpubp;
 
 namespace {
 
-bool chunk_len_valid(int c) { return c == 256 || c == 512 || c == 1024 || c == kChunk; }
+bool chunk_len_valid(int c) { return c == 32 || c == 64 || c == 128 || c == kPieceMax; }
 
 bool tuning_valid(const mip_problem* p, const bp_tuning* t) {
     return t->warp_min >= 2 && t->warp_min <= kThreadMax + 1 && t->block_min >= t->warp_min &&
@@ -32,8 +32,10 @@ int apply(mip_problem* p, const bp_tuning* t, cudaStream_t s) {
     p->tune_block_min = t->block_min;
     p->dp.chunk_len = t->chunk_len;
     p->grid_blocks = p->sms * t->blocks_per_sm;
-    if (reclass) BP_TRY(classify_rows(p, s));   // row classes and chunk counts per row
-    if (rechunk) BP_TRY(plan_chunks(p, s));     // chunk tasks and partial-sum slots
+    if (reclass) {
+        BP_TRY(classify_rows(p, s));   // row classes and piece counts per row
+        BP_TRY(plan_chunks(p, s));     // the round-0 piece list (block_min decides the piece rows)
+    }
     return BP_OK;
 }
 
@@ -69,8 +71,8 @@ extern "C" int bp_set_tuning(mip_problem* p, const bp_tuning* t, void* stream) {
     }
     if (!tuning_valid(p, t)) {
         set_error("bp_set_tuning: need 2 <= warp_min <= %d, warp_min <= block_min <= %d, 1 <= blocks_per_sm <= %d, "
-                  "chunk_len in {256, 512, 1024, %d} (got %d, %d, %d, %d)",
-                  kThreadMax + 1, kWarpMax + 1, p->occ_max, kChunk, t->warp_min, t->block_min, t->blocks_per_sm,
+                  "chunk_len in {32, 64, 128, %d} (got %d, %d, %d, %d)",
+                  kThreadMax + 1, kWarpMax + 1, p->occ_max, kPieceMax, t->warp_min, t->block_min, t->blocks_per_sm,
                   t->chunk_len);
         return BP_ERR_INVALID;
     }
@@ -144,7 +146,7 @@ extern "C" int bp_autotune(mip_problem* p, const double* lb, const double* ub, c
     rep.tried = 1;
     static const int kWarpMins[] = {2, kThreadMax + 1};
     static const int kBlockMins[] = {65, kWarpMax + 1};
-    static const int kChunkLens[] = {256, 512, 1024, kChunk};
+    static const int kChunkLens[] = {64, 128, kPieceMax};
     for (int bps = 1; rc == BP_OK && bps <= p->occ_max; ++bps)
         for (int wm : kWarpMins)
             for (int bm : kBlockMins)

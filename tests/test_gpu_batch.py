@@ -141,6 +141,12 @@ def test_uneven_batch_full_size_autotuned(pkg):
     _compare_instances(parts, ro, co, gl, gu, gres)
     prob.autotune(lb0, ub0, reps=1)
     gl2, gu2, gres2 = run()
+    # the tuned piece length may sum rows in another order: every decision is the same, integer
+    # bounds are identical and continuous bounds agree within the 1e-9 relative tolerance
     assert gres2 == gres
-    np.testing.assert_array_equal(gl2, gl)
-    np.testing.assert_array_equal(gu2, gu)
+    ints = big.is_int == 1
+    np.testing.assert_array_equal(gl2[ints], gl[ints])
+    np.testing.assert_array_equal(gu2[ints], gu[ints])
+    np.testing.assert_allclose(gl2, gl, rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(gu2, gu, rtol=1e-9, atol=1e-9)
+    _compare_instances(parts, ro, co, gl2, gu2, gres2)

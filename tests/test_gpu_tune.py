@@ -19,8 +19,8 @@ def pkg():
     return pkg
 
 
-CONFIGS = [(9, 257, 2, 2048), (2, 2, 2, 2048), (2, 65, 1, 512), (5, 129, 2, 1024), (9, 9, 1, 256),
-           (5, 257, 1, 2048), (2, 257, 2, 256), (9, 65, 2, 512), (2, 257, 1, 1024)]
+CONFIGS = [(9, 257, 2, 256), (2, 2, 2, 256), (2, 65, 1, 64), (5, 129, 2, 128), (9, 9, 1, 32),
+           (5, 257, 1, 256), (2, 257, 2, 32), (9, 65, 2, 64), (2, 257, 1, 128)]
 
 
 def exact_problems():
@@ -35,7 +35,7 @@ def exact_problems():
 def test_defaults(pkg):
     prob = pkg.Problem(synth.binary_knapsack())
     t = prob.get_tuning()
-    assert t["warp_min"] == 2 and t["block_min"] == 257 and t["blocks_per_sm"] >= 1 and t["chunk_len"] == 2048
+    assert t["warp_min"] == 2 and t["block_min"] == 257 and t["blocks_per_sm"] >= 1 and t["chunk_len"] == 256
 
 
 @pytest.mark.parametrize("cfg", CONFIGS, ids=[f"w{c[0]}-b{c[1]}-g{c[2]}-c{c[3]}" for c in CONFIGS])
@@ -55,8 +55,8 @@ def test_every_configuration_matches_oracle(pkg, cfg):
 def test_invalid_tuning_rejected(pkg):
     prob = pkg.Problem(synth.binary_knapsack())
     bps = prob.get_tuning()["blocks_per_sm"]
-    for bad in [(1, 257, 1, 2048), (10, 257, 1, 2048), (9, 8, 1, 2048), (9, 258, 1, 2048), (9, 257, 0, 2048),
-                (9, 257, bps + 1, 2048), (9, 257, 1, 300), (9, 257, 1, 4096), (9, 257, 1, 128)]:
+    for bad in [(1, 257, 1, 256), (10, 257, 1, 256), (9, 8, 1, 256), (9, 258, 1, 256), (9, 257, 0, 256),
+                (9, 257, bps + 1, 256), (9, 257, 1, 300), (9, 257, 1, 512), (9, 257, 1, 2048), (9, 257, 1, 16)]:
         with pytest.raises(pkg.GpuBpError) as e:
             prob.set_tuning(*bad)
         assert e.value.code == pkg.BP_ERR_INVALID

@@ -25,7 +25,7 @@ def pkg():
 def problems():
     return [
         synth.random_milp(31, 2000, 3000, len_lo=1, len_hi=400, inf_fraction=0.05, eq_fraction=0.2),
-        synth.random_milp(32, 60, 6000, len_lo=500, len_hi=5000, integer_coefs=True),   # chunked rows
+        synth.random_milp(32, 60, 6000, len_lo=500, len_hi=5000, integer_coefs=True),   # piece rows
         synth.binary_knapsack(),
     ]
 
@@ -60,6 +60,29 @@ def test_noalloc_matches_propagate_on_consecutive_calls(pkg):
     # the handle's own buffers are untouched by the static-scratch calls
     for q, p, r in zip(probs, ps, ref):
         same(p, r, run(q, p, "propagate"))
+
+
+def test_noalloc_leaves_free_device_memory_unchanged(pkg):
+    """The entry point allocates nothing, not even on its first call for a new handle: the
+    static scratch is reserved when the handle is created, so the device's free memory
+    (cudaMemGetInfo) is the same before and after three calls."""
+    import torch
+    p = synth.random_milp(34, 3000, 4000, len_lo=1, len_hi=600, inf_fraction=0.05, eq_fraction=0.2)
+    q = pkg.Problem(p)
+    l0 = torch.tensor(p.lb, device="cuda")
+    u0 = torch.tensor(p.ub, device="cuda")
+    gl, gu = l0.clone(), u0.clone()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    rs = []
+    for _ in range(3):
+        gl.copy_(l0)
+        gu.copy_(u0)
+        rs.append(q.propagate_noalloc(gl, gu))
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert rs[0] == rs[1] == rs[2] and rs[0]["error"] == 0
+    same(p, run(q, p, "propagate"), (gl.cpu().numpy(), gu.cpu().numpy(), rs[2]))
 
 
 def test_noalloc_full_size_workload(pkg):
