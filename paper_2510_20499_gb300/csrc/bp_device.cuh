@@ -62,6 +62,14 @@ __host__ __device__ inline int row_class_tuned(int len, int warp_min, int block_
     return row_class(len);
 }
 
+// Piece descriptor {row, piece index c, first nonzero of the piece, end of the row}: the piece
+// covers [beg, min(row end, beg + chunk_len)), the row has c + ceil((row end - beg) / chunk_len)
+// pieces, and the row's pieces sit in consecutive slots of the round's piece list, c first-ones
+// before this one, so no row data needs to be loaded to place or size the piece.
+__host__ __device__ inline int4 piece_desc(int k, int c, int rb, int re, int len_c) {
+    return make_int4(k, c, rb + c * len_c, re);
+}
+
 // ------------------------------------------------------------------ ordered keys
 // key(d) = bits(d) for d >= +0, bits(d) ^ 0x7fff...f for negative d; -0.0 maps to +0.0 first
 // so that the two zeros compare equal, as they do in IEEE arithmetic.
@@ -251,7 +259,7 @@ struct DevProblem {
     const unsigned char* rclass; // m
     const int* rinfo;            // m: class | pieces << 3 (pieces of a piece row, else 0)
     const int* static_list;      // m: row ids grouped by class, ascending within a class
-    const int2* static_tasks;    // every piece {row, piece} of the piece rows (round 0)
+    const int4* static_tasks;    // every piece of the piece rows (round 0), see piece_desc
     int class_off[kNumClass + 1];// class segments of static_list and of worklists
     int chunk_len;               // nonzeros per piece of a piece row (kPieceMin .. kPieceMax)
     int nlong, npieces;          // piece rows, their pieces at chunk_len

@@ -56,7 +56,7 @@ struct BpArgs {
     int* rstamp;
     int* list[2];
     int* chg[2];
-    int2* task[2];
+    int4* task[2];
     double* hpart;
     int2* hpinf;
     Ctl* ctl;
@@ -201,6 +201,7 @@ __device__ void warp_append(Stage& st, const BpArgs& A, const DevProblem& P, con
 // rare paths that run outside a converged warp).
 __device__ void lane_queue_row(const BpArgs& A, const DevProblem& P, const Phase& ph, int k) {
     const int info = __ldg(P.rinfo + k);   // issued before the stamp atomic: no dependency
+    const int rb = __ldg(P.row_ptr + k), re = __ldg(P.row_ptr + k + 1);
     if (atomicMax(&A.rstamp[k], ph.st_r) >= ph.st_r) return;
     const int cls = info & 7;
     if (cls != kClassPieces) {
@@ -210,7 +211,7 @@ __device__ void lane_queue_row(const BpArgs& A, const DevProblem& P, const Phase
     }
     const int nch = info >> 3;
     const int base = atomicAdd(&A.ctl->ntask[ph.ns3()].v, nch);
-    for (int c = 0; c < nch; ++c) A.task[ph.npar][base + c] = make_int2(k, c);
+    for (int c = 0; c < nch; ++c) A.task[ph.npar][base + c] = piece_desc(k, c, rb, re, P.chunk_len);
     atomicAdd(&A.ctl->cnt[ph.ns3()][kClassPieces].v, 1);
 }
 
@@ -220,7 +221,9 @@ __device__ void lane_queue_row(const BpArgs& A, const DevProblem& P, const Phase
 __device__ void warp_queue_rows(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, int k) {
     const int lane = threadIdx.x & 31;
     int slot = -1, nch = 0, base = 0;
-    const int info = k >= 0 ? __ldg(P.rinfo + k) : 0;   // issued before the stamp atomic
+    // issued before the stamp atomic (no dependency): class, pieces and the row's extent
+    const int info = k >= 0 ? __ldg(P.rinfo + k) : 0;
+    const int rb = k >= 0 ? __ldg(P.row_ptr + k) : 0, re = k >= 0 ? __ldg(P.row_ptr + k + 1) : 0;
     if (k >= 0 && atomicMax(&A.rstamp[k], ph.st_r) < ph.st_r) {
         const int cls = info & 7;
         if (cls != kClassPieces) {
@@ -237,7 +240,8 @@ __device__ void warp_queue_rows(Stage& st, const BpArgs& A, const DevProblem& P,
         const int kk = __shfl_sync(0xffffffffu, k, src);
         const int nn = __shfl_sync(0xffffffffu, nch, src);
         const int bb = __shfl_sync(0xffffffffu, base, src);
-        for (int c = lane; c < nn; c += 32) A.task[ph.npar][bb + c] = make_int2(kk, c);
+        const int rbb = __shfl_sync(0xffffffffu, rb, src), ree = __shfl_sync(0xffffffffu, re, src);
+        for (int c = lane; c < nn; c += 32) A.task[ph.npar][bb + c] = piece_desc(kk, c, rbb, ree, P.chunk_len);
         longs &= longs - 1;
     }
     warp_append(st, A, P, ph, slot, k);
@@ -382,27 +386,39 @@ __device__ __forceinline__ void load_elems(Elems& E, const DevProblem& P, const 
     for (int i = 0; i < kPerThread; ++i) E.bk[i] = E.j[i] >= 0 ? ld_bounds(ph.R, E.j[i]) : make_longlong2(0, 0);
 }
 
-// Candidates of the thread's nonzeros given the row total (registers only).
-__device__ __forceinline__ void elems_candidates(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph,
-                                                 const Elems& E, const Acc& tot, double g) {
-    if (tot.ninf >= 2) return;
+// Elements of E that may tighten a bound given the row total (bit i for element i): with one
+// infinite term only that term's variable (no prefilter), with none every element the FP32
+// prefilter cannot rule out.
+__device__ __forceinline__ unsigned elems_pass(const Elems& E, const Acc& tot, double g) {
+    unsigned pass = 0;
+    if (tot.ninf >= 2) return 0;
     if (tot.ninf == 1) {
 #pragma unroll
         for (int i = 0; i < kPerThread; ++i)
-            if (E.j[i] >= 0 && E.j[i] == tot.infj)
-                try_candidate(st, A, P, ph, E.a[i], E.j[i], E.bk[i], tot.minfin, 1, g);
-        return;
+            if (E.j[i] >= 0 && E.j[i] == tot.infj) pass |= 1u << i;
+        return pass;
     }
     const RowFilter f = row_filter(g, tot.minfin);
-    unsigned pass = 0;
 #pragma unroll
     for (int i = 0; i < kPerThread; ++i)
         if (E.j[i] >= 0 && !cannot_tighten(f, E.a[i], E.bk[i].x, E.bk[i].y)) pass |= 1u << i;
-    if (pass) {
+    return pass;
+}
+
+// Exact evaluation and application of the elements of E whose bit is set in `pass`, with the
+// lane's row data (finite activity, one-infinite-term flag, g).
+__device__ __forceinline__ void eval_pass(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph,
+                                          const Elems& E, unsigned pass, double minfin, bool inf1, double g) {
+    if (!pass) return;
 #pragma unroll
-        for (int i = 0; i < kPerThread; ++i)
-            if (pass & (1u << i)) try_candidate(st, A, P, ph, E.a[i], E.j[i], E.bk[i], tot.minfin, 0, g);
-    }
+    for (int i = 0; i < kPerThread; ++i)
+        if (pass & (1u << i)) try_candidate(st, A, P, ph, E.a[i], E.j[i], E.bk[i], minfin, inf1 ? 1 : 0, g);
+}
+
+// The candidates of the thread's elements given the row total.
+__device__ __forceinline__ void elems_candidates(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph,
+                                                 const Elems& E, const Acc& tot, double g) {
+    eval_pass(st, A, P, ph, E, elems_pass(E, tot, g), tot.minfin, tot.ninf == 1, g);
 }
 
 // ------------------------------------------------------------------- row kernels
@@ -447,17 +463,25 @@ __device__ void do_warp_row(Stage& st, const BpArgs& A, const DevProblem& P, con
     }
 }
 
-// Piece u = {row k, piece c} of a piece row, phase A: the partial activity of its nonzeros
-// [row start + c chunk_len, + chunk_len) into slot u.
-__device__ void do_piece_partial(const Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, int u,
-                                 int2 tk) {
+// Bounds of a piece's nonzeros kept in registers from phase A to phase B: the gather is the
+// dependent half of loading a piece, so phase B then only reissues the independent column and
+// coefficient loads, together with the loads of the row's partials.
+struct HeldBounds {
+    longlong2 bk[kPerThread];
+};
+
+// Piece u of a piece row (descriptor tk, see piece_desc), phase A: the partial activity of its
+// nonzeros into slot u; H (if given) keeps their bounds.
+__device__ __forceinline__ void piece_partial(const BpArgs& A, const DevProblem& P, const Phase& ph, int u, int4 tk,
+                                              HeldBounds* H) {
     const int lane = threadIdx.x & 31;
-    const int k = tk.x, c = tk.y;
-    if (!st.alive[row_inst(st, A, k)]) return;
-    const int rb = __ldg(P.row_ptr + k), re = __ldg(P.row_ptr + k + 1);
-    const int beg = rb + c * P.chunk_len, end = min(re, beg + P.chunk_len);
+    const int beg = tk.z, end = min(tk.w, beg + P.chunk_len);
     Elems E;
     const Acc s = warp_reduce(load_accumulate(E, P, ph, beg, end, lane, 32));
+    if (H) {
+#pragma unroll
+        for (int i = 0; i < kPerThread; ++i) H->bk[i] = E.bk[i];
+    }
     if (lane == 0) {
         A.hpart[u] = s.minfin;
         A.hpinf[u] = make_int2(s.ninf, s.infj);
@@ -465,18 +489,28 @@ __device__ void do_piece_partial(const Stage& st, const BpArgs& A, const DevProb
 }
 
 // Piece u, phase B: the row total is the sum of the row's piece partials in slot order (the
-// pieces of a row sit in consecutive slots, piece c in slot u - c + c); every piece of the row
-// computes it in the same order and gets the same value.  The first piece records the row's
-// verdict and its nonzeros; each piece then reloads its own nonzeros and bounds (L2) and
-// evaluates their candidates.
-__device__ void do_piece_candidates(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, int u,
-                                    int2 tk) {
+// row's pieces sit in the consecutive slots u - c ..); every piece of the row computes it in the
+// same order and gets the same value.  The first piece records the row's verdict and its
+// nonzeros; each piece then evaluates its own nonzeros' candidates, with the bounds kept in H
+// since phase A when given, else reloaded (L2).
+__device__ __forceinline__ void piece_candidates(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph,
+                                                 int u, int4 tk, const HeldBounds* H) {
     const int lane = threadIdx.x & 31;
-    const int k = tk.x, c = tk.y;
+    const int k = tk.x, c = tk.y, beg = tk.z, re = tk.w;
+    const int end = min(re, beg + P.chunk_len);
     const int ki = row_inst(st, A, k);
-    if (!st.alive[ki]) return;
-    const int rb = __ldg(P.row_ptr + k), re = __ldg(P.row_ptr + k + 1);
-    const int npc = __ldg(P.rinfo + k) >> 3;
+    const int npc = c + (re - beg + P.chunk_len - 1) / P.chunk_len;
+    Elems E;
+    if (H) {
+        // issued with the partials' loads below (independent)
+#pragma unroll
+        for (int i = 0; i < kPerThread; ++i) {
+            const int q = beg + lane + i * 32;
+            E.j[i] = q < end ? __ldg(P.col + q) : -1;
+            E.a[i] = q < end ? __ldg(P.val + q) : 0.0;
+            E.bk[i] = H->bk[i];
+        }
+    }
     const double2 g2 = __ldg(P.grow + k);
     const int first = u - c;
     Acc t{0.0, 0, -1};
@@ -489,15 +523,36 @@ __device__ void do_piece_candidates(Stage& st, const BpArgs& A, const DevProblem
     t = warp_reduce(t);
     const bool infeasible = row_infeasible(t.minfin, t.ninf, g2.y);
     if (c == 0 && lane == 0) {
-        atomicAdd(&st.nnz, (unsigned long long)(re - rb));
-        atomicAdd(&st.i_nnz[ki], (unsigned long long)(re - rb));
+        atomicAdd(&st.nnz, (unsigned long long)(re - beg));
+        atomicAdd(&st.i_nnz[ki], (unsigned long long)(re - beg));
         if (infeasible) atomicMin(&A.i_rowinf[ph.s3() * A.ninst + ki], k);
     }
     if (infeasible || t.ninf >= 2) return;
-    const int beg = rb + c * P.chunk_len, end = min(re, beg + P.chunk_len);
-    Elems E;
-    load_elems(E, P, ph, beg, end, lane, 32);
+    if (!H) load_elems(E, P, ph, beg, end, lane, 32);
     elems_candidates(st, A, P, ph, E, t, g2.x);
+}
+
+__device__ void do_fix(const Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, const int* chg_prev,
+                       int nprev, int tl);
+
+// Warp task tl of phase A after the pieces: [fix-ups][thread-per-row bins][warp rows].
+__device__ __forceinline__ void warp_task(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph, int tl,
+                                          const int* rows, const int* cnt, const int* s_bin, int s_fix,
+                                          const int* chg_prev, int nprev) {
+    if (tl < s_fix) {
+        do_fix(st, A, P, ph, chg_prev, nprev, tl);
+        return;
+    }
+    tl -= s_fix;
+#pragma unroll
+    for (int c = 0; c < kNumThreadBins; ++c) {
+        if (tl < s_bin[c]) {
+            do_thread_rows(st, A, P, ph, rows + P.class_off[c], cnt[c], tl);
+            return;
+        }
+        tl -= s_bin[c];
+    }
+    do_warp_row(st, A, P, ph, __ldcg(rows + P.class_off[kClassWarpRow] + tl));
 }
 
 // Variables changed in the previous round: bring their new bounds into this round's
@@ -868,7 +923,7 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
         ph.st_r = base + t + 1;
         const bool stat = (t == 0 && !A.w0 && !A.w0v);
         const int* rows = stat ? P.static_list : A.list[ph.par];
-        const int2* tasks = stat ? P.static_tasks : A.task[ph.par];
+        const int4* tasks = stat ? P.static_tasks : A.task[ph.par];
         const int ntask = st.d_ntask;
         const int nprev = st.d_nprev;
         const int* chg_prev = A.chg[ph.npar];
@@ -885,37 +940,41 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
             s_bin[c] = (cnt[c] + 31) / 32;
             total += s_bin[c];
         }
-        for (int task = gw_r; task < total; task += NW) {
-            int tl = task;
-            if (tl < ntask) {
-                do_piece_partial(st, A, P, ph, tl, __ldcg(tasks + tl));
-                continue;
+        // with at most one task per warp (short rounds), a piece's warp keeps its nonzeros and
+        // bounds in registers from phase A to phase B
+        const bool single = total <= NW;
+        HeldBounds H1;
+        int4 tk1 = make_int4(0, 0, 0, 0);
+        bool piece1 = false;
+        if (single) {
+            if (gw_r < ntask) {
+                tk1 = __ldcg(tasks + gw_r);
+                piece1 = st.alive[row_inst(st, A, tk1.x)] != 0;
+                if (piece1) piece_partial(A, P, ph, gw_r, tk1, &H1);
+            } else if (gw_r < total) {
+                warp_task(st, A, P, ph, gw_r - ntask, rows, cnt, s_bin, s_fix, chg_prev, nprev);
             }
-            tl -= ntask;
-            if (tl < s_fix) {
-                do_fix(st, A, P, ph, chg_prev, nprev, tl);
-                continue;
-            }
-            tl -= s_fix;
-            bool done = false;
-#pragma unroll
-            for (int c = 0; c < kNumThreadBins; ++c) {
-                if (!done) {
-                    if (tl < s_bin[c]) {
-                        do_thread_rows(st, A, P, ph, rows + P.class_off[c], cnt[c], tl);
-                        done = true;
-                    } else {
-                        tl -= s_bin[c];
-                    }
+        } else {
+            for (int task = gw_r; task < total; task += NW) {
+                if (task < ntask) {
+                    const int4 tk = __ldcg(tasks + task);
+                    if (st.alive[row_inst(st, A, tk.x)]) piece_partial(A, P, ph, task, tk, nullptr);
+                } else {
+                    warp_task(st, A, P, ph, task - ntask, rows, cnt, s_bin, s_fix, chg_prev, nprev);
                 }
             }
-            if (done) continue;
-            do_warp_row(st, A, P, ph, __ldcg(rows + P.class_off[kClassWarpRow] + tl));
         }
         // phase B: every piece's row total and candidates, once all partials are written
         if (ntask > 0) {
             grid_sync(st, ctl);
-            for (int task = gw_r; task < ntask; task += NW) do_piece_candidates(st, A, P, ph, task, __ldcg(tasks + task));
+            if (single) {
+                if (piece1) piece_candidates(st, A, P, ph, gw_r, tk1, &H1);
+            } else {
+                for (int task = gw_r; task < ntask; task += NW) {
+                    const int4 tk = __ldcg(tasks + task);
+                    if (st.alive[row_inst(st, A, tk.x)]) piece_candidates(st, A, P, ph, task, tk, nullptr);
+                }
+            }
         }
         // changes of this block: dedupe grid-wide, list them, queue their rows
         drain_changed(st, A, P, ph);
@@ -990,7 +1049,6 @@ static int ensure_instances(mip_problem* p, int ninst) {
 int engine_prepare(mip_problem* p) {
     Work& w = p->w;
     const int m = p->m, n = p->n;
-    const DevProblem& dp = p->dp;
     BP_TRY(dalloc(p, &w.bkey[0], (size_t)n));
     BP_TRY(dalloc(p, &w.bkey[1], (size_t)n));
     BP_TRY(dalloc(p, &w.vstamp, (size_t)n));

@@ -55,7 +55,7 @@ struct Work {
     int* rstamp = nullptr;                     // m: last round stamp a row was queued
     int* list[2] = {nullptr, nullptr};         // m each: worklist rows by class segment
     int* chg[2] = {nullptr, nullptr};          // n each: changed variables
-    int2* task[2] = {nullptr, nullptr};        // pieces {row, piece} of the piece rows of a round
+    int4* task[2] = {nullptr, nullptr};        // pieces of the piece rows of a round (piece_desc)
     double* hpart = nullptr;                   // partial activity per piece slot
     int2* hpinf = nullptr;                     // {ninf, infj} per piece slot
     Ctl* ctl = nullptr;

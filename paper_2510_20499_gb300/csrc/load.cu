@@ -159,12 +159,12 @@ __global__ void k_class_scatter(int m, const unsigned char* rclass, int c, const
 }
 
 // every piece {row, piece} of the piece rows, rows ascending, pieces in row order
-__global__ void k_piece_tasks(int m, const unsigned char* rclass, const int* pieces, const int* piece_pos,
-                              int2* tasks) {
+__global__ void k_piece_tasks(int m, const int* rp, const unsigned char* rclass, const int* pieces,
+                              const int* piece_pos, int len_c, int4* tasks) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
         if (rclass[k] != kClassPieces) continue;
         const int base = piece_pos[k];
-        for (int c = 0; c < pieces[k]; ++c) tasks[base + c] = make_int2(k, c);
+        for (int c = 0; c < pieces[k]; ++c) tasks[base + c] = piece_desc(k, c, rp[k], rp[k + 1], len_c);
     }
 }
 
@@ -283,7 +283,7 @@ int plan_chunks(mip_problem* p, cudaStream_t s) {
             return BP_ERR_CAPACITY;
         }
         p->chunk_cap = (int)cap;
-        int2* tasks = nullptr;
+        int4* tasks = nullptr;
         BP_TRY(dalloc(p, &tasks, (size_t)p->chunk_cap));
         dp.static_tasks = tasks;
     }
@@ -302,7 +302,8 @@ int plan_chunks(mip_problem* p, cudaStream_t s) {
     if (rc == BP_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = BP_ERR_CUDA;
     if (rc == BP_OK) {
         dp.npieces = np;
-        k_piece_tasks<<<grid_for(m), 256, 0, s>>>(m, dp.rclass, pieces, pos, const_cast<int2*>(dp.static_tasks));
+        k_piece_tasks<<<grid_for(m), 256, 0, s>>>(m, dp.row_ptr, dp.rclass, pieces, pos, dp.chunk_len,
+                                                  const_cast<int4*>(dp.static_tasks));
         if (cudaGetLastError() != cudaSuccess) rc = BP_ERR_CUDA;
     }
     for (void* q : {(void*)pieces, (void*)pos, (void*)total}) cudaFreeAsync(q, s);

@@ -70,8 +70,8 @@ size_t layout(const mip_problem* p, Carve& c, Work& w) {
     w.list[1] = c.take<int>(m);
     w.chg[0] = c.take<int>(n);
     w.chg[1] = c.take<int>(n);
-    w.task[0] = c.take<int2>(npieces);
-    w.task[1] = c.take<int2>(npieces);
+    w.task[0] = c.take<int4>(npieces);
+    w.task[1] = c.take<int4>(npieces);
     w.hpart = c.take<double>(npieces);
     w.hpinf = c.take<int2>(npieces);
     w.dres = c.take<bp_result>(1);
