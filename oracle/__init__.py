@@ -112,6 +112,8 @@ def _bind_fp(L):
     L.orc_fix_and_propagate.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                         C.POINTER(C.c_double), C.POINTER(Cache), C.POINTER(FpParams),
                                         C.POINTER(C.c_double), C.POINTER(FpResult)]
+    L.orc_implied_slack.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double)]
     L.orc_uniform.restype = C.c_double
     L.orc_uniform.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64]
     L.orc_splitmix64.restype = C.c_uint64
@@ -256,6 +258,18 @@ def _fix_and_propagate(self, x, lb, ub, seed=1, bulk_rule=0, fraction=0.01, last
 
 
 Problem.fix_and_propagate = _fix_and_propagate
+
+
+def _implied_slack(self, lb, ub):
+    """Implied slack S_i of every variable under bounds (lb, ub) (Section 2.3)."""
+    lb = np.ascontiguousarray(lb, dtype=np.float64)
+    ub = np.ascontiguousarray(ub, dtype=np.float64)
+    S = np.zeros(self.n)
+    lib().orc_implied_slack(self.h, _p(lb, C.c_double), _p(ub, C.c_double), _p(S, C.c_double))
+    return S
+
+
+Problem.implied_slack = _implied_slack
 
 
 def probe_split(is_int, l, u):

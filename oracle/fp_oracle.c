@@ -185,6 +185,12 @@ static void implied_slack(const orc_problem *p, const double *l, const double *u
     }
 }
 
+/* exported for the pins of the implied-slack equation (Section 2.3) */
+void orc_implied_slack(const orc_problem *p, const double *l, const double *u, double *S)
+{
+    implied_slack(p, l, u, S);
+}
+
 /* cache branch of (j, value): entry index 2*pair + b, or -1 */
 static int64_t cache_branch(const orc_cache *c, const int32_t *pair_of, int32_t j, double val)
 {

@@ -140,3 +140,17 @@ def test_hooks_fraction_rule(pkg, seed):
     x = rng.uniform(0, 20, p.n)
     _check(p, x, seed=seed, bulk_rule=1, fraction=0.01, order_score=rng.standard_normal(p.n),
            up_prob=rng.uniform(0, 1, p.n))
+
+
+def test_implied_slack_order_golden(pkg):
+    """The hand-worked implied-slack case (Section 2.3, Algorithm 1) on the GPU: the same first
+    bulk and result as the fixture."""
+    c = load_golden("fp_slack_order.json")
+    p = synth.Milp(c["m"], c["n"], np.array(c["row_ptr"], dtype=np.int64), np.array(c["col"], dtype=np.int32),
+                   np.array(c["val"], float), np.array(c["g"], float), np.array(c["lb"], float),
+                   np.array(c["ub"], float), np.array(c["is_int"], dtype=np.uint8), np.zeros(c["n"]))
+    for seed in (1, 2):
+        gx, gr = _gpu_fp(pkg, p, np.array(c["x"], float), seed=seed, last_single=c["last_single"])
+        np.testing.assert_array_equal(gx, c["x_out"])
+        assert (gr["status"], gr["bulks"], gr["bp_runs"], gr["recoveries"]) == \
+            (c["status"], c["bulks"], c["bp_runs"], c["recoveries"])

@@ -190,3 +190,50 @@ def test_recovery_one_variable_at_a_time():
         assert r["status"] == 0
         assert list(xo) == [1.0, 0.0]
         assert (r["bulks"], r["bp_runs"], r["recoveries"], r["fixed_by_choice"], r["nnz_updates"]) == (2, 5, 1, 1, 12)
+
+
+def _golden_slack_case():
+    c = load_golden("fp_slack_order.json")
+    p = synth.Milp(c["m"], c["n"], np.array(c["row_ptr"], dtype=np.int64), np.array(c["col"], dtype=np.int32),
+                   np.array(c["val"], float), np.array(c["g"], float), np.array(c["lb"], float),
+                   np.array(c["ub"], float), np.array(c["is_int"], dtype=np.uint8), np.zeros(c["n"]))
+    return c, p
+
+
+def test_implied_slack_values():
+    """Implied slack of the hand-worked case (Section 2.3): squares of a / slack summed over the
+    variable's rows, the slack floored at the tolerance (the 2^-21 row)."""
+    c, p = _golden_slack_case()
+    S = oracle.Problem(p).implied_slack(p.lb, p.ub)
+    np.testing.assert_allclose(S, c["S"], rtol=1e-12, atol=0)
+
+
+def test_implied_slack_special_rows():
+    """Rows whose minimal activity has an infinite term, and free rows (g = +inf), add nothing;
+    a row violated within the tolerance has its slack raised to the tolerance; a negative
+    coefficient takes the upper bound in L_min and adds its square.  Variables x (integer [0, 1]),
+    y (continuous, lower bound -inf), z (integer [0, 1]), w (integer [0, 4]):
+      x + y <= 3            L_min has the infinite term of y: skipped
+      x + z <= inf          free row: skipped
+      x <= -5e-7            L_min = 0, slack -5e-7 -> 1e-6: x gets (1 / 1e-6)^2 = 1e12
+      -2 z + w <= 1         L_min = -2, slack 3: z gets (-2/3)^2 = 4/9, w gets 1/9
+    """
+    inf = np.inf
+    A = np.array([[1.0, 1.0, 0, 0], [1.0, 0, 1.0, 0], [1.0, 0, 0, 0], [0, 0, -2.0, 1.0]])
+    p = milp_from_dense(A, [3.0, inf, -5e-7, 1.0], np.array([0.0, -inf, 0.0, 0.0]),
+                        np.array([1.0, 10.0, 1.0, 4.0]), np.array([1, 0, 1, 1]))
+    S = oracle.Problem(p).implied_slack(p.lb, p.ub)
+    np.testing.assert_allclose(S, [1e12, 0.0, 4.0 / 9.0, 1.0 / 9.0], rtol=1e-12, atol=0)
+
+
+def test_implied_slack_order_golden():
+    """The asymmetric hand-worked case: decreasing implied slack puts {B, A} in the first bulk
+    and C is propagated to 0.  Increasing order, |a / slack| instead of its square, or an
+    unfloored slack each change the first bulk and the result (see the fixture's note)."""
+    c, p = _golden_slack_case()
+    for seed in (1, 2, 3):
+        x, r = oracle.Problem(p).fix_and_propagate(np.array(c["x"], float), p.lb, p.ub, seed=seed,
+                                                   last_single=c["last_single"])
+        np.testing.assert_array_equal(x, c["x_out"])
+        assert (r["status"], r["bulks"], r["bp_runs"], r["recoveries"], r["fixed_by_choice"]) == \
+            (c["status"], c["bulks"], c["bp_runs"], c["recoveries"], c["fixed_by_choice"])
