@@ -372,14 +372,17 @@ typedef struct {
 /* Result of fix_and_propagate.  bulks: iterations (bulk and single); bp_runs: propagations
  * (the start one and every candidate vector with at least one kept fixing); recoveries: bulks
  * that failed both ways and were retried one variable at a time; fixed_by_choice: kept
- * fixings of the chosen vectors; nnz_updates: summed over all propagations. */
+ * fixings of the chosen vectors; refuted: 1 when every integer variable was fixed but the final
+ * check (a propagation of the caller's bounds with the integer variables fixed) was infeasible,
+ * so the status is FP_INFEASIBLE; nnz_updates: summed over the rounding's propagations (bp_runs;
+ * the final check is not counted). */
 typedef struct {
     int32_t status;
     int32_t bulks;
     int32_t bp_runs;
     int32_t recoveries;
     int32_t fixed_by_choice;
-    int32_t reserved;
+    int32_t refuted;
     int64_t nnz_updates;
 } fp_result;
 
@@ -397,6 +400,10 @@ void fp_params_default(fp_params *p);   /* seed 1, sqrt rule, last_single 36, fr
  * changes, and the first feasible result kept.  A bulk failing both ways is retried one
  * variable at a time; a single variable failing both ways ends the search and the remaining
  * integer variables are rounded to the nearest value inside their bounds (FP_INFEASIBLE).
+ * Once every integer variable is fixed, one more propagation starts from the caller's bounds
+ * with the integer variables at their values: under the continuous-bound threshold (Section
+ * 2.1) the incremental propagations can stop short of a contradiction that this one reaches,
+ * and then the result is FP_INFEASIBLE with refuted = 1.
  *
  * x:        DEVICE double[n], the point to round (e.g. an LP relaxation solution).
  * lb, ub:   DEVICE double[n] start bounds (not modified).

@@ -94,11 +94,11 @@ class FpParams(C.Structure):
 
 class FpResult(C.Structure):
     _fields_ = [("status", C.c_int32), ("bulks", C.c_int32), ("bp_runs", C.c_int32), ("recoveries", C.c_int32),
-                ("fixed_by_choice", C.c_int32), ("pad", C.c_int32), ("nnz_updates", C.c_int64),
+                ("fixed_by_choice", C.c_int32), ("refuted", C.c_int32), ("nnz_updates", C.c_int64),
                 ("fragile", C.c_int64)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class Cache(C.Structure):

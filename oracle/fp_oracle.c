@@ -29,11 +29,26 @@
  *       variable that fails both ways ends the search (repair disabled, Section 3): the
  *       remaining integer variables are rounded to the nearest value inside their bounds
  *       without propagation and the result is INFEASIBLE.
- *  4. FEASIBLE when every integer variable is fixed and the last propagation was feasible.
+ *  4. FEASIBLE when every integer variable is fixed, the last propagation was feasible, and a
+ *     propagation of the start bounds with every integer variable fixed at its value is not
+ *     infeasible either (`refuted` otherwise: under the threshold of Section 2.1 an incremental
+ *     propagation can stop short of a contradiction that one from the start bounds reaches).
  *
  * The random draws use splitmix64 (Steele, Lea, Flood, "Fast splittable pseudorandom number
  * generators", OOPSLA 2014) chained over (seed, bulk, variable, draw); the 53 high bits give a
  * uniform double in [0, 1).
+ *
+ * Fragile decisions (result field `fragile`): the propagations' own (bp_oracle.c), and the bulk
+ * boundary of each implied-slack sort.  S_i depends on each row's minimal activity, whose sum
+ * another implementation may round differently (any order, fused multiply-add) and whose
+ * continuous bounds carry the uncertainty the propagations report; both are bounded per row
+ * as in bp_oracle.c (twice the Higham bound plus the upstream uncertainty), and S_i's window
+ * is the exact range of its terms a^2 / max(slack, tol)^2 over the slack's window.  A bulk is
+ * fragile when a variable inside it and one outside could exchange places within their
+ * windows (with a probing cache, also two variables inside it, whose order decides which
+ * conflicting fixing is kept).  The draws need no window: their inputs (the fractional value
+ * clamped to exact integer bounds, the generator's integers) are the same on any IEEE
+ * implementation, and so is the comparison u < P(up).
  */
 #include <math.h>
 #include <stdint.h>
@@ -43,6 +58,9 @@
 #include "oracle.h"
 
 #define FP_TOL 1e-6
+#define FP_U 1.1102230246251565e-16 /* 2^-53 */
+
+static double fp_gam(double k) { return k * FP_U / (1.0 - k * FP_U); }
 
 typedef struct {
     uint64_t seed;
@@ -62,7 +80,7 @@ typedef struct {
     int32_t bp_runs;
     int32_t recoveries;
     int32_t fixed_by_choice; /* kept fixings of the chosen candidate vectors, summed over bulks */
-    int32_t pad;
+    int32_t refuted;         /* every integer fixed, but the final check from the start bounds failed */
     int64_t nnz_updates;
     int64_t fragile;
 } orc_fp_result;
@@ -191,6 +209,73 @@ void orc_implied_slack(const orc_problem *p, const double *l, const double *u, d
     implied_slack(p, l, u, S);
 }
 
+/* Window E_i of every S_i (see the header): the range of sum_k a^2 / max(slack_k, tol)^2 when
+ * each slack_k moves by its row's error bound; dl / du: uncertainty of the bounds. */
+static void implied_slack_window(const orc_problem *p, const double *l, const double *u, const double *dl,
+                                 const double *du, double *E)
+{
+    for (int32_t j = 0; j < p->n; ++j) E[j] = 0.0;
+    for (int32_t k = 0; k < p->m; ++k) {
+        if (isinf(p->g[k])) continue;
+        double minfin = 0.0, mag = fabs(p->g[k]), upstream = 0.0;
+        int ninf = 0, exact = p->g[k] == floor(p->g[k]);
+        for (int64_t q = p->row_ptr[k]; q < p->row_ptr[k + 1]; ++q) {
+            const double a = p->val[q];
+            const int32_t j = p->col[q];
+            const double b = a > 0 ? l[j] : u[j];
+            if (isinf(b)) { ninf++; continue; }
+            const double t = a * b;
+            minfin = minfin + t;
+            mag += fabs(t);
+            upstream += fabs(a) * (a > 0 ? dl[j] : du[j]);
+            exact = exact && a == floor(a) && b == floor(b);
+        }
+        if (ninf) continue;
+        /* integer terms and right-hand side below 2^53 and exact bounds: every summation order
+         * gives the same exact activity, so the slack has no window */
+        if (exact && upstream == 0.0 && mag < 9007199254740992.0) continue;
+        const double len = (double)(p->row_ptr[k + 1] - p->row_ptr[k]);
+        const double err = 2.0 * (fp_gam(len + 2.0) * mag + upstream);
+        if (err == 0.0) continue;
+        const double slack = p->g[k] - minfin;
+        const double lo = fmax(slack - err, FP_TOL), hi = fmax(slack + err, FP_TOL);
+        if (lo == hi) continue;   /* the floor holds over the whole window */
+        for (int64_t q = p->row_ptr[k]; q < p->row_ptr[k + 1]; ++q) {
+            const double a = p->val[q];
+            E[p->col[q]] += a * a * (1.0 / (lo * lo) - 1.0 / (hi * hi)) * (1.0 + 8.0 * FP_U);
+        }
+    }
+}
+
+/* Fragile bulk boundary: after the sort of work[0..nun) by decreasing S, can a variable of the
+ * bulk work[0..bsize) and one after it exchange places within their windows [S - E, S + E]?
+ * With `inside`, also two variables of the bulk.  Since the order is decreasing, a pair (a
+ * before b) can exchange iff S_b + E_b >= S_a - E_a with a nonzero window on either side; two
+ * zero windows overlap only in an exact tie, which every IEEE implementation reproduces and the
+ * stable sort keeps in order.  Both tests are linear: against the lowest S - E before b (any
+ * window, when E_b > 0; nonzero windows only, when E_b = 0). */
+static int slack_sort_fragile(const int32_t *work, int64_t nun, int64_t bsize, const double *S, const double *E,
+                              int inside)
+{
+    if (bsize >= nun) return 0;
+    double lo_any = INFINITY, lo_wide = INFINITY;   /* over the bulk: min S - E, and over E > 0 only */
+    for (int64_t i = 0; i < bsize; ++i) {
+        const int32_t a = work[i];
+        if (inside && i > 0) {
+            const double top = S[a] + E[a];
+            if ((E[a] > 0.0 && top >= lo_any) || top >= lo_wide) return 1;
+        }
+        lo_any = fmin(lo_any, S[a] - E[a]);
+        if (E[a] > 0.0) lo_wide = fmin(lo_wide, S[a] - E[a]);
+    }
+    for (int64_t i = bsize; i < nun; ++i) {
+        const int32_t b = work[i];
+        const double top = S[b] + E[b];
+        if ((E[b] > 0.0 && top >= lo_any) || top >= lo_wide) return 1;
+    }
+    return 0;
+}
+
 /* cache branch of (j, value): entry index 2*pair + b, or -1 */
 static int64_t cache_branch(const orc_cache *c, const int32_t *pair_of, int32_t j, double val)
 {
@@ -224,6 +309,16 @@ int orc_fix_and_propagate(const orc_problem *p, const double *x, const double *l
     int32_t *cls = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
     double *frac = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
     double *S = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+    double *E = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+    /* uncertainty of the current bounds and of each candidate vector's (continuous bounds only;
+     * the propagations report it, fixings and cached values are exact inputs) */
+    double *dl = (double *)calloc((size_t)(n ? n : 1), sizeof(double));
+    double *du = (double *)calloc((size_t)(n ? n : 1), sizeof(double));
+    double *cdl[2], *cdu[2];
+    for (int i = 0; i < 2; ++i) {
+        cdl[i] = (double *)calloc((size_t)(n ? n : 1), sizeof(double));
+        cdu[i] = (double *)calloc((size_t)(n ? n : 1), sizeof(double));
+    }
     double *val[2];
     val[0] = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
     val[1] = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
@@ -238,7 +333,7 @@ int orc_fix_and_propagate(const orc_problem *p, const double *x, const double *l
     memcpy(l, lb0, sizeof(double) * (size_t)n);
     memcpy(u, ub0, sizeof(double) * (size_t)n);
     orc_bp_result r;
-    orc_bp(p, l, u, NULL, NULL, NULL, 0, prm->theta, prm->max_rounds, 0, &r, NULL, NULL);
+    orc_bp(p, l, u, dl, du, NULL, 0, prm->theta, prm->max_rounds, 0, &r, NULL, NULL);
     res->bp_runs++;
     res->nnz_updates += r.nnz_updates;
     res->fragile += r.fragile;
@@ -293,6 +388,8 @@ int orc_fix_and_propagate(const orc_problem *p, const double *x, const double *l
             if (bsize > 1 && !prm->order_score) {
                 implied_slack(p, l, u, S);
                 merge_sort(work, tmp, nun, &ctx, cmp_slack);
+                implied_slack_window(p, l, u, dl, du, E);
+                if (slack_sort_fragile(work, nun, bsize, S, E, cache != NULL)) res->fragile++;
             }
             single = bsize == 1;
         }
@@ -316,6 +413,8 @@ int orc_fix_and_propagate(const orc_problem *p, const double *x, const double *l
         for (int c = 0; c < 2; ++c) {
             memcpy(cl[c], l, sizeof(double) * (size_t)n);
             memcpy(cu[c], u, sizeof(double) * (size_t)n);
+            memcpy(cdl[c], dl, sizeof(double) * (size_t)n);
+            memcpy(cdu[c], du, sizeof(double) * (size_t)n);
             for (int64_t i = 0; i < bsize; ++i) {
                 const int32_t j = bulk[i];
                 const double v = val[c][j];
@@ -335,12 +434,13 @@ int orc_fix_and_propagate(const orc_problem *p, const double *x, const double *l
                 kept[c]++;
                 cl[c][j] = v;
                 cu[c][j] = v;
+                cdl[c][j] = cdu[c][j] = 0.0;
                 if (e >= 0)
                     for (int64_t q = cache->offsets[e]; q < cache->offsets[e + 1]; ++q) {
                         const int32_t w = cache->ent_var[q];
                         if (w == j) continue;
-                        if (cache->ent_l[q] > cl[c][w]) cl[c][w] = cache->ent_l[q];
-                        if (cache->ent_u[q] < cu[c][w]) cu[c][w] = cache->ent_u[q];
+                        if (cache->ent_l[q] > cl[c][w]) { cl[c][w] = cache->ent_l[q]; cdl[c][w] = 0.0; }
+                        if (cache->ent_u[q] < cu[c][w]) { cu[c][w] = cache->ent_u[q]; cdu[c][w] = 0.0; }
                     }
             }
         }
@@ -356,7 +456,7 @@ int orc_fix_and_propagate(const orc_problem *p, const double *x, const double *l
             }
             for (int32_t k = 0; k < p->m; ++k)
                 if (rowmark[k]) w0[nw++] = k;
-            orc_bp(p, cl[c], cu[c], NULL, NULL, w0, nw, prm->theta, prm->max_rounds, 0, &r, NULL, NULL);
+            orc_bp(p, cl[c], cu[c], cdl[c], cdu[c], w0, nw, prm->theta, prm->max_rounds, 0, &r, NULL, NULL);
             res->bp_runs++;
             res->nnz_updates += r.nnz_updates;
             res->fragile += r.fragile;
@@ -369,6 +469,8 @@ int orc_fix_and_propagate(const orc_problem *p, const double *x, const double *l
             res->fixed_by_choice += kept[pick];
             memcpy(l, cl[pick], sizeof(double) * (size_t)n);
             memcpy(u, cu[pick], sizeof(double) * (size_t)n);
+            memcpy(dl, cdl[pick], sizeof(double) * (size_t)n);
+            memcpy(du, cdu[pick], sizeof(double) * (size_t)n);
         } else if (!single) {
             memcpy(recq, bulk, sizeof(int32_t) * (size_t)bsize);
             nrec = bsize;
@@ -393,9 +495,19 @@ int orc_fix_and_propagate(const orc_problem *p, const double *x, const double *l
             x_out[j] = clampd(x[j], l[j], u[j]);
         }
     }
-    res->status = rounding_infeasible ? 1 : 0;
-    for (int i = 0; i < 2; ++i) { free(cl[i]); free(cu[i]); free(val[i]); }
-    free(l); free(u); free(order); free(work); free(tmp); free(cls); free(frac); free(S);
+    /* final check: the start bounds with every integer variable fixed at its value */
+    if (!rounding_infeasible) {
+        memcpy(l, lb0, sizeof(double) * (size_t)n);
+        memcpy(u, ub0, sizeof(double) * (size_t)n);
+        for (int32_t j = 0; j < n; ++j)
+            if (p->is_int[j]) l[j] = u[j] = x_out[j];
+        orc_bp(p, l, u, NULL, NULL, NULL, 0, prm->theta, prm->max_rounds, 0, &r, NULL, NULL);
+        res->fragile += r.fragile;
+        if (r.status == ORC_INFEASIBLE) res->refuted = 1;
+    }
+    res->status = (rounding_infeasible || res->refuted) ? 1 : 0;
+    for (int i = 0; i < 2; ++i) { free(cl[i]); free(cu[i]); free(val[i]); free(cdl[i]); free(cdu[i]); }
+    free(l); free(u); free(order); free(work); free(tmp); free(cls); free(frac); free(S); free(E); free(dl); free(du);
     free(recq); free(w0); free(rowmark); free(pair_of);
     return 0;
 }

@@ -90,6 +90,33 @@ def forward(theta, X, quantize=True):
     return Z3, dict(X=X, H1=H1, H2=H2, W1=W1, W2=W2, W3=W3)
 
 
+def _gamma(k, u):
+    return k * u / (1.0 - k * u)
+
+
+def bf16_flip_rows(theta, X, u32=2.0 ** -22):
+    """Rows whose forward pass may round a hidden value to the other neighbouring BF16 value on a
+    device that accumulates in FP32: some pre-activation (X W1q^T + b1, or H1 W2q^T + b2) lies
+    within the accumulation error bound of a BF16 rounding boundary.  The bound holds for any
+    summation order (Higham, Lemma 3.4: |error| <= gamma_k sum |terms|, k = inputs + 1 for the
+    bias), with u32 the unit roundoff assumed per FP32 operation (2^-22: twice round-to-nearest's,
+    since a tensor core's accumulation rounding is not specified); BF16 x BF16 products are exact
+    in FP32.  In the other rows both sides round every hidden value alike, and the outputs differ
+    only by FP32 accumulation error.  Returns a bool array over rows."""
+    q = bf16
+    P = unpack(theta)
+    W1, W2 = q(P["W1"]), q(P["W2"])
+    X = np.asarray(X, dtype=np.float64)
+    pre1 = X @ W1.T + P["b1"]
+    w1 = _gamma(IN + 1, u32) * (np.abs(X) @ np.abs(W1).T + np.abs(P["b1"]))
+    flip = (q(np.maximum(pre1 - w1, 0.0)) != q(np.maximum(pre1 + w1, 0.0))).any(axis=1)
+    H1 = q(np.maximum(pre1, 0.0))
+    pre2 = H1 @ W2.T + P["b2"]
+    w2 = _gamma(HID + 1, u32) * (np.abs(H1) @ np.abs(W2).T + np.abs(P["b2"]))
+    flip |= (q(np.maximum(pre2 - w2, 0.0)) != q(np.maximum(pre2 + w2, 0.0))).any(axis=1)
+    return flip
+
+
 def sigmoid(z):
     return 1.0 / (1.0 + np.exp(-z))
 

@@ -329,6 +329,15 @@ __global__ void k_fill_int(int n, int* a, int v) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) a[j] = v;
 }
 
+// start bounds of the final check: the caller's bounds with the integer variables at x_out
+__global__ void k_fix_ints(int n, const unsigned char* is_int, const double* lb, const double* ub, const double* xo,
+                           double* l, double* u) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        l[j] = is_int[j] ? xo[j] : lb[j];
+        u[j] = is_int[j] ? xo[j] : ub[j];
+    }
+}
+
 __global__ void k_finalize(int n, const unsigned char* is_int, const double* x, const double* l, const double* u,
                            int rounding_infeasible, double* x_out) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
@@ -658,7 +667,21 @@ extern "C" int fix_and_propagate(mip_problem* p, const double* x, const double* 
     }
     k_finalize<<<gridn(n), 256, 0, s>>>(n, p->dp.is_int, x, Bl, Bu, rounding_infeasible ? 1 : 0, x_out);
     FP_CUDA(cudaGetLastError());
-    result->status = rounding_infeasible ? FP_INFEASIBLE : FP_FEASIBLE;
+    // final check: one propagation of the caller's bounds with every integer variable fixed at
+    // its value (in a slot of the pair that does not hold the current bounds)
+    if (!rounding_infeasible) {
+        const int fs = (cur + 2) % 4;
+        double* fl = L4 + (size_t)fs * n;
+        double* fu = U4 + (size_t)fs * n;
+        k_fix_ints<<<gridn(n), 256, 0, s>>>(n, p->dp.is_int, lb, ub, x_out, fl, fu);
+        FP_CUDA(cudaGetLastError());
+        FP_TRY(launch_propagate(p, fl, fu, nullptr, 0, prm.theta, prm.max_rounds, nullptr, s));
+        FP_CUDA(cudaMemcpyAsync(&hctl->res[0], p->w.dres, sizeof(bp_result), cudaMemcpyDeviceToHost, s));
+        FP_CUDA(cudaStreamSynchronize(s));
+        if (hctl->res[0].error) return fail(BP_ERR_TIMEOUT);
+        result->refuted = hctl->res[0].status == BP_INFEASIBLE ? 1 : 0;
+    }
+    result->status = (rounding_infeasible || result->refuted) ? FP_INFEASIBLE : FP_FEASIBLE;
     release();
     FP_CUDA(cudaStreamSynchronize(s));
     cudaFreeHost(hctl);

@@ -44,3 +44,28 @@ def compare(p, gl, gu, gr, ol, ou, orr, exact_counts=True):
         assert gr["n_changed"] == orr["n_changed"], (gr["n_changed"], orr["n_changed"])
     assert_bounds_match(p, gl, gu, ol, ou)
     return True
+
+
+def verified_feasible(p, P, xo):
+    """The oracle's verdict on a FEASIBLE result: integer values integral, propagation from the
+    original bounds with the integer variables fixed not infeasible, and (with SciPy) a
+    continuous completion within 1e-6 of every row (HiGHS on the remaining linear system)."""
+    ints = p.is_int == 1
+    if not (xo[ints] == np.round(xo[ints])).all():
+        return False
+    lo, hi = p.lb.copy(), p.ub.copy()
+    lo[ints] = hi[ints] = xo[ints]
+    _, _, rb, _ = P.bp(lo, hi)
+    if rb["status"] == oracle.INFEASIBLE:
+        return False
+    try:
+        import scipy.sparse as sp
+        from scipy.optimize import linprog
+    except ImportError:
+        return True
+    A = sp.csr_matrix((p.val, p.col, p.row_ptr), shape=(p.m, p.n))
+    cont = np.flatnonzero(~ints)
+    rhs = p.g - A[:, np.flatnonzero(ints)] @ xo[ints] + 1e-6
+    r = linprog(np.zeros(len(cont)), A_ub=A[:, cont], b_ub=rhs, bounds=list(zip(p.lb[cont], p.ub[cont])),
+                method="highs")
+    return r.status == 0

@@ -8,7 +8,7 @@ from tests.helpers import dense, load_golden
 
 pytestmark = pytest.mark.gpu
 
-KEYS = ("status", "bulks", "bp_runs", "recoveries", "fixed_by_choice", "nnz_updates")
+KEYS = ("status", "bulks", "bp_runs", "recoveries", "fixed_by_choice", "refuted", "nnz_updates")
 
 
 @pytest.fixture(scope="module")
@@ -105,18 +105,45 @@ def test_hooks(pkg):
 
 
 def test_general_data_soundness(pkg):
-    """Non-integer coefficients: results may differ from the oracle where summation order
-    decides a tie, but a FEASIBLE result always satisfies every row."""
-    p = synth.random_milp(55, 1500, 2000, len_lo=2, len_hi=30, int_fraction=0.7, slack_scale=0.2)
-    A = dense(p)
-    for seed in range(3):
-        gx, gr = _gpu_fp(pkg, p, np.clip(p.x0 + np.random.default_rng(seed).normal(0, 0.5, p.n), p.lb, p.ub), seed=seed)
-        if gr["status"] == 0:
-            ints = p.is_int == 1
-            assert (gx[ints] == np.round(gx[ints])).all()
-            # continuous variables are only clamped (no LP polish); check the integer part's rows
-            # against the continuous variables' final ranges by the propagated bounds being feasible
-            assert np.isfinite(gx).all()
+    """Non-integer coefficients: every FEASIBLE result is verified row by row by the oracle's
+    side (integer values integral, a propagation from the start bounds with them fixed not
+    infeasible, and a continuous completion found by HiGHS within 1e-6 of every row)."""
+    pytest.importorskip("scipy")
+    from tests.gpu_helpers import verified_feasible
+    feasible = 0
+    for inst in range(3):
+        p = synth.random_milp(55 + inst, 1500, 2000, len_lo=2, len_hi=30, int_fraction=0.7, slack_scale=0.2)
+        P = oracle.Problem(p)
+        for seed in range(3):
+            x = np.clip(p.x0 + np.random.default_rng(seed).normal(0, 0.5, p.n), p.lb, p.ub)
+            gx, gr = _gpu_fp(pkg, p, x, seed=seed)
+            if gr["status"] == 0:
+                feasible += 1
+                assert verified_feasible(p, P, gx), (inst, seed)
+    assert feasible >= 3
+
+
+MIXED = [(55, 0, {}), (56, 1, {}), (57, 2, dict(bulk_rule=1, fraction=0.02, last_single=10)),
+         (58, 0, dict(bulk_rule=1, fraction=0.05)), (59, 1, {})]
+
+
+@pytest.mark.parametrize("inst,seed,kw", MIXED, ids=[f"i{m[0]}-s{m[1]}" for m in MIXED])
+def test_mixed_data_parity(pkg, inst, seed, kw):
+    """Mixed integer/continuous problems with non-integer coefficients (power-of-ten decimals):
+    the oracle reports no fragile decision (propagations and implied-slack bulk boundaries), so
+    the GPU must take every decision the oracle takes: the same status, bulks, propagations,
+    recoveries, kept fixings and work, the same integer values, and continuous values within
+    1e-9 relative."""
+    p = synth.random_milp(inst, 1500, 2000, len_lo=2, len_hi=30, int_fraction=0.7, slack_scale=0.2)
+    x = np.clip(p.x0 + np.random.default_rng(seed).normal(0, 0.5, p.n), p.lb, p.ub)
+    ox, orr = oracle.Problem(p).fix_and_propagate(x, p.lb, p.ub, seed=seed, **kw)
+    assert orr["fragile"] == 0, orr
+    gx, gr = _gpu_fp(pkg, p, x, seed=seed, **kw)
+    for k in KEYS:
+        assert gr[k] == orr[k], (k, gr, orr)
+    ints = p.is_int == 1
+    np.testing.assert_array_equal(gx[ints], ox[ints])
+    np.testing.assert_allclose(gx[~ints], ox[~ints], rtol=1e-9, atol=1e-9)
 
 
 def test_order_score_replaces_implied_slack_order(pkg):
@@ -154,3 +181,14 @@ def test_implied_slack_order_golden(pkg):
         np.testing.assert_array_equal(gx, c["x_out"])
         assert (gr["status"], gr["bulks"], gr["bp_runs"], gr["recoveries"]) == \
             (c["status"], c["bulks"], c["bp_runs"], c["recoveries"])
+
+
+def test_final_check_refutes_an_incremental_verdict(pkg):
+    """The hand-worked case of the oracle's pin: every incremental propagation is feasible, the
+    final check from the caller's bounds is not (refuted, INFEASIBLE), as in the oracle."""
+    from tests.helpers import milp_from_dense
+    A = np.array([[50.0, 0, 1, 0], [0, 0.02, 1, 0], [0, 0, -1, 0], [0, 0, -1, 1], [0, 0, 0, -1]])
+    p = milp_from_dense(A, [100, 50.01, -49.985, -49.985, -0.01], np.zeros(4), np.array([1, 1, 100, 10.0]),
+                        np.array([1, 1, 0, 0]))
+    r = _check(p, np.array([0.8, 0.8, 50.0, 0.02]), seed=1)
+    assert (r["status"], r["refuted"], r["bulks"], r["bp_runs"]) == (1, 1, 2, 5)

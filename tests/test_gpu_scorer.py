@@ -52,7 +52,39 @@ def test_closed_form_network_is_exact(pkg):
     np.testing.assert_array_equal(z[:, 1], X.sum(axis=1) - 0.25)
 
 
+def grid_case(seed, rows):
+    """Parameters and features on dyadic grids small enough that every product and every partial
+    sum of both hidden layers is exact in FP32, in any order: X = k/16 (|k| <= 32), W1 = j/64
+    (|j| <= 8), b1 = i/1024 (|pre-activation| <= 4.25, multiples of 2^-10), W2 = j/64 (|j| <= 16),
+    b2 = i/2^16 (|pre-activation| <= 69, multiples of 2^-16, below 2^7 = 2^23 units).  Both sides
+    then round every hidden value alike, and the outputs differ only by FP32 accumulation error
+    in the last layer."""
+    rng = np.random.default_rng(seed)
+    P = {"W1": rng.integers(-8, 9, (64, 16)) / 64.0, "b1": rng.integers(-256, 257, 64) / 1024.0,
+         "W2": rng.integers(-16, 17, (64, 64)) / 64.0, "b2": rng.integers(-4096, 4097, 64) / 65536.0,
+         "W3": rng.integers(-16, 17, (2, 64)) / 64.0, "b3": rng.standard_normal(2).astype(np.float32).astype(np.float64)}
+    theta = mlp.pack(P).astype(np.float32)
+    assert (theta.astype(np.float64) == mlp.pack(P)).all()
+    X = rng.integers(-32, 33, (rows, 16)) / 16.0
+    return theta, X
+
+
+def test_forward_exact_grid(pkg):
+    """Every row agrees with the oracle to FP32 accuracy (1e-5 relative): on the grid no hidden
+    value can round differently, so no row is exempt."""
+    theta, X = grid_case(23, 3001)
+    s = pkg.Scorer()
+    s.set_params(theta)
+    z = s.forward(bf16_tensor(X)).cpu().numpy().astype(np.float64)
+    zo, _ = mlp.forward(theta.astype(np.float64), X)
+    rel = np.abs(z - zo) / (1.0 + np.abs(zo))
+    assert rel.max() < 1e-5, rel.max()
+
+
 def test_forward_matches_oracle(pkg):
+    """Random features and parameters: every row agrees within 1e-3 relative except rows where the
+    oracle shows that a hidden value may round to the other BF16 neighbour under FP32
+    accumulation (mlp.bf16_flip_rows); their number is reported."""
     rng = np.random.default_rng(21)
     theta = random_theta(21)
     X = mlp.bf16(rng.standard_normal((1537, 16)))
@@ -60,13 +92,12 @@ def test_forward_matches_oracle(pkg):
     s.set_params(theta)
     z = s.forward(bf16_tensor(X)).cpu().numpy().astype(np.float64)
     zo, _ = mlp.forward(theta.astype(np.float64), X)
-    d = np.abs(z - zo)
-    scale = 1.0 + np.abs(zo)
-    # FP32 sums against float64 ones: a hidden value near a BF16 rounding boundary may land on
-    # the other side (one BF16 unit, 2^-8 relative); most rows agree to FP32 accuracy
-    assert np.median(d / scale) < 1e-5, np.median(d / scale)
-    assert np.mean(d / scale < 1e-4) > 0.6
-    assert np.max(d / scale) < 2e-2, np.max(d / scale)
+    rel = (np.abs(z - zo) / (1.0 + np.abs(zo))).max(axis=1)
+    flip = mlp.bf16_flip_rows(theta.astype(np.float64), X)
+    print(f"\nrows that may round a hidden value differently: {int(flip.sum())} of {len(flip)}; "
+          f"largest difference elsewhere {rel[~flip].max() if (~flip).any() else 0.0:.2e}, "
+          f"in those rows {rel[flip].max() if flip.any() else 0.0:.2e}")
+    assert (rel[~flip] <= 1e-3).all(), rel[~flip].max()
 
 
 def test_empty_and_single_row(pkg):

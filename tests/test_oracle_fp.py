@@ -237,3 +237,44 @@ def test_implied_slack_order_golden():
         np.testing.assert_array_equal(x, c["x_out"])
         assert (r["status"], r["bulks"], r["bp_runs"], r["recoveries"], r["fixed_by_choice"]) == \
             (c["status"], c["bulks"], c["bp_runs"], c["recoveries"], c["fixed_by_choice"])
+
+
+@pytest.mark.parametrize("coef,fragile", [(0.1, True), (1.0, False)])
+def test_fragile_counts_implied_slack_ties_at_the_bulk_boundary(coef, fragile):
+    """Integer variables X, A, B (at x = 0.8, so every draw rounds up) and rows
+    2X <= 3, coef A + 2 Y <= 5, coef B + 2 Z <= 5 (Y, Z continuous in [0, 1], never tightened):
+    S_X = 4/9 > S_A = S_B = (coef / 5)^2, and the first bulk of ceil(sqrt(3)) = 2 takes X and A,
+    so the tie A = B sits on the bulk boundary.  With coef = 0.1 the rows' activities are sums
+    another implementation may round differently (their windows are nonzero), so an order that
+    breaks the tie the other way is as valid: the oracle counts the boundary as fragile.  With
+    coef = 1 every term is an integer, every summation order is exact, and the tie is not
+    fragile (the stable order holds everywhere)."""
+    A = np.array([[2.0, 0, 0, 0, 0], [0, coef, 0, 2.0, 0], [0, 0, coef, 0, 2.0]])
+    p = milp_from_dense(A, [3.0, 5.0, 5.0], np.zeros(5), np.ones(5), np.array([1, 1, 1, 0, 0]))
+    x, r = oracle.Problem(p).fix_and_propagate(np.array([0.8, 0.8, 0.8, 0.5, 0.5]), p.lb, p.ub, last_single=0)
+    assert r["bulks"] == 2 and r["status"] == 0
+    assert (r["fragile"] > 0) == fragile, r
+
+
+def test_final_check_refutes_an_incremental_verdict():
+    """Hand-worked (Sections 2.1 and 2.3): binaries x1, x2 at 0.8 (rounded up), continuous
+    y in [0, 100], z in [0, 10], rows 50 x1 + y <= 100, 0.02 x2 + y <= 50.01, -y <= -49.985,
+    z - y <= -49.985, -z <= -0.01.  The start propagation gives y in [49.985, 50.01],
+    z in [0.01, 0.025].  Fixing x1 = 1 proposes y <= 50 and then x2 = 1 proposes y <= 49.99:
+    improvements of 0.01 and 0.02, below the threshold 1e-3 * 50.01, so both are rejected and
+    every propagation of the rounding is feasible.  From the start bounds with x1 = x2 = 1 the
+    same rows move y's upper bound from 100 to 49.99 in one accepted step, then z <= 0.005 < 0.01:
+    row 3 is infeasible in round 2.  No continuous completion exists (z <= y - 49.985 <= 0.005),
+    so the result is INFEASIBLE, marked refuted; x_out keeps the rounded point."""
+    A = np.array([[50.0, 0, 1, 0], [0, 0.02, 1, 0], [0, 0, -1, 0], [0, 0, -1, 1], [0, 0, 0, -1]])
+    p = milp_from_dense(A, [100, 50.01, -49.985, -49.985, -0.01], np.zeros(4), np.array([1, 1, 100, 10.0]),
+                        np.array([1, 1, 0, 0]))
+    P = oracle.Problem(p)
+    out, r = P.fix_and_propagate(np.array([0.8, 0.8, 50.0, 0.02]), p.lb, p.ub, seed=1)
+    assert (r["status"], r["refuted"], r["bulks"], r["bp_runs"], r["fragile"]) == (1, 1, 2, 5, 0)
+    np.testing.assert_array_equal(out, [1.0, 1.0, 50.0, 0.02])
+    # one propagation from the start bounds with x1 = x2 = 1 reaches the contradiction
+    lo, hi = p.lb.copy(), p.ub.copy()
+    lo[:2] = hi[:2] = 1.0
+    _, _, rb, _ = P.bp(lo, hi)
+    assert rb["status"] == oracle.INFEASIBLE and rb["first_infeasible_row"] == 3 and rb["rounds"] == 2

@@ -156,3 +156,18 @@ def test_trajectory_labels_hand_worked():
     assert np.isnan(Y[2, 1])
     np.testing.assert_array_equal(mlp.trajectory_labels(x, runs, [3, 0]), Y[[3, 0]])
     assert np.isnan(mlp.trajectory_labels(x, [], [0, 1])).all()
+
+
+def test_bf16_flip_rows():
+    """A pre-activation on a BF16 rounding boundary is flagged; one on a BF16 value with a small
+    error bound is not.  Row 0: x = (1 + 2^-8, 0, ...) with W1[0, 0] = 1 gives exactly the
+    midpoint between the BF16 neighbours 1 and 1 + 2^-7; row 1: x = (1, 0, ...) gives 1.  All
+    other weights are 0, so every other pre-activation is 0 with a zero error bound."""
+    theta = np.zeros(mlp.NPARAM)
+    P = mlp.unpack(theta)
+    P["W1"][0, 0] = 1.0
+    theta = mlp.pack(P)
+    X = np.zeros((2, mlp.IN))
+    X[0, 0] = 1.0 + 2.0 ** -8
+    X[1, 0] = 1.0
+    np.testing.assert_array_equal(mlp.bf16_flip_rows(theta, X), [True, False])
