@@ -259,11 +259,61 @@ typedef struct {
  * index outside [0, n): the kernel skips such a pair and flags it; the other arrays are then
  * incomplete).  The call synchronises the stream once, at its end: the copy into the cache is
  * launched before the host knows the entry count and checks the capacity on the device, and
- * the count and the index flag are read back together.
+ * the count and the index flag are read back together (it is bp_probe_batch_async followed by
+ * that read).
  */
 int bp_probe_batch(mip_problem *p, const double *root_lb, const double *root_ub, int32_t P,
                    const int32_t *var, const double *boxes, const bp_params *params,
                    probe_cache *cache, void *stream);
+
+/*
+ * bp_probe_batch_async -- bp_probe_batch without any host synchronisation, so that the whole
+ * batch (bound keys, row caps, the persistent probe launch, offsets and the copy into the
+ * cache) can be captured in a CUDA graph and replayed.  Arguments as for bp_probe_batch, plus
+ * status_dev: caller-owned DEVICE int64[2] written by the call's last operation: [0] the
+ * entries the batch needs (the cache holds min(needed, cache->cap) of them; offsets are always
+ * complete), [1] nonzero when a variable index was outside [0, n) (that pair was skipped).  The
+ * caller reads them after the stream work (a graph replay) completes; cache->needed is not set.
+ * The handle's probing scratch grows on the first call for a given pair count and capacity:
+ * make one call of that size before capturing (inside a capture a call that would have to
+ * allocate returns BP_ERR_INVALID).  Returns BP_OK or BP_ERR_INVALID (arguments).
+ */
+int bp_probe_batch_async(mip_problem *p, const double *root_lb, const double *root_ub, int32_t P,
+                         const int32_t *var, const double *boxes, const bp_params *params,
+                         probe_cache *cache, int64_t *status_dev, void *stream);
+
+/* Result of probe_cache_apply.  status: BP_FIXPOINT, or BP_INFEASIBLE when a pair has both
+ * branches infeasible (first_infeasible_pair) or the derived bounds of a variable cross
+ * (first_infeasible_var: integer l > u, continuous l > u + 1e-6); fixed_pairs: pairs with exactly
+ * one infeasible branch; tightened: variables whose bounds changed. */
+typedef struct {
+    int32_t status;
+    int32_t first_infeasible_pair;
+    int32_t first_infeasible_var;
+    int32_t fixed_pairs;
+    int64_t tightened;
+} probe_apply_result;
+
+/*
+ * probe_cache_apply -- bounds valid for every solution, derived from a probing cache
+ * (Section 2.2: the cache serves early infeasibility detection).  The two branch boxes of a
+ * pair cover the probed variable's integer domain (see probe_split), so every feasible point
+ * lies in a feasible branch, inside that branch's implied box (the root bounds where the branch
+ * lists nothing).  For every pair the bounds are intersected with the hull of its feasible
+ * branches' boxes: one infeasible branch fixes the variable to the other branch together with
+ * all of that branch's implied bounds; two feasible branches tighten the variables both list to
+ * (min of the lower bounds, max of the upper bounds); two infeasible branches leave nothing, and
+ * the problem is infeasible.
+ * lb, ub:  DEVICE double[n]: in = the root bounds the cache was computed from, out = the
+ *          intersection (normalised as bp_propagate normalises bounds).  Follow with
+ *          bp_propagate to propagate what was derived.
+ * npairs, cache: the P pairs and the cache arrays of a bp_probe_batch call (status, offsets and
+ *          the entries; rounds and nnz_updates are not read).
+ * result:  HOST pointer, valid at return (the call synchronises the stream).
+ * Returns BP_OK or BP_ERR_INVALID; infeasibility is reported in result->status.
+ */
+int probe_cache_apply(mip_problem *p, double *lb, double *ub, int32_t npairs, const probe_cache *cache,
+                      probe_apply_result *result, void *stream);
 
 /*
  * bp_probe_priority -- probe priority keys (Section 2.2) under bounds lb/ub (device):

@@ -51,6 +51,14 @@ class BpResult(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class ApplyResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("first_infeasible_pair", C.c_int32), ("first_infeasible_var", C.c_int32),
+                ("fixed_pairs", C.c_int32), ("tightened", C.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 def _p(a, t):
     return a.ctypes.data_as(C.POINTER(t))
 
@@ -79,6 +87,9 @@ def lib():
                                       C.POINTER(C.c_int32), C.POINTER(C.c_int64),
                                       C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                                       C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int64]
+        L.orc_probe_cache_apply.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int32,
+                                            C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                            C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(ApplyResult)]
         L.orc_probe_priority.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                          C.POINTER(C.c_int32), C.POINTER(C.c_double),
                                          C.POINTER(C.c_double)]
@@ -212,6 +223,21 @@ class Problem:
                 return dict(status=status, rounds=rounds, nnz_updates=nnzu, offsets=offs,
                             var=ev[:need], l=el[:need], u=eu[:need])
             cap = int(need)
+
+    def probe_cache_apply(self, lb, ub, cache):
+        """Global bounds from a probing cache (dict of probe_batch); returns (lb, ub, result)."""
+        lb = np.array(lb, dtype=np.float64)
+        ub = np.array(ub, dtype=np.float64)
+        st = np.ascontiguousarray(cache["status"], dtype=np.int32)
+        off = np.ascontiguousarray(cache["offsets"], dtype=np.int64)
+        ev = np.ascontiguousarray(cache["var"], dtype=np.int32)
+        el = np.ascontiguousarray(cache["l"], dtype=np.float64)
+        eu = np.ascontiguousarray(cache["u"], dtype=np.float64)
+        r = ApplyResult()
+        lib().orc_probe_cache_apply(self.h, _p(lb, C.c_double), _p(ub, C.c_double), len(st) // 2, _p(st, C.c_int32),
+                                    _p(off, C.c_int64), _p(ev, C.c_int32), _p(el, C.c_double), _p(eu, C.c_double),
+                                    C.byref(r))
+        return lb, ub, r.as_dict()
 
     def probe_priority(self, lb, ub):
         lb = np.ascontiguousarray(lb, dtype=np.float64)

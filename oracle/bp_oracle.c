@@ -430,6 +430,84 @@ int64_t orc_probe_batch(const orc_problem *p, const double *root_l, const double
     return total;
 }
 
+/*
+ * Global bounds from a probing cache (Section 2.2: the cache gives early infeasibility
+ * detection and bounds valid for every solution).  The two branch boxes of a pair cover the
+ * probed variable's whole integer domain, so every feasible point lies in a feasible branch,
+ * inside that branch's implied box (root bounds where the branch lists nothing).  For each
+ * pair the bounds are therefore intersected with the hull of its feasible branches' boxes:
+ *   - one branch infeasible: the variable is fixed to the other branch's box together with all
+ *     of that branch's implied bounds;
+ *   - both feasible: a variable listed by both branches gets (min of the lower bounds, max of the
+ *     upper bounds); a variable listed by only one keeps its bounds;
+ *   - both infeasible: the hull is empty and the problem has no feasible point.
+ * lb/ub: in = the root bounds the cache was computed from (normalised here), out = the
+ * intersection.  Afterwards a variable whose bounds cross (integer l > u, continuous
+ * l > u + tol) also proves infeasibility.  Result: status (ORC_FIXPOINT or ORC_INFEASIBLE), the
+ * first pair with both branches infeasible, the first crossing variable, the pairs with
+ * exactly one infeasible branch, and the variables whose bounds changed.
+ */
+typedef struct {
+    int32_t status;
+    int32_t first_infeasible_pair;
+    int32_t first_infeasible_var;
+    int32_t fixed_pairs;
+    int64_t tightened;
+} orc_apply_result;
+
+void orc_probe_cache_apply(const orc_problem *p, double *lb, double *ub, int32_t npairs, const int32_t *status,
+                           const int64_t *offsets, const int32_t *ent_var, const double *ent_l,
+                           const double *ent_u, orc_apply_result *res)
+{
+    const int32_t n = p->n;
+    memset(res, 0, sizeof(*res));
+    res->first_infeasible_pair = -1;
+    res->first_infeasible_var = -1;
+    orc_normalize(p, lb, ub);
+    double *l0 = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+    double *u0 = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+    memcpy(l0, lb, sizeof(double) * (size_t)n);
+    memcpy(u0, ub, sizeof(double) * (size_t)n);
+    for (int32_t i = 0; i < npairs; ++i) {
+        const int f0 = status[2 * i] != ORC_INFEASIBLE, f1 = status[2 * i + 1] != ORC_INFEASIBLE;
+        if (!f0 && !f1) {
+            if (res->first_infeasible_pair < 0) res->first_infeasible_pair = i;
+            continue;
+        }
+        if (f0 != f1) {
+            const int e = 2 * i + (f0 ? 0 : 1);
+            res->fixed_pairs++;
+            for (int64_t q = offsets[e]; q < offsets[e + 1]; ++q) {
+                const int32_t w = ent_var[q];
+                if (ent_l[q] > lb[w]) lb[w] = ent_l[q];
+                if (ent_u[q] < ub[w]) ub[w] = ent_u[q];
+            }
+            continue;
+        }
+        /* both feasible: the variables listed by both branches (both lists ascend by variable) */
+        int64_t a = offsets[2 * i], b = offsets[2 * i + 1];
+        const int64_t ae = offsets[2 * i + 1], be = offsets[2 * i + 2];
+        while (a < ae && b < be) {
+            if (ent_var[a] < ent_var[b]) { a++; continue; }
+            if (ent_var[b] < ent_var[a]) { b++; continue; }
+            const int32_t w = ent_var[a];
+            const double hl = ent_l[a] < ent_l[b] ? ent_l[a] : ent_l[b];
+            const double hu = ent_u[a] > ent_u[b] ? ent_u[a] : ent_u[b];
+            if (hl > lb[w]) lb[w] = hl;
+            if (hu < ub[w]) ub[w] = hu;
+            a++;
+            b++;
+        }
+    }
+    for (int32_t j = 0; j < n; ++j) {
+        if (lb[j] != l0[j] || ub[j] != u0[j]) res->tightened++;
+        if (res->first_infeasible_var < 0 && crossed(p->is_int[j], lb[j], ub[j])) res->first_infeasible_var = j;
+    }
+    res->status = (res->first_infeasible_pair >= 0 || res->first_infeasible_var >= 0) ? ORC_INFEASIBLE : ORC_FIXPOINT;
+    free(l0);
+    free(u0);
+}
+
 /* ------------------------------------------------------------ priority ---- */
 
 /*

@@ -40,6 +40,14 @@ class ProbeCache(C.Structure):
                 ("ent_u", C.c_void_p), ("cap", C.c_int64), ("needed", C.c_int64)]
 
 
+class ProbeApplyResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("first_infeasible_pair", C.c_int32), ("first_infeasible_var", C.c_int32),
+                ("fixed_pairs", C.c_int32), ("tightened", C.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class FpParams(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("bulk_rule", C.c_int32), ("last_single", C.c_int32),
                 ("fraction", C.c_double), ("theta", C.c_double), ("max_rounds", C.c_int32),
@@ -125,6 +133,10 @@ SIGNATURES = {
     "probe_split": (C.c_int, [C.c_int32, C.c_double, C.c_double, C.POINTER(C.c_double)]),
     "bp_probe_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
                                  C.POINTER(BpParams), C.POINTER(ProbeCache), C.c_void_p]),
+    "bp_probe_batch_async": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                       C.POINTER(BpParams), C.POINTER(ProbeCache), C.c_void_p, C.c_void_p]),
+    "probe_cache_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(ProbeCache),
+                                    C.POINTER(ProbeApplyResult), C.c_void_p]),
     "bp_probe_priority": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.POINTER(C.c_int32), C.c_void_p]),
     "fp_params_default": (None, [C.POINTER(FpParams)]),
@@ -290,6 +302,39 @@ def _probe_batch(prob, root_lb, root_ub, var, boxes, theta=1e-3, max_rounds=1000
 
 
 Problem.probe_batch = _probe_batch
+
+
+def _cache_struct(c, cap=None):
+    return ProbeCache(_ptr(c["status"]).value, _ptr(c["rounds"]).value, _ptr(c["nnz_updates"]).value,
+                      _ptr(c["offsets"]).value, _ptr(c["var"]).value, _ptr(c["l"]).value, _ptr(c["u"]).value,
+                      int(c["var"].numel()) if cap is None else int(cap), 0)
+
+
+def _probe_batch_async(prob, root_lb, root_ub, var, boxes, cache, status_dev, theta=1e-3, max_rounds=10000,
+                       stream=None):
+    """bp_probe_batch_async into a preallocated cache (dict of device tensors as probe_batch
+    returns, entries of its full capacity) and status_dev (int64 device tensor of 2: entries
+    needed, index flag).  Nothing is synchronised: the call can be captured in a CUDA graph once a
+    call of the same size has run."""
+    prm = params(theta, max_rounds)
+    pc = _cache_struct(cache)
+    _check(lib().bp_probe_batch_async(prob.h, _ptr(root_lb), _ptr(root_ub), int(var.numel()), _ptr(var), _ptr(boxes),
+                                      C.byref(prm), C.byref(pc), _ptr(status_dev), _stream(stream)))
+
+
+def _probe_cache_apply(prob, lb, ub, cache, stream=None):
+    """probe_cache_apply: bounds valid for every solution from a probing cache (dict of
+    probe_batch); lb/ub (float64 device, the root bounds) are tightened in place.  Returns the
+    result dict."""
+    P = int(cache["status"].numel()) // 2
+    pc = _cache_struct(cache)
+    r = ProbeApplyResult()
+    _check(lib().probe_cache_apply(prob.h, _ptr(lb), _ptr(ub), P, C.byref(pc), C.byref(r), _stream(stream)))
+    return r.as_dict()
+
+
+Problem.probe_batch_async = _probe_batch_async
+Problem.probe_cache_apply = _probe_cache_apply
 
 
 def _probe_priority(prob, lb, ub, stream=None):

@@ -71,6 +71,8 @@ struct Work {
     double* stage_ub = nullptr;
     int* stamp = nullptr;                      // device: stamp of the next launch's round 0
     int* nvars_dev = nullptr;                  // device word: variable count of bp_propagate_from
+    long long* aux = nullptr;                  // 4 device words: probe_cache_apply's result, the
+                                               // entry total and index check of bp_probe_batch
 };
 
 }  // namespace gpubp

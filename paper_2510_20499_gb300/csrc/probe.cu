@@ -839,19 +839,174 @@ static int probe_prepare(mip_problem* p, int nbranches, long long cap, cudaStrea
     return BP_OK;
 }
 
+// ------------------------------------------------------------------ cache application
+// Global bounds from a probing cache (Section 2.2): each pair's two branch boxes cover the
+// probed variable's integer domain, so every solution lies in a feasible branch's implied box
+// (the root bounds where the branch lists nothing); the bounds are intersected, pair by pair,
+// with the hull of the feasible branches' boxes.  Bounds are ordered keys, so every
+// intersection is an atomicMax / atomicMin and the pairs apply in any order.
+struct ApplyCtl {
+    int first_pair, first_var, fixed_pairs, pad;
+    unsigned long long tightened;
+};
+
+__global__ void k_apply_init(int n, const double* lb, const double* ub, const unsigned char* is_int, longlong2* K,
+                             ApplyCtl* ctl) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        K[j] = normalized_keys(lb[j], ub[j], is_int[j] != 0);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->first_pair = INT_MAX;
+        ctl->first_var = INT_MAX;
+        ctl->fixed_pairs = 0;
+        ctl->tightened = 0;
+    }
+}
+
+// One warp per pair.  Both branches feasible: each entry of branch 0 looks its variable up in
+// branch 1's entries (both ascend by variable) and a variable listed by both gets the hull.
+__global__ void k_apply_pairs(int npairs, const int32_t* status, const int64_t* off, const int32_t* ev,
+                              const double* el, const double* eu, longlong2* K, ApplyCtl* ctl) {
+    const int lane = threadIdx.x & 31;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < npairs; i += (gridDim.x * blockDim.x) >> 5) {
+        const bool f0 = status[2 * i] != BP_INFEASIBLE, f1 = status[2 * i + 1] != BP_INFEASIBLE;
+        if (!f0 && !f1) {
+            if (lane == 0) atomicMin(&ctl->first_pair, i);
+            continue;
+        }
+        if (f0 != f1) {
+            const int e = 2 * i + (f0 ? 0 : 1);
+            if (lane == 0) atomicAdd(&ctl->fixed_pairs, 1);
+            for (long long q = off[e] + lane; q < off[e + 1]; q += 32) {
+                const int w = ev[q];
+                atomicMax(&K[w].x, dkey(el[q]));
+                atomicMin(&K[w].y, dkey(eu[q]));
+            }
+            continue;
+        }
+        const long long b0 = off[2 * i + 1], b1 = off[2 * i + 2];
+        for (long long q = off[2 * i] + lane; q < b0; q += 32) {
+            const int w = ev[q];
+            long long lo = b0, hi = b1;   // first entry of branch 1 with variable >= w
+            while (lo < hi) {
+                const long long mid = (lo + hi) >> 1;
+                if (ev[mid] < w) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo < b1 && ev[lo] == w) {
+                atomicMax(&K[w].x, dkey(fmin(el[q], el[lo])));
+                atomicMin(&K[w].y, dkey(fmax(eu[q], eu[lo])));
+            }
+        }
+    }
+}
+
+__global__ void k_apply_finish(int n, double* lb, double* ub, const unsigned char* is_int, const longlong2* K,
+                               ApplyCtl* ctl) {
+    const int lane = threadIdx.x & 31;
+    for (int jb = blockIdx.x * blockDim.x; jb < n; jb += gridDim.x * blockDim.x) {
+        const int j = jb + threadIdx.x;
+        bool changed = false;
+        if (j < n) {
+            const bool ii = is_int[j] != 0;
+            const longlong2 k = K[j];
+            const longlong2 in = normalized_keys(lb[j], ub[j], ii);
+            changed = k.x != in.x || k.y != in.y;
+            lb[j] = kdec(k.x);
+            ub[j] = kdec(k.y);
+            if (crossed(ii, k.x, k.y)) atomicMin(&ctl->first_var, j);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, changed);
+        if (lane == 0 && m) atomicAdd(&ctl->tightened, (unsigned long long)__popc(m));
+    }
+}
+
+static bool probe_scratch_ready(const mip_problem* p, int nbranches, long long cap) {
+    const ProbeWork* pw = static_cast<const ProbeWork*>(p->probe_work);
+    return pw && nbranches <= pw->cap_branches && cap <= pw->tcap;
+}
+
 }  // namespace gpubp
 
 using namespace gpubp;
 
+extern "C" int probe_cache_apply(mip_problem* p, double* lb, double* ub, int32_t npairs, const probe_cache* cache,
+                                 probe_apply_result* result, void* stream) {
+    if (!p || !result || npairs < 0 || (p->n && (!lb || !ub)) ||
+        (npairs && (!cache || !cache->status || !cache->offsets))) {
+        set_error("probe_cache_apply: null or negative argument");
+        return BP_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    Work& w = p->w;
+    if (!w.aux) BP_TRY(dalloc(p, &w.aux, 4));
+    ApplyCtl* ctl = reinterpret_cast<ApplyCtl*>(w.aux);
+    longlong2* K = w.bkey[1];
+    const int n = p->n;
+    const int gn = (n + 255) / 256 < 1216 ? ((n + 255) / 256 > 0 ? (n + 255) / 256 : 1) : 1216;
+    k_apply_init<<<gn, 256, 0, s>>>(n, lb, ub, p->dp.is_int, K, ctl);
+    BP_CUDA_TRY(cudaGetLastError());
+    if (npairs) {
+        const int gp = (npairs * 32 + 255) / 256 < 1216 ? (npairs * 32 + 255) / 256 : 1216;
+        k_apply_pairs<<<gp, 256, 0, s>>>(npairs, cache->status, cache->offsets, cache->ent_var, cache->ent_l,
+                                         cache->ent_u, K, ctl);
+        BP_CUDA_TRY(cudaGetLastError());
+    }
+    k_apply_finish<<<gn, 256, 0, s>>>(n, lb, ub, p->dp.is_int, K, ctl);
+    BP_CUDA_TRY(cudaGetLastError());
+    ApplyCtl h;
+    BP_CUDA_TRY(cudaMemcpyAsync(&h, ctl, sizeof(h), cudaMemcpyDeviceToHost, s));
+    BP_CUDA_TRY(cudaStreamSynchronize(s));
+    p->last_stream = s;
+    result->first_infeasible_pair = h.first_pair == INT_MAX ? -1 : h.first_pair;
+    result->first_infeasible_var = h.first_var == INT_MAX ? -1 : h.first_var;
+    result->fixed_pairs = h.fixed_pairs;
+    result->tightened = (int64_t)h.tightened;
+    result->status = (h.first_pair != INT_MAX || h.first_var != INT_MAX) ? BP_INFEASIBLE : BP_FIXPOINT;
+    return BP_OK;
+}
+
+extern "C" int bp_probe_batch_async(mip_problem* p, const double* root_lb, const double* root_ub, int32_t npairs,
+                                    const int32_t* var, const double* boxes, const bp_params* params,
+                                    probe_cache* cache, int64_t* status_dev, void* stream);
+
 extern "C" int bp_probe_batch(mip_problem* p, const double* root_lb, const double* root_ub, int32_t npairs,
                               const int32_t* var, const double* boxes, const bp_params* params, probe_cache* cache,
                               void* stream) {
-    if (!p || !cache || npairs < 0 || (npairs && (!var || !boxes)) || (p->n && (!root_lb || !root_ub))) {
+    if (!p || !cache) {
+        set_error("bp_probe_batch: null argument");
+        return BP_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    Work& w = p->w;
+    if (!w.aux) BP_TRY(dalloc(p, &w.aux, 4));
+    int64_t* words_dev = reinterpret_cast<int64_t*>(w.aux) + 2;
+    cache->needed = 0;
+    BP_TRY(bp_probe_batch_async(p, root_lb, root_ub, npairs, var, boxes, params, cache, words_dev, stream));
+    int64_t words[2] = {0, 0};   // entry total and the index check, read together
+    BP_CUDA_TRY(cudaMemcpyAsync(words, words_dev, sizeof(words), cudaMemcpyDeviceToHost, s));
+    BP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (words[1]) {
+        set_error("bp_probe_batch: a variable index is outside [0, n)");
+        return BP_ERR_INVALID;
+    }
+    cache->needed = words[0];
+    if (words[0] > cache->cap) {
+        set_error("probing cache needs %lld entries, capacity %lld", (long long)words[0], (long long)cache->cap);
+        return BP_ERR_CAPACITY;
+    }
+    return BP_OK;
+}
+
+extern "C" int bp_probe_batch_async(mip_problem* p, const double* root_lb, const double* root_ub, int32_t npairs,
+                                    const int32_t* var, const double* boxes, const bp_params* params,
+                                    probe_cache* cache, int64_t* status_dev, void* stream) {
+    if (!p || !cache || !status_dev || npairs < 0 || (npairs && (!var || !boxes)) ||
+        (p->n && (!root_lb || !root_ub))) {
         set_error("bp_probe_batch: null or negative argument");
         return BP_ERR_INVALID;
     }
-    if (npairs && (!cache->status || !cache->rounds || !cache->nnz_updates || !cache->offsets) ||
-        cache->cap < 0 || (cache->cap > 0 && (!cache->ent_var || !cache->ent_l || !cache->ent_u))) {
+    if ((npairs && (!cache->status || !cache->rounds || !cache->nnz_updates || !cache->offsets)) || cache->cap < 0 ||
+        (cache->cap > 0 && (!cache->ent_var || !cache->ent_l || !cache->ent_u))) {
         set_error("bp_probe_batch: cache arrays missing");
         return BP_ERR_INVALID;
     }
@@ -863,14 +1018,21 @@ extern "C" int bp_probe_batch(mip_problem* p, const double* root_lb, const doubl
         return BP_ERR_INVALID;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    cache->needed = 0;
     if (npairs == 0) {
-        int64_t zero = 0;
-        if (cache->offsets) BP_CUDA_TRY(cudaMemcpyAsync(cache->offsets, &zero, sizeof(zero), cudaMemcpyHostToDevice, s));
-        BP_CUDA_TRY(cudaStreamSynchronize(s));
+        BP_CUDA_TRY(cudaMemsetAsync(status_dev, 0, 2 * sizeof(int64_t), s));
+        if (cache->offsets) BP_CUDA_TRY(cudaMemsetAsync(cache->offsets, 0, sizeof(int64_t), s));
         return BP_OK;
     }
-    BP_TRY(probe_prepare(p, 2 * npairs, cache->cap > 0 ? cache->cap : 1, s));
+    const long long cap = cache->cap > 0 ? cache->cap : 1;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    BP_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone && !probe_scratch_ready(p, 2 * npairs, cap)) {
+        set_error("bp_probe_batch_async: the probing scratch for %d pairs and %lld cache entries is not allocated; "
+                  "make one call of this size before capturing",
+                  npairs, cap);
+        return BP_ERR_INVALID;
+    }
+    BP_TRY(probe_prepare(p, 2 * npairs, cap, s));
     ProbeWork* pw = probe_work(p);
     longlong2* root = p->w.bkey[0];
     BP_TRY(root_keys(p, root_lb, root_ub, root, s));
@@ -916,19 +1078,8 @@ extern "C" int bp_probe_batch(mip_problem* p, const double* root_lb, const doubl
         nb, pw->ecount, pw->estart, cache->offsets, pw->ectr, cache->cap, pw->tv, pw->tl, pw->tu, cache->ent_var,
         cache->ent_l, cache->ent_u);
     BP_CUDA_TRY(cudaGetLastError());
-    unsigned long long words[2] = {0, 0};   // entry total and the index check, read together
-    BP_CUDA_TRY(cudaMemcpyAsync(words, pw->ectr, sizeof(words), cudaMemcpyDeviceToHost, s));
-    BP_CUDA_TRY(cudaStreamSynchronize(s));
+    // the entry total and the index check go to the caller's device words: no synchronisation
+    BP_CUDA_TRY(cudaMemcpyAsync(status_dev, pw->ectr, 2 * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
     p->last_stream = s;
-    if (words[1]) {
-        set_error("bp_probe_batch: a variable index is outside [0, n)");
-        return BP_ERR_INVALID;
-    }
-    const unsigned long long total = words[0];
-    cache->needed = (int64_t)total;
-    if ((long long)total > cache->cap) {
-        set_error("probing cache needs %llu entries, capacity %lld", total, (long long)cache->cap);
-        return BP_ERR_CAPACITY;
-    }
     return BP_OK;
 }

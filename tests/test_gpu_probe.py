@@ -129,17 +129,127 @@ def test_probe_round_limit_and_capacity(pkg):
     _compare(p, g, o)
 
 
-def test_probes_full_size(pkg):
-    """The 50k x 100k, 1M-nonzero probing instance: 2,048 pairs chosen by the priority order."""
+@pytest.fixture(scope="module")
+def full_size():
+    """The 50k x 100k, 1M-nonzero probing instance, its root fixpoint, the 2,048 pairs chosen by
+    the priority order and the oracle's cache of them."""
     p = synth.knapsack_cover()
     P = oracle.Problem(p)
     rl, ru, r, _ = P.bp(p.lb, p.ub)
     k1, k2, k3 = P.probe_priority(rl, ru)
     var = oracle.priority_order(k1, k2, k3)[:2048].astype(np.int32)
     boxes = np.array([oracle.probe_split(1, rl[j], ru[j]) for j in var], dtype=np.float64).reshape(-1, 4)
-    o = P.probe_batch(rl, ru, var, boxes)
+    return p, P, rl, ru, var, boxes, P.probe_batch(rl, ru, var, boxes)
+
+
+def test_probes_full_size(pkg, full_size):
+    p, P, rl, ru, var, boxes, o = full_size
     g = _gpu_probe(pkg, p, rl, ru, var, boxes)
     _compare(p, g, o)
+
+
+def test_probe_batch_graph_capture_full_size(pkg, full_size):
+    """bp_probe_batch_async captured in a CUDA graph with the whole batch (bound keys, row caps,
+    the persistent probe launch, offsets, the cache copy, the entry-count and index words) and
+    replayed three times: every replay's cache equals the oracle's."""
+    import torch
+    p, P, rl, ru, var, boxes, o = full_size
+    prob = pkg.Problem(p)
+    d = {k: torch.tensor(a, device="cuda") for k, a in (("rl", rl), ("ru", ru), ("var", var), ("boxes", boxes))}
+    ref = prob.probe_batch(d["rl"], d["ru"], d["var"], d["boxes"])     # sizes the scratch
+    cap = int(ref["var"].numel()) + 256
+    cache = pkg._probe_cache(torch, prob.device, len(var), cap)
+    words = torch.zeros(2, dtype=torch.int64, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        prob.probe_batch_async(d["rl"], d["ru"], d["var"], d["boxes"], cache, words, stream=s)   # warm-up at size
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        prob.probe_batch_async(d["rl"], d["ru"], d["var"], d["boxes"], cache, words)
+    for rep in range(3):
+        for t in cache.values():
+            t.zero_()
+        words.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        needed, bad = (int(x) for x in words.cpu())
+        assert bad == 0 and needed == len(o["var"]), (needed, bad)
+        got = {k: v.cpu().numpy() for k, v in cache.items()}
+        got["var"], got["l"], got["u"] = got["var"][:needed], got["l"][:needed], got["u"][:needed]
+        _compare(p, got, o)
+
+
+def test_probe_cache_apply_full_size(pkg, full_size):
+    """Bounds derived from the GPU's cache of the full-size batch equal those the oracle derives
+    from its own cache (Section 2.2)."""
+    import torch
+    p, P, rl, ru, var, boxes, o = full_size
+    prob = pkg.Problem(p)
+    c = prob.probe_batch(torch.tensor(rl, device="cuda"), torch.tensor(ru, device="cuda"),
+                         torch.tensor(var, device="cuda"), torch.tensor(boxes, device="cuda"))
+    gl, gu = torch.tensor(rl, device="cuda"), torch.tensor(ru, device="cuda")
+    gr = prob.probe_cache_apply(gl, gu, c)
+    ol, ou, orr = P.probe_cache_apply(rl, ru, o)
+    assert gr == orr, (gr, orr)
+    np.testing.assert_array_equal(gl.cpu().numpy(), ol)
+    np.testing.assert_array_equal(gu.cpu().numpy(), ou)
+    print(f"\nprobing cache of {len(var)} pairs: {orr['fixed_pairs']} variables fixed by an infeasible branch, "
+          f"{orr['tightened']} variables tightened, status {orr['status']}")
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_probe_cache_apply_golden(pkg, case):
+    """The hand-worked cases of the oracle's pin (Section 2.2), probed and applied on the GPU."""
+    import torch
+    from tests.helpers import milp_from_dense
+    c = load_golden("probe_apply.json")["cases"][case]
+    p = milp_from_dense(np.array(c["A"], float), c["g"], np.array(c["lb"], float), np.array(c["ub"], float),
+                        np.array(c["is_int"]))
+    prob = pkg.Problem(p)
+    gl, gu = torch.tensor(p.lb, device="cuda"), torch.tensor(p.ub, device="cuda")
+    prob.propagate(gl, gu)
+    rl, ru = gl.cpu().numpy(), gu.cpu().numpy()
+    var = np.array(c["probe"], dtype=np.int32)
+    boxes = np.array([oracle.probe_split(p.is_int[j], rl[j], ru[j]) for j in var], dtype=float).reshape(-1, 4)
+    cache = prob.probe_batch(gl, gu, torch.tensor(var, device="cuda"), torch.tensor(boxes, device="cuda"))
+    r = prob.probe_cache_apply(gl, gu, cache)
+    for k in ("status", "first_infeasible_pair", "first_infeasible_var", "fixed_pairs"):
+        assert r[k] == c[k], (k, r, c["note"])
+    if "out_lb" in c:
+        np.testing.assert_array_equal(gl.cpu().numpy(), c["out_lb"])
+        np.testing.assert_array_equal(gu.cpu().numpy(), c["out_ub"])
+        assert r["tightened"] == c["tightened"]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_probe_cache_apply_random(pkg, seed):
+    """Random mixed problems with integer variables probed: the GPU's derived bounds and result
+    equal the oracle's (caches compared first)."""
+    import torch
+    p = synth.random_milp(700 + seed, 400, 600, len_lo=2, len_hi=20, integer_coefs=True, int_fraction=0.8,
+                          slack_scale=0.05, eq_fraction=0.1)
+    P = oracle.Problem(p)
+    rl, ru, r, _ = P.bp(p.lb, p.ub)
+    if r["status"] == oracle.INFEASIBLE:
+        pytest.skip("root infeasible")
+    var, boxes = _pairs(p, rl, ru, 200, seed)
+    o = P.probe_batch(rl, ru, var, boxes)
+    prob = pkg.Problem(p)
+    c = prob.probe_batch(torch.tensor(rl, device="cuda"), torch.tensor(ru, device="cuda"),
+                         torch.tensor(var, device="cuda"), torch.tensor(boxes, device="cuda"))
+    _compare(p, {k: v.cpu().numpy() for k, v in c.items()}, o)
+    gl, gu = torch.tensor(rl, device="cuda"), torch.tensor(ru, device="cuda")
+    gr = prob.probe_cache_apply(gl, gu, c)
+    ol, ou, orr = P.probe_cache_apply(rl, ru, o)
+    assert gr == orr
+    ints = p.is_int == 1
+    np.testing.assert_array_equal(gl.cpu().numpy()[ints], ol[ints])
+    np.testing.assert_array_equal(gu.cpu().numpy()[ints], ou[ints])
+    np.testing.assert_allclose(gl.cpu().numpy(), ol, rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(gu.cpu().numpy(), ou, rtol=1e-9, atol=1e-9)
 
 
 def _gpu_priority(pkg, p, lb, ub):

@@ -146,3 +146,63 @@ def test_priority_order_on_probing_instance():
     assert len(order) == int(((k1 >= 0)).sum())
     keys = [(-k1[j], -k2[j], k3[j], j) for j in order]
     assert keys == sorted(keys)
+
+
+
+def _apply_case(c):
+    p = milp_from_dense(np.array(c["A"], float), c["g"], np.array(c["lb"], float), np.array(c["ub"], float),
+                        np.array(c["is_int"]))
+    P = oracle.Problem(p)
+    rl, ru, _, _ = P.bp(p.lb, p.ub)
+    var = np.array(c["probe"], dtype=np.int32)
+    boxes = np.array([oracle.probe_split(p.is_int[j], rl[j], ru[j]) for j in var], dtype=float).reshape(-1, 4)
+    return p, P, rl, ru, P.probe_batch(rl, ru, var, boxes)
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_probe_cache_apply_golden(case):
+    """Hand-worked global bounds from the probing cache (Section 2.2): a branch proven
+    infeasible fixes its variable, an implication of both branches holds everywhere, two
+    infeasible branches prove the problem infeasible."""
+    c = load_golden("probe_apply.json")["cases"][case]
+    p, P, rl, ru, cache = _apply_case(c)
+    l, u, r = P.probe_cache_apply(rl, ru, cache)
+    for k in ("status", "first_infeasible_pair", "first_infeasible_var", "fixed_pairs"):
+        assert r[k] == c[k], (k, r, c["note"])
+    if "out_lb" in c:
+        np.testing.assert_array_equal(l, c["out_lb"])
+        np.testing.assert_array_equal(u, c["out_ub"])
+        assert r["tightened"] == c["tightened"]
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_probe_cache_apply_brute_force(seed):
+    """Tiny general-integer problems: every integer point satisfying all rows lies inside the
+    bounds derived from the cache of every probeable variable, and INFEASIBLE is reported only
+    when there is no such point; the derived bounds never loosen the root's."""
+    rng = np.random.default_rng(500 + seed)
+    n, m = int(rng.integers(3, 7)), int(rng.integers(2, 6))
+    A = rng.integers(-4, 5, size=(m, n)).astype(float)
+    A[rng.uniform(size=(m, n)) < 0.3] = 0.0
+    for k in range(m):
+        if not A[k].any():
+            A[k, rng.integers(0, n)] = 1.0
+    ub = rng.integers(1, 4, size=n).astype(float)
+    g = rng.integers(-3, 8, size=m).astype(float)
+    p = milp_from_dense(A, g, np.zeros(n), ub, np.ones(n))
+    P = oracle.Problem(p)
+    rl, ru, r0, _ = P.bp(p.lb, p.ub)
+    if r0["status"] == oracle.INFEASIBLE:
+        return
+    var = np.array([j for j in range(n) if rl[j] < ru[j]], dtype=np.int32)
+    if len(var) == 0:
+        return
+    boxes = np.array([oracle.probe_split(1, rl[j], ru[j]) for j in var], dtype=float).reshape(-1, 4)
+    cache = P.probe_batch(rl, ru, var, boxes)
+    l, u, r = P.probe_cache_apply(rl, ru, cache)
+    assert (l >= rl).all() and (u <= ru).all()
+    pts = feasible_points(p, p.lb, p.ub)
+    if r["status"] == oracle.INFEASIBLE:
+        assert len(pts) == 0
+    else:
+        assert ((pts >= l) & (pts <= u)).all()
