@@ -21,6 +21,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -37,7 +39,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the probing, batch, learned and scorer measurements")
-    ap.add_argument("--extras", default="probing,batch,learned,scorer",
+    ap.add_argument("--extras", default="probing,batch,fp,learned,scorer",
                     help="comma-separated subset of the extra measurements to run")
     return ap.parse_args()
 
@@ -110,7 +112,7 @@ class ClockSampler:
 # DRAM bytes (read + write) of one bp_kernel launch on this workload, from the ncu capture
 # summarised in profiles/bp_kernel_mixed_powerlaw_5M.md; reported only while the kernel's
 # sources are the ones that capture was taken on.
-NCU_TRAFFIC = {"sources_sha256_16": "86daee5486a4bae9", "bytes": 196_688_384}
+NCU_TRAFFIC = {"sources_sha256_16": "cba2857eae9b4b71", "bytes": 217_590_016}
 KERNEL_SOURCES = ["bp_engine.cu", "bp_device.cuh", "bp_host.h"]
 
 
@@ -174,6 +176,92 @@ def run_reference(args):
     }), flush=True)
 
 
+def _milp_arrays(p):
+    return dict(m=p.m, n=p.n, row_ptr=p.row_ptr, col=p.col, val=p.val, g=p.g, lb=p.lb, ub=p.ub, is_int=p.is_int)
+
+
+def _oracle_problem(d):
+    import oracle
+    from paper_2510_20499_gb300 import synth
+    p = synth.Milp(d["m"], d["n"], d["row_ptr"], d["col"], d["val"], d["g"], d["lb"], d["ub"], d["is_int"],
+                   np.zeros(d["n"]))
+    return p, oracle.Problem(p)
+
+
+def _probe_worker(args):
+    """One worker of the all-core probing baseline: the oracle's probe batch on its share of the
+    pairs; returns its own compute time."""
+    d, rl, ru, var, boxes = args
+    _, P = _oracle_problem(d)
+    t0 = time.perf_counter()
+    P.probe_batch(rl, ru, var, boxes)
+    return time.perf_counter() - t0
+
+
+def _bp_worker(args):
+    """One worker of the all-core batch baseline: the oracle's propagation of its instances."""
+    nnz = 0
+    t = 0.0
+    for d in args:
+        p, P = _oracle_problem(d)
+        t0 = time.perf_counter()
+        _, _, r, _ = P.bp(p.lb, p.ub)
+        t += time.perf_counter() - t0
+        nnz += r["nnz_updates"]
+    return t, nnz
+
+
+def all_core_baselines():
+    """The oracle over all host cores for the two workloads of independent units: the 4,096
+    probes of the probing workload (pairs split evenly over the workers) and the 64 instances of
+    the batch (balanced by size).  Workers are spawned processes, each timing only its own
+    compute; the throughput divides all units by the slowest worker's time."""
+    import concurrent.futures
+    import multiprocessing as mp
+    import oracle
+    from paper_2510_20499_gb300 import synth
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    out = {"cores": cores, "kind": "oracle",
+           "cpu": platform_cpu()}
+    p = synth.knapsack_cover()
+    P = oracle.Problem(p)
+    rl, ru, _, _ = P.bp(p.lb, p.ub)
+    k1, k2, k3 = P.probe_priority(rl, ru)
+    var = oracle.priority_order(k1, k2, k3)[:2048].astype(np.int32)
+    boxes = np.array([oracle.probe_split(1, rl[j], ru[j]) for j in var], dtype=np.float64).reshape(-1, 4)
+    d = _milp_arrays(p)
+    chunks = [(d, rl, ru, var[i::cores].copy(), boxes[i::cores].copy()) for i in range(cores)]
+    with concurrent.futures.ProcessPoolExecutor(max_workers=cores, mp_context=ctx) as ex:
+        times = list(ex.map(_probe_worker, chunks))
+    out["probing"] = {"probes_per_s": 2 * len(var) / max(times),
+                      "sample": f"all {len(var)} priority pairs = {2 * len(var)} propagations over {cores} workers"}
+    parts = synth.uneven_batch()
+    order = np.argsort([-q.nnz for q in parts])
+    shares = [[] for _ in range(cores)]
+    for i, k in enumerate(order):                   # snake order: balances the uneven sizes
+        r = i % (2 * cores)
+        shares[r if r < cores else 2 * cores - 1 - r].append(_milp_arrays(parts[k]))
+    with concurrent.futures.ProcessPoolExecutor(max_workers=cores, mp_context=ctx) as ex:
+        res = list(ex.map(_bp_worker, [sh for sh in shares if sh]))
+    out["batch"] = {"nnz_updates_per_s": sum(r[1] for r in res) / max(r[0] for r in res),
+                    "sample": f"all {len(parts)} instances over {cores} workers"}
+    return out
+
+
+def platform_cpu():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                for key in ("model name", "CPU part", "Hardware"):
+                    if line.startswith(key):
+                        return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline(p, budget_s=12.0):
     import oracle
     P = oracle.Problem(p)
@@ -187,6 +275,7 @@ def cpu_baseline(p, budget_s=12.0):
     out = {"value": nnz / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
            "sample": f"{runs} full propagations of the workload ({dt:.1f} s, single thread)"}
     out["probing"] = cpu_probing_baseline()
+    out["all_cores"] = all_core_baselines()
     return out
 
 
@@ -259,7 +348,15 @@ def probing_extra(pkg, torch, dev):
     e1.record()
     torch.cuda.synchronize()
     t_plain = e0.elapsed_time(e1)
+    # algorithmic bytes: 12 B per nonzero processed (column, coefficient) and 20 B per cache entry
+    # written (variable, bounds); the bound gathers of the branches' few variables hit L2
+    entries = int(c["var"].numel())
+    pbytes = 12 * nnz + 20 * entries
+    hbm, _ = peaks()
     return {"workload": "knapsack/cover 50k x 100k, 1M nnz; 2,048 priority pairs = 4,096 propagations",
+            "roofline": {"bound": "hbm", "kernel": "probe_kernel (whole call)", "bytes": pbytes,
+                         "achieved": pbytes / (t_batch / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": pbytes / (t_batch / 1e3) / 1e9 / hbm},
             "probes_per_s": 2 * P / (t_batch / 1e3), "ms_batched": t_batch,
             "probes_per_s_plain": 2 * P / (t_plain / 1e3), "ms_plain": t_plain,
             "speedup_batched_vs_plain": t_plain / t_batch, "nnz_updates": nnz,
@@ -309,7 +406,13 @@ def batch_extra(pkg, torch, dev):
     t_tuned, rs_tuned = graph_ms()
     assert rs_tuned == rs
     nnz = sum(r["nnz_updates"] for r in rs)
+    t_best = min(t_def, t_tuned)
+    bbytes = 12 * nnz + 80 * big.n    # per nonzero processed; bounds in, both buffers, bounds out
+    hbm, _ = peaks()
     return {"workload": f"{len(parts)} uneven instances, {big.nnz} nnz total (one graph-captured launch)",
+            "roofline": {"bound": "hbm", "kernel": "bp_kernel (batch)", "bytes": bbytes,
+                         "achieved": bbytes / (t_best / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": bbytes / (t_best / 1e3) / 1e9 / hbm},
             "nnz_updates_per_s": nnz / (min(t_def, t_tuned) / 1e3), "ms": min(t_def, t_tuned),
             "nnz_updates": nnz, "ms_default": t_def, "ms_autotuned": t_tuned, "autotune": rep,
             "rounds_max": max(r["rounds"] for r in rs),
@@ -394,6 +497,33 @@ def learned_extra(pkg, torch, dev):
                         "seconds_per_run": t_run[arm] / len(rs)}
         out[f"test_{nnz // 1000}k_nnz"] = rep
     return out
+
+
+def fp_extra(pkg, torch, dev):
+    """Plain fix-and-propagate (the paper's order, 1% bulks) on the 1M-nonzero rounding instance:
+    seconds per run, bulks per second, and the bytes the bulks must move (12 B per nonzero the
+    candidate propagations process, plus per bulk the two candidate vectors' bounds, filled from
+    the current ones: 2 x 32 B per variable)."""
+    from paper_2510_20499_gb300 import synth
+    p, x = synth.rounding_instance(2000, 1_000_000)
+    prob = pkg.Problem(p)
+    xd, lb, ub = (torch.tensor(a, device=dev) for a in (x, p.lb, p.ub))
+    kw = dict(bulk_rule=1, fraction=0.01, seed=1)
+    prob.fix_and_propagate(xd, lb, ub, **kw)          # warm-up (loads the instance pair)
+    runs = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, r = prob.fix_and_propagate(xd, lb, ub, **kw)
+        runs.append((time.perf_counter() - t0, r))
+    t, r = sorted(runs, key=lambda q: q[0])[1]
+    fbytes = 12 * r["nnz_updates"] + r["bulks"] * 64 * p.n
+    hbm, _ = peaks()
+    return {"workload": f"rounding instance 2000 ({p.m} x {p.n}, {p.nnz} nnz), 1% bulks, seed 1",
+            "seconds_per_run": t, "bulks": r["bulks"], "bulks_per_s": r["bulks"] / t,
+            "us_per_bulk": 1e6 * t / r["bulks"], "status": r["status"], "nnz_updates": r["nnz_updates"],
+            "roofline": {"bound": "hbm", "kernel": "fix_and_propagate (whole run)", "bytes": fbytes,
+                         "achieved": fbytes / t / 1e9, "peak": hbm, "unit": "GB/s", "frac": fbytes / t / 1e9 / hbm}}
 
 
 def scorer_extra(pkg, torch, dev, tflops_peak):
@@ -524,6 +654,8 @@ def main():
     hbm, peak_kind = peaks()
     kern_avg = float(np.mean(kern_ms))
     achieved = bytes_launch / (kern_avg / 1e3) / 1e9
+    fp64_peak = pkg.fp64_rate()                      # measured here: FP64 FMA TFLOP/s
+    fp64_achieved = 2.0 * r0["nnz_updates"] / (kern_avg / 1e3) / 1e12
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -538,14 +670,19 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": kernel_traffic(),
                      "peak_kind": peak_kind, "bytes_per_launch": bytes_launch, "kernel": "bp_kernel",
-                     "launch_ms": kern_avg},
+                     "launch_ms": kern_avg,
+                     "fp64": {"achieved": fp64_achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                              "frac": fp64_achieved / fp64_peak,
+                              "note": "one FMA (2 flops) per nonzero-update of the activities; peak: bp_fp64_rate, "
+                                      "measured in this run"}},
     }
     if rank == 0 and not args.no_extras:
         todo = [e for e in args.extras.split(",") if e]
-        bad = [e for e in todo if e not in ("probing", "batch", "learned", "scorer")]
+        bad = [e for e in todo if e not in ("probing", "batch", "fp", "learned", "scorer")]
         if bad:
             raise SystemExit(f"unknown extras: {bad}")
         fns = {"probing": lambda: probing_extra(pkg, torch, dev), "batch": lambda: batch_extra(pkg, torch, dev),
+               "fp": lambda: fp_extra(pkg, torch, dev),
                "learned": lambda: learned_extra(pkg, torch, dev), "scorer": lambda: scorer_extra(pkg, torch, dev, tensor_peak())}
         out["extras"] = {e: fns[e]() for e in todo}
     if rank == 0 and not args.no_cpu_baseline:

@@ -568,6 +568,12 @@ int scorer_load(scorer *s, const char *path);
 
 /* ------------------------------------------------------------------- errors */
 
+/* bp_fp64_rate -- measures the current device's FP64 fused multiply-add throughput in TFLOP/s
+ * (2 flops per FMA; the best of five timed launches of independent FMA chains), the denominator
+ * of the FP64 pipe fraction reported beside the HBM fraction.  No paper counterpart: a
+ * measurement helper.  Synchronises the stream; returns BP_OK, BP_ERR_INVALID or BP_ERR_CUDA. */
+int bp_fp64_rate(double *tflops, void *stream);
+
 /* Thread-local message of the last error ("" if none). */
 const char *bp_last_error(void);
 

@@ -145,6 +145,7 @@ SIGNATURES = {
     "mip_set_instances": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "bp_propagate_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(BpParams), C.c_void_p,
                                      C.c_void_p]),
+    "bp_fp64_rate": (C.c_int, [C.POINTER(C.c_double), C.c_void_p]),
     "bp_last_error": (C.c_char_p, []),
     "bp_version": (C.c_char_p, []),
 }
@@ -561,6 +562,13 @@ def probe_split(is_int, l, u):
     out = (C.c_double * 4)()
     ok = lib().probe_split(int(is_int), float(l), float(u), out)
     return (out[0], out[1], out[2], out[3]) if ok else None
+
+
+def fp64_rate(stream=None):
+    """The device's measured FP64 FMA throughput in TFLOP/s (bp_fp64_rate)."""
+    v = C.c_double(0.0)
+    _check(lib().bp_fp64_rate(C.byref(v), _stream(stream)))
+    return v.value
 
 
 def version():
