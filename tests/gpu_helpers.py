@@ -29,13 +29,22 @@ def assert_bounds_match(p, gl, gu, ol, ou):
         assert len(bad) == 0, f"continuous {what} bounds differ beyond 1e-9 rel at {len(bad)} vars, max {d.max()}"
 
 
-def compare(p, gl, gu, gr, ol, ou, orr, exact_counts=True):
+def compare(p, gl, gu, gr, ol, ou, orr, exact_counts=True, planted=None):
     """The GPU must match the oracle: status, rounds, work count, first infeasible indices
-    and integer bounds exactly, continuous bounds within 1e-9 relative.  Only when the
-    oracle saw a fragile decision (a decision that summation order may flip) is the run
-    compared on soundness alone."""
+    and integer bounds exactly, continuous bounds within 1e-9 relative.  When the oracle saw a
+    fragile decision (one that summation order may flip) the two may legitimately differ: the
+    function then returns False (the caller skips the exact comparison), after checking what
+    still holds, if the caller gives `planted`, a point satisfying every row inside the start
+    bounds: propagation never cuts off a feasible point, so the GPU must not report
+    infeasibility and its bounds must contain the point (integers exactly, continuous values
+    within 1e-6 relative)."""
     assert gr["error"] == 0, gr
     if orr["fragile"]:
+        if planted is not None:
+            assert gr["status"] != oracle.INFEASIBLE, gr
+            ints = p.is_int == 1
+            slack = np.where(ints, 0.0, 1e-6 * np.maximum(1.0, np.abs(planted)))
+            assert (gl <= planted + slack).all() and (gu >= planted - slack).all()
         return False
     for key in ("status", "rounds", "first_infeasible_row", "first_infeasible_var"):
         assert gr[key] == orr[key], (key, gr[key], orr[key])

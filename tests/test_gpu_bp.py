@@ -78,7 +78,8 @@ def test_random_sweep(pkg, case, fix):
     lb, ub = synth.tighten_random(seed, p, fix, planted=(seed % 2 == 0))
     ol, ou, orr, _ = oracle.Problem(p).bp(lb, ub)
     gl, gu, gr = run_gpu(pkg.Problem(p), lb, ub)
-    if not compare(p, gl, gu, gr, ol, ou, orr):
+    feasible = fix == 0 or seed % 2 == 0          # the planted point is inside the start bounds
+    if not compare(p, gl, gu, gr, ol, ou, orr, planted=p.x0 if feasible else None):
         pytest.skip(f"oracle reported {orr['fragile']} fragile decisions")
 
 
@@ -143,5 +144,5 @@ def test_mixed_powerlaw_infinite_bounds(pkg):
     p = synth.mixed_powerlaw(seed=77, m=20_000, n=50_000, nnz=500_000, max_row=20_000, inf_fraction=0.05)
     ol, ou, orr, _ = oracle.Problem(p).bp(p.lb, p.ub)
     gl, gu, gr = run_gpu(pkg.Problem(p), p.lb, p.ub)
-    if not compare(p, gl, gu, gr, ol, ou, orr):
+    if not compare(p, gl, gu, gr, ol, ou, orr, planted=p.x0):
         pytest.skip("fragile")
