@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the probing, batch, learned and scorer measurements")
     ap.add_argument("--extras", default="probing,batch,fp,learned,scorer",
-                    help="comma-separated subset of the extra measurements to run")
+                    help="comma-separated subset of the extra measurements to run (learned_full, the "
+                         "160/40-instance learned-order experiment at 1M nonzeros, is not in the default set)")
     return ap.parse_args()
 
 
@@ -445,57 +446,110 @@ def _verified(pkg, torch, prob, p, xo):
     return r.status == 0
 
 
-def learned_extra(pkg, torch, dev):
-    """The learned rounding order against the paper's order in fix-and-propagate (1% of the
-    integer variables per bulk).  The scorer is trained on the feasible plain trajectories of
-    16 instances with 100k nonzeros (8 seeds each), then both orders run on held-out instances:
-    12 with 100k nonzeros (4 seeds) and 8 with 1M nonzeros (2 seeds), the same seeds for both.
-    Feasible means verified again (fresh propagation with the integers fixed, and a continuous
-    completion by HiGHS)."""
+def _sign_test(wins, losses):
+    """Two-sided exact sign test p-value for `wins` against `losses` (ties dropped)."""
+    import math
+    k, n = min(wins, losses), wins + losses
+    if n == 0:
+        return None
+    return min(1.0, 2.0 * sum(math.comb(n, i) for i in range(k + 1)) / 2.0 ** n)
+
+
+def learned_experiment(pkg, torch, dev, nnz, eq_fraction, train_idx, train_seeds, test_idx, test_seeds):
+    """Train the scorer on the plain trajectories of `train_idx` rounding instances (one run per
+    seed of `train_seeds`, labels from the runs that ended feasible), then run both orders with
+    the same seeds on the held-out `test_idx` instances.  Feasible means verified again (fresh
+    propagation with the integers fixed, and a continuous completion by HiGHS).  Bulks to
+    feasibility are compared paired: over the (instance, seed) runs that both orders solve."""
     import numpy as np
     from paper_2510_20499_gb300 import learned, synth
     fp = dict(bulk_rule=1, fraction=0.01)
     t0 = time.perf_counter()
     data = []
-    for i in range(16):
-        p, x = synth.rounding_instance(i, 100_000)
+    for i in train_idx:
+        p, x = synth.rounding_instance(i, nnz, eq_fraction=eq_fraction)
         prob = pkg.Problem(p)
         xd, lb, ub = (torch.tensor(a, device=dev) for a in (x, p.lb, p.ub))
-        data.append(learned.collect(prob, xd, lb, ub, seeds=range(100, 108), **fp))
+        d = learned.collect(prob, xd, lb, ub, seeds=train_seeds, **fp)
+        d["runs"] = None
+        data.append(d)
+        del prob
     scorer = pkg.Scorer(seed=3)
     losses = learned.train(scorer, data, epochs=6, batch=4096, lr=3e-3, seed=0)
     t_train = time.perf_counter() - t0
-    out = {"workload": "rounding instances (mixed power-law, planted point + N(0, 0.3) as the fractional point)",
-           "train": {"instances": 16, "nnz": 100_000, "runs": 16 * 8,
+    out = {"nnz": nnz, "eq_fraction": eq_fraction,
+           "train": {"instances": len(train_idx), "seeds": len(train_seeds),
+                     "runs": len(train_idx) * len(train_seeds),
                      "feasible_runs": int(sum(d["feasible"] for d in data)),
+                     "labelled_instances": int(sum(d["labels"] is not None for d in data)),
                      "labelled_rows": int(sum(d["feat"].shape[0] for d in data if d["labels"] is not None)),
                      "loss_first_last": [losses[0], losses[-1]] if losses else None, "seconds": t_train}}
-    for nnz, idx, seeds in ((100_000, range(1000, 1012), range(1, 5)), (1_000_000, range(2000, 2008), range(1, 3))):
-        arms = {"plain": [], "learned": []}
-        t_run = {"plain": 0.0, "learned": 0.0}
-        for i in idx:
-            p, x = synth.rounding_instance(i, nnz)
-            prob = pkg.Problem(p)
-            xd, lb, ub = (torch.tensor(a, device=dev) for a in (x, p.lb, p.ub))
-            order, up = learned.scores(prob, scorer, xd, lb, ub)
-            for s in seeds:
-                for arm, kw in (("plain", {}), ("learned", dict(order_score=order, up_prob=up))):
-                    torch.cuda.synchronize()
-                    ta = time.perf_counter()
-                    xo, r = prob.fix_and_propagate(xd, lb, ub, seed=s, **kw, **fp)
-                    t_run[arm] += time.perf_counter() - ta
-                    r["verified"] = r["status"] == 0 and _verified(pkg, torch, prob, p, xo.cpu().numpy())
-                    arms[arm].append(r)
-        rep = {}
-        for arm, rs in arms.items():
-            ok = [r for r in rs if r["verified"]]
-            rep[arm] = {"runs": len(rs), "feasible_reported": sum(r["status"] == 0 for r in rs),
-                        "feasible_verified": len(ok),
-                        "bulks_to_feasibility": float(np.mean([r["bulks"] for r in ok])) if ok else None,
-                        "bulks_mean_all_runs": float(np.mean([r["bulks"] for r in rs])),
-                        "fixed_by_choice_mean": float(np.mean([r["fixed_by_choice"] for r in rs])),
-                        "seconds_per_run": t_run[arm] / len(rs)}
-        out[f"test_{nnz // 1000}k_nnz"] = rep
+    del data
+    arms = {"plain": [], "learned": []}
+    t_run = {"plain": 0.0, "learned": 0.0}
+    t1 = time.perf_counter()
+    for i in test_idx:
+        p, x = synth.rounding_instance(i, nnz, eq_fraction=eq_fraction)
+        prob = pkg.Problem(p)
+        xd, lb, ub = (torch.tensor(a, device=dev) for a in (x, p.lb, p.ub))
+        order, up = learned.scores(prob, scorer, xd, lb, ub)
+        for s in test_seeds:
+            for arm, kw in (("plain", {}), ("learned", dict(order_score=order, up_prob=up))):
+                torch.cuda.synchronize()
+                ta = time.perf_counter()
+                xo, r = prob.fix_and_propagate(xd, lb, ub, seed=s, **kw, **fp)
+                t_run[arm] += time.perf_counter() - ta
+                r["verified"] = r["status"] == 0 and _verified(pkg, torch, prob, p, xo.cpu().numpy())
+                arms[arm].append(r)
+        del prob
+    for arm, rs in arms.items():
+        ok = [r for r in rs if r["verified"]]
+        out[arm] = {"runs": len(rs), "feasible_reported": sum(r["status"] == 0 for r in rs),
+                    "feasible_verified": len(ok),
+                    "bulks_to_feasibility": float(np.mean([r["bulks"] for r in ok])) if ok else None,
+                    "bulks_mean_all_runs": float(np.mean([r["bulks"] for r in rs])),
+                    "fixed_by_choice_mean": float(np.mean([r["fixed_by_choice"] for r in rs])),
+                    "seconds_per_run": t_run[arm] / len(rs)}
+    both = [(a["bulks"], b["bulks"]) for a, b in zip(arms["plain"], arms["learned"]) if a["verified"] and b["verified"]]
+    wins = sum(bl < bp for bp, bl in both)
+    losses_ = sum(bl > bp for bp, bl in both)
+    only_p = sum(a["verified"] and not b["verified"] for a, b in zip(arms["plain"], arms["learned"]))
+    only_l = sum(b["verified"] and not a["verified"] for a, b in zip(arms["plain"], arms["learned"]))
+    out["paired"] = {
+        "runs_both_feasible": len(both),
+        "bulks_plain": float(np.mean([q[0] for q in both])) if both else None,
+        "bulks_learned": float(np.mean([q[1] for q in both])) if both else None,
+        "bulks_ratio_learned_over_plain": (float(np.mean([q[1] for q in both]) / np.mean([q[0] for q in both]))
+                                           if both else None),
+        "learned_fewer_bulks": wins, "learned_more_bulks": losses_, "same_bulks": len(both) - wins - losses_,
+        "sign_test_p": _sign_test(wins, losses_),
+        "feasible_plain_only": only_p, "feasible_learned_only": only_l,
+        "feasibility_sign_test_p": _sign_test(only_l, only_p)}
+    out["test_seconds"] = time.perf_counter() - t1
+    return out
+
+
+def learned_extra(pkg, torch, dev):
+    """The learned rounding order against the paper's order in fix-and-propagate (1% of the
+    integer variables per bulk), at two sizes.  100k nonzeros (20% equality pairs): trained on 16
+    instances x 8 seeds, tested on 12 held-out instances x 4 seeds.  1M nonzeros (1% equality
+    pairs, with which the plain method reaches feasibility in part of the runs): trained on 16
+    instances x 4 seeds, tested on 8 held-out instances x 2 seeds.  The full 1M experiment (160
+    training and 40 test instances) is the separate `learned_full` extra."""
+    out = {"workload": "rounding instances (mixed power-law, planted point + N(0, 0.3) as the fractional point)"}
+    out["100k_nnz"] = learned_experiment(pkg, torch, dev, 100_000, 0.2, range(16), range(100, 108),
+                                         range(1000, 1012), range(1, 5))
+    out["1m_nnz"] = learned_experiment(pkg, torch, dev, 1_000_000, 0.01, range(16), range(100, 104),
+                                       range(2000, 2008), range(1, 3))
+    return out
+
+
+def learned_full_extra(pkg, torch, dev):
+    """The learned rounding order at 1M nonzeros (1% equality pairs): trained on 160 instances x
+    2 seeds, tested on 40 held-out instances x 4 seeds (several minutes on one GPU)."""
+    out = {"workload": "rounding instances (mixed power-law, planted point + N(0, 0.3) as the fractional point)"}
+    out["1m_nnz"] = learned_experiment(pkg, torch, dev, 1_000_000, 0.01, range(160), range(100, 102),
+                                       range(2000, 2040), range(1, 5))
     return out
 
 
@@ -678,12 +732,13 @@ def main():
     }
     if rank == 0 and not args.no_extras:
         todo = [e for e in args.extras.split(",") if e]
-        bad = [e for e in todo if e not in ("probing", "batch", "fp", "learned", "scorer")]
+        bad = [e for e in todo if e not in ("probing", "batch", "fp", "learned", "learned_full", "scorer")]
         if bad:
             raise SystemExit(f"unknown extras: {bad}")
         fns = {"probing": lambda: probing_extra(pkg, torch, dev), "batch": lambda: batch_extra(pkg, torch, dev),
                "fp": lambda: fp_extra(pkg, torch, dev),
-               "learned": lambda: learned_extra(pkg, torch, dev), "scorer": lambda: scorer_extra(pkg, torch, dev, tensor_peak())}
+               "learned": lambda: learned_extra(pkg, torch, dev),
+               "learned_full": lambda: learned_full_extra(pkg, torch, dev), "scorer": lambda: scorer_extra(pkg, torch, dev, tensor_peak())}
         out["extras"] = {e: fns[e]() for e in todo}
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(p)

@@ -382,17 +382,21 @@ def uneven_batch(seed: int = SEED_BASE + 4, count: int = 64, nnz_lo: float = 1e3
     return out
 
 
-def rounding_instance(index: int, nnz: int = 1_000_000, sigma: float = 0.3) -> tuple[Milp, np.ndarray]:
+def rounding_instance(index: int, nnz: int = 1_000_000, sigma: float = 0.3,
+                      eq_fraction: float = 0.2) -> tuple[Milp, np.ndarray]:
     """Instance `index` of the learned-rounding workload and the fractional point it rounds.
 
     The problem is the mixed power-law instance scaled to `nnz` nonzeros (m = nnz / 25,
     n = nnz / 10, the longest row nnz / 50; 1M nonzeros: 40k x 100k), seed
-    (SEED_BASE + 5) * 2^16 + index, objective N(0, 1).  The fractional point stands in for an
-    LP relaxation solution: the planted feasible point plus N(0, sigma) noise, clamped to the
-    bounds.  It is close to a feasible point by construction (the planted one), which a real
-    LP solution need not be."""
+    (SEED_BASE + 5) * 2^16 + index, objective N(0, 1), with a fraction eq_fraction of the rows
+    as equality pairs (0.2 as in the large mixed instance; the 1M-nonzero experiment takes 0.01,
+    with which the plain method reaches feasibility in part of the runs).  The fractional point
+    stands in for an LP relaxation solution: the planted feasible point plus N(0, sigma) noise,
+    clamped to the bounds.  It is close to a feasible point by construction (the planted one),
+    which a real LP solution need not be."""
     seed = ((SEED_BASE + 5) << 16) + int(index)
-    p = mixed_powerlaw(seed=seed, m=nnz // 25, n=nnz // 10, nnz=nnz, max_row=max(100, nnz // 50))
+    p = mixed_powerlaw(seed=seed, m=nnz // 25, n=nnz // 10, nnz=nnz, max_row=max(100, nnz // 50),
+                       eq_fraction=eq_fraction)
     rng = np.random.default_rng(seed + 1)
     x = np.clip(p.x0 + rng.normal(0.0, sigma, p.n), p.lb, p.ub)
     p.name = f"rounding_{index}_{p.m}x{p.n}_{nnz}"
