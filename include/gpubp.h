@@ -461,7 +461,8 @@ void fp_params_default(fp_params *p);   /* seed 1, sqrt rule, last_single 36, fr
  * x_out:    DEVICE double[n]: integer variables at their fixed values, continuous variables
  *           x clamped to their final bounds.
  * result:   HOST pointer, valid at return (the call synchronises the stream: every bulk's
- *           control decision reads a few words back).
+ *           control decision reads a few words back; without a cache, the one-variable
+ *           retries of a failed bulk run in one device-driven launch and report back once).
  * Memory: the first call on a handle also loads a second copy of the problem, as two
  * instances of a block-diagonal pair, so that each bulk's two candidate vectors propagate in
  * one launch; the handle keeps it until mip_free (about twice the handle's own device memory).

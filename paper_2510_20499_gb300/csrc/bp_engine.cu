@@ -32,6 +32,7 @@
 #include <cstdlib>
 
 #include "bp_host.h"
+#include "fp_draw.cuh"
 
 namespace gpubp {
 
@@ -77,6 +78,11 @@ struct BpArgs {
     const int* row_off;
     const int* col_off;
     InstState* inst;
+    // optional (device-driven rounding loop): every variable changed during the propagation is
+    // listed once in dirty[0 .. *ndirty), deduplicated by vdirty[v] == the block's dstamp
+    int* vdirty;
+    int* dirty;
+    int* ndirty;
     unsigned long long* i_nnz;   // [kPhaseSlots][ninst] nonzeros processed in the round of that slot
     int* i_rowinf;               // [kPhaseSlots][ninst] smallest infeasible row of the round
     int* i_cross;                // [kPhaseSlots][ninst] smallest crossing variable found in the round
@@ -108,6 +114,8 @@ struct Stage {
     int last_block;
     unsigned bar_k;                              // grid barriers passed in this launch
     int epi_n, epi_par;                          // variables changed in the last round, their list
+    int dstamp;                                  // stamp of the current propagation in vdirty
+    int go;                                      // block-uniform decision of a device-driven loop
 };
 
 // ------------------------------------------------------------------ phase state
@@ -251,6 +259,11 @@ __device__ void warp_queue_rows(Stage& st, const BpArgs& A, const DevProblem& P,
 // memory only; no global round trip on the task's path).  drain_changed later keeps the first
 // report of each variable across the grid and queues its rows.  A full queue falls back to
 // doing that work from this lane.
+// Lists variable v once per propagation in the dirty list (device-driven rounding loop only).
+__device__ __noinline__ void note_dirty(const BpArgs& A, int stamp, int v) {
+    if (atomicMax(&A.vdirty[v], stamp) < stamp) A.dirty[atomicAdd(A.ndirty, 1)] = v;
+}
+
 __device__ __forceinline__ void note_changed(Stage& st, const BpArgs& A, const DevProblem& P, const Phase& ph,
                                              int j) {
     const int i = atomicAdd(&st.bq_n, 1);
@@ -260,6 +273,7 @@ __device__ __forceinline__ void note_changed(Stage& st, const BpArgs& A, const D
     }
     if (atomicMax(&A.vstamp[j], ph.st_v) >= ph.st_v) return;
     A.i_chg[ph.s3() * A.ninst + var_inst(st, A, j)] = 1;
+    if (A.vdirty) note_dirty(A, st.dstamp, j);
     const int pos = atomicAdd(&A.ctl->nchg[ph.s3()].v, 1);
     A.chg[ph.par][pos] = j;
     const int e = __ldg(P.col_ptr + j + 1);
@@ -282,6 +296,7 @@ __device__ void drain_changed(Stage& st, const BpArgs& A, const DevProblem& P, c
         const int ce = v >= 0 ? __ldg(P.col_ptr + v + 1) : 0;
         if (v >= 0 && atomicMax(&A.vstamp[v], ph.st_v) >= ph.st_v) v = -1;
         if (v >= 0) A.i_chg[ph.s3() * A.ninst + var_inst(st, A, v)] = 1;
+        if (A.vdirty && v >= 0) note_dirty(A, st.dstamp, v);
         warp_append(st, A, P, ph, v >= 0 ? kSlotChg : -1, v);
         const int deg = v >= 0 ? ce - cb : 0;
         int incl = deg;
@@ -768,6 +783,156 @@ __device__ void finish_block(Stage& st, const BpArgs& A) {
     }
 }
 
+// The Jacobi rounds of one propagation, from the round-0 descriptor in `st` until every
+// instance has stopped (or the error flag is set).  Stamps of round t: base + t.
+__device__ __forceinline__ void run_rounds(Stage& st, const DevProblem& P, const BpArgs& A, int base) {
+    Ctl* ctl = A.ctl;
+    const int gw_r = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+    const int NW = gridDim.x * kWarpsPerBlock;
+    for (int t = 0; !st.flag; ++t) {
+        Phase ph;
+        ph.t = t;
+        ph.par = t & 1;
+        ph.npar = ph.par ^ 1;
+        ph.R = A.bk[ph.par];
+        ph.X = A.bk[ph.npar];
+        ph.st_v = base + t;
+        ph.st_r = base + t + 1;
+        const bool stat = (t == 0 && !A.w0 && !A.w0v);
+        const int* rows = stat ? P.static_list : A.list[ph.par];
+        const int4* tasks = stat ? P.static_tasks : A.task[ph.par];
+        const int ntask = st.d_ntask;
+        const int nprev = st.d_nprev;
+        const int* chg_prev = A.chg[ph.npar];
+        int cnt[kNumClass];
+#pragma unroll
+        for (int c = 0; c < kNumClass; ++c) cnt[c] = st.d_cnt[c];
+        // phase A, warp tasks: pieces of piece rows (partials), fix-ups of the previous round's
+        // changes, thread-per-row bins, warp rows
+        const int s_fix = (nprev + 31) / 32;
+        int s_bin[kNumThreadBins];
+        int total = ntask + s_fix + cnt[kClassWarpRow];
+#pragma unroll
+        for (int c = 0; c < kNumThreadBins; ++c) {
+            s_bin[c] = (cnt[c] + 31) / 32;
+            total += s_bin[c];
+        }
+        // with at most one task per warp (short rounds), a piece's warp keeps its nonzeros and
+        // bounds in registers from phase A to phase B
+        const bool single = total <= NW;
+        HeldBounds H1;
+        int4 tk1 = make_int4(0, 0, 0, 0);
+        bool piece1 = false;
+        if (single) {
+            if (gw_r < ntask) {
+                tk1 = __ldcg(tasks + gw_r);
+                piece1 = st.alive[row_inst(st, A, tk1.x)] != 0;
+                if (piece1) piece_partial(A, P, ph, gw_r, tk1, &H1);
+            } else if (gw_r < total) {
+                warp_task(st, A, P, ph, gw_r - ntask, rows, cnt, s_bin, s_fix, chg_prev, nprev);
+            }
+        } else {
+            for (int task = gw_r; task < total; task += NW) {
+                if (task < ntask) {
+                    const int4 tk = __ldcg(tasks + task);
+                    if (st.alive[row_inst(st, A, tk.x)]) piece_partial(A, P, ph, task, tk, nullptr);
+                } else {
+                    warp_task(st, A, P, ph, task - ntask, rows, cnt, s_bin, s_fix, chg_prev, nprev);
+                }
+            }
+        }
+        // phase B: every piece's row total and candidates, once all partials are written
+        if (ntask > 0) {
+            grid_sync(st, ctl);
+            if (single) {
+                if (piece1) piece_candidates(st, A, P, ph, gw_r, tk1, &H1);
+            } else {
+                for (int task = gw_r; task < ntask; task += NW) {
+                    const int4 tk = __ldcg(tasks + task);
+                    if (st.alive[row_inst(st, A, tk.x)]) piece_candidates(st, A, P, ph, task, tk, nullptr);
+                }
+            }
+        }
+        // changes of this block: dedupe grid-wide, list them, queue their rows
+        drain_changed(st, A, P, ph);
+        // staged appends to the global lists; nonzeros of this phase: one atomic per block
+        warp_flush_all(st, A, P, ph);
+        __syncthreads();
+        if (threadIdx.x == 0 && st.nnz) {
+            atomicAdd(&ctl->nnz[ph.s3()].v, st.nnz);
+            st.nnz = 0;
+        }
+        flush_inst_nnz(st, A, ph.s3());
+        if (A.skip_block == (int)blockIdx.x) {
+            // test-only failure: this block stops arriving at the grid barrier, so the others'
+            // bounded waits run out and the launch reports BP_ERR_TIMEOUT
+            st.flag = 2;
+            break;
+        }
+        grid_sync(st, ctl);
+        end_round(st, ctl, P, A, t);
+    }
+
+}
+
+// After the round-0 lists are queued (and a grid barrier): every block decides which instances
+// run round 0 (block 0 records the others' verdicts) and loads the round-0 descriptor.
+__device__ __forceinline__ void round0_state(Stage& st, const DevProblem& P, const BpArgs& A) {
+    Ctl* ctl = A.ctl;
+    int rows0 = 0;
+    if (A.w0 || A.w0v)
+        for (int c = 0; c < kNumClass; ++c) rows0 += __ldcg(&ctl->cnt[0][c].v);
+    if (threadIdx.x == 0) st.any_alive = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < A.ninst; i += kThreads) {
+        InstState* I = A.inst + i;
+        // rows in round 0: with a variable start list and several instances, each
+        // instance's own (a nonzero count is all that matters here)
+        const int ri = (A.w0v && A.ninst > 1) ? __ldcg(&I->start_rows)
+                       : (A.w0 || A.w0v)      ? rows0
+                                              : st.roff[i + 1] - st.roff[i];
+        const int ec = __ldcg(&I->entry_cross);
+        int alive = 1;
+        if (ec != INT_MAX) {
+            alive = 0;
+            if (blockIdx.x == 0) {
+                I->status = BP_INFEASIBLE;
+                I->first_var = ec;
+            }
+        } else if (ri == 0 || A.max_rounds <= 0) {
+            alive = 0;
+            if (blockIdx.x == 0) I->status = ri == 0 ? BP_FIXPOINT : BP_ROUND_LIMIT;
+        }
+        if (blockIdx.x == 0) I->alive = alive;
+        st.alive[i] = (unsigned char)alive;
+        if (alive) atomicOr(&st.any_alive, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        load_descriptor(st, ctl, P, A, 0);
+        st.flag = (!st.any_alive || __ldcg(&ctl->error)) ? 1 : 0;
+    }
+    __syncthreads();
+}
+
+// Crossing check of the last round of the instances whose check is pending (their last
+// round's changed variables).
+__device__ __forceinline__ void last_round_cross(Stage& st, const DevProblem& P, const BpArgs& A) {
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthreads = gridDim.x * blockDim.x;
+    const int epi_n = st.epi_n;
+    if (epi_n > 0) {
+        // crossing check of the last round of the instances whose check is pending
+        const int* lst = A.chg[st.epi_par];
+        for (int i = gtid; i < epi_n; i += gthreads) {
+            const int v = __ldcg(lst + i);
+            const int vi = var_inst(st, A, v);
+            if (!st.pending[vi]) continue;
+            const longlong2 b = __ldcg(A.bk[st.rpar[vi]] + v);
+            if (crossed(P.is_int[v] != 0, b.x, b.y)) atomicMin(&A.inst[vi].first_var, v);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------- kernel
 __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProblem P, BpArgs A) {
     __shared__ Stage st;
@@ -873,143 +1038,15 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
         warp_flush_all(st, A, P, q);
     }
     grid_sync(st, ctl);
-    // every block: which instances run round 0 (block 0 records the others' verdicts)
-    {
-        int rows0 = 0;
-        if (A.w0 || A.w0v)
-            for (int c = 0; c < kNumClass; ++c) rows0 += __ldcg(&ctl->cnt[0][c].v);
-        if (threadIdx.x == 0) st.any_alive = 0;
-        __syncthreads();
-        for (int i = threadIdx.x; i < A.ninst; i += kThreads) {
-            InstState* I = A.inst + i;
-            // rows in round 0: with a variable start list and several instances, each
-            // instance's own (a nonzero count is all that matters here)
-            const int ri = (A.w0v && A.ninst > 1) ? __ldcg(&I->start_rows)
-                           : (A.w0 || A.w0v)      ? rows0
-                                                  : st.roff[i + 1] - st.roff[i];
-            const int ec = __ldcg(&I->entry_cross);
-            int alive = 1;
-            if (ec != INT_MAX) {
-                alive = 0;
-                if (blockIdx.x == 0) {
-                    I->status = BP_INFEASIBLE;
-                    I->first_var = ec;
-                }
-            } else if (ri == 0 || A.max_rounds <= 0) {
-                alive = 0;
-                if (blockIdx.x == 0) I->status = ri == 0 ? BP_FIXPOINT : BP_ROUND_LIMIT;
-            }
-            if (blockIdx.x == 0) I->alive = alive;
-            st.alive[i] = (unsigned char)alive;
-            if (alive) atomicOr(&st.any_alive, 1);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            load_descriptor(st, ctl, P, A, 0);
-            st.flag = (!st.any_alive || __ldcg(&ctl->error)) ? 1 : 0;
-        }
-        __syncthreads();
-    }
+    // every block: which instances run round 0
+    round0_state(st, P, A);
 
     // ---- rounds
-    for (int t = 0; !st.flag; ++t) {
-        Phase ph;
-        ph.t = t;
-        ph.par = t & 1;
-        ph.npar = ph.par ^ 1;
-        ph.R = A.bk[ph.par];
-        ph.X = A.bk[ph.npar];
-        ph.st_v = base + t;
-        ph.st_r = base + t + 1;
-        const bool stat = (t == 0 && !A.w0 && !A.w0v);
-        const int* rows = stat ? P.static_list : A.list[ph.par];
-        const int4* tasks = stat ? P.static_tasks : A.task[ph.par];
-        const int ntask = st.d_ntask;
-        const int nprev = st.d_nprev;
-        const int* chg_prev = A.chg[ph.npar];
-        int cnt[kNumClass];
-#pragma unroll
-        for (int c = 0; c < kNumClass; ++c) cnt[c] = st.d_cnt[c];
-        // phase A, warp tasks: pieces of piece rows (partials), fix-ups of the previous round's
-        // changes, thread-per-row bins, warp rows
-        const int s_fix = (nprev + 31) / 32;
-        int s_bin[kNumThreadBins];
-        int total = ntask + s_fix + cnt[kClassWarpRow];
-#pragma unroll
-        for (int c = 0; c < kNumThreadBins; ++c) {
-            s_bin[c] = (cnt[c] + 31) / 32;
-            total += s_bin[c];
-        }
-        // with at most one task per warp (short rounds), a piece's warp keeps its nonzeros and
-        // bounds in registers from phase A to phase B
-        const bool single = total <= NW;
-        HeldBounds H1;
-        int4 tk1 = make_int4(0, 0, 0, 0);
-        bool piece1 = false;
-        if (single) {
-            if (gw_r < ntask) {
-                tk1 = __ldcg(tasks + gw_r);
-                piece1 = st.alive[row_inst(st, A, tk1.x)] != 0;
-                if (piece1) piece_partial(A, P, ph, gw_r, tk1, &H1);
-            } else if (gw_r < total) {
-                warp_task(st, A, P, ph, gw_r - ntask, rows, cnt, s_bin, s_fix, chg_prev, nprev);
-            }
-        } else {
-            for (int task = gw_r; task < total; task += NW) {
-                if (task < ntask) {
-                    const int4 tk = __ldcg(tasks + task);
-                    if (st.alive[row_inst(st, A, tk.x)]) piece_partial(A, P, ph, task, tk, nullptr);
-                } else {
-                    warp_task(st, A, P, ph, task - ntask, rows, cnt, s_bin, s_fix, chg_prev, nprev);
-                }
-            }
-        }
-        // phase B: every piece's row total and candidates, once all partials are written
-        if (ntask > 0) {
-            grid_sync(st, ctl);
-            if (single) {
-                if (piece1) piece_candidates(st, A, P, ph, gw_r, tk1, &H1);
-            } else {
-                for (int task = gw_r; task < ntask; task += NW) {
-                    const int4 tk = __ldcg(tasks + task);
-                    if (st.alive[row_inst(st, A, tk.x)]) piece_candidates(st, A, P, ph, task, tk, nullptr);
-                }
-            }
-        }
-        // changes of this block: dedupe grid-wide, list them, queue their rows
-        drain_changed(st, A, P, ph);
-        // staged appends to the global lists; nonzeros of this phase: one atomic per block
-        warp_flush_all(st, A, P, ph);
-        __syncthreads();
-        if (threadIdx.x == 0 && st.nnz) {
-            atomicAdd(&ctl->nnz[ph.s3()].v, st.nnz);
-            st.nnz = 0;
-        }
-        flush_inst_nnz(st, A, ph.s3());
-        if (A.skip_block == (int)blockIdx.x) {
-            // test-only failure: this block stops arriving at the grid barrier, so the others'
-            // bounded waits run out and the launch reports BP_ERR_TIMEOUT
-            st.flag = 2;
-            break;
-        }
-        grid_sync(st, ctl);
-        end_round(st, ctl, P, A, t);
-    }
+    run_rounds(st, P, A, base);
 
     // ---- epilogue
     if (st.flag != 2 && !ld_acquire_s32(&ctl->error)) {
-        const int epi_n = st.epi_n;
-        if (epi_n > 0) {
-            // crossing check of the last round of the instances whose check is pending
-            const int* lst = A.chg[st.epi_par];
-            for (int i = gtid; i < epi_n; i += gthreads) {
-                const int v = __ldcg(lst + i);
-                const int vi = var_inst(st, A, v);
-                if (!st.pending[vi]) continue;
-                const longlong2 b = __ldcg(A.bk[st.rpar[vi]] + v);
-                if (crossed(P.is_int[v] != 0, b.x, b.y)) atomicMin(&A.inst[vi].first_var, v);
-            }
-        }
+        last_round_cross(st, P, A);
         for (int vb = blockIdx.x * kThreads; vb < P.n; vb += gthreads) {
             const int v = vb + threadIdx.x;
             int changed = 0, vi = -1;
@@ -1028,6 +1065,216 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) bp_kernel(DevProbl
         }
     }
     finish_block(st, A);
+}
+
+// ------------------------------------------------- device-driven single fixings (Section 2.3)
+// fix_and_propagate's one-variable bulks (the recovery of a failed bulk, Algorithm 1) run in one
+// persistent launch over the instance pair: for each queued variable still unfixed, the two
+// candidate values (the draw and the other rounding) are fixed in the two copies, both copies
+// propagate from that variable's rows (the same rounds as run_rounds in a launch of their own),
+// and the first feasible candidate becomes the current bounds.  The current bounds stay ordered
+// keys on the device between fixings; only the variables a propagation changed (the dirty list)
+// are copied back into the pair's buffers, so a fixing costs its rounds, not a pass over n.
+struct FpSingleArgs {
+    longlong2* cur;            // n0: the current bounds (ordered keys)
+    const int* queue;          // variables to fix one at a time, in order
+    int qlen;
+    int n0;                    // variables of one copy
+    const double* x;
+    const double* up_prob;
+    unsigned long long seed, bulk0;
+    int* words;                // [0..1] start list, [2] its length, [3] dirty count
+    FpSingleOut* out;
+};
+
+__global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) fp_single_kernel(DevProblem P, BpArgs A, FpSingleArgs F) {
+    __shared__ Stage st;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthreads = gridDim.x * blockDim.x;
+    Ctl* ctl = A.ctl;
+    const int n0 = F.n0;
+    for (int i = threadIdx.x; i < kWarpsPerBlock * kSlots; i += kThreads) (&st.wcnt[0][0])[i] = 0;
+    if (threadIdx.x == 0) {
+        st.bq_n = 0;
+        st.nnz = 0;
+        st.bar_k = 0;
+    }
+    for (int i = threadIdx.x; i <= A.ninst; i += kThreads) {
+        st.roff[i] = A.row_off[i];
+        st.coff[i] = A.col_off[i];
+    }
+    int base = __ldcg(A.stamp);
+    long long bulks = 0, runs = 0, nnz = 0, fixed = 0;
+    int infeasible = 0;
+    __syncthreads();
+    for (int q = 0; q < F.qlen; ++q) {
+        if (base > (1 << 30)) {
+            // the stamps restart (every block sees the same base)
+            for (int v = gtid; v < P.n; v += gthreads) {
+                A.vstamp[v] = 0;
+                A.vdirty[v] = 0;
+            }
+            for (int k = gtid; k < P.m; k += gthreads) A.rstamp[k] = 0;
+            base = 1;
+            grid_sync(st, ctl);
+        }
+        const int j = __ldg(F.queue + q);
+        if (threadIdx.x == 0) {
+            int go = 0;
+            if ((unsigned)j < (unsigned)n0) {
+                const longlong2 c = __ldcg(F.cur + j);
+                go = c.x < c.y ? 1 : 0;     // fixed meanwhile: skipped, no bulk
+            } else if (gtid == 0) {
+                atomicExch(&ctl->error, BP_ERR_INVALID);
+            }
+            st.go = go;
+        }
+        __syncthreads();
+        const int go = st.go;
+        __syncthreads();
+        if (!go) continue;
+        // this propagation's block state
+        for (int i = threadIdx.x; i < A.ninst; i += kThreads) {
+            st.alive[i] = 1;
+            st.pending[i] = 0;
+            st.rpar[i] = 0;
+            st.i_nnz[i] = 0;
+        }
+        if (threadIdx.x == 0) {
+            st.epi_n = 0;
+            st.epi_par = 0;
+            st.dstamp = base;
+        }
+        if (blockIdx.x == 0) {
+            // block 0: counters, instance states, the two candidate fixings (the draw in copy 0,
+            // the other rounding in copy 1), the start list and the rows of round 0
+            if (threadIdx.x == 0) {
+                for (int q3 = 0; q3 < kPhaseSlots; ++q3) {
+#pragma unroll
+                    for (int c = 0; c < kNumClass; ++c) ctl->cnt[q3][c].v = 0;
+                    ctl->ntask[q3].v = 0;
+                    ctl->nchg[q3].v = 0;
+                    ctl->nnz[q3].v = 0;
+                }
+                ctl->phases = 0;
+                for (int i = 0; i < A.ninst; ++i) {
+                    InstState I;
+                    I.status = BP_FIXPOINT;
+                    I.rounds = 0;
+                    I.result_par = 0;
+                    I.first_row = INT_MAX;
+                    I.first_var = INT_MAX;
+                    I.alive = 1;
+                    I.pending = 0;
+                    I.entry_cross = INT_MAX;
+                    I.start_rows = 0;
+                    I.nnz_total = 0;
+                    I.n_changed = 0;
+                    A.inst[i] = I;
+                    for (int q3 = 0; q3 < kPhaseSlots; ++q3) {
+                        A.i_nnz[q3 * A.ninst + i] = 0;
+                        A.i_rowinf[q3 * A.ninst + i] = INT_MAX;
+                        A.i_cross[q3 * A.ninst + i] = INT_MAX;
+                        A.i_chg[q3 * A.ninst + i] = 0;
+                    }
+                }
+                const longlong2 c = __ldcg(F.cur + j);
+                const double l = kdec(c.x), u = kdec(c.y);
+                const double xh = clampd(__ldg(F.x + j), l, u);
+                const double va = clampd(draw_value(xh, F.seed, F.bulk0 + (unsigned long long)bulks, j, 0, F.up_prob), l, u);
+                const double fl = floor(xh);
+                const double vb = clampd(va == fl ? __dadd_rn(fl, 1.0) : fl, l, u);
+                const bool is_i = P.is_int[j] != 0;
+                const longlong2 ka = normalized_keys(va, va, is_i), kb = normalized_keys(vb, vb, is_i);
+                A.bk[0][j] = ka;
+                A.bk[1][j] = ka;
+                A.bk[0][n0 + j] = kb;
+                A.bk[1][n0 + j] = kb;
+                if (crossed(is_i, ka.x, ka.y)) A.inst[0].entry_cross = j;
+                if (crossed(is_i, kb.x, kb.y)) A.inst[1].entry_cross = n0 + j;
+                A.vdirty[j] = base;
+                A.vdirty[n0 + j] = base;
+                A.dirty[0] = j;
+                A.dirty[1] = n0 + j;
+                *A.ndirty = 2;
+                F.words[0] = j;
+                F.words[1] = n0 + j;
+                F.words[2] = 2;
+                __threadfence();
+            }
+            __syncthreads();
+            Phase qph{0, 0, 1, A.bk[0], A.bk[1], base, base};
+            qph.npar = 0;     // round 0's list and counter slot (t = -1: next slot 0)
+            qph.t = -1;
+            if (warp < 2) {
+                const int u = warp == 0 ? j : n0 + j;
+                const int cb = __ldg(P.col_ptr + u), ce = __ldg(P.col_ptr + u + 1);
+                if (lane == 0 && ce > cb) atomicAdd(&A.inst[warp].start_rows, 1);
+                for (int s0 = cb; s0 < ce; s0 += 32) {
+                    const int sidx = s0 + lane;
+                    warp_queue_rows(st, A, P, qph, sidx < ce ? __ldg(P.row_idx + sidx) : -1);
+                }
+            }
+            warp_flush_all(st, A, P, qph);
+        }
+        grid_sync(st, ctl);
+        round0_state(st, P, A);
+        run_rounds(st, P, A, base);
+        if (ld_acquire_s32(&ctl->error)) break;
+        last_round_cross(st, P, A);
+        grid_sync(st, ctl);
+        // every block reads the same verdicts and picks the same candidate
+        if (threadIdx.x == 0) {
+            int pick = -1;
+            for (int c = 1; c >= 0; --c) {
+                const int status = __ldcg(&A.inst[c].status), fv = __ldcg(&A.inst[c].first_var);
+                if (status != BP_INFEASIBLE && fv == INT_MAX) pick = c;
+            }
+            st.go = pick;
+        }
+        __syncthreads();
+        const int pick = st.go;
+        // the changed variables of both copies back to the current bounds (the picked copy's
+        // values when a candidate is feasible)
+        const int nd = __ldcg(A.ndirty);
+        const longlong2* R = pick >= 0 ? A.bk[st.rpar[pick]] : nullptr;
+        for (int i = gtid; i < nd; i += gthreads) {
+            const int d = __ldcg(A.dirty + i);
+            const int b = d < n0 ? d : d - n0;
+            longlong2 kv;
+            if (pick >= 0) {
+                kv = __ldcg(R + (size_t)pick * n0 + b);
+                F.cur[b] = kv;
+            } else {
+                kv = __ldcg(F.cur + b);
+            }
+            A.bk[0][b] = kv;
+            A.bk[1][b] = kv;
+            A.bk[0][n0 + b] = kv;
+            A.bk[1][n0 + b] = kv;
+        }
+        if (gtid == 0) {
+            bulks += 1;
+            runs += 2;
+            nnz += (long long)(__ldcg(&A.inst[0].nnz_total) + __ldcg(&A.inst[1].nnz_total));
+            if (pick >= 0) fixed += 1;
+            else infeasible = 1;
+        }
+        base += __ldcg(&ctl->phases) + 3;
+        grid_sync(st, ctl);
+        if (pick < 0) break;
+    }
+    if (gtid == 0) {
+        const int err = __ldcg(&ctl->error);
+        F.out->bulks = bulks;
+        F.out->bp_runs = runs;
+        F.out->nnz_updates = nnz;
+        F.out->fixed = fixed;
+        F.out->infeasible = infeasible;
+        F.out->error = err;
+        // a propagation cut short by an error may have used stamps up to base + max_rounds + 1
+        *A.stamp = err ? base + A.max_rounds + 3 : base;
+    }
 }
 
 // ------------------------------------------------------------------------ host
@@ -1142,11 +1389,90 @@ int launch_propagate(mip_problem* p, double* lb, double* ub, const int* w0, int 
     a.i_rowinf = w.i_rowinf;
     a.i_cross = w.i_cross;
     a.i_chg = w.i_chg;
+    a.vdirty = nullptr;
+    a.dirty = nullptr;
+    a.ndirty = nullptr;
     BP_CUDA_TRY(cudaMemcpyAsync(w.ctl, w.ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     DevProblem dp = p->dp;
     void* args[] = {&dp, &a};
     BP_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)bp_kernel, dim3(p->grid_blocks), dim3(kThreads), args, 0, s));
     p->last_stream = s;
+    return BP_OK;
+}
+
+int launch_fp_single(mip_problem* tw, int n0, longlong2* cur, const int* queue, int qlen, const double* x,
+                     const double* up_prob, unsigned long long seed, unsigned long long bulk0, double theta,
+                     int max_rounds, int* vdirty, int* dirty, int* words, FpSingleOut* out, cudaStream_t s) {
+    Work& w = tw->w;
+    if (!tw->inst_row_off || !tw->inst_col_off || 2 * (long long)n0 != tw->n) {
+        set_error("launch_fp_single: not an instance pair");
+        return BP_ERR_INVALID;
+    }
+    BP_TRY(ensure_instances(tw, 2));
+    static int occ_single = -1;
+    if (occ_single < 0) {
+        int occ = 0;
+        BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp_single_kernel, kThreads, 0));
+        occ_single = occ;
+    }
+    if (occ_single < 1) {
+        set_error("fix-and-propagate kernel cannot be resident on this device");
+        return BP_ERR_CUDA;
+    }
+    const int occ = occ_single < tw->occ_max ? occ_single : tw->occ_max;
+    BpArgs a;
+    a.lb = nullptr;
+    a.ub = nullptr;
+    a.bk[0] = w.bkey[0];
+    a.bk[1] = w.bkey[1];
+    a.vstamp = w.vstamp;
+    a.rstamp = w.rstamp;
+    a.list[0] = w.list[0];
+    a.list[1] = w.list[1];
+    a.chg[0] = w.chg[0];
+    a.chg[1] = w.chg[1];
+    a.task[0] = w.task[0];
+    a.task[1] = w.task[1];
+    a.hpart = w.hpart;
+    a.hpinf = w.hpinf;
+    a.ctl = w.ctl;
+    a.dres = w.dres;
+    a.w0 = nullptr;
+    a.w0_len = 0;
+    a.w0v = words;
+    a.w0v_len = words + 2;
+    a.theta = theta;
+    a.max_rounds = max_rounds;
+    a.stamp = w.stamp;
+    a.trace = nullptr;
+    a.skip_block = -1;
+    a.ninst = 2;
+    a.row_off = tw->inst_row_off;
+    a.col_off = tw->inst_col_off;
+    a.inst = w.inst;
+    a.i_nnz = w.i_nnz;
+    a.i_rowinf = w.i_rowinf;
+    a.i_cross = w.i_cross;
+    a.i_chg = w.i_chg;
+    a.vdirty = vdirty;
+    a.dirty = dirty;
+    a.ndirty = words + 3;
+    FpSingleArgs f;
+    f.cur = cur;
+    f.queue = queue;
+    f.qlen = qlen;
+    f.n0 = n0;
+    f.x = x;
+    f.up_prob = up_prob;
+    f.seed = seed;
+    f.bulk0 = bulk0;
+    f.words = words;
+    f.out = out;
+    BP_CUDA_TRY(cudaMemcpyAsync(w.ctl, w.ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    DevProblem dp = tw->dp;
+    void* args[] = {&dp, &a, &f};
+    BP_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)fp_single_kernel, dim3(tw->sms * occ), dim3(kThreads), args, 0, s));
+    tw->last_stream = s;
     return BP_OK;
 }
 

@@ -146,6 +146,10 @@ int plan_chunks(mip_problem* p, cudaStream_t s);
 int root_keys(mip_problem* p, const double* lb, const double* ub, longlong2* out, cudaStream_t s);
 
 // stable LSD radix sort of (key, value) pairs on bits [begin_bit, end_bit)
+// The values of the first k pairs of the stable ascending sort of (keys, vals)[0..n), into
+// out[0..k), for 1 <= k <= min(n, kSelectMax) (one block; keys and vals unchanged).
+constexpr int kSelectMax = 2048;
+int select_smallest(const unsigned long long* keys, const int* vals, int n, int k, int* out, cudaStream_t s);
 int radix_sort_pairs(unsigned long long* keys, int* vals, unsigned long long* tmp_keys, int* tmp_vals, int n,
                      int begin_bit, int end_bit, cudaStream_t s);
 // one propagation on device bounds lb/ub (modified in place); round 0 holds every row, or the
@@ -154,6 +158,19 @@ int launch_propagate(mip_problem* p, double* lb, double* ub, const int* w0, int 
                      double theta, int max_rounds, int64_t* trace, cudaStream_t s,
                      const int* w0v = nullptr, const int* w0v_len = nullptr, int ninst = 1,
                      const int* row_off = nullptr, const int* col_off = nullptr);
+// Device-driven one-variable fixings of fix_and_propagate over the instance pair `tw` (two
+// copies of a problem with n0 variables): for each variable of queue[0..qlen) still unfixed in
+// cur (ordered keys, updated in place), the two candidates propagate and the first feasible
+// one becomes cur; stops after the first variable whose candidates are both infeasible.  The
+// pair's key buffers must hold [cur, cur] on entry and hold it again on exit.  vdirty (2 n0,
+// zero or older stamps), dirty (2 n0) and words (4) are scratch; out is device memory.
+struct FpSingleOut {
+    long long bulks, bp_runs, nnz_updates, fixed;
+    int infeasible, error, pad0, pad1;
+};
+int launch_fp_single(mip_problem* tw, int n0, longlong2* cur, const int* queue, int qlen, const double* x,
+                     const double* up_prob, unsigned long long seed, unsigned long long bulk0, double theta,
+                     int max_rounds, int* vdirty, int* dirty, int* words, FpSingleOut* out, cudaStream_t s);
 constexpr int kMaxInstances = 1024;
 
 }  // namespace gpubp

@@ -1,11 +1,14 @@
 // Bulk fix-and-propagate rounding (Section 2.3, Algorithm 1): fix_and_propagate.
 //
 // The loop itself is sequential (every bulk depends on the previous result), so the host
-// drives it and reads a few words per bulk for its control decisions; every step on the data
-// runs in kernels: the list of unfixed variables, the implied-slack sums and the stable radix
-// sorts, the counter-based draws, the probing-cache conflict filter, the start boxes of the
-// two candidate vectors, their propagations (the persistent engine, round 0 = rows of the
-// variables the vector changes) and the final rounding.
+// drives the bulks and reads a few words per bulk for its control decisions; every step on the
+// data runs in kernels: the list of unfixed variables, the implied-slack sums, the selection of
+// the bulk (the first entries of the stable implied-slack order, selected, not sorted in full),
+// the counter-based draws, the probing-cache conflict filter, the start boxes of the two
+// candidate vectors, their propagations (the persistent engine, round 0 = rows of the variables
+// the vector changes) and the final rounding.  The retry of a failed bulk one variable at a
+// time runs on the device as a whole (without a probing cache): one persistent launch keeps
+// the bounds as ordered keys and copies back only the variables each propagation changed.
 //
 // Random draws: splitmix64 (Steele, Lea, Flood, OOPSLA 2014) chained over (seed, bulk,
 // variable, draw); the 53 high bits give a uniform double in [0, 1).
@@ -15,38 +18,9 @@
 #include <vector>
 
 #include "bp_host.h"
+#include "fp_draw.cuh"
 
 namespace gpubp {
-
-__device__ __forceinline__ unsigned long long sm64(unsigned long long z) {
-    z += 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
-__device__ __forceinline__ double uniform01(unsigned long long seed, unsigned long long bulk, unsigned long long var,
-                                            unsigned long long draw) {
-    unsigned long long h = sm64(seed);
-    h = sm64(h ^ bulk);
-    h = sm64(h ^ var);
-    h = sm64(h ^ draw);
-    return __dmul_rn(__ull2double_rn(h >> 11), 1.0 / 9007199254740992.0);
-}
-
-__device__ __forceinline__ double clampd(double x, double l, double u) { return x < l ? l : (x > u ? u : x); }
-
-__device__ __forceinline__ double draw_value(double x, unsigned long long seed, unsigned long long bulk, int j, int d,
-                                             const double* up_prob) {
-    const double fl = floor(x);
-    const double f = __dsub_rn(x, fl);
-    if (f == 0.0) return x;
-    double pup;
-    if (f <= 0.25) pup = 0.0;
-    else if (f >= 0.75) pup = 1.0;
-    else pup = up_prob ? up_prob[j] : __ddiv_rn(__dsub_rn(f, 0.25), 0.5);
-    return uniform01(seed, bulk, (unsigned long long)j, (unsigned long long)d) < pup ? __dadd_rn(fl, 1.0) : fl;
-}
 
 // radix key of a double, ascending (descending when desc)
 __device__ __forceinline__ unsigned long long fp_sort_key(double d, bool desc) {
@@ -361,7 +335,30 @@ struct FpCtl {
     int kept[2];
     int ucnt[2];      // unfixed integer variables under each candidate's propagated bounds
     bp_result res[2];
+    FpSingleOut single;   // counters of a device-driven run of one-variable bulks
 };
+
+// The current bounds as ordered keys (cur) and in both copies of both key buffers of the
+// instance pair: the state the device-driven one-variable bulks start from.
+__global__ void k_keys_init(int n, const unsigned char* is_int, const double* l, const double* u, longlong2* cur,
+                            longlong2* bk0, longlong2* bk1) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const longlong2 k = normalized_keys(l[j], u[j], is_int[j] != 0);
+        cur[j] = k;
+        bk0[j] = k;
+        bk0[(size_t)n + j] = k;
+        bk1[j] = k;
+        bk1[(size_t)n + j] = k;
+    }
+}
+
+__global__ void k_keys_out(int n, const longlong2* cur, double* l, double* u) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const longlong2 k = cur[j];
+        l[j] = kdec(k.x);
+        u[j] = kdec(k.y);
+    }
+}
 
 // Blocks of row c (blockIdx.y) count the integer variables left unfixed by candidate c (bounds
 // l + c n, u + c n) into out[c], zeroed by k_fill_pair: the next bulk's unfixed count, read with
@@ -456,6 +453,9 @@ extern "C" int fix_and_propagate(mip_problem* p, const double* x, const double* 
     double *Bl, *Bu, *cl[2], *cu[2], *v[2], *rmin, *L4, *U4;
     int *flag, *pos, *ivars, *order, *work, *twork, *rninf, *dlist, *dcnt, *pair_of = nullptr, *total;
     unsigned long long *keys, *tkeys;
+    longlong2* curk = nullptr;     // device-driven one-variable bulks (allocated on first use)
+    int *vdirty = nullptr, *dirtyl = nullptr, *words = nullptr;
+    FpSingleOut* sout = nullptr;
     FpCtl* dctl;
     FpCtl* hctl = nullptr;
 #define FP_ALLOC(ptr, cnt)                      \
@@ -599,7 +599,13 @@ extern "C" int fix_and_propagate(mip_problem* p, const double* x, const double* 
             if (bsize > 1 && !prm.order_score) {
                 if (p->m) k_row_act<<<gridn((long long)p->m * 32), 256, 0, s>>>(p->dp, Bl, Bu, rmin, rninf);
                 k_implied_slack<<<gridn(nun), 256, 0, s>>>(p->dp, nun, work, rmin, rninf, keys);
-                FP_TRY(radix_sort_pairs(keys, work, tkeys, twork, nun, 0, 64, s));
+                if (bsize <= kSelectMax) {
+                    // only the bulk is needed: the first bsize of the stable sort, selected
+                    FP_TRY(select_smallest(keys, work, nun, (int)bsize, twork, s));
+                    bulk = twork;
+                } else {
+                    FP_TRY(radix_sort_pairs(keys, work, tkeys, twork, nun, 0, 64, s));
+                }
             }
             single = bsize == 1;
         }
@@ -653,6 +659,36 @@ extern "C" int fix_and_propagate(mip_problem* p, const double* x, const double* 
             Bu = U4 + (size_t)cur * n;
             next_nun = hctl->ucnt[pick];
             have_nun = nint > 0;
+        } else if (!single && !use_cache) {
+            // recovery on the device: the failed bulk's variables one at a time, in one launch
+            result->recoveries++;
+            if (!curk) {
+                FP_TRY(alloc(&curk, (size_t)n));
+                FP_TRY(alloc(&vdirty, 2 * (size_t)n));
+                FP_TRY(alloc(&dirtyl, 2 * (size_t)n));
+                FP_TRY(alloc(&words, 4));
+                FP_TRY(alloc(&sout, 1));
+            }
+            // cleared for every run: a plain propagation launch in between may have restarted the
+            // stamps, which this array's entries are compared with
+            FP_CUDA(cudaMemsetAsync(vdirty, 0, sizeof(int) * 2 * (size_t)n, s));
+            k_keys_init<<<gridn(n), 256, 0, s>>>(n, p->dp.is_int, Bl, Bu, curk, tw->w.bkey[0], tw->w.bkey[1]);
+            FP_CUDA(cudaGetLastError());
+            FP_TRY(launch_fp_single(tw, n, curk, bulk, (int)bsize, x, prm.up_prob, prm.seed, bulk_index, prm.theta,
+                                    prm.max_rounds, vdirty, dirtyl, words, sout, s));
+            k_keys_out<<<gridn(n), 256, 0, s>>>(n, curk, Bl, Bu);
+            FP_CUDA(cudaGetLastError());
+            FP_CUDA(cudaMemcpyAsync(&hctl->single, sout, sizeof(FpSingleOut), cudaMemcpyDeviceToHost, s));
+            FP_CUDA(cudaStreamSynchronize(s));
+            const FpSingleOut& so = hctl->single;
+            if (so.error) return fail(so.error);
+            result->bulks += so.bulks;
+            bulk_index += (unsigned long long)so.bulks;
+            result->bp_runs += so.bp_runs;
+            result->nnz_updates += so.nnz_updates;
+            result->fixed_by_choice += so.fixed;
+            if (so.infeasible) rounding_infeasible = true;
+            have_nun = false;
         } else if (!single) {
             recq.resize((size_t)bsize);
             FP_CUDA(cudaMemcpyAsync(recq.data(), bulk, sizeof(int) * bsize, cudaMemcpyDeviceToHost, s));

@@ -117,4 +117,162 @@ int radix_sort_pairs(unsigned long long* keys, int* vals, unsigned long long* tm
     return BP_OK;
 }
 
+// ---------------------------------------------------------------- selection of the k smallest
+// The first k entries of the stable sort of (key, value) pairs, without sorting the rest: an
+// element's rank key is the 96-bit composite (key, position), unique, so the k smallest
+// composites are exactly the stable sort's first k.  One block: a most-significant-digit radix
+// select (12 digits of 8 bits: the key's 8 bytes, then the position's 4) finds the k-th smallest
+// composite, the candidates sharing the prefix move to shared memory once few enough remain,
+// then the k selected elements are gathered and sorted by their composite (bitonic network in
+// shared memory).
+constexpr int kSelThreads = 1024;
+
+__device__ __forceinline__ int sel_digit(unsigned long long key, unsigned idx, int d) {
+    return d < 8 ? (int)((key >> (56 - 8 * d)) & 0xff) : (int)((idx >> (24 - 8 * (d - 8))) & 0xff);
+}
+
+// -1, 0, 1: the composite's first `nd` digits below, equal to or above the prefix (pk, pi)
+__device__ __forceinline__ int sel_cmp(unsigned long long key, unsigned idx, int nd, unsigned long long pk,
+                                       unsigned pi) {
+    if (nd <= 0) return 0;
+    const int kb = nd < 8 ? nd : 8;
+    const unsigned long long a = kb == 8 ? key : key >> (64 - 8 * kb), b = kb == 8 ? pk : pk >> (64 - 8 * kb);
+    if (a != b) return a < b ? -1 : 1;
+    if (nd <= 8) return 0;
+    const int ib = nd - 8;
+    const unsigned c = ib == 4 ? idx : idx >> (32 - 8 * ib), e = ib == 4 ? pi : pi >> (32 - 8 * ib);
+    return c == e ? 0 : (c < e ? -1 : 1);
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_select_smallest(const unsigned long long* keys, const int* vals,
+                                                                 int n, int k, int* out) {
+    __shared__ unsigned long long ck[kSelectMax];
+    __shared__ unsigned ci[kSelectMax];
+    __shared__ int hist[256];
+    __shared__ int s_digit, s_kk, s_nc, s_pos;
+    unsigned long long pk = 0;
+    unsigned pi = 0;
+    int kk = k;          // rank of the k-th smallest among the elements sharing the prefix
+    bool shared_set = false;
+    int nc = n;          // elements sharing the prefix
+    int nd = 0;          // digits of the prefix
+    while (nd < 12 && nc != kk) {
+        for (int i = threadIdx.x; i < 256; i += kSelThreads) hist[i] = 0;
+        __syncthreads();
+        if (shared_set) {
+            for (int i = threadIdx.x; i < nc; i += kSelThreads) atomicAdd(&hist[sel_digit(ck[i], ci[i], nd)], 1);
+        } else {
+            for (int i = threadIdx.x; i < n; i += kSelThreads) {
+                const unsigned long long key = keys[i];
+                if (sel_cmp(key, (unsigned)i, nd, pk, pi) == 0) atomicAdd(&hist[sel_digit(key, (unsigned)i, nd)], 1);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int below = 0, g = 0;
+            while (below + hist[g] < kk) below += hist[g++];
+            s_digit = g;
+            s_kk = kk - below;
+            s_nc = hist[g];
+        }
+        __syncthreads();
+        const int g = s_digit;
+        kk = s_kk;
+        const int nc_new = s_nc;
+        if (nd < 8) pk |= (unsigned long long)g << (56 - 8 * nd);
+        else pi |= (unsigned)g << (24 - 8 * (nd - 8));
+        ++nd;
+        __syncthreads();
+        if (shared_set) {
+            // keep the candidates with the new digit (order does not matter: composites are unique)
+            if (threadIdx.x == 0) s_pos = 0;
+            __syncthreads();
+            unsigned long long mk[(kSelectMax + kSelThreads - 1) / kSelThreads];
+            unsigned mi[(kSelectMax + kSelThreads - 1) / kSelThreads];
+            int mine = 0;
+            for (int i = threadIdx.x; i < nc; i += kSelThreads)
+                if (sel_digit(ck[i], ci[i], nd - 1) == g) {
+                    mk[mine] = ck[i];
+                    mi[mine] = ci[i];
+                    ++mine;
+                }
+            __syncthreads();
+            for (int q = 0; q < mine; ++q) {
+                const int p = atomicAdd(&s_pos, 1);
+                ck[p] = mk[q];
+                ci[p] = mi[q];
+            }
+        } else if (nc_new <= kSelectMax) {
+            if (threadIdx.x == 0) s_pos = 0;
+            __syncthreads();
+            for (int i = threadIdx.x; i < n; i += kSelThreads) {
+                const unsigned long long key = keys[i];
+                if (sel_cmp(key, (unsigned)i, nd, pk, pi) == 0) {
+                    const int p = atomicAdd(&s_pos, 1);
+                    ck[p] = key;
+                    ci[p] = (unsigned)i;
+                }
+            }
+            shared_set = true;
+        }
+        nc = nc_new;
+        __syncthreads();
+    }
+    // the selected elements: first `nd` digits at or below the prefix (exactly k of them)
+    if (threadIdx.x == 0) s_pos = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += kSelThreads) {
+        const unsigned long long key = keys[i];
+        if (sel_cmp(key, (unsigned)i, nd, pk, pi) <= 0) {
+            const int p = atomicAdd(&s_pos, 1);
+            if (p < kSelectMax) {
+                ck[p] = key;
+                ci[p] = (unsigned)i;
+            }
+        }
+    }
+    __syncthreads();
+    int np2 = 1;
+    while (np2 < k) np2 <<= 1;
+    for (int i = k + threadIdx.x; i < np2; i += kSelThreads) {
+        ck[i] = ~0ull;
+        ci[i] = ~0u;
+    }
+    __syncthreads();
+    // bitonic sort, ascending by (key, position)
+    for (int size = 2; size <= np2; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < np2; i += kSelThreads) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const bool up = (i & size) == 0;
+                    const unsigned long long a = ck[i], b = ck[j];
+                    const unsigned ia = ci[i], ib = ci[j];
+                    const bool gt = a > b || (a == b && ia > ib);
+                    if (gt == up) {
+                        ck[i] = b;
+                        ck[j] = a;
+                        ci[i] = ib;
+                        ci[j] = ia;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < k; i += kSelThreads) out[i] = vals[ci[i]];
+}
+
+// out[0..k) = the values of the first k pairs of the stable ascending sort of (keys, vals)[0..n),
+// for 1 <= k <= min(n, kSelectMax); keys and vals are not modified.
+int select_smallest(const unsigned long long* keys, const int* vals, int n, int k, int* out, cudaStream_t s) {
+    if (k < 1 || k > n || k > kSelectMax) {
+        set_error("select_smallest: k out of range");
+        return BP_ERR_INVALID;
+    }
+    k_select_smallest<<<1, kSelThreads, 0, s>>>(keys, vals, n, k, out);
+    BP_CUDA_TRY(cudaGetLastError());
+    return BP_OK;
+}
+
 }  // namespace gpubp

@@ -192,3 +192,49 @@ def test_final_check_refutes_an_incremental_verdict(pkg):
                         np.array([1, 1, 0, 0]))
     r = _check(p, np.array([0.8, 0.8, 50.0, 0.02]), seed=1)
     assert (r["status"], r["refuted"], r["bulks"], r["bp_runs"]) == (1, 1, 2, 5)
+
+
+RECOVERY = [(3000, 1, False), (3001, 1, True), (3004, 2, False), (3005, 1, True)]
+
+
+@pytest.mark.parametrize("inst,seed,learned", RECOVERY, ids=[f"i{r[0]}-s{r[1]}-{'up' if r[2] else 'plain'}"
+                                                             for r in RECOVERY])
+def test_recovery_on_device_parity(pkg, inst, seed, learned):
+    """Runs with several failed bulks (Algorithm 1's recovery: the failed bulk's variables one at
+    a time, each with the drawn value and the other rounding) on 100k-nonzero rounding
+    instances; without a probing cache the one-variable bulks run in one device-driven launch
+    per recovery.  With and without given up-probabilities (which replace the draw's band), the
+    result must equal the oracle's: every count, the integer values, and the continuous values
+    within 1e-9 relative (the oracle reports no fragile decision)."""
+    p, x = synth.rounding_instance(inst, 100_000, eq_fraction=0.01)
+    kw = dict(seed=seed, bulk_rule=1, fraction=0.01)
+    if learned:
+        kw["up_prob"] = np.random.default_rng((inst - 3000) * 10 + seed).uniform(0, 1, p.n)
+    ox, orr = oracle.Problem(p).fix_and_propagate(x, p.lb, p.ub, **kw)
+    assert orr["fragile"] == 0 and orr["recoveries"] > 0, orr
+    gx, gr = _gpu_fp(pkg, p, x, **kw)
+    for k in KEYS:
+        assert gr[k] == orr[k], (k, gr, orr)
+    ints = p.is_int == 1
+    np.testing.assert_array_equal(gx[ints], ox[ints])
+    np.testing.assert_allclose(gx[~ints], ox[~ints], rtol=1e-9, atol=1e-9)
+
+
+def test_recovery_ending_infeasible_parity(pkg):
+    """A run whose recovery meets a variable with both values infeasible (the rounding fails,
+    status 1):
+    20% equality pairs at 100k nonzeros.  Same counts and output as the oracle."""
+    for inst in range(1000, 1012):
+        p, x = synth.rounding_instance(inst, 100_000)
+        ox, orr = oracle.Problem(p).fix_and_propagate(x, p.lb, p.ub, seed=1, bulk_rule=1, fraction=0.01)
+        if orr["status"] == 1 and orr["recoveries"] > 0 and orr["refuted"] == 0 \
+                and orr["fragile"] == 0:
+            break
+    else:
+        pytest.fail("no instance of the set ends infeasible in a recovery")
+    gx, gr = _gpu_fp(pkg, p, x, seed=1, bulk_rule=1, fraction=0.01)
+    for k in KEYS:
+        assert gr[k] == orr[k], (k, gr, orr)
+    ints = p.is_int == 1
+    np.testing.assert_array_equal(gx[ints], ox[ints])
+    np.testing.assert_allclose(gx[~ints], ox[~ints], rtol=1e-9, atol=1e-9)
