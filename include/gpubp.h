@@ -257,7 +257,11 @@ typedef struct {
  * Returns BP_OK, BP_ERR_CAPACITY (cache->needed holds the required entry count; the status,
  * rounds, nnz_updates and offsets arrays are complete), BP_ERR_INVALID (also for a variable
  * index outside [0, n): the kernel skips such a pair and flags it; the other arrays are then
- * incomplete).  The call synchronises the stream once, at its end: the copy into the cache is
+ * incomplete) or BP_ERR_TIMEOUT (a bounded device wait ran out).  Scratch: each block of the
+ * launch keeps the variables a pair touches in a table of 2,048 slots (about 0.2 MB per block
+ * plus 16 bytes per row); a pair whose branches touch more variables than that is re-run by
+ * the blocks that own a dense scratch (104 bytes per variable each, at most 1 GB in total, at
+ * least one).  The call synchronises the stream once, at its end: the copy into the cache is
  * launched before the host knows the entry count and checks the capacity on the device, and
  * the count and the index flag are read back together (it is bp_probe_batch_async followed by
  * that read).
@@ -272,7 +276,8 @@ int bp_probe_batch(mip_problem *p, const double *root_lb, const double *root_ub,
  * cache) can be captured in a CUDA graph and replayed.  Arguments as for bp_probe_batch, plus
  * status_dev: caller-owned DEVICE int64[2] written by the call's last operation: [0] the
  * entries the batch needs (the cache holds min(needed, cache->cap) of them; offsets are always
- * complete), [1] nonzero when a variable index was outside [0, n) (that pair was skipped).  The
+ * complete), [1] 1 when a variable index was outside [0, n) (that pair was skipped), 2 when a
+ * bounded device wait ran out (the batch's results are not valid; BP_ERR_TIMEOUT).  The
  * caller reads them after the stream work (a graph replay) completes; cache->needed is not set.
  * The handle's probing scratch grows on the first call for a given pair count and capacity:
  * make one call of that size before capturing (inside a capture a call that would have to

@@ -319,3 +319,37 @@ def test_probe_index_out_of_range(pkg):
         assert e.value.code == pkg.BP_ERR_INVALID
     c = prob.probe_batch(dl, du, torch.tensor(var, device="cuda"), torch.tensor(boxes, device="cuda"))
     _compare(p, {k: x.cpu().numpy() for k, x in c.items()}, P.probe_batch(rl, ru, var, boxes))
+
+
+def _stars(sizes):
+    """Binary stars: hub h with spokes s, one row x_h - x_s <= 0 per spoke (the hub at 1 forces
+    every spoke to 1 in one round)."""
+    n = len(sizes) + sum(sizes)
+    rows, hubs, j = [], [], len(sizes)
+    for h, size in enumerate(sizes):
+        hubs.append(h)
+        for s in range(j, j + size):
+            rows.append((h, s))
+        j += size
+    m = len(rows)
+    col = np.array([c for r in rows for c in r], dtype=np.int32)
+    val = np.tile(np.array([1.0, -1.0]), m)
+    return synth.Milp(m, n, np.arange(0, 2 * m + 1, 2, dtype=np.int64), col, val, np.zeros(m), np.zeros(n),
+                      np.ones(n), np.ones(n, dtype=np.uint8), np.zeros(n)), hubs
+
+
+def test_probes_beyond_the_sparse_table(pkg):
+    """Pairs whose branches touch more variables than a block's sparse table holds (4,096 slots:
+    a hub fixing 12,000 or 4,500 spokes) go to the dense pass; the others stay in the sparse
+    pass.  Both together must equal the oracle: statuses, rounds, work and every implied bound."""
+    p, hubs = _stars([12_000, 4_500, 3_000, 1_000, 50, 5])
+    P = oracle.Problem(p)
+    rl, ru = p.lb.copy(), p.ub.copy()
+    spokes = np.random.default_rng(4).choice(np.arange(len(hubs), p.n), 300, replace=False)
+    var = np.concatenate([np.array(hubs), spokes]).astype(np.int32)
+    boxes = np.array([oracle.probe_split(1, 0.0, 1.0) for _ in var], dtype=np.float64).reshape(-1, 4)
+    o = P.probe_batch(rl, ru, var, boxes)
+    g = _gpu_probe(pkg, p, rl, ru, var, boxes)
+    _compare(p, g, o)
+    counts = np.diff(o["offsets"])
+    assert counts[1] == 12_001 and counts[3] == 4_501   # the up branches: the hub and every spoke
