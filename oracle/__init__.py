@@ -100,13 +100,14 @@ def lib():
 class FpParams(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("bulk_rule", C.c_int32), ("fraction", C.c_double),
                 ("last_single", C.c_int32), ("theta", C.c_double), ("max_rounds", C.c_int32),
-                ("order_score", C.POINTER(C.c_double)), ("up_prob", C.POINTER(C.c_double))]
+                ("order_score", C.POINTER(C.c_double)), ("up_prob", C.POINTER(C.c_double)),
+                ("repair_max", C.c_int32), ("repair_cycles", C.c_int32)]
 
 
 class FpResult(C.Structure):
     _fields_ = [("status", C.c_int32), ("bulks", C.c_int32), ("bp_runs", C.c_int32), ("recoveries", C.c_int32),
                 ("fixed_by_choice", C.c_int32), ("refuted", C.c_int32), ("nnz_updates", C.c_int64),
-                ("fragile", C.c_int64)]
+                ("fragile", C.c_int64), ("repairs", C.c_int32), ("repair_runs", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -123,6 +124,10 @@ def _bind_fp(L):
     L.orc_fix_and_propagate.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                         C.POINTER(C.c_double), C.POINTER(Cache), C.POINTER(FpParams),
                                         C.POINTER(C.c_double), C.POINTER(FpResult)]
+    L.orc_repair_step.restype = C.c_int32
+    L.orc_repair_step.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int32, C.c_int32,
+                                  C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_uint8),
+                                  C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     L.orc_implied_slack.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                     C.POINTER(C.c_double)]
     L.orc_uniform.restype = C.c_double
@@ -251,9 +256,10 @@ class Problem:
 
 
 def _fix_and_propagate(self, x, lb, ub, seed=1, bulk_rule=0, fraction=0.01, last_single=36, theta=1e-3,
-                       max_rounds=10000, cache=None, order_score=None, up_prob=None):
+                       max_rounds=10000, cache=None, order_score=None, up_prob=None, repair_max=0, repair_cycles=8):
     """Fix-and-propagate (Algorithm 1); cache: dict from probe_batch plus 'pairs' and 'boxes'.
-    Returns (x_out, result dict)."""
+    repair_max > 0 turns the repair on (at most that many repairs per run, each at most
+    repair_cycles propagations; not with a cache).  Returns (x_out, result dict)."""
     x = np.ascontiguousarray(x, dtype=np.float64)
     lb = np.ascontiguousarray(lb, dtype=np.float64)
     ub = np.ascontiguousarray(ub, dtype=np.float64)
@@ -261,7 +267,8 @@ def _fix_and_propagate(self, x, lb, ub, seed=1, bulk_rule=0, fraction=0.01, last
     osc = None if order_score is None else np.ascontiguousarray(order_score, dtype=np.float64)
     upp = None if up_prob is None else np.ascontiguousarray(up_prob, dtype=np.float64)
     prm = FpParams(seed, bulk_rule, fraction, last_single, theta, max_rounds,
-                   None if osc is None else _p(osc, C.c_double), None if upp is None else _p(upp, C.c_double))
+                   None if osc is None else _p(osc, C.c_double), None if upp is None else _p(upp, C.c_double),
+                   int(repair_max), int(repair_cycles))
     res = FpResult()
     cp = None
     keep = []
@@ -276,14 +283,35 @@ def _fix_and_propagate(self, x, lb, ub, seed=1, bulk_rule=0, fraction=0.01, last
         keep = arrs
         cp = Cache(len(arrs[0]), _p(arrs[0], C.c_int32), _p(arrs[1], C.c_double), _p(arrs[2], C.c_int32),
                    _p(arrs[3], C.c_int64), _p(arrs[4], C.c_int32), _p(arrs[5], C.c_double), _p(arrs[6], C.c_double))
-    lib().orc_fix_and_propagate(self.h, _p(x, C.c_double), _p(lb, C.c_double), _p(ub, C.c_double),
-                                C.byref(cp) if cp is not None else None, C.byref(prm), _p(out, C.c_double),
-                                C.byref(res))
+    rc = lib().orc_fix_and_propagate(self.h, _p(x, C.c_double), _p(lb, C.c_double), _p(ub, C.c_double),
+                                     C.byref(cp) if cp is not None else None, C.byref(prm), _p(out, C.c_double),
+                                     C.byref(res))
     del keep
+    if rc != 0:
+        raise ValueError("the repair is defined without a probing cache")
     return out, res.as_dict()
 
 
 Problem.fix_and_propagate = _fix_and_propagate
+
+
+def _repair_step(self, l, u, row, var, lb, ub, chosen, cval):
+    """One repair step (see fp_oracle.c) after an infeasible propagation with final bounds (l, u),
+    first infeasible row `row` (or -1) and first crossing variable `var` (or -1).  Returns
+    (moved variable or -1, new cval, fragile count)."""
+    l = np.ascontiguousarray(l, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    lb = np.ascontiguousarray(lb, dtype=np.float64)
+    ub = np.ascontiguousarray(ub, dtype=np.float64)
+    ch = np.ascontiguousarray(chosen, dtype=np.uint8)
+    cv = np.array(cval, dtype=np.float64)
+    fr = C.c_int64(0)
+    i = lib().orc_repair_step(self.h, _p(l, C.c_double), _p(u, C.c_double), int(row), int(var), _p(lb, C.c_double),
+                              _p(ub, C.c_double), _p(ch, C.c_uint8), _p(cv, C.c_double), C.byref(fr))
+    return int(i), cv, int(fr.value)
+
+
+Problem.repair_step = _repair_step
 
 
 def _implied_slack(self, lb, ub):

@@ -11,7 +11,7 @@
  *     l <= x <= u, x_i integer for integer variables),
  *   - Section 2.1 (minimal activity L_min and the bound update formulas),
  *   - Section 2.2 (probe split of integer domains, probe priority keys),
- * with the readings listed in the design notes for every point the paper leaves open:
+ * with a stated reading for every point the paper leaves open:
  *   - only <= rows; equalities come as two rows;
  *   - an infinite bound is never summed: it is counted (ninf) and a residual activity
  *     is finite only when ninf == 0, or ninf == 1 and the variable is the infinite one;

@@ -1,11 +1,11 @@
 /*
  * Oracle of bulk fix-and-propagate rounding (Section 2.3, Algorithm 1 "Bound Propagation
- * Rounding", repair and LP polish off as in the paper's experiments).
+ * Rounding"; LP polish off, repair optional and off by default, as in the paper's experiments).
  *
  * TEST INFRASTRUCTURE ONLY: called by the tests and the benchmark's CPU leg, never by the
  * library.  Plain sequential C over IEEE double (-ffp-contract=off).
  *
- * Steps, in the paper's order, with the readings of the design notes where the paper is open:
+ * Steps, in the paper's order, with a stated reading wherever the paper leaves a point open:
  *  1. propagate the start bounds (every row);
  *  2. initial sort of the integer variables (Section 2.3): binary (u - l <= 1) before ternary
  *     (u - l = 2) before the rest, then ascending fractionality |x - round(x)|, then index;
@@ -26,9 +26,12 @@
  *     - both candidate vectors are propagated from the rows of the variables whose bounds
  *       they change; the first feasible result is kept (probe 0 first);
  *     - both infeasible: a bulk's variables are retried one by one (recovery); a single
- *       variable that fails both ways ends the search (repair disabled, Section 3): the
- *       remaining integer variables are rounded to the nearest value inside their bounds
- *       without propagation and the result is INFEASIBLE.
+ *       variable that fails both ways ends the search (repair disabled, as in the paper's
+ *       experiments, Section 3): the remaining integer variables are rounded to the nearest
+ *       value inside their bounds without propagation and the result is INFEASIBLE.  With
+ *       repair on (repair_max > 0, no probing cache) it first tries up to repair_max times in
+ *       the run to shift earlier fixings until a propagation from the start bounds is feasible
+ *       (the repair branch of Algorithm 1; see repair() for the reading).
  *  4. FEASIBLE when every integer variable is fixed, the last propagation was feasible, and a
  *     propagation of the start bounds with every integer variable fixed at its value is not
  *     infeasible either (`refuted` otherwise: under the threshold of Section 2.1 an incremental
@@ -72,6 +75,8 @@ typedef struct {
     const double *order_score;  /* optional: order by class, descending score, fractionality, index; no
                                  * per-bulk implied-slack sort */
     const double *up_prob;      /* optional: P(up) for fractions strictly inside (0.25, 0.75) */
+    int32_t repair_max;         /* repairs a run may attempt (0: repair off, as in the paper's experiments) */
+    int32_t repair_cycles;      /* propagations one repair may run */
 } orc_fp_params;
 
 typedef struct {
@@ -83,6 +88,8 @@ typedef struct {
     int32_t refuted;         /* every integer fixed, but the final check from the start bounds failed */
     int64_t nnz_updates;
     int64_t fragile;
+    int32_t repairs;         /* repairs that ended with a feasible propagation */
+    int32_t repair_runs;     /* propagations run by repairs (also counted in bp_runs and nnz_updates) */
 } orc_fp_result;
 
 /* probing cache in the layout of bp_probe_batch */
@@ -291,11 +298,163 @@ static int64_t cache_branch(const orc_cache *c, const int32_t *pair_of, int32_t 
 
 static int var_cross(int is_i, double l, double u) { return is_i ? l > u : l > u + FP_TOL; }
 
+/* Minimal activity of row k under (l, u): finite part (row order, separate multiply and add,
+ * as in bp_oracle.c), number of infinite contributions, and the error bound of the finite part
+ * (twice the Higham bound plus the continuous bounds' uncertainty; 0 when every term and
+ * partial sum is an integer below 2^50, which makes the sum exact in any order). */
+static double row_min_activity(const orc_problem *p, int32_t k, const double *l, const double *u, const double *dl,
+                               const double *du, int32_t *ninf, double *err)
+{
+    const int64_t beg = p->row_ptr[k], end = p->row_ptr[k + 1];
+    double minfin = 0.0, mag = fabs(p->g[k]), upstream = 0.0;
+    int exact = p->g[k] == floor(p->g[k]);
+    *ninf = 0;
+    for (int64_t q = beg; q < end; ++q) {
+        const double a = p->val[q];
+        const int32_t j = p->col[q];
+        const double b = (a > 0) ? l[j] : u[j];
+        if (isinf(b)) { (*ninf)++; continue; }
+        const double t = a * b;
+        minfin = minfin + t;
+        mag += fabs(t);
+        const double ub = dl ? fabs(a) * ((a > 0) ? dl[j] : du[j]) : 0.0;
+        upstream += ub;
+        if (a != floor(a) || b != floor(b) || ub != 0.0) exact = 0;
+    }
+    *err = (exact && mag < 1125899906842624.0) ? 0.0 : 2.0 * (fp_gam((double)(end - beg) + 2.0) * mag + upstream);
+    return minfin;
+}
+
+/* ceil(e / c) for e > 0, c > 0; exact when both are integers below 2^50 */
+static double ceil_div(double e, double c)
+{
+    double d = ceil(e / c);
+    if (e == floor(e) && c == floor(c)) {
+        while (d > 1.0 && (d - 1.0) * c >= e) d -= 1.0;
+        while (d * c < e) d += 1.0;
+    }
+    return d;
+}
+
+/* One repair step after an infeasible propagation whose final bounds are (l, u) (uncertainty dl,
+ * du): the infeasible constraint (row k0, or the smallest violated row of the crossing variable
+ * w0) and the move of one fixed variable, applied to cval.  Returns the moved variable, or -1
+ * when no fixed variable of the row can move.  Fragile decisions are added to *fragile. */
+static int32_t repair_step(const orc_problem *p, const double *l, const double *u, const double *dl, const double *du,
+                           int32_t k0, int32_t w0, const double *lb0, const double *ub0, const uint8_t *chosen,
+                           double *cval, int64_t *fragile)
+{
+    const double *tl = l, *tu = u, *tdl = dl, *tdu = du;
+    int32_t k = k0;
+    if (k < 0 && w0 >= 0) {
+        const int32_t w = w0;
+        for (int64_t s = p->col_ptr[w]; s < p->col_ptr[w + 1]; ++s) {
+            const int32_t kk = p->row_idx[s];
+            int32_t ninf;
+            double err;
+            const double mf = row_min_activity(p, kk, tl, tu, tdl, tdu, &ninf, &err);
+            const double gt = p->g[kk] + FP_TOL;
+            if (ninf || !isfinite(p->g[kk])) continue;
+            if (fabs(mf - gt) <= err && err > 0.0) (*fragile)++;
+            if (mf > gt && (k < 0 || kk < k)) k = kk;
+        }
+    }
+    if (k < 0) return -1;
+    int32_t ninf;
+    double err;
+    const double e = row_min_activity(p, k, tl, tu, tdl, tdu, &ninf, &err) - p->g[k];
+    if (ninf || !(e > 0.0)) return -1;
+    int32_t best = -1;
+    double best_r = 0.0, best_d = 0.0, best_a = 0.0;
+    for (int64_t q = p->row_ptr[k]; q < p->row_ptr[k + 1]; ++q) {
+        const int32_t i = p->col[q];
+        if (!chosen[i]) continue;
+        const double a = p->val[q], aa = fabs(a);
+        const double need = ceil_div(e, aa);
+        if (err > 0.0 && ceil((e - err) / aa) != ceil((e + err) / aa)) (*fragile)++;
+        const double room = a > 0 ? floor(cval[i] - lb0[i]) : floor(ub0[i] - cval[i]);   /* +inf when unbounded */
+        const double d = need < room ? need : room;
+        if (!(d > 0.0)) continue;
+        const double rr = aa * d;
+        if (rr > best_r || (rr == best_r && i < best)) {
+            best = i;
+            best_r = rr;
+            best_d = d;
+            best_a = a;
+        }
+    }
+    if (best < 0) return -1;
+    cval[best] = best_a > 0 ? cval[best] - best_d : cval[best] + best_d;
+    return best;
+}
+
+/* repair_step for the tests (dl, du may be NULL: exact bounds) */
+int32_t orc_repair_step(const orc_problem *p, const double *l, const double *u, int32_t k0, int32_t w0,
+                        const double *lb0, const double *ub0, const uint8_t *chosen, double *cval, int64_t *fragile)
+{
+    *fragile = 0;
+    return repair_step(p, l, u, NULL, NULL, k0, w0, lb0, ub0, chosen, cval, fragile);
+}
+
+/*
+ * Repair (Section 2.3, the repair branch of Algorithm 1; the paper describes it in words only,
+ * and this is the reading taken).
+ * Called when a one-variable bulk fails both ways, with the variable j and its drawn value v.
+ * Every variable fixed by choice so far (chosen, at cval) and j at v are taken as the fixings,
+ * and up to `repair_cycles` times:
+ *   - propagate the start bounds with the fixings; feasible: the repair succeeds and these
+ *     bounds become the current ones;
+ *   - else the infeasible constraint: the propagation's first infeasible row, or, when only a
+ *     crossing variable is reported, the smallest row of that variable whose minimal activity
+ *     under the propagation's final bounds exceeds g + tol;
+ *   - for each fixed variable i of that row a shift that alone makes it feasible: its value
+ *     moves against its coefficient by d_i = ceil((L_min - g) / |a_i|), at most down to its
+ *     start lower bound (a > 0) or up to its start upper bound (a < 0);
+ *   - the variable whose shift lowers the minimal activity most (|a_i| d_i, ties to the
+ *     smallest index) is shifted, and the next cycle propagates again from the start bounds.
+ * Fails when no variable of the row can move or the cycles run out.  Fragile decisions (the
+ * violation test and the shift size within the activity's error bound) are counted.
+ */
+static int repair(const orc_problem *p, const double *lb0, const double *ub0, uint8_t *chosen, double *cval,
+                  int32_t j, double v, const orc_fp_params *prm, double *l, double *u, double *dl, double *du,
+                  double *tl, double *tu, double *tdl, double *tdu, orc_fp_result *res)
+{
+    const int32_t n = p->n;
+    chosen[j] = 1;
+    cval[j] = v;
+    for (int32_t c = 0; c < prm->repair_cycles; ++c) {
+        memcpy(tl, lb0, sizeof(double) * (size_t)n);
+        memcpy(tu, ub0, sizeof(double) * (size_t)n);
+        memset(tdl, 0, sizeof(double) * (size_t)n);
+        memset(tdu, 0, sizeof(double) * (size_t)n);
+        for (int32_t i = 0; i < n; ++i)
+            if (chosen[i]) tl[i] = tu[i] = cval[i];
+        orc_bp_result r;
+        orc_bp(p, tl, tu, tdl, tdu, NULL, 0, prm->theta, prm->max_rounds, 0, &r, NULL, NULL);
+        res->bp_runs++;
+        res->repair_runs++;
+        res->nnz_updates += r.nnz_updates;
+        res->fragile += r.fragile;
+        if (r.status != ORC_INFEASIBLE) {
+            memcpy(l, tl, sizeof(double) * (size_t)n);
+            memcpy(u, tu, sizeof(double) * (size_t)n);
+            memcpy(dl, tdl, sizeof(double) * (size_t)n);
+            memcpy(du, tdu, sizeof(double) * (size_t)n);
+            return 1;
+        }
+        if (repair_step(p, tl, tu, tdl, tdu, r.first_infeasible_row, r.first_infeasible_var, lb0, ub0, chosen, cval,
+                        &res->fragile) < 0)
+            return 0;
+    }
+    return 0;
+}
+
 int orc_fix_and_propagate(const orc_problem *p, const double *x, const double *lb0, const double *ub0,
                           const orc_cache *cache, const orc_fp_params *prm, double *x_out, orc_fp_result *res)
 {
     const int32_t n = p->n;
     memset(res, 0, sizeof(*res));
+    if (cache && prm->repair_max > 0) return -1;   /* repair is defined without a probing cache */
     double *l = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
     double *u = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
     double *cl[2], *cu[2];
@@ -323,6 +482,13 @@ int orc_fix_and_propagate(const orc_problem *p, const double *x, const double *l
     val[0] = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
     val[1] = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
     int32_t *recq = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    /* fixings by choice (the repair's fixings) and, per candidate, which bulk fixings were kept */
+    uint8_t *chosen = (uint8_t *)calloc((size_t)(n ? n : 1), 1);
+    double *cval = (double *)calloc((size_t)(n ? n : 1), sizeof(double));
+    uint8_t *keptv[2];
+    keptv[0] = (uint8_t *)calloc((size_t)(n ? n : 1), 1);
+    keptv[1] = (uint8_t *)calloc((size_t)(n ? n : 1), 1);
+    int32_t repairs_tried = 0;
     int32_t *w0 = (int32_t *)malloc(sizeof(int32_t) * (size_t)(p->m ? p->m : 1));
     uint8_t *rowmark = (uint8_t *)calloc((size_t)(p->m ? p->m : 1), 1);
     int32_t *pair_of = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
@@ -418,6 +584,7 @@ int orc_fix_and_propagate(const orc_problem *p, const double *x, const double *l
             for (int64_t i = 0; i < bsize; ++i) {
                 const int32_t j = bulk[i];
                 const double v = val[c][j];
+                keptv[c][i] = 0;
                 if (!(v >= cl[c][j] && v <= cu[c][j])) continue;
                 const int64_t e = cache_branch(cache, pair_of, j, v);
                 int ok = 1;
@@ -432,6 +599,7 @@ int orc_fix_and_propagate(const orc_problem *p, const double *x, const double *l
                 }
                 if (!ok) continue;
                 kept[c]++;
+                keptv[c][i] = 1;
                 cl[c][j] = v;
                 cu[c][j] = v;
                 cdl[c][j] = cdu[c][j] = 0.0;
@@ -467,6 +635,11 @@ int orc_fix_and_propagate(const orc_problem *p, const double *x, const double *l
         const int pick = feasible[0] ? 0 : (feasible[1] ? 1 : -1);
         if (pick >= 0) {
             res->fixed_by_choice += kept[pick];
+            for (int64_t i = 0; i < bsize; ++i)
+                if (keptv[pick][i]) {
+                    chosen[bulk[i]] = 1;
+                    cval[bulk[i]] = val[pick][bulk[i]];
+                }
             memcpy(l, cl[pick], sizeof(double) * (size_t)n);
             memcpy(u, cu[pick], sizeof(double) * (size_t)n);
             memcpy(dl, cdl[pick], sizeof(double) * (size_t)n);
@@ -476,6 +649,14 @@ int orc_fix_and_propagate(const orc_problem *p, const double *x, const double *l
             nrec = bsize;
             rec_pos = 0;
             res->recoveries++;
+        } else if (repairs_tried < prm->repair_max) {
+            /* a single variable failing both ways: repair (off unless repair_max > 0) */
+            repairs_tried++;
+            if (repair(p, lb0, ub0, chosen, cval, bulk[0], val[0][bulk[0]], prm, l, u, dl, du, cl[0], cu[0], cdl[0],
+                       cdu[0], res))
+                res->repairs++;
+            else
+                rounding_infeasible = 1;
         } else {
             rounding_infeasible = 1;
         }
@@ -509,5 +690,6 @@ int orc_fix_and_propagate(const orc_problem *p, const double *x, const double *l
     for (int i = 0; i < 2; ++i) { free(cl[i]); free(cu[i]); free(val[i]); free(cdl[i]); free(cdu[i]); }
     free(l); free(u); free(order); free(work); free(tmp); free(cls); free(frac); free(S); free(E); free(dl); free(du);
     free(recq); free(w0); free(rowmark); free(pair_of);
+    free(chosen); free(cval); free(keptv[0]); free(keptv[1]);
     return 0;
 }

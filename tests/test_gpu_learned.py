@@ -7,7 +7,7 @@ instances the learned order and up probabilities are compared with the plain met
 same seeds.  A result counts as feasible only when the oracle verifies it: with the integer
 variables fixed to their values, the oracle's propagation from the original bounds must not
 find the problem infeasible, and (with SciPy) the continuous variables must have a completion
-satisfying every row (R19: a FEASIBLE verdict of fix-and-propagate is propagation-feasible,
+satisfying every row (a FEASIBLE verdict of fix-and-propagate is propagation-feasible,
 which an incremental propagation under the improvement threshold can report for a point that
 a fresh propagation refutes).  Where the oracle's own fix-and-propagate run from the same
 scores has no fragile decision, it must give the same result (integer values bit-exact,
