@@ -397,7 +397,10 @@ int bp_autotune(mip_problem *p, const double *lb, const double *ub, const bp_par
  *   implied-slack sort (NULL keeps the paper's order).
  * up_prob (DEVICE double[n] or NULL): when given, replaces the rounding distribution's
  *   probability of rounding up for fractions strictly between 0.25 and 0.75 (the random band);
- *   outside the band the nearest value is always drawn.  Propagation still judges every fix. */
+ *   outside the band the nearest value is always drawn.  Propagation still judges every fix.
+ * repair_max: repairs a run may attempt (Section 2.3, the repair branch of Algorithm 1); 0, the
+ *   default, turns the repair off, as in the paper's experiments.  Not with a probing cache.
+ * repair_cycles: propagations one repair may run (default 8). */
 typedef struct {
     uint64_t seed;
     int32_t bulk_rule;
@@ -405,9 +408,11 @@ typedef struct {
     double fraction;
     double theta;
     int32_t max_rounds;
-    int32_t reserved;
+    int32_t repair_max;
     const double *order_score;
     const double *up_prob;
+    int32_t repair_cycles;
+    int32_t reserved;
 } fp_params;
 
 /* A probing cache (bp_probe_batch's layout, all DEVICE arrays): the pairs' variables and
@@ -430,7 +435,8 @@ typedef struct {
  * fixings of the chosen vectors; refuted: 1 when every integer variable was fixed but the final
  * check (a propagation of the caller's bounds with the integer variables fixed) was infeasible,
  * so the status is FP_INFEASIBLE; nnz_updates: summed over the rounding's propagations (bp_runs;
- * the final check is not counted). */
+ * the final check is not counted); repairs: repairs that ended with a feasible propagation;
+ * repair_runs: propagations run by repairs (included in bp_runs and nnz_updates). */
 typedef struct {
     int32_t status;
     int32_t bulks;
@@ -439,13 +445,16 @@ typedef struct {
     int32_t fixed_by_choice;
     int32_t refuted;
     int64_t nnz_updates;
+    int32_t repairs;
+    int32_t repair_runs;
 } fp_result;
 
-void fp_params_default(fp_params *p);   /* seed 1, sqrt rule, last_single 36, fraction 0.01 */
+void fp_params_default(fp_params *p);   /* seed 1, sqrt rule, last_single 36, fraction 0.01, repair off
+                                          * (repair_max 0, repair_cycles 8) */
 
 /*
- * fix_and_propagate -- bulk rounding with bound propagation (Section 2.3, Algorithm 1;
- * repair and LP polish off, as in the paper's experiments).
+ * fix_and_propagate -- bulk rounding with bound propagation (Section 2.3, Algorithm 1; LP
+ * polish off; the repair optional and off by default, as in the paper's experiments).
  *
  * Propagates the start bounds, sorts the integer variables (binary, ternary, rest; then
  * fractionality of x), and fixes them in bulks: per bulk a stable implied-slack sort
@@ -455,6 +464,13 @@ void fp_params_default(fp_params *p);   /* seed 1, sqrt rule, last_single 36, fr
  * changes, and the first feasible result kept.  A bulk failing both ways is retried one
  * variable at a time; a single variable failing both ways ends the search and the remaining
  * integer variables are rounded to the nearest value inside their bounds (FP_INFEASIBLE).
+ * Repair (repair_max > 0): before giving up on such a variable, up to repair_cycles times,
+ * the caller's bounds are propagated with every fixing made by choice so far and the variable
+ * at its drawn value; if infeasible, the infeasible row (or, when only a crossing variable is
+ * reported, its smallest row whose minimal activity under the final bounds exceeds g + tol)
+ * is made feasible by moving the one fixed variable whose move lowers the minimal activity
+ * most: by ceil((L_min - g) / |a|) against its coefficient's sign, within the caller's bounds
+ * (ties to the smallest index).  A feasible propagation continues the rounding from its bounds.
  * Once every integer variable is fixed, one more propagation starts from the caller's bounds
  * with the integer variables at their values: under the continuous-bound threshold (Section
  * 2.1) the incremental propagations can stop short of a contradiction that this one reaches,

@@ -51,7 +51,8 @@ class ProbeApplyResult(C.Structure):
 class FpParams(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("bulk_rule", C.c_int32), ("last_single", C.c_int32),
                 ("fraction", C.c_double), ("theta", C.c_double), ("max_rounds", C.c_int32),
-                ("reserved", C.c_int32), ("order_score", C.c_void_p), ("up_prob", C.c_void_p)]
+                ("repair_max", C.c_int32), ("order_score", C.c_void_p), ("up_prob", C.c_void_p),
+                ("repair_cycles", C.c_int32), ("reserved", C.c_int32)]
 
 
 class FpCache(C.Structure):
@@ -62,7 +63,8 @@ class FpCache(C.Structure):
 
 class FpResult(C.Structure):
     _fields_ = [("status", C.c_int32), ("bulks", C.c_int32), ("bp_runs", C.c_int32), ("recoveries", C.c_int32),
-                ("fixed_by_choice", C.c_int32), ("refuted", C.c_int32), ("nnz_updates", C.c_int64)]
+                ("fixed_by_choice", C.c_int32), ("refuted", C.c_int32), ("nnz_updates", C.c_int64),
+                ("repairs", C.c_int32), ("repair_runs", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -357,15 +359,18 @@ Problem.probe_priority = _probe_priority
 
 
 def _fix_and_propagate(prob, x, lb, ub, seed=1, bulk_rule=0, fraction=0.01, last_single=36, theta=1e-3,
-                       max_rounds=10000, cache=None, order_score=None, up_prob=None, stream=None):
+                       max_rounds=10000, cache=None, order_score=None, up_prob=None, repair_max=0, repair_cycles=8,
+                       stream=None):
     """fix_and_propagate on device tensors (x, lb, ub float64).  cache: the dict returned by
-    probe_batch plus 'pairs' (int32 device) and 'boxes' (float64 device, P x 4).
+    probe_batch plus 'pairs' (int32 device) and 'boxes' (float64 device, P x 4).  repair_max > 0
+    turns the repair on (at most that many per run, each at most repair_cycles propagations).
     Returns (x_out device tensor, result dict)."""
     torch = _torch()
     prm = FpParams()
     lib().fp_params_default(C.byref(prm))
     prm.seed, prm.bulk_rule, prm.fraction, prm.last_single = int(seed), int(bulk_rule), float(fraction), int(last_single)
     prm.theta, prm.max_rounds = float(theta), int(max_rounds)
+    prm.repair_max, prm.repair_cycles = int(repair_max), int(repair_cycles)
     prm.order_score = order_score.data_ptr() if order_score is not None else None
     prm.up_prob = up_prob.data_ptr() if up_prob is not None else None
     fc = _fp_cache_struct(cache) if cache is not None else None

@@ -1085,6 +1085,8 @@ struct FpSingleArgs {
     unsigned long long seed, bulk0;
     int* words;                // [0..1] start list, [2] its length, [3] dirty count
     FpSingleOut* out;
+    unsigned char* chosen;     // or NULL: kept fixings are recorded (the repair's fixings by choice)
+    double* cval;
 };
 
 __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) fp_single_kernel(DevProblem P, BpArgs A, FpSingleArgs F) {
@@ -1105,7 +1107,8 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) fp_single_kernel(D
     }
     int base = __ldcg(A.stamp);
     long long bulks = 0, runs = 0, nnz = 0, fixed = 0;
-    int infeasible = 0;
+    int infeasible = 0, stop_q = -1, stop_j = -1;
+    __shared__ double s_val[2];   // block 0: the current variable's two candidate values
     __syncthreads();
     for (int q = 0; q < F.qlen; ++q) {
         if (base > (1 << 30)) {
@@ -1186,6 +1189,8 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) fp_single_kernel(D
                 const double vb = clampd(va == fl ? __dadd_rn(fl, 1.0) : fl, l, u);
                 const bool is_i = P.is_int[j] != 0;
                 const longlong2 ka = normalized_keys(va, va, is_i), kb = normalized_keys(vb, vb, is_i);
+                s_val[0] = va;
+                s_val[1] = vb;
                 A.bk[0][j] = ka;
                 A.bk[1][j] = ka;
                 A.bk[0][n0 + j] = kb;
@@ -1257,8 +1262,18 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) fp_single_kernel(D
             bulks += 1;
             runs += 2;
             nnz += (long long)(__ldcg(&A.inst[0].nnz_total) + __ldcg(&A.inst[1].nnz_total));
-            if (pick >= 0) fixed += 1;
-            else infeasible = 1;
+            if (pick >= 0) {
+                fixed += 1;
+                if (F.chosen) {
+                    F.chosen[j] = 1;
+                    F.cval[j] = s_val[pick];
+                }
+            } else {
+                infeasible = 1;
+                stop_q = q;
+                stop_j = j;
+                F.out->v0 = s_val[0];
+            }
         }
         base += __ldcg(&ctl->phases) + 3;
         grid_sync(st, ctl);
@@ -1272,6 +1287,8 @@ __global__ void __launch_bounds__(kThreads, GPUBP_MIN_BLOCKS) fp_single_kernel(D
         F.out->fixed = fixed;
         F.out->infeasible = infeasible;
         F.out->error = err;
+        F.out->stop_q = stop_q;
+        F.out->j = stop_j;
         // a propagation cut short by an error may have used stamps up to base + max_rounds + 1
         *A.stamp = err ? base + A.max_rounds + 3 : base;
     }
@@ -1402,7 +1419,8 @@ int launch_propagate(mip_problem* p, double* lb, double* ub, const int* w0, int 
 
 int launch_fp_single(mip_problem* tw, int n0, longlong2* cur, const int* queue, int qlen, const double* x,
                      const double* up_prob, unsigned long long seed, unsigned long long bulk0, double theta,
-                     int max_rounds, int* vdirty, int* dirty, int* words, FpSingleOut* out, cudaStream_t s) {
+                     int max_rounds, int* vdirty, int* dirty, int* words, FpSingleOut* out, unsigned char* chosen,
+                     double* cval, cudaStream_t s) {
     Work& w = tw->w;
     if (!tw->inst_row_off || !tw->inst_col_off || 2 * (long long)n0 != tw->n) {
         set_error("launch_fp_single: not an instance pair");
@@ -1468,6 +1486,8 @@ int launch_fp_single(mip_problem* tw, int n0, longlong2* cur, const int* queue, 
     f.bulk0 = bulk0;
     f.words = words;
     f.out = out;
+    f.chosen = chosen;
+    f.cval = cval;
     BP_CUDA_TRY(cudaMemcpyAsync(w.ctl, w.ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     DevProblem dp = tw->dp;
     void* args[] = {&dp, &a, &f};

@@ -164,13 +164,18 @@ int launch_propagate(mip_problem* p, double* lb, double* ub, const int* w0, int 
 // one becomes cur; stops after the first variable whose candidates are both infeasible.  The
 // pair's key buffers must hold [cur, cur] on entry and hold it again on exit.  vdirty (2 n0,
 // zero or older stamps), dirty (2 n0) and words (4) are scratch; out is device memory.
+// On a stop (infeasible = 1) stop_q is the queue index of the variable that failed, j that
+// variable and v0 its drawn value.  chosen / cval (both NULL, or device arrays of n0): every kept
+// fixing is recorded there (the repair's fixings by choice).
 struct FpSingleOut {
     long long bulks, bp_runs, nnz_updates, fixed;
-    int infeasible, error, pad0, pad1;
+    int infeasible, error, stop_q, j;
+    double v0;
 };
 int launch_fp_single(mip_problem* tw, int n0, longlong2* cur, const int* queue, int qlen, const double* x,
                      const double* up_prob, unsigned long long seed, unsigned long long bulk0, double theta,
-                     int max_rounds, int* vdirty, int* dirty, int* words, FpSingleOut* out, cudaStream_t s);
+                     int max_rounds, int* vdirty, int* dirty, int* words, FpSingleOut* out, unsigned char* chosen,
+                     double* cval, cudaStream_t s);
 constexpr int kMaxInstances = 1024;
 
 }  // namespace gpubp

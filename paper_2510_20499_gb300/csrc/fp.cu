@@ -325,6 +325,163 @@ __global__ void k_finalize(int n, const unsigned char* is_int, const double* x, 
     }
 }
 
+// ------------------------------------------------------------------------ repair
+// The repair of Algorithm 1 (Section 2.3): see fix_and_propagate's documentation.  The fixings
+// by choice are kept on the device: chosen[j] and its value cval[j].
+
+__global__ void k_mark_chosen(int bsize, const int* bulk, const double* v, unsigned char* chosen, double* cval) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < bsize; i += gridDim.x * blockDim.x) {
+        chosen[bulk[i]] = 1;
+        cval[bulk[i]] = v[i];
+    }
+}
+
+// the start of one repair propagation: the caller's bounds with every fixing by choice, and the
+// failed variable j at v (entered as a fixing by choice)
+// (j = -1 after the first cycle: j is then one of the fixings, possibly moved)
+__global__ void k_repair_start(int n, const double* lb, const double* ub, unsigned char* chosen, double* cval, int j,
+                               double v, double* fl, double* fu) {
+    if (j >= 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+        chosen[j] = 1;
+        cval[j] = v;
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const bool c = chosen[i] != 0 || i == j;
+        const double x = i == j ? v : cval[i];
+        fl[i] = c ? x : lb[i];
+        fu[i] = c ? x : ub[i];
+    }
+}
+
+constexpr int kRepThreads = 256;
+
+// the minimal activity of row k under (l, u) over one block: finite part, infinite terms
+__device__ void block_min_activity(const DevProblem& P, int k, const double* l, const double* u, double* red,
+                                   int* redn, double* minfin, int* ninf) {
+    double acc = 0.0;
+    int ni = 0;
+    for (int q = P.row_ptr[k] + threadIdx.x; q < P.row_ptr[k + 1]; q += kRepThreads) {
+        const double a = P.val[q];
+        const int j = P.col[q];
+        const double b = a > 0 ? l[j] : u[j];
+        if (isinf(b)) ++ni;
+        else acc = __dadd_rn(acc, __dmul_rn(a, b));
+    }
+    red[threadIdx.x] = acc;
+    redn[threadIdx.x] = ni;
+    __syncthreads();
+    for (int o = kRepThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            red[threadIdx.x] = __dadd_rn(red[threadIdx.x], red[threadIdx.x + o]);
+            redn[threadIdx.x] += redn[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    *minfin = red[0];
+    *ninf = redn[0];
+    __syncthreads();
+}
+
+// ceil(e / c) for e > 0, c > 0, corrected to the exact integer quotient's ceiling when both are
+// integers (their products are exact below 2^53)
+__device__ __forceinline__ double ceil_div(double e, double c) {
+    double d = ceil(__ddiv_rn(e, c));
+    if (e == floor(e) && c == floor(c)) {
+        for (int it = 0; it < 4 && d > 1.0 && __dmul_rn(d - 1.0, c) >= e; ++it) d -= 1.0;
+        for (int it = 0; it < 4 && __dmul_rn(d, c) < e; ++it) d += 1.0;
+    }
+    return d;
+}
+
+// One repair step after an infeasible propagation (fl, fu: its final bounds; k: its first
+// infeasible row or -1; w: its first crossing variable or -1).  The target row is k, else the
+// smallest row of w violated under (fl, fu); each fixed variable of it proposes the move that
+// makes the row feasible alone, capped by the caller's bounds; the move that lowers the minimal
+// activity most (ties: smallest variable) is applied to cval.  *out = 1 when a move was made.
+// One block.
+__global__ void __launch_bounds__(kRepThreads) k_repair_shift(DevProblem P, const double* fl, const double* fu,
+                                                              const double* lb, const double* ub,
+                                                              const unsigned char* chosen, double* cval, int k, int w,
+                                                              int* out) {
+    __shared__ double red[kRepThreads];
+    __shared__ int redn[kRepThreads];
+    __shared__ int red_i[kRepThreads];
+    int target = k;
+    if (target < 0 && w >= 0) {
+        int best = INT_MAX;
+        for (int s = P.col_ptr[w]; s < P.col_ptr[w + 1]; ++s) {
+            const int kk = P.row_idx[s];
+            double mf;
+            int ni;
+            block_min_activity(P, kk, fl, fu, red, redn, &mf, &ni);
+            const double2 g2 = P.grow[kk];
+            if (ni == 0 && isfinite(g2.x) && mf > g2.y && kk < best) best = kk;
+        }
+        target = best == INT_MAX ? -1 : best;
+    }
+    if (target < 0) {
+        if (threadIdx.x == 0) *out = 0;
+        return;
+    }
+    double mf;
+    int ni;
+    block_min_activity(P, target, fl, fu, red, redn, &mf, &ni);
+    const double e = __dsub_rn(mf, P.grow[target].x);
+    if (ni != 0 || !(e > 0.0)) {
+        if (threadIdx.x == 0) *out = 0;
+        return;
+    }
+    // each thread's best move over its nonzeros, then a block reduction (largest reduction,
+    // smallest variable)
+    double br = 0.0;
+    int bi = INT_MAX;
+    for (int q = P.row_ptr[target] + threadIdx.x; q < P.row_ptr[target + 1]; q += kRepThreads) {
+        const int i = P.col[q];
+        if (!chosen[i]) continue;
+        const double a = P.val[q], aa = fabs(a);
+        const double need = ceil_div(e, aa);
+        const double room = a > 0 ? floor(__dsub_rn(cval[i], lb[i])) : floor(__dsub_rn(ub[i], cval[i]));
+        const double d = need < room ? need : room;
+        if (!(d > 0.0)) continue;
+        const double rr = __dmul_rn(aa, d);
+        if (rr > br || (rr == br && i < bi)) {
+            br = rr;
+            bi = i;
+        }
+    }
+    red[threadIdx.x] = br;
+    red_i[threadIdx.x] = bi;
+    __syncthreads();
+    for (int o = kRepThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            const double r2 = red[threadIdx.x + o];
+            const int i2 = red_i[threadIdx.x + o];
+            if (r2 > red[threadIdx.x] || (r2 == red[threadIdx.x] && i2 < red_i[threadIdx.x])) {
+                red[threadIdx.x] = r2;
+                red_i[threadIdx.x] = i2;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int i = red_i[0];
+        if (i == INT_MAX) {
+            *out = 0;
+            return;
+        }
+        // the chosen move again (its coefficient from the row)
+        double a = 0.0;
+        for (int q = P.row_ptr[target]; q < P.row_ptr[target + 1]; ++q)
+            if (P.col[q] == i) a = P.val[q];
+        const double aa = fabs(a);
+        const double room = a > 0 ? floor(__dsub_rn(cval[i], lb[i])) : floor(__dsub_rn(ub[i], cval[i]));
+        const double need = ceil_div(e, aa);
+        const double d = need < room ? need : room;
+        cval[i] = a > 0 ? __dsub_rn(cval[i], d) : __dadd_rn(cval[i], d);
+        *out = 1;
+    }
+}
+
 static int gridn(long long work) {
     long long b = (work + 255) / 256;
     return (int)(b < 1 ? 1 : (b > 1216 ? 1216 : b));
@@ -336,6 +493,9 @@ struct FpCtl {
     int ucnt[2];      // unfixed integer variables under each candidate's propagated bounds
     bp_result res[2];
     FpSingleOut single;   // counters of a device-driven run of one-variable bulks
+    int rep_j;            // repair: the failed variable and its drawn value, read back
+    double rep_v;
+    int rep_moved;        // repair: a fixing was moved
 };
 
 // The current bounds as ordered keys (cur) and in both copies of both key buffers of the
@@ -406,6 +566,8 @@ extern "C" void fp_params_default(fp_params* p) {
     p->fraction = 0.01;
     p->theta = 1e-3;
     p->max_rounds = 10000;
+    p->repair_max = 0;
+    p->repair_cycles = 8;
     p->reserved = 0;
     p->order_score = nullptr;
     p->up_prob = nullptr;
@@ -432,6 +594,14 @@ extern "C" int fix_and_propagate(mip_problem* p, const double* x, const double* 
         set_error("fix_and_propagate: incomplete cache");
         return BP_ERR_INVALID;
     }
+    if (prm.repair_max < 0 || (prm.repair_max > 0 && prm.repair_cycles < 1)) {
+        set_error("fix_and_propagate: invalid repair parameters");
+        return BP_ERR_INVALID;
+    }
+    if (prm.repair_max > 0 && cache && cache->npairs > 0) {
+        set_error("fix_and_propagate: the repair is defined without a probing cache");
+        return BP_ERR_INVALID;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     const int n = p->n;
     memset(result, 0, sizeof(*result));
@@ -453,6 +623,9 @@ extern "C" int fix_and_propagate(mip_problem* p, const double* x, const double* 
     double *Bl, *Bu, *cl[2], *cu[2], *v[2], *rmin, *L4, *U4;
     int *flag, *pos, *ivars, *order, *work, *twork, *rninf, *dlist, *dcnt, *pair_of = nullptr, *total;
     unsigned long long *keys, *tkeys;
+    unsigned char* chosen = nullptr;   // repair: fixings by choice and their values
+    double* cval = nullptr;
+    int* rep_out = nullptr;
     longlong2* curk = nullptr;     // device-driven one-variable bulks (allocated on first use)
     int *vdirty = nullptr, *dirtyl = nullptr, *words = nullptr;
     FpSingleOut* sout = nullptr;
@@ -507,6 +680,14 @@ extern "C" int fix_and_propagate(mip_problem* p, const double* x, const double* 
         if (_e != cudaSuccess) return fail(fail_cuda(_e, #expr)); \
     } while (0)
     const bool use_cache = cache && cache->npairs > 0;
+    const bool repair_on = prm.repair_max > 0;
+    int repairs_tried = 0;
+    if (repair_on) {
+        FP_TRY(alloc(&chosen, (size_t)n));
+        FP_TRY(alloc(&cval, (size_t)n));
+        FP_TRY(alloc(&rep_out, 1));
+        FP_CUDA(cudaMemsetAsync(chosen, 0, (size_t)(n ? n : 1), s));
+    }
     if (use_cache) {
         FP_ALLOC(pair_of, n);
         k_fill_int<<<gridn(n), 256, 0, s>>>(n, pair_of, INT_MAX);
@@ -541,6 +722,42 @@ extern "C" int fix_and_propagate(mip_problem* p, const double* x, const double* 
             FP_TRY(radix_sort_pairs(keys, order, tkeys, twork, nint, 0, which == 2 ? 8 : 64, s));
         }
     }
+    // Repair of a one-variable bulk that failed both ways (variable j, drawn value v0): returns 1
+    // when a propagation became feasible (its bounds are then the current ones), 0 when not,
+    // or minus an error code.
+    auto do_repair = [&](int j, double v0) -> int {
+        const int fs = (cur + 2) % 4;
+        double* fl = L4 + (size_t)fs * n;
+        double* fu = U4 + (size_t)fs * n;
+        for (int c = 0; c < prm.repair_cycles; ++c) {
+            k_repair_start<<<gridn(n), 256, 0, s>>>(n, lb, ub, chosen, cval, c == 0 ? j : -1, v0, fl, fu);
+            if (cudaGetLastError() != cudaSuccess) return -BP_ERR_CUDA;
+            int rc2 = launch_propagate(p, fl, fu, nullptr, 0, prm.theta, prm.max_rounds, nullptr, s);
+            if (rc2 != BP_OK) return -rc2;
+            if (cudaMemcpyAsync(&hctl->res[0], p->w.dres, sizeof(bp_result), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return -BP_ERR_CUDA;
+            const bp_result r = hctl->res[0];
+            if (r.error) return -BP_ERR_TIMEOUT;
+            result->bp_runs++;
+            result->repair_runs++;
+            result->nnz_updates += r.nnz_updates;
+            if (r.status != BP_INFEASIBLE) {
+                cur = fs;
+                Bl = fl;
+                Bu = fu;
+                return 1;
+            }
+            k_repair_shift<<<1, kRepThreads, 0, s>>>(p->dp, fl, fu, lb, ub, chosen, cval, r.first_infeasible_row,
+                                                      r.first_infeasible_var, rep_out);
+            if (cudaGetLastError() != cudaSuccess) return -BP_ERR_CUDA;
+            if (cudaMemcpyAsync(&hctl->rep_moved, rep_out, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return -BP_ERR_CUDA;
+            if (!hctl->rep_moved) return 0;
+        }
+        return 0;
+    };
     std::vector<int> recq;
     size_t rec_pos = 0;
     unsigned long long bulk_index = 0;
@@ -659,6 +876,10 @@ extern "C" int fix_and_propagate(mip_problem* p, const double* x, const double* 
             Bu = U4 + (size_t)cur * n;
             next_nun = hctl->ucnt[pick];
             have_nun = nint > 0;
+            if (repair_on) {
+                k_mark_chosen<<<gridn(bsize), 256, 0, s>>>((int)bsize, bulk, v[pick], chosen, cval);
+                FP_CUDA(cudaGetLastError());
+            }
         } else if (!single && !use_cache) {
             // recovery on the device: the failed bulk's variables one at a time, in one launch
             result->recoveries++;
@@ -669,25 +890,43 @@ extern "C" int fix_and_propagate(mip_problem* p, const double* x, const double* 
                 FP_TRY(alloc(&words, 4));
                 FP_TRY(alloc(&sout, 1));
             }
-            // cleared for every run: a plain propagation launch in between may have restarted the
-            // stamps, which this array's entries are compared with
-            FP_CUDA(cudaMemsetAsync(vdirty, 0, sizeof(int) * 2 * (size_t)n, s));
-            k_keys_init<<<gridn(n), 256, 0, s>>>(n, p->dp.is_int, Bl, Bu, curk, tw->w.bkey[0], tw->w.bkey[1]);
-            FP_CUDA(cudaGetLastError());
-            FP_TRY(launch_fp_single(tw, n, curk, bulk, (int)bsize, x, prm.up_prob, prm.seed, bulk_index, prm.theta,
-                                    prm.max_rounds, vdirty, dirtyl, words, sout, s));
-            k_keys_out<<<gridn(n), 256, 0, s>>>(n, curk, Bl, Bu);
-            FP_CUDA(cudaGetLastError());
-            FP_CUDA(cudaMemcpyAsync(&hctl->single, sout, sizeof(FpSingleOut), cudaMemcpyDeviceToHost, s));
-            FP_CUDA(cudaStreamSynchronize(s));
-            const FpSingleOut& so = hctl->single;
-            if (so.error) return fail(so.error);
-            result->bulks += so.bulks;
-            bulk_index += (unsigned long long)so.bulks;
-            result->bp_runs += so.bp_runs;
-            result->nnz_updates += so.nnz_updates;
-            result->fixed_by_choice += so.fixed;
-            if (so.infeasible) rounding_infeasible = true;
+            // the queue from qstart; after a successful repair the launch resumes behind the
+            // repaired variable
+            for (int qstart = 0; qstart < (int)bsize;) {
+                // cleared for every run: a plain propagation launch in between may have restarted
+                // the stamps, which this array's entries are compared with
+                FP_CUDA(cudaMemsetAsync(vdirty, 0, sizeof(int) * 2 * (size_t)n, s));
+                k_keys_init<<<gridn(n), 256, 0, s>>>(n, p->dp.is_int, Bl, Bu, curk, tw->w.bkey[0], tw->w.bkey[1]);
+                FP_CUDA(cudaGetLastError());
+                FP_TRY(launch_fp_single(tw, n, curk, bulk + qstart, (int)bsize - qstart, x, prm.up_prob, prm.seed,
+                                        bulk_index, prm.theta, prm.max_rounds, vdirty, dirtyl, words, sout, chosen,
+                                        cval, s));
+                k_keys_out<<<gridn(n), 256, 0, s>>>(n, curk, Bl, Bu);
+                FP_CUDA(cudaGetLastError());
+                FP_CUDA(cudaMemcpyAsync(&hctl->single, sout, sizeof(FpSingleOut), cudaMemcpyDeviceToHost, s));
+                FP_CUDA(cudaStreamSynchronize(s));
+                const FpSingleOut so = hctl->single;
+                if (so.error) return fail(so.error);
+                result->bulks += so.bulks;
+                bulk_index += (unsigned long long)so.bulks;
+                result->bp_runs += so.bp_runs;
+                result->nnz_updates += so.nnz_updates;
+                result->fixed_by_choice += so.fixed;
+                if (!so.infeasible) break;
+                if (!(repair_on && repairs_tried < prm.repair_max)) {
+                    rounding_infeasible = true;
+                    break;
+                }
+                repairs_tried++;
+                const int rr = do_repair(so.j, so.v0);
+                if (rr < 0) return fail(-rr);
+                if (!rr) {
+                    rounding_infeasible = true;
+                    break;
+                }
+                result->repairs++;
+                qstart += so.stop_q + 1;
+            }
             have_nun = false;
         } else if (!single) {
             recq.resize((size_t)bsize);
@@ -697,6 +936,17 @@ extern "C" int fix_and_propagate(mip_problem* p, const double* x, const double* 
             result->recoveries++;
             next_nun = nun;   // the bounds did not move
             have_nun = true;
+        } else if (repair_on && repairs_tried < prm.repair_max) {
+            // a one-variable bulk failed both ways: repair
+            repairs_tried++;
+            FP_CUDA(cudaMemcpyAsync(&hctl->rep_j, bulk, sizeof(int), cudaMemcpyDeviceToHost, s));
+            FP_CUDA(cudaMemcpyAsync(&hctl->rep_v, v[0], sizeof(double), cudaMemcpyDeviceToHost, s));
+            FP_CUDA(cudaStreamSynchronize(s));
+            const int rr = do_repair(hctl->rep_j, hctl->rep_v);
+            if (rr < 0) return fail(-rr);
+            if (rr) result->repairs++;
+            else rounding_infeasible = true;
+            have_nun = false;
         } else {
             rounding_infeasible = true;
         }

@@ -238,3 +238,74 @@ def test_recovery_ending_infeasible_parity(pkg):
     ints = p.is_int == 1
     np.testing.assert_array_equal(gx[ints], ox[ints])
     np.testing.assert_allclose(gx[~ints], ox[~ints], rtol=1e-9, atol=1e-9)
+
+
+RKEYS = KEYS + ("repairs", "repair_runs")
+
+
+@pytest.mark.parametrize("which", ["case", "with_implied"])
+@pytest.mark.parametrize("seed", range(1, 7))
+def test_repair_golden(pkg, which, seed):
+    """The hand-worked repair cases (Section 2.3, the repair branch of Algorithm 1) on the GPU."""
+    from tests.helpers import milp_from_dense
+    d = load_golden("fp_repair.json")
+    c = d if which == "case" else d["with_implied"]
+    p = milp_from_dense(c["A"], c["g"], c["lb"], c["ub"], [1] * len(c["lb"]))
+    x = np.array(c["x"])
+    up = oracle.uniform(seed, 1, 1, 0) < d["p_up_x1"]
+    want = c["with_repair"]["x1_drawn_up" if up else "x1_drawn_down"]
+    gx, gr = _gpu_fp(pkg, p, x, seed=seed, repair_max=4)
+    for k in ("status", "bulks", "fixed_by_choice", "repairs", "repair_runs", "bp_runs"):
+        assert gr[k] == want[k], (k, gr, want)
+    np.testing.assert_array_equal(gx, want["x_out"])
+    gx, gr = _gpu_fp(pkg, p, x, seed=seed)
+    assert gr["status"] == c["without_repair"]["status"] and gr["repairs"] == 0
+    np.testing.assert_array_equal(gx, c["without_repair"]["x_out"])
+
+
+def test_repair_tiny_planted_parity(pkg):
+    """Tiny planted problems rounded from the opposite corner (one-variable bulks driven by the
+    host): with repair the GPU takes the oracle's every decision."""
+    from tests.test_oracle_repair import _tiny_planted
+    rng = np.random.default_rng(11)
+    repaired = 0
+    for _ in range(200):
+        n = int(rng.integers(4, 9))
+        p, A, g, ub, x = _tiny_planted(rng, n, int(rng.integers(3, 7)), 0.3, 2)
+        seed = int(rng.integers(1, 1000))
+        ox, orr = oracle.Problem(p).fix_and_propagate(x, p.lb, p.ub, seed=seed, repair_max=6)
+        gx, gr = _gpu_fp(pkg, p, x, seed=seed, repair_max=6)
+        for k in RKEYS:
+            assert gr[k] == orr[k], (k, gr, orr)
+        np.testing.assert_array_equal(gx, ox)
+        repaired += orr["repair_runs"] > 0
+    assert repaired >= 5
+
+
+@pytest.mark.parametrize("inst", [1001, 1002, 1003])
+def test_repair_parity_rounding_instances(pkg, inst):
+    """100k-nonzero rounding instances (20% equality pairs, 1% bulks) whose retries of a failed
+    bulk run into a variable failing both ways: the repair starts from the device-driven retry
+    launch, which resumes behind the repaired variable.  1001: the repair fails; 1002: it
+    succeeds and the rounding ends feasible; 1003: one success, then a failure."""
+    p, x = synth.rounding_instance(inst, 100_000)
+    kw = dict(seed=1, bulk_rule=1, fraction=0.01, repair_max=4)
+    ox, orr = oracle.Problem(p).fix_and_propagate(x, p.lb, p.ub, **kw)
+    assert orr["fragile"] == 0 and orr["repair_runs"] > 0, orr
+    gx, gr = _gpu_fp(pkg, p, x, **kw)
+    for k in RKEYS:
+        assert gr[k] == orr[k], (k, gr, orr)
+    ints = p.is_int == 1
+    np.testing.assert_array_equal(gx[ints], ox[ints])
+    np.testing.assert_allclose(gx[~ints], ox[~ints], rtol=1e-9, atol=1e-9)
+
+
+def test_repair_rejects_a_cache(pkg):
+    d = load_golden("fp_repair.json")
+    from tests.helpers import milp_from_dense
+    p = milp_from_dense(d["A"], d["g"], d["lb"], d["ub"], [1] * 3)
+    cache = {"pairs": np.array([0], np.int32), "boxes": np.array([[0, 0, 1, 1]], float),
+             "status": np.array([0, 0], np.int32), "offsets": np.array([0, 0, 0], np.int64),
+             "var": np.zeros(0, np.int32), "l": np.zeros(0), "u": np.zeros(0)}
+    with pytest.raises(Exception):
+        _gpu_fp(pkg, p, np.array(d["x"]), cache=cache, repair_max=1)
