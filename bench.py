@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the probing, batch, learned and scorer measurements")
-    ap.add_argument("--extras", default="probing,batch,fp,learned,scorer",
+    ap.add_argument("--extras", default="probing,batch,fp,learned,scorer,pdhg",
                     help="comma-separated subset of the extra measurements to run (learned_full, the "
                          "160/40-instance learned-order experiment at 1M nonzeros, is not in the default set)")
     return ap.parse_args()
@@ -580,6 +580,49 @@ def fp_extra(pkg, torch, dev):
                          "achieved": fbytes / t / 1e9, "peak": hbm, "unit": "GB/s", "frac": fbytes / t / 1e9 / hbm}}
 
 
+def pdhg_extra(pkg, torch, dev):
+    """The approximate LP (pdhg_solve) on the benchmark instance (200k x 500k, 5M nonzeros;
+    infinite bounds boxed at +-1000, objective N(0, 1)): time per PDHG iteration from the
+    difference of a 220- and a 20-iteration call (the start and the KKT evaluation cancel), and
+    its roofline.  Algorithmic bytes per iteration: both copies of the matrix (CSR for A xe,
+    transpose for A^T y: 12 B per nonzero each), per variable x, c, l, u read, x+ and the
+    extrapolation written, the extrapolation read by the rows and the restart sum read and
+    written (72 B), per row y, g read, y+ written and the restart sum read and written (40 B)."""
+    import numpy as np
+    from paper_2510_20499_gb300 import synth
+    p = synth.mixed_powerlaw()
+    p.lb = np.where(np.isfinite(p.lb), p.lb, -1000.0)
+    p.ub = np.where(np.isfinite(p.ub), p.ub, 1000.0)
+    p.c = np.random.default_rng(5).normal(0, 1, p.n)
+    prob = pkg.Problem(p)
+    lb, ub = torch.tensor(p.lb, device=dev), torch.tensor(p.ub, device=dev)
+
+    def run(iters):
+        x = torch.zeros(p.n, dtype=torch.float64, device=dev)
+        y = torch.zeros(p.m, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = prob.pdhg(lb, ub, x, y, iterations=iters, restart_period=100)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), r
+    run(20)
+    t_short = min(run(20)[0] for _ in range(3))
+    runs = [run(220) for _ in range(3)]
+    t_long, r = min(runs, key=lambda q: q[0])
+    per_it = (t_long - t_short) / 200.0
+    bytes_it = 24 * p.nnz + 72 * p.n + 40 * p.m
+    hbm, _ = peaks()
+    return {"workload": f"mixed power-law {p.m} x {p.n}, {p.nnz} nnz (bounds boxed at +-1000, c ~ N(0, 1)), "
+                        "restarts every 100",
+            "ms_per_iteration": per_it, "iterations_per_s": 1e3 / per_it,
+            "after_220": {k: r[k] for k in ("primal_residual", "dual_residual", "primal_obj", "dual_obj")},
+            "roofline": {"bound": "hbm", "kernel": "k_pdhg_cols + k_pdhg_rows + k_pdhg_long (one iteration)",
+                         "bytes": bytes_it, "achieved": bytes_it / per_it / 1e6, "peak": hbm, "unit": "GB/s",
+                         "frac": bytes_it / per_it / 1e6 / hbm}}
+
+
 def scorer_extra(pkg, torch, dev, tflops_peak):
     """The scorer's forward and training-step throughput on 1M rows of BF16 features (the
     tcgen05 MLP kernel k_mlp), against the measured BF16 tensor peak."""
@@ -732,13 +775,14 @@ def main():
     }
     if rank == 0 and not args.no_extras:
         todo = [e for e in args.extras.split(",") if e]
-        bad = [e for e in todo if e not in ("probing", "batch", "fp", "learned", "learned_full", "scorer")]
+        bad = [e for e in todo if e not in ("probing", "batch", "fp", "learned", "learned_full", "scorer", "pdhg")]
         if bad:
             raise SystemExit(f"unknown extras: {bad}")
         fns = {"probing": lambda: probing_extra(pkg, torch, dev), "batch": lambda: batch_extra(pkg, torch, dev),
                "fp": lambda: fp_extra(pkg, torch, dev),
                "learned": lambda: learned_extra(pkg, torch, dev),
-               "learned_full": lambda: learned_full_extra(pkg, torch, dev), "scorer": lambda: scorer_extra(pkg, torch, dev, tensor_peak())}
+               "learned_full": lambda: learned_full_extra(pkg, torch, dev),
+               "pdhg": lambda: pdhg_extra(pkg, torch, dev), "scorer": lambda: scorer_extra(pkg, torch, dev, tensor_peak())}
         out["extras"] = {e: fns[e]() for e in todo}
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(p)

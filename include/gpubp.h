@@ -453,6 +453,52 @@ void fp_params_default(fp_params *p);   /* seed 1, sqrt rule, last_single 36, fr
                                           * (repair_max 0, repair_cycles 8) */
 
 /*
+ * pdhg_solve -- the approximate LP (Sections 1 and 2.5: the paper's GPU PDLP, warm-started).
+ *
+ * Primal-dual hybrid gradient for min c^T x s.t. A x <= g, lb <= x <= ub (c: the handle's
+ * objective; rows with g = +inf are free), with row duals y >= 0:
+ *     x+ = proj_[lb, ub](x - tau (c + A^T y)),  y+ = max(0, y + sigma (A (2 x+ - x) - g)),
+ *     tau = step / primal_weight,  sigma = step * primal_weight,
+ * and with restart_period R > 0 every R iterations the iterate is replaced by the mean of the
+ * period's R iterates.  step 0: 0.9 / sqrt(max column |a| sum * max row |a| sum) (a bound on
+ * ||A||_2); primal_weight 0: ||c||_2 / ||g||_2 over the finite rows (1 if either is zero).
+ * No preconditioning.  Approximate by design: the caller chooses the iterations (the paper
+ * limits each projection by time) and reads the KKT measures.
+ *
+ * lb, ub:  DEVICE double[n] box (not modified).
+ * x:       DEVICE double[n], the primal warm start on entry, the final iterate on return.
+ * y:       DEVICE double[m], the dual warm start on entry (>= 0), the final iterate on return.
+ * result:  HOST pointer, valid at return (the call synchronises the stream): iterations,
+ *          restarts, the step and primal weight used, primal residual ||max(Ax - g, 0)||_2
+ *          (finite rows), dual residual (norm of the reduced costs c + A^T y that push a
+ *          variable toward an infinite bound), primal objective c^T x, dual objective
+ *          -g^T y + sum_j min over [lb_j, ub_j] of r_j x_j (finite parts).
+ * Scratch: 3 n + 2 m + pieces doubles (plus n + m with restarts), stream-ordered, freed at return.
+ * Returns BP_OK, BP_ERR_INVALID (null pointers, negative counts or steps), BP_ERR_OOM or BP_ERR_CUDA.
+ */
+typedef struct {
+    int32_t iterations;
+    int32_t restart_period;
+    double step;
+    double primal_weight;
+} pdhg_params;
+
+typedef struct {
+    int32_t iterations;
+    int32_t restarts;
+    double step;
+    double primal_weight;
+    double primal_residual;
+    double dual_residual;
+    double primal_obj;
+    double dual_obj;
+} pdhg_result;
+
+void pdhg_params_default(pdhg_params *p);   /* 1000 iterations, restart period 100, defaults */
+int pdhg_solve(mip_problem *p, const double *lb, const double *ub, double *x, double *y,
+               const pdhg_params *params, pdhg_result *result, void *stream);
+
+/*
  * fix_and_propagate -- bulk rounding with bound propagation (Section 2.3, Algorithm 1; LP
  * polish off; the repair optional and off by default, as in the paper's experiments).
  *

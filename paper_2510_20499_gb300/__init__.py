@@ -70,6 +70,20 @@ class FpResult(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class PdhgParams(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("restart_period", C.c_int32), ("step", C.c_double),
+                ("primal_weight", C.c_double)]
+
+
+class PdhgResult(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("restarts", C.c_int32), ("step", C.c_double),
+                ("primal_weight", C.c_double), ("primal_residual", C.c_double), ("dual_residual", C.c_double),
+                ("primal_obj", C.c_double), ("dual_obj", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class BpTuning(C.Structure):
     _fields_ = [("warp_min", C.c_int32), ("block_min", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("chunk_len", C.c_int32)]
@@ -142,6 +156,9 @@ SIGNATURES = {
     "bp_probe_priority": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.POINTER(C.c_int32), C.c_void_p]),
     "fp_params_default": (None, [C.POINTER(FpParams)]),
+    "pdhg_params_default": (None, [C.POINTER(PdhgParams)]),
+    "pdhg_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(PdhgParams),
+                             C.POINTER(PdhgResult), C.c_void_p]),
     "fix_and_propagate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(FpCache),
                                     C.POINTER(FpParams), C.c_void_p, C.POINTER(FpResult), C.c_void_p]),
     "mip_set_instances": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
@@ -382,6 +399,19 @@ def _fix_and_propagate(prob, x, lb, ub, seed=1, bulk_rule=0, fraction=0.01, last
 
 
 Problem.fix_and_propagate = _fix_and_propagate
+
+
+def _pdhg(prob, lb, ub, x, y, iterations=1000, restart_period=100, step=0.0, primal_weight=0.0, stream=None):
+    """pdhg_solve (the approximate LP) on device tensors: lb, ub (n), x (n) and y (m) float64; x
+    and y are the warm start and receive the final iterate.  Returns the result dict."""
+    prm = PdhgParams(int(iterations), int(restart_period), float(step), float(primal_weight))
+    res = PdhgResult()
+    _check(lib().pdhg_solve(prob.h, _ptr(lb), _ptr(ub), _ptr(x), _ptr(y), C.byref(prm), C.byref(res),
+                            _stream(stream)))
+    return res.as_dict()
+
+
+Problem.pdhg = _pdhg
 
 RESULT_FIELDS = [f for f, _ in BpResult._fields_ if f != "reserved"]
 

@@ -1,0 +1,374 @@
+// The approximate LP (Sections 1 and 2.5: the paper's GPU PDLP): warm-started primal-dual
+// hybrid gradient for
+//     min c^T x   subject to   A x <= g,   l <= x <= u        (rows with g = +inf are free)
+// with row duals y >= 0:
+//     x+ = proj_[l, u](x - tau (c + A^T y)),      xe = 2 x+ - x,
+//     y+ = max(0, y + sigma (A xe - g)),          tau = eta / omega, sigma = eta * omega,
+// and, with a restart period R > 0, every R iterations the iterate replaced by the mean of the
+// period's R iterates (a fixed period: every step is a plain function of the inputs).  Default
+// eta = 0.9 / sqrt(max column |a| sum * max row |a| sum) (a bound on ||A||_2), default primal
+// weight omega = ||c||_2 / ||g||_2 over the finite rows (PDLP's initial weight).
+//
+// One iteration streams the matrix twice, both passes HBM-bound:
+//   k_pdhg_cols   groups of 8 lanes per column over the transpose (row_idx, col_val): A^T y,
+//                 fused with the x step, the extrapolation and the restart sums;
+//   k_pdhg_rows   a flat task space over the row classes of the handle: a warp per piece of a
+//                 long row (partial sum into its slot), a warp per warp row, a thread per
+//                 thread row; finished rows take the y step at once;
+//   k_pdhg_long   a warp per long row sums its pieces' partials in slot order, then the y step.
+// The same kernels with `eval` set produce A x and c + A^T y for the KKT measures; every sum over
+// a row, a column or the whole problem has a fixed order, so repeated runs are bit-identical.
+#include <climits>
+#include <cmath>
+
+#include "bp_host.h"
+
+namespace gpubp {
+
+constexpr int kPdThreads = 256;
+constexpr int kPdColLanes = 8;            // lanes per column
+constexpr int kPdRedBlocks = 304;         // blocks of the reductions (fixed: a fixed order)
+
+struct PdhgVecs {
+    const double* c;
+    const double* l;
+    const double* u;
+    double tau, sigma;
+};
+
+// ---------------------------------------------------------------- column pass
+// x+ = clamp(x - tau (c + A^T y), l, u), xe = 2 x+ - x, xs += x+ (restart sums, when given).
+// eval: r = c + A^T y into xn (nothing else).
+__global__ void __launch_bounds__(kPdThreads) k_pdhg_cols(DevProblem P, PdhgVecs V, const double* __restrict__ x,
+                                                          const double* __restrict__ y, double* __restrict__ xn,
+                                                          double* __restrict__ xe, double* __restrict__ xs, int eval) {
+    const int lane = threadIdx.x & 31, gl = lane & (kPdColLanes - 1);
+    const int groups = (gridDim.x * blockDim.x) / kPdColLanes;
+    const int rpw = 32 / kPdColLanes;
+    const int wi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    for (int jb = wi * rpw; jb < P.n; jb += (groups / rpw) * rpw) {
+        const int j = jb + lane / kPdColLanes;
+        double s = 0.0;
+        if (j < P.n) {
+            const int b = P.col_ptr[j], e = P.col_ptr[j + 1];
+            for (int q = b + gl; q < e; q += kPdColLanes) s = __dadd_rn(s, __dmul_rn(P.col_val[q], y[P.row_idx[q]]));
+        }
+#pragma unroll
+        for (int o = kPdColLanes / 2; o > 0; o >>= 1) s = __dadd_rn(s, __shfl_xor_sync(0xffffffffu, s, o));
+        if (j < P.n && gl == 0) {
+            const double r = __dadd_rn(V.c[j], s);
+            if (eval) {
+                xn[j] = r;
+            } else {
+                const double xj = x[j];
+                double v = __dsub_rn(xj, __dmul_rn(V.tau, r));
+                v = v < V.l[j] ? V.l[j] : v;   // max(v, l), then min(., u)
+                v = v > V.u[j] ? V.u[j] : v;
+                xn[j] = v;
+                xe[j] = __dsub_rn(__dmul_rn(2.0, v), xj);
+                if (xs) xs[j] = __dadd_rn(xs[j], v);
+            }
+        }
+    }
+}
+
+// the y step of row k from its sum s = (A xe)_k; eval: A x into yn
+__device__ __forceinline__ void pdhg_row_done(const DevProblem& P, const PdhgVecs& V, int k, double s, const double* y,
+                                              double* yn, double* ys, int eval) {
+    if (eval) {
+        yn[k] = s;
+        return;
+    }
+    const double v = __dadd_rn(y[k], __dmul_rn(V.sigma, __dsub_rn(s, P.grow[k].x)));
+    const double w = v > 0.0 ? v : 0.0;
+    yn[k] = w;
+    if (ys) ys[k] = __dadd_rn(ys[k], w);
+}
+
+// ---------------------------------------------------------------- row pass
+// Warp tasks [pieces of long rows][warp rows][thread rows in groups of 32]: pieces write their
+// partial sums (slot = the piece's index in the round-0 piece list), the others finish their
+// rows.
+__global__ void __launch_bounds__(kPdThreads) k_pdhg_rows(DevProblem P, PdhgVecs V, const double* __restrict__ xe,
+                                                          const double* __restrict__ y, double* __restrict__ yn,
+                                                          double* __restrict__ ys, double* __restrict__ part, int eval) {
+    const int lane = threadIdx.x & 31;
+    const int nwarp_rows = P.class_off[kClassWarpRow + 1] - P.class_off[kClassWarpRow];
+    const int nthread_rows = P.class_off[kNumThreadBins] - P.class_off[0];
+    const int t_pieces = P.npieces, t_warp = nwarp_rows, t_thread = (nthread_rows + 31) / 32;
+    const int total = t_pieces + t_warp + t_thread;
+    const int NW = (gridDim.x * blockDim.x) >> 5;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < total; t += NW) {
+        if (t < t_pieces) {
+            const int4 tk = P.static_tasks[t];
+            const int beg = tk.z, end = min(tk.w, tk.z + P.chunk_len);
+            double s = 0.0;
+            for (int q = beg + lane; q < end; q += 32) s = __dadd_rn(s, __dmul_rn(P.val[q], xe[P.col[q]]));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s = __dadd_rn(s, __shfl_xor_sync(0xffffffffu, s, o));
+            if (lane == 0) part[t] = s;
+        } else if (t < t_pieces + t_warp) {
+            const int k = P.static_list[P.class_off[kClassWarpRow] + (t - t_pieces)];
+            double s = 0.0;
+            for (int q = P.row_ptr[k] + lane; q < P.row_ptr[k + 1]; q += 32)
+                s = __dadd_rn(s, __dmul_rn(P.val[q], xe[P.col[q]]));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s = __dadd_rn(s, __shfl_xor_sync(0xffffffffu, s, o));
+            if (lane == 0) pdhg_row_done(P, V, k, s, y, yn, ys, eval);
+        } else {
+            const int i = (t - t_pieces - t_warp) * 32 + lane;
+            if (i < nthread_rows) {
+                const int k = P.static_list[P.class_off[0] + i];
+                double s = 0.0;
+                for (int q = P.row_ptr[k]; q < P.row_ptr[k + 1]; ++q) s = __dadd_rn(s, __dmul_rn(P.val[q], xe[P.col[q]]));
+                pdhg_row_done(P, V, k, s, y, yn, ys, eval);
+            }
+        }
+    }
+}
+
+// A warp per long row (its first piece's descriptor): the partials of its pieces in slot order
+// (lanes strided, then a fixed reduction), then the y step.
+__global__ void __launch_bounds__(kPdThreads) k_pdhg_long(DevProblem P, PdhgVecs V, const double* __restrict__ part,
+                                                          const double* __restrict__ y, double* __restrict__ yn,
+                                                          double* __restrict__ ys, int eval) {
+    const int lane = threadIdx.x & 31;
+    const int NW = (gridDim.x * blockDim.x) >> 5;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < P.npieces; t += NW) {
+        const int4 tk = P.static_tasks[t];
+        if (tk.y != 0) continue;   // not the row's first piece
+        const int npc = (tk.w - tk.z + P.chunk_len - 1) / P.chunk_len;
+        double s = 0.0;
+        for (int i = lane; i < npc; i += 32) s = __dadd_rn(s, part[t + i]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s = __dadd_rn(s, __shfl_xor_sync(0xffffffffu, s, o));
+        if (lane == 0) pdhg_row_done(P, V, tk.x, s, y, yn, ys, eval);
+    }
+}
+
+// restart: (x, y) = (xs, ys) / R, sums cleared
+__global__ void k_pdhg_restart(int n, int m, double r, double* x, double* y, double* xs, double* ys) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        x[j] = __ddiv_rn(xs[j], r);
+        xs[j] = 0.0;
+    }
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += stride) {
+        y[k] = __ddiv_rn(ys[k], r);
+        ys[k] = 0.0;
+    }
+}
+
+// ---------------------------------------------------------------- reductions (fixed order)
+// Block sums of up to 5 values per thread into part[5 * block + i]: a fixed tree per block.
+__device__ void block_sum5(double v[5], double* part) {
+    __shared__ double sh[5][kPdThreads];
+    for (int i = 0; i < 5; ++i) sh[i][threadIdx.x] = v[i];
+    __syncthreads();
+    for (int o = kPdThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int i = 0; i < 5; ++i) sh[i][threadIdx.x] = __dadd_rn(sh[i][threadIdx.x], sh[i][threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x < 5) part[5 * blockIdx.x + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// Step-size inputs: [0] max column |a| sum, [1] max row |a| sum (per block maxima), [2] sum of c^2,
+// [3] sum of g^2 over finite rows (per block sums).
+__global__ void __launch_bounds__(kPdThreads) k_pdhg_norms(DevProblem P, const double* c, double* part) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int j = tid; j < P.n; j += stride) {
+        double s = 0.0;
+        for (int q = P.col_ptr[j]; q < P.col_ptr[j + 1]; ++q) s = __dadd_rn(s, fabs(P.col_val[q]));
+        v[0] = s > v[0] ? s : v[0];
+        v[2] = __dadd_rn(v[2], __dmul_rn(c[j], c[j]));
+    }
+    for (int k = tid; k < P.m; k += stride) {
+        double s = 0.0;
+        for (int q = P.row_ptr[k]; q < P.row_ptr[k + 1]; ++q) s = __dadd_rn(s, fabs(P.val[q]));
+        v[1] = s > v[1] ? s : v[1];
+        const double g = P.grow[k].x;
+        if (isfinite(g)) v[3] = __dadd_rn(v[3], __dmul_rn(g, g));
+    }
+    // maxima through the sum tree would be wrong: reduce them separately
+    __shared__ double mx[2][kPdThreads];
+    mx[0][threadIdx.x] = v[0];
+    mx[1][threadIdx.x] = v[1];
+    __syncthreads();
+    for (int o = kPdThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int i = 0; i < 2; ++i) mx[i][threadIdx.x] = fmax(mx[i][threadIdx.x], mx[i][threadIdx.x + o]);
+        __syncthreads();
+    }
+    // the block maxima enter the same tree from thread 0 (adding zeros is exact)
+    v[0] = threadIdx.x == 0 ? mx[0][0] : 0.0;
+    v[1] = threadIdx.x == 0 ? mx[1][0] : 0.0;
+    block_sum5(v, part);
+}
+
+// KKT sums: [0] sum over finite rows of max(Ax - g, 0)^2, [1] sum over finite rows of g y,
+// [2] c^T x, [3] sum of the squared reduced costs pushing toward an infinite bound, [4] sum of
+// the finite parts of min over [l, u] of r_j x_j (Ax in ax, r = c + A^T y in r).
+__global__ void __launch_bounds__(kPdThreads) k_pdhg_kkt(DevProblem P, const double* c, const double* l,
+                                                         const double* u, const double* x, const double* y,
+                                                         const double* ax, const double* r, double* part) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int k = tid; k < P.m; k += stride) {
+        const double g = P.grow[k].x;
+        if (!isfinite(g)) continue;
+        const double d = __dsub_rn(ax[k], g);
+        if (d > 0.0) v[0] = __dadd_rn(v[0], __dmul_rn(d, d));
+        v[1] = __dadd_rn(v[1], __dmul_rn(g, y[k]));
+    }
+    for (int j = tid; j < P.n; j += stride) {
+        v[2] = __dadd_rn(v[2], __dmul_rn(c[j], x[j]));
+        const double rj = r[j];
+        const bool lf = isfinite(l[j]), uf = isfinite(u[j]);
+        if (rj > 0.0 && !lf) v[3] = __dadd_rn(v[3], __dmul_rn(rj, rj));
+        if (rj < 0.0 && !uf) v[3] = __dadd_rn(v[3], __dmul_rn(rj, rj));
+        v[4] = __dadd_rn(v[4], rj > 0.0 ? __dmul_rn(rj, lf ? l[j] : 0.0) : __dmul_rn(rj, uf ? u[j] : 0.0));
+    }
+    block_sum5(v, part);
+}
+
+// sums (or, for the step inputs' first two, maxima) of the blocks' partials, in block order
+__global__ void k_pdhg_finish(const double* part, int nblocks, int maxima, double* out) {
+    if (threadIdx.x >= 5) return;
+    const int i = threadIdx.x;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+        const double v = part[5 * b + i];
+        s = (maxima && i < 2) ? fmax(s, v) : __dadd_rn(s, v);
+    }
+    out[i] = s;
+}
+
+}  // namespace gpubp
+
+using namespace gpubp;
+
+extern "C" void pdhg_params_default(pdhg_params* p) {
+    if (!p) return;
+    p->iterations = 1000;
+    p->restart_period = 100;
+    p->step = 0.0;
+    p->primal_weight = 0.0;
+}
+
+extern "C" int pdhg_solve(mip_problem* p, const double* lb, const double* ub, double* x, double* y,
+                          const pdhg_params* params, pdhg_result* result, void* stream) {
+    if (!p || !result || (p->n && (!lb || !ub || !x)) || (p->m && !y)) {
+        set_error("pdhg_solve: null argument");
+        return BP_ERR_INVALID;
+    }
+    pdhg_params prm;
+    if (params) prm = *params;
+    else pdhg_params_default(&prm);
+    if (prm.iterations < 0 || prm.restart_period < 0 || !(prm.step >= 0.0) || !(prm.primal_weight >= 0.0)) {
+        set_error("pdhg_solve: invalid parameters");
+        return BP_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = p->n, m = p->m, np_ = p->dp.npieces;
+    memset(result, 0, sizeof(*result));
+    std::vector<void*> tmp;
+    auto alloc = [&](double** ptr, size_t count) -> int {
+        void* q = nullptr;
+        cudaError_t e = cudaMallocAsync(&q, (count ? count : 1) * sizeof(double), s);
+        if (e != cudaSuccess) return fail_cuda(e, "cudaMallocAsync");
+        tmp.push_back(q);
+        *ptr = static_cast<double*>(q);
+        return BP_OK;
+    };
+    auto release = [&]() {
+        for (void* q : tmp) cudaFreeAsync(q, s);
+        tmp.clear();
+    };
+#define PD_TRY(expr)                       \
+    do {                                   \
+        int _r = (expr);                   \
+        if (_r != BP_OK) {                 \
+            release();                     \
+            return _r;                     \
+        }                                  \
+    } while (0)
+#define PD_CUDA(expr)                                      \
+    do {                                                   \
+        cudaError_t _e = (expr);                           \
+        if (_e != cudaSuccess) {                           \
+            release();                                     \
+            return fail_cuda(_e, #expr);                   \
+        }                                                  \
+    } while (0)
+    const bool restarts = prm.restart_period > 0;
+    double *xn, *xe, *yn, *part, *xs = nullptr, *ys = nullptr, *red, *sums;
+    PD_TRY(alloc(&xn, (size_t)n));
+    PD_TRY(alloc(&xe, (size_t)n));
+    PD_TRY(alloc(&yn, (size_t)m));
+    PD_TRY(alloc(&part, (size_t)np_));
+    PD_TRY(alloc(&red, 5 * (size_t)kPdRedBlocks));
+    PD_TRY(alloc(&sums, 5));
+    if (restarts) {
+        PD_TRY(alloc(&xs, (size_t)n));
+        PD_TRY(alloc(&ys, (size_t)m));
+        PD_CUDA(cudaMemsetAsync(xs, 0, sizeof(double) * (size_t)n, s));
+        PD_CUDA(cudaMemsetAsync(ys, 0, sizeof(double) * (size_t)m, s));
+    }
+    double hs[5];
+    // step and primal weight
+    double eta = prm.step, omega = prm.primal_weight;
+    if (eta == 0.0 || omega == 0.0) {
+        k_pdhg_norms<<<kPdRedBlocks, kPdThreads, 0, s>>>(p->dp, p->obj, red);
+        k_pdhg_finish<<<1, 32, 0, s>>>(red, kPdRedBlocks, 1, sums);
+        PD_CUDA(cudaGetLastError());
+        PD_CUDA(cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, s));
+        PD_CUDA(cudaStreamSynchronize(s));
+        if (eta == 0.0) eta = (hs[0] > 0.0 && hs[1] > 0.0) ? 0.9 / std::sqrt(hs[0] * hs[1]) : 1.0;
+        if (omega == 0.0) {
+            const double nc = std::sqrt(hs[2]), ng = std::sqrt(hs[3]);
+            omega = (nc > 0.0 && ng > 0.0) ? nc / ng : 1.0;
+        }
+    }
+    PdhgVecs V{p->obj, lb, ub, eta / omega, eta * omega};
+    const int grid = p->sms * 8;   // 8 blocks of 256 threads per SM
+    double *xc = x, *xo = xn, *yc = y, *yo = yn;
+    int restarts_done = 0;
+    for (int it = 0; it < prm.iterations; ++it) {
+        k_pdhg_cols<<<grid, kPdThreads, 0, s>>>(p->dp, V, xc, yc, xo, xe, xs, 0);
+        k_pdhg_rows<<<grid, kPdThreads, 0, s>>>(p->dp, V, xe, yc, yo, ys, part, 0);
+        if (np_) k_pdhg_long<<<grid, kPdThreads, 0, s>>>(p->dp, V, part, yc, yo, ys, 0);
+        std::swap(xc, xo);
+        std::swap(yc, yo);
+        if (restarts && (it + 1) % prm.restart_period == 0) {
+            k_pdhg_restart<<<grid, kPdThreads, 0, s>>>(n, m, (double)prm.restart_period, xc, yc, xs, ys);
+            ++restarts_done;
+        }
+    }
+    PD_CUDA(cudaGetLastError());
+    if (xc != x && n) PD_CUDA(cudaMemcpyAsync(x, xc, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    if (yc != y && m) PD_CUDA(cudaMemcpyAsync(y, yc, sizeof(double) * (size_t)m, cudaMemcpyDeviceToDevice, s));
+    // KKT measures of the final iterate: A x into yn, c + A^T y into xn
+    k_pdhg_rows<<<grid, kPdThreads, 0, s>>>(p->dp, V, x, y, yn, nullptr, part, 1);
+    if (np_) k_pdhg_long<<<grid, kPdThreads, 0, s>>>(p->dp, V, part, y, yn, nullptr, 1);
+    k_pdhg_cols<<<grid, kPdThreads, 0, s>>>(p->dp, V, x, y, xn, xe, nullptr, 1);
+    k_pdhg_kkt<<<kPdRedBlocks, kPdThreads, 0, s>>>(p->dp, p->obj, lb, ub, x, y, yn, xn, red);
+    k_pdhg_finish<<<1, 32, 0, s>>>(red, kPdRedBlocks, 0, sums);
+    PD_CUDA(cudaGetLastError());
+    PD_CUDA(cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    release();
+    PD_CUDA(cudaStreamSynchronize(s));
+    result->iterations = prm.iterations;
+    result->restarts = restarts_done;
+    result->step = eta;
+    result->primal_weight = omega;
+    result->primal_residual = std::sqrt(hs[0]);
+    result->dual_residual = std::sqrt(hs[3]);
+    result->primal_obj = hs[2];
+    result->dual_obj = -hs[1] + hs[4];
+    p->last_stream = s;
+    return BP_OK;
+#undef PD_TRY
+#undef PD_CUDA
+}
