@@ -9,9 +9,10 @@
 // eta = 0.9 / sqrt(max column |a| sum * max row |a| sum) (a bound on ||A||_2), default primal
 // weight omega = ||c||_2 / ||g||_2 over the finite rows (PDLP's initial weight).
 //
-// One iteration streams the matrix twice, both passes HBM-bound:
-//   k_pdhg_cols   groups of 8 lanes per column over the transpose (row_idx, col_val): A^T y,
-//                 fused with the x step, the extrapolation and the restart sums;
+// One iteration streams the matrix twice (one fused multiply-add per nonzero: this part's FP64
+// rate, about 1.7 lane-operations per SM and clock, is the other bound besides HBM):
+//   k_pdhg_cols   a thread per column over the transpose (row_idx, col_val): A^T y, fused
+//                 with the x step, the extrapolation and the restart sums;
 //   k_pdhg_rows   a flat task space over the row classes of the handle: a warp per piece of a
 //                 long row (partial sum into its slot), a warp per warp row, a thread per
 //                 thread row; finished rows take the y step at once;
@@ -26,7 +27,6 @@
 namespace gpubp {
 
 constexpr int kPdThreads = 256;
-constexpr int kPdColLanes = 8;            // lanes per column
 constexpr int kPdRedBlocks = 304;         // blocks of the reductions (fixed: a fixed order)
 
 struct PdhgVecs {
@@ -42,32 +42,41 @@ struct PdhgVecs {
 __global__ void __launch_bounds__(kPdThreads) k_pdhg_cols(DevProblem P, PdhgVecs V, const double* __restrict__ x,
                                                           const double* __restrict__ y, double* __restrict__ xn,
                                                           double* __restrict__ xe, double* __restrict__ xs, int eval) {
-    const int lane = threadIdx.x & 31, gl = lane & (kPdColLanes - 1);
-    const int groups = (gridDim.x * blockDim.x) / kPdColLanes;
-    const int rpw = 32 / kPdColLanes;
-    const int wi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    for (int jb = wi * rpw; jb < P.n; jb += (groups / rpw) * rpw) {
-        const int j = jb + lane / kPdColLanes;
-        double s = 0.0;
-        if (j < P.n) {
-            const int b = P.col_ptr[j], e = P.col_ptr[j + 1];
-            for (int q = b + gl; q < e; q += kPdColLanes) s = __dadd_rn(s, __dmul_rn(P.col_val[q], y[P.row_idx[q]]));
+    // a thread per column: 32 columns in flight per warp, the column's own vectors loaded
+    // before its sum, the sum's loads unrolled (independent of each other)
+    const int stride = gridDim.x * blockDim.x;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < P.n; j += stride) {
+        const int b = P.col_ptr[j], e = P.col_ptr[j + 1];
+        const double cj = V.c[j];
+        double xj = 0.0, lj = 0.0, uj = 0.0, sj = 0.0;
+        if (!eval) {
+            xj = x[j];
+            lj = V.l[j];
+            uj = V.u[j];
+            if (xs) sj = xs[j];
         }
-#pragma unroll
-        for (int o = kPdColLanes / 2; o > 0; o >>= 1) s = __dadd_rn(s, __shfl_xor_sync(0xffffffffu, s, o));
-        if (j < P.n && gl == 0) {
-            const double r = __dadd_rn(V.c[j], s);
-            if (eval) {
-                xn[j] = r;
-            } else {
-                const double xj = x[j];
-                double v = __dsub_rn(xj, __dmul_rn(V.tau, r));
-                v = v < V.l[j] ? V.l[j] : v;   // max(v, l), then min(., u)
-                v = v > V.u[j] ? V.u[j] : v;
-                xn[j] = v;
-                xe[j] = __dsub_rn(__dmul_rn(2.0, v), xj);
-                if (xs) xs[j] = __dadd_rn(xs[j], v);
-            }
+        double s = 0.0;
+        int q = b;
+        for (; q + 4 <= e; q += 4) {
+            const int r0 = P.row_idx[q], r1 = P.row_idx[q + 1], r2 = P.row_idx[q + 2], r3 = P.row_idx[q + 3];
+            const double a0 = P.col_val[q], a1 = P.col_val[q + 1], a2 = P.col_val[q + 2], a3 = P.col_val[q + 3];
+            const double y0 = y[r0], y1 = y[r1], y2 = y[r2], y3 = y[r3];
+            s = fma(a0, y0, s);
+            s = fma(a1, y1, s);
+            s = fma(a2, y2, s);
+            s = fma(a3, y3, s);
+        }
+        for (; q < e; ++q) s = fma(P.col_val[q], y[P.row_idx[q]], s);
+        const double r = __dadd_rn(cj, s);
+        if (eval) {
+            xn[j] = r;
+        } else {
+            double v = __dsub_rn(xj, __dmul_rn(V.tau, r));
+            v = v < lj ? lj : v;   // max(v, l), then min(., u)
+            v = v > uj ? uj : v;
+            xn[j] = v;
+            xe[j] = __dsub_rn(__dmul_rn(2.0, v), xj);
+            if (xs) xs[j] = __dadd_rn(sj, v);
         }
     }
 }
@@ -86,6 +95,14 @@ __device__ __forceinline__ void pdhg_row_done(const DevProblem& P, const PdhgVec
 }
 
 // ---------------------------------------------------------------- row pass
+// This lane's share of sum over [beg, end) of val * v[col] (nonzeros lane, lane + 32, ...).
+__device__ __forceinline__ double warp_dot(const DevProblem& P, const double* __restrict__ v, int beg, int end,
+                                           int lane) {
+    double s = 0.0;
+    for (int q = beg + lane; q < end; q += 32) s = fma(P.val[q], v[P.col[q]], s);
+    return s;
+}
+
 // Warp tasks [pieces of long rows][warp rows][thread rows in groups of 32]: pieces write their
 // partial sums (slot = the piece's index in the round-0 piece list), the others finish their
 // rows.
@@ -102,16 +119,14 @@ __global__ void __launch_bounds__(kPdThreads) k_pdhg_rows(DevProblem P, PdhgVecs
         if (t < t_pieces) {
             const int4 tk = P.static_tasks[t];
             const int beg = tk.z, end = min(tk.w, tk.z + P.chunk_len);
-            double s = 0.0;
-            for (int q = beg + lane; q < end; q += 32) s = __dadd_rn(s, __dmul_rn(P.val[q], xe[P.col[q]]));
+            const double s0 = warp_dot(P, xe, beg, end, lane);
+            double s = s0;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s = __dadd_rn(s, __shfl_xor_sync(0xffffffffu, s, o));
             if (lane == 0) part[t] = s;
         } else if (t < t_pieces + t_warp) {
             const int k = P.static_list[P.class_off[kClassWarpRow] + (t - t_pieces)];
-            double s = 0.0;
-            for (int q = P.row_ptr[k] + lane; q < P.row_ptr[k + 1]; q += 32)
-                s = __dadd_rn(s, __dmul_rn(P.val[q], xe[P.col[q]]));
+            double s = warp_dot(P, xe, P.row_ptr[k], P.row_ptr[k + 1], lane);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s = __dadd_rn(s, __shfl_xor_sync(0xffffffffu, s, o));
             if (lane == 0) pdhg_row_done(P, V, k, s, y, yn, ys, eval);
@@ -120,7 +135,7 @@ __global__ void __launch_bounds__(kPdThreads) k_pdhg_rows(DevProblem P, PdhgVecs
             if (i < nthread_rows) {
                 const int k = P.static_list[P.class_off[0] + i];
                 double s = 0.0;
-                for (int q = P.row_ptr[k]; q < P.row_ptr[k + 1]; ++q) s = __dadd_rn(s, __dmul_rn(P.val[q], xe[P.col[q]]));
+                for (int q = P.row_ptr[k]; q < P.row_ptr[k + 1]; ++q) s = fma(P.val[q], xe[P.col[q]], s);
                 pdhg_row_done(P, V, k, s, y, yn, ys, eval);
             }
         }
@@ -174,9 +189,10 @@ __device__ void block_sum5(double v[5], double* part) {
 }
 
 // Step-size inputs: [0] max column |a| sum, [1] max row |a| sum (per block maxima), [2] sum of c^2,
-// [3] sum of g^2 over finite rows (per block sums).
+// [3] sum of g^2 over finite rows (per block sums).  A thread per column, a warp per row.
 __global__ void __launch_bounds__(kPdThreads) k_pdhg_norms(DevProblem P, const double* c, double* part) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
     double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int j = tid; j < P.n; j += stride) {
         double s = 0.0;
@@ -184,12 +200,16 @@ __global__ void __launch_bounds__(kPdThreads) k_pdhg_norms(DevProblem P, const d
         v[0] = s > v[0] ? s : v[0];
         v[2] = __dadd_rn(v[2], __dmul_rn(c[j], c[j]));
     }
-    for (int k = tid; k < P.m; k += stride) {
+    for (int k = tid >> 5; k < P.m; k += stride >> 5) {
         double s = 0.0;
-        for (int q = P.row_ptr[k]; q < P.row_ptr[k + 1]; ++q) s = __dadd_rn(s, fabs(P.val[q]));
-        v[1] = s > v[1] ? s : v[1];
-        const double g = P.grow[k].x;
-        if (isfinite(g)) v[3] = __dadd_rn(v[3], __dmul_rn(g, g));
+        for (int q = P.row_ptr[k] + lane; q < P.row_ptr[k + 1]; q += 32) s = __dadd_rn(s, fabs(P.val[q]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s = __dadd_rn(s, __shfl_xor_sync(0xffffffffu, s, o));
+        if (lane == 0) {
+            v[1] = s > v[1] ? s : v[1];
+            const double g = P.grow[k].x;
+            if (isfinite(g)) v[3] = __dadd_rn(v[3], __dmul_rn(g, g));
+        }
     }
     // maxima through the sum tree would be wrong: reduce them separately
     __shared__ double mx[2][kPdThreads];
@@ -233,16 +253,30 @@ __global__ void __launch_bounds__(kPdThreads) k_pdhg_kkt(DevProblem P, const dou
     block_sum5(v, part);
 }
 
-// sums (or, for the step inputs' first two, maxima) of the blocks' partials, in block order
-__global__ void k_pdhg_finish(const double* part, int nblocks, int maxima, double* out) {
-    if (threadIdx.x >= 5) return;
-    const int i = threadIdx.x;
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) {
-        const double v = part[5 * b + i];
-        s = (maxima && i < 2) ? fmax(s, v) : __dadd_rn(s, v);
+// sums (or, for the step inputs' first two, maxima) of the blocks' partials: thread t takes
+// blocks t, t + 256, ..., then a fixed tree (one block of kPdThreads threads)
+__global__ void __launch_bounds__(kPdThreads) k_pdhg_finish(const double* part, int nblocks, int maxima, double* out) {
+    __shared__ double sh[5][kPdThreads];
+    for (int i = 0; i < 5; ++i) {
+        const bool mx = maxima && i < 2;
+        double s = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += kPdThreads) {
+            const double v = part[5 * b + i];
+            s = mx ? fmax(s, v) : __dadd_rn(s, v);
+        }
+        sh[i][threadIdx.x] = s;
     }
-    out[i] = s;
+    __syncthreads();
+    for (int o = kPdThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int i = 0; i < 5; ++i) {
+                const bool mx = maxima && i < 2;
+                sh[i][threadIdx.x] = mx ? fmax(sh[i][threadIdx.x], sh[i][threadIdx.x + o])
+                                        : __dadd_rn(sh[i][threadIdx.x], sh[i][threadIdx.x + o]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x < 5) out[threadIdx.x] = sh[threadIdx.x][0];
 }
 
 }  // namespace gpubp
@@ -321,7 +355,7 @@ extern "C" int pdhg_solve(mip_problem* p, const double* lb, const double* ub, do
     double eta = prm.step, omega = prm.primal_weight;
     if (eta == 0.0 || omega == 0.0) {
         k_pdhg_norms<<<kPdRedBlocks, kPdThreads, 0, s>>>(p->dp, p->obj, red);
-        k_pdhg_finish<<<1, 32, 0, s>>>(red, kPdRedBlocks, 1, sums);
+        k_pdhg_finish<<<1, kPdThreads, 0, s>>>(red, kPdRedBlocks, 1, sums);
         PD_CUDA(cudaGetLastError());
         PD_CUDA(cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, s));
         PD_CUDA(cudaStreamSynchronize(s));
@@ -332,13 +366,21 @@ extern "C" int pdhg_solve(mip_problem* p, const double* lb, const double* ub, do
         }
     }
     PdhgVecs V{p->obj, lb, ub, eta / omega, eta * omega};
-    const int grid = p->sms * 8;   // 8 blocks of 256 threads per SM
+    // grids of resident blocks (every block stays resident through its grid-stride loop)
+    static int occ[3] = {-1, -1, -1};
+    if (occ[0] < 0) {
+        PD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_pdhg_cols, kPdThreads, 0));
+        PD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_pdhg_rows, kPdThreads, 0));
+        PD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], k_pdhg_long, kPdThreads, 0));
+    }
+    const int grid_c = p->sms * (occ[0] > 0 ? occ[0] : 1), grid = p->sms * (occ[1] > 0 ? occ[1] : 1);
+    const int grid_l = p->sms * (occ[2] > 0 ? occ[2] : 1);
     double *xc = x, *xo = xn, *yc = y, *yo = yn;
     int restarts_done = 0;
     for (int it = 0; it < prm.iterations; ++it) {
-        k_pdhg_cols<<<grid, kPdThreads, 0, s>>>(p->dp, V, xc, yc, xo, xe, xs, 0);
+        k_pdhg_cols<<<grid_c, kPdThreads, 0, s>>>(p->dp, V, xc, yc, xo, xe, xs, 0);
         k_pdhg_rows<<<grid, kPdThreads, 0, s>>>(p->dp, V, xe, yc, yo, ys, part, 0);
-        if (np_) k_pdhg_long<<<grid, kPdThreads, 0, s>>>(p->dp, V, part, yc, yo, ys, 0);
+        if (np_) k_pdhg_long<<<grid_l, kPdThreads, 0, s>>>(p->dp, V, part, yc, yo, ys, 0);
         std::swap(xc, xo);
         std::swap(yc, yo);
         if (restarts && (it + 1) % prm.restart_period == 0) {
@@ -351,10 +393,10 @@ extern "C" int pdhg_solve(mip_problem* p, const double* lb, const double* ub, do
     if (yc != y && m) PD_CUDA(cudaMemcpyAsync(y, yc, sizeof(double) * (size_t)m, cudaMemcpyDeviceToDevice, s));
     // KKT measures of the final iterate: A x into yn, c + A^T y into xn
     k_pdhg_rows<<<grid, kPdThreads, 0, s>>>(p->dp, V, x, y, yn, nullptr, part, 1);
-    if (np_) k_pdhg_long<<<grid, kPdThreads, 0, s>>>(p->dp, V, part, y, yn, nullptr, 1);
-    k_pdhg_cols<<<grid, kPdThreads, 0, s>>>(p->dp, V, x, y, xn, xe, nullptr, 1);
+    if (np_) k_pdhg_long<<<grid_l, kPdThreads, 0, s>>>(p->dp, V, part, y, yn, nullptr, 1);
+    k_pdhg_cols<<<grid_c, kPdThreads, 0, s>>>(p->dp, V, x, y, xn, xe, nullptr, 1);
     k_pdhg_kkt<<<kPdRedBlocks, kPdThreads, 0, s>>>(p->dp, p->obj, lb, ub, x, y, yn, xn, red);
-    k_pdhg_finish<<<1, 32, 0, s>>>(red, kPdRedBlocks, 0, sums);
+    k_pdhg_finish<<<1, kPdThreads, 0, s>>>(red, kPdRedBlocks, 0, sums);
     PD_CUDA(cudaGetLastError());
     PD_CUDA(cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, s));
     release();
