@@ -455,12 +455,15 @@ def _sign_test(wins, losses):
     return min(1.0, 2.0 * sum(math.comb(n, i) for i in range(k + 1)) / 2.0 ** n)
 
 
-def learned_experiment(pkg, torch, dev, nnz, eq_fraction, train_idx, train_seeds, test_idx, test_seeds):
+def learned_experiment(pkg, torch, dev, nnz, eq_fraction, train_idx, train_seeds, test_idx, test_seeds,
+                       lp_iterations=0):
     """Train the scorer on the plain trajectories of `train_idx` rounding instances (one run per
     seed of `train_seeds`, labels from the runs that ended feasible), then run both orders with
     the same seeds on the held-out `test_idx` instances.  Feasible means verified again (fresh
     propagation with the integers fixed, and a continuous completion by HiGHS).  Bulks to
-    feasibility are compared paired: over the (instance, seed) runs that both orders solve."""
+    feasibility are compared paired: over the (instance, seed) runs that both orders solve.
+    lp_iterations > 0: the point to round is the approximate LP (pdhg_solve from zero, that many
+    iterations, restarts every 100) instead of the planted point plus noise."""
     import numpy as np
     from paper_2510_20499_gb300 import learned, synth
     fp = dict(bulk_rule=1, fraction=0.01)
@@ -470,6 +473,8 @@ def learned_experiment(pkg, torch, dev, nnz, eq_fraction, train_idx, train_seeds
         p, x = synth.rounding_instance(i, nnz, eq_fraction=eq_fraction)
         prob = pkg.Problem(p)
         xd, lb, ub = (torch.tensor(a, device=dev) for a in (x, p.lb, p.ub))
+        if lp_iterations:
+            xd = _lp_point(prob, p, lb, ub, torch, dev, lp_iterations)
         d = learned.collect(prob, xd, lb, ub, seeds=train_seeds, **fp)
         d["runs"] = None
         data.append(d)
@@ -478,6 +483,7 @@ def learned_experiment(pkg, torch, dev, nnz, eq_fraction, train_idx, train_seeds
     losses = learned.train(scorer, data, epochs=6, batch=4096, lr=3e-3, seed=0)
     t_train = time.perf_counter() - t0
     out = {"nnz": nnz, "eq_fraction": eq_fraction,
+           "point": f"approximate LP ({lp_iterations} PDHG iterations)" if lp_iterations else "planted + N(0, 0.3)",
            "train": {"instances": len(train_idx), "seeds": len(train_seeds),
                      "runs": len(train_idx) * len(train_seeds),
                      "feasible_runs": int(sum(d["feasible"] for d in data)),
@@ -492,6 +498,8 @@ def learned_experiment(pkg, torch, dev, nnz, eq_fraction, train_idx, train_seeds
         p, x = synth.rounding_instance(i, nnz, eq_fraction=eq_fraction)
         prob = pkg.Problem(p)
         xd, lb, ub = (torch.tensor(a, device=dev) for a in (x, p.lb, p.ub))
+        if lp_iterations:
+            xd = _lp_point(prob, p, lb, ub, torch, dev, lp_iterations)
         order, up = learned.scores(prob, scorer, xd, lb, ub)
         for s in test_seeds:
             for arm, kw in (("plain", {}), ("learned", dict(order_score=order, up_prob=up))):
@@ -529,18 +537,29 @@ def learned_experiment(pkg, torch, dev, nnz, eq_fraction, train_idx, train_seeds
     return out
 
 
+def _lp_point(prob, p, lb, ub, torch, dev, iterations):
+    """The approximate LP's primal iterate (pdhg_solve from zero, restarts every 100)."""
+    x = torch.zeros(p.n, dtype=torch.float64, device=dev).clamp_(lb, ub)
+    y = torch.zeros(p.m, dtype=torch.float64, device=dev)
+    prob.pdhg(lb, ub, x, y, iterations=iterations, restart_period=100)
+    return x
+
+
 def learned_extra(pkg, torch, dev):
     """The learned rounding order against the paper's order in fix-and-propagate (1% of the
     integer variables per bulk), at two sizes.  100k nonzeros (20% equality pairs): trained on 16
     instances x 8 seeds, tested on 12 held-out instances x 4 seeds.  1M nonzeros (1% equality
     pairs, with which the plain method reaches feasibility in part of the runs): trained on 16
-    instances x 4 seeds, tested on 8 held-out instances x 2 seeds.  The full 1M experiment (160
-    training and 40 test instances) is the separate `learned_full` extra."""
+    instances x 4 seeds, tested on 8 held-out instances x 2 seeds, once from the planted point
+    plus noise and once from the approximate LP (2,000 PDHG iterations).  The full 1M experiment
+    (160 training and 40 test instances) is the separate `learned_full` extra."""
     out = {"workload": "rounding instances (mixed power-law, planted point + N(0, 0.3) as the fractional point)"}
     out["100k_nnz"] = learned_experiment(pkg, torch, dev, 100_000, 0.2, range(16), range(100, 108),
                                          range(1000, 1012), range(1, 5))
     out["1m_nnz"] = learned_experiment(pkg, torch, dev, 1_000_000, 0.01, range(16), range(100, 104),
                                        range(2000, 2008), range(1, 3))
+    out["1m_nnz_lp_point"] = learned_experiment(pkg, torch, dev, 1_000_000, 0.01, range(16), range(100, 104),
+                                                range(2000, 2008), range(1, 3), lp_iterations=2000)
     return out
 
 
