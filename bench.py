@@ -113,7 +113,7 @@ class ClockSampler:
 # DRAM bytes (read + write) of one bp_kernel launch on this workload, from the ncu capture
 # summarised in profiles/bp_kernel_mixed_powerlaw_5M.md; reported only while the kernel's
 # sources are the ones that capture was taken on.
-NCU_TRAFFIC = {"sources_sha256_16": "cba2857eae9b4b71", "bytes": 217_590_016}
+NCU_TRAFFIC = {"sources_sha256_16": "4ea1c434c63a4110", "bytes": 219_092_224}
 KERNEL_SOURCES = ["bp_engine.cu", "bp_device.cuh", "bp_host.h"]
 
 
