@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the probing, batch, learned and scorer measurements")
-    ap.add_argument("--extras", default="probing,batch,fp,learned,scorer,pdhg",
+    ap.add_argument("--extras", default="probing,batch,fp,learned,scorer,pdhg,local_mip",
                     help="comma-separated subset of the extra measurements to run (learned_full, the "
                          "160/40-instance learned-order experiment at 1M nonzeros, is not in the default set)")
     return ap.parse_args()
@@ -642,6 +642,39 @@ def pdhg_extra(pkg, torch, dev):
                          "frac": bytes_it / per_it / 1e6 / hbm}}
 
 
+def local_mip_extra(pkg, torch, dev):
+    """The local search's move scoring (local_search_mtm) on the knapsack/cover instance (50k x
+    100k, 1M nonzeros) from a random 0/1 point: time per iteration (every violated row's
+    candidates scored in full, the best applied or the weights bumped) from the difference of a
+    1,100- and a 100-iteration call, and the violation left."""
+    import numpy as np
+    from paper_2510_20499_gb300 import synth
+    p = synth.knapsack_cover()
+    prob = pkg.Problem(p)
+    lb, ub = torch.tensor(p.lb, device=dev), torch.tensor(p.ub, device=dev)
+    x0 = np.clip((np.random.default_rng(3).random(p.n) < 0.5).astype(float), p.lb, p.ub)
+
+    def run(iters):
+        x = torch.tensor(x0, device=dev)
+        w = torch.ones(p.m, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = prob.local_search(lb, ub, x, w, iterations=iters)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), r
+    run(100)
+    t_short = min(run(100)[0] for _ in range(3))
+    t_long, r = min((run(1100) for _ in range(3)), key=lambda q: q[0])
+    per_it = (t_long - t_short) / 1000.0
+    r0 = run(0)[1]
+    return {"workload": f"knapsack/cover {p.m} x {p.n}, {p.nnz} nnz, random 0/1 start",
+            "ms_per_iteration": per_it, "iterations_per_s": 1e3 / per_it,
+            "start": {"violated": r0["violated"], "weighted_violation": r0["weighted_violation"]},
+            "after_1100": {k: r[k] for k in ("moves", "bumps", "violated", "weighted_violation")}}
+
+
 def scorer_extra(pkg, torch, dev, tflops_peak):
     """The scorer's forward and training-step throughput on 1M rows of BF16 features (the
     tcgen05 MLP kernel k_mlp), against the measured BF16 tensor peak."""
@@ -794,14 +827,16 @@ def main():
     }
     if rank == 0 and not args.no_extras:
         todo = [e for e in args.extras.split(",") if e]
-        bad = [e for e in todo if e not in ("probing", "batch", "fp", "learned", "learned_full", "scorer", "pdhg")]
+        bad = [e for e in todo
+               if e not in ("probing", "batch", "fp", "learned", "learned_full", "scorer", "pdhg", "local_mip")]
         if bad:
             raise SystemExit(f"unknown extras: {bad}")
         fns = {"probing": lambda: probing_extra(pkg, torch, dev), "batch": lambda: batch_extra(pkg, torch, dev),
                "fp": lambda: fp_extra(pkg, torch, dev),
                "learned": lambda: learned_extra(pkg, torch, dev),
                "learned_full": lambda: learned_full_extra(pkg, torch, dev),
-               "pdhg": lambda: pdhg_extra(pkg, torch, dev), "scorer": lambda: scorer_extra(pkg, torch, dev, tensor_peak())}
+               "pdhg": lambda: pdhg_extra(pkg, torch, dev), "local_mip": lambda: local_mip_extra(pkg, torch, dev),
+               "scorer": lambda: scorer_extra(pkg, torch, dev, tensor_peak())}
         out["extras"] = {e: fns[e]() for e in todo}
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(p)

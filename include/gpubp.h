@@ -499,6 +499,47 @@ int pdhg_solve(mip_problem *p, const double *lb, const double *ub, double *x, do
                const pdhg_params *params, pdhg_result *result, void *stream);
 
 /*
+ * local_search_mtm -- the local search's move scoring (Section 2.4, the paper's GPU Local-MIP):
+ * the mixed-tight-move core under a weighted violation F = sum_k w_k max(0, (A x)_k - g_k)
+ * (rows with g = +inf are free).
+ *
+ * Each iteration forms, for every violated row and every variable in it, the value that alone
+ * satisfies the row (integer variables by the smallest integer step: x - ceil(v / a) for
+ * a > 0, x + ceil(v / |a|) for a < 0; continuous ones exactly), clamped to [lb, ub], and
+ * scores every such move by the drop of F over the variable's column (rows ascending), all
+ * scores recomputed each iteration.  The best move (largest score; ties: smallest variable,
+ * then smallest value) is applied when its score is positive; otherwise every violated row's
+ * weight grows by 1.  Lift and breakthrough moves (objective improvement) are not included.
+ * Deterministic: the same inputs give the same moves bit for bit.
+ *
+ * lb, ub:  DEVICE double[n] bounds (not modified).
+ * x:       DEVICE double[n], the start point on entry, the final point on return.
+ * w:       DEVICE double[m], the weights (1 for a fresh search), updated in place.
+ * params:  iterations >= 0.
+ * result:  HOST pointer, valid at return (the call synchronises the stream): moves applied,
+ *          weight bumps, violated rows at the end, sum of w_k v_k, and c^T x (the handle's
+ *          objective).
+ * Scratch: m doubles and a few KB, stream-ordered, freed at return.
+ * Returns BP_OK, BP_ERR_INVALID, BP_ERR_OOM or BP_ERR_CUDA.
+ */
+typedef struct {
+    int32_t iterations;
+    int32_t reserved;
+} ls_params;
+
+typedef struct {
+    int32_t iterations;
+    int32_t moves;
+    int32_t bumps;
+    int32_t violated;
+    double weighted_violation;
+    double objective;
+} ls_result;
+
+int local_search_mtm(mip_problem *p, const double *lb, const double *ub, double *x, double *w,
+                     const ls_params *params, ls_result *result, void *stream);
+
+/*
  * fix_and_propagate -- bulk rounding with bound propagation (Section 2.3, Algorithm 1; LP
  * polish off; the repair optional and off by default, as in the paper's experiments).
  *

@@ -84,6 +84,18 @@ class PdhgResult(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class LsParams(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("reserved", C.c_int32)]
+
+
+class LsResult(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("moves", C.c_int32), ("bumps", C.c_int32), ("violated", C.c_int32),
+                ("weighted_violation", C.c_double), ("objective", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class BpTuning(C.Structure):
     _fields_ = [("warp_min", C.c_int32), ("block_min", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("chunk_len", C.c_int32)]
@@ -156,6 +168,8 @@ SIGNATURES = {
     "bp_probe_priority": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.POINTER(C.c_int32), C.c_void_p]),
     "fp_params_default": (None, [C.POINTER(FpParams)]),
+    "local_search_mtm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(LsParams),
+                                   C.POINTER(LsResult), C.c_void_p]),
     "pdhg_params_default": (None, [C.POINTER(PdhgParams)]),
     "pdhg_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(PdhgParams),
                              C.POINTER(PdhgResult), C.c_void_p]),
@@ -412,6 +426,19 @@ def _pdhg(prob, lb, ub, x, y, iterations=1000, restart_period=100, step=0.0, pri
 
 
 Problem.pdhg = _pdhg
+
+
+def _local_search(prob, lb, ub, x, w, iterations=100, stream=None):
+    """local_search_mtm on device tensors: lb, ub and x (n), w (m) float64; x and w are updated
+    in place.  Returns the result dict."""
+    prm = LsParams(int(iterations), 0)
+    res = LsResult()
+    _check(lib().local_search_mtm(prob.h, _ptr(lb), _ptr(ub), _ptr(x), _ptr(w), C.byref(prm), C.byref(res),
+                                  _stream(stream)))
+    return res.as_dict()
+
+
+Problem.local_search = _local_search
 
 RESULT_FIELDS = [f for f, _ in BpResult._fields_ if f != "reserved"]
 

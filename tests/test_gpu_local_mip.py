@@ -1,0 +1,100 @@
+"""GPU local search move scoring (local_search_mtm through the C ABI) against the oracle
+(oracle/local_mip.py).  Both sides apply the same operations in the same order, so points,
+weights and counts must agree bit for bit."""
+import numpy as np
+import pytest
+
+from oracle import local_mip as lm
+from paper_2510_20499_gb300 import synth
+from tests.helpers import load_golden, milp_from_dense
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("gpu tests need a CUDA device")
+    import paper_2510_20499_gb300 as pkg
+    return pkg
+
+
+def _t(a):
+    import torch
+    return torch.tensor(np.asarray(a, dtype=np.float64), device="cuda")
+
+
+def _gpu(pkg, p, x0, w0, iterations):
+    prob = pkg.Problem(p)
+    x, w = _t(x0), _t(w0)
+    r = prob.local_search(_t(p.lb), _t(p.ub), x, w, iterations=iterations)
+    return x.cpu().numpy(), w.cpu().numpy(), r
+
+
+def _same(p, x0, w0, iterations, pkg):
+    ox, ow, orr = lm.search(p, p.lb, p.ub, x0, w0, iterations)
+    gx, gw, gr = _gpu(pkg, p, x0, w0, iterations)
+    np.testing.assert_array_equal(gx, ox)
+    np.testing.assert_array_equal(gw, ow)
+    for k in ("moves", "bumps", "violated"):
+        assert gr[k] == orr[k], (k, gr, orr)
+    assert abs(gr["weighted_violation"] - orr["weighted_violation"]) <= 1e-9 * max(1.0, orr["weighted_violation"])
+    return orr
+
+
+@pytest.mark.parametrize("case", range(2))
+def test_hand_worked_steps(pkg, case):
+    c = load_golden("local_mip_small.json")["cases"][case]
+    p = milp_from_dense(c["A"], c["g"], c["lb"], c["ub"], c["is_int"])
+    p.c = np.array(c["c"], dtype=float)
+    for k, (want_x, want_w) in enumerate(c["steps"]):
+        x, w, r = _gpu(pkg, p, c["x0"], c["w0"], k + 1)
+        np.testing.assert_array_equal(x, want_x)
+        np.testing.assert_array_equal(w, want_w)
+    assert r["moves"] == c["moves"] and r["bumps"] == c["bumps"]
+
+
+def _integer_problem(seed, m, n):
+    p = synth.random_milp(seed, m, n, len_lo=2, len_hi=8, int_fraction=1.0, slack_scale=0.3, integer_coefs=True)
+    p.lb = np.where(np.isfinite(p.lb), p.lb, -5.0)
+    p.ub = np.where(np.isfinite(p.ub), p.ub, 5.0)
+    return p
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_matches_oracle_integer_data(pkg, seed):
+    p = _integer_problem(500 + seed, 300, 250)
+    x0 = np.clip(np.round(np.random.default_rng(seed).normal(0, 3, p.n)), p.lb, p.ub)
+    r = _same(p, x0, np.ones(p.m), 60, pkg)
+    assert r["moves"] > 0
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_matches_oracle_general_data(pkg, seed):
+    """Non-integer coefficients and continuous variables: the same operation order on both sides
+    still gives identical results."""
+    p = synth.random_milp(600 + seed, 200, 180, len_lo=2, len_hi=8, int_fraction=0.6, slack_scale=0.3)
+    p.lb = np.where(np.isfinite(p.lb), p.lb, -50.0)
+    p.ub = np.where(np.isfinite(p.ub), p.ub, 50.0)
+    rng = np.random.default_rng(seed)
+    x0 = np.clip(rng.normal(0, 10, p.n), p.lb, p.ub)
+    x0[p.is_int == 1] = np.round(x0[p.is_int == 1])
+    _same(p, x0, np.ones(p.m), 40, pkg)
+
+
+def test_matches_oracle_knapsack_cover(pkg):
+    """A 2k x 4k, 40k-nonzero knapsack/cover instance from a random 0/1 point, 80 iterations."""
+    p = synth.knapsack_cover(seed=91, m=2000, n=4000, nnz=40_000)
+    x0 = (np.random.default_rng(3).random(p.n) < 0.5).astype(float)
+    x0 = np.clip(x0, p.lb, p.ub)
+    r = _same(p, x0, np.ones(p.m), 80, pkg)
+    assert r["moves"] > 0
+
+
+def test_repeatable(pkg):
+    p = _integer_problem(77, 400, 300)
+    x0 = np.clip(np.round(np.random.default_rng(0).normal(0, 3, p.n)), p.lb, p.ub)
+    a = _gpu(pkg, p, x0, np.ones(p.m), 50)
+    b = _gpu(pkg, p, x0, np.ones(p.m), 50)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2] == b[2]
