@@ -456,7 +456,8 @@ void fp_params_default(fp_params *p);   /* seed 1, sqrt rule, last_single 36, fr
  * pdhg_solve -- the approximate LP (Sections 1 and 2.5: the paper's GPU PDLP, warm-started).
  *
  * Primal-dual hybrid gradient for min c^T x s.t. A x <= g, lb <= x <= ub (c: the handle's
- * objective; rows with g = +inf are free), with row duals y >= 0:
+ * objective, or params->objective when given; rows with g = +inf are free), with row duals
+ * y >= 0:
  *     x+ = proj_[lb, ub](x - tau (c + A^T y)),  y+ = max(0, y + sigma (A (2 x+ - x) - g)),
  *     tau = step / primal_weight,  sigma = step * primal_weight,
  * and with restart_period R > 0 every R iterations the iterate is replaced by the mean of the
@@ -481,6 +482,7 @@ typedef struct {
     int32_t restart_period;
     double step;
     double primal_weight;
+    const double *objective;   /* DEVICE double[n] in place of the handle's objective, or NULL */
 } pdhg_params;
 
 typedef struct {
@@ -538,6 +540,49 @@ typedef struct {
 
 int local_search_mtm(mip_problem *p, const double *lb, const double *ub, double *x, double *w,
                      const ls_params *params, ls_result *result, void *stream);
+
+/*
+ * extended_fp -- the extended feasibility pump's orchestration (Section 2.5, Algorithm 2), in
+ * generation mode (it stops at the first feasible point; no objective cut).
+ *
+ * Start: the approximate LP from zero (pdhg_solve, lp_iterations), snapped to multiples of
+ * 2^-20, rounded by fix_and_propagate (seed), then local_search_mtm (ls_iterations, fresh
+ * weights); failing that, local_search_mtm from the all-zero point; the loop starts from the
+ * end point with fewer violated rows and keeps its weights.  Each round: project (pdhg_solve
+ * warm-started from the previous primal and dual iterates, objective +1 / -1 for an integer
+ * variable at its lower / upper bound, 0 otherwise), snap, distance = sum over integer
+ * variables of |projection - point|, fix_and_propagate from the projection (seed + round + 1),
+ * local_search_mtm for ls_iterations / 5 (a feasible point ends the pump); a cycle (at least
+ * cycle_window earlier distances, and the distance improving on their mean by no more than
+ * cycle_ratio of it) is broken by local_search_mtm from the point with the kept weights
+ * (ls_iterations), otherwise the next point is the projection rounded to the nearest integers.
+ *
+ * x_out:   DEVICE double[n]: the feasible point found, else the loop's last point.
+ * result:  HOST pointer (the call synchronises the stream): status FP_FEASIBLE / FP_INFEASIBLE,
+ *          found_at (-2 the start rounding, -1 the all-zero start, r >= 0 round r, -3 none),
+ *          rounds run, cycle breaks, the last distance.
+ * Returns BP_OK, BP_ERR_INVALID, BP_ERR_OOM, BP_ERR_CUDA or BP_ERR_TIMEOUT.
+ */
+typedef struct {
+    int32_t rounds;            /* FP rounds at most (20) */
+    int32_t lp_iterations;     /* PDHG iterations of the LP and of each projection (500) */
+    int32_t ls_iterations;     /* local search iterations (200) */
+    int32_t cycle_window;      /* N (3) */
+    double cycle_ratio;        /* (0.1) */
+    uint64_t seed;             /* fix_and_propagate's seed of the start; round r uses seed + r + 1 */
+} efp_params;
+
+typedef struct {
+    int32_t status;
+    int32_t found_at;
+    int32_t rounds;
+    int32_t cycles;
+    double last_distance;
+} efp_result;
+
+void efp_params_default(efp_params *p);
+int extended_fp(mip_problem *p, const double *lb, const double *ub, double *x_out, const efp_params *params,
+                efp_result *result, void *stream);
 
 /*
  * fix_and_propagate -- bulk rounding with bound propagation (Section 2.3, Algorithm 1; LP

@@ -72,7 +72,7 @@ class FpResult(C.Structure):
 
 class PdhgParams(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("restart_period", C.c_int32), ("step", C.c_double),
-                ("primal_weight", C.c_double)]
+                ("primal_weight", C.c_double), ("objective", C.c_void_p)]
 
 
 class PdhgResult(C.Structure):
@@ -91,6 +91,19 @@ class LsParams(C.Structure):
 class LsResult(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("moves", C.c_int32), ("bumps", C.c_int32), ("violated", C.c_int32),
                 ("weighted_violation", C.c_double), ("objective", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class EfpParams(C.Structure):
+    _fields_ = [("rounds", C.c_int32), ("lp_iterations", C.c_int32), ("ls_iterations", C.c_int32),
+                ("cycle_window", C.c_int32), ("cycle_ratio", C.c_double), ("seed", C.c_uint64)]
+
+
+class EfpResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("found_at", C.c_int32), ("rounds", C.c_int32), ("cycles", C.c_int32),
+                ("last_distance", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -168,6 +181,9 @@ SIGNATURES = {
     "bp_probe_priority": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.POINTER(C.c_int32), C.c_void_p]),
     "fp_params_default": (None, [C.POINTER(FpParams)]),
+    "efp_params_default": (None, [C.POINTER(EfpParams)]),
+    "extended_fp": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(EfpParams),
+                              C.POINTER(EfpResult), C.c_void_p]),
     "local_search_mtm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(LsParams),
                                    C.POINTER(LsResult), C.c_void_p]),
     "pdhg_params_default": (None, [C.POINTER(PdhgParams)]),
@@ -415,10 +431,13 @@ def _fix_and_propagate(prob, x, lb, ub, seed=1, bulk_rule=0, fraction=0.01, last
 Problem.fix_and_propagate = _fix_and_propagate
 
 
-def _pdhg(prob, lb, ub, x, y, iterations=1000, restart_period=100, step=0.0, primal_weight=0.0, stream=None):
+def _pdhg(prob, lb, ub, x, y, iterations=1000, restart_period=100, step=0.0, primal_weight=0.0, objective=None,
+          stream=None):
     """pdhg_solve (the approximate LP) on device tensors: lb, ub (n), x (n) and y (m) float64; x
-    and y are the warm start and receive the final iterate.  Returns the result dict."""
-    prm = PdhgParams(int(iterations), int(restart_period), float(step), float(primal_weight))
+    and y are the warm start and receive the final iterate; objective: a float64 device tensor in
+    place of the handle's objective, or None.  Returns the result dict."""
+    prm = PdhgParams(int(iterations), int(restart_period), float(step), float(primal_weight),
+                     objective.data_ptr() if objective is not None else None)
     res = PdhgResult()
     _check(lib().pdhg_solve(prob.h, _ptr(lb), _ptr(ub), _ptr(x), _ptr(y), C.byref(prm), C.byref(res),
                             _stream(stream)))
@@ -439,6 +458,22 @@ def _local_search(prob, lb, ub, x, w, iterations=100, stream=None):
 
 
 Problem.local_search = _local_search
+
+
+def _extended_fp(prob, lb, ub, rounds=20, lp_iterations=500, ls_iterations=200, cycle_window=3, cycle_ratio=0.1,
+                 seed=1, stream=None):
+    """extended_fp (Algorithm 2, generation mode) on device bounds.  Returns (x device tensor,
+    result dict)."""
+    torch = _torch()
+    prm = EfpParams(int(rounds), int(lp_iterations), int(ls_iterations), int(cycle_window), float(cycle_ratio),
+                    int(seed))
+    res = EfpResult()
+    x = torch.empty_like(lb)
+    _check(lib().extended_fp(prob.h, _ptr(lb), _ptr(ub), _ptr(x), C.byref(prm), C.byref(res), _stream(stream)))
+    return x, res.as_dict()
+
+
+Problem.extended_fp = _extended_fp
 
 RESULT_FIELDS = [f for f, _ in BpResult._fields_ if f != "reserved"]
 

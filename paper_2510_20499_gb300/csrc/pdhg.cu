@@ -289,6 +289,7 @@ extern "C" void pdhg_params_default(pdhg_params* p) {
     p->restart_period = 100;
     p->step = 0.0;
     p->primal_weight = 0.0;
+    p->objective = nullptr;
 }
 
 extern "C" int pdhg_solve(mip_problem* p, const double* lb, const double* ub, double* x, double* y,
@@ -306,6 +307,7 @@ extern "C" int pdhg_solve(mip_problem* p, const double* lb, const double* ub, do
     }
     cudaStream_t s = (cudaStream_t)stream;
     const int n = p->n, m = p->m, np_ = p->dp.npieces;
+    const double* cobj = prm.objective ? prm.objective : p->obj;
     memset(result, 0, sizeof(*result));
     std::vector<void*> tmp;
     auto alloc = [&](double** ptr, size_t count) -> int {
@@ -354,7 +356,7 @@ extern "C" int pdhg_solve(mip_problem* p, const double* lb, const double* ub, do
     // step and primal weight
     double eta = prm.step, omega = prm.primal_weight;
     if (eta == 0.0 || omega == 0.0) {
-        k_pdhg_norms<<<kPdRedBlocks, kPdThreads, 0, s>>>(p->dp, p->obj, red);
+        k_pdhg_norms<<<kPdRedBlocks, kPdThreads, 0, s>>>(p->dp, cobj, red);
         k_pdhg_finish<<<1, kPdThreads, 0, s>>>(red, kPdRedBlocks, 1, sums);
         PD_CUDA(cudaGetLastError());
         PD_CUDA(cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, s));
@@ -365,7 +367,7 @@ extern "C" int pdhg_solve(mip_problem* p, const double* lb, const double* ub, do
             omega = (nc > 0.0 && ng > 0.0) ? nc / ng : 1.0;
         }
     }
-    PdhgVecs V{p->obj, lb, ub, eta / omega, eta * omega};
+    PdhgVecs V{cobj, lb, ub, eta / omega, eta * omega};
     // grids of resident blocks (every block stays resident through its grid-stride loop)
     static int occ[3] = {-1, -1, -1};
     if (occ[0] < 0) {
@@ -395,7 +397,7 @@ extern "C" int pdhg_solve(mip_problem* p, const double* lb, const double* ub, do
     k_pdhg_rows<<<grid, kPdThreads, 0, s>>>(p->dp, V, x, y, yn, nullptr, part, 1);
     if (np_) k_pdhg_long<<<grid_l, kPdThreads, 0, s>>>(p->dp, V, part, y, yn, nullptr, 1);
     k_pdhg_cols<<<grid_c, kPdThreads, 0, s>>>(p->dp, V, x, y, xn, xe, nullptr, 1);
-    k_pdhg_kkt<<<kPdRedBlocks, kPdThreads, 0, s>>>(p->dp, p->obj, lb, ub, x, y, yn, xn, red);
+    k_pdhg_kkt<<<kPdRedBlocks, kPdThreads, 0, s>>>(p->dp, cobj, lb, ub, x, y, yn, xn, red);
     k_pdhg_finish<<<1, kPdThreads, 0, s>>>(red, kPdRedBlocks, 0, sums);
     PD_CUDA(cudaGetLastError());
     PD_CUDA(cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, s));
