@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the probing, batch, learned and scorer measurements")
-    ap.add_argument("--extras", default="probing,batch,fp,learned,scorer,pdhg,local_mip",
+    ap.add_argument("--extras", default="probing,batch,fp,learned,scorer,pdhg,local_mip,efp",
                     help="comma-separated subset of the extra measurements to run (learned_full, the "
                          "160/40-instance learned-order experiment at 1M nonzeros, is not in the default set)")
     return ap.parse_args()
@@ -675,6 +675,34 @@ def local_mip_extra(pkg, torch, dev):
             "after_1100": {k: r[k] for k in ("moves", "bumps", "violated", "weighted_violation")}}
 
 
+def efp_extra(pkg, torch, dev):
+    """The extended feasibility pump (extended_fp, generation mode) on the knapsack/cover instance
+    (50k x 100k, 1M nonzeros, objective N(0, 1)): where the feasible point was found, rounds,
+    cycle breaks, wall time of the call (CUDA events), and the point checked row by row."""
+    import numpy as np
+    import scipy.sparse as sp
+    from paper_2510_20499_gb300 import synth
+    p = synth.knapsack_cover()
+    p.c = np.random.default_rng(7).normal(0, 1, p.n)
+    prob = pkg.Problem(p)
+    lb, ub = torch.tensor(p.lb, device=dev), torch.tensor(p.ub, device=dev)
+    kw = dict(rounds=10, lp_iterations=300, ls_iterations=200, seed=1)
+    prob.extended_fp(lb, ub, **kw)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    x, r = prob.extended_fp(lb, ub, **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    xh = x.cpu().numpy()
+    A = sp.csr_matrix((p.val, p.col, p.row_ptr), shape=(p.m, p.n))
+    fin = np.isfinite(p.g)
+    ok = bool(((A @ xh)[fin] <= p.g[fin] + 1e-9).all()) and bool(((xh >= p.lb) & (xh <= p.ub)).all())
+    return {"workload": f"knapsack/cover {p.m} x {p.n}, {p.nnz} nnz, c ~ N(0, 1); " + ", ".join(f"{k}={v}" for k, v in kw.items()),
+            "seconds": e0.elapsed_time(e1) / 1e3, "result": r, "point_satisfies_every_row": ok,
+            "objective": float(p.c @ xh)}
+
+
 def scorer_extra(pkg, torch, dev, tflops_peak):
     """The scorer's forward and training-step throughput on 1M rows of BF16 features (the
     tcgen05 MLP kernel k_mlp), against the measured BF16 tensor peak."""
@@ -828,7 +856,7 @@ def main():
     if rank == 0 and not args.no_extras:
         todo = [e for e in args.extras.split(",") if e]
         bad = [e for e in todo
-               if e not in ("probing", "batch", "fp", "learned", "learned_full", "scorer", "pdhg", "local_mip")]
+               if e not in ("probing", "batch", "fp", "learned", "learned_full", "scorer", "pdhg", "local_mip", "efp")]
         if bad:
             raise SystemExit(f"unknown extras: {bad}")
         fns = {"probing": lambda: probing_extra(pkg, torch, dev), "batch": lambda: batch_extra(pkg, torch, dev),
@@ -836,6 +864,7 @@ def main():
                "learned": lambda: learned_extra(pkg, torch, dev),
                "learned_full": lambda: learned_full_extra(pkg, torch, dev),
                "pdhg": lambda: pdhg_extra(pkg, torch, dev), "local_mip": lambda: local_mip_extra(pkg, torch, dev),
+               "efp": lambda: efp_extra(pkg, torch, dev),
                "scorer": lambda: scorer_extra(pkg, torch, dev, tensor_peak())}
         out["extras"] = {e: fns[e]() for e in todo}
     if rank == 0 and not args.no_cpu_baseline:

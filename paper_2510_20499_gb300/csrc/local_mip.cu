@@ -102,14 +102,29 @@ __global__ void __launch_bounds__(kLsThreads) k_ls_score(DevProblem P, const dou
             if (t == xj) continue;
             const double dx = __dsub_rn(t, xj);
             double s = 0.0;
-            for (int c = P.col_ptr[j]; c < P.col_ptr[j + 1]; ++c) {
-                const int r = P.row_idx[c];
-                const double gr = P.grow[r].x;
-                if (!isfinite(gr)) continue;
-                const double o = __dsub_rn(L[r], gr);
-                const double nw = __dsub_rn(__dadd_rn(L[r], __dmul_rn(P.col_val[c], dx)), gr);
-                const double ov = o > 0.0 ? o : 0.0, nv = nw > 0.0 ? nw : 0.0;
-                s = __dadd_rn(s, __dmul_rn(w[r], __dsub_rn(ov, nv)));
+            // the column's rows in order; the loads of four entries are issued together
+            const int cb = P.col_ptr[j], ce = P.col_ptr[j + 1];
+            for (int c0 = cb; c0 < ce; c0 += 4) {
+                int rr[4];
+                double gg[4], ll[4], ww[4], aa[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) rr[i] = c0 + i < ce ? P.row_idx[c0 + i] : -1;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int r = rr[i] >= 0 ? rr[i] : 0;
+                    gg[i] = P.grow[r].x;
+                    ll[i] = L[r];
+                    ww[i] = w[r];
+                    aa[i] = c0 + i < ce ? P.col_val[c0 + i] : 0.0;
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (rr[i] < 0 || !isfinite(gg[i])) continue;
+                    const double o = __dsub_rn(ll[i], gg[i]);
+                    const double nw = __dsub_rn(__dadd_rn(ll[i], __dmul_rn(aa[i], dx)), gg[i]);
+                    const double ov = o > 0.0 ? o : 0.0, nv = nw > 0.0 ? nw : 0.0;
+                    s = __dadd_rn(s, __dmul_rn(ww[i], __dsub_rn(ov, nv)));
+                }
             }
             const LsKey key{s, t, j, 0};
             if (ls_before(key, best)) best = key;
@@ -235,13 +250,20 @@ extern "C" int local_search_mtm(mip_problem* p, const double* lb, const double* 
     cudaStream_t s = (cudaStream_t)stream;
     memset(result, 0, sizeof(*result));
     void *pL = nullptr, *pPart = nullptr, *pCtl = nullptr, *pSum = nullptr, *pOut = nullptr;
+    // the scoring pass on every resident block (its per-block bests are reduced by k_ls_apply)
+    static int occ_score = -1;
+    if (occ_score < 0) {
+        cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_score, k_ls_score, kLsThreads, 0);
+        if (oe != cudaSuccess) return fail_cuda(oe, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    }
+    const int grid_score = p->sms * (occ_score > 0 ? occ_score : 1);
     auto release = [&]() {
         for (void* q : {pL, pPart, pCtl, pSum, pOut})
             if (q) cudaFreeAsync(q, s);
     };
     cudaError_t e = cudaSuccess;
     if ((e = cudaMallocAsync(&pL, sizeof(double) * (size_t)(p->m ? p->m : 1), s)) != cudaSuccess ||
-        (e = cudaMallocAsync(&pPart, sizeof(LsKey) * kLsRedBlocks, s)) != cudaSuccess ||
+        (e = cudaMallocAsync(&pPart, sizeof(LsKey) * (size_t)grid_score, s)) != cudaSuccess ||
         (e = cudaMallocAsync(&pCtl, sizeof(LsCtl), s)) != cudaSuccess ||
         (e = cudaMallocAsync(&pSum, sizeof(double) * 3 * kLsRedBlocks, s)) != cudaSuccess ||
         (e = cudaMallocAsync(&pOut, sizeof(double) * 3, s)) != cudaSuccess) {
@@ -258,8 +280,8 @@ extern "C" int local_search_mtm(mip_problem* p, const double* lb, const double* 
     }
     k_ls_activities<<<grid_rows, kLsThreads, 0, s>>>(p->dp, x, L);
     for (int it = 0; it < params->iterations; ++it) {
-        k_ls_score<<<kLsRedBlocks, kLsThreads, 0, s>>>(p->dp, lb, ub, x, w, L, part, ctl);
-        k_ls_apply<<<1, kLsThreads, 0, s>>>(p->dp, x, L, part, kLsRedBlocks, ctl);
+        k_ls_score<<<grid_score, kLsThreads, 0, s>>>(p->dp, lb, ub, x, w, L, part, ctl);
+        k_ls_apply<<<1, kLsThreads, 0, s>>>(p->dp, x, L, part, grid_score, ctl);
         k_ls_bump<<<grid_rows, kLsThreads, 0, s>>>(p->dp, L, w, ctl);
     }
     k_ls_summary<<<kLsRedBlocks, kLsThreads, 0, s>>>(p->dp, p->obj, x, w, L, static_cast<double*>(pSum));
