@@ -29,7 +29,8 @@ def lib():
 
 def test_header_parses():
     names = declared()
-    for must in ("mip_load_csr", "bp_propagate", "bp_probe_batch", "bp_probe_priority", "probe_split"):
+    for must in ("mip_load_csr", "bp_propagate", "bp_probe_batch", "bp_probe_priority", "probe_split",
+                 "probe_cache_apply", "pdhg_solve", "local_search_mtm", "extended_fp", "fix_and_propagate"):
         assert must in names
 
 
