@@ -21,8 +21,8 @@ here is the mixed-tight-move core, for A x <= g (rows with g = +inf are free), l
   step         score > 0: x_j = t and L_r += a_rj (t - x_j) for the rows of column j (ascending);
                otherwise every violated row's weight grows by 1.
 
-Lift and breakthrough moves (objective improvement) are not part of this core.  Plain Python
-loops over the rows and columns, IEEE double.
+Lift and breakthrough moves (objective improvement) extend this core in `search_objective`
+(reading at its section below).  Plain Python loops over the rows and columns, IEEE double.
 """
 from __future__ import annotations
 
@@ -134,3 +134,175 @@ def search(p, lb, ub, x0, w0, iterations):
     return x, w, {"iterations": int(iterations), "moves": moves, "bumps": bumps,
                   "violated": int((v > 0).sum()), "weighted_violation": float(w @ v),
                   "objective": float(np.asarray(p.c, dtype=np.float64) @ x)}
+
+
+# ---------------------------------------------------------------------------------------------
+# Objective moves (Section 2.4: Local-MIP's lift and breakthrough moves, a weighted objective).
+#
+# The reading taken for the moves the paper names but does not define, for min c^T x:
+#
+#   incumbent     at the start of an iteration, a point with no violated row whose objective is
+#                 below the incumbent's (or the first such point) becomes the incumbent x*; the
+#                 search keeps D = c^T x - c^T x* incrementally (D = 0 when x* is recorded, then
+#                 D += c_j (t - x_j) with every move), so no absolute objective sum is needed;
+#   objective row once an incumbent exists, the row  c^T x <= c^T x* - delta  joins the weighted
+#                 violation with its own weight w0: its violation is v0 = max(0, D + delta);
+#                 delta = 1 when every variable with a nonzero cost is integer with an integral
+#                 cost (a better point is then at least 1 lower), 1e-4 otherwise;
+#   lift          at a point with no violated row: for every variable with c_j != 0, the move
+#                 in the direction sigma = -sign(c_j) as far as every row stays satisfied:
+#                     step_r = (g_r - L_r) / |a_rj|   (continuous),  floor of it  (integer)
+#                 over the rows of column j with a_rj * sigma > 0 and finite g_r, then
+#                 t = x_j + sigma * min_r step_r (no such row: the bound in direction sigma),
+#                 clamped to [l_j, u_j]; no move when t = x_j or t is infinite.  The largest
+#                 gain -c_j (t - x_j) is applied when positive (ties: smallest variable), and
+#                 ends the iteration;
+#   breakthrough  while the objective row is violated: for every variable with c_j != 0
+#                 (ascending), the value that alone satisfies the objective row, formed as the
+#                 mixed tight move of a row with coefficients c and violation v0;
+#   score         every mixed tight and breakthrough candidate: the column's weighted-violation
+#                 drop (rows ascending), then plus w0 (v0 - max(0, (D + c_j dx) + delta)) when an
+#                 incumbent exists; the largest score wins, ties: smallest variable, smallest
+#                 value, then a mixed tight move before a breakthrough move;
+#   step          a positive best score moves the variable; otherwise every violated row's
+#                 weight grows by 1, or, with no violated row, w0 grows by 1.
+# With c = 0 no objective move exists and the search is the mixed-tight-move core above.
+# ---------------------------------------------------------------------------------------------
+
+
+def objective_delta(p):
+    """delta of the objective row: 1 for an integral objective on integer variables, else 1e-4."""
+    c = np.asarray(p.c, dtype=np.float64)
+    nz = c != 0.0
+    if nz.any() and np.all(np.asarray(p.is_int)[nz] != 0) and np.all(c[nz] == np.floor(c[nz])):
+        return 1.0
+    return 1e-4
+
+
+def _floor_div(e, c):
+    """floor(e / c) for e >= 0, c > 0, exact when both are integers."""
+    d = math.floor(e / c)
+    if e == math.floor(e) and c == math.floor(c):
+        while (d + 1) * c <= e:
+            d += 1
+        while d > 0 and d * c > e:
+            d -= 1
+    return float(d)
+
+
+def lift_target(cols, g, L, x, lb, ub, is_int, cj, j):
+    """The lift move's value for variable j at a point with no violated row, or None."""
+    if cj == 0.0:
+        return None
+    sigma = -1.0 if cj > 0 else 1.0
+    step = math.inf
+    for r, a in cols[j]:
+        if not np.isfinite(g[r]) or not a * sigma > 0:
+            continue
+        slack = g[r] - L[r]
+        s = _floor_div(slack, abs(a)) if is_int[j] else slack / abs(a)
+        step = min(step, s)
+    if math.isinf(step):
+        t = ub[j] if sigma > 0 else lb[j]
+    else:
+        t = x[j] + step if sigma > 0 else x[j] - step
+        t = min(max(t, lb[j]), ub[j])
+    if not math.isfinite(t) or t == x[j]:
+        return None
+    return t
+
+
+def tight_value(xj, a, v, integer):
+    """The value that alone removes violation v > 0 of a row with coefficient a on x_j."""
+    if integer:
+        d = _ceil_div(v, abs(a))
+        return xj - d if a > 0 else xj + d
+    return xj - v / a
+
+
+def search_objective(p, lb, ub, x0, w0, iterations, obj_weight=1.0):
+    """Local search with the objective moves, from (x0, w0, obj_weight).  Returns
+    (x, w, x_best or None, result dict)."""
+    cols = _csc(p)
+    c = np.asarray(p.c, dtype=np.float64)
+    g = p.g
+    x = np.array(x0, dtype=np.float64)
+    w = np.array(w0, dtype=np.float64)
+    lb = np.asarray(lb, dtype=np.float64)
+    ub = np.asarray(ub, dtype=np.float64)
+    delta = objective_delta(p)
+    L = activities(p, x)
+    w_obj = float(obj_weight)
+    D = 0.0
+    best = None
+    moves = bumps = lifts = breaks = improvements = 0
+
+    def apply(j, t):
+        nonlocal D
+        dx = t - x[j]
+        for r, a in cols[j]:
+            L[r] = L[r] + a * dx
+        D = D + c[j] * dx
+        x[j] = t
+
+    for _ in range(int(iterations)):
+        nviol = int((violation(L, g) > 0.0).sum())
+        if nviol == 0:
+            if best is None or D < 0.0:
+                best = x.copy()
+                D = 0.0
+                improvements += 1
+            pick = None
+            for j in range(p.n):
+                t = lift_target(cols, g, L, x, lb, ub, p.is_int, c[j], j)
+                if t is None:
+                    continue
+                gain = -(c[j] * (t - x[j]))
+                key = (-gain, j)
+                if pick is None or key < pick[0]:
+                    pick = (key, j, t, gain)
+            if pick is not None and pick[3] > 0.0:
+                apply(pick[1], pick[2])
+                moves += 1
+                lifts += 1
+                continue
+        cands = [(j, t, 0) for _, j, t in candidates(p, x, L, lb, ub)]
+        has_best = best is not None
+        v0 = D + delta
+        if has_best and v0 > 0.0:
+            for j in range(p.n):
+                if c[j] == 0.0:
+                    continue
+                t = min(max(tight_value(x[j], c[j], v0, p.is_int[j]), lb[j]), ub[j])
+                if t != x[j]:
+                    cands.append((j, t, 1))
+        pick = None
+        for j, t, kind in cands:
+            sc = score(cols, g, w, x, L, j, t)
+            if has_best:
+                dx = t - x[j]
+                ov0 = max(0.0, D + delta)
+                nv0 = max(0.0, (D + c[j] * dx) + delta)
+                sc = sc + w_obj * (ov0 - nv0)
+            key = (-sc, j, t, kind)
+            if pick is None or key < pick[0]:
+                pick = (key, j, t, sc, kind)
+        if pick is not None and pick[3] > 0.0:
+            apply(pick[1], pick[2])
+            moves += 1
+            breaks += pick[4]
+        else:
+            viol = violation(L, g) > 0.0
+            if viol.any():
+                w[viol] += 1.0
+                bumps += 1
+            elif has_best:
+                w_obj += 1.0
+                bumps += 1
+    v = violation(L, g)
+    res = {"iterations": int(iterations), "moves": moves, "bumps": bumps, "lifts": lifts,
+           "breakthroughs": breaks, "improvements": improvements, "found": best is not None,
+           "violated": int((v > 0).sum()), "weighted_violation": float(w @ v),
+           "objective": float(c @ x), "best_objective": float(c @ best) if best is not None else math.inf,
+           "obj_weight": w_obj, "delta": delta}
+    return x, w, best, res

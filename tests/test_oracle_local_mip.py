@@ -1,5 +1,6 @@
-"""The local search oracle (oracle/local_mip.py: mixed tight moves, Section 2.4) against
-hand-worked steps and from-scratch recomputation on random integer problems."""
+"""The local search oracle (oracle/local_mip.py: mixed tight moves and the objective moves,
+Section 2.4) against hand-worked steps, from-scratch recomputation and brute force on random
+integer problems."""
 import numpy as np
 import pytest
 
@@ -85,3 +86,136 @@ def test_reaches_feasibility_on_planted_problems():
             assert (lm.activities(p, x)[np.isfinite(p.g)] <= p.g[np.isfinite(p.g)]).all()
             found += 1
     assert found >= 5
+
+
+# --- objective moves (Section 2.4: lift and breakthrough moves, the weighted objective) ---
+
+
+@pytest.mark.parametrize("case", range(2))
+def test_objective_hand_worked_steps(case):
+    c = load_golden("local_mip_objective.json")["cases"][case]
+    p = _case(c)
+    for k, st in enumerate(c["steps"]):
+        x, w, best, r = lm.search_objective(p, p.lb, p.ub, c["x0"], c["w0"], k + 1, obj_weight=c["obj_weight"])
+        np.testing.assert_array_equal(x, st["x"])
+        np.testing.assert_array_equal(w, st["w"])
+        np.testing.assert_array_equal(best, st["best"])
+        assert r["obj_weight"] == st["w0"]
+    for key in ("moves", "bumps", "lifts", "breakthroughs", "improvements", "best_objective"):
+        assert r[key] == c[key], key
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_zero_cost_is_the_mixed_tight_move_core(seed):
+    """With c = 0 no lift or breakthrough move exists and the objective row never scores: the
+    search is the mixed-tight-move core, step for step."""
+    p = _problem(700 + seed)
+    p.c = np.zeros(p.n)
+    x0 = np.clip(np.round(np.random.default_rng(seed).normal(0, 3, p.n)), p.lb, p.ub)
+    for it in (10, 40):
+        ax, aw, ar = lm.search(p, p.lb, p.ub, x0, np.ones(p.m), it)
+        bx, bw, best, br = lm.search_objective(p, p.lb, p.ub, x0, np.ones(p.m), it)
+        np.testing.assert_array_equal(ax, bx)
+        np.testing.assert_array_equal(aw, bw)
+        assert br["lifts"] == 0 and br["breakthroughs"] == 0
+        assert ar["moves"] == br["moves"]
+        # a bump at a feasible point raises w0 instead of a row weight
+        assert ar["bumps"] + (br["obj_weight"] - 1.0) == br["bumps"]
+
+
+def _feasible_start(p, rng):
+    """The generator's planted point satisfies every row."""
+    x = np.asarray(p.x0, dtype=np.float64)
+    assert (lm.violation(lm.activities(p, x), p.g) == 0).all()
+    return x
+
+
+def _exact_feasible(p, x):
+    A = np.zeros((p.m, p.n))
+    for k in range(p.m):
+        for q in range(int(p.row_ptr[k]), int(p.row_ptr[k + 1])):
+            A[k, int(p.col[q])] = p.val[q]
+    return bool(np.all(A @ x <= p.g)), A
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_lift_target_is_the_farthest_feasible_value(seed):
+    """On integer data, the lift value of every variable is, by brute force over its integer
+    values, the farthest one against the sign of its cost that keeps every row satisfied (all
+    values in between stay feasible too, so the range is an interval)."""
+    p = _problem(800 + seed, m=25, n=20)
+    rng = np.random.default_rng(seed)
+    p.c = rng.integers(-3, 4, p.n).astype(float)
+    x = _feasible_start(p, rng)
+    L = lm.activities(p, x)
+    cols = lm._csc(p)
+    for j in range(p.n):
+        t = lm.lift_target(cols, p.g, L, x, p.lb, p.ub, p.is_int, p.c[j], j)
+        if p.c[j] == 0:
+            assert t is None
+            continue
+        sigma = -1 if p.c[j] > 0 else 1
+        far = x[j]
+        v = x[j] + sigma
+        while p.lb[j] <= v <= p.ub[j]:
+            x2 = x.copy()
+            x2[j] = v
+            if not _exact_feasible(p, x2)[0]:
+                break
+            far = v
+            v += sigma
+        assert (t is None and far == x[j]) or t == far, (j, t, far)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_breakthrough_value_is_the_nearest_satisfying_integer(seed):
+    """The objective row's tight move of an integer variable is, by brute force, the nearest
+    integer value (clamped) at which D + c_j dx + delta <= 0."""
+    rng = np.random.default_rng(seed)
+    for _ in range(200):
+        cj = float(rng.integers(1, 9)) * (1 if rng.random() < 0.5 else -1)
+        xj = float(rng.integers(-5, 6))
+        v0 = float(rng.integers(1, 30))
+        t = lm.tight_value(xj, cj, v0, True)
+        sgn = -1 if cj > 0 else 1
+        d = 0
+        while cj * (sgn * d) + v0 > 0:
+            d += 1
+        assert t == xj + sgn * d
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_incumbents_are_feasible_and_improve(seed):
+    """Every incumbent satisfies every row exactly (integer data), its objective is the result's
+    best objective, and over longer runs the incumbent's objective never rises."""
+    p = _problem(900 + seed, m=30, n=25)
+    rng = np.random.default_rng(seed)
+    p.c = rng.integers(-4, 5, p.n).astype(float)
+    x0 = np.clip(np.round(rng.normal(0, 3, p.n)), p.lb, p.ub)
+    prev = np.inf
+    found_any = False
+    for it in (5, 20, 60, 150):
+        x, w, best, r = lm.search_objective(p, p.lb, p.ub, x0, np.ones(p.m), it)
+        if best is None:
+            assert not r["found"]
+            continue
+        found_any = True
+        assert _exact_feasible(p, best)[0]
+        assert r["best_objective"] == float(p.c @ best)
+        assert r["best_objective"] <= prev
+        prev = r["best_objective"]
+        assert r["moves"] + r["bumps"] == it
+    assert found_any
+
+
+def test_delta_reading():
+    p = milp_from_dense([[1, 1]], [3], [0, 0], [4, 4], [1, 1])
+    p.c = np.array([2.0, -1.0])
+    assert lm.objective_delta(p) == 1.0
+    p.c = np.array([2.5, -1.0])
+    assert lm.objective_delta(p) == 1e-4
+    p2 = milp_from_dense([[1, 1]], [3], [0, 0], [4, 4], [1, 0])
+    p2.c = np.array([1.0, 1.0])
+    assert lm.objective_delta(p2) == 1e-4
+    p2.c = np.array([1.0, 0.0])
+    assert lm.objective_delta(p2) == 1.0
