@@ -511,7 +511,7 @@ int pdhg_solve(mip_problem *p, const double *lb, const double *ub, double *x, do
  * scores every such move by the drop of F over the variable's column (rows ascending), all
  * scores recomputed each iteration.  The best move (largest score; ties: smallest variable,
  * then smallest value) is applied when its score is positive; otherwise every violated row's
- * weight grows by 1.  Lift and breakthrough moves (objective improvement) are not included.
+ * weight grows by 1.  Lift and breakthrough moves (objective improvement): local_search_objective.
  * Deterministic: the same inputs give the same moves bit for bit.
  *
  * lb, ub:  DEVICE double[n] bounds (not modified).
@@ -540,6 +540,64 @@ typedef struct {
 
 int local_search_mtm(mip_problem *p, const double *lb, const double *ub, double *x, double *w,
                      const ls_params *params, ls_result *result, void *stream);
+
+/*
+ * local_search_objective -- the local search with its objective moves (Section 2.4: Local-MIP's
+ * lift and breakthrough moves, the weighted objective), for min c^T x with c the handle's
+ * objective.  It extends local_search_mtm's iteration:
+ *   - at the start of an iteration, a point with no violated row becomes the incumbent x* when
+ *     it is the first such point or its objective is lower; the search keeps D = c x - c x*
+ *     through every move (D restarts at 0 with each incumbent);
+ *   - lift: at a point with no violated row, every variable with c_j != 0 may move against the
+ *     sign of c_j as far as every row of its column stays satisfied (steps (g_r - L_r) / |a|,
+ *     floored for integer variables; no limiting row: to the bound), clamped to its bounds; the
+ *     largest gain -c_j dx > 0 (ties: smallest variable) is applied and ends the iteration;
+ *   - once an incumbent exists, the objective row c x <= c x* - delta joins the weighted
+ *     violation with weight w0: every candidate's score adds
+ *     w0 (max(0, D + delta) - max(0, D + c_j dx + delta)) to the column's drop, and while the
+ *     row is violated its tight values (breakthrough moves) are candidates too; ties between a
+ *     mixed tight and a breakthrough move of the same variable and value go to the former;
+ *   - with no positive move, the violated rows' weights grow by 1, or, with no violated row,
+ *     w0 grows by 1.
+ * delta = 1 when every variable with a nonzero cost is integer with an integral cost, else 1e-4.
+ * With c = 0 the iterations are local_search_mtm's.  Deterministic: the same inputs give the
+ * same moves bit for bit.
+ *
+ * lb, ub:  DEVICE double[n] bounds (not modified).
+ * x:       DEVICE double[n], the start point on entry, the final point on return.
+ * w:       DEVICE double[m], the row weights, updated in place.
+ * x_best:  DEVICE double[n], written with each incumbent (untouched when none is found).
+ * params:  iterations >= 0; obj_weight = w0 at the start (finite, >= 0).
+ * result:  HOST pointer, valid at return (the call synchronises the stream): local_search_mtm's
+ *          fields, then lift moves, breakthrough moves (applied), incumbents recorded, found (an
+ *          incumbent exists), c^T x_best (+inf when none), w0 at the end, and delta.
+ * Scratch: m doubles and a few KB, stream-ordered, freed at return.
+ * Returns BP_OK, BP_ERR_INVALID, BP_ERR_OOM or BP_ERR_CUDA.
+ */
+typedef struct {
+    int32_t iterations;
+    int32_t reserved;
+    double obj_weight;
+} ls_obj_params;
+
+typedef struct {
+    int32_t iterations;
+    int32_t moves;
+    int32_t bumps;
+    int32_t violated;
+    double weighted_violation;
+    double objective;
+    int32_t lifts;
+    int32_t breakthroughs;
+    int32_t improvements;
+    int32_t found;
+    double best_objective;
+    double obj_weight;
+    double delta;
+} ls_obj_result;
+
+int local_search_objective(mip_problem *p, const double *lb, const double *ub, double *x, double *w,
+                           double *x_best, const ls_obj_params *params, ls_obj_result *result, void *stream);
 
 /*
  * extended_fp -- the extended feasibility pump's orchestration (Section 2.5, Algorithm 2), in

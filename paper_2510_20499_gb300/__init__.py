@@ -96,6 +96,22 @@ class LsResult(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class LsObjParams(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("reserved", C.c_int32), ("obj_weight", C.c_double)]
+
+
+class LsObjResult(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("moves", C.c_int32), ("bumps", C.c_int32), ("violated", C.c_int32),
+                ("weighted_violation", C.c_double), ("objective", C.c_double), ("lifts", C.c_int32),
+                ("breakthroughs", C.c_int32), ("improvements", C.c_int32), ("found", C.c_int32),
+                ("best_objective", C.c_double), ("obj_weight", C.c_double), ("delta", C.c_double)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["found"] = bool(d["found"])
+        return d
+
+
 class EfpParams(C.Structure):
     _fields_ = [("rounds", C.c_int32), ("lp_iterations", C.c_int32), ("ls_iterations", C.c_int32),
                 ("cycle_window", C.c_int32), ("cycle_ratio", C.c_double), ("seed", C.c_uint64)]
@@ -186,6 +202,8 @@ SIGNATURES = {
                               C.POINTER(EfpResult), C.c_void_p]),
     "local_search_mtm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(LsParams),
                                    C.POINTER(LsResult), C.c_void_p]),
+    "local_search_objective": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.POINTER(LsObjParams), C.POINTER(LsObjResult), C.c_void_p]),
     "pdhg_params_default": (None, [C.POINTER(PdhgParams)]),
     "pdhg_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(PdhgParams),
                              C.POINTER(PdhgResult), C.c_void_p]),
@@ -458,6 +476,19 @@ def _local_search(prob, lb, ub, x, w, iterations=100, stream=None):
 
 
 Problem.local_search = _local_search
+
+
+def _local_search_objective(prob, lb, ub, x, w, x_best, iterations=100, obj_weight=1.0, stream=None):
+    """local_search_objective on device tensors: lb, ub, x and x_best (n), w (m) float64; x and
+    w are updated in place, x_best receives each incumbent.  Returns the result dict."""
+    prm = LsObjParams(int(iterations), 0, float(obj_weight))
+    res = LsObjResult()
+    _check(lib().local_search_objective(prob.h, _ptr(lb), _ptr(ub), _ptr(x), _ptr(w), _ptr(x_best), C.byref(prm),
+                                        C.byref(res), _stream(stream)))
+    return res.as_dict()
+
+
+Problem.local_search_objective = _local_search_objective
 
 
 def _extended_fp(prob, lb, ub, rounds=20, lp_iterations=500, ls_iterations=200, cycle_window=3, cycle_ratio=0.1,

@@ -1,17 +1,27 @@
 // The local search's move scoring (Section 2.4, the paper's GPU Local-MIP): the mixed-tight-move
-// core under a weighted violation F = sum_k w_k max(0, (A x)_k - g_k).
+// core under a weighted violation F = sum_k w_k max(0, (A x)_k - g_k), and its objective moves
+// (Local-MIP's lift and breakthrough moves under a weighted objective row).
 //
 // Per iteration, every candidate and its full score are recomputed (as the paper does, instead
 // of the score deltas of the original Feasibility Jump):
 //   k_ls_score   a warp per violated row: each lane takes nonzeros of the row, forms the value
 //                that alone satisfies the row (integers by the smallest integer step, clamped to
 //                the bounds) and scores it by walking the variable's column (rows ascending);
-//                warp and block reductions keep the best (largest score; ties: smallest variable,
-//                then smallest value), one per block;
+//                with the objective moves, a thread per variable with a cost also forms the
+//                objective row's tight value (breakthrough) while that row is violated, and every
+//                score adds the objective row's weighted drop; warp and block reductions keep the
+//                best (largest score; ties: smallest variable, smallest value, then a mixed tight
+//                move before a breakthrough move), one per block;
 //   k_ls_apply   one block: the best over the blocks (a total order, so the result does not
 //                depend on the reduction's order); a positive score moves the variable and
 //                updates the activities of its column, otherwise the weights are to grow;
 //   k_ls_bump    every violated row's weight grows by 1 when no move improved.
+// With the objective moves, each iteration starts with
+//   k_lso_lift        at a point with no violated row: the point is copied out when it becomes
+//                     the incumbent, and a thread per variable with a cost forms its lift move
+//                     (as far against the cost's sign as every row of its column allows);
+//   k_lso_lift_apply  one block: records the incumbent (D = c x - c x* restarts at 0) and applies
+//                     the best lift move when its gain is positive, which ends the iteration.
 // Everything stays on the device (no host read per iteration).  The activities start from a
 // thread-per-row sum in row order and are updated in the order of the moves, so the search is
 // bit-for-bit that of a sequential implementation with the same operation order.
@@ -29,16 +39,17 @@ struct LsKey {
     double score;
     double t;
     int j;
-    int pad;
+    int kind;   // 0: a mixed tight move, 1: a breakthrough move (the objective row's tight move)
 };
 
-__device__ __forceinline__ LsKey ls_none() { return LsKey{-INFINITY, INFINITY, INT_MAX, 0}; }
+__device__ __forceinline__ LsKey ls_none() { return LsKey{-INFINITY, INFINITY, INT_MAX, 2}; }
 
-// a before b: larger score; ties: smaller variable, then smaller value
+// a before b: larger score; ties: smaller variable, smaller value, then the smaller kind
 __device__ __forceinline__ bool ls_before(const LsKey& a, const LsKey& b) {
     if (a.score != b.score) return a.score > b.score;
     if (a.j != b.j) return a.j < b.j;
-    return a.t < b.t;
+    if (a.t != b.t) return a.t < b.t;
+    return a.kind < b.kind;
 }
 
 __device__ __forceinline__ LsKey ls_shfl(const LsKey& k, int lane) {
@@ -46,7 +57,7 @@ __device__ __forceinline__ LsKey ls_shfl(const LsKey& k, int lane) {
     o.score = __shfl_sync(0xffffffffu, k.score, lane);
     o.t = __shfl_sync(0xffffffffu, k.t, lane);
     o.j = __shfl_sync(0xffffffffu, k.j, lane);
-    o.pad = 0;
+    o.kind = __shfl_sync(0xffffffffu, k.kind, lane);
     return o;
 }
 
@@ -54,13 +65,30 @@ struct LsCtl {
     int nviol;        // violated rows seen by this iteration's scoring pass
     int bump;         // the weights grow in this iteration
     int moves, bumps;
+    // objective moves
+    int nv;           // violated rows of the current point (kept through every move)
+    int has_best;     // an incumbent exists
+    int done;         // a lift move ended this iteration
+    int lifts, breakthroughs, improvements;
+    int cost_any, cost_frac;   // some cost is nonzero / some nonzero cost is not integral on an integer
+    double D;         // c x - c x* since the incumbent was recorded
+    double w0;        // the objective row's weight
+    double delta;     // the objective row's step
 };
 
-__global__ void k_ls_activities(DevProblem P, const double* __restrict__ x, double* __restrict__ L) {
+// L = A x in row order; with nv, the violated rows are counted too
+__global__ void k_ls_activities(DevProblem P, const double* __restrict__ x, double* __restrict__ L, int* nv) {
+    int cnt = 0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < P.m; k += gridDim.x * blockDim.x) {
         double s = 0.0;
         for (int q = P.row_ptr[k]; q < P.row_ptr[k + 1]; ++q) s = __dadd_rn(s, __dmul_rn(P.val[q], x[P.col[q]]));
         L[k] = s;
+        const double g = P.grow[k].x;
+        if (isfinite(g) && __dsub_rn(s, g) > 0.0) ++cnt;
+    }
+    if (nv) {
+        cnt = __reduce_add_sync(0xffffffffu, cnt);
+        if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(nv, cnt);
     }
 }
 
@@ -74,11 +102,80 @@ __device__ __forceinline__ double ls_ceil_div(double e, double c) {
     return d;
 }
 
+// floor(e / c) for e >= 0, c > 0, corrected to the exact quotient's floor for integers
+__device__ __forceinline__ double ls_floor_div(double e, double c) {
+    double d = floor(__ddiv_rn(e, c));
+    if (e == floor(e) && c == floor(c)) {
+        for (int it = 0; it < 4 && __dmul_rn(d + 1.0, c) <= e; ++it) d += 1.0;
+        for (int it = 0; it < 4 && d > 0.0 && __dmul_rn(d, c) > e; ++it) d -= 1.0;
+    }
+    return d;
+}
+
+// the value that alone removes violation v > 0 of a row with coefficient a on x_j
+__device__ __forceinline__ double ls_tight(double xj, double a, double v, bool integer) {
+    if (integer) {
+        const double d = ls_ceil_div(v, fabs(a));
+        return a > 0.0 ? __dsub_rn(xj, d) : __dadd_rn(xj, d);
+    }
+    return __dsub_rn(xj, __ddiv_rn(v, a));
+}
+
+// the drop of the weighted row violation if x_j alone moves by dx: the column's rows in order,
+// the loads of four entries issued together
+__device__ __forceinline__ double ls_column_score(const DevProblem& P, const double* __restrict__ w,
+                                                  const double* __restrict__ L, int j, double dx) {
+    double s = 0.0;
+    const int cb = P.col_ptr[j], ce = P.col_ptr[j + 1];
+    for (int c0 = cb; c0 < ce; c0 += 4) {
+        int rr[4];
+        double gg[4], ll[4], ww[4], aa[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) rr[i] = c0 + i < ce ? P.row_idx[c0 + i] : -1;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = rr[i] >= 0 ? rr[i] : 0;
+            gg[i] = P.grow[r].x;
+            ll[i] = L[r];
+            ww[i] = w[r];
+            aa[i] = c0 + i < ce ? P.col_val[c0 + i] : 0.0;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (rr[i] < 0 || !isfinite(gg[i])) continue;
+            const double o = __dsub_rn(ll[i], gg[i]);
+            const double nw = __dsub_rn(__dadd_rn(ll[i], __dmul_rn(aa[i], dx)), gg[i]);
+            const double ov = o > 0.0 ? o : 0.0, nv = nw > 0.0 ? nw : 0.0;
+            s = __dadd_rn(s, __dmul_rn(ww[i], __dsub_rn(ov, nv)));
+        }
+    }
+    return s;
+}
+
+// the objective row's weighted drop: w0 (max(0, D + delta) - max(0, (D + c_j dx) + delta))
+__device__ __forceinline__ double ls_objective_term(double D, double delta, double w0, double cj, double dx) {
+    const double o = __dadd_rn(D, delta);
+    const double nw = __dadd_rn(__dadd_rn(D, __dmul_rn(cj, dx)), delta);
+    const double ov = o > 0.0 ? o : 0.0, nv = nw > 0.0 ? nw : 0.0;
+    return __dmul_rn(w0, __dsub_rn(ov, nv));
+}
+
+template <bool OBJ>
 __global__ void __launch_bounds__(kLsThreads) k_ls_score(DevProblem P, const double* __restrict__ lb,
                                                          const double* __restrict__ ub, const double* __restrict__ x,
                                                          const double* __restrict__ w, const double* __restrict__ L,
-                                                         LsKey* __restrict__ part, LsCtl* ctl) {
+                                                         LsKey* __restrict__ part, LsCtl* ctl,
+                                                         const double* __restrict__ cost) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    bool with_obj = false;
+    double D = 0.0, delta = 0.0, w0 = 0.0;
+    if constexpr (OBJ) {
+        if (ctl->done) return;   // a lift move ended this iteration
+        with_obj = ctl->has_best != 0;
+        D = ctl->D;
+        delta = ctl->delta;
+        w0 = ctl->w0;
+    }
     LsKey best = ls_none();
     int nviol = 0;
     for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < P.m; k += (gridDim.x * blockDim.x) >> 5) {
@@ -90,44 +187,34 @@ __global__ void __launch_bounds__(kLsThreads) k_ls_score(DevProblem P, const dou
         for (int q = P.row_ptr[k] + lane; q < P.row_ptr[k + 1]; q += 32) {
             const int j = P.col[q];
             const double a = P.val[q], xj = x[j];
-            double t;
-            if (P.is_int[j]) {
-                const double d = ls_ceil_div(v, fabs(a));
-                t = a > 0.0 ? __dsub_rn(xj, d) : __dadd_rn(xj, d);
-            } else {
-                t = __dsub_rn(xj, __ddiv_rn(v, a));
-            }
+            double t = ls_tight(xj, a, v, P.is_int[j] != 0);
             t = t < lb[j] ? lb[j] : t;   // max(t, l), then min(., u)
             t = t > ub[j] ? ub[j] : t;
             if (t == xj) continue;
             const double dx = __dsub_rn(t, xj);
-            double s = 0.0;
-            // the column's rows in order; the loads of four entries are issued together
-            const int cb = P.col_ptr[j], ce = P.col_ptr[j + 1];
-            for (int c0 = cb; c0 < ce; c0 += 4) {
-                int rr[4];
-                double gg[4], ll[4], ww[4], aa[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) rr[i] = c0 + i < ce ? P.row_idx[c0 + i] : -1;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int r = rr[i] >= 0 ? rr[i] : 0;
-                    gg[i] = P.grow[r].x;
-                    ll[i] = L[r];
-                    ww[i] = w[r];
-                    aa[i] = c0 + i < ce ? P.col_val[c0 + i] : 0.0;
-                }
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    if (rr[i] < 0 || !isfinite(gg[i])) continue;
-                    const double o = __dsub_rn(ll[i], gg[i]);
-                    const double nw = __dsub_rn(__dadd_rn(ll[i], __dmul_rn(aa[i], dx)), gg[i]);
-                    const double ov = o > 0.0 ? o : 0.0, nv = nw > 0.0 ? nw : 0.0;
-                    s = __dadd_rn(s, __dmul_rn(ww[i], __dsub_rn(ov, nv)));
-                }
-            }
+            double s = ls_column_score(P, w, L, j, dx);
+            if (OBJ && with_obj) s = __dadd_rn(s, ls_objective_term(D, delta, w0, cost[j], dx));
             const LsKey key{s, t, j, 0};
             if (ls_before(key, best)) best = key;
+        }
+    }
+    if constexpr (OBJ) {
+        // breakthrough moves: the objective row's tight values while it is violated
+        const double v0 = __dadd_rn(D, delta);
+        if (with_obj && v0 > 0.0) {
+            for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < P.n; j += gridDim.x * blockDim.x) {
+                const double cj = cost[j];
+                if (cj == 0.0) continue;
+                const double xj = x[j];
+                double t = ls_tight(xj, cj, v0, P.is_int[j] != 0);
+                t = t < lb[j] ? lb[j] : t;
+                t = t > ub[j] ? ub[j] : t;
+                if (t == xj) continue;
+                const double dx = __dsub_rn(t, xj);
+                const double s = __dadd_rn(ls_column_score(P, w, L, j, dx), ls_objective_term(D, delta, w0, cj, dx));
+                const LsKey key{s, t, j, 1};
+                if (ls_before(key, best)) best = key;
+            }
         }
     }
     // warp, then block reduction of the keys; violated rows counted once per warp
@@ -154,8 +241,43 @@ __global__ void __launch_bounds__(kLsThreads) k_ls_score(DevProblem P, const dou
     }
 }
 
-__global__ void __launch_bounds__(kLsThreads) k_ls_apply(DevProblem P, double* __restrict__ x, double* __restrict__ L,
-                                                         const LsKey* __restrict__ part, int nparts, LsCtl* ctl) {
+// one block moves x_j to t: the activities of its column, then x_j (and, with the objective
+// moves, D and the count of violated rows)
+template <bool OBJ>
+__device__ void ls_move(const DevProblem& P, double* __restrict__ x, double* __restrict__ L, int j, double t,
+                        LsCtl* ctl, const double* __restrict__ cost) {
+    __shared__ int sdv[kLsThreads / 32];
+    const double dx = __dsub_rn(t, x[j]);
+    int dv = 0;
+    for (int c = P.col_ptr[j] + threadIdx.x; c < P.col_ptr[j + 1]; c += kLsThreads) {
+        const int r = P.row_idx[c];
+        const double old = L[r];
+        const double nw = __dadd_rn(old, __dmul_rn(P.col_val[c], dx));
+        L[r] = nw;
+        if constexpr (OBJ) {
+            const double g = P.grow[r].x;
+            if (isfinite(g)) dv += (__dsub_rn(nw, g) > 0.0 ? 1 : 0) - (__dsub_rn(old, g) > 0.0 ? 1 : 0);
+        }
+    }
+    if constexpr (OBJ) {
+        dv = __reduce_add_sync(0xffffffffu, dv);
+        if ((threadIdx.x & 31) == 0) sdv[threadIdx.x >> 5] = dv;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if constexpr (OBJ) {
+            int tot = 0;
+            for (int i = 0; i < kLsThreads / 32; ++i) tot += sdv[i];
+            ctl->nv += tot;
+            ctl->D = __dadd_rn(ctl->D, __dmul_rn(cost[j], dx));
+        }
+        x[j] = t;
+        ctl->moves += 1;
+    }
+}
+
+// the best of the per-block keys, in every thread
+__device__ LsKey ls_block_best(const LsKey* __restrict__ part, int nparts) {
     __shared__ LsKey sk[kLsThreads];
     LsKey b = ls_none();
     for (int i = threadIdx.x; i < nparts; i += kLsThreads)
@@ -167,26 +289,151 @@ __global__ void __launch_bounds__(kLsThreads) k_ls_apply(DevProblem P, double* _
         __syncthreads();
     }
     const LsKey best = sk[0];
-    const int nviol = ctl->nviol;
+    __syncthreads();
+    return best;
+}
+
+template <bool OBJ>
+__global__ void __launch_bounds__(kLsThreads) k_ls_apply(DevProblem P, double* __restrict__ x, double* __restrict__ L,
+                                                         const LsKey* __restrict__ part, int nparts, LsCtl* ctl,
+                                                         const double* __restrict__ cost) {
+    if constexpr (OBJ) {
+        if (ctl->done) {   // a lift move ended this iteration
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                ctl->done = 0;
+                ctl->bump = 0;
+                ctl->nviol = 0;
+            }
+            return;
+        }
+    }
+    const LsKey best = ls_block_best(part, nparts);
+    const int nviol = OBJ ? ctl->nv : ctl->nviol;
     __syncthreads();
     if (best.j != INT_MAX && best.score > 0.0) {
-        const int j = best.j;
-        const double dx = __dsub_rn(best.t, x[j]);
-        for (int c = P.col_ptr[j] + threadIdx.x; c < P.col_ptr[j + 1]; c += kLsThreads) {
-            const int r = P.row_idx[c];
-            L[r] = __dadd_rn(L[r], __dmul_rn(P.col_val[c], dx));
-        }
-        __syncthreads();
+        ls_move<OBJ>(P, x, L, best.j, best.t, ctl, cost);
         if (threadIdx.x == 0) {
-            x[j] = best.t;
-            ctl->moves += 1;
             ctl->bump = 0;
+            if (OBJ) ctl->breakthroughs += best.kind;
         }
     } else if (threadIdx.x == 0) {
         ctl->bump = nviol > 0 ? 1 : 0;
-        if (nviol > 0) ctl->bumps += 1;
+        if (nviol > 0) {
+            ctl->bumps += 1;
+        } else if (OBJ && ctl->has_best) {   // no violated row: the objective row's weight grows
+            ctl->w0 = __dadd_rn(ctl->w0, 1.0);
+            ctl->bumps += 1;
+        }
     }
     if (threadIdx.x == 0) ctl->nviol = 0;
+}
+
+// the lift moves at a point with no violated row; the point is copied to x_best first when it
+// becomes the incumbent (the first such point, or D < 0)
+__global__ void __launch_bounds__(kLsThreads) k_lso_lift(DevProblem P, const double* __restrict__ lb,
+                                                         const double* __restrict__ ub, const double* __restrict__ x,
+                                                         const double* __restrict__ L, const double* __restrict__ cost,
+                                                         double* __restrict__ x_best, LsKey* __restrict__ part,
+                                                         const LsCtl* ctl) {
+    if (ctl->nv != 0) return;
+    const bool rec = !ctl->has_best || ctl->D < 0.0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    LsKey best = ls_none();
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < P.n; j += gridDim.x * blockDim.x) {
+        const double xj = x[j];
+        if (rec) x_best[j] = xj;
+        const double cj = cost[j];
+        if (cj == 0.0) continue;
+        const bool up = cj < 0.0;   // the direction sigma = -sign(c_j)
+        const bool integer = P.is_int[j] != 0;
+        double step = INFINITY;
+        for (int c = P.col_ptr[j]; c < P.col_ptr[j + 1]; ++c) {
+            const double a = P.col_val[c];
+            if (up ? !(a > 0.0) : !(a < 0.0)) continue;
+            const int r = P.row_idx[c];
+            const double g = P.grow[r].x;
+            if (!isfinite(g)) continue;
+            const double slack = __dsub_rn(g, L[r]);
+            const double sr = integer ? ls_floor_div(slack, fabs(a)) : __ddiv_rn(slack, fabs(a));
+            step = sr < step ? sr : step;
+        }
+        double t;
+        if (isinf(step)) {
+            t = up ? ub[j] : lb[j];
+        } else {
+            t = up ? __dadd_rn(xj, step) : __dsub_rn(xj, step);
+            t = t < lb[j] ? lb[j] : t;
+            t = t > ub[j] ? ub[j] : t;
+        }
+        if (!isfinite(t) || t == xj) continue;
+        const double gain = -__dmul_rn(cj, __dsub_rn(t, xj));
+        const LsKey key{gain, t, j, 0};
+        if (ls_before(key, best)) best = key;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const LsKey other = ls_shfl(best, lane ^ o);
+        if (ls_before(other, best)) best = other;
+    }
+    __shared__ LsKey wk[kLsThreads / 32];
+    if (lane == 0) wk[wid] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        LsKey b = wk[0];
+        for (int i = 1; i < kLsThreads / 32; ++i)
+            if (ls_before(wk[i], b)) b = wk[i];
+        part[blockIdx.x] = b;
+    }
+}
+
+// records the incumbent, then applies the best lift move when its gain is positive
+__global__ void __launch_bounds__(kLsThreads) k_lso_lift_apply(DevProblem P, double* __restrict__ x,
+                                                               double* __restrict__ L, const LsKey* __restrict__ part,
+                                                               int nparts, LsCtl* ctl, const double* __restrict__ cost) {
+    const int nv = ctl->nv;
+    const bool rec = nv == 0 && (!ctl->has_best || ctl->D < 0.0);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ctl->done = 0;
+        if (rec) {
+            ctl->has_best = 1;
+            ctl->D = 0.0;
+            ctl->improvements += 1;
+        }
+    }
+    if (nv != 0) return;
+    const LsKey best = ls_block_best(part, nparts);
+    if (best.j != INT_MAX && best.score > 0.0) {
+        ls_move<true>(P, x, L, best.j, best.t, ctl, cost);
+        if (threadIdx.x == 0) {
+            ctl->lifts += 1;
+            ctl->done = 1;
+        }
+    }
+}
+
+// the objective row's step: 1 when every nonzero cost sits on an integer variable and is
+// integral, else 1e-4
+__global__ void k_lso_cost_flags(DevProblem P, const double* __restrict__ cost, LsCtl* ctl) {
+    int any = 0, frac = 0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < P.n; j += gridDim.x * blockDim.x) {
+        const double cj = cost[j];
+        if (cj == 0.0) continue;
+        any = 1;
+        if (!P.is_int[j] || cj != floor(cj)) frac = 1;
+    }
+    any = __reduce_or_sync(0xffffffffu, any);
+    frac = __reduce_or_sync(0xffffffffu, frac);
+    if ((threadIdx.x & 31) == 0) {
+        if (any) atomicOr(&ctl->cost_any, 1);
+        if (frac) atomicOr(&ctl->cost_frac, 1);
+    }
+}
+
+__global__ void k_lso_init(LsCtl* ctl, double w0) {
+    ctl->delta = ctl->cost_any && !ctl->cost_frac ? 1.0 : 1e-4;
+    ctl->w0 = w0;
+    ctl->D = 0.0;
 }
 
 __global__ void k_ls_bump(DevProblem P, const double* __restrict__ L, double* __restrict__ w, const LsCtl* ctl) {
@@ -237,6 +484,91 @@ __global__ void k_ls_summary_finish(const double* part, int nblocks, double* out
 
 using namespace gpubp;
 
+namespace gpubp {
+
+struct LsOut {
+    double summary[6];   // violated rows, sum w_k v_k, c x; then the same for x_best
+    LsCtl ctl;
+};
+
+// the search on the stream: `iterations` iterations from (x, w), the objective moves when OBJ
+template <bool OBJ>
+static int ls_run(mip_problem* p, const double* lb, const double* ub, double* x, double* w, double* x_best,
+                  int iterations, double w0, LsOut* out, cudaStream_t s) {
+    void *pL = nullptr, *pPart = nullptr, *pCtl = nullptr, *pSum = nullptr, *pOut = nullptr;
+    // the scoring pass on every resident block (its per-block bests are reduced by k_ls_apply)
+    static int occ_score[2] = {-1, -1}, occ_lift = -1;
+    if (occ_score[OBJ] < 0) {
+        cudaError_t oe =
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_score[OBJ], k_ls_score<OBJ>, kLsThreads, 0);
+        if (oe != cudaSuccess) return fail_cuda(oe, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    }
+    if (OBJ && occ_lift < 0) {
+        cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_lift, k_lso_lift, kLsThreads, 0);
+        if (oe != cudaSuccess) return fail_cuda(oe, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    }
+    const int grid_score = p->sms * (occ_score[OBJ] > 0 ? occ_score[OBJ] : 1);
+    const int grid_lift = p->sms * (occ_lift > 0 ? occ_lift : 1);
+    const int nparts = grid_score > grid_lift ? grid_score : grid_lift;
+    auto release = [&]() {
+        for (void* q : {pL, pPart, pCtl, pSum, pOut})
+            if (q) cudaFreeAsync(q, s);
+    };
+    cudaError_t e = cudaSuccess;
+    if ((e = cudaMallocAsync(&pL, sizeof(double) * (size_t)(p->m ? p->m : 1), s)) != cudaSuccess ||
+        (e = cudaMallocAsync(&pPart, sizeof(LsKey) * (size_t)nparts, s)) != cudaSuccess ||
+        (e = cudaMallocAsync(&pCtl, sizeof(LsCtl), s)) != cudaSuccess ||
+        (e = cudaMallocAsync(&pSum, sizeof(double) * 3 * kLsRedBlocks, s)) != cudaSuccess ||
+        (e = cudaMallocAsync(&pOut, sizeof(double) * 6, s)) != cudaSuccess) {
+        release();
+        return fail_cuda(e, "cudaMallocAsync");
+    }
+    double* L = static_cast<double*>(pL);
+    LsKey* part = static_cast<LsKey*>(pPart);
+    LsCtl* ctl = static_cast<LsCtl*>(pCtl);
+    double* sum = static_cast<double*>(pSum);
+    double* dout = static_cast<double*>(pOut);
+    const double* cost = p->obj;
+    const int grid_rows = p->sms * 8;
+    if ((e = cudaMemsetAsync(ctl, 0, sizeof(LsCtl), s)) != cudaSuccess) {
+        release();
+        return fail_cuda(e, "cudaMemsetAsync");
+    }
+    k_ls_activities<<<grid_rows, kLsThreads, 0, s>>>(p->dp, x, L, OBJ ? &ctl->nv : nullptr);
+    if (OBJ) {
+        k_lso_cost_flags<<<grid_rows, kLsThreads, 0, s>>>(p->dp, cost, ctl);
+        k_lso_init<<<1, 1, 0, s>>>(ctl, w0);
+    }
+    for (int it = 0; it < iterations; ++it) {
+        if (OBJ) {
+            k_lso_lift<<<grid_lift, kLsThreads, 0, s>>>(p->dp, lb, ub, x, L, cost, x_best, part, ctl);
+            k_lso_lift_apply<<<1, kLsThreads, 0, s>>>(p->dp, x, L, part, grid_lift, ctl, cost);
+        }
+        k_ls_score<OBJ><<<grid_score, kLsThreads, 0, s>>>(p->dp, lb, ub, x, w, L, part, ctl, cost);
+        k_ls_apply<OBJ><<<1, kLsThreads, 0, s>>>(p->dp, x, L, part, grid_score, ctl, cost);
+        k_ls_bump<<<grid_rows, kLsThreads, 0, s>>>(p->dp, L, w, ctl);
+    }
+    k_ls_summary<<<kLsRedBlocks, kLsThreads, 0, s>>>(p->dp, cost, x, w, L, sum);
+    k_ls_summary_finish<<<1, 32, 0, s>>>(sum, kLsRedBlocks, dout);
+    if (OBJ) {   // c x_best (the other two sums are not used)
+        k_ls_summary<<<kLsRedBlocks, kLsThreads, 0, s>>>(p->dp, cost, x_best, w, L, sum);
+        k_ls_summary_finish<<<1, 32, 0, s>>>(sum, kLsRedBlocks, dout + 3);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) {
+        release();
+        return fail_cuda(e, "local search launch");
+    }
+    e = cudaMemcpyAsync(out->summary, dout, sizeof(out->summary), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&out->ctl, ctl, sizeof(LsCtl), cudaMemcpyDeviceToHost, s);
+    release();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(e, "local search results");
+    p->last_stream = s;
+    return BP_OK;
+}
+
+}  // namespace gpubp
+
 extern "C" int local_search_mtm(mip_problem* p, const double* lb, const double* ub, double* x, double* w,
                                 const ls_params* params, ls_result* result, void* stream) {
     if (!p || !params || !result || (p->n && (!lb || !ub || !x)) || (p->m && !w)) {
@@ -247,62 +579,47 @@ extern "C" int local_search_mtm(mip_problem* p, const double* lb, const double* 
         set_error("local_search_mtm: negative iteration count");
         return BP_ERR_INVALID;
     }
-    cudaStream_t s = (cudaStream_t)stream;
     memset(result, 0, sizeof(*result));
-    void *pL = nullptr, *pPart = nullptr, *pCtl = nullptr, *pSum = nullptr, *pOut = nullptr;
-    // the scoring pass on every resident block (its per-block bests are reduced by k_ls_apply)
-    static int occ_score = -1;
-    if (occ_score < 0) {
-        cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_score, k_ls_score, kLsThreads, 0);
-        if (oe != cudaSuccess) return fail_cuda(oe, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-    }
-    const int grid_score = p->sms * (occ_score > 0 ? occ_score : 1);
-    auto release = [&]() {
-        for (void* q : {pL, pPart, pCtl, pSum, pOut})
-            if (q) cudaFreeAsync(q, s);
-    };
-    cudaError_t e = cudaSuccess;
-    if ((e = cudaMallocAsync(&pL, sizeof(double) * (size_t)(p->m ? p->m : 1), s)) != cudaSuccess ||
-        (e = cudaMallocAsync(&pPart, sizeof(LsKey) * (size_t)grid_score, s)) != cudaSuccess ||
-        (e = cudaMallocAsync(&pCtl, sizeof(LsCtl), s)) != cudaSuccess ||
-        (e = cudaMallocAsync(&pSum, sizeof(double) * 3 * kLsRedBlocks, s)) != cudaSuccess ||
-        (e = cudaMallocAsync(&pOut, sizeof(double) * 3, s)) != cudaSuccess) {
-        release();
-        return fail_cuda(e, "cudaMallocAsync");
-    }
-    double* L = static_cast<double*>(pL);
-    LsKey* part = static_cast<LsKey*>(pPart);
-    LsCtl* ctl = static_cast<LsCtl*>(pCtl);
-    const int grid_rows = p->sms * 8;
-    if ((e = cudaMemsetAsync(ctl, 0, sizeof(LsCtl), s)) != cudaSuccess) {
-        release();
-        return fail_cuda(e, "cudaMemsetAsync");
-    }
-    k_ls_activities<<<grid_rows, kLsThreads, 0, s>>>(p->dp, x, L);
-    for (int it = 0; it < params->iterations; ++it) {
-        k_ls_score<<<grid_score, kLsThreads, 0, s>>>(p->dp, lb, ub, x, w, L, part, ctl);
-        k_ls_apply<<<1, kLsThreads, 0, s>>>(p->dp, x, L, part, grid_score, ctl);
-        k_ls_bump<<<grid_rows, kLsThreads, 0, s>>>(p->dp, L, w, ctl);
-    }
-    k_ls_summary<<<kLsRedBlocks, kLsThreads, 0, s>>>(p->dp, p->obj, x, w, L, static_cast<double*>(pSum));
-    k_ls_summary_finish<<<1, 32, 0, s>>>(static_cast<double*>(pSum), kLsRedBlocks, static_cast<double*>(pOut));
-    if ((e = cudaGetLastError()) != cudaSuccess) {
-        release();
-        return fail_cuda(e, "local search launch");
-    }
-    double out[3];
-    LsCtl hc;
-    e = cudaMemcpyAsync(out, pOut, sizeof(out), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, ctl, sizeof(hc), cudaMemcpyDeviceToHost, s);
-    release();
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return fail_cuda(e, "local search results");
+    LsOut out;
+    const int rc = ls_run<false>(p, lb, ub, x, w, nullptr, params->iterations, 0.0, &out, (cudaStream_t)stream);
+    if (rc != BP_OK) return rc;
     result->iterations = params->iterations;
-    result->moves = hc.moves;
-    result->bumps = hc.bumps;
-    result->violated = (int32_t)out[0];
-    result->weighted_violation = out[1];
-    result->objective = out[2];
-    p->last_stream = s;
+    result->moves = out.ctl.moves;
+    result->bumps = out.ctl.bumps;
+    result->violated = (int32_t)out.summary[0];
+    result->weighted_violation = out.summary[1];
+    result->objective = out.summary[2];
+    return BP_OK;
+}
+
+extern "C" int local_search_objective(mip_problem* p, const double* lb, const double* ub, double* x, double* w,
+                                      double* x_best, const ls_obj_params* params, ls_obj_result* result,
+                                      void* stream) {
+    if (!p || !params || !result || (p->n && (!lb || !ub || !x || !x_best)) || (p->m && !w)) {
+        set_error("local_search_objective: null argument");
+        return BP_ERR_INVALID;
+    }
+    if (params->iterations < 0 || !(params->obj_weight >= 0.0) || !std::isfinite(params->obj_weight)) {
+        set_error("local_search_objective: negative iteration count or invalid objective weight");
+        return BP_ERR_INVALID;
+    }
+    memset(result, 0, sizeof(*result));
+    LsOut out;
+    const int rc =
+        ls_run<true>(p, lb, ub, x, w, x_best, params->iterations, params->obj_weight, &out, (cudaStream_t)stream);
+    if (rc != BP_OK) return rc;
+    result->iterations = params->iterations;
+    result->moves = out.ctl.moves;
+    result->bumps = out.ctl.bumps;
+    result->violated = (int32_t)out.summary[0];
+    result->weighted_violation = out.summary[1];
+    result->objective = out.summary[2];
+    result->lifts = out.ctl.lifts;
+    result->breakthroughs = out.ctl.breakthroughs;
+    result->improvements = out.ctl.improvements;
+    result->found = out.ctl.has_best;
+    result->best_objective = out.ctl.has_best ? out.summary[5] : INFINITY;
+    result->obj_weight = out.ctl.w0;
+    result->delta = out.ctl.delta;
     return BP_OK;
 }

@@ -1,5 +1,5 @@
-"""GPU local search move scoring (local_search_mtm through the C ABI) against the oracle
-(oracle/local_mip.py).  Both sides apply the same operations in the same order, so points,
+"""GPU local search move scoring (local_search_mtm and local_search_objective through the C ABI)
+against the oracle (oracle/local_mip.py).  Both sides apply the same operations in the same order, so points,
 weights and counts must agree bit for bit."""
 import numpy as np
 import pytest
@@ -98,3 +98,111 @@ def test_repeatable(pkg):
     a = _gpu(pkg, p, x0, np.ones(p.m), 50)
     b = _gpu(pkg, p, x0, np.ones(p.m), 50)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2] == b[2]
+
+
+# --- objective moves (local_search_objective) ---
+
+
+def _gpu_obj(pkg, p, x0, w0, iterations, obj_weight=1.0):
+    import torch
+    prob = pkg.Problem(p)
+    x, w = _t(x0), _t(w0)
+    xb = torch.full((p.n,), float("nan"), dtype=torch.float64, device="cuda")
+    r = prob.local_search_objective(_t(p.lb), _t(p.ub), x, w, xb, iterations=iterations, obj_weight=obj_weight)
+    return x.cpu().numpy(), w.cpu().numpy(), xb.cpu().numpy(), r
+
+
+def _same_obj(p, x0, w0, iterations, pkg):
+    ox, ow, ob, orr = lm.search_objective(p, p.lb, p.ub, x0, w0, iterations)
+    gx, gw, gb, gr = _gpu_obj(pkg, p, x0, w0, iterations)
+    np.testing.assert_array_equal(gx, ox)
+    np.testing.assert_array_equal(gw, ow)
+    for k in ("moves", "bumps", "violated", "lifts", "breakthroughs", "improvements", "found", "obj_weight", "delta"):
+        assert gr[k] == orr[k], (k, gr, orr)
+    if orr["found"]:
+        np.testing.assert_array_equal(gb, ob)
+        assert abs(gr["best_objective"] - orr["best_objective"]) <= 1e-9 * max(1.0, abs(orr["best_objective"]))
+    else:
+        assert np.isnan(gb).all() and gr["best_objective"] == np.inf
+    assert abs(gr["weighted_violation"] - orr["weighted_violation"]) <= 1e-9 * max(1.0, orr["weighted_violation"])
+    return orr
+
+
+@pytest.mark.parametrize("case", range(2))
+def test_objective_hand_worked_steps(pkg, case):
+    c = load_golden("local_mip_objective.json")["cases"][case]
+    p = milp_from_dense(c["A"], c["g"], c["lb"], c["ub"], c["is_int"])
+    p.c = np.array(c["c"], dtype=float)
+    for k, st in enumerate(c["steps"]):
+        x, w, xb, r = _gpu_obj(pkg, p, c["x0"], c["w0"], k + 1, obj_weight=c["obj_weight"])
+        np.testing.assert_array_equal(x, st["x"])
+        np.testing.assert_array_equal(w, st["w"])
+        np.testing.assert_array_equal(xb, st["best"])
+        assert r["obj_weight"] == st["w0"]
+    for key in ("moves", "bumps", "lifts", "breakthroughs", "improvements", "best_objective"):
+        assert r[key] == c[key], key
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_objective_matches_oracle_integer_data(pkg, seed):
+    """Integer data and integral costs (delta = 1), started from the planted feasible point:
+    lift moves first, then breakthrough moves, row and objective weight bumps."""
+    p = _integer_problem(520 + seed, 80, 60)
+    p.c = np.random.default_rng(seed).integers(-5, 6, p.n).astype(float)
+    r = _same_obj(p, np.asarray(p.x0, dtype=float), np.ones(p.m), 300, pkg)
+    assert r["lifts"] > 0 and r["improvements"] > 0 and r["breakthroughs"] > 0
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_objective_matches_oracle_many_blocks(pkg, seed):
+    """2,500 variables (ten blocks of the per-variable passes), 3,000 rows, 40 nonzero costs
+    spread over the variables: the lifts run out early and the breakthrough phase follows."""
+    p = _integer_problem(580 + seed, 3000, 2500)
+    rng = np.random.default_rng(seed)
+    c = np.zeros(p.n)
+    pick = rng.choice(p.n, 40, replace=False)
+    c[pick] = rng.integers(1, 6, 40) * rng.choice([-1, 1], 40)
+    p.c = c
+    r = _same_obj(p, np.asarray(p.x0, dtype=float), np.ones(p.m), 300, pkg)
+    assert r["lifts"] > 0 and r["breakthroughs"] > 0 and r["obj_weight"] > 1.0
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_objective_matches_oracle_from_infeasible_point(pkg, seed):
+    p = _integer_problem(540 + seed, 300, 250)
+    p.c = np.random.default_rng(seed).integers(-5, 6, p.n).astype(float)
+    x0 = np.clip(np.round(np.random.default_rng(seed).normal(0, 3, p.n)), p.lb, p.ub)
+    _same_obj(p, x0, np.ones(p.m), 120, pkg)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_objective_matches_oracle_general_data(pkg, seed):
+    """Non-integer coefficients and costs, continuous variables (delta = 1e-4): the same
+    operation order on both sides still gives identical results."""
+    p = synth.random_milp(620 + seed, 60, 50, len_lo=2, len_hi=8, int_fraction=0.6, slack_scale=0.3)
+    p.lb = np.where(np.isfinite(p.lb), p.lb, -50.0)
+    p.ub = np.where(np.isfinite(p.ub), p.ub, 50.0)
+    r = _same_obj(p, np.clip(np.asarray(p.x0, dtype=float), p.lb, p.ub), np.ones(p.m), 300, pkg)
+    assert r["delta"] == 1e-4 and r["lifts"] > 0
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_objective_zero_cost_is_local_search_mtm(pkg, seed):
+    p = _integer_problem(560 + seed, 300, 250)
+    p.c = np.zeros(p.n)
+    x0 = np.clip(np.round(np.random.default_rng(seed).normal(0, 3, p.n)), p.lb, p.ub)
+    ax, aw, ar = _gpu(pkg, p, x0, np.ones(p.m), 60)
+    bx, bw, _, br = _gpu_obj(pkg, p, x0, np.ones(p.m), 60)
+    np.testing.assert_array_equal(ax, bx)
+    np.testing.assert_array_equal(aw, bw)
+    assert ar["moves"] == br["moves"] and br["lifts"] == 0 and br["breakthroughs"] == 0
+
+
+def test_objective_rejects_bad_weight(pkg):
+    import torch
+    p = _integer_problem(77, 40, 30)
+    prob = pkg.Problem(p)
+    x, w = _t(p.x0), _t(np.ones(p.m))
+    xb = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(Exception):
+        prob.local_search_objective(_t(p.lb), _t(p.ub), x, w, xb, iterations=5, obj_weight=-1.0)
