@@ -27,7 +27,17 @@ approximate LP (oracle/pdhg.py), fix-and-propagate rounding (fp_oracle.c) and th
             no more than `cycle_ratio` of that mean; a cycle is broken by the local search from
             the current point with the kept weights (ls_iterations), otherwise the next point is
             the snapped projection rounded to the nearest integers (ties up).
-No objective cut (the improvement mode); the budget is a round count in place of a time limit.
+The budget is a round count in place of a time limit.
+
+Improvement mode (`improve=True`; the paper's extension of the procedure from a generation to an
+improvement heuristic, a cut perpendicular to the objective at each feasible point): the reading
+taken is that a feasible point (from the start or a round) becomes the incumbent x* instead of
+ending the pump; the problem then carries one more row, the cut  c x <= c x* - delta  (delta as
+in the local search's objective row: 1 for an integral objective on integer variables, else
+1e-4), reset at each incumbent; the loop continues from x* with an empty distance history, the
+LP's dual iterate extended by 0 and the kept weights by 1 for the cut row; a point satisfying
+every row of the cut problem is a better incumbent.  The round budget ends the pump, which
+returns the incumbent.
 """
 from __future__ import annotations
 
@@ -71,10 +81,39 @@ def nearest(is_int, x, lb, ub):
     return out
 
 
-def run(p, lb, ub, rounds=20, lp_iterations=500, ls_iterations=200, cycle_window=3, cycle_ratio=0.1, seed=1):
-    """Returns (x, result dict): status 0 when a feasible point was found (x is it), found_at
-    -2 (start rounding), -1 (all-zero start), r >= 0 (round r) or -3 (none), rounds run, cycle
-    breaks, the distances."""
+class _WithCut:
+    """The problem with the objective cut c x <= rhs appended as its last row."""
+
+    def __init__(self, p, rhs):
+        c = np.asarray(p.c, dtype=np.float64)
+        cols = np.flatnonzero(c != 0.0).astype(np.int32)
+        self.m, self.n = int(p.m) + 1, int(p.n)
+        self.row_ptr = np.append(np.asarray(p.row_ptr, dtype=np.int64), int(p.row_ptr[-1]) + len(cols))
+        self.col = np.concatenate([np.asarray(p.col, dtype=np.int32), cols])
+        self.val = np.concatenate([np.asarray(p.val, dtype=np.float64), c[cols]])
+        self.g = np.append(np.asarray(p.g, dtype=np.float64), rhs)
+        self.lb, self.ub, self.is_int, self.c = p.lb, p.ub, p.is_int, c
+
+    @property
+    def nnz(self):
+        return int(self.row_ptr[-1])
+
+
+def with_cut(p, x_best):
+    """The cut problem for incumbent x_best: rhs = c x_best - delta (plain sum in index order)."""
+    c = np.asarray(p.c, dtype=np.float64)
+    f = 0.0
+    for j in range(p.n):
+        f = f + c[j] * float(x_best[j])
+    return _WithCut(p, f - local_mip.objective_delta(p))
+
+
+def run(p, lb, ub, rounds=20, lp_iterations=500, ls_iterations=200, cycle_window=3, cycle_ratio=0.1, seed=1,
+        improve=False):
+    """Returns (x, result dict): status 0 when a feasible point was found (x is it, or the best
+    one in improvement mode), found_at -2 (start rounding), -1 (all-zero start), r >= 0 (round
+    r) or -3 (none) for the first feasible point, rounds run, cycle breaks, the distances, and in
+    improvement mode the incumbents recorded and the best objective."""
     lb = np.asarray(lb, dtype=np.float64)
     ub = np.asarray(ub, dtype=np.float64)
     P = oracle.Problem(p)
@@ -83,33 +122,64 @@ def run(p, lb, ub, rounds=20, lp_iterations=500, ls_iterations=200, cycle_window
     xl = snap(x, lb, ub)
     s, _ = P.fix_and_propagate(xl, lb, ub, seed=seed)
     s1, w1, r1 = local_mip.search(p, lb, ub, s, np.ones(p.m), ls_iterations)
-    res = {"status": 1, "found_at": -3, "rounds": 0, "cycles": 0, "distances": []}
+    res = {"status": 1, "found_at": -3, "rounds": 0, "cycles": 0, "distances": [], "improvements": 0,
+           "best_objective": float("inf"), "incumbents": []}
+    best = None
+    q, Q = p, P   # the problem the loop works on (with the cut once an incumbent exists)
+
+    def incumbent(pt, where):
+        nonlocal best, q, Q, y, W
+        if best is None:
+            res.update(status=0, found_at=where)
+            y = np.append(y, 0.0)
+            W = np.append(W, 1.0)
+        best = np.array(pt, dtype=np.float64)
+        res["improvements"] += 1
+        res["best_objective"] = float(np.asarray(p.c, dtype=np.float64) @ best)
+        res["incumbents"].append(best.copy())
+        q = with_cut(p, best)
+        Q = oracle.Problem(q)
+
+    W = None
     if r1["violated"] == 0:
-        res.update(status=0, found_at=-2)
-        return s1, res
-    s2, w2, r2 = local_mip.search(p, lb, ub, zero, np.ones(p.m), ls_iterations)
-    if r2["violated"] == 0:
-        res.update(status=0, found_at=-1)
-        return s2, res
-    s, W = (s2, w2) if r2["violated"] < r1["violated"] else (s1, w1)
+        if not improve:
+            res.update(status=0, found_at=-2)
+            return s1, res
+        s, W = s1, w1
+        incumbent(s1, -2)
+    else:
+        s2, w2, r2 = local_mip.search(p, lb, ub, zero, np.ones(p.m), ls_iterations)
+        if r2["violated"] == 0:
+            if not improve:
+                res.update(status=0, found_at=-1)
+                return s2, res
+            s, W = s2, w2
+            incumbent(s2, -1)
+        else:
+            s, W = (s2, w2) if r2["violated"] < r1["violated"] else (s1, w1)
     hist = []
     for r in range(rounds):
         c = projection_objective(p.is_int, s, lb, ub)
-        x, y, _ = pdhg.solve(p, lb, ub, x, y, iterations=lp_iterations, restart_period=100, c=c)
+        x, y, _ = pdhg.solve(q, lb, ub, x, y, iterations=lp_iterations, restart_period=100, c=c)
         xp = snap(x, lb, ub)
         d = distance(p.is_int, xp, s)
         cyc = cycle(hist, d, cycle_window, cycle_ratio)
         hist.append(d)
         res["rounds"] = r + 1
-        sr, _ = P.fix_and_propagate(xp, lb, ub, seed=seed + r + 1)
-        st, _, rt = local_mip.search(p, lb, ub, sr, np.ones(p.m), max(1, ls_iterations // 5))
+        sr, _ = Q.fix_and_propagate(xp, lb, ub, seed=seed + r + 1)
+        st, _, rt = local_mip.search(q, lb, ub, sr, np.ones(q.m), max(1, ls_iterations // 5))
         if rt["violated"] == 0:
-            res.update(status=0, found_at=r, distances=hist)
-            return st, res
+            if not improve:
+                res.update(status=0, found_at=r, distances=hist)
+                return st, res
+            incumbent(st, r)
+            s = best.copy()
+            hist = []
+            continue
         if cyc:
-            s, W, _ = local_mip.search(p, lb, ub, s, W, ls_iterations)
+            s, W, _ = local_mip.search(q, lb, ub, s, W, ls_iterations)
             res["cycles"] += 1
         else:
             s = nearest(p.is_int, xp, lb, ub)
     res["distances"] = hist
-    return s, res
+    return (best if best is not None else s), res

@@ -46,3 +46,60 @@ def test_end_to_end_sound(seed):
         fin = np.isfinite(p.g)
         assert (L[fin] <= p.g[fin]).all()
     assert r["found_at"] in (-3, -2, -1) or 0 <= r["found_at"] < 6
+
+
+# --- improvement mode (the objective cut at each feasible point) ---
+
+
+def test_with_cut_row():
+    """The cut problem appends one row: the nonzero costs in column order, right-hand side
+    c x* - delta; its other rows are the problem's."""
+    p = synth.knapsack_cover(seed=711, m=30, n=60, nnz=300)
+    p.c = np.zeros(p.n)
+    p.c[[3, 17, 40]] = [2.0, -1.0, 5.0]
+    xb = np.zeros(p.n)
+    xb[[3, 40]] = 1.0
+    q = efp.with_cut(p, xb)
+    assert q.m == p.m + 1 and q.nnz == p.nnz + 3
+    np.testing.assert_array_equal(q.col[p.nnz:], [3, 17, 40])
+    np.testing.assert_array_equal(q.val[p.nnz:], [2.0, -1.0, 5.0])
+    assert q.g[-1] == 7.0 - 1.0                         # c x* = 7, integral objective: delta = 1
+    np.testing.assert_array_equal(q.g[:-1], p.g)
+    np.testing.assert_array_equal(q.col[:p.nnz], p.col)
+    p.c[17] = -0.5                                      # a fractional cost: delta = 1e-4
+    assert efp.with_cut(p, xb).g[-1] == 7.0 - 1e-4
+
+
+def _rows_ok(p, x):
+    L = local_mip.activities(p, x)
+    fin = np.isfinite(p.g)
+    return bool((L[fin] <= p.g[fin]).all())
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_improvement_mode(seed):
+    """The first incumbent is generation mode's point; every incumbent satisfies every row of
+    the problem, is integral on integer variables, and improves on the previous one by at least
+    delta (1: integral costs); the returned point is the last incumbent."""
+    p = synth.knapsack_cover(seed=700 + seed, m=300, n=600, nnz=3000)
+    p.c = np.random.default_rng(seed).integers(-5, 6, p.n).astype(float)
+    kw = dict(rounds=6, lp_iterations=200, ls_iterations=100, seed=seed + 1)
+    xg, rg = efp.run(p, p.lb, p.ub, **kw)
+    xi, ri = efp.run(p, p.lb, p.ub, improve=True, **kw)
+    assert ri["status"] == rg["status"] and ri["found_at"] == rg["found_at"]
+    if rg["status"] != 0:
+        assert ri["improvements"] == 0 and ri["rounds"] == kw["rounds"]
+        return
+    inc = ri["incumbents"]
+    assert len(inc) == ri["improvements"] >= 1
+    np.testing.assert_array_equal(inc[0], xg)
+    np.testing.assert_array_equal(inc[-1], xi)
+    prev = np.inf
+    for x in inc:
+        assert _rows_ok(p, x)
+        assert (x >= p.lb).all() and (x <= p.ub).all()
+        assert (x[p.is_int == 1] == np.round(x[p.is_int == 1])).all()
+        f = float(p.c @ x)
+        assert f <= prev - 1.0
+        prev = f
+    assert ri["best_objective"] == prev
