@@ -601,7 +601,8 @@ int local_search_objective(mip_problem *p, const double *lb, const double *ub, d
 
 /*
  * extended_fp -- the extended feasibility pump's orchestration (Section 2.5, Algorithm 2), in
- * generation mode (it stops at the first feasible point; no objective cut).
+ * generation mode (it stops at the first feasible point) or improvement mode (improve = 1: the
+ * objective cut at each feasible point).
  *
  * Start: the approximate LP from zero (pdhg_solve, lp_iterations), snapped to multiples of
  * 2^-20, rounded by fix_and_propagate (seed), then local_search_mtm (ls_iterations, fresh
@@ -615,10 +616,21 @@ int local_search_objective(mip_problem *p, const double *lb, const double *ub, d
  * cycle_ratio of it) is broken by local_search_mtm from the point with the kept weights
  * (ls_iterations), otherwise the next point is the projection rounded to the nearest integers.
  *
- * x_out:   DEVICE double[n]: the feasible point found, else the loop's last point.
+ * Improvement mode: a feasible point (from the start or a round) becomes the incumbent x*
+ * instead of ending the pump.  The loop then works on the problem with one more row, the cut
+ * c x <= c x* - delta (delta = 1 when every variable with a nonzero cost is integer with an
+ * integral cost, else 1e-4; c x* summed in index order), a handle built on the device and
+ * rebuilt at each incumbent; it continues from x* with an empty distance history, the LP's dual
+ * iterate extended by 0 and the kept weights by 1 for the cut row.  A point satisfying every row
+ * of the cut problem is a better incumbent.  The round budget ends the pump.  Costs of magnitude
+ * below 1e-12 are rejected by the cut row's load (BP_ERR_INVALID).
+ *
+ * x_out:   DEVICE double[n]: the feasible point found (improvement mode: the last incumbent),
+ *          else the loop's last point.
  * result:  HOST pointer (the call synchronises the stream): status FP_FEASIBLE / FP_INFEASIBLE,
- *          found_at (-2 the start rounding, -1 the all-zero start, r >= 0 round r, -3 none),
- *          rounds run, cycle breaks, the last distance.
+ *          found_at (-2 the start rounding, -1 the all-zero start, r >= 0 round r, -3 none) of
+ *          the first feasible point, rounds run, cycle breaks, the last distance; improvement
+ *          mode: incumbents recorded and c x* of the last (+inf when none).
  * Returns BP_OK, BP_ERR_INVALID, BP_ERR_OOM, BP_ERR_CUDA or BP_ERR_TIMEOUT.
  */
 typedef struct {
@@ -628,6 +640,8 @@ typedef struct {
     int32_t cycle_window;      /* N (3) */
     double cycle_ratio;        /* (0.1) */
     uint64_t seed;             /* fix_and_propagate's seed of the start; round r uses seed + r + 1 */
+    int32_t improve;           /* 0: generation mode, 1: improvement mode (0) */
+    int32_t reserved;
 } efp_params;
 
 typedef struct {
@@ -636,6 +650,9 @@ typedef struct {
     int32_t rounds;
     int32_t cycles;
     double last_distance;
+    int32_t improvements;
+    int32_t reserved;
+    double best_objective;
 } efp_result;
 
 void efp_params_default(efp_params *p);

@@ -52,3 +52,41 @@ def test_loop_runs_somewhere():
         _, r = efp.run(p, p.lb, p.ub, seed=seed + 1, **KW)
         seen += r["rounds"] > 0 and r["cycles"] > 0
     assert seen >= 1
+
+
+def _improve_case(pkg, seed, rounds):
+    import torch
+    p = synth.knapsack_cover(seed=700 + seed, m=300, n=600, nnz=3000)
+    p.c = np.random.default_rng(seed).integers(-5, 6, p.n).astype(float)
+    kw = dict(KW, rounds=rounds)
+    ox, orr = efp.run(p, p.lb, p.ub, seed=seed + 1, improve=True, **kw)
+    prob = pkg.Problem(p)
+    gx, gr = prob.extended_fp(torch.tensor(p.lb, device="cuda"), torch.tensor(p.ub, device="cuda"), seed=seed + 1,
+                              improve=True, **kw)
+    gx = gx.cpu().numpy()
+    for k in ("status", "found_at", "rounds", "cycles", "improvements", "best_objective"):
+        assert gr[k] == orr[k], (k, gr, orr)
+    if orr["distances"]:
+        assert gr["last_distance"] == orr["distances"][-1]
+    np.testing.assert_array_equal(gx, ox)
+    if gr["status"] == 0:
+        L = local_mip.activities(p, gx)
+        fin = np.isfinite(p.g)
+        assert (L[fin] <= p.g[fin]).all()
+        assert float(p.c @ gx) == gr["best_objective"]
+    return orr
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_improvement_mode_matches_oracle(pkg, seed):
+    """Improvement mode (the objective cut at each incumbent) with integral costs, so the cut's
+    right-hand side is exact on both sides: the incumbents, rounds, cycle breaks and the final
+    point agree; seeds 3 and 5 find no feasible point and run on the problem without a cut."""
+    _improve_case(pkg, seed, 6)
+
+
+def test_improvement_mode_cycle_after_cut(pkg):
+    """Sixteen rounds: the cut tightens until a round fails and the loop breaks a cycle on the
+    cut problem."""
+    r = _improve_case(pkg, 0, 16)
+    assert r["cycles"] >= 1 and r["improvements"] >= 10
