@@ -65,6 +65,7 @@ struct LsCtl {
     int nviol;        // violated rows seen by this iteration's scoring pass
     int bump;         // the weights grow in this iteration
     int moves, bumps;
+    int moved_j;      // the variable this iteration moved, -1 if none
     // objective moves
     int nv;           // violated rows of the current point (kept through every move)
     int has_best;     // an incumbent exists
@@ -315,9 +316,11 @@ __global__ void __launch_bounds__(kLsThreads) k_ls_apply(DevProblem P, double* _
         ls_move<OBJ>(P, x, L, best.j, best.t, ctl, cost);
         if (threadIdx.x == 0) {
             ctl->bump = 0;
+            ctl->moved_j = best.j;
             if (OBJ) ctl->breakthroughs += best.kind;
         }
     } else if (threadIdx.x == 0) {
+        ctl->moved_j = -1;
         ctl->bump = nviol > 0 ? 1 : 0;
         if (nviol > 0) {
             ctl->bumps += 1;
@@ -436,6 +439,157 @@ __global__ void k_lso_init(LsCtl* ctl, double w0) {
     ctl->D = 0.0;
 }
 
+// ---- the score cache of the mixed-tight-move search (distance-2 neighbourhood updates) ----
+//
+// The candidate of violated row k on the variable of its nonzero q is kept in slot q: its value
+// T[q] and score S[q] (-inf: no candidate).  A slot depends on row k's activity, on x_j and on
+// the activities and weights of the rows of column j.  A move of x_j* changes x_j* and the
+// activities of the rows of column j* only, so the slots that change are those (k, j) with j
+// in a row of column j* (the distance-2 neighbourhood of j*): k_ls_neighbors recomputes exactly
+// those, with the same function, so every score equals a full recomputation bit for bit.  A
+// weight bump changes every slot: k_ls_full recomputes them all.
+
+// CSC entry -> CSR position: each nonzero finds its row in its column's ascending row list
+__global__ void k_ls_perm(DevProblem P, int* __restrict__ perm) {
+    const int lane = threadIdx.x & 31;
+    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < P.m; k += (gridDim.x * blockDim.x) >> 5) {
+        for (int q = P.row_ptr[k] + lane; q < P.row_ptr[k + 1]; q += 32) {
+            const int j = P.col[q];
+            int lo = P.col_ptr[j], hi = P.col_ptr[j + 1] - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (P.row_idx[mid] < k) lo = mid + 1;
+                else hi = mid;
+            }
+            perm[lo] = q;
+        }
+    }
+}
+
+// the slot of row k (violation v > 0) on variable j with coefficient a
+__device__ __forceinline__ void ls_slot(const DevProblem& P, const double* __restrict__ lb,
+                                        const double* __restrict__ ub, const double* __restrict__ x,
+                                        const double* __restrict__ w, const double* __restrict__ L, int j, double a,
+                                        double v, double* __restrict__ T, double* __restrict__ S, int q) {
+    const double xj = x[j];
+    double t = ls_tight(xj, a, v, P.is_int[j] != 0);
+    t = t < lb[j] ? lb[j] : t;
+    t = t > ub[j] ? ub[j] : t;
+    if (t == xj) {
+        S[q] = -INFINITY;
+        return;
+    }
+    S[q] = ls_column_score(P, w, L, j, __dsub_rn(t, xj));
+    T[q] = t;
+}
+
+// every slot of every violated row (at the start, and after a weight bump)
+__global__ void __launch_bounds__(kLsThreads) k_ls_full(DevProblem P, const double* __restrict__ lb,
+                                                        const double* __restrict__ ub, const double* __restrict__ x,
+                                                        const double* __restrict__ w, const double* __restrict__ L,
+                                                        double* __restrict__ T, double* __restrict__ S,
+                                                        const LsCtl* ctl, int force) {
+    if (!force && !ctl->bump) return;
+    const int lane = threadIdx.x & 31;
+    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < P.m; k += (gridDim.x * blockDim.x) >> 5) {
+        const double g = P.grow[k].x;
+        if (!isfinite(g)) continue;
+        const double v = __dsub_rn(L[k], g);
+        if (!(v > 0.0)) continue;
+        for (int q = P.row_ptr[k] + lane; q < P.row_ptr[k + 1]; q += 32)
+            ls_slot(P, lb, ub, x, w, L, P.col[q], P.val[q], v, T, S, q);
+    }
+}
+
+// after a move of x_j*: the slots (k, j) of the violated rows k of every j in a row of column
+// j*: the entries of the rows of column j*, taken in one flat sequence, are spread over the
+// grid's warps (a long row spreads over the whole grid, short rows run side by side), each
+// warp's lanes over the variable's column (a slot reached through several rows is written with
+// the same value)
+__global__ void __launch_bounds__(kLsThreads) k_ls_neighbors(DevProblem P, const double* __restrict__ lb,
+                                                             const double* __restrict__ ub,
+                                                             const double* __restrict__ x,
+                                                             const double* __restrict__ w,
+                                                             const double* __restrict__ L,
+                                                             const int* __restrict__ perm, double* __restrict__ T,
+                                                             double* __restrict__ S, const LsCtl* ctl) {
+    const int js = ctl->moved_j;
+    if (js < 0) return;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    const int ce = P.col_ptr[js + 1];
+    int ci = P.col_ptr[js], base = 0;   // the row of column j* holding flat entry f starts at base
+    int rb = 0, rlen = 0;
+    if (ci < ce) {
+        const int r = P.row_idx[ci];
+        rb = P.row_ptr[r];
+        rlen = P.row_ptr[r + 1] - rb;
+    }
+    for (int f = gw;; f += nw) {
+        while (ci < ce && f >= base + rlen) {
+            base += rlen;
+            if (++ci < ce) {
+                const int r = P.row_idx[ci];
+                rb = P.row_ptr[r];
+                rlen = P.row_ptr[r + 1] - rb;
+            }
+        }
+        if (ci >= ce) break;
+        const int j = P.col[rb + (f - base)];
+        for (int c = P.col_ptr[j] + lane; c < P.col_ptr[j + 1]; c += 32) {
+            const int k = P.row_idx[c];
+            const double g = P.grow[k].x;
+            if (!isfinite(g)) continue;
+            const double v = __dsub_rn(L[k], g);
+            if (!(v > 0.0)) continue;
+            ls_slot(P, lb, ub, x, w, L, j, P.col_val[c], v, T, S, perm[c]);
+        }
+    }
+}
+
+// the best cached candidate (larger score; ties: smaller variable, then smaller value), one key
+// per block, and the count of violated rows
+__global__ void __launch_bounds__(kLsThreads) k_ls_select(DevProblem P, const double* __restrict__ L,
+                                                          const double* __restrict__ T, const double* __restrict__ S,
+                                                          LsKey* __restrict__ part, LsCtl* ctl) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    LsKey best = ls_none();
+    int nviol = 0;
+    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < P.m; k += (gridDim.x * blockDim.x) >> 5) {
+        const double g = P.grow[k].x;
+        if (!isfinite(g)) continue;
+        if (!(__dsub_rn(L[k], g) > 0.0)) continue;
+        ++nviol;
+        for (int q = P.row_ptr[k] + lane; q < P.row_ptr[k + 1]; q += 32) {
+            const double sc = S[q];
+            if (sc == -INFINITY) continue;
+            const LsKey key{sc, T[q], P.col[q], 0};
+            if (ls_before(key, best)) best = key;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const LsKey other = ls_shfl(best, lane ^ o);
+        if (ls_before(other, best)) best = other;
+    }
+    __shared__ LsKey wk[kLsThreads / 32];
+    __shared__ int wn[kLsThreads / 32];
+    if (lane == 0) {
+        wk[wid] = best;
+        wn[wid] = nviol;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        LsKey b = wk[0];
+        int nv = wn[0];
+        for (int i = 1; i < kLsThreads / 32; ++i) {
+            if (ls_before(wk[i], b)) b = wk[i];
+            nv += wn[i];
+        }
+        part[blockIdx.x] = b;
+        if (nv) atomicAdd(&ctl->nviol, nv);
+    }
+}
+
 __global__ void k_ls_bump(DevProblem P, const double* __restrict__ L, double* __restrict__ w, const LsCtl* ctl) {
     if (!ctl->bump) return;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < P.m; k += gridDim.x * blockDim.x) {
@@ -496,11 +650,18 @@ template <bool OBJ>
 static int ls_run(mip_problem* p, const double* lb, const double* ub, double* x, double* w, double* x_best,
                   int iterations, double w0, LsOut* out, cudaStream_t s) {
     void *pL = nullptr, *pPart = nullptr, *pCtl = nullptr, *pSum = nullptr, *pOut = nullptr;
-    // the scoring pass on every resident block (its per-block bests are reduced by k_ls_apply)
-    static int occ_score[2] = {-1, -1}, occ_lift = -1;
+    void *pS = nullptr, *pT = nullptr, *pPerm = nullptr;
+    // the scoring passes on every resident block (their per-block bests are reduced by
+    // k_ls_apply): k_ls_score with the objective moves, else the cache's full pass and selection
+    static int occ_score[2] = {-1, -1}, occ_lift = -1, occ_select = -1;
     if (occ_score[OBJ] < 0) {
-        cudaError_t oe =
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_score[OBJ], k_ls_score<OBJ>, kLsThreads, 0);
+        cudaError_t oe = OBJ ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_score[OBJ], k_ls_score<OBJ>,
+                                                                             kLsThreads, 0)
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_score[OBJ], k_ls_full, kLsThreads, 0);
+        if (oe != cudaSuccess) return fail_cuda(oe, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    }
+    if (!OBJ && occ_select < 0) {
+        cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_select, k_ls_select, kLsThreads, 0);
         if (oe != cudaSuccess) return fail_cuda(oe, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     }
     if (OBJ && occ_lift < 0) {
@@ -509,12 +670,24 @@ static int ls_run(mip_problem* p, const double* lb, const double* ub, double* x,
     }
     const int grid_score = p->sms * (occ_score[OBJ] > 0 ? occ_score[OBJ] : 1);
     const int grid_lift = p->sms * (occ_lift > 0 ? occ_lift : 1);
-    const int nparts = grid_score > grid_lift ? grid_score : grid_lift;
+    const int grid_select = p->sms * (occ_select > 0 ? occ_select : 1);
+    int nparts = grid_score > grid_lift ? grid_score : grid_lift;
+    nparts = nparts > grid_select ? nparts : grid_select;
     auto release = [&]() {
-        for (void* q : {pL, pPart, pCtl, pSum, pOut})
+        for (void* q : {pL, pPart, pCtl, pSum, pOut, pS, pT, pPerm})
             if (q) cudaFreeAsync(q, s);
     };
     cudaError_t e = cudaSuccess;
+    const size_t nz = (size_t)(p->nnz ? p->nnz : 1);
+    if (!OBJ && ((e = cudaMallocAsync(&pS, sizeof(double) * nz, s)) != cudaSuccess ||
+                 (e = cudaMallocAsync(&pT, sizeof(double) * nz, s)) != cudaSuccess ||
+                 (e = cudaMallocAsync(&pPerm, sizeof(int) * nz, s)) != cudaSuccess)) {
+        release();
+        return fail_cuda(e, "cudaMallocAsync");
+    }
+    double* S = static_cast<double*>(pS);
+    double* T = static_cast<double*>(pT);
+    int* perm = static_cast<int*>(pPerm);
     if ((e = cudaMallocAsync(&pL, sizeof(double) * (size_t)(p->m ? p->m : 1), s)) != cudaSuccess ||
         (e = cudaMallocAsync(&pPart, sizeof(LsKey) * (size_t)nparts, s)) != cudaSuccess ||
         (e = cudaMallocAsync(&pCtl, sizeof(LsCtl), s)) != cudaSuccess ||
@@ -539,14 +712,24 @@ static int ls_run(mip_problem* p, const double* lb, const double* ub, double* x,
         k_lso_cost_flags<<<grid_rows, kLsThreads, 0, s>>>(p->dp, cost, ctl);
         k_lso_init<<<1, 1, 0, s>>>(ctl, w0);
     }
+    if (!OBJ && iterations > 0) {
+        k_ls_perm<<<grid_rows, kLsThreads, 0, s>>>(p->dp, perm);
+        k_ls_full<<<grid_score, kLsThreads, 0, s>>>(p->dp, lb, ub, x, w, L, T, S, ctl, 1);
+    }
     for (int it = 0; it < iterations; ++it) {
         if (OBJ) {
             k_lso_lift<<<grid_lift, kLsThreads, 0, s>>>(p->dp, lb, ub, x, L, cost, x_best, part, ctl);
             k_lso_lift_apply<<<1, kLsThreads, 0, s>>>(p->dp, x, L, part, grid_lift, ctl, cost);
+            k_ls_score<OBJ><<<grid_score, kLsThreads, 0, s>>>(p->dp, lb, ub, x, w, L, part, ctl, cost);
+            k_ls_apply<OBJ><<<1, kLsThreads, 0, s>>>(p->dp, x, L, part, grid_score, ctl, cost);
+            k_ls_bump<<<grid_rows, kLsThreads, 0, s>>>(p->dp, L, w, ctl);
+        } else {
+            k_ls_select<<<grid_select, kLsThreads, 0, s>>>(p->dp, L, T, S, part, ctl);
+            k_ls_apply<OBJ><<<1, kLsThreads, 0, s>>>(p->dp, x, L, part, grid_select, ctl, cost);
+            k_ls_bump<<<grid_rows, kLsThreads, 0, s>>>(p->dp, L, w, ctl);
+            k_ls_full<<<grid_score, kLsThreads, 0, s>>>(p->dp, lb, ub, x, w, L, T, S, ctl, 0);
+            k_ls_neighbors<<<2 * p->sms, kLsThreads, 0, s>>>(p->dp, lb, ub, x, w, L, perm, T, S, ctl);
         }
-        k_ls_score<OBJ><<<grid_score, kLsThreads, 0, s>>>(p->dp, lb, ub, x, w, L, part, ctl, cost);
-        k_ls_apply<OBJ><<<1, kLsThreads, 0, s>>>(p->dp, x, L, part, grid_score, ctl, cost);
-        k_ls_bump<<<grid_rows, kLsThreads, 0, s>>>(p->dp, L, w, ctl);
     }
     k_ls_summary<<<kLsRedBlocks, kLsThreads, 0, s>>>(p->dp, cost, x, w, L, sum);
     k_ls_summary_finish<<<1, 32, 0, s>>>(sum, kLsRedBlocks, dout);
