@@ -2,26 +2,33 @@
 // core under a weighted violation F = sum_k w_k max(0, (A x)_k - g_k), and its objective moves
 // (Local-MIP's lift and breakthrough moves under a weighted objective row).
 //
-// Per iteration, every candidate and its full score are recomputed (as the paper does, instead
-// of the score deltas of the original Feasibility Jump):
-//   k_ls_score   a warp per violated row: each lane takes nonzeros of the row, forms the value
-//                that alone satisfies the row (integers by the smallest integer step, clamped to
-//                the bounds) and scores it by walking the variable's column (rows ascending);
-//                with the objective moves, a thread per variable with a cost also forms the
-//                objective row's tight value (breakthrough) while that row is violated, and every
-//                score adds the objective row's weighted drop; warp and block reductions keep the
-//                best (largest score; ties: smallest variable, smallest value, then a mixed tight
-//                move before a breakthrough move), one per block;
-//   k_ls_apply   one block: the best over the blocks (a total order, so the result does not
-//                depend on the reduction's order); a positive score moves the variable and
-//                updates the activities of its column, otherwise the weights are to grow;
-//   k_ls_bump    every violated row's weight grows by 1 when no move improved.
-// With the objective moves, each iteration starts with
+// A candidate is, for a violated row and a variable in it, the value that alone satisfies the
+// row (integers by the smallest integer step, clamped to the bounds), scored by the drop of F
+// over the variable's column (rows ascending); the best (largest score; ties: smallest variable,
+// smallest value, then a mixed tight move before a breakthrough move) moves when its score is
+// positive, otherwise every violated row's weight grows by 1.
+//
+// local_search_mtm keeps every candidate's score in a slot per nonzero and, after a move,
+// recomputes only the moved variable's distance-2 neighbourhood (the paper's neighbour lists,
+// found on the fly), all of it after a weight bump; the iterations run in one persistent
+// cooperative launch (k_ls_loop: selection, the move by block 0, the neighbourhood update,
+// separated by grid barriers).
+//
+// local_search_objective recomputes every score each iteration (D = c x - c x* enters every
+// score), five launches per iteration:
 //   k_lso_lift        at a point with no violated row: the point is copied out when it becomes
 //                     the incumbent, and a thread per variable with a cost forms its lift move
 //                     (as far against the cost's sign as every row of its column allows);
-//   k_lso_lift_apply  one block: records the incumbent (D = c x - c x* restarts at 0) and applies
-//                     the best lift move when its gain is positive, which ends the iteration.
+//   k_lso_lift_apply  one block: records the incumbent (D restarts at 0) and applies the best
+//                     lift move when its gain is positive, which ends the iteration;
+//   k_ls_score        a warp per violated row, lanes over its nonzeros, each candidate scored by
+//                     a walk of its column; a thread per costed variable adds the objective
+//                     row's tight values (breakthrough) while that row is violated; every score
+//                     adds the objective row's weighted drop; one best key per block;
+//   k_ls_apply        one block: the best over the blocks (a total order, so the result does
+//                     not depend on the reduction's order); the move and its column's activity
+//                     updates, or the weights are to grow (w0 when no row is violated);
+//   k_ls_bump         every violated row's weight grows by 1.
 // Everything stays on the device (no host read per iteration).  The activities start from a
 // thread-per-row sum in row order and are updated in the order of the moves, so the search is
 // bit-for-bit that of a sequential implementation with the same operation order.
@@ -33,6 +40,7 @@
 namespace gpubp {
 
 constexpr int kLsThreads = 256;
+constexpr int kLsLongRow = 256;   // longer rows are scanned by the whole grid, not one thread or warp
 constexpr int kLsRedBlocks = 304;
 
 struct LsKey {
@@ -66,6 +74,10 @@ struct LsCtl {
     int bump;         // the weights grow in this iteration
     int moves, bumps;
     int moved_j;      // the variable this iteration moved, -1 if none
+    unsigned bar_count;   // arrivals at the persistent search's grid barriers
+    int error;            // a barrier wait gave up
+    int nbr_count;        // rows of the moved variable's column
+    int nbr_total;        // their entries, in one flat sequence
     // objective moves
     int nv;           // violated rows of the current point (kept through every move)
     int has_best;     // an incumbent exists
@@ -122,8 +134,18 @@ __device__ __forceinline__ double ls_tight(double xj, double a, double v, bool i
     return __dsub_rn(xj, __ddiv_rn(v, a));
 }
 
+// loads of the data that moves during a search (activities, weights, points, cached slots):
+// through L2 (CG) inside the persistent search, where other blocks wrote it since the last
+// barrier; plain loads between launches
+template <bool CG, typename Tp>
+__device__ __forceinline__ Tp ls_ld(const Tp* p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
 // the drop of the weighted row violation if x_j alone moves by dx: the column's rows in order,
 // the loads of four entries issued together
+template <bool CG = false>
 __device__ __forceinline__ double ls_column_score(const DevProblem& P, const double* __restrict__ w,
                                                   const double* __restrict__ L, int j, double dx) {
     double s = 0.0;
@@ -137,8 +159,8 @@ __device__ __forceinline__ double ls_column_score(const DevProblem& P, const dou
         for (int i = 0; i < 4; ++i) {
             const int r = rr[i] >= 0 ? rr[i] : 0;
             gg[i] = P.grow[r].x;
-            ll[i] = L[r];
-            ww[i] = w[r];
+            ll[i] = ls_ld<CG>(L + r);
+            ww[i] = ls_ld<CG>(w + r);
             aa[i] = c0 + i < ce ? P.col_val[c0 + i] : 0.0;
         }
 #pragma unroll
@@ -244,15 +266,15 @@ __global__ void __launch_bounds__(kLsThreads) k_ls_score(DevProblem P, const dou
 
 // one block moves x_j to t: the activities of its column, then x_j (and, with the objective
 // moves, D and the count of violated rows)
-template <bool OBJ>
+template <bool OBJ, bool CG = false, int NT = kLsThreads>
 __device__ void ls_move(const DevProblem& P, double* __restrict__ x, double* __restrict__ L, int j, double t,
                         LsCtl* ctl, const double* __restrict__ cost) {
-    __shared__ int sdv[kLsThreads / 32];
-    const double dx = __dsub_rn(t, x[j]);
+    __shared__ int sdv[NT / 32];
+    const double dx = __dsub_rn(t, ls_ld<CG>(x + j));
     int dv = 0;
-    for (int c = P.col_ptr[j] + threadIdx.x; c < P.col_ptr[j + 1]; c += kLsThreads) {
+    for (int c = P.col_ptr[j] + threadIdx.x; c < P.col_ptr[j + 1]; c += NT) {
         const int r = P.row_idx[c];
-        const double old = L[r];
+        const double old = ls_ld<CG>(L + r);
         const double nw = __dadd_rn(old, __dmul_rn(P.col_val[c], dx));
         L[r] = nw;
         if constexpr (OBJ) {
@@ -268,7 +290,7 @@ __device__ void ls_move(const DevProblem& P, double* __restrict__ x, double* __r
     if (threadIdx.x == 0) {
         if constexpr (OBJ) {
             int tot = 0;
-            for (int i = 0; i < kLsThreads / 32; ++i) tot += sdv[i];
+            for (int i = 0; i < NT / 32; ++i) tot += sdv[i];
             ctl->nv += tot;
             ctl->D = __dadd_rn(ctl->D, __dmul_rn(cost[j], dx));
         }
@@ -445,9 +467,9 @@ __global__ void k_lso_init(LsCtl* ctl, double w0) {
 // T[q] and score S[q] (-inf: no candidate).  A slot depends on row k's activity, on x_j and on
 // the activities and weights of the rows of column j.  A move of x_j* changes x_j* and the
 // activities of the rows of column j* only, so the slots that change are those (k, j) with j
-// in a row of column j* (the distance-2 neighbourhood of j*): k_ls_neighbors recomputes exactly
-// those, with the same function, so every score equals a full recomputation bit for bit.  A
-// weight bump changes every slot: k_ls_full recomputes them all.
+// in a row of column j* (the distance-2 neighbourhood of j*): the persistent search recomputes
+// exactly those, with the same function, so every score equals a full recomputation bit for
+// bit.  A weight bump changes every slot: all are recomputed.
 
 // CSC entry -> CSR position: each nonzero finds its row in its column's ascending row list
 __global__ void k_ls_perm(DevProblem P, int* __restrict__ perm) {
@@ -467,11 +489,12 @@ __global__ void k_ls_perm(DevProblem P, int* __restrict__ perm) {
 }
 
 // the slot of row k (violation v > 0) on variable j with coefficient a
+template <bool CG = false>
 __device__ __forceinline__ void ls_slot(const DevProblem& P, const double* __restrict__ lb,
                                         const double* __restrict__ ub, const double* __restrict__ x,
                                         const double* __restrict__ w, const double* __restrict__ L, int j, double a,
                                         double v, double* __restrict__ T, double* __restrict__ S, int q) {
-    const double xj = x[j];
+    const double xj = ls_ld<CG>(x + j);
     double t = ls_tight(xj, a, v, P.is_int[j] != 0);
     t = t < lb[j] ? lb[j] : t;
     t = t > ub[j] ? ub[j] : t;
@@ -479,114 +502,315 @@ __device__ __forceinline__ void ls_slot(const DevProblem& P, const double* __res
         S[q] = -INFINITY;
         return;
     }
-    S[q] = ls_column_score(P, w, L, j, __dsub_rn(t, xj));
+    S[q] = ls_column_score<CG>(P, w, L, j, __dsub_rn(t, xj));
     T[q] = t;
 }
 
-// every slot of every violated row (at the start, and after a weight bump)
+// the rows longer than kLsLongRow (their order does not matter: every reduction over them is
+// under a total order)
+__global__ void k_ls_long_rows(DevProblem P, int* __restrict__ list, int* __restrict__ count) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < P.m; k += gridDim.x * blockDim.x)
+        if (P.row_ptr[k + 1] - P.row_ptr[k] > kLsLongRow) list[atomicAdd(count, 1)] = k;
+}
+
+// every slot of every violated row (at the start; after a weight bump the persistent search
+// does the same): a warp per row, and the long rows' slots over the whole grid
 __global__ void __launch_bounds__(kLsThreads) k_ls_full(DevProblem P, const double* __restrict__ lb,
                                                         const double* __restrict__ ub, const double* __restrict__ x,
                                                         const double* __restrict__ w, const double* __restrict__ L,
                                                         double* __restrict__ T, double* __restrict__ S,
-                                                        const LsCtl* ctl, int force) {
-    if (!force && !ctl->bump) return;
+                                                        const int* __restrict__ long_list,
+                                                        const int* __restrict__ long_count) {
     const int lane = threadIdx.x & 31;
     for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < P.m; k += (gridDim.x * blockDim.x) >> 5) {
         const double g = P.grow[k].x;
         if (!isfinite(g)) continue;
         const double v = __dsub_rn(L[k], g);
         if (!(v > 0.0)) continue;
-        for (int q = P.row_ptr[k] + lane; q < P.row_ptr[k + 1]; q += 32)
+        const int qb = P.row_ptr[k], qe = P.row_ptr[k + 1];
+        if (qe - qb > kLsLongRow) continue;
+        for (int q = qb + lane; q < qe; q += 32) ls_slot(P, lb, ub, x, w, L, P.col[q], P.val[q], v, T, S, q);
+    }
+    const int nl = *long_count;
+    for (int i = 0; i < nl; ++i) {
+        const int k = long_list[i];
+        const double g = P.grow[k].x;
+        if (!isfinite(g)) continue;
+        const double v = __dsub_rn(L[k], g);
+        if (!(v > 0.0)) continue;
+        for (int q = P.row_ptr[k] + blockIdx.x * blockDim.x + threadIdx.x; q < P.row_ptr[k + 1];
+             q += gridDim.x * blockDim.x)
             ls_slot(P, lb, ub, x, w, L, P.col[q], P.val[q], v, T, S, q);
     }
 }
 
-// after a move of x_j*: the slots (k, j) of the violated rows k of every j in a row of column
-// j*: the entries of the rows of column j*, taken in one flat sequence, are spread over the
-// grid's warps (a long row spreads over the whole grid, short rows run side by side), each
-// warp's lanes over the variable's column (a slot reached through several rows is written with
-// the same value)
-__global__ void __launch_bounds__(kLsThreads) k_ls_neighbors(DevProblem P, const double* __restrict__ lb,
-                                                             const double* __restrict__ ub,
-                                                             const double* __restrict__ x,
-                                                             const double* __restrict__ w,
-                                                             const double* __restrict__ L,
-                                                             const int* __restrict__ perm, double* __restrict__ T,
-                                                             double* __restrict__ S, const LsCtl* ctl) {
-    const int js = ctl->moved_j;
-    if (js < 0) return;
-    const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-    const int ce = P.col_ptr[js + 1];
-    int ci = P.col_ptr[js], base = 0;   // the row of column j* holding flat entry f starts at base
-    int rb = 0, rlen = 0;
-    if (ci < ce) {
-        const int r = P.row_idx[ci];
-        rb = P.row_ptr[r];
-        rlen = P.row_ptr[r + 1] - rb;
-    }
-    for (int f = gw;; f += nw) {
-        while (ci < ce && f >= base + rlen) {
-            base += rlen;
-            if (++ci < ce) {
-                const int r = P.row_idx[ci];
-                rb = P.row_ptr[r];
-                rlen = P.row_ptr[r + 1] - rb;
-            }
-        }
-        if (ci >= ce) break;
-        const int j = P.col[rb + (f - base)];
-        for (int c = P.col_ptr[j] + lane; c < P.col_ptr[j + 1]; c += 32) {
-            const int k = P.row_idx[c];
-            const double g = P.grow[k].x;
-            if (!isfinite(g)) continue;
-            const double v = __dsub_rn(L[k], g);
-            if (!(v > 0.0)) continue;
-            ls_slot(P, lb, ub, x, w, L, j, P.col_val[c], v, T, S, perm[c]);
-        }
-    }
-}
+// ---- the whole mixed-tight-move search in one persistent cooperative launch ----
+//
+// One block per SM: the three grid barriers of an iteration cost less with fewer arrivals on
+// their counter (knapsack/cover, 1M nonzeros, 256-thread blocks: 0.049 ms per iteration with
+// 152 blocks, 0.053 with 304, 0.088 with every resident block; 0.062 as five launches per
+// iteration; 1,024-thread blocks: 0.089).
+// Per iteration: selection over the cached slots (a thread per row, so a warp checks 32 rows
+// at once and each violated row's slots are read by its own thread), a grid barrier, the move
+// or the bump decision by block 0, a grid barrier, then the neighbourhood update: the entries
+// of the rows of column j*, taken as one flat sequence, spread over the grid's warps (a dense
+// row spreads over the whole grid, short rows run side by side), each warp's lanes over the
+// variable's column (a slot reached through several rows is written with the same value); or,
+// after a bump, the weights, a barrier and the full recomputation; a grid barrier.  Every load
+// of moving data goes through L2.
 
-// the best cached candidate (larger score; ties: smaller variable, then smaller value), one key
-// per block, and the count of violated rows
-__global__ void __launch_bounds__(kLsThreads) k_ls_select(DevProblem P, const double* __restrict__ L,
-                                                          const double* __restrict__ T, const double* __restrict__ S,
-                                                          LsKey* __restrict__ part, LsCtl* ctl) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    LsKey best = ls_none();
-    int nviol = 0;
-    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < P.m; k += (gridDim.x * blockDim.x) >> 5) {
-        const double g = P.grow[k].x;
-        if (!isfinite(g)) continue;
-        if (!(__dsub_rn(L[k], g) > 0.0)) continue;
-        ++nviol;
-        for (int q = P.row_ptr[k] + lane; q < P.row_ptr[k + 1]; q += 32) {
-            const double sc = S[q];
-            if (sc == -INFINITY) continue;
-            const LsKey key{sc, T[q], P.col[q], 0};
-            if (ls_before(key, best)) best = key;
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        const LsKey other = ls_shfl(best, lane ^ o);
-        if (ls_before(other, best)) best = other;
-    }
-    __shared__ LsKey wk[kLsThreads / 32];
-    __shared__ int wn[kLsThreads / 32];
-    if (lane == 0) {
-        wk[wid] = best;
-        wn[wid] = nviol;
-    }
+constexpr long long kLsSpinLimit = 4000000000LL;   // clock64 cycles (about 2 s) per barrier wait
+
+// every block arrives once on a count that only grows; the wait is a bounded spin of acquire
+// loads (a timeout sets the error word, and every block leaves the search at its next check)
+__device__ __forceinline__ bool ls_grid_sync(LsCtl* ctl, unsigned& bar_k) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        LsKey b = wk[0];
-        int nv = wn[0];
-        for (int i = 1; i < kLsThreads / 32; ++i) {
-            if (ls_before(wk[i], b)) b = wk[i];
-            nv += wn[i];
+        atom_add_acqrel_u32(&ctl->bar_count, 1u);
+        const unsigned target = gridDim.x * (bar_k + 1u);
+        const long long t0 = clock64();
+        while (ld_acquire_u32(&ctl->bar_count) < target) {
+            if (clock64() - t0 > kLsSpinLimit) {
+                atomicExch(&ctl->error, 1);
+                break;
+            }
         }
-        part[blockIdx.x] = b;
-        if (nv) atomicAdd(&ctl->nviol, nv);
+    }
+    bar_k += 1u;
+    __syncthreads();
+    return __ldcg(&ctl->error) == 0;
+}
+
+constexpr int kLsLoopThreads = 256;
+constexpr int kLsNbrStaged = 1024;   // rows of the moved column staged in shared memory
+
+__global__ void __launch_bounds__(kLsLoopThreads) k_ls_loop(DevProblem P, const double* __restrict__ lb,
+                                                        const double* __restrict__ ub, double* __restrict__ x,
+                                                        double* __restrict__ w, double* __restrict__ L,
+                                                        double* __restrict__ T, double* __restrict__ S,
+                                                        const int* __restrict__ perm, LsKey* __restrict__ part,
+                                                        int* __restrict__ nbr_row, int* __restrict__ nbr_start,
+                                                        const int* __restrict__ long_list,
+                                                        const int* __restrict__ long_count, LsCtl* ctl,
+                                                        int iterations) {
+    __shared__ int s_row[kLsNbrStaged], s_start[kLsNbrStaged];
+    __shared__ int s_wsum[kLsLoopThreads / 32];
+    __shared__ int s_carry;
+    __shared__ LsKey wk[kLsLoopThreads / 32];
+    __shared__ int wn[kLsLoopThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+    const int gw = tid >> 5, nw = nthr >> 5;
+    const int nlong = *long_count;
+    unsigned bar_k = 0;
+    for (int it = 0; it < iterations; ++it) {
+        // selection: the best cached key of the violated rows
+        LsKey best = ls_none();
+        int nviol = 0;
+        for (int k = tid; k < P.m; k += nthr) {
+            const double g = P.grow[k].x;
+            if (!isfinite(g) || !(__dsub_rn(L[k], g) > 0.0)) continue;
+            ++nviol;
+            const int qb = P.row_ptr[k], qe = P.row_ptr[k + 1];
+            if (qe - qb > kLsLongRow) continue;   // scanned below by the whole grid
+            for (int q0 = qb; q0 < qe; q0 += 4) {
+                double sc[4], tt[4];
+                int jj[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int q = q0 + i < qe ? q0 + i : q0;
+                    sc[i] = S[q];
+                    tt[i] = T[q];
+                    jj[i] = P.col[q];
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (q0 + i >= qe || sc[i] == -INFINITY) continue;
+                    const LsKey key{sc[i], tt[i], jj[i], 0};
+                    if (ls_before(key, best)) best = key;
+                }
+            }
+        }
+        for (int i = 0; i < nlong; ++i) {
+            const int k = long_list[i];
+            const double g = P.grow[k].x;
+            if (!isfinite(g) || !(__dsub_rn(L[k], g) > 0.0)) continue;
+            for (int q = P.row_ptr[k] + tid; q < P.row_ptr[k + 1]; q += nthr) {
+                const double sc = S[q];
+                if (sc == -INFINITY) continue;
+                const LsKey key{sc, T[q], P.col[q], 0};
+                if (ls_before(key, best)) best = key;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const LsKey other = ls_shfl(best, lane ^ o);
+            if (ls_before(other, best)) best = other;
+        }
+        nviol = __reduce_add_sync(0xffffffffu, nviol);
+        if (lane == 0) {
+            wk[wid] = best;
+            wn[wid] = nviol;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            LsKey b = wk[0];
+            int nv = wn[0];
+            for (int i = 1; i < kLsLoopThreads / 32; ++i) {
+                if (ls_before(wk[i], b)) b = wk[i];
+                nv += wn[i];
+            }
+            part[blockIdx.x] = b;
+            if (nv) atomicAdd(&ctl->nviol, nv);
+        }
+        if (!ls_grid_sync(ctl, bar_k)) return;
+        // block 0: the best over the blocks; the move, or the bump decision
+        if (blockIdx.x == 0) {
+            __shared__ LsKey sk[kLsLoopThreads];
+            LsKey b = ls_none();
+            for (int i = threadIdx.x; i < (int)gridDim.x; i += kLsLoopThreads) {
+                const LsKey pk{__ldcg(&part[i].score), __ldcg(&part[i].t), __ldcg(&part[i].j), 0};
+                if (ls_before(pk, b)) b = pk;
+            }
+            sk[threadIdx.x] = b;
+            __syncthreads();
+            for (int o = kLsLoopThreads / 2; o > 0; o >>= 1) {
+                if (threadIdx.x < o && ls_before(sk[threadIdx.x + o], sk[threadIdx.x]))
+                    sk[threadIdx.x] = sk[threadIdx.x + o];
+                __syncthreads();
+            }
+            const LsKey bb = sk[0];
+            const int nv = __ldcg(&ctl->nviol);
+            __syncthreads();
+            if (bb.j != INT_MAX && bb.score > 0.0) {
+                ls_move<false, false, kLsLoopThreads>(P, x, L, bb.j, bb.t, ctl, nullptr);
+                // the rows of column j* and the starts of their entries in one flat sequence
+                // (a block-wide exclusive scan of the row lengths)
+                const int cb = P.col_ptr[bb.j], cn = P.col_ptr[bb.j + 1] - cb;
+                if (threadIdx.x == 0) s_carry = 0;
+                __syncthreads();
+                for (int base = 0; base < cn; base += kLsLoopThreads) {
+                    const int i = base + threadIdx.x;
+                    int r = 0, len = 0;
+                    if (i < cn) {
+                        r = P.row_idx[cb + i];
+                        len = P.row_ptr[r + 1] - P.row_ptr[r];
+                    }
+                    int v = len;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int u = __shfl_up_sync(0xffffffffu, v, o);
+                        if (lane >= o) v += u;
+                    }
+                    if (lane == 31) s_wsum[wid] = v;
+                    __syncthreads();
+                    if (wid == 0) {
+                        int ws = lane < kLsLoopThreads / 32 ? s_wsum[lane] : 0;
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int u = __shfl_up_sync(0xffffffffu, ws, o);
+                            if (lane >= o) ws += u;
+                        }
+                        if (lane < kLsLoopThreads / 32) s_wsum[lane] = ws;
+                    }
+                    __syncthreads();
+                    if (i < cn) {
+                        nbr_row[i] = r;
+                        nbr_start[i] = s_carry + (wid ? s_wsum[wid - 1] : 0) + v - len;
+                    }
+                    __syncthreads();
+                    if (threadIdx.x == 0) s_carry += s_wsum[kLsLoopThreads / 32 - 1];
+                    __syncthreads();
+                }
+                if (threadIdx.x == 0) {
+                    ctl->bump = 0;
+                    ctl->moved_j = bb.j;
+                    ctl->nbr_count = cn;
+                    ctl->nbr_total = s_carry;
+                }
+            } else if (threadIdx.x == 0) {
+                ctl->moved_j = -1;
+                ctl->bump = nv > 0 ? 1 : 0;
+                if (nv > 0) ctl->bumps += 1;
+            }
+            if (threadIdx.x == 0) ctl->nviol = 0;
+        }
+        if (!ls_grid_sync(ctl, bar_k)) return;
+        const int bump = __ldcg(&ctl->bump), js = __ldcg(&ctl->moved_j);
+        if (bump) {
+            for (int k = tid; k < P.m; k += nthr) {
+                const double g = P.grow[k].x;
+                if (isfinite(g) && __dsub_rn(L[k], g) > 0.0) w[k] = __dadd_rn(w[k], 1.0);
+            }
+            if (!ls_grid_sync(ctl, bar_k)) return;
+            for (int k = gw; k < P.m; k += nw) {
+                const double g = P.grow[k].x;
+                if (!isfinite(g)) continue;
+                const double v = __dsub_rn(L[k], g);
+                if (!(v > 0.0)) continue;
+                const int qb = P.row_ptr[k], qe = P.row_ptr[k + 1];
+                if (qe - qb > kLsLongRow) continue;
+                for (int q = qb + lane; q < qe; q += 32)
+                    ls_slot<false>(P, lb, ub, x, w, L, P.col[q], P.val[q], v, T, S, q);
+            }
+            for (int i = 0; i < nlong; ++i) {
+                const int k = long_list[i];
+                const double g = P.grow[k].x;
+                if (!isfinite(g)) continue;
+                const double v = __dsub_rn(L[k], g);
+                if (!(v > 0.0)) continue;
+                for (int q = P.row_ptr[k] + tid; q < P.row_ptr[k + 1]; q += nthr)
+                    ls_slot<false>(P, lb, ub, x, w, L, P.col[q], P.val[q], v, T, S, q);
+            }
+        } else if (js >= 0) {
+            const int cn = __ldcg(&ctl->nbr_count), E = __ldcg(&ctl->nbr_total);
+            const bool staged = cn <= kLsNbrStaged;
+            if (staged)
+                for (int i = threadIdx.x; i < cn; i += kLsLoopThreads) {
+                    s_row[i] = __ldcg(nbr_row + i);
+                    s_start[i] = __ldcg(nbr_start + i);
+                }
+            __syncthreads();
+            // flat entry f -> its row (the last with start <= f; empty rows are passed over)
+            // and the variable there
+            auto entry_var = [&](int f) -> int {
+                int lo = 0, hi = cn - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    const int st = staged ? s_start[mid] : __ldcg(nbr_start + mid);
+                    if (st <= f) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int r = staged ? s_row[lo] : __ldcg(nbr_row + lo);
+                const int st = staged ? s_start[lo] : __ldcg(nbr_start + lo);
+                return P.col[P.row_ptr[r] + (f - st)];
+            };
+            if (E <= 8 * nw) {
+                // a warp per entry, its lanes over the variable's column
+                for (int f = gw; f < E; f += nw) {
+                    const int j = entry_var(f);
+                    for (int c = P.col_ptr[j] + lane; c < P.col_ptr[j + 1]; c += 32) {
+                        const int k = P.row_idx[c];
+                        const double g = P.grow[k].x;
+                        if (!isfinite(g)) continue;
+                        const double v = __dsub_rn(L[k], g);
+                        if (!(v > 0.0)) continue;
+                        ls_slot<false>(P, lb, ub, x, w, L, j, P.col_val[c], v, T, S, perm[c]);
+                    }
+                }
+            } else {
+                // many entries (a dense row in the column): a thread per entry, its column in turn
+                for (int f = tid; f < E; f += nthr) {
+                    const int j = entry_var(f);
+                    for (int c = P.col_ptr[j]; c < P.col_ptr[j + 1]; ++c) {
+                        const int k = P.row_idx[c];
+                        const double g = P.grow[k].x;
+                        if (!isfinite(g)) continue;
+                        const double v = __dsub_rn(L[k], g);
+                        if (!(v > 0.0)) continue;
+                        ls_slot<false>(P, lb, ub, x, w, L, j, P.col_val[c], v, T, S, perm[c]);
+                    }
+                }
+            }
+        }
+        if (!ls_grid_sync(ctl, bar_k)) return;
     }
 }
 
@@ -650,44 +874,47 @@ template <bool OBJ>
 static int ls_run(mip_problem* p, const double* lb, const double* ub, double* x, double* w, double* x_best,
                   int iterations, double w0, LsOut* out, cudaStream_t s) {
     void *pL = nullptr, *pPart = nullptr, *pCtl = nullptr, *pSum = nullptr, *pOut = nullptr;
-    void *pS = nullptr, *pT = nullptr, *pPerm = nullptr;
+    void *pS = nullptr, *pT = nullptr, *pPerm = nullptr, *pNbr = nullptr, *pLong = nullptr;
     // the scoring passes on every resident block (their per-block bests are reduced by
-    // k_ls_apply): k_ls_score with the objective moves, else the cache's full pass and selection
-    static int occ_score[2] = {-1, -1}, occ_lift = -1, occ_select = -1;
+    // k_ls_apply): k_ls_score with the objective moves, else the cache's first full pass
+    static int occ_score[2] = {-1, -1}, occ_lift = -1;
     if (occ_score[OBJ] < 0) {
         cudaError_t oe = OBJ ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_score[OBJ], k_ls_score<OBJ>,
                                                                              kLsThreads, 0)
                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_score[OBJ], k_ls_full, kLsThreads, 0);
         if (oe != cudaSuccess) return fail_cuda(oe, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     }
-    if (!OBJ && occ_select < 0) {
-        cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_select, k_ls_select, kLsThreads, 0);
-        if (oe != cudaSuccess) return fail_cuda(oe, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-    }
+
     if (OBJ && occ_lift < 0) {
         cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_lift, k_lso_lift, kLsThreads, 0);
         if (oe != cudaSuccess) return fail_cuda(oe, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     }
     const int grid_score = p->sms * (occ_score[OBJ] > 0 ? occ_score[OBJ] : 1);
     const int grid_lift = p->sms * (occ_lift > 0 ? occ_lift : 1);
-    const int grid_select = p->sms * (occ_select > 0 ? occ_select : 1);
+    const int grid_select = p->sms;   // the persistent search: one block per SM
     int nparts = grid_score > grid_lift ? grid_score : grid_lift;
     nparts = nparts > grid_select ? nparts : grid_select;
     auto release = [&]() {
-        for (void* q : {pL, pPart, pCtl, pSum, pOut, pS, pT, pPerm})
+        for (void* q : {pL, pPart, pCtl, pSum, pOut, pS, pT, pPerm, pNbr, pLong})
             if (q) cudaFreeAsync(q, s);
     };
     cudaError_t e = cudaSuccess;
     const size_t nz = (size_t)(p->nnz ? p->nnz : 1);
     if (!OBJ && ((e = cudaMallocAsync(&pS, sizeof(double) * nz, s)) != cudaSuccess ||
                  (e = cudaMallocAsync(&pT, sizeof(double) * nz, s)) != cudaSuccess ||
-                 (e = cudaMallocAsync(&pPerm, sizeof(int) * nz, s)) != cudaSuccess)) {
+                 (e = cudaMallocAsync(&pPerm, sizeof(int) * nz, s)) != cudaSuccess ||
+                 (e = cudaMallocAsync(&pNbr, sizeof(int) * 2 * (size_t)(p->m + 1), s)) != cudaSuccess ||
+                 (e = cudaMallocAsync(&pLong, sizeof(int) * (size_t)(p->m + 1), s)) != cudaSuccess)) {
         release();
         return fail_cuda(e, "cudaMallocAsync");
     }
     double* S = static_cast<double*>(pS);
     double* T = static_cast<double*>(pT);
     int* perm = static_cast<int*>(pPerm);
+    int* nbr_row = static_cast<int*>(pNbr);
+    int* nbr_start = nbr_row + (p->m + 1);
+    int* long_count = static_cast<int*>(pLong);   // then the list of long rows
+    int* long_list = long_count + 1;
     if ((e = cudaMallocAsync(&pL, sizeof(double) * (size_t)(p->m ? p->m : 1), s)) != cudaSuccess ||
         (e = cudaMallocAsync(&pPart, sizeof(LsKey) * (size_t)nparts, s)) != cudaSuccess ||
         (e = cudaMallocAsync(&pCtl, sizeof(LsCtl), s)) != cudaSuccess ||
@@ -714,21 +941,37 @@ static int ls_run(mip_problem* p, const double* lb, const double* ub, double* x,
     }
     if (!OBJ && iterations > 0) {
         k_ls_perm<<<grid_rows, kLsThreads, 0, s>>>(p->dp, perm);
-        k_ls_full<<<grid_score, kLsThreads, 0, s>>>(p->dp, lb, ub, x, w, L, T, S, ctl, 1);
+        if ((e = cudaMemsetAsync(long_count, 0, sizeof(int), s)) != cudaSuccess) {
+            release();
+            return fail_cuda(e, "cudaMemsetAsync");
+        }
+        k_ls_long_rows<<<grid_rows, kLsThreads, 0, s>>>(p->dp, long_list, long_count);
+        k_ls_full<<<grid_score, kLsThreads, 0, s>>>(p->dp, lb, ub, x, w, L, T, S, long_list, long_count);
     }
-    for (int it = 0; it < iterations; ++it) {
-        if (OBJ) {
+    for (int it = 0; OBJ && it < iterations; ++it) {
+        {
             k_lso_lift<<<grid_lift, kLsThreads, 0, s>>>(p->dp, lb, ub, x, L, cost, x_best, part, ctl);
             k_lso_lift_apply<<<1, kLsThreads, 0, s>>>(p->dp, x, L, part, grid_lift, ctl, cost);
             k_ls_score<OBJ><<<grid_score, kLsThreads, 0, s>>>(p->dp, lb, ub, x, w, L, part, ctl, cost);
             k_ls_apply<OBJ><<<1, kLsThreads, 0, s>>>(p->dp, x, L, part, grid_score, ctl, cost);
             k_ls_bump<<<grid_rows, kLsThreads, 0, s>>>(p->dp, L, w, ctl);
-        } else {
-            k_ls_select<<<grid_select, kLsThreads, 0, s>>>(p->dp, L, T, S, part, ctl);
-            k_ls_apply<OBJ><<<1, kLsThreads, 0, s>>>(p->dp, x, L, part, grid_select, ctl, cost);
-            k_ls_bump<<<grid_rows, kLsThreads, 0, s>>>(p->dp, L, w, ctl);
-            k_ls_full<<<grid_score, kLsThreads, 0, s>>>(p->dp, lb, ub, x, w, L, T, S, ctl, 0);
-            k_ls_neighbors<<<2 * p->sms, kLsThreads, 0, s>>>(p->dp, lb, ub, x, w, L, perm, T, S, ctl);
+        }
+    }
+    if (!OBJ && iterations > 0) {
+        // launches of at most 2^16 iterations: at most four barriers per iteration keep the
+        // arrival count (reset between launches) far from 32-bit wrap-around
+        DevProblem dp = p->dp;
+        for (int done = 0; done < iterations;) {
+            int its = iterations - done < 65536 ? iterations - done : 65536;
+            void* args[] = {&dp,   (void*)&lb, (void*)&ub, &x,        &w,         &L,   &T,  &S,
+                            &perm, &part,      &nbr_row,   &nbr_start, &long_list, &long_count, &ctl, &its};
+            if ((done > 0 && (e = cudaMemsetAsync(&ctl->bar_count, 0, sizeof(unsigned), s)) != cudaSuccess) ||
+                (e = cudaLaunchCooperativeKernel((const void*)k_ls_loop, dim3(grid_select), dim3(kLsLoopThreads), args, 0,
+                                                 s)) != cudaSuccess) {
+                release();
+                return fail_cuda(e, "local search cooperative launch");
+            }
+            done += its;
         }
     }
     k_ls_summary<<<kLsRedBlocks, kLsThreads, 0, s>>>(p->dp, cost, x, w, L, sum);
@@ -747,6 +990,10 @@ static int ls_run(mip_problem* p, const double* lb, const double* ub, double* x,
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail_cuda(e, "local search results");
     p->last_stream = s;
+    if (out->ctl.error) {
+        set_error("local search: a grid barrier wait gave up");
+        return BP_ERR_TIMEOUT;
+    }
     return BP_OK;
 }
 

@@ -206,3 +206,25 @@ def test_objective_rejects_bad_weight(pkg):
     xb = torch.zeros(p.n, dtype=torch.float64, device="cuda")
     with pytest.raises(Exception):
         prob.local_search_objective(_t(p.lb), _t(p.ub), x, w, xb, iterations=5, obj_weight=-1.0)
+
+
+def _with_dense_row(p, seed):
+    """p plus one row over every variable (coefficients 1..3), its right-hand side 30% below the
+    row's value at the planted point, so that the row is violated there."""
+    rng = np.random.default_rng(seed)
+    a = rng.integers(1, 4, p.n).astype(float)
+    x0 = np.asarray(p.x0, dtype=float)
+    rp = np.append(np.asarray(p.row_ptr, dtype=np.int64), int(p.row_ptr[-1]) + p.n)
+    col = np.concatenate([np.asarray(p.col, dtype=np.int32), np.arange(p.n, dtype=np.int32)])
+    val = np.concatenate([np.asarray(p.val, dtype=float), a])
+    g = np.append(p.g, np.floor(0.7 * float(a @ x0)))
+    return synth.Milp(p.m + 1, p.n, rp, col, val, g, p.lb, p.ub, p.is_int, p.c, x0=x0, name=p.name + "_dense")
+
+
+def test_matches_oracle_with_a_dense_row(pkg):
+    """A row over all 12,000 variables: every move's distance-2 neighbourhood holds more entries
+    than the grid has warps (a thread per entry), and the dense row's cached candidates are
+    scanned and recomputed by the whole grid."""
+    p = _with_dense_row(_integer_problem(590, 2000, 12000), 590)
+    r = _same(p, np.asarray(p.x0, dtype=float), np.ones(p.m), 25, pkg)
+    assert r["moves"] > 0
