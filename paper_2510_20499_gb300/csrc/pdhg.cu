@@ -134,8 +134,20 @@ __global__ void __launch_bounds__(kPdThreads) k_pdhg_rows(DevProblem P, PdhgVecs
             const int i = (t - t_pieces - t_warp) * 32 + lane;
             if (i < nthread_rows) {
                 const int k = P.static_list[P.class_off[0] + i];
+                const int e = P.row_ptr[k + 1];
                 double s = 0.0;
-                for (int q = P.row_ptr[k]; q < P.row_ptr[k + 1]; ++q) s = fma(P.val[q], xe[P.col[q]], s);
+                int q = P.row_ptr[k];
+                // four nonzeros' loads issued together; the sum keeps the row order
+                for (; q + 4 <= e; q += 4) {
+                    const int c0 = P.col[q], c1 = P.col[q + 1], c2 = P.col[q + 2], c3 = P.col[q + 3];
+                    const double a0 = P.val[q], a1 = P.val[q + 1], a2 = P.val[q + 2], a3 = P.val[q + 3];
+                    const double v0 = xe[c0], v1 = xe[c1], v2 = xe[c2], v3 = xe[c3];
+                    s = fma(a0, v0, s);
+                    s = fma(a1, v1, s);
+                    s = fma(a2, v2, s);
+                    s = fma(a3, v3, s);
+                }
+                for (; q < e; ++q) s = fma(P.val[q], xe[P.col[q]], s);
                 pdhg_row_done(P, V, k, s, y, yn, ys, eval);
             }
         }
