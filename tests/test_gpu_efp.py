@@ -90,3 +90,19 @@ def test_improvement_mode_cycle_after_cut(pkg):
     cut problem."""
     r = _improve_case(pkg, 0, 16)
     assert r["cycles"] >= 1 and r["improvements"] >= 10
+
+
+def test_improvement_mode_with_zero_costs(pkg):
+    """c = 0: the first feasible point is the only incumbent; the cut row is empty with
+    right-hand side -1e-4, so the cut problem has no feasible point and every round fails."""
+    import torch
+    p = synth.knapsack_cover(seed=700, m=300, n=600, nnz=3000)
+    p.c = np.zeros(p.n)
+    ox, orr = efp.run(p, p.lb, p.ub, seed=1, improve=True, **KW)
+    prob = pkg.Problem(p)
+    gx, gr = prob.extended_fp(torch.tensor(p.lb, device="cuda"), torch.tensor(p.ub, device="cuda"), seed=1,
+                              improve=True, **KW)
+    for k in ("status", "found_at", "rounds", "cycles", "improvements"):
+        assert gr[k] == orr[k], (k, gr, orr)
+    np.testing.assert_array_equal(gx.cpu().numpy(), ox)
+    assert orr["improvements"] <= 1

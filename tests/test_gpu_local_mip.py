@@ -228,3 +228,30 @@ def test_matches_oracle_with_a_dense_row(pkg):
     p = _with_dense_row(_integer_problem(590, 2000, 12000), 590)
     r = _same(p, np.asarray(p.x0, dtype=float), np.ones(p.m), 25, pkg)
     assert r["moves"] > 0
+
+
+# --- edge cases ---
+
+
+def test_zero_iterations_leave_the_point(pkg):
+    p = _integer_problem(71, 200, 150)
+    x0 = np.clip(np.round(np.random.default_rng(1).normal(0, 3, p.n)), p.lb, p.ub)
+    gx, gw, gr = _gpu(pkg, p, x0, np.ones(p.m), 0)
+    _, _, orr = lm.search(p, p.lb, p.ub, x0, np.ones(p.m), 0)
+    np.testing.assert_array_equal(gx, x0)
+    np.testing.assert_array_equal(gw, np.ones(p.m))
+    assert gr["moves"] == 0 and gr["bumps"] == 0 and gr["violated"] == orr["violated"]
+    ox, ow, ob, ro = lm.search_objective(p, p.lb, p.ub, x0, np.ones(p.m), 0)
+    bx, bw, bb, br = _gpu_obj(pkg, p, x0, np.ones(p.m), 0)
+    np.testing.assert_array_equal(bx, x0)
+    assert not br["found"] and np.isnan(bb).all() and br["improvements"] == ro["improvements"] == 0
+
+
+def test_feasible_start_does_not_move(pkg):
+    """At a point with no violated row there is no candidate and no weight to raise."""
+    p = _integer_problem(72, 200, 150)
+    x0 = np.asarray(p.x0, dtype=float)
+    gx, gw, gr = _gpu(pkg, p, x0, np.ones(p.m), 25)
+    np.testing.assert_array_equal(gx, x0)
+    np.testing.assert_array_equal(gw, np.ones(p.m))
+    assert gr["moves"] == 0 and gr["bumps"] == 0 and gr["violated"] == 0
