@@ -38,6 +38,13 @@ in the local search's objective row: 1 for an integral objective on integer vari
 LP's dual iterate extended by 0 and the kept weights by 1 for the cut row; a point satisfying
 every row of the cut problem is a better incumbent.  The round budget ends the pump, which
 returns the incumbent.
+
+Polish (`polish=True`, improvement mode; the paper also uses Local-MIP to search the
+neighbourhood of an integer point): each new incumbent is first searched by the local search
+with its objective moves (oracle/local_mip.py `search_objective`, ls_iterations, fresh weights,
+objective weight 1) on the problem without the cut; its best point replaces the incumbent when
+that search recorded a later incumbent than its start (an improvement by its own exact account
+D < 0, so no separately summed objective decides).
 """
 from __future__ import annotations
 
@@ -109,7 +116,7 @@ def with_cut(p, x_best):
 
 
 def run(p, lb, ub, rounds=20, lp_iterations=500, ls_iterations=200, cycle_window=3, cycle_ratio=0.1, seed=1,
-        improve=False):
+        improve=False, polish=False):
     """Returns (x, result dict): status 0 when a feasible point was found (x is it, or the best
     one in improvement mode), found_at -2 (start rounding), -1 (all-zero start), r >= 0 (round
     r) or -3 (none) for the first feasible point, rounds run, cycle breaks, the distances, and in
@@ -123,7 +130,7 @@ def run(p, lb, ub, rounds=20, lp_iterations=500, ls_iterations=200, cycle_window
     s, _ = P.fix_and_propagate(xl, lb, ub, seed=seed)
     s1, w1, r1 = local_mip.search(p, lb, ub, s, np.ones(p.m), ls_iterations)
     res = {"status": 1, "found_at": -3, "rounds": 0, "cycles": 0, "distances": [], "improvements": 0,
-           "best_objective": float("inf"), "incumbents": []}
+           "best_objective": float("inf"), "incumbents": [], "polished": 0}
     best = None
     q, Q = p, P   # the problem the loop works on (with the cut once an incumbent exists)
 
@@ -134,6 +141,11 @@ def run(p, lb, ub, rounds=20, lp_iterations=500, ls_iterations=200, cycle_window
             y = np.append(y, 0.0)
             W = np.append(W, 1.0)
         best = np.array(pt, dtype=np.float64)
+        if polish:
+            _, _, xb, rr = local_mip.search_objective(p, lb, ub, best, np.ones(p.m), ls_iterations)
+            if rr["improvements"] > 1:
+                best = xb
+                res["polished"] += 1
         res["improvements"] += 1
         res["best_objective"] = float(np.asarray(p.c, dtype=np.float64) @ best)
         res["incumbents"].append(best.copy())

@@ -103,3 +103,28 @@ def test_improvement_mode(seed):
         assert f <= prev - 1.0
         prev = f
     assert ri["best_objective"] == prev
+
+
+@pytest.mark.parametrize("seed", [0, 2, 4])
+def test_improvement_mode_polish(seed):
+    """With the polish, the first incumbent is the local search's best from generation mode's
+    point (never worse than it), every incumbent satisfies every row and improves on the last by
+    at least delta, and the polish replaced at least one incumbent on these instances."""
+    p = synth.knapsack_cover(seed=700 + seed, m=300, n=600, nnz=3000)
+    p.c = np.random.default_rng(seed).integers(-5, 6, p.n).astype(float)
+    kw = dict(rounds=6, lp_iterations=200, ls_iterations=100, seed=seed + 1)
+    xg, rg = efp.run(p, p.lb, p.ub, **kw)
+    xi, ri = efp.run(p, p.lb, p.ub, improve=True, polish=True, **kw)
+    assert ri["status"] == rg["status"] == 0 and ri["found_at"] == rg["found_at"]
+    assert ri["polished"] >= 1
+    inc = ri["incumbents"]
+    assert float(p.c @ inc[0]) <= float(p.c @ xg)
+    _, _, xb, rr = local_mip.search_objective(p, p.lb, p.ub, xg, np.ones(p.m), kw["ls_iterations"])
+    np.testing.assert_array_equal(inc[0], xb if rr["improvements"] > 1 else xg)
+    prev = np.inf
+    for x in inc:
+        assert _rows_ok(p, x) and (x[p.is_int == 1] == np.round(x[p.is_int == 1])).all()
+        f = float(p.c @ x)
+        assert f <= prev - 1.0
+        prev = f
+    np.testing.assert_array_equal(inc[-1], xi)
