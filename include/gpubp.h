@@ -623,14 +623,19 @@ int local_search_objective(mip_problem *p, const double *lb, const double *ub, d
  * rebuilt at each incumbent; it continues from x* with an empty distance history, the LP's dual
  * iterate extended by 0 and the kept weights by 1 for the cut row.  A point satisfying every row
  * of the cut problem is a better incumbent.  The round budget ends the pump.  Costs of magnitude
- * below 1e-12 are rejected by the cut row's load (BP_ERR_INVALID).
+ * below 1e-12 are rejected by the cut row's load (BP_ERR_INVALID).  With polish = 1 each new
+ * incumbent is first searched by local_search_objective (ls_iterations, fresh weights, objective
+ * weight 1) on the problem without the cut, and that search's best replaces it when the search
+ * recorded a later incumbent than its start (Section 1: Local-MIP searching the neighbourhood
+ * of an integer point).
  *
  * x_out:   DEVICE double[n]: the feasible point found (improvement mode: the last incumbent),
  *          else the loop's last point.
  * result:  HOST pointer (the call synchronises the stream): status FP_FEASIBLE / FP_INFEASIBLE,
  *          found_at (-2 the start rounding, -1 the all-zero start, r >= 0 round r, -3 none) of
  *          the first feasible point, rounds run, cycle breaks, the last distance; improvement
- *          mode: incumbents recorded and c x* of the last (+inf when none).
+ *          mode: incumbents recorded, how many the polish replaced, and c x* of the last (+inf
+ *          when none).
  * Returns BP_OK, BP_ERR_INVALID, BP_ERR_OOM, BP_ERR_CUDA or BP_ERR_TIMEOUT.
  */
 typedef struct {
@@ -641,7 +646,7 @@ typedef struct {
     double cycle_ratio;        /* (0.1) */
     uint64_t seed;             /* fix_and_propagate's seed of the start; round r uses seed + r + 1 */
     int32_t improve;           /* 0: generation mode, 1: improvement mode (0) */
-    int32_t reserved;
+    int32_t polish;            /* improvement mode: 1 to polish each incumbent (0) */
 } efp_params;
 
 typedef struct {
@@ -651,7 +656,7 @@ typedef struct {
     int32_t cycles;
     double last_distance;
     int32_t improvements;
-    int32_t reserved;
+    int32_t polished;
     double best_objective;
 } efp_result;
 

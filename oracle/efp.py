@@ -159,6 +159,7 @@ def run(p, lb, ub, rounds=20, lp_iterations=500, ls_iterations=200, cycle_window
             return s1, res
         s, W = s1, w1
         incumbent(s1, -2)
+        s = best.copy()
     else:
         s2, w2, r2 = local_mip.search(p, lb, ub, zero, np.ones(p.m), ls_iterations)
         if r2["violated"] == 0:
@@ -167,6 +168,7 @@ def run(p, lb, ub, rounds=20, lp_iterations=500, ls_iterations=200, cycle_window
                 return s2, res
             s, W = s2, w2
             incumbent(s2, -1)
+            s = best.copy()
         else:
             s, W = (s2, w2) if r2["violated"] < r1["violated"] else (s1, w1)
     hist = []

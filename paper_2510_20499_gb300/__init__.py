@@ -115,16 +115,16 @@ class LsObjResult(C.Structure):
 class EfpParams(C.Structure):
     _fields_ = [("rounds", C.c_int32), ("lp_iterations", C.c_int32), ("ls_iterations", C.c_int32),
                 ("cycle_window", C.c_int32), ("cycle_ratio", C.c_double), ("seed", C.c_uint64),
-                ("improve", C.c_int32), ("reserved", C.c_int32)]
+                ("improve", C.c_int32), ("polish", C.c_int32)]
 
 
 class EfpResult(C.Structure):
     _fields_ = [("status", C.c_int32), ("found_at", C.c_int32), ("rounds", C.c_int32), ("cycles", C.c_int32),
-                ("last_distance", C.c_double), ("improvements", C.c_int32), ("reserved", C.c_int32),
+                ("last_distance", C.c_double), ("improvements", C.c_int32), ("polished", C.c_int32),
                 ("best_objective", C.c_double)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class BpTuning(C.Structure):
@@ -494,12 +494,13 @@ Problem.local_search_objective = _local_search_objective
 
 
 def _extended_fp(prob, lb, ub, rounds=20, lp_iterations=500, ls_iterations=200, cycle_window=3, cycle_ratio=0.1,
-                 seed=1, improve=False, stream=None):
-    """extended_fp (Algorithm 2; generation mode, or improvement mode with improve=True) on
-    device bounds.  Returns (x device tensor, result dict)."""
+                 seed=1, improve=False, polish=False, stream=None):
+    """extended_fp (Algorithm 2; generation mode, or improvement mode with improve=True, each
+    incumbent polished by the local search's objective moves with polish=True) on device bounds.
+    Returns (x device tensor, result dict)."""
     torch = _torch()
     prm = EfpParams(int(rounds), int(lp_iterations), int(ls_iterations), int(cycle_window), float(cycle_ratio),
-                    int(seed), 1 if improve else 0, 0)
+                    int(seed), 1 if improve else 0, 1 if polish else 0)
     res = EfpResult()
     x = torch.empty_like(lb)
     _check(lib().extended_fp(prob.h, _ptr(lb), _ptr(ub), _ptr(x), C.byref(prm), C.byref(res), _stream(stream)))

@@ -155,7 +155,7 @@ extern "C" void efp_params_default(efp_params* p) {
     p->cycle_ratio = 0.1;
     p->seed = 1;
     p->improve = 0;
-    p->reserved = 0;
+    p->polish = 0;
 }
 
 extern "C" int extended_fp(mip_problem* p, const double* lb, const double* ub, double* x_out, const efp_params* params,
@@ -168,7 +168,7 @@ extern "C" int extended_fp(mip_problem* p, const double* lb, const double* ub, d
     if (params) prm = *params;
     else efp_params_default(&prm);
     if (prm.rounds < 0 || prm.lp_iterations < 0 || prm.ls_iterations < 0 || prm.cycle_window < 1 ||
-        !(prm.cycle_ratio >= 0.0) || (prm.improve != 0 && prm.improve != 1)) {
+        !(prm.cycle_ratio >= 0.0) || (prm.improve != 0 && prm.improve != 1) || (prm.polish != 0 && prm.polish != 1)) {
         set_error("extended_fp: invalid parameters");
         return BP_ERR_INVALID;
     }
@@ -209,7 +209,8 @@ extern "C" int extended_fp(mip_problem* p, const double* lb, const double* ub, d
         }                      \
     } while (0)
     // y, the weights and the ones carry one more entry for the cut row of the improvement mode
-    double *x, *y, *xp, *sc, *s1, *s2, *w1, *w2, *c, *part, *dout, *ones_m, *xbest, *rhs;
+    double *x, *y, *xp, *sc, *s1, *s2, *w1, *w2, *c, *part, *dout, *ones_m, *xbest, *rhs, *xls = nullptr,
+           *bls = nullptr;
     EF_TRY(alloc(&x, n));
     EF_TRY(alloc(&y, m + 1));
     EF_TRY(alloc(&xp, n));
@@ -224,6 +225,10 @@ extern "C" int extended_fp(mip_problem* p, const double* lb, const double* ub, d
     EF_TRY(alloc(&ones_m, m + 1));
     EF_TRY(alloc(&xbest, n));
     EF_TRY(alloc(&rhs, 2));
+    if (improve && prm.polish) {
+        EF_TRY(alloc(&xls, n));
+        EF_TRY(alloc(&bls, n));
+    }
     const int g = kEfpBlocks;
     auto fill = [&](double* a, int cnt, double v) { k_efp_fill<<<g, kEfpThreads, 0, s>>>(cnt, v, a); };
     auto copy = [&](double* dst, const double* src, int cnt) -> int {
@@ -280,6 +285,19 @@ extern "C" int extended_fp(mip_problem* p, const double* lb, const double* ub, d
             fill(W + m, 1, 1.0);
         }
         if ((rc = copy(xbest, pt, n)) != BP_OK) return rc;
+        if (prm.polish) {
+            // the local search with its objective moves from the incumbent, on the problem
+            // without the cut: its best when it recorded a later incumbent than its start
+            ls_obj_params op{prm.ls_iterations, 0, 1.0};
+            ls_obj_result orr;
+            if ((rc = copy(xls, pt, n)) != BP_OK) return rc;
+            fill(ones_m, m, 1.0);
+            if ((rc = local_search_objective(p, lb, ub, xls, ones_m, bls, &op, &orr, stream)) != BP_OK) return rc;
+            if (orr.improvements > 1) {
+                if ((rc = copy(xbest, bls, n)) != BP_OK) return rc;
+                result->polished += 1;
+            }
+        }
         result->improvements += 1;
         k_efp_cut_rhs<<<1, kEfpThreads, 0, s>>>(n, p->obj, p->dp.is_int, xbest, rhs);
         if ((rc = copy(cut_g + m, rhs, 1)) != BP_OK) return rc;
@@ -332,6 +350,7 @@ extern "C" int extended_fp(mip_problem* p, const double* lb, const double* ub, d
             return BP_OK;
         }
         EF_TRY(incumbent(s1, -2));
+        EF_TRY(copy(cur, xbest, n));   // the loop continues from the incumbent
         start_found = true;
     }
     if (!start_found) {
@@ -348,6 +367,7 @@ extern "C" int extended_fp(mip_problem* p, const double* lb, const double* ub, d
             cur = s2;
             W = w2;
             EF_TRY(incumbent(s2, -1));
+            EF_TRY(copy(cur, xbest, n));
         } else if (r2.violated < r1.violated) {
             // the main loop's point and its kept weights: the start with fewer violated rows
             cur = s2;

@@ -106,3 +106,20 @@ def test_improvement_mode_with_zero_costs(pkg):
         assert gr[k] == orr[k], (k, gr, orr)
     np.testing.assert_array_equal(gx.cpu().numpy(), ox)
     assert orr["improvements"] <= 1
+
+
+@pytest.mark.parametrize("seed", [0, 2, 3])
+def test_improvement_mode_polish_matches_oracle(pkg, seed):
+    """Each incumbent polished by the local search's objective moves (integral costs): the
+    incumbents, the polish count, the rounds and the point agree with the oracle (seed 3 finds
+    no feasible point)."""
+    import torch
+    p = synth.knapsack_cover(seed=700 + seed, m=300, n=600, nnz=3000)
+    p.c = np.random.default_rng(seed).integers(-5, 6, p.n).astype(float)
+    ox, orr = efp.run(p, p.lb, p.ub, seed=seed + 1, improve=True, polish=True, **KW)
+    prob = pkg.Problem(p)
+    gx, gr = prob.extended_fp(torch.tensor(p.lb, device="cuda"), torch.tensor(p.ub, device="cuda"), seed=seed + 1,
+                              improve=True, polish=True, **KW)
+    for k in ("status", "found_at", "rounds", "cycles", "improvements", "polished", "best_objective"):
+        assert gr[k] == orr[k], (k, gr, orr)
+    np.testing.assert_array_equal(gx.cpu().numpy(), ox)
