@@ -18,8 +18,12 @@ here is the mixed-tight-move core, for A x <= g (rows with g = +inf are free), l
                    sum over the rows r of column j (ascending) of
                    w_r (v_r - max(0, L_r + a_rj (t - x_j) - g_r));
   selection    the largest score; ties: smallest variable, then smallest value;
-  step         score > 0: x_j = t and L_r += a_rj (t - x_j) for the rows of column j (ascending);
-               otherwise every violated row's weight grows by 1.
+  step         score > 0: x_j = t and L_r += a_rj (t - x_j) for the rows of column j (ascending),
+               each a compensated (Kahan) sum with a per-row compensation term (the paper's
+               Local-MIP keeps its row activities so); otherwise every violated row's weight
+               grows by 1;
+  recompute    every `recompute_period` iterations (0: never) the activities are summed afresh
+               in row order and the compensation cleared, at the start of the iteration.
 
 Lift and breakthrough moves (objective improvement) extend this core in `search_objective`
 (reading at its section below).  Plain Python loops over the rows and columns, IEEE double.
@@ -49,6 +53,14 @@ def activities(p, x):
             s = s + float(p.val[q]) * float(x[int(p.col[q])])
         L[k] = s
     return L
+
+
+def kahan_add(L, C, r, inc):
+    """L[r] += inc as a compensated sum with compensation C[r] (Kahan)."""
+    y = inc - C[r]
+    t = L[r] + y
+    C[r] = (t - L[r]) - y
+    L[r] = t
 
 
 def violation(L, g):
@@ -102,7 +114,7 @@ def score(cols, g, w, x, L, j, t):
     return s
 
 
-def search(p, lb, ub, x0, w0, iterations):
+def search(p, lb, ub, x0, w0, iterations, recompute_period=0):
     """Runs `iterations` steps from (x0, w0).  Returns (x, w, result dict)."""
     cols = _csc(p)
     x = np.array(x0, dtype=np.float64)
@@ -110,8 +122,12 @@ def search(p, lb, ub, x0, w0, iterations):
     lb = np.asarray(lb, dtype=np.float64)
     ub = np.asarray(ub, dtype=np.float64)
     L = activities(p, x)
+    C = np.zeros(p.m)
     moves = bumps = 0
-    for _ in range(int(iterations)):
+    for it in range(int(iterations)):
+        if recompute_period > 0 and it > 0 and it % recompute_period == 0:
+            L = activities(p, x)
+            C = np.zeros(p.m)
         best = None
         for k, j, t in candidates(p, x, L, lb, ub):
             sc = score(cols, p.g, w, x, L, j, t)
@@ -122,7 +138,7 @@ def search(p, lb, ub, x0, w0, iterations):
             _, j, t, _ = best
             dx = t - x[j]
             for r, a in cols[j]:
-                L[r] = L[r] + a * dx
+                kahan_add(L, C, r, a * dx)
             x[j] = t
             moves += 1
         else:
@@ -220,7 +236,7 @@ def tight_value(xj, a, v, integer):
     return xj - v / a
 
 
-def search_objective(p, lb, ub, x0, w0, iterations, obj_weight=1.0):
+def search_objective(p, lb, ub, x0, w0, iterations, obj_weight=1.0, recompute_period=0):
     """Local search with the objective moves, from (x0, w0, obj_weight).  Returns
     (x, w, x_best or None, result dict)."""
     cols = _csc(p)
@@ -232,6 +248,7 @@ def search_objective(p, lb, ub, x0, w0, iterations, obj_weight=1.0):
     ub = np.asarray(ub, dtype=np.float64)
     delta = objective_delta(p)
     L = activities(p, x)
+    C = np.zeros(p.m)
     w_obj = float(obj_weight)
     D = 0.0
     best = None
@@ -241,11 +258,14 @@ def search_objective(p, lb, ub, x0, w0, iterations, obj_weight=1.0):
         nonlocal D
         dx = t - x[j]
         for r, a in cols[j]:
-            L[r] = L[r] + a * dx
+            kahan_add(L, C, r, a * dx)
         D = D + c[j] * dx
         x[j] = t
 
-    for _ in range(int(iterations)):
+    for it in range(int(iterations)):
+        if recompute_period > 0 and it > 0 and it % recompute_period == 0:
+            L[:] = activities(p, x)
+            C[:] = 0.0
         nviol = int((violation(L, g) > 0.0).sum())
         if nviol == 0:
             if best is None or D < 0.0:

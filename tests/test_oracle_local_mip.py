@@ -219,3 +219,50 @@ def test_delta_reading():
     assert lm.objective_delta(p2) == 1e-4
     p2.c = np.array([1.0, 0.0])
     assert lm.objective_delta(p2) == 1.0
+
+
+# --- compensated activity updates and the periodic recompute ---
+
+
+def test_kahan_add_compensates():
+    """Ten additions of 0.1 give exactly 1.0 with the compensation (plain sums give
+    0.9999999999999999); ten additions of 1.0 to 1e16 keep every unit (plain sums keep none)."""
+    L, C = np.zeros(1), np.zeros(1)
+    plain = 0.0
+    for _ in range(10):
+        lm.kahan_add(L, C, 0, 0.1)
+        plain += 0.1
+    assert L[0] == 1.0 and plain != 1.0
+    L, C = np.array([1e16]), np.zeros(1)
+    plain = 1e16
+    for _ in range(10):
+        lm.kahan_add(L, C, 0, 1.0)
+        plain += 1.0
+    assert L[0] == 1e16 + 10 and plain == 1e16
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_recompute_every_iteration_is_chained_single_steps(seed):
+    """With recompute_period = 1 every iteration starts from activities summed afresh, which is
+    what a chain of one-iteration searches does: the two agree step for step, on general data."""
+    p = synth.random_milp(330 + seed, 60, 50, len_lo=2, len_hi=8, int_fraction=0.6, slack_scale=0.3)
+    p.lb = np.where(np.isfinite(p.lb), p.lb, -50.0)
+    p.ub = np.where(np.isfinite(p.ub), p.ub, 50.0)
+    rng = np.random.default_rng(seed)
+    x0 = np.clip(rng.normal(0, 10, p.n), p.lb, p.ub)
+    x0[p.is_int == 1] = np.round(x0[p.is_int == 1])
+    xa, wa, _ = lm.search(p, p.lb, p.ub, x0, np.ones(p.m), 30, recompute_period=1)
+    xb, wb = x0, np.ones(p.m)
+    for _ in range(30):
+        xb, wb, _ = lm.search(p, p.lb, p.ub, xb, wb, 1)
+    np.testing.assert_array_equal(xa, xb)
+    np.testing.assert_array_equal(wa, wb)
+
+
+def test_recompute_changes_nothing_on_integer_data():
+    p = _problem(340)
+    x0 = np.clip(np.round(np.random.default_rng(0).normal(0, 3, p.n)), p.lb, p.ub)
+    a = lm.search(p, p.lb, p.ub, x0, np.ones(p.m), 40)
+    b = lm.search(p, p.lb, p.ub, x0, np.ones(p.m), 40, recompute_period=7)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
