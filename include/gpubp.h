@@ -512,12 +512,15 @@ int pdhg_solve(mip_problem *p, const double *lb, const double *ub, double *x, do
  * scores recomputed each iteration.  The best move (largest score; ties: smallest variable,
  * then smallest value) is applied when its score is positive; otherwise every violated row's
  * weight grows by 1.  Lift and breakthrough moves (objective improvement): local_search_objective.
+ * The row activities follow the moves as compensated (Kahan) sums, one compensation term per
+ * row, and are summed afresh in row order every recompute_period iterations (0: never), at the
+ * start of the iteration (Local-MIP's numerics).
  * Deterministic: the same inputs give the same moves bit for bit.
  *
  * lb, ub:  DEVICE double[n] bounds (not modified).
  * x:       DEVICE double[n], the start point on entry, the final point on return.
  * w:       DEVICE double[m], the weights (1 for a fresh search), updated in place.
- * params:  iterations >= 0.
+ * params:  iterations >= 0, recompute_period >= 0.
  * result:  HOST pointer, valid at return (the call synchronises the stream): moves applied,
  *          weight bumps, violated rows at the end, sum of w_k v_k, and c^T x (the handle's
  *          objective).
@@ -526,7 +529,7 @@ int pdhg_solve(mip_problem *p, const double *lb, const double *ub, double *x, do
  */
 typedef struct {
     int32_t iterations;
-    int32_t reserved;
+    int32_t recompute_period;   /* activities summed afresh every this many iterations (0: never) */
 } ls_params;
 
 typedef struct {
@@ -567,7 +570,8 @@ int local_search_mtm(mip_problem *p, const double *lb, const double *ub, double 
  * x:       DEVICE double[n], the start point on entry, the final point on return.
  * w:       DEVICE double[m], the row weights, updated in place.
  * x_best:  DEVICE double[n], written with each incumbent (untouched when none is found).
- * params:  iterations >= 0; obj_weight = w0 at the start (finite, >= 0).
+ * params:  iterations >= 0; recompute_period >= 0 (as local_search_mtm's); obj_weight = w0 at
+ *          the start (finite, >= 0).
  * result:  HOST pointer, valid at return (the call synchronises the stream): local_search_mtm's
  *          fields, then lift moves, breakthrough moves (applied), incumbents recorded, found (an
  *          incumbent exists), c^T x_best (+inf when none), w0 at the end, and delta.
@@ -576,7 +580,7 @@ int local_search_mtm(mip_problem *p, const double *lb, const double *ub, double 
  */
 typedef struct {
     int32_t iterations;
-    int32_t reserved;
+    int32_t recompute_period;   /* as in ls_params */
     double obj_weight;
 } ls_obj_params;
 

@@ -85,7 +85,7 @@ class PdhgResult(C.Structure):
 
 
 class LsParams(C.Structure):
-    _fields_ = [("iterations", C.c_int32), ("reserved", C.c_int32)]
+    _fields_ = [("iterations", C.c_int32), ("recompute_period", C.c_int32)]
 
 
 class LsResult(C.Structure):
@@ -97,7 +97,7 @@ class LsResult(C.Structure):
 
 
 class LsObjParams(C.Structure):
-    _fields_ = [("iterations", C.c_int32), ("reserved", C.c_int32), ("obj_weight", C.c_double)]
+    _fields_ = [("iterations", C.c_int32), ("recompute_period", C.c_int32), ("obj_weight", C.c_double)]
 
 
 class LsObjResult(C.Structure):
@@ -467,10 +467,10 @@ def _pdhg(prob, lb, ub, x, y, iterations=1000, restart_period=100, step=0.0, pri
 Problem.pdhg = _pdhg
 
 
-def _local_search(prob, lb, ub, x, w, iterations=100, stream=None):
+def _local_search(prob, lb, ub, x, w, iterations=100, recompute_period=0, stream=None):
     """local_search_mtm on device tensors: lb, ub and x (n), w (m) float64; x and w are updated
     in place.  Returns the result dict."""
-    prm = LsParams(int(iterations), 0)
+    prm = LsParams(int(iterations), int(recompute_period))
     res = LsResult()
     _check(lib().local_search_mtm(prob.h, _ptr(lb), _ptr(ub), _ptr(x), _ptr(w), C.byref(prm), C.byref(res),
                                   _stream(stream)))
@@ -480,10 +480,11 @@ def _local_search(prob, lb, ub, x, w, iterations=100, stream=None):
 Problem.local_search = _local_search
 
 
-def _local_search_objective(prob, lb, ub, x, w, x_best, iterations=100, obj_weight=1.0, stream=None):
+def _local_search_objective(prob, lb, ub, x, w, x_best, iterations=100, obj_weight=1.0, recompute_period=0,
+                            stream=None):
     """local_search_objective on device tensors: lb, ub, x and x_best (n), w (m) float64; x and
     w are updated in place, x_best receives each incumbent.  Returns the result dict."""
-    prm = LsObjParams(int(iterations), 0, float(obj_weight))
+    prm = LsObjParams(int(iterations), int(recompute_period), float(obj_weight))
     res = LsObjResult()
     _check(lib().local_search_objective(prob.h, _ptr(lb), _ptr(ub), _ptr(x), _ptr(w), _ptr(x_best), C.byref(prm),
                                         C.byref(res), _stream(stream)))

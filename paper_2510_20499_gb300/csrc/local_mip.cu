@@ -266,16 +266,20 @@ __global__ void __launch_bounds__(kLsThreads) k_ls_score(DevProblem P, const dou
 
 // one block moves x_j to t: the activities of its column, then x_j (and, with the objective
 // moves, D and the count of violated rows)
+// the activity update of a move: L_r += a dx as a compensated (Kahan) sum with the row's
+// compensation term C_r
 template <bool OBJ, bool CG = false, int NT = kLsThreads>
-__device__ void ls_move(const DevProblem& P, double* __restrict__ x, double* __restrict__ L, int j, double t,
-                        LsCtl* ctl, const double* __restrict__ cost) {
+__device__ void ls_move(const DevProblem& P, double* __restrict__ x, double* __restrict__ L, double* __restrict__ C,
+                        int j, double t, LsCtl* ctl, const double* __restrict__ cost) {
     __shared__ int sdv[NT / 32];
     const double dx = __dsub_rn(t, ls_ld<CG>(x + j));
     int dv = 0;
     for (int c = P.col_ptr[j] + threadIdx.x; c < P.col_ptr[j + 1]; c += NT) {
         const int r = P.row_idx[c];
         const double old = ls_ld<CG>(L + r);
-        const double nw = __dadd_rn(old, __dmul_rn(P.col_val[c], dx));
+        const double y = __dsub_rn(__dmul_rn(P.col_val[c], dx), ls_ld<CG>(C + r));
+        const double nw = __dadd_rn(old, y);
+        C[r] = __dsub_rn(__dsub_rn(nw, old), y);
         L[r] = nw;
         if constexpr (OBJ) {
             const double g = P.grow[r].x;
@@ -318,8 +322,8 @@ __device__ LsKey ls_block_best(const LsKey* __restrict__ part, int nparts) {
 
 template <bool OBJ>
 __global__ void __launch_bounds__(kLsThreads) k_ls_apply(DevProblem P, double* __restrict__ x, double* __restrict__ L,
-                                                         const LsKey* __restrict__ part, int nparts, LsCtl* ctl,
-                                                         const double* __restrict__ cost) {
+                                                         double* __restrict__ C, const LsKey* __restrict__ part,
+                                                         int nparts, LsCtl* ctl, const double* __restrict__ cost) {
     if constexpr (OBJ) {
         if (ctl->done) {   // a lift move ended this iteration
             __syncthreads();
@@ -335,7 +339,7 @@ __global__ void __launch_bounds__(kLsThreads) k_ls_apply(DevProblem P, double* _
     const int nviol = OBJ ? ctl->nv : ctl->nviol;
     __syncthreads();
     if (best.j != INT_MAX && best.score > 0.0) {
-        ls_move<OBJ>(P, x, L, best.j, best.t, ctl, cost);
+        ls_move<OBJ>(P, x, L, C, best.j, best.t, ctl, cost);
         if (threadIdx.x == 0) {
             ctl->bump = 0;
             ctl->moved_j = best.j;
@@ -413,8 +417,9 @@ __global__ void __launch_bounds__(kLsThreads) k_lso_lift(DevProblem P, const dou
 
 // records the incumbent, then applies the best lift move when its gain is positive
 __global__ void __launch_bounds__(kLsThreads) k_lso_lift_apply(DevProblem P, double* __restrict__ x,
-                                                               double* __restrict__ L, const LsKey* __restrict__ part,
-                                                               int nparts, LsCtl* ctl, const double* __restrict__ cost) {
+                                                               double* __restrict__ L, double* __restrict__ C,
+                                                               const LsKey* __restrict__ part, int nparts, LsCtl* ctl,
+                                                               const double* __restrict__ cost) {
     const int nv = ctl->nv;
     const bool rec = nv == 0 && (!ctl->has_best || ctl->D < 0.0);
     __syncthreads();
@@ -429,7 +434,7 @@ __global__ void __launch_bounds__(kLsThreads) k_lso_lift_apply(DevProblem P, dou
     if (nv != 0) return;
     const LsKey best = ls_block_best(part, nparts);
     if (best.j != INT_MAX && best.score > 0.0) {
-        ls_move<true>(P, x, L, best.j, best.t, ctl, cost);
+        ls_move<true>(P, x, L, C, best.j, best.t, ctl, cost);
         if (threadIdx.x == 0) {
             ctl->lifts += 1;
             ctl->done = 1;
@@ -581,6 +586,33 @@ __device__ __forceinline__ bool ls_grid_sync(LsCtl* ctl, unsigned& bar_k) {
     return __ldcg(&ctl->error) == 0;
 }
 
+// every slot of every violated row, inside the persistent search: a warp per row, the long
+// rows' slots over the whole grid
+__device__ void ls_all_slots(const DevProblem& P, const double* __restrict__ lb, const double* __restrict__ ub,
+                             const double* __restrict__ x, const double* __restrict__ w,
+                             const double* __restrict__ L, double* __restrict__ T, double* __restrict__ S,
+                             const int* __restrict__ long_list, int nlong, int gw, int nw, int lane, int tid,
+                             int nthr) {
+    for (int k = gw; k < P.m; k += nw) {
+        const double g = P.grow[k].x;
+        if (!isfinite(g)) continue;
+        const double v = __dsub_rn(L[k], g);
+        if (!(v > 0.0)) continue;
+        const int qb = P.row_ptr[k], qe = P.row_ptr[k + 1];
+        if (qe - qb > kLsLongRow) continue;
+        for (int q = qb + lane; q < qe; q += 32) ls_slot<false>(P, lb, ub, x, w, L, P.col[q], P.val[q], v, T, S, q);
+    }
+    for (int i = 0; i < nlong; ++i) {
+        const int k = long_list[i];
+        const double g = P.grow[k].x;
+        if (!isfinite(g)) continue;
+        const double v = __dsub_rn(L[k], g);
+        if (!(v > 0.0)) continue;
+        for (int q = P.row_ptr[k] + tid; q < P.row_ptr[k + 1]; q += nthr)
+            ls_slot<false>(P, lb, ub, x, w, L, P.col[q], P.val[q], v, T, S, q);
+    }
+}
+
 constexpr int kLsLoopThreads = 256;
 constexpr int kLsNbrStaged = 1024;   // rows of the moved column staged in shared memory
 
@@ -591,8 +623,8 @@ __global__ void __launch_bounds__(kLsLoopThreads) k_ls_loop(DevProblem P, const 
                                                         const int* __restrict__ perm, LsKey* __restrict__ part,
                                                         int* __restrict__ nbr_row, int* __restrict__ nbr_start,
                                                         const int* __restrict__ long_list,
-                                                        const int* __restrict__ long_count, LsCtl* ctl,
-                                                        int iterations) {
+                                                        const int* __restrict__ long_count, double* __restrict__ C,
+                                                        LsCtl* ctl, int it0, int iterations, int recompute_period) {
     __shared__ int s_row[kLsNbrStaged], s_start[kLsNbrStaged];
     __shared__ int s_wsum[kLsLoopThreads / 32];
     __shared__ int s_carry;
@@ -604,6 +636,20 @@ __global__ void __launch_bounds__(kLsLoopThreads) k_ls_loop(DevProblem P, const 
     const int nlong = *long_count;
     unsigned bar_k = 0;
     for (int it = 0; it < iterations; ++it) {
+        if (recompute_period > 0 && it0 + it > 0 && (it0 + it) % recompute_period == 0) {
+            // the activities summed afresh in row order, the compensation cleared, then every
+            // violated row's slots
+            for (int k = tid; k < P.m; k += nthr) {
+                double sum = 0.0;
+                for (int q = P.row_ptr[k]; q < P.row_ptr[k + 1]; ++q)
+                    sum = __dadd_rn(sum, __dmul_rn(P.val[q], x[P.col[q]]));
+                L[k] = sum;
+                C[k] = 0.0;
+            }
+            if (!ls_grid_sync(ctl, bar_k)) return;
+            ls_all_slots(P, lb, ub, x, w, L, T, S, long_list, nlong, gw, nw, lane, tid, nthr);
+            if (!ls_grid_sync(ctl, bar_k)) return;
+        }
         // selection: the best cached key of the violated rows
         LsKey best = ls_none();
         int nviol = 0;
@@ -682,7 +728,7 @@ __global__ void __launch_bounds__(kLsLoopThreads) k_ls_loop(DevProblem P, const 
             const int nv = __ldcg(&ctl->nviol);
             __syncthreads();
             if (bb.j != INT_MAX && bb.score > 0.0) {
-                ls_move<false, false, kLsLoopThreads>(P, x, L, bb.j, bb.t, ctl, nullptr);
+                ls_move<false, false, kLsLoopThreads>(P, x, L, C, bb.j, bb.t, ctl, nullptr);
                 // the rows of column j* and the starts of their entries in one flat sequence
                 // (a block-wide exclusive scan of the row lengths)
                 const int cb = P.col_ptr[bb.j], cn = P.col_ptr[bb.j + 1] - cb;
@@ -740,25 +786,7 @@ __global__ void __launch_bounds__(kLsLoopThreads) k_ls_loop(DevProblem P, const 
                 if (isfinite(g) && __dsub_rn(L[k], g) > 0.0) w[k] = __dadd_rn(w[k], 1.0);
             }
             if (!ls_grid_sync(ctl, bar_k)) return;
-            for (int k = gw; k < P.m; k += nw) {
-                const double g = P.grow[k].x;
-                if (!isfinite(g)) continue;
-                const double v = __dsub_rn(L[k], g);
-                if (!(v > 0.0)) continue;
-                const int qb = P.row_ptr[k], qe = P.row_ptr[k + 1];
-                if (qe - qb > kLsLongRow) continue;
-                for (int q = qb + lane; q < qe; q += 32)
-                    ls_slot<false>(P, lb, ub, x, w, L, P.col[q], P.val[q], v, T, S, q);
-            }
-            for (int i = 0; i < nlong; ++i) {
-                const int k = long_list[i];
-                const double g = P.grow[k].x;
-                if (!isfinite(g)) continue;
-                const double v = __dsub_rn(L[k], g);
-                if (!(v > 0.0)) continue;
-                for (int q = P.row_ptr[k] + tid; q < P.row_ptr[k + 1]; q += nthr)
-                    ls_slot<false>(P, lb, ub, x, w, L, P.col[q], P.val[q], v, T, S, q);
-            }
+            ls_all_slots(P, lb, ub, x, w, L, T, S, long_list, nlong, gw, nw, lane, tid, nthr);
         } else if (js >= 0) {
             const int cn = __ldcg(&ctl->nbr_count), E = __ldcg(&ctl->nbr_total);
             const bool staged = cn <= kLsNbrStaged;
@@ -872,8 +900,8 @@ struct LsOut {
 // the search on the stream: `iterations` iterations from (x, w), the objective moves when OBJ
 template <bool OBJ>
 static int ls_run(mip_problem* p, const double* lb, const double* ub, double* x, double* w, double* x_best,
-                  int iterations, double w0, LsOut* out, cudaStream_t s) {
-    void *pL = nullptr, *pPart = nullptr, *pCtl = nullptr, *pSum = nullptr, *pOut = nullptr;
+                  int iterations, int recompute_period, double w0, LsOut* out, cudaStream_t s) {
+    void *pL = nullptr, *pC = nullptr, *pPart = nullptr, *pCtl = nullptr, *pSum = nullptr, *pOut = nullptr;
     void *pS = nullptr, *pT = nullptr, *pPerm = nullptr, *pNbr = nullptr, *pLong = nullptr;
     // the scoring passes on every resident block (their per-block bests are reduced by
     // k_ls_apply): k_ls_score with the objective moves, else the cache's first full pass
@@ -895,7 +923,7 @@ static int ls_run(mip_problem* p, const double* lb, const double* ub, double* x,
     int nparts = grid_score > grid_lift ? grid_score : grid_lift;
     nparts = nparts > grid_select ? nparts : grid_select;
     auto release = [&]() {
-        for (void* q : {pL, pPart, pCtl, pSum, pOut, pS, pT, pPerm, pNbr, pLong})
+        for (void* q : {pL, pC, pPart, pCtl, pSum, pOut, pS, pT, pPerm, pNbr, pLong})
             if (q) cudaFreeAsync(q, s);
     };
     cudaError_t e = cudaSuccess;
@@ -916,6 +944,7 @@ static int ls_run(mip_problem* p, const double* lb, const double* ub, double* x,
     int* long_count = static_cast<int*>(pLong);   // then the list of long rows
     int* long_list = long_count + 1;
     if ((e = cudaMallocAsync(&pL, sizeof(double) * (size_t)(p->m ? p->m : 1), s)) != cudaSuccess ||
+        (e = cudaMallocAsync(&pC, sizeof(double) * (size_t)(p->m ? p->m : 1), s)) != cudaSuccess ||
         (e = cudaMallocAsync(&pPart, sizeof(LsKey) * (size_t)nparts, s)) != cudaSuccess ||
         (e = cudaMallocAsync(&pCtl, sizeof(LsCtl), s)) != cudaSuccess ||
         (e = cudaMallocAsync(&pSum, sizeof(double) * 3 * kLsRedBlocks, s)) != cudaSuccess ||
@@ -924,13 +953,15 @@ static int ls_run(mip_problem* p, const double* lb, const double* ub, double* x,
         return fail_cuda(e, "cudaMallocAsync");
     }
     double* L = static_cast<double*>(pL);
+    double* C = static_cast<double*>(pC);   // the activities' compensation terms
     LsKey* part = static_cast<LsKey*>(pPart);
     LsCtl* ctl = static_cast<LsCtl*>(pCtl);
     double* sum = static_cast<double*>(pSum);
     double* dout = static_cast<double*>(pOut);
     const double* cost = p->obj;
     const int grid_rows = p->sms * 8;
-    if ((e = cudaMemsetAsync(ctl, 0, sizeof(LsCtl), s)) != cudaSuccess) {
+    if ((e = cudaMemsetAsync(ctl, 0, sizeof(LsCtl), s)) != cudaSuccess ||
+        (p->m && (e = cudaMemsetAsync(C, 0, sizeof(double) * (size_t)p->m, s)) != cudaSuccess)) {
         release();
         return fail_cuda(e, "cudaMemsetAsync");
     }
@@ -949,13 +980,21 @@ static int ls_run(mip_problem* p, const double* lb, const double* ub, double* x,
         k_ls_full<<<grid_score, kLsThreads, 0, s>>>(p->dp, lb, ub, x, w, L, T, S, long_list, long_count);
     }
     for (int it = 0; OBJ && it < iterations; ++it) {
-        {
-            k_lso_lift<<<grid_lift, kLsThreads, 0, s>>>(p->dp, lb, ub, x, L, cost, x_best, part, ctl);
-            k_lso_lift_apply<<<1, kLsThreads, 0, s>>>(p->dp, x, L, part, grid_lift, ctl, cost);
-            k_ls_score<OBJ><<<grid_score, kLsThreads, 0, s>>>(p->dp, lb, ub, x, w, L, part, ctl, cost);
-            k_ls_apply<OBJ><<<1, kLsThreads, 0, s>>>(p->dp, x, L, part, grid_score, ctl, cost);
-            k_ls_bump<<<grid_rows, kLsThreads, 0, s>>>(p->dp, L, w, ctl);
+        if (recompute_period > 0 && it > 0 && it % recompute_period == 0) {
+            // the activities summed afresh in row order (violated rows counted again), the
+            // compensation cleared
+            if ((e = cudaMemsetAsync(&ctl->nv, 0, sizeof(int), s)) != cudaSuccess ||
+                (e = cudaMemsetAsync(C, 0, sizeof(double) * (size_t)p->m, s)) != cudaSuccess) {
+                release();
+                return fail_cuda(e, "cudaMemsetAsync");
+            }
+            k_ls_activities<<<grid_rows, kLsThreads, 0, s>>>(p->dp, x, L, &ctl->nv);
         }
+        k_lso_lift<<<grid_lift, kLsThreads, 0, s>>>(p->dp, lb, ub, x, L, cost, x_best, part, ctl);
+        k_lso_lift_apply<<<1, kLsThreads, 0, s>>>(p->dp, x, L, C, part, grid_lift, ctl, cost);
+        k_ls_score<OBJ><<<grid_score, kLsThreads, 0, s>>>(p->dp, lb, ub, x, w, L, part, ctl, cost);
+        k_ls_apply<OBJ><<<1, kLsThreads, 0, s>>>(p->dp, x, L, C, part, grid_score, ctl, cost);
+        k_ls_bump<<<grid_rows, kLsThreads, 0, s>>>(p->dp, L, w, ctl);
     }
     if (!OBJ && iterations > 0) {
         // launches of at most 2^16 iterations: at most four barriers per iteration keep the
@@ -963,8 +1002,9 @@ static int ls_run(mip_problem* p, const double* lb, const double* ub, double* x,
         DevProblem dp = p->dp;
         for (int done = 0; done < iterations;) {
             int its = iterations - done < 65536 ? iterations - done : 65536;
-            void* args[] = {&dp,   (void*)&lb, (void*)&ub, &x,        &w,         &L,   &T,  &S,
-                            &perm, &part,      &nbr_row,   &nbr_start, &long_list, &long_count, &ctl, &its};
+            int it0 = done, rp = recompute_period;
+            void* args[] = {&dp,        (void*)&lb,  (void*)&ub, &x,   &w,   &L,  &T,    &S,  &perm, &part,
+                            &nbr_row,   &nbr_start,  &long_list, &long_count, &C, &ctl, &it0, &its, &rp};
             if ((done > 0 && (e = cudaMemsetAsync(&ctl->bar_count, 0, sizeof(unsigned), s)) != cudaSuccess) ||
                 (e = cudaLaunchCooperativeKernel((const void*)k_ls_loop, dim3(grid_select), dim3(kLsLoopThreads), args, 0,
                                                  s)) != cudaSuccess) {
@@ -1005,13 +1045,14 @@ extern "C" int local_search_mtm(mip_problem* p, const double* lb, const double* 
         set_error("local_search_mtm: null argument");
         return BP_ERR_INVALID;
     }
-    if (params->iterations < 0) {
-        set_error("local_search_mtm: negative iteration count");
+    if (params->iterations < 0 || params->recompute_period < 0) {
+        set_error("local_search_mtm: negative iteration count or recompute period");
         return BP_ERR_INVALID;
     }
     memset(result, 0, sizeof(*result));
     LsOut out;
-    const int rc = ls_run<false>(p, lb, ub, x, w, nullptr, params->iterations, 0.0, &out, (cudaStream_t)stream);
+    const int rc = ls_run<false>(p, lb, ub, x, w, nullptr, params->iterations, params->recompute_period, 0.0, &out,
+                                 (cudaStream_t)stream);
     if (rc != BP_OK) return rc;
     result->iterations = params->iterations;
     result->moves = out.ctl.moves;
@@ -1029,14 +1070,16 @@ extern "C" int local_search_objective(mip_problem* p, const double* lb, const do
         set_error("local_search_objective: null argument");
         return BP_ERR_INVALID;
     }
-    if (params->iterations < 0 || !(params->obj_weight >= 0.0) || !std::isfinite(params->obj_weight)) {
+    if (params->iterations < 0 || params->recompute_period < 0 || !(params->obj_weight >= 0.0) ||
+        !std::isfinite(params->obj_weight)) {
         set_error("local_search_objective: negative iteration count or invalid objective weight");
         return BP_ERR_INVALID;
     }
     memset(result, 0, sizeof(*result));
     LsOut out;
     const int rc =
-        ls_run<true>(p, lb, ub, x, w, x_best, params->iterations, params->obj_weight, &out, (cudaStream_t)stream);
+        ls_run<true>(p, lb, ub, x, w, x_best, params->iterations, params->recompute_period, params->obj_weight, &out,
+                     (cudaStream_t)stream);
     if (rc != BP_OK) return rc;
     result->iterations = params->iterations;
     result->moves = out.ctl.moves;

@@ -255,3 +255,45 @@ def test_feasible_start_does_not_move(pkg):
     np.testing.assert_array_equal(gx, x0)
     np.testing.assert_array_equal(gw, np.ones(p.m))
     assert gr["moves"] == 0 and gr["bumps"] == 0 and gr["violated"] == 0
+
+
+# --- compensated activities with a periodic recompute ---
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_recompute_period_matches_oracle(pkg, seed):
+    """General data (the compensation terms are nonzero) with the activities summed afresh
+    every 7 iterations: points, weights and counts agree with the oracle bit for bit."""
+    p = synth.random_milp(640 + seed, 200, 180, len_lo=2, len_hi=8, int_fraction=0.6, slack_scale=0.3)
+    p.lb = np.where(np.isfinite(p.lb), p.lb, -50.0)
+    p.ub = np.where(np.isfinite(p.ub), p.ub, 50.0)
+    rng = np.random.default_rng(seed)
+    x0 = np.clip(rng.normal(0, 10, p.n), p.lb, p.ub)
+    x0[p.is_int == 1] = np.round(x0[p.is_int == 1])
+    ox, ow, orr = lm.search(p, p.lb, p.ub, x0, np.ones(p.m), 50, recompute_period=7)
+    prob = pkg.Problem(p)
+    x, w = _t(x0), _t(np.ones(p.m))
+    gr = prob.local_search(_t(p.lb), _t(p.ub), x, w, iterations=50, recompute_period=7)
+    np.testing.assert_array_equal(x.cpu().numpy(), ox)
+    np.testing.assert_array_equal(w.cpu().numpy(), ow)
+    assert gr["moves"] == orr["moves"] and gr["bumps"] == orr["bumps"]
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_objective_recompute_period_matches_oracle(pkg, seed):
+    import torch
+    p = synth.random_milp(660 + seed, 60, 50, len_lo=2, len_hi=8, int_fraction=0.6, slack_scale=0.3)
+    p.lb = np.where(np.isfinite(p.lb), p.lb, -50.0)
+    p.ub = np.where(np.isfinite(p.ub), p.ub, 50.0)
+    x0 = np.clip(np.asarray(p.x0, dtype=float), p.lb, p.ub)
+    ox, ow, ob, orr = lm.search_objective(p, p.lb, p.ub, x0, np.ones(p.m), 200, recompute_period=13)
+    prob = pkg.Problem(p)
+    x, w = _t(x0), _t(np.ones(p.m))
+    xb = torch.full((p.n,), float("nan"), dtype=torch.float64, device="cuda")
+    gr = prob.local_search_objective(_t(p.lb), _t(p.ub), x, w, xb, iterations=200, recompute_period=13)
+    np.testing.assert_array_equal(x.cpu().numpy(), ox)
+    np.testing.assert_array_equal(w.cpu().numpy(), ow)
+    for k in ("moves", "bumps", "lifts", "breakthroughs", "improvements", "obj_weight"):
+        assert gr[k] == orr[k], (k, gr, orr)
+    if orr["found"]:
+        np.testing.assert_array_equal(xb.cpu().numpy(), ob)
