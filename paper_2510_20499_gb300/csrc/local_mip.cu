@@ -33,6 +33,7 @@
 // thread-per-row sum in row order and are updated in the order of the moves, so the search is
 // bit-for-bit that of a sequential implementation with the same operation order.
 #include <climits>
+#include <cstdlib>
 #include <cmath>
 
 #include "bp_host.h"
@@ -624,7 +625,8 @@ __global__ void __launch_bounds__(kLsLoopThreads) k_ls_loop(DevProblem P, const 
                                                         int* __restrict__ nbr_row, int* __restrict__ nbr_start,
                                                         const int* __restrict__ long_list,
                                                         const int* __restrict__ long_count, double* __restrict__ C,
-                                                        LsCtl* ctl, int it0, int iterations, int recompute_period) {
+                                                        LsCtl* ctl, int it0, int iterations, int recompute_period,
+                                                        int skip_block) {
     __shared__ int s_row[kLsNbrStaged], s_start[kLsNbrStaged];
     __shared__ int s_wsum[kLsLoopThreads / 32];
     __shared__ int s_carry;
@@ -636,6 +638,11 @@ __global__ void __launch_bounds__(kLsLoopThreads) k_ls_loop(DevProblem P, const 
     const int nlong = *long_count;
     unsigned bar_k = 0;
     for (int it = 0; it < iterations; ++it) {
+        if (skip_block == (int)blockIdx.x) {
+            // test-only failure: this block stops arriving at the grid barriers, so the others'
+            // bounded waits run out and the call reports BP_ERR_TIMEOUT
+            return;
+        }
         if (recompute_period > 0 && it0 + it > 0 && (it0 + it) % recompute_period == 0) {
             // the activities summed afresh in row order, the compensation cleared, then every
             // violated row's slots
@@ -1000,11 +1007,15 @@ static int ls_run(mip_problem* p, const double* lb, const double* ub, double* x,
         // launches of at most 2^16 iterations: at most four barriers per iteration keep the
         // arrival count (reset between launches) far from 32-bit wrap-around
         DevProblem dp = p->dp;
+        // test-only failure injection: GPUBP_TEST_SKIP_BLOCK=b makes block b leave the search
+        // without arriving at the grid barriers (the failure-detection tests; never set otherwise)
+        const char* skip_env = getenv("GPUBP_TEST_SKIP_BLOCK");
+        int skip = (skip_env && *skip_env) ? atoi(skip_env) : -1;
         for (int done = 0; done < iterations;) {
             int its = iterations - done < 65536 ? iterations - done : 65536;
             int it0 = done, rp = recompute_period;
-            void* args[] = {&dp,        (void*)&lb,  (void*)&ub, &x,   &w,   &L,  &T,    &S,  &perm, &part,
-                            &nbr_row,   &nbr_start,  &long_list, &long_count, &C, &ctl, &it0, &its, &rp};
+            void* args[] = {&dp,        (void*)&lb,  (void*)&ub, &x,   &w,   &L,   &T,   &S,  &perm, &part,
+                            &nbr_row,   &nbr_start,  &long_list, &long_count, &C, &ctl, &it0, &its, &rp, &skip};
             if ((done > 0 && (e = cudaMemsetAsync(&ctl->bar_count, 0, sizeof(unsigned), s)) != cudaSuccess) ||
                 (e = cudaLaunchCooperativeKernel((const void*)k_ls_loop, dim3(grid_select), dim3(kLsLoopThreads), args, 0,
                                                  s)) != cudaSuccess) {

@@ -4,7 +4,8 @@ Every device-side wait of the propagation kernel gives up after a bounded spin a
 BP_ERR_TIMEOUT through the result.  The test makes one block leave the rounds without arriving
 at the grid barrier (a test-only environment variable read at launch), so the other blocks'
 waits run out; the launch must end by itself with that status, and the same handle must then
-propagate correctly.  Nothing faults or traps the device."""
+propagate correctly.  The persistent local search is tested the same way.  Nothing faults or
+traps the device."""
 import time
 
 import numpy as np
@@ -70,3 +71,31 @@ def test_repeated_runs_are_bit_identical(pkg):
     _, _, orr, _ = oracle.Problem(p).bp(p.lb, p.ub)
     if orr["fragile"] == 0:
         assert (r0["status"], r0["rounds"], r0["nnz_updates"]) == (orr["status"], orr["rounds"], orr["nnz_updates"])
+
+
+def test_local_search_barrier_timeout_is_reported_and_the_search_recovers(pkg, monkeypatch):
+    """The persistent local search's grid barriers wait boundedly too: with one block leaving
+    the search without arriving, the call ends by itself with BP_ERR_TIMEOUT, and the same handle
+    then searches exactly as the oracle does."""
+    import torch
+    from oracle import local_mip as lm
+    p = synth.knapsack_cover(seed=91, m=2000, n=4000, nnz=40_000)
+    x0 = np.clip((np.random.default_rng(3).random(p.n) < 0.5).astype(float), p.lb, p.ub)
+    prob = pkg.Problem(p)
+    lb, ub = _dev(p)
+    monkeypatch.setenv("GPUBP_TEST_SKIP_BLOCK", "5")
+    x = torch.tensor(x0, device="cuda")
+    w = torch.ones(p.m, dtype=torch.float64, device="cuda")
+    t0 = time.time()
+    with pytest.raises(pkg.GpuBpError) as err:
+        prob.local_search(lb, ub, x, w, iterations=20)
+    assert err.value.code == pkg.BP_ERR_TIMEOUT
+    assert time.time() - t0 < 60
+    monkeypatch.delenv("GPUBP_TEST_SKIP_BLOCK")
+    x = torch.tensor(x0, device="cuda")
+    w = torch.ones(p.m, dtype=torch.float64, device="cuda")
+    r = prob.local_search(lb, ub, x, w, iterations=20)
+    ox, ow, orr = lm.search(p, p.lb, p.ub, x0, np.ones(p.m), 20)
+    np.testing.assert_array_equal(x.cpu().numpy(), ox)
+    np.testing.assert_array_equal(w.cpu().numpy(), ow)
+    assert r["moves"] == orr["moves"]
