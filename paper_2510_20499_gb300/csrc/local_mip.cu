@@ -30,8 +30,10 @@
 //                     updates, or the weights are to grow (w0 when no row is violated);
 //   k_ls_bump         every violated row's weight grows by 1.
 // Everything stays on the device (no host read per iteration).  The activities start from a
-// thread-per-row sum in row order and are updated in the order of the moves, so the search is
-// bit-for-bit that of a sequential implementation with the same operation order.
+// thread-per-row sum in row order and are updated in the order of the moves as compensated
+// (Kahan) sums, one compensation term per row, summed afresh every recompute_period iterations
+// (Local-MIP's numerics), so the search is bit-for-bit that of a sequential implementation with
+// the same operation order.
 #include <climits>
 #include <cstdlib>
 #include <cmath>
