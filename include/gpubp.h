@@ -463,8 +463,13 @@ void fp_params_default(fp_params *p);   /* seed 1, sqrt rule, last_single 36, fr
  * and with restart_period R > 0 every R iterations the iterate is replaced by the mean of the
  * period's R iterates.  step 0: 0.9 / sqrt(max column |a| sum * max row |a| sum) (a bound on
  * ||A||_2); primal_weight 0: ||c||_2 / ||g||_2 over the finite rows (1 if either is zero).
- * No preconditioning.  Approximate by design: the caller chooses the iterations (the paper
- * limits each projection by time) and reads the KKT measures.
+ * With scaling_iterations K > 0 (PDLP's diagonal preconditioning): K passes of Ruiz
+ * equilibration, each dividing every row factor D_r and column factor D_c by the square root of
+ * the largest scaled |a| = (D_r |a|) D_c of its row or column (both from the same factors); the
+ * iteration then runs on D_r A D_c, D_c c, D_r g, lb / D_c, ub / D_c from x / D_c, y / D_r (the
+ * default step and weight taken on the scaled data), and returns x = D_c x~, y = D_r y~.
+ * Approximate by design: the caller chooses the iterations (the paper limits each projection by
+ * time) and reads the KKT measures (of the original problem).
  *
  * lb, ub:  DEVICE double[n] box (not modified).
  * x:       DEVICE double[n], the primal warm start on entry, the final iterate on return.
@@ -474,7 +479,8 @@ void fp_params_default(fp_params *p);   /* seed 1, sqrt rule, last_single 36, fr
  *          (finite rows), dual residual (norm of the reduced costs c + A^T y that push a
  *          variable toward an infinite bound), primal objective c^T x, dual objective
  *          -g^T y + sum_j min over [lb_j, ub_j] of r_j x_j (finite parts).
- * Scratch: 3 n + 2 m + pieces doubles (plus n + m with restarts), stream-ordered, freed at return.
+ * Scratch: 3 n + 2 m + pieces doubles (plus n + m with restarts, plus 2 nnz + 5 n + 4 m with
+ * scaling), stream-ordered, freed at return.
  * Returns BP_OK, BP_ERR_INVALID (null pointers, negative counts or steps), BP_ERR_OOM or BP_ERR_CUDA.
  */
 typedef struct {
@@ -483,6 +489,8 @@ typedef struct {
     double step;
     double primal_weight;
     const double *objective;   /* DEVICE double[n] in place of the handle's objective, or NULL */
+    int32_t scaling_iterations; /* Ruiz preconditioning passes, 0 for none (0) */
+    int32_t reserved;
 } pdhg_params;
 
 typedef struct {

@@ -72,7 +72,8 @@ class FpResult(C.Structure):
 
 class PdhgParams(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("restart_period", C.c_int32), ("step", C.c_double),
-                ("primal_weight", C.c_double), ("objective", C.c_void_p)]
+                ("primal_weight", C.c_double), ("objective", C.c_void_p), ("scaling_iterations", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class PdhgResult(C.Structure):
@@ -452,12 +453,13 @@ Problem.fix_and_propagate = _fix_and_propagate
 
 
 def _pdhg(prob, lb, ub, x, y, iterations=1000, restart_period=100, step=0.0, primal_weight=0.0, objective=None,
-          stream=None):
+          scaling_iterations=0, stream=None):
     """pdhg_solve (the approximate LP) on device tensors: lb, ub (n), x (n) and y (m) float64; x
     and y are the warm start and receive the final iterate; objective: a float64 device tensor in
-    place of the handle's objective, or None.  Returns the result dict."""
+    place of the handle's objective, or None; scaling_iterations: Ruiz passes (0: none).
+    Returns the result dict."""
     prm = PdhgParams(int(iterations), int(restart_period), float(step), float(primal_weight),
-                     objective.data_ptr() if objective is not None else None)
+                     objective.data_ptr() if objective is not None else None, int(scaling_iterations), 0)
     res = PdhgResult()
     _check(lib().pdhg_solve(prob.h, _ptr(lb), _ptr(ub), _ptr(x), _ptr(y), C.byref(prm), C.byref(res),
                             _stream(stream)))

@@ -173,6 +173,83 @@ __global__ void __launch_bounds__(kPdThreads) k_pdhg_long(DevProblem P, PdhgVecs
     }
 }
 
+// ---------------------------------------------------------------- Ruiz preconditioning
+// A pass computes the largest scaled |a| = (D_r |a|) D_c of every row (a warp per row) and of
+// every column (a thread per column over the transpose) from the same factors, then divides
+// each factor by the square root of its maximum (factor kept where the maximum is 0).
+__global__ void __launch_bounds__(kPdThreads) k_ruiz_rows(DevProblem P, const double* __restrict__ Dr,
+                                                          const double* __restrict__ Dc, double* __restrict__ R) {
+    const int lane = threadIdx.x & 31;
+    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < P.m; k += (gridDim.x * blockDim.x) >> 5) {
+        double mx = 0.0;
+        for (int q = P.row_ptr[k] + lane; q < P.row_ptr[k + 1]; q += 32)
+            mx = fmax(mx, __dmul_rn(__dmul_rn(Dr[k], fabs(P.val[q])), Dc[P.col[q]]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) R[k] = mx;
+    }
+}
+
+__global__ void __launch_bounds__(kPdThreads) k_ruiz_cols(DevProblem P, const double* __restrict__ Dr,
+                                                          const double* __restrict__ Dc, double* __restrict__ C) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < P.n; j += gridDim.x * blockDim.x) {
+        double mx = 0.0;
+        for (int c = P.col_ptr[j]; c < P.col_ptr[j + 1]; ++c)
+            mx = fmax(mx, __dmul_rn(__dmul_rn(Dr[P.row_idx[c]], fabs(P.col_val[c])), Dc[j]));
+        C[j] = mx;
+    }
+}
+
+__global__ void k_ruiz_update(int cnt, double* __restrict__ D, const double* __restrict__ M) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x)
+        if (M[i] > 0.0) D[i] = __ddiv_rn(D[i], sqrt(M[i]));
+}
+
+// the scaled matrix (D_r a) D_c in both layouts, the scaled right-hand sides D_r g
+__global__ void __launch_bounds__(kPdThreads) k_scale_rows(DevProblem P, const double* __restrict__ Dr,
+                                                           const double* __restrict__ Dc, double* __restrict__ sval,
+                                                           double2* __restrict__ sgrow) {
+    const int lane = threadIdx.x & 31;
+    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < P.m; k += (gridDim.x * blockDim.x) >> 5) {
+        for (int q = P.row_ptr[k] + lane; q < P.row_ptr[k + 1]; q += 32)
+            sval[q] = __dmul_rn(__dmul_rn(Dr[k], P.val[q]), Dc[P.col[q]]);
+        if (lane == 0) {
+            const double g = __dmul_rn(Dr[k], P.grow[k].x);
+            sgrow[k] = make_double2(g, g);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kPdThreads) k_scale_cols(DevProblem P, const double* __restrict__ Dr,
+                                                           const double* __restrict__ Dc, double* __restrict__ scol) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < P.n; j += gridDim.x * blockDim.x)
+        for (int c = P.col_ptr[j]; c < P.col_ptr[j + 1]; ++c)
+            scol[c] = __dmul_rn(__dmul_rn(Dr[P.row_idx[c]], P.col_val[c]), Dc[j]);
+}
+
+// D_c c, l / D_c, u / D_c and the warm start x / D_c
+__global__ void k_scale_cvecs(int n, const double* __restrict__ Dc, const double* __restrict__ c,
+                              const double* __restrict__ l, const double* __restrict__ u, double* __restrict__ cs,
+                              double* __restrict__ ls, double* __restrict__ us, double* __restrict__ x) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const double d = Dc[j];
+        cs[j] = __dmul_rn(d, c[j]);
+        ls[j] = __ddiv_rn(l[j], d);
+        us[j] = __ddiv_rn(u[j], d);
+        x[j] = __ddiv_rn(x[j], d);
+    }
+}
+
+// v = v / D (into the scaled space) or v = D v (back)
+__global__ void k_scale_vec(int cnt, const double* __restrict__ D, double* __restrict__ v, int back) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x)
+        v[i] = back ? __dmul_rn(D[i], v[i]) : __ddiv_rn(v[i], D[i]);
+}
+
+__global__ void k_pdhg_fill(int cnt, double v, double* __restrict__ a) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) a[i] = v;
+}
+
 // restart: (x, y) = (xs, ys) / R, sums cleared
 __global__ void k_pdhg_restart(int n, int m, double r, double* x, double* y, double* xs, double* ys) {
     const int stride = gridDim.x * blockDim.x;
@@ -302,6 +379,8 @@ extern "C" void pdhg_params_default(pdhg_params* p) {
     p->step = 0.0;
     p->primal_weight = 0.0;
     p->objective = nullptr;
+    p->scaling_iterations = 0;
+    p->reserved = 0;
 }
 
 extern "C" int pdhg_solve(mip_problem* p, const double* lb, const double* ub, double* x, double* y,
@@ -313,7 +392,8 @@ extern "C" int pdhg_solve(mip_problem* p, const double* lb, const double* ub, do
     pdhg_params prm;
     if (params) prm = *params;
     else pdhg_params_default(&prm);
-    if (prm.iterations < 0 || prm.restart_period < 0 || !(prm.step >= 0.0) || !(prm.primal_weight >= 0.0)) {
+    if (prm.iterations < 0 || prm.restart_period < 0 || !(prm.step >= 0.0) || !(prm.primal_weight >= 0.0) ||
+        prm.scaling_iterations < 0) {
         set_error("pdhg_solve: invalid parameters");
         return BP_ERR_INVALID;
     }
@@ -365,10 +445,49 @@ extern "C" int pdhg_solve(mip_problem* p, const double* lb, const double* ub, do
         PD_CUDA(cudaMemsetAsync(ys, 0, sizeof(double) * (size_t)m, s));
     }
     double hs[5];
+    // Ruiz preconditioning: the iteration runs on the scaled problem (Ps, cv, lv, uv) from the
+    // scaled warm start; the final measures use the original one
+    DevProblem Ps = p->dp;
+    const double *cv = cobj, *lv = lb, *uv = ub;
+    double *Dr = nullptr, *Dc = nullptr;
+    const int K = prm.scaling_iterations;
+    if (K > 0) {
+        double *R, *Cm, *sval, *scol, *sgrow, *cs, *ls, *us;
+        PD_TRY(alloc(&Dr, (size_t)m));
+        PD_TRY(alloc(&Dc, (size_t)n));
+        PD_TRY(alloc(&R, (size_t)m));
+        PD_TRY(alloc(&Cm, (size_t)n));
+        PD_TRY(alloc(&sval, (size_t)p->nnz));
+        PD_TRY(alloc(&scol, (size_t)p->nnz));
+        PD_TRY(alloc(&sgrow, 2 * (size_t)m));
+        PD_TRY(alloc(&cs, (size_t)n));
+        PD_TRY(alloc(&ls, (size_t)n));
+        PD_TRY(alloc(&us, (size_t)n));
+        const int gr = p->sms * 8;
+        k_pdhg_fill<<<gr, kPdThreads, 0, s>>>(m, 1.0, Dr);
+        k_pdhg_fill<<<gr, kPdThreads, 0, s>>>(n, 1.0, Dc);
+        for (int k = 0; k < K; ++k) {
+            k_ruiz_rows<<<gr, kPdThreads, 0, s>>>(p->dp, Dr, Dc, R);
+            k_ruiz_cols<<<gr, kPdThreads, 0, s>>>(p->dp, Dr, Dc, Cm);
+            k_ruiz_update<<<gr, kPdThreads, 0, s>>>(m, Dr, R);
+            k_ruiz_update<<<gr, kPdThreads, 0, s>>>(n, Dc, Cm);
+        }
+        k_scale_rows<<<gr, kPdThreads, 0, s>>>(p->dp, Dr, Dc, sval, reinterpret_cast<double2*>(sgrow));
+        k_scale_cols<<<gr, kPdThreads, 0, s>>>(p->dp, Dr, Dc, scol);
+        k_scale_cvecs<<<gr, kPdThreads, 0, s>>>(n, Dc, cobj, lb, ub, cs, ls, us, x);
+        k_scale_vec<<<gr, kPdThreads, 0, s>>>(m, Dr, y, 0);
+        PD_CUDA(cudaGetLastError());
+        Ps.val = sval;
+        Ps.col_val = scol;
+        Ps.grow = reinterpret_cast<const double2*>(sgrow);
+        cv = cs;
+        lv = ls;
+        uv = us;
+    }
     // step and primal weight
     double eta = prm.step, omega = prm.primal_weight;
     if (eta == 0.0 || omega == 0.0) {
-        k_pdhg_norms<<<kPdRedBlocks, kPdThreads, 0, s>>>(p->dp, cobj, red);
+        k_pdhg_norms<<<kPdRedBlocks, kPdThreads, 0, s>>>(Ps, cv, red);
         k_pdhg_finish<<<1, kPdThreads, 0, s>>>(red, kPdRedBlocks, 1, sums);
         PD_CUDA(cudaGetLastError());
         PD_CUDA(cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, s));
@@ -379,7 +498,8 @@ extern "C" int pdhg_solve(mip_problem* p, const double* lb, const double* ub, do
             omega = (nc > 0.0 && ng > 0.0) ? nc / ng : 1.0;
         }
     }
-    PdhgVecs V{cobj, lb, ub, eta / omega, eta * omega};
+    PdhgVecs V{cv, lv, uv, eta / omega, eta * omega};
+    const PdhgVecs V0{cobj, lb, ub, eta / omega, eta * omega};   // the original problem's vectors
     // grids of resident blocks (every block stays resident through its grid-stride loop)
     static int occ[3] = {-1, -1, -1};
     if (occ[0] < 0) {
@@ -392,9 +512,9 @@ extern "C" int pdhg_solve(mip_problem* p, const double* lb, const double* ub, do
     double *xc = x, *xo = xn, *yc = y, *yo = yn;
     int restarts_done = 0;
     for (int it = 0; it < prm.iterations; ++it) {
-        k_pdhg_cols<<<grid_c, kPdThreads, 0, s>>>(p->dp, V, xc, yc, xo, xe, xs, 0);
-        k_pdhg_rows<<<grid, kPdThreads, 0, s>>>(p->dp, V, xe, yc, yo, ys, part, 0);
-        if (np_) k_pdhg_long<<<grid_l, kPdThreads, 0, s>>>(p->dp, V, part, yc, yo, ys, 0);
+        k_pdhg_cols<<<grid_c, kPdThreads, 0, s>>>(Ps, V, xc, yc, xo, xe, xs, 0);
+        k_pdhg_rows<<<grid, kPdThreads, 0, s>>>(Ps, V, xe, yc, yo, ys, part, 0);
+        if (np_) k_pdhg_long<<<grid_l, kPdThreads, 0, s>>>(Ps, V, part, yc, yo, ys, 0);
         std::swap(xc, xo);
         std::swap(yc, yo);
         if (restarts && (it + 1) % prm.restart_period == 0) {
@@ -405,10 +525,14 @@ extern "C" int pdhg_solve(mip_problem* p, const double* lb, const double* ub, do
     PD_CUDA(cudaGetLastError());
     if (xc != x && n) PD_CUDA(cudaMemcpyAsync(x, xc, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
     if (yc != y && m) PD_CUDA(cudaMemcpyAsync(y, yc, sizeof(double) * (size_t)m, cudaMemcpyDeviceToDevice, s));
-    // KKT measures of the final iterate: A x into yn, c + A^T y into xn
-    k_pdhg_rows<<<grid, kPdThreads, 0, s>>>(p->dp, V, x, y, yn, nullptr, part, 1);
-    if (np_) k_pdhg_long<<<grid_l, kPdThreads, 0, s>>>(p->dp, V, part, y, yn, nullptr, 1);
-    k_pdhg_cols<<<grid_c, kPdThreads, 0, s>>>(p->dp, V, x, y, xn, xe, nullptr, 1);
+    if (K > 0) {   // back to the original variables: x = D_c x~, y = D_r y~
+        k_scale_vec<<<p->sms * 8, kPdThreads, 0, s>>>(n, Dc, x, 1);
+        k_scale_vec<<<p->sms * 8, kPdThreads, 0, s>>>(m, Dr, y, 1);
+    }
+    // KKT measures of the final iterate (original problem): A x into yn, c + A^T y into xn
+    k_pdhg_rows<<<grid, kPdThreads, 0, s>>>(p->dp, V0, x, y, yn, nullptr, part, 1);
+    if (np_) k_pdhg_long<<<grid_l, kPdThreads, 0, s>>>(p->dp, V0, part, y, yn, nullptr, 1);
+    k_pdhg_cols<<<grid_c, kPdThreads, 0, s>>>(p->dp, V0, x, y, xn, xe, nullptr, 1);
     k_pdhg_kkt<<<kPdRedBlocks, kPdThreads, 0, s>>>(p->dp, cobj, lb, ub, x, y, yn, xn, red);
     k_pdhg_finish<<<1, kPdThreads, 0, s>>>(red, kPdRedBlocks, 0, sums);
     PD_CUDA(cudaGetLastError());

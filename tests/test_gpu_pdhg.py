@@ -131,3 +131,23 @@ def test_repeatable_and_validated(pkg):
     assert np.array_equal(x1, x2) and np.array_equal(y1, y2) and r1 == r2
     with pytest.raises(Exception):
         _gpu(pkg, p, p.lb, p.ub, np.zeros(p.n), np.zeros(p.m), iterations=-1)
+
+
+@pytest.mark.parametrize("seed,restart", [(44, 50), (45, 0)])
+def test_scaled_matches_oracle(pkg, seed, restart):
+    """Ruiz preconditioning (10 passes): the scaling factors are formed in the oracle's order
+    with correctly rounded square roots, the iteration runs on the scaled data; x, y, the step,
+    the weight and the KKT measures of the original problem agree with the oracle."""
+    p = _lp(seed, 3000, 8000, 60_000, 3000)
+    rng = np.random.default_rng(seed)
+    x0 = np.clip(rng.normal(0, 5, p.n), p.lb, p.ub)
+    y0 = np.abs(rng.normal(0, 0.01, p.m))
+    kw = dict(iterations=300, restart_period=restart, scaling_iterations=10)
+    ox, oy, orr = _compare(p, x0, y0, **kw)
+    gx, gy, gr = _gpu(pkg, p, p.lb, p.ub, x0, y0, **kw)
+    assert abs(gr["step"] - orr["step"]) <= 1e-13 * orr["step"]
+    assert abs(gr["primal_weight"] - orr["primal_weight"]) <= 1e-13 * orr["primal_weight"]
+    _close(gx, ox)
+    _close(gy, oy)
+    for k in ("primal_obj", "dual_obj", "primal_residual", "dual_residual"):
+        assert abs(gr[k] - orr[k]) <= 1e-8 * max(1.0, abs(orr[k])), (k, gr[k], orr[k])
