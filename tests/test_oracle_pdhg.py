@@ -187,3 +187,16 @@ def test_zero_scaling_passes_are_the_plain_solver():
                    scaling_iterations=0)
     np.testing.assert_array_equal(a[0], b[0])
     np.testing.assert_array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_scaled_warm_start_from_the_optimum_stays(seed):
+    """Warm-started at HiGHS's optimal pair, the scaled iteration stays there: the warm start is
+    carried into the scaled space (x*/D_c, y*/D_r, a fixed point) and back."""
+    pytest.importorskip("scipy")
+    p = _badly_scaled_lp(160 + seed)
+    x_star, y_star, f_star = _highs(p)
+    x, y, r = pdhg.solve(p, p.lb, p.ub, x_star, y_star, iterations=50, restart_period=10, scaling_iterations=10)
+    np.testing.assert_allclose(x, x_star, atol=1e-6 * (1 + np.abs(x_star).max()))
+    np.testing.assert_allclose(y, y_star, atol=1e-6 * (1 + np.abs(y_star).max()))
+    assert abs(r["primal_obj"] - f_star) <= 1e-6 * (1 + abs(f_star))
