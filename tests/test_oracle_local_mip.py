@@ -266,3 +266,29 @@ def test_recompute_changes_nothing_on_integer_data():
     b = lm.search(p, p.lb, p.ub, x0, np.ones(p.m), 40, recompute_period=7)
     np.testing.assert_array_equal(a[0], b[0])
     np.testing.assert_array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("objective", [False, True])
+def test_moves_update_activities_through_the_compensated_add(objective, monkeypatch):
+    """Every activity update of a move is a compensated add: one per nonzero of the moved
+    variable's column, in both searches."""
+    p = _problem(350)
+    p.c = np.random.default_rng(1).integers(-3, 4, p.n).astype(float)
+    x0 = np.clip(np.round(np.random.default_rng(2).normal(0, 3, p.n)), p.lb, p.ub)
+    calls = []
+    real = lm.kahan_add
+
+    def counting(L, C, r, inc):
+        calls.append(r)
+        real(L, C, r, inc)
+
+    monkeypatch.setattr(lm, "kahan_add", counting)
+    cols = lm._csc(p)
+    if objective:
+        x, w, best, r = lm.search_objective(p, p.lb, p.ub, x0, np.ones(p.m), 40)
+    else:
+        x, w, r = lm.search(p, p.lb, p.ub, x0, np.ones(p.m), 40)
+    assert r["moves"] > 0
+    moved = np.flatnonzero(x != x0)
+    assert len(calls) >= sum(len(cols[j]) for j in moved)
+    assert set(calls) <= {k for j in range(p.n) for k, _ in cols[j]}
