@@ -331,3 +331,48 @@ def test_block_diagonal_pair_propagates_each_copy_alone(seed):
     assert R["status"] == oracle.FIXPOINT
     assert R["nnz_updates"] == alone[0][2]["nnz_updates"] + alone[1][2]["nnz_updates"]
     assert R["rounds"] == max(alone[0][2]["rounds"], alone[1][2]["rounds"])
+
+
+# --- hand-worked readings at the edges of the tolerances and of the infinity counts ---
+
+
+def test_row_violation_within_the_tolerance_is_feasible():
+    """Row infeasibility is L_min > g + 1e-6 (Section 3's tolerance): x0 <= -5e-7 with x0 in
+    [0, 1] has L_min = 0, within the tolerance of g, so it is not infeasible; x0 <= -2e-6 is."""
+    lb, ub = np.array([0.0]), np.array([1.0])
+    p = milp_from_dense([[1.0]], [-5e-7], lb, ub, [0])
+    ol, ou, r, _ = oracle.Problem(p).bp(lb, ub)
+    assert r["status"] == oracle.FIXPOINT
+    p = milp_from_dense([[1.0]], [-2e-6], lb, ub, [0])
+    _, _, r, _ = oracle.Problem(p).bp(lb, ub)
+    assert r["status"] == oracle.INFEASIBLE and r["first_infeasible_row"] == 0
+
+
+def test_two_infinite_contributions_propose_no_bound():
+    """x0 + x1 + x2 <= 5 with x0, x1 unbounded below: L_min has two infinite contributions, so no
+    residual is finite and x2 in [0, 10] keeps its bounds (with one, x2 would get u = 5 - ...)."""
+    lb = np.array([-np.inf, -np.inf, 0.0])
+    ub = np.array([10.0, 10.0, 10.0])
+    p = milp_from_dense([[1.0, 1.0, 1.0]], [5.0], lb, ub, [0, 0, 0])
+    ol, ou, r, _ = oracle.Problem(p).bp(lb, ub)
+    np.testing.assert_array_equal(ol, lb)
+    np.testing.assert_array_equal(ou, ub)
+    assert r["rounds"] == 1 and r["n_changed"] == 0
+    # one infinite contribution: only the infinite variable gets a bound, 5 - L_min(others)
+    lb1 = np.array([-np.inf, 0.0, 0.0])
+    p = milp_from_dense([[1.0, 1.0, 1.0]], [5.0], lb1, ub, [0, 0, 0])
+    ol, ou, r, _ = oracle.Problem(p).bp(lb1, ub)
+    np.testing.assert_array_equal(ou, [5.0, 10.0, 10.0])
+
+
+def test_continuous_threshold_uses_at_least_one():
+    """A continuous bound moves only when the improvement exceeds theta * max(1, |bound|):
+    x0 <= 0.4993 with x0 in [0, 0.5] improves u by 7e-4 < 1e-3 * max(1, 0.5), so nothing moves
+    (theta * |u| = 5e-4 would have accepted it); x0 <= 0.4985 (1.5e-3) moves u."""
+    lb, ub = np.array([0.0]), np.array([0.5])
+    p = milp_from_dense([[1.0]], [0.4993], lb, ub, [0])
+    ol, ou, r, _ = oracle.Problem(p).bp(lb, ub)
+    assert ou[0] == 0.5 and r["n_changed"] == 0
+    p = milp_from_dense([[1.0]], [0.4985], lb, ub, [0])
+    ol, ou, r, _ = oracle.Problem(p).bp(lb, ub)
+    assert ou[0] == 0.4985
