@@ -278,3 +278,25 @@ def test_final_check_refutes_an_incremental_verdict():
     lo[:2] = hi[:2] = 1.0
     _, _, rb, _ = P.bp(lo, hi)
     assert rb["status"] == oracle.INFEASIBLE and rb["first_infeasible_row"] == 3 and rb["rounds"] == 2
+
+
+def test_last_single_boundary():
+    """Exactly last_single = 36 remaining variables are fixed one per bulk (36 bulks); 37 take
+    one bulk of ceil(sqrt(37)) = 7 and then 30 singles (31 bulks)."""
+    for n, want in ((36, 36), (37, 31)):
+        p = milp_from_dense(np.zeros((0, n)), [], np.zeros(n), np.ones(n), np.ones(n))
+        _, r = oracle.Problem(p).fix_and_propagate(np.full(n, 0.5), p.lb, p.ub)
+        assert r["bulks"] == want, (n, r["bulks"])
+
+
+def test_ternary_class_before_general_integers():
+    """The initial order puts a ternary variable (u - l = 2) before a general integer whatever
+    their fractionality (Section 2.3: binary and ternary first).  z in [0, 2] at 1.8, v in [0, 5]
+    at 4.9, z + v <= 5 (the start propagation changes nothing): z goes first and rounds up to 2
+    (fraction 0.8), propagation gives v <= 3, and v's upward rounding is clamped to 3: (2, 3).
+    Ordered by fractionality alone, v (0.1 from an integer) would go first: v = 5 and
+    propagation fixes z = 0."""
+    p = milp_from_dense(np.array([[1.0, 1.0]]), [5.0], np.array([0.0, 0.0]), np.array([2.0, 5.0]), np.ones(2))
+    out, r = oracle.Problem(p).fix_and_propagate(np.array([1.8, 4.9]), p.lb, p.ub)
+    np.testing.assert_array_equal(out, [2.0, 3.0])
+    assert r["status"] == 0
