@@ -206,3 +206,27 @@ def test_probe_cache_apply_brute_force(seed):
         assert len(pts) == 0
     else:
         assert ((pts >= l) & (pts <= u)).all()
+
+
+def test_priority_flip_uses_the_tolerance():
+    """Key 1 counts rows whose flipped activity L_min + |a| (u - l) exceeds g + 1e-6 (reading
+    R11 with Section 3's tolerance): x0 in {0, 1} with rows x0 <= 1 - 5e-7 and -x0 <= 0 (both
+    signs): the first flips to 1, within the tolerance of g, so neither row counts."""
+    A = np.array([[1.0, 0.0], [-1.0, 0.0]])
+    lb, ub = np.array([0.0, 0.0]), np.array([1.0, 1.0])
+    p = milp_from_dense(A, [1.0 - 5e-7, 0.0], lb, ub, [1, 0])
+    k1, k2, k3 = oracle.Problem(p).probe_priority(lb, ub)
+    assert k1[0] == 0 and k2[0] == 0.0
+    p = milp_from_dense(A, [1.0 - 2e-6, 0.0], lb, ub, [1, 0])   # beyond the tolerance: counted
+    k1, k2, k3 = oracle.Problem(p).probe_priority(lb, ub)
+    assert k1[0] == 1 and abs(k2[0] - 2e-6) < 1e-15
+
+
+def test_priority_ignores_rows_with_an_infinite_minimal_activity():
+    """x0 in [0, 3] integer, y unbounded below, x0 + y <= 4: the row's L_min is -inf, so it takes
+    no part and x0's smallest unit slack stays +inf (counted, it would be 4)."""
+    lb, ub = np.array([0.0, -np.inf]), np.array([3.0, 5.0])
+    p = milp_from_dense(np.array([[1.0, 1.0]]), [4.0], lb, ub, [1, 0])
+    k1, k2, k3 = oracle.Problem(p).probe_priority(lb, ub)
+    assert k1[0] == 0 and k3[0] == np.inf
+    assert k1[1] == -1   # continuous: not probeable
