@@ -179,3 +179,17 @@ def test_brute_force_planted_dead_ends():
         tried += r1["repair_runs"] > 0
         helped += r0["status"] == 1 and r1["status"] == 0
     assert helped >= 3 and tried > helped, (helped, tried)
+
+
+def test_repair_step_skips_a_row_with_an_infinite_minimal_activity():
+    """A target row whose minimal activity is -inf (an unbounded-below variable in it) is not
+    violated, so no fixing shifts: x0 + y <= 1 with x0 chosen at 5 in [0, 10] and y unbounded
+    below (counting only x0's finite part, the row would look violated by 4)."""
+    lb = np.array([0.0, -np.inf])
+    ub = np.array([10.0, 10.0])
+    p = milp_from_dense([[1.0, 1.0]], [1.0], lb, ub, [1, 0])
+    l = np.array([5.0, -np.inf])
+    u = np.array([5.0, 10.0])
+    moved, cval, fragile = oracle.Problem(p).repair_step(l, u, 0, -1, lb, ub, [1, 0], [5.0, 0.0])
+    assert moved == -1
+    np.testing.assert_array_equal(cval, [5.0, 0.0])
