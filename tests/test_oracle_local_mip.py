@@ -292,3 +292,18 @@ def test_moves_update_activities_through_the_compensated_add(objective, monkeypa
     moved = np.flatnonzero(x != x0)
     assert len(calls) >= sum(len(cols[j]) for j in moved)
     assert set(calls) <= {k for j in range(p.n) for k, _ in cols[j]}
+
+
+def test_equal_scores_on_one_variable_take_the_smaller_value():
+    """x0 integer in [0, 10] at 10, rows x0 <= 8, x0 <= 7, -x0 <= -8: the first row proposes 8
+    (drops 2 + 2), the second 7 (drops 2 + 3, then breaks the third by 1): both score 4, and
+    the tie goes to the smaller value, 7."""
+    p = milp_from_dense([[1.0], [1.0], [-1.0]], [8.0, 7.0, -8.0], [0.0], [10.0], [1])
+    p.c = np.zeros(1)
+    L = lm.activities(p, np.array([10.0]))
+    cols = lm._csc(p)
+    cands = lm.candidates(p, np.array([10.0]), L, p.lb, p.ub)
+    assert [(k, t) for k, _, t in cands] == [(0, 8.0), (1, 7.0)]
+    assert {lm.score(cols, p.g, np.ones(3), np.array([10.0]), L, 0, t) for _, _, t in cands} == {4.0}
+    x, w, r = lm.search(p, p.lb, p.ub, [10.0], np.ones(3), 1)
+    assert x[0] == 7.0 and r["moves"] == 1
