@@ -40,6 +40,26 @@ def test_forward_closed_form():
     np.testing.assert_array_equal(Z3[:, 1], X.sum(axis=1) - 0.25)
 
 
+def test_forward_rounds_both_hidden_layers_to_bf16():
+    """Each hidden layer is rounded to BF16 (8 significant bits) before the next layer: with
+    x_0 = 1, W1[0, 0] = 1 and b1[0] = 2^-10, H1[0] = bf16(1 + 2^-10) = 1; with W2[0, 0] = 1 and
+    b2[0] = 2^-10, H2[0] = bf16(1 + 2^-10) = 1 again; W3[0, 0] = 1 then gives Z3[0] = 1 exactly
+    (without either rounding it would be 1 + 2^-10 or 1 + 2^-9)."""
+    d = {name: np.zeros(shape) for name, shape in mlp.SHAPES}
+    d["W1"][0, 0] = 1.0
+    d["b1"][0] = 2.0 ** -10
+    d["W2"][0, 0] = 1.0
+    d["b2"][0] = 2.0 ** -10
+    d["W3"][0, 0] = 1.0
+    X = np.zeros((1, 16))
+    X[0, 0] = 1.0
+    Z3, cache = mlp.forward(mlp.pack(d), X)
+    assert cache["H1"][0, 0] == 1.0 and cache["H2"][0, 0] == 1.0
+    assert Z3[0, 0] == 1.0
+    Zf, _ = mlp.forward(mlp.pack(d), X, quantize=False)
+    assert Zf[0, 0] == 1.0 + 2.0 ** -9
+
+
 def test_loss_values():
     Z3 = np.zeros((4, 2))
     Y = np.array([[1, 0], [0, np.nan], [np.nan, np.nan], [1, 1]], dtype=float)
