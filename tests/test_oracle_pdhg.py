@@ -200,3 +200,14 @@ def test_scaled_warm_start_from_the_optimum_stays(seed):
     np.testing.assert_allclose(x, x_star, atol=1e-6 * (1 + np.abs(x_star).max()))
     np.testing.assert_allclose(y, y_star, atol=1e-6 * (1 + np.abs(y_star).max()))
     assert abs(r["primal_obj"] - f_star) <= 1e-6 * (1 + abs(f_star))
+
+
+def test_default_step_and_weight_hand_example():
+    """Reading R30's defaults on a hand example: A = [[1, 2], [3, 4]] has largest column |a| sum
+    6 and largest row sum 7, so eta = 0.9 / sqrt(42) = 0.138873...; c = (3, 4) and g = (12, +inf)
+    give omega = ||c|| / ||g over finite rows|| = 5 / 12 (the free row takes no part)."""
+    import scipy.sparse as sp
+    eta = pdhg.default_step(sp.csr_matrix(np.array([[1.0, 2.0], [3.0, 4.0]])))
+    assert abs(eta - 0.13887301496588270) < 1e-15
+    assert pdhg.default_weight(np.array([3.0, 4.0]), np.array([12.0, np.inf])) == 5.0 / 12.0
+    assert pdhg.default_weight(np.array([3.0, 4.0]), np.array([np.inf, np.inf])) == 1.0
