@@ -32,6 +32,8 @@ def test_cycle_rule():
     assert not efp.cycle(h, 7.0 - 0.71, 3, 0.1)         # mean 8: improves by 1.71 > 0.8
     assert efp.cycle(h, 7.2, 3, 0.1)                    # improves by 0.8 <= 0.1 * 8
     assert efp.cycle(h, 9.0, 3, 0.1)                    # worse than the mean
+    assert efp.cycle([10.0, 10.0, 10.0], 9.0, 3, 0.1)   # improves by exactly 10% of the mean: a cycle
+    assert efp.cycle([100.0, 10.0, 10.0, 10.0], 9.5, 3, 0.1)   # the mean of the last N only (10, not 32.5)
 
 
 @pytest.mark.parametrize("seed", range(4))
