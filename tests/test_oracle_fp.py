@@ -300,3 +300,62 @@ def test_ternary_class_before_general_integers():
     out, r = oracle.Problem(p).fix_and_propagate(np.array([1.8, 4.9]), p.lb, p.ub)
     np.testing.assert_array_equal(out, [2.0, 3.0])
     assert r["status"] == 0
+
+
+# --- the probing cache inside a bulk (Section 2.2 and 2.3, readings R15 and R16), hand-made caches ---
+
+
+def _cache(pairs, boxes, status, entries):
+    """A probing cache written by hand: `entries[b]` lists (var, l, u) for branch b (2i: down,
+    2i + 1: up of pair i)."""
+    off, var, lo, hi = [0], [], [], []
+    for b in range(2 * len(pairs)):
+        for w, l, u in entries.get(b, []):
+            var.append(w)
+            lo.append(l)
+            hi.append(u)
+        off.append(len(var))
+    return {"pairs": np.array(pairs, dtype=np.int32), "boxes": np.array(boxes, dtype=float),
+            "status": np.array(status, dtype=np.int32), "offsets": np.array(off, dtype=np.int64),
+            "var": np.array(var, dtype=np.int32), "l": np.array(lo, dtype=float), "u": np.array(hi, dtype=float)}
+
+
+def test_cache_infeasible_branch_drops_the_fixing():
+    """Two free binaries, no rows; x0 at 0.9 rounds up, but the cache marks x0 = 1 infeasible:
+    that fixing is dropped, the other neighbour x0 = 0 is kept."""
+    p = milp_from_dense(np.zeros((0, 2)), [], np.zeros(2), np.ones(2), np.ones(2))
+    cache = _cache([0], [[0, 0, 1, 1]], [0, 1], {})
+    out, r = oracle.Problem(p).fix_and_propagate(np.array([0.9, 0.1]), p.lb, p.ub, cache=cache)
+    np.testing.assert_array_equal(out, [0.0, 0.0])
+    out, r = oracle.Problem(p).fix_and_propagate(np.array([0.9, 0.1]), p.lb, p.ub)
+    np.testing.assert_array_equal(out, [1.0, 0.0])       # without the cache it rounds up
+
+
+def test_cache_implications_warm_start_the_fixing():
+    """The cache says x0 = 1 implies x1 = 1: fixing x0 = 1 starts from x1 in [1, 1], so x1 (at
+    0.1, which alone rounds down) ends at 1."""
+    p = milp_from_dense(np.zeros((0, 2)), [], np.zeros(2), np.ones(2), np.ones(2))
+    cache = _cache([0], [[0, 0, 1, 1]], [0, 0], {1: [(1, 1.0, 1.0)]})
+    out, r = oracle.Problem(p).fix_and_propagate(np.array([0.9, 0.1]), p.lb, p.ub, cache=cache)
+    np.testing.assert_array_equal(out, [1.0, 1.0])
+
+
+def test_cache_implication_that_empties_a_domain_drops_the_fixing():
+    """The cache says x0 = 1 implies x1 = 1 while x1 is fixed at 0: the implication leaves x1
+    no value, so the fixing x0 = 1 is dropped before any propagation: two propagation runs (the
+    start and the kept candidate x0 = 0) where trying it would take three."""
+    lb, ub = np.zeros(2), np.array([1.0, 0.0])
+    p = milp_from_dense(np.zeros((0, 2)), [], lb, ub, np.ones(2))
+    cache = _cache([0], [[0, 0, 1, 1]], [0, 0], {1: [(1, 1.0, 1.0)]})
+    out, r = oracle.Problem(p).fix_and_propagate(np.array([0.9, 0.0]), lb, ub, cache=cache)
+    np.testing.assert_array_equal(out, [0.0, 0.0])
+    assert r["bp_runs"] == 2 and r["status"] == 0
+
+
+def test_continuous_values_are_clamped_to_the_final_bounds():
+    """x0 binary at 0.9 rounds up; x0 + y <= 1 then gives y <= 0, so the continuous y given at 3
+    is returned as 0."""
+    lb, ub = np.zeros(2), np.array([1.0, 5.0])
+    p = milp_from_dense(np.array([[1.0, 1.0]]), [1.0], lb, ub, np.array([1, 0]))
+    out, r = oracle.Problem(p).fix_and_propagate(np.array([0.9, 3.0]), lb, ub)
+    np.testing.assert_array_equal(out, [1.0, 0.0])
