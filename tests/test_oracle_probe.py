@@ -230,3 +230,25 @@ def test_priority_ignores_rows_with_an_infinite_minimal_activity():
     k1, k2, k3 = oracle.Problem(p).probe_priority(lb, ub)
     assert k1[0] == 0 and k3[0] == np.inf
     assert k1[1] == -1   # continuous: not probeable
+
+
+def test_branch_starts_from_root_intersected_with_its_box():
+    """A branch runs from root ∩ box (reading of Section 2.2's double probe): x0 integer with
+    root [1, 3] and a down box [0, 1] starts the branch at [1, 1], so the cache lists x0 with
+    l = 1 (unchanged) and u = 1, never the box's l = 0."""
+    lb, ub = np.array([1.0, 0.0]), np.array([3.0, 5.0])
+    p = milp_from_dense(np.array([[1.0, 1.0]]), [6.0], lb, ub, [1, 1])
+    c = oracle.Problem(p).probe_batch(lb, ub, np.array([0], dtype=np.int32), np.array([[0.0, 1.0, 2.0, 3.0]]))
+    b = slice(int(c["offsets"][0]), int(c["offsets"][1]))
+    ents = {int(v): (l, u) for v, l, u in zip(c["var"][b], c["l"][b], c["u"][b])}
+    assert c["status"][0] == oracle.FIXPOINT and ents[0] == (1.0, 1.0)
+
+
+def test_infeasible_branch_lists_nothing():
+    """x0 + x1 <= 1 with x1 fixed at 1: the up branch of x0 ([1, 1]) is infeasible and lists no
+    implied bounds; the down branch is feasible and lists x0 = 0."""
+    lb, ub = np.array([0.0, 1.0]), np.array([1.0, 1.0])
+    p = milp_from_dense(np.array([[1.0, 1.0]]), [1.0], lb, ub, [1, 1])
+    c = oracle.Problem(p).probe_batch(lb, ub, np.array([0], dtype=np.int32), np.array([[0.0, 0.0, 1.0, 1.0]]))
+    assert c["status"][1] == oracle.INFEASIBLE and c["offsets"][2] == c["offsets"][1]
+    assert c["status"][0] == oracle.FIXPOINT and list(c["var"][:c["offsets"][1]]) == [0]
