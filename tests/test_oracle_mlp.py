@@ -191,3 +191,23 @@ def test_bf16_flip_rows():
     X[0, 0] = 1.0 + 2.0 ** -8
     X[1, 0] = 1.0
     np.testing.assert_array_equal(mlp.bf16_flip_rows(theta, X), [True, False])
+
+
+def test_standardize_closed_form():
+    """Population standardisation: a feature column (0, 2) has mean 1 and standard deviation 1,
+    so it becomes (-1, 1) (the sample deviation sqrt(2) would give -0.707, 0.707)."""
+    F = np.zeros((2, 16))
+    F[:, 0] = [0.0, 2.0]
+    S = mlp.standardize(F)
+    np.testing.assert_array_equal(S[:, 0], [-1.0, 1.0])
+    assert np.all(S[:, 1:] == 0)
+
+
+def test_binary_flag_and_range_cap():
+    """Feature 6 (binary) needs an integer variable with range at most 1: a continuous variable
+    in [0, 1] has 0; feature 5 is log(1 + range) with the range capped at 1e9, also for a finite
+    range of 1e12."""
+    p = milp_from_dense([[1.0, 1.0, 1.0]], [5.0], [0, 0, 0], [1, 1, 1e12], [1, 0, 1])
+    F = mlp.raw_features(p, [0.5, 0.5, 3.0], [0, 0, 0], [1, 1, 1e12], [0, 1, 2])
+    assert list(F[:, 6]) == [1.0, 0.0, 0.0]
+    assert F[2, 5] == math.log1p(1e9)
