@@ -1,0 +1,55 @@
+"""The binding's ctypes structures mirror the C structs of include/gpubp.h field by field (name,
+order and type), so a field added to one side alone fails here, without a GPU."""
+import os
+import re
+
+import ctypes as C
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+CTYPE = {"int32_t": C.c_int32, "uint32_t": C.c_uint32, "int64_t": C.c_int64, "uint64_t": C.c_uint64,
+         "double": C.c_double, "float": C.c_float}
+
+PAIRS = {"bp_params": "BpParams", "bp_result": "BpResult", "probe_cache": "ProbeCache",
+         "probe_apply_result": "ProbeApplyResult", "bp_tuning": "BpTuning", "bp_tune_report": "BpTuneReport",
+         "fp_params": "FpParams", "fp_cache": "FpCache", "fp_result": "FpResult", "pdhg_params": "PdhgParams",
+         "pdhg_result": "PdhgResult", "ls_params": "LsParams", "ls_result": "LsResult",
+         "ls_obj_params": "LsObjParams", "ls_obj_result": "LsObjResult", "efp_params": "EfpParams",
+         "efp_result": "EfpResult"}
+
+
+def header_structs():
+    text = open(os.path.join(ROOT, "include", "gpubp.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef\s+struct\s*\{(.*?)\}\s*(\w+)\s*;", text, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            m = re.match(r"(const\s+)?([\w]+)\s*(\*?)\s*(\w+)$", decl)
+            assert m, (name, decl)
+            fields.append((m.group(4), m.group(2), bool(m.group(3))))
+        out[name] = fields
+    return out
+
+
+def test_every_header_struct_has_a_mirror():
+    assert set(header_structs()) == set(PAIRS)
+
+
+def test_mirrors_match_field_by_field():
+    import paper_2510_20499_gb300 as pkg
+    hs = header_structs()
+    for cname, pyname in PAIRS.items():
+        py = getattr(pkg, pyname)._fields_
+        assert [f for f, _ in py] == [f for f, _, _ in hs[cname]], cname
+        for (fname, ctype), (_, htype, ptr) in zip(py, hs[cname]):
+            if ptr:
+                assert C.sizeof(ctype) == C.sizeof(C.c_void_p), (cname, fname)
+            elif htype in PAIRS:   # a nested struct: its own mirror
+                assert ctype is getattr(pkg, PAIRS[htype]), (cname, fname, ctype, htype)
+            else:
+                assert ctype._type_ == CTYPE[htype]._type_, (cname, fname, ctype, htype)
+        assert C.sizeof(getattr(pkg, pyname)) > 0
