@@ -1,9 +1,13 @@
 """The binding's ctypes structures mirror the C structs of include/gpubp.h field by field (name,
 order and type), so a field added to one side alone fails here, without a GPU."""
+import ctypes as C
 import os
 import re
+import shutil
+import subprocess
+import tempfile
 
-import ctypes as C
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -53,3 +57,29 @@ def test_mirrors_match_field_by_field():
             else:
                 assert ctype._type_ == CTYPE[htype]._type_, (cname, fname, ctype, htype)
         assert C.sizeof(getattr(pkg, pyname)) > 0
+
+
+def test_c_layout_equals_the_mirrors():
+    """A C program compiled against the header prints every field's offset and every struct's
+    size; the ctypes mirrors have the same layout (padding and widths included)."""
+    import paper_2510_20499_gb300 as pkg
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    hs = header_structs()
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "gpubp.h"', "int main(void) {"]
+    for cname in PAIRS:
+        lines.append(f'printf("{cname} . %zu\\n", sizeof({cname}));')
+        for fname, _, _ in hs[cname]:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0; }")
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        open(src, "w").write("\n".join(lines))
+        subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    for line in filter(None, out):
+        cname, fname, val = line.split()
+        cls = getattr(pkg, PAIRS[cname])
+        want = C.sizeof(cls) if fname == "." else getattr(cls, fname).offset
+        assert int(val) == want, (cname, fname, int(val), want)
