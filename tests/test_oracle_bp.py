@@ -376,3 +376,19 @@ def test_continuous_threshold_uses_at_least_one():
     p = milp_from_dense([[1.0]], [0.4985], lb, ub, [0])
     ol, ou, r, _ = oracle.Problem(p).bp(lb, ub)
     assert ou[0] == 0.4985
+
+
+def test_first_infeasible_indices_are_the_smallest():
+    """When several variables cross (or rows are infeasible) in the same round, the result
+    reports the smallest index.  Variables: x0, x1 integer in [0, 1], z, w continuous in [0, 1];
+    rows -x - z <= -2 give x >= 1 and x + w <= 0.5 give x <= 0 for both x0 and x1 in round 0,
+    with every row feasible: both cross, the first infeasible variable is 0.  Rows -x1 <= -2 and
+    -x0 <= -2 (x0, x1 in [0, 1]) are both infeasible in round 0: the first infeasible row is 0."""
+    A = [[-1, 0, -1, 0], [1, 0, 0, 1], [0, -1, -1, 0], [0, 1, 0, 1]]
+    lb, ub = np.zeros(4), np.ones(4)
+    p = milp_from_dense(A, [-2, 0.5, -2, 0.5], lb, ub, [1, 1, 0, 0])
+    _, _, r, _ = oracle.Problem(p).bp(lb, ub)
+    assert (r["status"], r["rounds"], r["first_infeasible_var"], r["first_infeasible_row"]) == (oracle.INFEASIBLE, 1, 0, -1)
+    p = milp_from_dense([[0, -1], [-1, 0]], [-2, -2], np.zeros(2), np.ones(2), [1, 1])
+    _, _, r, _ = oracle.Problem(p).bp(np.zeros(2), np.ones(2))
+    assert (r["status"], r["first_infeasible_row"], r["first_infeasible_var"]) == (oracle.INFEASIBLE, 0, -1)
